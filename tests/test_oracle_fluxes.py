@@ -1,0 +1,193 @@
+"""Pins of the oracle's point fluxes and wall model.
+
+Numerical fluxes: consistency, symmetry of the two-point flux and Roe's
+property A~ (UR - UL) = F(UR) - F(UL) (paper Sec. 4: Roe solver with
+Harten's entropy fix).  Wall model (paper Sec. 3.2 and Algorithms 1-2):
+Spalding's law as printed, the Reichardt law's limits, the Newton solve of
+SolveWallStress, and the Van Driest transform against its defining
+integral."""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate, optimize
+
+from paper_2606_18927_gb300 import inputs as I
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _state(rho, u, p, gamma=1.4):
+    u = np.asarray(u, dtype=float)
+    return np.array([rho, *(rho * u), p / (gamma - 1) + 0.5 * rho * u @ u])
+
+
+def _euler_flux(U, n, gamma=1.4):
+    rho = U[0]; u = U[1:4] / rho; p = (gamma - 1) * (U[4] - 0.5 * rho * u @ u)
+    un = u @ n
+    return np.array([rho * un, *(rho * un * u + p * n), (U[4] + p) * un])
+
+
+def _rand_unit(rng):
+    v = rng.normal(size=3)
+    return v / np.linalg.norm(v)
+
+
+@pytest.mark.parametrize("vol", [0, 1])
+@pytest.mark.parametrize("kind", [0, 1, 2])
+def test_consistency_and_symmetry(ora, vol, kind):
+    phys = I.phys_params(Ma=0.5)
+    rng = np.random.default_rng(1)
+    for _ in range(20):
+        n = _rand_unit(rng)
+        U = _state(rng.uniform(0.5, 2), rng.normal(size=3), rng.uniform(1, 3))
+        F = ora.riemann(phys, vol, kind, U, U, n)
+        assert np.allclose(F, _euler_flux(U, n), rtol=1e-14, atol=1e-13)
+        V = _state(rng.uniform(0.5, 2), rng.normal(size=3), rng.uniform(1, 3))
+        Fc1 = ora.riemann(phys, vol, 0, U, V, n)
+        Fc2 = ora.riemann(phys, vol, 0, V, U, n)
+        assert np.allclose(Fc1, Fc2, rtol=1e-14, atol=1e-14)
+        # flipping the normal and the sides flips the flux
+        Fa = ora.riemann(phys, vol, kind, U, V, n)
+        Fb = ora.riemann(phys, vol, kind, V, U, -n)
+        assert np.allclose(Fa, -Fb, rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("sign", [1.0, -1.0])
+def test_roe_property_supersonic(ora, sign):
+    # every wave speed beyond the entropy-fix band: |A~| = +-A~, and Roe's
+    # linearisation satisfies A~ dU = dF exactly
+    phys = I.phys_params()
+    rng = np.random.default_rng(2)
+    for _ in range(20):
+        n = _rand_unit(rng)
+        t = np.cross(n, _rand_unit(rng))
+        c = math.sqrt(1.4 * 1.0 / 1.0)
+        UL = _state(rng.uniform(0.8, 1.2), sign * 3.0 * c * n + 0.3 * t, rng.uniform(0.8, 1.2))
+        UR = _state(rng.uniform(0.8, 1.2), sign * 3.2 * c * n - 0.2 * t, rng.uniform(0.8, 1.2))
+        Froe = ora.riemann(phys, 0, 2, UL, UR, n)
+        Fc = ora.riemann(phys, 0, 0, UL, UR, n)
+        dF = _euler_flux(UR, n) - _euler_flux(UL, n)
+        assert np.allclose(Froe - Fc, -0.5 * sign * dF, rtol=1e-12, atol=1e-12)
+
+
+def test_roe_entropy_fix_continuous(ora):
+    # the fixed |lambda| meets |lambda| at the band edge: no jump in the flux
+    phys = I.phys_params()
+    n = np.array([1.0, 0.0, 0.0])
+    c = math.sqrt(1.4)
+    out = []
+    for un in (1.1 * c - 1e-9, 1.1 * c + 1e-9):  # |un - c~| crosses 0.1 c~
+        U = _state(1.0, [un, 0.1, 0.0], 1.0)
+        V = _state(1.0, [un, 0.1, 0.0], 1.0 + 1e-3)
+        out.append(ora.riemann(phys, 0, 2, U, V, n))
+    assert np.abs(out[0] - out[1]).max() < 1e-7
+
+
+def test_llf_dissipation_bounds(ora):
+    # LLF dissipation: the upwind flux of a supersonic pair is bracketed
+    phys = I.phys_params()
+    n = np.array([0.0, 1.0, 0.0])
+    UL = _state(1.0, [0.0, 0.2, 0.0], 1.0)
+    UR = _state(1.1, [0.0, 0.1, 0.0], 1.2)
+    F = ora.riemann(phys, 0, 1, UL, UR, n)
+    Fc = ora.riemann(phys, 0, 0, UL, UR, n)
+    lam = max(0.2 + math.sqrt(1.4 * 1.0 / 1.0), 0.1 + math.sqrt(1.4 * 1.2 / 1.1))
+    assert np.allclose(F - Fc, -0.5 * lam * (UR - UL), rtol=1e-13, atol=1e-14)
+
+
+def _read_golden():
+    vals = {}
+    with open(os.path.join(HERE, "golden", "spalding_paper.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            k, v = line.split()
+            vals[k] = float(v)
+    return vals
+
+
+def test_spalding_as_printed(ora):
+    g = _read_golden()
+    k = g["kappa"]; A = g["exp_minus_kappa_B"]
+    B = -math.log(A) / k  # the B that the printed constant stands for
+    assert abs(B - 5.5) < 1e-3
+    for up in np.linspace(0.0, 30.0, 31):
+        ku = k * up
+        printed = up + A * (math.exp(ku) - 1 - ku - ku ** 2 / 2 - ku ** 3 / 6 - ku ** 4 / 24)
+        assert abs(ora.law_value(0, up, 0.4, 5.5) - printed) <= 5e-5 * max(1.0, printed)
+
+
+def test_reichardt_limits(ora):
+    kap, B = 0.41, 5.2
+    yp = 1e-4
+    assert abs(ora.law_value(1, yp, kap, B) / yp - 1) < 1e-5
+    for yp in (1e5, 1e6):
+        assert abs(ora.law_value(1, yp, kap, B) - (math.log(yp) / kap + B)) < 1e-4
+
+
+@pytest.mark.parametrize("law", [0, 1])
+def test_wall_law_solve(ora, law):
+    kap, B = (0.41, 5.2)
+    h, nu = 0.1, 5e-5
+    for u in np.geomspace(1e-6, 500.0, 40):
+        ut, it = ora.solve_utau(law, u, h, nu, kap, B)
+        assert 0 < it <= 200
+        up, yp = u / ut, h * ut / nu
+        if law == 1:
+            assert abs(up - ora.law_value(1, yp, kap, B)) < 1e-12 * max(1.0, up)
+        else:
+            assert abs(yp - ora.law_value(0, up, kap, B)) < 1e-12 * max(1.0, yp)
+        # independent bracketing root finder on the same law
+        if law == 1:
+            g = lambda x: u / x - ora.law_value(1, h * x / nu, kap, B)
+        else:
+            g = lambda x: h * x / nu - ora.law_value(0, u / x, kap, B)
+        ref = optimize.brentq(g, 1e-12, 1e3, xtol=1e-300, rtol=1e-15, maxiter=500)
+        assert abs(ut - ref) < 1e-13 * ref
+    # viscous sublayer (y+ ~ 0.01): tau_w / rho = nu u / h
+    ut, _ = ora.solve_utau(law, 1e-7, h, nu, kap, B)
+    assert abs(ut * ut - nu * 1e-7 / h) < 1e-3 * nu * 1e-7 / h
+
+
+@pytest.mark.parametrize("law", [0, 1])
+@pytest.mark.parametrize("Ma", [0.1, 0.8])
+def test_wall_flux_van_driest_chain(ora, law, Ma):
+    """tau_w from sample state: Van Driest by quadrature of its definition
+    (u_VD = int_0^u sqrt(rho/rho_w) du' with the adiabatic Crocco-Busemann
+    temperature T(u') = T_w - r u'^2 / (2 c_p)), then the law by bracketing."""
+    phys = I.phys_params(Ma=Ma, Re=20000.0, kappa=0.41, B=5.2, hwm=0.1)
+    g, R, mu, Pr = phys["gamma"], phys["R"], phys["mu"], phys["Pr"]
+    cp = g * R / (g - 1); r = Pr ** (1 / 3)
+    nout = np.array([0.0, -1.0, 0.0])
+    rng = np.random.default_rng(3)
+    for _ in range(6):
+        vel = np.array([rng.uniform(0.2, 1.5), rng.uniform(-0.3, 0.3), rng.uniform(-0.5, 0.5)])
+        rho = rng.uniform(0.9, 1.1); p = phys["p0"] * rng.uniform(0.95, 1.05)
+        U = _state(rho, vel, p)
+        fm, tau, st = ora.wall_flux(phys, law, U, nout)
+        assert st == 0
+        T = p / (rho * R)
+        upar = vel - (vel @ nout) * nout
+        um = np.linalg.norm(upar)
+        Tw = T + r * um ** 2 / (2 * cp)
+        rhow = rho * T / Tw
+        uvd = integrate.quad(lambda s: math.sqrt(Tw / (Tw - r * s * s / (2 * cp))), 0.0, um,
+                             epsabs=0, epsrel=2e-14)[0]
+        nuw = mu / rhow
+        kap, B = 0.41, 5.2
+        if law == 1:
+            gf = lambda x: uvd / x - ora.law_value(1, 0.1 * x / nuw, kap, B)
+        else:
+            gf = lambda x: 0.1 * x / nuw - ora.law_value(0, uvd / x, kap, B)
+        ut = optimize.brentq(gf, 1e-12, 1e3, xtol=1e-300, rtol=1e-15)
+        tw = rhow * ut * ut
+        assert np.allclose(tau, tw * upar / um, rtol=1e-11, atol=1e-16)
+        assert np.allclose(fm, -tau, rtol=0, atol=0)
+        assert abs(tau @ nout) < 1e-15 * tw
+    # low speed: the transform is the identity (a -> 0)
+    U = _state(1.0, [1e-6, 0.0, 0.0], phys["p0"])
+    fm, tau, st = ora.wall_flux(phys, law, U, nout)
+    ut, _ = ora.solve_utau(law, 1e-6, 0.1, mu / 1.0, 0.41, 5.2)
+    assert abs(tau[0] - ut * ut) < 1e-9 * ut * ut
