@@ -1,0 +1,341 @@
+"""Throughput of the GB300 DGSEM operator: DOF-stage updates/s and PID.
+
+One step = one LSERK4 stage (lifting, face fluxes incl. Riemann solver,
+split-form volume integral, surface integral, 1/J scaling and the fused RK
+register update) of the whole mesh.  Default workload: Taylor-Green vortex,
+N = 7, 32^3 affine periodic elements (16.8M DOF), KEP (Pirozzoli) volume
+flux, Roe surface flux, BR1 lifting, FP64 (paper Sec. 2.3 measures the PID of
+the N = 7 split-form DGSEM; Eq. for PID: wall time / (DOF * stages)).
+
+Launch: python bench.py [--gpus N --steps K --warmup W] [--precision fp64|fp32]
+        [--impl ours|reference]
+Under torchrun every rank runs an independent replica of the workload on its
+own GPU (the single-GPU operator has no collective); value = DOF-stage
+updates of all ranks / max time over ranks ("scaling": "weak").
+
+--impl reference times the plain FP64 CPU oracle (the reference arm) on the
+host cores on a bounded sample of the same workload (N = 7, 8^3 elements).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DOF-stage updates/s (PID ns/DOF) at N=7"
+UNIT = "DOF-stage/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP64 pipe of a GB300 SM: 2 DFMA per clock per SM (1 instruction/clock per
+# 16 lanes); 152 SMs at the 2070 MHz maximum clock: 152 * 2 * 2 * 2.07e9.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def algorithmic_flops_per_dof(N, kernel, viscous=True, surf="roe"):
+    """Algorithmic FP64 flops per DOF and operator evaluation (FMA = 2).
+
+    Counted on the formulas of the operator, independent of how a kernel
+    schedules them (each unordered two-point pair once, as the split form
+    with a symmetric flux allows)."""
+    n = N + 1
+    if kernel == "volume":
+        pairs = 3 * N / 2.0                     # unordered pairs per node, 3 directions
+        pair = 6 + 3 + 5 + 1 + 9 + 1 + 20       # averages, metric sum, u.a, m, F_m, F_E, 2 x 5 FMA
+        prim = 13                               # 1/rho, u, |u|^2, p, h
+        surf_int = (6.0 / n) * 5 * 2            # face nodes per DOF x 5 FMA
+        return pairs * pair + prim + (4 if viscous else 0) + surf_int + 5 + 20
+    if kernel == "lift":
+        if not viscous:
+            return 0.0
+        return 13 + (6.0 / n) * 13 + 24 * n + 60 + (6.0 / n) * 24 + 12 + 50 + 60 + 24 * n
+    if kernel == "face":
+        per_node = 26 + 25 + (80 if surf == "roe" else 12) + 8 + 10
+        return (3.0 / n) * per_node
+    return 0.0
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1])); mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(mx)) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def build_case(wl_name, precision, lgl):
+    from paper_2606_18927_gb300 import inputs as I
+    wl = I.workload(wl_name)
+    x, _ = lgl(wl.spec.N)
+    X = I.node_coordinates(wl.spec, x)
+    nbr = I.connectivity(wl.spec)
+    U = I.initial_state(wl, X)
+    return wl, X, nbr, U
+
+
+def cpu_reference_run(steps, warmup, sample_elems=8, budget_s=None):
+    """Oracle timing on the host cores: RK stages on an N = 7, sample^3
+    element TGV box (same per-DOF work as the 32^3 workload)."""
+    import oracle
+    from paper_2606_18927_gb300 import inputs as I
+    wl = I.workload("tgv_n7_32", elems=(sample_elems,) * 3)
+    x, w, D = oracle.lgl(wl.spec.N)
+    X = I.node_coordinates(wl.spec, x)
+    nbr = I.connectivity(wl.spec)
+    U = I.initial_state(wl, X)
+    o = oracle.Oracle(wl.spec.N, X, nbr, wl.phys, vol_flux=wl.vol_flux, surf_flux=wl.surf_flux)
+    cores = oracle.max_threads()
+    dt = o.dt(U, 0.9)
+    dU = np.zeros_like(U)
+    Uc = U.copy()
+    for s in range(warmup):
+        o.rk_stage(Uc, dU, s % 5, 0.0, dt)
+    t0 = time.perf_counter()
+    done = 0
+    for s in range(steps):
+        o.rk_stage(Uc, dU, s % 5, 0.0, dt)
+        done += 1
+        if budget_s is not None and time.perf_counter() - t0 > budget_s:
+            break
+    el = time.perf_counter() - t0
+    dofs = wl.spec.dofs
+    return {"value": dofs * done / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "N=7 TGV on %d^3 elements (%d DOF), %d RK stages, Roe/KEP/BR1, FP64, %d OpenMP threads"
+                      % (sample_elems, dofs, done, cores),
+            "seconds": el, "stages": done, "dofs": dofs}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    r = cpu_reference_run(args.steps, args.warmup, budget_s=None)
+    ms = 1e3 * r["seconds"] / r["stages"]
+    line = {
+        "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": args.gpus, "steps": r["stages"],
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "tgv_n7 (CPU oracle sample: N=7, 8^3 elements)", "N": 7,
+                   "elements": [8, 8, 8], "dofs": r["dofs"], "surf_flux": "roe", "vol_flux": "kep_pirozzoli",
+                   "pid_ns": 1e9 / r["value"]},
+        "impl": "reference",
+        "cpu_baseline": {k: r[k] for k in ("value", "unit", "cores", "kind", "sample")},
+        "e2e": {"value": r["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+    from paper_2606_18927_gb300 import dg
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    precision = dg.FP32_MIXED if args.precision == "fp32" else dg.FP64
+    wl, X, nbr, U = build_case(args.workload, precision, dg.lgl_nodes)
+    stream = torch.cuda.current_stream()
+    free0 = torch.cuda.mem_get_info()[0]
+    op = dg.Operator(wl.spec.N, X, nbr, wl.phys, precision=precision, vol_flux=wl.vol_flux,
+                     surf_flux=wl.surf_flux, viscous=wl.viscous, law=wl.law, stream=stream)
+    Ud = torch.from_numpy(U).cuda()
+    op.set_state(Ud)
+    footprint = free0 - torch.cuda.mem_get_info()[0]
+    dofs = wl.spec.dofs
+    # explicit time step from the CFL rule (value irrelevant to throughput)
+    dt = 1e-4
+    for s in range(args.warmup):
+        op.rk_stage(s % 5, 0.0, dt)
+    torch.cuda.synchronize()
+    op.check_status()
+
+    # ---- timed region: K stages on device-resident data
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    op.profile_enable(True)
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for s in range(args.steps):
+        op.rk_stage(s % 5, 0.0, dt)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms_total = e0.elapsed_time(e1)
+    prof = op.profile_read()
+    op.profile_enable(False)
+    clk = clocks.stop()
+    op.check_status()
+    if dist:
+        t = torch.tensor([ms_total], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    value = world * dofs * args.steps / (ms_total * 1e-3)
+
+    # ---- end to end through the public API with host buffers
+    Uh = torch.from_numpy(U).pin_memory()
+    e2e_steps = max(3, min(args.steps, 20))
+    for s in range(2):
+        op.set_state(Uh.numpy()); op.rk_stage(0, 0.0, dt); op.get_state(Uh.numpy())
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for s in range(e2e_steps):
+        op.set_state(Uh.numpy())       # host -> device copy of the step's input
+        op.rk_stage(0, 0.0, dt)
+        op.get_state(Uh.numpy())       # device -> host copy of the step's result
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * dofs * e2e_steps / e2e_s
+    nbytes = U.nbytes
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    # ---- roofline of the dominant kernel
+    kernels = {}
+    for k, (ms, cnt) in prof.items():
+        if cnt:
+            flops = algorithmic_flops_per_dof(wl.spec.N, k, bool(wl.viscous), "roe" if wl.surf_flux == 2 else "llf")
+            avg = ms / cnt
+            kernels[k] = {"ms_per_launch": avg, "launches": cnt, "share": ms / max(ms_total, 1e-30),
+                          "flops_per_dof": flops,
+                          "achieved_tflops": flops * dofs / (avg * 1e-3) / 1e12 if flops else None}
+    dom = max(kernels, key=lambda k: kernels[k]["ms_per_launch"] * kernels[k]["launches"])
+    peaks = load_peaks()
+    if precision == dg.FP64:
+        achieved = kernels[dom]["achieved_tflops"]
+        roof = {"bound": "alu", "kernel": "k_" + dom, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS if achieved else None,
+                "traffic": None,
+                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 pipe)"}
+    else:
+        hbm = peaks.get("hbm_gbs", 6800.0)
+        roof = {"bound": "hbm", "kernel": "k_" + dom, "achieved": None, "peak": hbm, "unit": "GB/s",
+                "frac": None, "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
+    launches_per_step = sum(1 for k in kernels)
+    # CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only)
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        r = cpu_reference_run(10 ** 6, 1, sample_elems=8, budget_s=args.cpu_seconds)
+        cpu = {k: r[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if precision == dg.FP64 else "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": wl.name, "N": wl.spec.N, "elements": [wl.spec.nx, wl.spec.ny, wl.spec.nz],
+                   "dofs": dofs, "precision": args.precision, "vol_flux": "kep_pirozzoli",
+                   "surf_flux": {0: "central", 1: "llf", 2: "roe"}[wl.surf_flux], "lifting": "br1",
+                   "pid_ns": 1e9 / (value / world), "l2": "inputs larger than L2 (U alone %.0f MB)" % (nbytes / 1e6),
+                   "footprint_gb": footprint / 1e9, "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": roof,
+        "kernels": kernels,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+                "steps": e2e_steps},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk,
+    }
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
+    ap.add_argument("--workload", default="tgv_n7_32")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,162 @@
+/*
+ * dg.h -- C ABI of the GB300 DGSEM operator library (libdg_gb300.so).
+ *
+ * The library evaluates the semi-discrete time derivative Ut = DG_Operator(U)
+ * of the 3D compressible Navier-Stokes equations with the split-form
+ * discontinuous Galerkin spectral element method on Legendre-Gauss-Lobatto
+ * nodes (paper Sec. 2.2 "split-form DG scheme"; Sec. 4 "split DGSE
+ * formulation"), and advances it with the five-stage fourth-order low-storage
+ * Runge-Kutta scheme (paper Sec. 4).  The operator is:
+ *   - BR1 lifting of the primitive gradients grad(u, v, w, T);
+ *   - the kinetic-energy-preserving two-point volume flux differencing on
+ *     curvilinear hexahedra (curl-form metrics);
+ *   - the Riemann (central / local Lax-Friedrichs / Roe with Harten's entropy
+ *     fix, Sec. 4) and BR1 viscous surface fluxes, with the equilibrium
+ *     wall-stress model on slip walls (Sec. 3.1-3.2, Algorithms 1-2:
+ *     Van Driest transform, Spalding or Reichardt law, Newton solve);
+ *   - the surface integral, the 1/J scaling and a constant body force.
+ *
+ * Conventions shared by every entry point
+ *   - Return value: 0 (DG_OK) or a negative DG_ERR_* code; the message of the
+ *     last error of a context is returned by dg_last_error().
+ *   - Field layout ("SoA"): double U[5][K][n^3], n = N + 1, variable v in
+ *     (rho, rho u, rho v, rho w, E), node p = i + n (j + n k) of element e.
+ *   - Ownership: the context owns all device storage (mesh, metrics, state,
+ *     scratch).  Caller pointers are borrowed for the duration of the call
+ *     only.  "on_device" arguments say whether a caller pointer is a device
+ *     pointer (1) or a host pointer (0); host pointers may be pageable or
+ *     pinned.
+ *   - Stream: every device operation of a context is enqueued on the stream
+ *     given to dg_init_mesh / dg_set_stream (a cudaStream_t, 0 = legacy
+ *     default stream).  Calls that return results to the host synchronise
+ *     that stream; the others are asynchronous.
+ *   - Errors never trap or hang the GPU: device-side failures (non-finite
+ *     state, wall-model Newton without convergence) set flags that the host
+ *     reads with dg_check_status().
+ */
+#ifndef DG_GB300_H
+#define DG_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum dg_status_code {
+  DG_OK = 0,
+  DG_ERR_ARG = -1,             /* invalid argument (null pointer, bad enum, bad size) */
+  DG_ERR_NOT_INIT = -2,        /* state not set before use */
+  DG_ERR_MESH = -3,            /* non-positive Jacobian, non-matching faces, bad neighbour */
+  DG_ERR_CUDA = -4,            /* CUDA runtime error (message has the CUDA error string) */
+  DG_ERR_NONFINITE = -5,       /* a non-finite value appeared in the state */
+  DG_ERR_WM_NOCONV = -6,       /* wall-model Newton iteration did not converge */
+  DG_ERR_DEVICE_BOUNDS = -7,   /* device index check failed (debug builds) */
+  DG_ERR_NOT_IMPLEMENTED = -8, /* option combination not available */
+  DG_ERR_OOM = -9              /* device allocation failed */
+};
+
+enum dg_precision { DG_FP64 = 0, DG_FP32_MIXED = 1 };
+enum dg_vol_flux { DG_VOL_KEP_PIROZZOLI = 0, DG_VOL_KEP_KENNEDY_GRUBER = 1 };
+enum dg_surf_flux { DG_SURF_CENTRAL = 0, DG_SURF_LLF = 1, DG_SURF_ROE = 2 };
+enum dg_wall_law { DG_LAW_SPALDING = 0, DG_LAW_REICHARDT = 1 };
+
+/* Neighbour code of a wall-modelled slip wall in dg_mesh_desc.nbr. */
+#define DG_BC_WALL (-1)
+
+typedef struct dg_ctx dg_ctx;
+
+/* Mesh of K hexahedra of degree N (paper Sec. 2.2: tensor-product LGL nodes).
+ *   X   host, double[3][K][n^3]: node coordinates at the LGL nodes returned by
+ *       dg_lgl_nodes (degree-N geometry).  Copied during dg_init_mesh.
+ *   nbr host, int[K][6]: neighbour across local face l (0 -xi, 1 +xi, 2 -eta,
+ *       3 +eta, 4 -zeta, 5 +zeta).  A neighbour e' must list e across face
+ *       l^1 and share its face nodes in the same order (faces may differ by
+ *       one translation: periodic images).  DG_BC_WALL marks a slip wall
+ *       with the wall model.  Copied during dg_init_mesh. */
+typedef struct {
+  int N;
+  int K;
+  const double* X;
+  const int* nbr;
+} dg_mesh_desc;
+
+/* Ideal gas and wall-model constants (paper Sec. 4: ideal gas; Sec. 3.2:
+ * law of the wall).  mu is constant; kappa and B are the law's constants;
+ * hwm the sampling distance of the wall model; force a constant body force
+ * per unit volume entering momentum (and its work f.u the energy). */
+typedef struct {
+  double gamma, R, mu, Pr;
+  double force[3];
+  double kappa, B, hwm;
+  int law; /* dg_wall_law */
+} dg_phys;
+
+typedef struct {
+  int precision; /* dg_precision */
+  int vol_flux;  /* dg_vol_flux */
+  int surf_flux; /* dg_surf_flux */
+  int viscous;   /* 1: Navier-Stokes (lifting + viscous fluxes), 0: Euler */
+} dg_options;
+
+/* LGL nodes xi[n] and weights w[n] on [-1, 1] (host arrays of N + 1 doubles).
+ * 1 <= N <= 8. */
+int dg_lgl_nodes(int N, double* xi, double* w);
+
+/* Builds the geometry (curl-form metrics, Jacobians, face normals, wall-model
+ * sampling points) on the host, validates it, allocates the device storage
+ * and uploads it.  stream: cudaStream_t (may be 0).  On success *out owns
+ * everything; free it with dg_destroy.  Errors: DG_ERR_ARG, DG_ERR_MESH,
+ * DG_ERR_OOM, DG_ERR_CUDA (the message is then available through
+ * dg_last_error(NULL)). */
+int dg_init_mesh(dg_ctx** out, const dg_mesh_desc* m, const dg_phys* p, const dg_options* o,
+                 void* stream);
+int dg_destroy(dg_ctx* c);
+
+/* Last error message of c (or of the last failed dg_init_mesh if c is NULL). */
+const char* dg_last_error(const dg_ctx* c);
+
+int dg_set_stream(dg_ctx* c, void* stream);
+
+/* Sizes: number of elements, nodes per element and total doubles of U. */
+int dg_sizes(const dg_ctx* c, int* N, int* K, long long* n_state);
+
+/* Copies U (5 K n^3 doubles) into / out of the context's state. */
+int dg_set_state(dg_ctx* c, const double* U, int on_device);
+int dg_get_state(dg_ctx* c, double* U, int on_device);
+
+/* Ut = DG_Operator(U) at time t (paper Sec. 2.2 / Sec. 4).  U: caller
+ * array, or NULL for the context's state.  Ut: caller array (5 K n^3).
+ * Both on the device or both on the host as on_device says. */
+int dg_time_derivative(dg_ctx* c, const double* U, double* Ut, double t, int on_device);
+
+/* One LSERK4 stage s (0..4) of the context's state (Carpenter-Kennedy
+ * five-stage fourth-order 2N-storage scheme, paper Sec. 4):
+ *   dU = A_s dU + dt Ut(U, t + c_s dt);  U = U + B_s dU.
+ * A_0 = 0, so a step (s = 0..4) needs no reset of dU.  The volume kernel
+ * applies the update in registers, in place. */
+int dg_rk_stage(dg_ctx* c, int s, double t, double dt);
+
+/* nsteps full LSERK4 steps from time t. */
+int dg_rk_steps(dg_ctx* c, double t, double dt, int nsteps);
+
+/* Reads and clears the device status flags.  Returns DG_OK,
+ * DG_ERR_NONFINITE or DG_ERR_WM_NOCONV (synchronises the stream). */
+int dg_check_status(dg_ctx* c);
+
+/* Per-kernel timing with CUDA events on the context's stream (tracing).
+ * dg_profile_enable(c, 1) records events around the lift, face, wall and
+ * volume kernels of every subsequent operator evaluation; dg_profile_read
+ * synchronises the stream, returns the summed milliseconds ms[4] and the
+ * launch counts launches[4] (order: lift, face, wall, volume) since the last
+ * read, and resets them. */
+int dg_profile_enable(dg_ctx* c, int enable);
+int dg_profile_read(dg_ctx* c, double* ms, int* launches);
+
+/* Host copies of the geometry (for checking): Ja[K][n^3][3 dir][3 comp],
+ * J[K][n^3]. */
+int dg_get_metrics(const dg_ctx* c, double* Ja, double* J);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DG_GB300_H */

@@ -1,0 +1,376 @@
+// api.cu -- C ABI of the GB300 DGSEM library (declared in include/dg.h).
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/dg.h"
+#include "geometry.h"
+#include "kernels.cuh"
+#include "ops.h"
+
+// Five-stage fourth-order 2N-storage Runge-Kutta scheme of Carpenter and
+// Kennedy (1994), the low-storage scheme of paper Sec. 4.  These are the
+// published rational coefficients.
+static const double kRkA[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
+                               -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
+static const double kRkB[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+                               1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+                               2277821191437.0 / 14882151754819.0};
+static const double kRkC[5] = {0.0, 1432997174477.0 / 9575080441755.0, 2526269341429.0 / 6820363962896.0,
+                               2006345519317.0 / 3224310063776.0, 2802321613138.0 / 2924317926251.0};
+
+struct dg_ctx {
+  int N = 0, n = 0, n2 = 0, n3 = 0, K = 0, F = 0;
+  size_t S = 0;  // K n^3
+  dg_phys phys{};
+  dg_options opts{};
+  dg::PhysDev ph{};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  dg::Geometry geo;
+  // device storage
+  double* U = nullptr;
+  double* dU = nullptr;
+  double* io = nullptr;   // staging of a host input
+  double* io2 = nullptr;  // staging of a host output
+  void* Ja = nullptr;
+  void* invJ = nullptr;
+  double* fgeo = nullptr;
+  int* nbr = nullptr;
+  int* elem_face = nullptr;
+  int4* faces = nullptr;
+  int* ws_elem = nullptr;
+  double* ws_lag = nullptr;
+  void* Rv = nullptr;
+  void* Gf = nullptr;
+  void* Fs = nullptr;
+  double* tau = nullptr;
+  int* status = nullptr;
+  bool state_set = false;
+  std::string err;
+  // optional per-kernel timing: 5 events per operator evaluation
+  bool profiling = false;
+  std::vector<cudaEvent_t> events;
+  size_t events_used = 0;
+};
+
+static std::string g_init_error;
+
+namespace {
+
+int fail(dg_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg; else g_init_error = msg;
+  return code;
+}
+
+int cuda_fail(dg_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, e == cudaErrorMemoryAllocation ? DG_ERR_OOM : DG_ERR_CUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+template <typename T>
+cudaError_t alloc(T** p, size_t count) {
+  if (count == 0) { *p = nullptr; return cudaSuccess; }
+  return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+}
+
+void free_all(dg_ctx* c) {
+  for (cudaEvent_t ev : c->events) cudaEventDestroy(ev);
+  c->events.clear();
+  void* ptrs[] = {c->U, c->dU, c->io, c->io2, c->Ja, c->invJ, c->fgeo, c->nbr, c->elem_face, c->faces,
+                  c->ws_elem, c->ws_lag, c->Rv, c->Gf, c->Fs, c->tau, c->status};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+}
+
+int launch(dg_ctx* c, const double* Uin, int mode, double* Out, double A, double B, double dt, int read_dU,
+           double* Uout) {
+  dg::OpArgs a{};
+  a.N = c->N; a.K = c->K; a.F = c->F; a.n_interior = c->geo.n_interior; a.n_wall = c->geo.n_wall;
+  a.fp32 = c->opts.precision == DG_FP32_MIXED;
+  a.Ja = c->Ja; a.invJ = c->invJ; a.fgeo = c->fgeo; a.nbr = c->nbr; a.elem_face = c->elem_face;
+  a.faces = c->faces; a.ws_elem = c->ws_elem; a.ws_lag = c->ws_lag;
+  a.D = c->geo.basis.D.data(); a.w = c->geo.basis.w.data();
+  a.Uin = Uin; a.Rv = c->Rv; a.Gf = c->Gf; a.Fs = c->Fs; a.tau = c->tau; a.status = c->status;
+  a.mode = mode; a.Out = Out; a.dU = c->dU; a.Uout = Uout;
+  a.A = A; a.B = B; a.dt = dt; a.read_dU = read_dU;
+  a.ev = nullptr;
+  if (c->profiling) {
+    if (c->events_used + 5 > c->events.size()) {
+      for (int x = 0; x < 5 * 64; ++x) {
+        cudaEvent_t ev;
+        cudaError_t e = cudaEventCreate(&ev);
+        if (e != cudaSuccess) return cuda_fail(c, e, "profiling events");
+        c->events.push_back(ev);
+      }
+    }
+    a.ev = &c->events[c->events_used];
+    c->events_used += 5;
+  }
+  int rc = dg::run_operator(a, c->ph, c->stream);
+  if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "kernel launch");
+  return DG_OK;
+}
+
+}  // namespace
+
+namespace dg {
+int run_operator(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {
+  switch (a.N) {
+    case 1: return run_operator_n1(a, ph, s);
+    case 2: return run_operator_n2(a, ph, s);
+    case 3: return run_operator_n3(a, ph, s);
+    case 4: return run_operator_n4(a, ph, s);
+    case 5: return run_operator_n5(a, ph, s);
+    case 6: return run_operator_n6(a, ph, s);
+    case 7: return run_operator_n7(a, ph, s);
+    case 8: return run_operator_n8(a, ph, s);
+    default: return (int)cudaErrorInvalidValue;
+  }
+}
+}  // namespace dg
+
+extern "C" {
+
+int dg_lgl_nodes(int N, double* xi, double* w) {
+  if (N < 1 || N > 8 || !xi || !w) return fail(nullptr, DG_ERR_ARG, "dg_lgl_nodes: need 1 <= N <= 8 and arrays");
+  dg::Basis b = dg::make_basis(N);
+  std::memcpy(xi, b.x.data(), sizeof(double) * (N + 1));
+  std::memcpy(w, b.w.data(), sizeof(double) * (N + 1));
+  return DG_OK;
+}
+
+const char* dg_last_error(const dg_ctx* c) { return c ? c->err.c_str() : g_init_error.c_str(); }
+
+int dg_init_mesh(dg_ctx** out, const dg_mesh_desc* m, const dg_phys* p, const dg_options* o, void* stream) {
+  if (!out || !m || !p || !o) return fail(nullptr, DG_ERR_ARG, "dg_init_mesh: null argument");
+  *out = nullptr;
+  if (m->N < 1 || m->N > 8) return fail(nullptr, DG_ERR_ARG, "dg_init_mesh: N must be in 1..8");
+  if (m->K < 1 || !m->X || !m->nbr) return fail(nullptr, DG_ERR_ARG, "dg_init_mesh: empty mesh");
+  if (o->precision != DG_FP64 && o->precision != DG_FP32_MIXED)
+    return fail(nullptr, DG_ERR_ARG, "dg_init_mesh: bad precision");
+  if (o->vol_flux < 0 || o->vol_flux > 1) return fail(nullptr, DG_ERR_ARG, "dg_init_mesh: bad vol_flux");
+  if (o->surf_flux < 0 || o->surf_flux > 2) return fail(nullptr, DG_ERR_ARG, "dg_init_mesh: bad surf_flux");
+  if (p->law < 0 || p->law > 1) return fail(nullptr, DG_ERR_ARG, "dg_init_mesh: bad wall law");
+  if (!(p->gamma > 1.0) || !(p->R > 0.0) || !(p->mu >= 0.0) || !(p->Pr > 0.0))
+    return fail(nullptr, DG_ERR_ARG, "dg_init_mesh: bad gas constants");
+  dg_ctx* c = new dg_ctx();
+  c->N = m->N; c->n = m->N + 1; c->n2 = c->n * c->n; c->n3 = c->n2 * c->n; c->K = m->K;
+  c->S = (size_t)c->K * c->n3;
+  c->phys = *p; c->opts = *o;
+  c->stream = static_cast<cudaStream_t>(stream);
+  std::string gerr = dg::build_geometry(c->geo, c->N, c->K, m->X, m->nbr, p->hwm);
+  if (!gerr.empty()) { delete c; return fail(nullptr, DG_ERR_MESH, "dg_init_mesh: " + gerr); }
+  if (c->geo.n_wall > 0 && o->viscous && !(p->hwm > 0.0)) {
+    delete c;
+    return fail(nullptr, DG_ERR_ARG, "dg_init_mesh: wall faces need hwm > 0");
+  }
+  c->F = (int)c->geo.faces.size();
+  // physics constants for the kernels
+  dg::PhysDev& ph = c->ph;
+  ph.gamma = p->gamma; ph.gm1 = p->gamma - 1.0; ph.R = p->R; ph.mu = p->mu; ph.Pr = p->Pr;
+  ph.cp = p->gamma * p->R / (p->gamma - 1.0); ph.kcond = p->mu * ph.cp / p->Pr; ph.rcp_R = 1.0 / p->R;
+  for (int d = 0; d < 3; ++d) ph.f[d] = p->force[d];
+  ph.kappa = p->kappa; ph.B = p->B; ph.hwm = p->hwm; ph.law = p->law;
+  ph.vol_flux = o->vol_flux; ph.surf_flux = o->surf_flux; ph.viscous = o->viscous ? 1 : 0;
+  cudaGetDevice(&c->device);
+  // device storage
+  const size_t S = c->S, n2 = c->n2;
+  const bool f32 = o->precision == DG_FP32_MIXED;
+  const size_t rs = f32 ? sizeof(float) : sizeof(double);
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+  chk(alloc(&c->U, 5 * S));
+  chk(alloc(&c->dU, 5 * S));
+  chk(alloc(&c->io, 5 * S));
+  chk(alloc(&c->io2, 5 * S));
+  chk(cudaMalloc(&c->Ja, 9 * S * rs));
+  chk(cudaMalloc(&c->invJ, S * rs));
+  chk(alloc(&c->fgeo, 4 * (size_t)c->F * n2));
+  chk(alloc(&c->nbr, 6 * (size_t)c->K));
+  chk(alloc(&c->elem_face, 6 * (size_t)c->K));
+  chk(alloc(&c->faces, (size_t)c->F));
+  chk(alloc(&c->ws_elem, (size_t)c->geo.n_wall * n2));
+  chk(alloc(&c->ws_lag, (size_t)c->geo.n_wall * n2 * 3 * c->n));
+  chk(alloc(&c->tau, (size_t)c->geo.n_wall * n2 * 3));
+  chk(cudaMalloc(&c->Rv, (o->viscous ? 4 * S : 1) * rs));
+  chk(cudaMalloc(&c->Gf, (o->viscous ? 24 * (size_t)c->K * n2 : 1) * rs));
+  chk(cudaMalloc(&c->Fs, 5 * (size_t)c->F * n2 * rs));
+  chk(alloc(&c->status, 1));
+  if (e != cudaSuccess) { free_all(c); delete c; return cuda_fail(nullptr, e, "dg_init_mesh: allocation"); }
+  // uploads (metrics transposed to [9][S], comp-major for coalesced loads)
+  {
+    std::vector<double> ja(9 * S), ij(S);
+    for (size_t x = 0; x < S; ++x) {
+      for (int cc = 0; cc < 9; ++cc) ja[cc * S + x] = c->geo.Ja[x * 9 + cc];
+      ij[x] = 1.0 / c->geo.J[x];
+    }
+    if (f32) {
+      std::vector<float> ja32(ja.begin(), ja.end()), ij32(ij.begin(), ij.end());
+      chk(cudaMemcpy(c->Ja, ja32.data(), ja32.size() * sizeof(float), cudaMemcpyHostToDevice));
+      chk(cudaMemcpy(c->invJ, ij32.data(), ij32.size() * sizeof(float), cudaMemcpyHostToDevice));
+    } else {
+      chk(cudaMemcpy(c->Ja, ja.data(), ja.size() * sizeof(double), cudaMemcpyHostToDevice));
+      chk(cudaMemcpy(c->invJ, ij.data(), ij.size() * sizeof(double), cudaMemcpyHostToDevice));
+    }
+  }
+  chk(cudaMemcpy(c->fgeo, c->geo.fgeo.data(), c->geo.fgeo.size() * sizeof(double), cudaMemcpyHostToDevice));
+  chk(cudaMemcpy(c->nbr, c->geo.nbr.data(), c->geo.nbr.size() * sizeof(int), cudaMemcpyHostToDevice));
+  chk(cudaMemcpy(c->elem_face, c->geo.elem_face.data(), c->geo.elem_face.size() * sizeof(int),
+                 cudaMemcpyHostToDevice));
+  {
+    std::vector<int4> fc(c->F);
+    for (int f = 0; f < c->F; ++f) {
+      const dg::Face& x = c->geo.faces[f];
+      fc[f] = make_int4(x.eM, x.lM, x.eS, x.lS);
+    }
+    if (c->F) chk(cudaMemcpy(c->faces, fc.data(), fc.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  }
+  if (c->geo.n_wall) {
+    chk(cudaMemcpy(c->ws_elem, c->geo.ws_elem.data(), c->geo.ws_elem.size() * sizeof(int), cudaMemcpyHostToDevice));
+    chk(cudaMemcpy(c->ws_lag, c->geo.ws_lag.data(), c->geo.ws_lag.size() * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  chk(cudaMemset(c->status, 0, sizeof(int)));
+  chk(cudaMemset(c->dU, 0, 5 * S * sizeof(double)));
+  if (e != cudaSuccess) { free_all(c); delete c; return cuda_fail(nullptr, e, "dg_init_mesh: upload"); }
+  *out = c;
+  return DG_OK;
+}
+
+int dg_destroy(dg_ctx* c) {
+  if (!c) return DG_ERR_ARG;
+  cudaStreamSynchronize(c->stream);
+  free_all(c);
+  delete c;
+  return DG_OK;
+}
+
+int dg_set_stream(dg_ctx* c, void* stream) {
+  if (!c) return DG_ERR_ARG;
+  c->stream = static_cast<cudaStream_t>(stream);
+  return DG_OK;
+}
+
+int dg_sizes(const dg_ctx* c, int* N, int* K, long long* n_state) {
+  if (!c) return DG_ERR_ARG;
+  if (N) *N = c->N;
+  if (K) *K = c->K;
+  if (n_state) *n_state = (long long)(5 * c->S);
+  return DG_OK;
+}
+
+int dg_set_state(dg_ctx* c, const double* U, int on_device) {
+  if (!c || !U) return c ? fail(c, DG_ERR_ARG, "dg_set_state: null U") : DG_ERR_ARG;
+  cudaError_t e = cudaMemcpyAsync(c->U, U, 5 * c->S * sizeof(double),
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "dg_set_state");
+  if (!on_device) {
+    e = cudaStreamSynchronize(c->stream);  // the caller may reuse a pageable buffer
+    if (e != cudaSuccess) return cuda_fail(c, e, "dg_set_state");
+  }
+  c->state_set = true;
+  return DG_OK;
+}
+
+int dg_get_state(dg_ctx* c, double* U, int on_device) {
+  if (!c || !U) return c ? fail(c, DG_ERR_ARG, "dg_get_state: null U") : DG_ERR_ARG;
+  if (!c->state_set) return fail(c, DG_ERR_NOT_INIT, "dg_get_state: state not set");
+  cudaError_t e = cudaMemcpyAsync(U, c->U, 5 * c->S * sizeof(double),
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "dg_get_state");
+  return DG_OK;
+}
+
+int dg_time_derivative(dg_ctx* c, const double* U, double* Ut, double t, int on_device) {
+  (void)t;  // the operator is autonomous (constant body force)
+  if (!c || !Ut) return c ? fail(c, DG_ERR_ARG, "dg_time_derivative: null Ut") : DG_ERR_ARG;
+  const size_t bytes = 5 * c->S * sizeof(double);
+  const double* Uin = U;
+  cudaError_t e;
+  if (!U) {
+    if (!c->state_set) return fail(c, DG_ERR_NOT_INIT, "dg_time_derivative: state not set");
+    Uin = c->U;
+  } else if (!on_device) {
+    e = cudaMemcpyAsync(c->io, U, bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "dg_time_derivative: upload");
+    Uin = c->io;
+  }
+  double* out = on_device ? Ut : c->io2;
+  int rc = launch(c, Uin, 0, out, 0, 0, 0, 0, nullptr);
+  if (rc != DG_OK) return rc;
+  if (!on_device) {
+    e = cudaMemcpyAsync(Ut, out, bytes, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "dg_time_derivative: download");
+  }
+  return DG_OK;
+}
+
+int dg_rk_stage(dg_ctx* c, int s, double t, double dt) {
+  (void)t;
+  if (!c) return DG_ERR_ARG;
+  if (s < 0 || s > 4) return fail(c, DG_ERR_ARG, "dg_rk_stage: stage must be 0..4");
+  if (!c->state_set) return fail(c, DG_ERR_NOT_INIT, "dg_rk_stage: state not set");
+  return launch(c, c->U, 1, nullptr, kRkA[s], kRkB[s], dt, s > 0 ? 1 : 0, c->U);
+}
+
+int dg_rk_steps(dg_ctx* c, double t, double dt, int nsteps) {
+  if (!c || nsteps < 0) return c ? fail(c, DG_ERR_ARG, "dg_rk_steps: nsteps < 0") : DG_ERR_ARG;
+  for (int it = 0; it < nsteps; ++it)
+    for (int s = 0; s < 5; ++s) {
+      int rc = dg_rk_stage(c, s, t + (it + kRkC[s]) * dt, dt);
+      if (rc != DG_OK) return rc;
+    }
+  return DG_OK;
+}
+
+int dg_check_status(dg_ctx* c) {
+  if (!c) return DG_ERR_ARG;
+  int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, sizeof(int), c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "dg_check_status");
+  if (h & dg::ST_NONFINITE) return fail(c, DG_ERR_NONFINITE, "non-finite value in the state");
+  if (h & dg::ST_WM_NOCONV) return fail(c, DG_ERR_WM_NOCONV, "wall-model Newton iteration did not converge");
+  return DG_OK;
+}
+
+int dg_profile_enable(dg_ctx* c, int enable) {
+  if (!c) return DG_ERR_ARG;
+  c->profiling = enable != 0;
+  c->events_used = 0;
+  return DG_OK;
+}
+
+int dg_profile_read(dg_ctx* c, double* ms, int* launches) {
+  if (!c || !ms || !launches) return c ? fail(c, DG_ERR_ARG, "dg_profile_read: null output") : DG_ERR_ARG;
+  for (int k = 0; k < 4; ++k) { ms[k] = 0.0; launches[k] = 0; }
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "dg_profile_read");
+  const bool visc = c->opts.viscous != 0;
+  const bool work[4] = {visc, c->geo.n_interior > 0, c->geo.n_wall > 0, true};
+  for (size_t b = 0; b + 5 <= c->events_used; b += 5)
+    for (int k = 0; k < 4; ++k) {
+      float t = 0.0f;
+      e = cudaEventElapsedTime(&t, c->events[b + k], c->events[b + k + 1]);
+      if (e != cudaSuccess) return cuda_fail(c, e, "dg_profile_read");
+      ms[k] += t;
+      if (work[k]) launches[k] += 1;
+    }
+  c->events_used = 0;
+  return DG_OK;
+}
+
+int dg_get_metrics(const dg_ctx* c, double* Ja, double* J) {
+  if (!c) return DG_ERR_ARG;
+  if (Ja) std::memcpy(Ja, c->geo.Ja.data(), c->geo.Ja.size() * sizeof(double));
+  if (J) std::memcpy(J, c->geo.J.data(), c->geo.J.size() * sizeof(double));
+  return DG_OK;
+}
+
+}  // extern "C"

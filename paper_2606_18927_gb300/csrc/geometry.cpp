@@ -1,0 +1,336 @@
+// geometry.cpp -- host-side mesh preprocessing (see geometry.h).
+#include "geometry.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+
+namespace dg {
+
+static void legendre_pair(int N, double x, double* PN, double* PNm1) {
+  double a = 1.0, b = x;  // P_0, P_1
+  if (N == 0) { *PN = 1.0; *PNm1 = 0.0; return; }
+  for (int k = 2; k <= N; ++k) {
+    double c = ((2 * k - 1) * x * b - (k - 1) * a) / k;
+    a = b; b = c;
+  }
+  *PN = b; *PNm1 = a;
+}
+
+Basis make_basis(int N) {
+  Basis B;
+  B.N = N; B.n = N + 1;
+  const int n = B.n;
+  B.x.resize(n); B.w.resize(n); B.D.assign(n * n, 0.0);
+  // Chebyshev-Gauss-Lobatto start, then x <- x - (x P_N - P_{N-1}) / ((N+1) P_N)
+  // (a Newton step on (1 - x^2) P_N'(x) written through the recurrence).
+  for (int i = 0; i < n; ++i) {
+    double x = std::cos(M_PI * (N - i) / N);
+    for (int it = 0; it < 200; ++it) {
+      double P, Q;
+      legendre_pair(N, x, &P, &Q);
+      double dx = (x * P - Q) / ((N + 1) * P);
+      x -= dx;
+      if (std::fabs(dx) <= 1e-17) break;
+    }
+    B.x[i] = x;
+  }
+  B.x[0] = -1.0; B.x[N] = 1.0;
+  for (int i = 0; i < n / 2; ++i) {  // exact symmetry
+    double m = 0.5 * (B.x[N - i] - B.x[i]);
+    B.x[i] = -m; B.x[N - i] = m;
+  }
+  if (n % 2) B.x[N / 2] = 0.0;
+  std::vector<double> PN(n);
+  for (int i = 0; i < n; ++i) {
+    double P, Q;
+    legendre_pair(N, B.x[i], &P, &Q);
+    PN[i] = P;
+    B.w[i] = 2.0 / (N * (N + 1.0) * P * P);
+  }
+  // closed form: D_ij = P_N(x_i) / (P_N(x_j) (x_i - x_j)) for i != j,
+  // D_00 = -N(N+1)/4, D_NN = N(N+1)/4, other diagonal entries 0
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j)
+      if (i != j) B.D[i * n + j] = PN[i] / (PN[j] * (B.x[i] - B.x[j]));
+  B.D[0] = -N * (N + 1.0) / 4.0;
+  B.D[N * n + N] = N * (N + 1.0) / 4.0;
+  return B;
+}
+
+void lagrange_at(const Basis& b, double s, double* l) {
+  const int n = b.n;
+  // barycentric weights
+  double num = 0.0;
+  std::vector<double> lam(n, 1.0);
+  for (int j = 0; j < n; ++j)
+    for (int k = 0; k < n; ++k)
+      if (k != j) lam[j] /= (b.x[j] - b.x[k]);
+  for (int j = 0; j < n; ++j)
+    if (s == b.x[j]) {
+      for (int k = 0; k < n; ++k) l[k] = (k == j) ? 1.0 : 0.0;
+      return;
+    }
+  for (int j = 0; j < n; ++j) {
+    l[j] = lam[j] / (s - b.x[j]);
+    num += l[j];
+  }
+  for (int j = 0; j < n; ++j) l[j] /= num;
+}
+
+// --------------------------------------------------------------------------
+static bool metrics(Geometry& g, std::string& err) {
+  const int n = g.n, n3 = g.n3, K = g.K;
+  const std::vector<double>& D = g.basis.D;
+  g.Ja.assign((size_t)K * n3 * 9, 0.0);
+  g.J.assign((size_t)K * n3, 0.0);
+  std::vector<double> xl(3 * n3), dx(9 * n3), v(3 * n3);
+  auto dxi = [&](const double* f, int dir, int p) {
+    const int i = p % n, j = (p / n) % n, k = p / (n * n);
+    double s = 0.0;
+    if (dir == 0) for (int m = 0; m < n; ++m) s += D[i * n + m] * f[m + n * (j + n * k)];
+    else if (dir == 1) for (int m = 0; m < n; ++m) s += D[j * n + m] * f[i + n * (m + n * k)];
+    else for (int m = 0; m < n; ++m) s += D[k * n + m] * f[i + n * (j + n * m)];
+    return s;
+  };
+  for (int e = 0; e < K; ++e) {
+    // element-local coordinates (relative to the element centroid): the curl
+    // form and the derivatives are unchanged by a constant shift, and the
+    // roundoff then does not grow with the distance from the origin
+    for (int c = 0; c < 3; ++c) {
+      double mean = 0.0;
+      for (int p = 0; p < n3; ++p) mean += g.X[(size_t)c * K * n3 + (size_t)e * n3 + p];
+      mean /= n3;
+      for (int p = 0; p < n3; ++p) xl[c * n3 + p] = g.X[(size_t)c * K * n3 + (size_t)e * n3 + p] - mean;
+    }
+    for (int c = 0; c < 3; ++c)
+      for (int d = 0; d < 3; ++d)
+        for (int p = 0; p < n3; ++p) dx[(c * 3 + d) * n3 + p] = dxi(&xl[c * n3], d, p);
+    for (int p = 0; p < n3; ++p) {
+      const double* a = &dx[0];
+      double m[3][3];
+      for (int c = 0; c < 3; ++c)
+        for (int d = 0; d < 3; ++d) m[c][d] = a[(c * 3 + d) * n3 + p];
+      double det = m[0][0] * (m[1][1] * m[2][2] - m[2][1] * m[1][2]) -
+                   m[1][0] * (m[0][1] * m[2][2] - m[2][1] * m[0][2]) +
+                   m[2][0] * (m[0][1] * m[1][2] - m[1][1] * m[0][2]);
+      g.J[(size_t)e * n3 + p] = det;
+      if (!(det > 0.0)) {
+        char buf[128];
+        std::snprintf(buf, sizeof buf, "non-positive Jacobian %.3e in element %d", det, e);
+        err = buf;
+        return false;
+      }
+    }
+    // Ja^i_c = -(curl_xi (x_l grad_xi x_m))_i with (c, m, l) cyclic
+    for (int c = 0; c < 3; ++c) {
+      const int mm = (c + 1) % 3, ll = (c + 2) % 3;
+      for (int d = 0; d < 3; ++d)
+        for (int p = 0; p < n3; ++p) v[d * n3 + p] = xl[ll * n3 + p] * dx[(mm * 3 + d) * n3 + p];
+      for (int p = 0; p < n3; ++p) {
+        double* ja = &g.Ja[((size_t)e * n3 + p) * 9];
+        ja[0 * 3 + c] = dxi(&v[1 * n3], 2, p) - dxi(&v[2 * n3], 1, p);
+        ja[1 * 3 + c] = dxi(&v[2 * n3], 0, p) - dxi(&v[0 * n3], 2, p);
+        ja[2 * 3 + c] = dxi(&v[0 * n3], 1, p) - dxi(&v[1 * n3], 0, p);
+      }
+    }
+  }
+  return true;
+}
+
+static bool faces(Geometry& g, std::string& err) {
+  const int n = g.n, n2 = g.n2, n3 = g.n3, K = g.K;
+  double scale = 1.0;
+  for (double x : g.X) scale = std::max(scale, std::fabs(x));
+  for (int e = 0; e < K; ++e)
+    for (int l = 0; l < 6; ++l) {
+      const int nb = g.nbr[e * 6 + l];
+      if (nb < -1 || nb >= K) { err = "neighbour index out of range"; return false; }
+      if (nb < 0) continue;
+      if (g.nbr[nb * 6 + (l ^ 1)] != e) { err = "connectivity is not reciprocal"; return false; }
+      // the two sides must coincide up to a single translation
+      double sh[3] = {0, 0, 0};
+      for (int ab = 0; ab < n2; ++ab) {
+        const int p = face_node(n, l, ab % n, ab / n), q = face_node(n, l ^ 1, ab % n, ab / n);
+        for (int c = 0; c < 3; ++c) {
+          const double d = g.X[(size_t)c * K * n3 + (size_t)nb * n3 + q] - g.X[(size_t)c * K * n3 + (size_t)e * n3 + p];
+          if (ab == 0) sh[c] = d;
+          else if (std::fabs(d - sh[c]) > 1e-9 * scale) {
+            err = "face nodes of neighbouring elements do not match";
+            return false;
+          }
+        }
+      }
+    }
+  g.faces.clear();
+  g.elem_face.assign((size_t)K * 6, -1);
+  for (int e = 0; e < K; ++e)
+    for (int l = 1; l < 6; l += 2) {
+      const int nb = g.nbr[e * 6 + l];
+      if (nb < 0) continue;
+      const int id = (int)g.faces.size();
+      g.faces.push_back({e, l, nb, l ^ 1});
+      g.elem_face[e * 6 + l] = 2 * id;
+      g.elem_face[nb * 6 + (l ^ 1)] = 2 * id + 1;
+    }
+  g.n_interior = (int)g.faces.size();
+  for (int e = 0; e < K; ++e)
+    for (int l = 0; l < 6; ++l)
+      if (g.nbr[e * 6 + l] < 0) {
+        const int id = (int)g.faces.size();
+        g.faces.push_back({e, l, -1, -1});
+        g.elem_face[e * 6 + l] = 2 * id;
+      }
+  g.n_wall = (int)g.faces.size() - g.n_interior;
+  const size_t F = g.faces.size();
+  g.fgeo.assign(4 * F * n2, 0.0);
+  for (size_t f = 0; f < F; ++f) {
+    const Face& fc = g.faces[f];
+    const double sgn = (fc.lM & 1) ? 1.0 : -1.0;
+    for (int ab = 0; ab < n2; ++ab) {
+      const int p = face_node(n, fc.lM, ab % n, ab / n);
+      const double* ja = &g.Ja[((size_t)fc.eM * n3 + p) * 9 + (fc.lM / 2) * 3];
+      const double s = std::sqrt(ja[0] * ja[0] + ja[1] * ja[1] + ja[2] * ja[2]);
+      for (int c = 0; c < 3; ++c) g.fgeo[(size_t)c * F * n2 + f * n2 + ab] = sgn * ja[c] / s;
+      g.fgeo[3 * F * n2 + f * n2 + ab] = s;
+    }
+  }
+  return true;
+}
+
+// Newton on the element map x(r) = sum X_ijk l_i(r0) l_j(r1) l_k(r2); the
+// derivative of the interpolant uses l_j'(s) = sum_k l_k(s) D_kj.
+static bool invert_map(const Geometry& g, int e, const double xs[3], double r[3]) {
+  const int n = g.n, n3 = g.n3, K = g.K;
+  const std::vector<double>& D = g.basis.D;
+  std::vector<double> L(3 * n), dL(3 * n);
+  r[0] = r[1] = r[2] = 0.0;
+  for (int it = 0; it < 80; ++it) {
+    for (int a = 0; a < 3; ++a) {
+      lagrange_at(g.basis, r[a], &L[a * n]);
+      for (int j = 0; j < n; ++j) {
+        double s = 0.0;
+        for (int k = 0; k < n; ++k) s += L[a * n + k] * D[k * n + j];
+        dL[a * n + j] = s;
+      }
+    }
+    double x[3] = {0, 0, 0}, A[3][3] = {{0}};
+    for (int k = 0; k < n; ++k)
+      for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) {
+          const int p = i + n * (j + n * k);
+          const double l0 = L[i], l1 = L[n + j], l2 = L[2 * n + k];
+          for (int c = 0; c < 3; ++c) {
+            const double X = g.X[(size_t)c * K * n3 + (size_t)e * n3 + p];
+            x[c] += X * l0 * l1 * l2;
+            A[c][0] += X * dL[i] * l1 * l2;
+            A[c][1] += X * l0 * dL[n + j] * l2;
+            A[c][2] += X * l0 * l1 * dL[2 * n + k];
+          }
+        }
+    // r += A^{-1} (xs - x) by the adjugate
+    double inv[3][3];
+    inv[0][0] = A[1][1] * A[2][2] - A[1][2] * A[2][1];
+    inv[0][1] = A[0][2] * A[2][1] - A[0][1] * A[2][2];
+    inv[0][2] = A[0][1] * A[1][2] - A[0][2] * A[1][1];
+    inv[1][0] = A[1][2] * A[2][0] - A[1][0] * A[2][2];
+    inv[1][1] = A[0][0] * A[2][2] - A[0][2] * A[2][0];
+    inv[1][2] = A[0][2] * A[1][0] - A[0][0] * A[1][2];
+    inv[2][0] = A[1][0] * A[2][1] - A[1][1] * A[2][0];
+    inv[2][1] = A[0][1] * A[2][0] - A[0][0] * A[2][1];
+    inv[2][2] = A[0][0] * A[1][1] - A[0][1] * A[1][0];
+    const double det = A[0][0] * inv[0][0] + A[0][1] * inv[1][0] + A[0][2] * inv[2][0];
+    if (det == 0.0 || !std::isfinite(det)) return false;
+    const double res[3] = {xs[0] - x[0], xs[1] - x[1], xs[2] - x[2]};
+    double step = 0.0;
+    for (int a = 0; a < 3; ++a) {
+      const double d = (inv[a][0] * res[0] + inv[a][1] * res[1] + inv[a][2] * res[2]) / det;
+      r[a] = std::min(3.0, std::max(-3.0, r[a] + d));
+      step = std::max(step, std::fabs(d));
+    }
+    if (step < 1e-15) break;
+  }
+  return true;
+}
+
+static bool wall_samples(Geometry& g, double hwm, std::string& err) {
+  const int n = g.n, n2 = g.n2, n3 = g.n3, K = g.K;
+  const int F = (int)g.faces.size();
+  g.ws_elem.assign((size_t)g.n_wall * n2, -1);
+  g.ws_ref.assign((size_t)g.n_wall * n2 * 3, 0.0);
+  g.ws_lag.assign((size_t)g.n_wall * n2 * 3 * n, 0.0);
+  if (g.n_wall == 0) return true;
+  std::vector<double> lo((size_t)K * 3, 1e300), hi((size_t)K * 3, -1e300);
+  for (int e = 0; e < K; ++e)
+    for (int c = 0; c < 3; ++c)
+      for (int p = 0; p < n3; ++p) {
+        const double x = g.X[(size_t)c * K * n3 + (size_t)e * n3 + p];
+        lo[e * 3 + c] = std::min(lo[e * 3 + c], x);
+        hi[e * 3 + c] = std::max(hi[e * 3 + c], x);
+      }
+  for (int wf = 0; wf < g.n_wall; ++wf) {
+    const int f = g.n_interior + wf;
+    const Face& fc = g.faces[f];
+    // candidate elements: neighbourhood of the wall element (3 layers)
+    std::vector<int> cand{fc.eM};
+    for (int layer = 0; layer < 3; ++layer) {
+      const size_t m = cand.size();
+      for (size_t c = 0; c < m; ++c)
+        for (int l = 0; l < 6; ++l) {
+          const int nb = g.nbr[cand[c] * 6 + l];
+          if (nb >= 0 && std::find(cand.begin(), cand.end(), nb) == cand.end()) cand.push_back(nb);
+        }
+    }
+    std::sort(cand.begin(), cand.end());
+    for (int ab = 0; ab < n2; ++ab) {
+      const int p = face_node(n, fc.lM, ab % n, ab / n);
+      double xs[3];
+      for (int c = 0; c < 3; ++c)
+        xs[c] = g.X[(size_t)c * K * n3 + (size_t)fc.eM * n3 + p] - hwm * g.fgeo[(size_t)c * F * n2 + (size_t)f * n2 + ab];
+      int best = -1;
+      double bestm = 0.0, br[3] = {0, 0, 0};
+      for (int e : cand) {
+        bool in = true;
+        for (int c = 0; c < 3; ++c) {
+          const double pad = 0.05 * (hi[e * 3 + c] - lo[e * 3 + c]) + 1e-12;
+          in = in && xs[c] >= lo[e * 3 + c] - pad && xs[c] <= hi[e * 3 + c] + pad;
+        }
+        if (!in) continue;
+        double r[3];
+        if (!invert_map(g, e, xs, r)) continue;
+        const double mx = std::max(std::fabs(r[0]), std::max(std::fabs(r[1]), std::fabs(r[2])));
+        if (mx <= 1.0 + 1e-10 && (best < 0 || mx < bestm)) {
+          best = e; bestm = mx;
+          br[0] = r[0]; br[1] = r[1]; br[2] = r[2];
+        }
+      }
+      if (best < 0) {
+        char buf[160];
+        std::snprintf(buf, sizeof buf, "wall-model sample point of element %d is not inside the mesh", fc.eM);
+        err = buf;
+        return false;
+      }
+      const size_t slot = (size_t)wf * n2 + ab;
+      g.ws_elem[slot] = best;
+      for (int a = 0; a < 3; ++a) {
+        g.ws_ref[slot * 3 + a] = br[a];
+        lagrange_at(g.basis, br[a], &g.ws_lag[(slot * 3 + a) * n]);
+      }
+    }
+  }
+  return true;
+}
+
+std::string build_geometry(Geometry& g, int N, int K, const double* X, const int* nbr, double hwm) {
+  g.N = N; g.n = N + 1; g.n2 = g.n * g.n; g.n3 = g.n2 * g.n; g.K = K;
+  g.basis = make_basis(N);
+  g.X.assign(X, X + (size_t)3 * K * g.n3);
+  g.nbr.assign(nbr, nbr + (size_t)6 * K);
+  std::string err;
+  if (!metrics(g, err)) return err;
+  if (!faces(g, err)) return err;
+  if (!wall_samples(g, hwm, err)) return err;
+  return "";
+}
+
+}  // namespace dg

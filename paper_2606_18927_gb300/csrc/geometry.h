@@ -1,0 +1,66 @@
+// geometry.h -- host-side mesh preprocessing of the GB300 DGSEM library.
+//
+// Builds, from node coordinates at the Legendre-Gauss-Lobatto nodes (paper
+// Sec. 2.2: tensor-product LGL nodes of degree N), everything the kernels
+// read: the curl-form metric terms Ja^i (Kopriva's conservative form, which
+// keeps free-stream preservation on curvilinear elements), the Jacobian J,
+// the face list with master-side unit normals and surface elements, and the
+// wall-model sampling data (Sec. 3.1: the wall model samples the LES solution
+// at the distance h_wm from the wall).
+#pragma once
+#include <string>
+#include <vector>
+
+namespace dg {
+
+struct Basis {
+  int N = 0, n = 0;
+  std::vector<double> x, w;  // LGL nodes and weights
+  std::vector<double> D;     // D[i*n + j] = l_j'(x_i)
+};
+
+// LGL nodes by the Lobatto fixed-point/Newton iteration
+// x <- x - (x P_N - P_{N-1}) / ((N+1) P_N), weights 2/(N(N+1) P_N^2),
+// derivative matrix in closed form.
+Basis make_basis(int N);
+
+// Lagrange basis l_j(s) (barycentric form) on the basis nodes.
+void lagrange_at(const Basis& b, double s, double* l);
+
+struct Face {
+  int eM, lM;  // master element and its local face
+  int eS, lS;  // slave element and local face, or -1 for a wall
+};
+
+struct Geometry {
+  int N = 0, n = 0, n2 = 0, n3 = 0, K = 0;
+  Basis basis;
+  std::vector<int> nbr;          // [K*6]
+  std::vector<double> X;         // [3][K*n3]
+  std::vector<double> Ja;        // [K*n3][3 dir][3 comp]
+  std::vector<double> J;         // [K*n3]
+  std::vector<Face> faces;       // interior faces first, then wall faces
+  int n_interior = 0, n_wall = 0;
+  std::vector<int> elem_face;    // [K*6] = 2 * face id + side (0 master, 1 slave)
+  std::vector<double> fgeo;      // [4][F*n2]: unit normal (master outward) and s
+  std::vector<int> ws_elem;      // [n_wall*n2] element containing the sample point
+  std::vector<double> ws_ref;    // [n_wall*n2][3] its reference coordinates
+  std::vector<double> ws_lag;    // [n_wall*n2][3][n] Lagrange weights
+};
+
+// Returns an empty string on success, else the reason for rejecting the mesh.
+std::string build_geometry(Geometry& g, int N, int K, const double* X, const int* nbr, double hwm);
+
+inline int face_node(int n, int l, int a, int b) {
+  const int N = n - 1;
+  switch (l) {
+    case 0: return 0 + n * (a + n * b);
+    case 1: return N + n * (a + n * b);
+    case 2: return a + n * (0 + n * b);
+    case 3: return a + n * (N + n * b);
+    case 4: return a + n * (b + n * 0);
+    default: return a + n * (b + n * N);
+  }
+}
+
+}  // namespace dg

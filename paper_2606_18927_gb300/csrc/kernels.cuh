@@ -1,0 +1,613 @@
+// kernels.cuh -- sm_103a kernels of the DGSEM operator.
+//
+// One operator evaluation (paper Sec. 2.2 / Sec. 4: split-form DGSEM on LGL
+// nodes; Sec. 3: equilibrium wall model) is three kernel launches:
+//   k_lift   one CTA per element: primitives, BR1 lifting of grad(u,v,w,T),
+//            viscous flux, its weak-form volume divergence R_v, and the
+//            element's own outward viscous flux at its six faces;
+//   k_face   one thread per face node: Riemann flux (central / LLF / Roe with
+//            Harten's entropy fix) plus the BR1 average of the viscous flux;
+//            wall faces: mirror state and the wall-stress model;
+//   k_volume one CTA per element: two-point KEP flux differencing with the
+//            split-form matrix DVS = 2D - B/w (zero corners), the surface
+//            integral, 1/J scaling, body force, and either Ut or the LSERK4
+//            register update of U and dU.
+// R is the arithmetic type of the fluxes and their sums (double, or float in
+// the mixed form); the state U, dU, the pressure recovery and the RK update
+// are always double.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dg {
+
+enum { ST_NONFINITE = 1, ST_WM_NOCONV = 2 };
+
+struct PhysDev {
+  double gamma, gm1, R, mu, Pr, cp, kcond, rcp_R;
+  double f[3];
+  double kappa, B, hwm;
+  int law, vol_flux, surf_flux, viscous;
+};
+
+// device-side views of the context's arrays
+template <typename R>
+struct MeshDev {
+  int K, F, n_interior, n_wall;
+  const R* Ja;           // [9][K*n3] (dir*3+comp)
+  const R* invJ;         // [K*n3]
+  const double* fgeo;    // [4][F*n2]
+  const int* nbr;        // [K*6]
+  const int* elem_face;  // [K*6]
+  const int4* faces;     // [F]
+  const int* ws_elem;    // [n_wall*n2]
+  const double* ws_lag;  // [n_wall*n2*3*n]
+};
+
+template <int N>
+struct Tables {
+  double D[(N + 1) * (N + 1)];
+  double DVS8[(N + 1) * (N + 1)];   // (2D - B/w) / 8
+  double Dvisc[(N + 1) * (N + 1)];  // (w_m / w_i) D_mi
+  double iw[N + 1];                 // 1 / w
+};
+
+template <int N>
+__device__ __forceinline__ int fnode(int l, int a, int b) {
+  constexpr int n = N + 1;
+  switch (l) {
+    case 0: return n * (a + n * b);
+    case 1: return N + n * (a + n * b);
+    case 2: return a + n * n * b;
+    case 3: return a + n * (N + n * b);
+    case 4: return a + n * b;
+    default: return a + n * (b + n * N);
+  }
+}
+
+__device__ __forceinline__ bool finite_bits(double x) {
+  const unsigned hi = (unsigned)(__double_as_longlong(x) >> 32);
+  return (hi & 0x7ff00000u) != 0x7ff00000u;
+}
+
+// Primitive state in the flux type.  p is recovered in double from the
+// double state (p = (gamma-1)(E - rho |u|^2 / 2) cancels at low Mach number)
+// and only then rounded to R.
+template <typename R>
+struct Prim {
+  R rho, u, v, w, p, h;
+};
+
+template <typename R>
+__device__ __forceinline__ Prim<R> primitive(const double U0, const double U1, const double U2,
+                                             const double U3, const double U4, const PhysDev& ph) {
+  Prim<R> q;
+  const double ir = 1.0 / U0;
+  const double u = U1 * ir, v = U2 * ir, w = U3 * ir;
+  const double p = ph.gm1 * (U4 - 0.5 * (U1 * u + U2 * v + U3 * w));
+  q.rho = (R)U0; q.u = (R)u; q.v = (R)v; q.w = (R)w; q.p = (R)p;
+  q.h = (R)((U4 + p) * ir);
+  return q;
+}
+
+// Two-point KEP flux F#(L, R) . a (a need not be unit).
+template <typename R>
+__device__ __forceinline__ void twopoint(int kind, const Prim<R>& A, const Prim<R>& B, R a0, R a1, R a2,
+                                         R F[5]) {
+  const R rho = R(0.5) * (A.rho + B.rho);
+  const R u = R(0.5) * (A.u + B.u), v = R(0.5) * (A.v + B.v), w = R(0.5) * (A.w + B.w);
+  const R p = R(0.5) * (A.p + B.p);
+  const R ua = u * a0 + v * a1 + w * a2;
+  const R m = rho * ua;
+  F[0] = m;
+  F[1] = m * u + p * a0;
+  F[2] = m * v + p * a1;
+  F[3] = m * w + p * a2;
+  if (kind == 0) {
+    F[4] = m * (R(0.5) * (A.h + B.h));
+  } else {  // Kennedy-Gruber: {rho}{u.a}{e} + {p}{u.a}, e = E / rho = h - p / rho
+    const R eA = A.h - A.p / A.rho, eB = B.h - B.p / B.rho;
+    F[4] = m * (R(0.5) * (eA + eB)) + p * ua;
+  }
+}
+
+// Numerical inviscid flux along the unit normal (nx, ny, nz), side A = master.
+template <typename R>
+__device__ __forceinline__ void riemann(const PhysDev& ph, const Prim<R>& A, const double UA[5],
+                                        const Prim<R>& B, const double UB[5], R nx, R ny, R nz, R F[5]) {
+  twopoint<R>(ph.vol_flux, A, B, nx, ny, nz, F);
+  const R g = (R)ph.gamma;
+  if (ph.surf_flux == 1) {  // local Lax-Friedrichs
+    const R cA = sqrt(g * A.p / A.rho), cB = sqrt(g * B.p / B.rho);
+    const R lA = fabs(A.u * nx + A.v * ny + A.w * nz) + cA;
+    const R lB = fabs(B.u * nx + B.v * ny + B.w * nz) + cB;
+    const R lam = R(0.5) * (lA >= lB ? lA : lB);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) F[v] -= lam * (R)(UB[v] - UA[v]);
+  } else if (ph.surf_flux == 2) {  // Roe with Harten's entropy fix on the acoustic waves
+    const R sA = sqrt(A.rho), sB = sqrt(B.rho);
+    const R is = R(1) / (sA + sB);
+    const R rt = sA * sB;
+    const R u = (sA * A.u + sB * B.u) * is, v = (sA * A.v + sB * B.v) * is, w = (sA * A.w + sB * B.w) * is;
+    const R H = (sA * A.h + sB * B.h) * is;
+    const R q2 = u * u + v * v + w * w;
+    const R c2 = (g - R(1)) * (H - R(0.5) * q2);
+    const R c = sqrt(c2);
+    const R un = u * nx + v * ny + w * nz;
+    const R dr = B.rho - A.rho, dp = B.p - A.p;
+    const R du = B.u - A.u, dv = B.v - A.v, dw = B.w - A.w;
+    const R dun = du * nx + dv * ny + dw * nz;
+    const R i2c2 = R(0.5) / c2;
+    const R a1 = (dp - rt * c * dun) * i2c2;
+    const R a2 = dr - dp / c2;
+    const R a5 = (dp + rt * c * dun) * i2c2;
+    R l1 = fabs(un - c), l2 = fabs(un), l5 = fabs(un + c);
+    const R del = R(0.1) * c;
+    if (l1 < del) l1 = (l1 * l1 + del * del) / (R(2) * del);
+    if (l5 < del) l5 = (l5 * l5 + del * del) / (R(2) * del);
+    const R w1 = l1 * a1, w2 = l2 * a2, w5 = l5 * a5, ws = l2 * rt;
+    const R dut = du - dun * nx, dvt = dv - dun * ny, dwt = dw - dun * nz;
+    const R D0 = w1 + w2 + w5;
+    const R D1 = w1 * (u - c * nx) + w2 * u + w5 * (u + c * nx) + ws * dut;
+    const R D2 = w1 * (v - c * ny) + w2 * v + w5 * (v + c * ny) + ws * dvt;
+    const R D3 = w1 * (w - c * nz) + w2 * w + w5 * (w + c * nz) + ws * dwt;
+    const R D4 = w1 * (H - c * un) + w2 * (R(0.5) * q2) + w5 * (H + c * un) +
+                 ws * (u * du + v * dv + w * dw - un * dun);
+    F[0] -= R(0.5) * D0; F[1] -= R(0.5) * D1; F[2] -= R(0.5) * D2;
+    F[3] -= R(0.5) * D3; F[4] -= R(0.5) * D4;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Wall model (paper Sec. 3.2, Algorithms 1-2), always in double.
+// ---------------------------------------------------------------------------
+// law L(w) and w L'(w) / L(w) for w = y+ (Reichardt, L = u+) or w = u+
+// (Spalding, L = y+)
+__device__ __forceinline__ void law_eval(int law, double w, double kap, double B, double* L, double* wdL) {
+  if (law == 1) {
+    const double C = B - log(kap) / kap;
+    const double e1 = exp(-w / 11.0), e2 = exp(-0.33 * w);
+    const double Lv = log1p(kap * w) / kap + C * (1.0 - e1 - (w / 11.0) * e2);
+    const double dL = 1.0 / (1.0 + kap * w) + C * (e1 / 11.0 - e2 / 11.0 + 0.33 * (w / 11.0) * e2);
+    *L = Lv; *wdL = w * dL;
+  } else {
+    const double ku = kap * w;
+    const double eb = exp(-kap * B), ek = exp(ku);
+    const double t3 = ku * ku * ku / 6.0;
+    const double Lv = w + eb * (ek - 1.0 - ku - 0.5 * ku * ku - t3 - 0.25 * ku * t3);
+    const double dL = 1.0 + eb * kap * (ek - 1.0 - ku - 0.5 * ku * ku - t3);
+    *L = Lv; *wdL = w * dL;
+  }
+}
+
+// Solve t + ln L(e^t) = ln Re_h (Re_h = h u / nu = u+ y+): bracket by growing
+// steps from the laminar estimate t = ln(Re_h)/2, then Newton with bisection
+// whenever a step would leave the bracket.  Returns u_tau (and *ok).
+static __device__ double solve_utau(int law, double u, double h, double nu, double kap, double B, bool* ok) {
+  *ok = true;
+  if (!(u > 0.0)) return 0.0;
+  const double lnRe = log(h * u / nu);
+  auto F = [&](double t, double* dF) {
+    const double w = exp(t);
+    double L, wdL;
+    law_eval(law, w, kap, B, &L, &wdL);
+    *dF = 1.0 + wdL / L;
+    return t + log(L) - lnRe;
+  };
+  double dF;
+  double lo = 0.5 * lnRe, hi = lo, st = 1.0;
+  int it = 0;
+  while (!(F(lo, &dF) < 0.0) && it < 200) { lo -= st; st *= 2.0; ++it; }
+  st = 1.0;
+  while (!(F(hi, &dF) > 0.0) && it < 200) { hi += st; st *= 2.0; ++it; }
+  double t = 0.5 * lnRe;
+  if (!(t > lo && t < hi)) t = 0.5 * (lo + hi);
+  bool done = false;
+  for (; it < 200; ++it) {
+    const double Ft = F(t, &dF);
+    if (Ft == 0.0) { done = true; break; }
+    if (Ft < 0.0) lo = t; else hi = t;
+    double nt = t - Ft / dF;
+    const bool newton = (nt >= lo && nt <= hi);
+    if (!newton) nt = 0.5 * (lo + hi);
+    const double step = fabs(nt - t);
+    t = nt;
+    const double sc = fmax(1.0, fabs(t));
+    if ((newton && step <= 1e-12 * sc) || hi - lo <= 2e-15 * sc) { done = true; break; }
+  }
+  *ok = done;
+  return law == 1 ? exp(t) * nu / h : u / exp(t);
+}
+
+// Wall shear stress from the sample state: Van Driest transform for an
+// adiabatic wall (Crocco-Busemann: T_w = T + r u^2 / (2 cp), rho_w = rho T / T_w,
+// u_VD = asin(a u) / a with a = sqrt(r / (2 cp T_w)), r = Pr^(1/3)), then the
+// law of the wall for u_tau, tau_w = rho_w u_tau^2 along the sample's
+// wall-parallel velocity.
+static __device__ void wall_stress(const PhysDev& ph, const double Us[5], double nx, double ny, double nz,
+                            double tau[3], bool* ok) {
+  const double rho = Us[0], ir = 1.0 / rho;
+  const double u = Us[1] * ir, v = Us[2] * ir, w = Us[3] * ir;
+  const double p = ph.gm1 * (Us[4] - 0.5 * rho * (u * u + v * v + w * w));
+  const double T = p * ph.rcp_R * ir;
+  const double un = u * nx + v * ny + w * nz;
+  const double ux = u - un * nx, uy = v - un * ny, uz = w - un * nz;
+  const double u2 = ux * ux + uy * uy + uz * uz;
+  tau[0] = tau[1] = tau[2] = 0.0;
+  *ok = true;
+  if (!(u2 > 0.0)) return;
+  const double um = sqrt(u2);
+  const double r = cbrt(ph.Pr);
+  const double Tw = T + r * u2 / (2.0 * ph.cp);
+  const double rhow = rho * T / Tw;
+  const double a = sqrt(r / (2.0 * ph.cp * Tw));
+  const double uvd = asin(a * um) / a;
+  const double ut = solve_utau(ph.law, uvd, ph.hwm, ph.mu / rhow, ph.kappa, ph.B, ok);
+  const double tw = rhow * ut * ut / um;
+  tau[0] = tw * ux; tau[1] = tw * uy; tau[2] = tw * uz;
+}
+
+// ---------------------------------------------------------------------------
+// k_lift: one CTA of n^3 threads per element.
+// ---------------------------------------------------------------------------
+template <int N, typename R>
+__global__ void __launch_bounds__((N + 1) * (N + 1) * (N + 1))
+k_lift(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const Tables<N> tab,
+       R* __restrict__ Rv, R* __restrict__ Gf) {
+  constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* sW = reinterpret_cast<R*>(smem_raw);      // [4][n3]
+  R* sC = sW + 4 * n3;                          // [6][4][n2]
+  R* sG = sC + 24 * n2;                         // [3][4][n3]
+  R* sD = sG + 12 * n3;                         // [n2]
+  R* sDv = sD + n2;                             // [n2]
+  R* siw = sDv + n2;                            // [n]
+  const int e = blockIdx.x, p = threadIdx.x;
+  const int i = p % n, j = (p / n) % n, k = p / n2;
+  const size_t S = (size_t)m.K * n3;
+  const size_t g = (size_t)e * n3 + p;
+  for (int t = p; t < n2; t += n3) { sD[t] = (R)tab.D[t]; sDv[t] = (R)tab.Dvisc[t]; }
+  if (p < n) siw[p] = (R)tab.iw[p];
+  // own primitives W = (u, v, w, T)
+  {
+    const double U0 = U[g], ir = 1.0 / U0;
+    const double u = U[S + g] * ir, v = U[2 * S + g] * ir, w = U[3 * S + g] * ir;
+    const double pr = ph.gm1 * (U[4 * S + g] - 0.5 * U0 * (u * u + v * v + w * w));
+    sW[p] = (R)u; sW[n3 + p] = (R)v; sW[2 * n3 + p] = (R)w; sW[3 * n3 + p] = (R)(pr * ph.rcp_R * ir);
+  }
+  // own metrics
+  R ja[9];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) ja[c] = m.Ja[(size_t)c * S + g];
+  const R iJ = m.invJ[g];
+  __syncthreads();
+  // W* - W at the six faces (BR1 average with the neighbour, or the mirror
+  // state at a slip wall)
+  for (int t = p; t < 6 * n2; t += n3) {
+    const int l = t / n2, ab = t - l * n2, a = ab % n, b = ab / n;
+    const int q = fnode<N>(l, a, b);
+    const int nb = m.nbr[e * 6 + l];
+    const R Wo0 = sW[q], Wo1 = sW[n3 + q], Wo2 = sW[2 * n3 + q], Wo3 = sW[3 * n3 + q];
+    R d0, d1, d2, d3;
+    if (nb >= 0) {
+      const size_t gn = (size_t)nb * n3 + fnode<N>(l ^ 1, a, b);
+      const double U0 = U[gn], ir = 1.0 / U0;
+      const double u = U[S + gn] * ir, v = U[2 * S + gn] * ir, w = U[3 * S + gn] * ir;
+      const double pr = ph.gm1 * (U[4 * S + gn] - 0.5 * U0 * (u * u + v * v + w * w));
+      d0 = R(0.5) * ((R)u - Wo0); d1 = R(0.5) * ((R)v - Wo1); d2 = R(0.5) * ((R)w - Wo2);
+      d3 = R(0.5) * ((R)(pr * ph.rcp_R * ir) - Wo3);
+    } else {
+      // mirror: W* - W = -(u . n) n, T unchanged (n: own outward unit normal)
+      const size_t gq = (size_t)e * n3 + q;
+      const int dir = l >> 1;
+      const R a0 = m.Ja[(size_t)(dir * 3 + 0) * S + gq], a1 = m.Ja[(size_t)(dir * 3 + 1) * S + gq],
+              a2 = m.Ja[(size_t)(dir * 3 + 2) * S + gq];
+      const R is = R(1) / sqrt(a0 * a0 + a1 * a1 + a2 * a2);
+      const R nx = a0 * is, ny = a1 * is, nz = a2 * is;  // sign irrelevant: (u.n) n
+      const R un = Wo0 * nx + Wo1 * ny + Wo2 * nz;
+      d0 = -un * nx; d1 = -un * ny; d2 = -un * nz; d3 = R(0);
+    }
+    sC[(l * 4 + 0) * n2 + ab] = d0; sC[(l * 4 + 1) * n2 + ab] = d1;
+    sC[(l * 4 + 2) * n2 + ab] = d2; sC[(l * 4 + 3) * n2 + ab] = d3;
+  }
+  __syncthreads();
+  // gradients in reference space
+  R dW[3][4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    R s0 = 0, s1 = 0, s2 = 0;
+#pragma unroll
+    for (int mm = 0; mm < n; ++mm) {
+      s0 += sD[i * n + mm] * sW[v * n3 + mm + n * (j + n * k)];
+      s1 += sD[j * n + mm] * sW[v * n3 + i + n * (mm + n * k)];
+      s2 += sD[k * n + mm] * sW[v * n3 + i + n * (j + n * mm)];
+    }
+    dW[0][v] = s0; dW[1][v] = s1; dW[2][v] = s2;
+  }
+  // physical gradients q[d][v] = (1/J) (sum_dir Ja^dir_d dW_dir + surface terms)
+  R q[3][4];
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) q[d][v] = ja[0 * 3 + d] * dW[0][v] + ja[1 * 3 + d] * dW[1][v] + ja[2 * 3 + d] * dW[2][v];
+  // surface corrections: (W* - W) (n s)_d / w_perp with n s = +-Ja^dir
+  auto surf = [&](int l, int ab, R sgn_iw) {
+    const int dir = l >> 1;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const R f = sgn_iw * ja[dir * 3 + d];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) q[d][v] += f * sC[(l * 4 + v) * n2 + ab];
+    }
+  };
+  if (i == 0) surf(0, j + n * k, -siw[0]);
+  if (i == N) surf(1, j + n * k, siw[N]);
+  if (j == 0) surf(2, i + n * k, -siw[0]);
+  if (j == N) surf(3, i + n * k, siw[N]);
+  if (k == 0) surf(4, i + n * j, -siw[0]);
+  if (k == N) surf(5, i + n * j, siw[N]);
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) q[d][v] *= iJ;
+  // viscous flux Fv_d = (0, tau_1d, tau_2d, tau_3d, tau_jd u_j + k dT/dx_d)
+  const R mu = (R)ph.mu, kc = (R)ph.kcond;
+  const R div = q[0][0] + q[1][1] + q[2][2];
+  R tau[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) tau[a][b] = mu * (q[b][a] + q[a][b]);
+  tau[0][0] -= R(2.0 / 3.0) * mu * div;
+  tau[1][1] -= R(2.0 / 3.0) * mu * div;
+  tau[2][2] -= R(2.0 / 3.0) * mu * div;
+  const R uu = sW[p], vv = sW[n3 + p], ww = sW[2 * n3 + p];
+  R Fv[3][4];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    Fv[d][0] = tau[0][d]; Fv[d][1] = tau[1][d]; Fv[d][2] = tau[2][d];
+    Fv[d][3] = tau[0][d] * uu + tau[1][d] * vv + tau[2][d] * ww + kc * q[d][3];
+  }
+  // contravariant G^dir = sum_d Ja^dir_d Fv_d
+  R G[3][4];
+#pragma unroll
+  for (int dir = 0; dir < 3; ++dir)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      G[dir][v] = ja[dir * 3 + 0] * Fv[0][v] + ja[dir * 3 + 1] * Fv[1][v] + ja[dir * 3 + 2] * Fv[2][v];
+      sG[(dir * 4 + v) * n3 + p] = G[dir][v];
+    }
+  // own outward viscous flux at face nodes: Gf[e][l][v][ab] = +-G^{l/2}
+  auto gface = [&](int l, int ab, R sgn) {
+    R* dst = Gf + ((size_t)e * 6 + l) * 4 * n2 + ab;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) dst[v * n2] = sgn * G[l >> 1][v];
+  };
+  if (i == 0) gface(0, j + n * k, R(-1));
+  if (i == N) gface(1, j + n * k, R(1));
+  if (j == 0) gface(2, i + n * k, R(-1));
+  if (j == N) gface(3, i + n * k, R(1));
+  if (k == 0) gface(4, i + n * j, R(-1));
+  if (k == N) gface(5, i + n * j, R(1));
+  __syncthreads();
+  // weak-form viscous volume term R_v = sum_dir sum_m (w_m / w_i) D_mi G^dir_m
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    R s = 0;
+#pragma unroll
+    for (int mm = 0; mm < n; ++mm) {
+      s += sDv[i * n + mm] * sG[(0 * 4 + v) * n3 + mm + n * (j + n * k)];
+      s += sDv[j * n + mm] * sG[(1 * 4 + v) * n3 + i + n * (mm + n * k)];
+      s += sDv[k * n + mm] * sG[(2 * 4 + v) * n3 + i + n * (j + n * mm)];
+    }
+    Rv[(size_t)v * S + g] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_face: one thread per node of an interior face.
+// ---------------------------------------------------------------------------
+template <int N, typename R>
+__global__ void __launch_bounds__(256)
+k_face(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const R* __restrict__ Gf,
+       R* __restrict__ Fs) {
+  constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int f = tid / n2, ab = tid - f * n2;
+  if (f >= m.n_interior) return;
+  const int4 fc = m.faces[f];
+  const size_t S = (size_t)m.K * n3;
+  const size_t gM = (size_t)fc.x * n3 + fnode<N>(fc.y, ab % n, ab / n);
+  const size_t gS = (size_t)fc.z * n3 + fnode<N>(fc.w, ab % n, ab / n);
+  double UA[5], UB[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) { UA[v] = U[v * S + gM]; UB[v] = U[v * S + gS]; }
+  const Prim<R> A = primitive<R>(UA[0], UA[1], UA[2], UA[3], UA[4], ph);
+  const Prim<R> B = primitive<R>(UB[0], UB[1], UB[2], UB[3], UB[4], ph);
+  const size_t FN = (size_t)m.F * n2, fg = (size_t)f * n2 + ab;
+  const R nx = (R)m.fgeo[fg], ny = (R)m.fgeo[FN + fg], nz = (R)m.fgeo[2 * FN + fg], s = (R)m.fgeo[3 * FN + fg];
+  R F[5];
+  riemann<R>(ph, A, UA, B, UB, nx, ny, nz, F);
+  R* out = Fs + (size_t)f * 5 * n2 + ab;
+  out[0] = F[0] * s;
+  if (ph.viscous) {
+    const R* gA = Gf + ((size_t)fc.x * 6 + fc.y) * 4 * n2 + ab;
+    const R* gB = Gf + ((size_t)fc.z * 6 + fc.w) * 4 * n2 + ab;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) out[(v + 1) * n2] = F[v + 1] * s - R(0.5) * (gA[v * n2] - gB[v * n2]);
+  } else {
+#pragma unroll
+    for (int v = 1; v < 5; ++v) out[v * n2] = F[v] * s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_wall: one thread per node of a wall face (slip wall + wall model).
+// ---------------------------------------------------------------------------
+template <int N, typename R>
+__global__ void __launch_bounds__(128)
+k_wall(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, R* __restrict__ Fs,
+       double* __restrict__ tau_out, int* __restrict__ status) {
+  constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int wf = tid / n2, ab = tid - wf * n2;
+  if (wf >= m.n_wall) return;
+  const int f = m.n_interior + wf;
+  const int4 fc = m.faces[f];
+  const size_t S = (size_t)m.K * n3;
+  const size_t gM = (size_t)fc.x * n3 + fnode<N>(fc.y, ab % n, ab / n);
+  const size_t FN = (size_t)m.F * n2, fg = (size_t)f * n2 + ab;
+  const double nxd = m.fgeo[fg], nyd = m.fgeo[FN + fg], nzd = m.fgeo[2 * FN + fg], sd = m.fgeo[3 * FN + fg];
+  double UA[5], UB[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) UA[v] = U[v * S + gM];
+  const double mn = UA[1] * nxd + UA[2] * nyd + UA[3] * nzd;
+  UB[0] = UA[0]; UB[1] = UA[1] - 2.0 * mn * nxd; UB[2] = UA[2] - 2.0 * mn * nyd;
+  UB[3] = UA[3] - 2.0 * mn * nzd; UB[4] = UA[4];
+  const Prim<R> A = primitive<R>(UA[0], UA[1], UA[2], UA[3], UA[4], ph);
+  const Prim<R> B = primitive<R>(UB[0], UB[1], UB[2], UB[3], UB[4], ph);
+  R F[5];
+  riemann<R>(ph, A, UA, B, UB, (R)nxd, (R)nyd, (R)nzd, F);
+  double tau[3] = {0.0, 0.0, 0.0};
+  if (ph.viscous) {
+    // sample state at h_wm: tensor-product Lagrange interpolation of U
+    const size_t slot = (size_t)wf * n2 + ab;
+    const int es = m.ws_elem[slot];
+    const double* L = m.ws_lag + slot * 3 * n;
+    double Us[5] = {0, 0, 0, 0, 0};
+    for (int kk = 0; kk < n; ++kk)
+      for (int jj = 0; jj < n; ++jj) {
+        const double ljk = L[n + jj] * L[2 * n + kk];
+        double row[5] = {0, 0, 0, 0, 0};
+        for (int ii = 0; ii < n; ++ii) {
+          const size_t gs = (size_t)es * n3 + ii + n * (jj + n * kk);
+#pragma unroll
+          for (int v = 0; v < 5; ++v) row[v] += L[ii] * U[v * S + gs];
+        }
+#pragma unroll
+        for (int v = 0; v < 5; ++v) Us[v] += ljk * row[v];
+      }
+    bool ok;
+    wall_stress(ph, Us, nxd, nyd, nzd, tau, &ok);
+    if (!ok) atomicOr(status, ST_WM_NOCONV);
+    if (tau_out) {
+      tau_out[slot * 3 + 0] = tau[0]; tau_out[slot * 3 + 1] = tau[1]; tau_out[slot * 3 + 2] = tau[2];
+    }
+  }
+  // viscous wall flux Fv . n = (0, -tau_w t, 0): the wall decelerates the flow
+  R* out = Fs + (size_t)f * 5 * n2 + ab;
+  const R s = (R)sd;
+  out[0] = F[0] * s;
+  out[n2] = F[1] * s + (R)(tau[0] * sd);
+  out[2 * n2] = F[2] * s + (R)(tau[1] * sd);
+  out[3 * n2] = F[3] * s + (R)(tau[2] * sd);
+  out[4 * n2] = F[4] * s;
+}
+
+// ---------------------------------------------------------------------------
+// k_volume: one CTA of n^3 threads per element.  MODE 0 writes Ut; MODE 1
+// applies the LSERK4 stage to U and dU in place.
+// ---------------------------------------------------------------------------
+struct StageArgs {
+  double A, B, dt;
+  int read_dU;
+};
+
+template <int N, typename R, int MODE>
+__global__ void __launch_bounds__((N + 1) * (N + 1) * (N + 1))
+k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, const Tables<N> tab,
+         const R* __restrict__ Rv, const R* __restrict__ Fs, double* __restrict__ Out,
+         double* __restrict__ dU, double* __restrict__ Uout, const StageArgs st, int* __restrict__ status) {
+  constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* sQ = reinterpret_cast<R*>(smem_raw);  // [6][n3]: rho u v w p h
+  R* sA = sQ + 6 * n3;                      // [9][n3]: Ja (dir*3+comp)
+  R* sDVS = sA + 9 * n3;                    // [n2]
+  R* siw = sDVS + n2;                       // [n]
+  const int e = blockIdx.x, p = threadIdx.x;
+  const int i = p % n, j = (p / n) % n, k = p / n2;
+  const size_t S = (size_t)m.K * n3;
+  const size_t g = (size_t)e * n3 + p;
+  for (int t = p; t < n2; t += n3) sDVS[t] = (R)tab.DVS8[t];
+  if (p < n) siw[p] = (R)tab.iw[p];
+  double Uo[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) Uo[v] = Uin[v * S + g];
+  const Prim<R> qo = primitive<R>(Uo[0], Uo[1], Uo[2], Uo[3], Uo[4], ph);
+  sQ[p] = qo.rho; sQ[n3 + p] = qo.u; sQ[2 * n3 + p] = qo.v; sQ[3 * n3 + p] = qo.w;
+  sQ[4 * n3 + p] = qo.p; sQ[5 * n3 + p] = qo.h;
+#pragma unroll
+  for (int c = 0; c < 9; ++c) sA[c * n3 + p] = m.Ja[(size_t)c * S + g];
+  const R iJ = m.invJ[g];
+  __syncthreads();
+  R acc[5] = {0, 0, 0, 0, 0};
+  // split-form volume integral: sum_dir sum_m DVS_im F#(p, m) . {Ja^dir}
+#pragma unroll
+  for (int dir = 0; dir < 3; ++dir) {
+    const int idx = dir == 0 ? i : (dir == 1 ? j : k);
+    const int base = p - idx * (dir == 0 ? 1 : (dir == 1 ? n : n2));
+    const int stride = dir == 0 ? 1 : (dir == 1 ? n : n2);
+    const R a0 = sA[(dir * 3 + 0) * n3 + p], a1 = sA[(dir * 3 + 1) * n3 + p], a2 = sA[(dir * 3 + 2) * n3 + p];
+#pragma unroll
+    for (int mm = 0; mm < n; ++mm) {
+      if (mm == idx) continue;
+      const int q = base + mm * stride;
+      Prim<R> qm;
+      qm.rho = sQ[q]; qm.u = sQ[n3 + q]; qm.v = sQ[2 * n3 + q]; qm.w = sQ[3 * n3 + q];
+      qm.p = sQ[4 * n3 + q]; qm.h = sQ[5 * n3 + q];
+      R F[5];
+      // metric average {Ja} = (Ja_p + Ja_m) / 2; DVS8 carries 2D/8 so the
+      // flux is evaluated with 4 {Ja} ... folded below as (Ja_p + Ja_m) * 4
+      twopoint<R>(ph.vol_flux, qo, qm, a0 + sA[(dir * 3 + 0) * n3 + q], a1 + sA[(dir * 3 + 1) * n3 + q],
+                  a2 + sA[(dir * 3 + 2) * n3 + q], F);
+      const R c = R(4) * sDVS[idx * n + mm];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) acc[v] += c * F[v];
+    }
+  }
+  if (ph.viscous) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[v + 1] += Rv[(size_t)v * S + g];
+  }
+  // surface integral: + sgn * Fs / w_perp on the faces that touch p
+  auto surf = [&](int l, int ab, R iw) {
+    const int code = m.elem_face[e * 6 + l];
+    const int f = code >> 1;
+    const R sg = (code & 1) ? -iw : iw;
+    const R* src = Fs + (size_t)f * 5 * n2 + ab;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) acc[v] += sg * src[v * n2];
+  };
+  if (i == 0) surf(0, j + n * k, siw[0]);
+  if (i == N) surf(1, j + n * k, siw[N]);
+  if (j == 0) surf(2, i + n * k, siw[0]);
+  if (j == N) surf(3, i + n * k, siw[N]);
+  if (k == 0) surf(4, i + n * j, siw[0]);
+  if (k == N) surf(5, i + n * j, siw[N]);
+  // Ut = -(1/J) acc + S, S = (0, f, f . u)
+  double Ut[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) Ut[v] = -(double)(iJ * acc[v]);
+  {
+    const double ir = 1.0 / Uo[0];
+    Ut[1] += ph.f[0]; Ut[2] += ph.f[1]; Ut[3] += ph.f[2];
+    Ut[4] += (ph.f[0] * Uo[1] + ph.f[1] * Uo[2] + ph.f[2] * Uo[3]) * ir;
+  }
+  if (MODE == 0) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) Out[v * S + g] = Ut[v];
+  } else {
+    bool bad = false;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      const double d = st.read_dU ? fma(st.A, dU[v * S + g], st.dt * Ut[v]) : st.dt * Ut[v];
+      const double un = fma(st.B, d, Uo[v]);
+      dU[v * S + g] = d;
+      Uout[v * S + g] = un;
+      bad |= !finite_bits(un);
+    }
+    if (bad) atomicOr(status, ST_NONFINITE);
+  }
+}
+
+}  // namespace dg

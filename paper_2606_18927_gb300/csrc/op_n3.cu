@@ -1,0 +1,3 @@
+// Kernel instantiations and launch code for polynomial degree N = 3.
+#include "ops_impl.cuh"
+DG_DEFINE_N(3)

@@ -1,0 +1,3 @@
+// Kernel instantiations and launch code for polynomial degree N = 5.
+#include "ops_impl.cuh"
+DG_DEFINE_N(5)

@@ -1,0 +1,52 @@
+// ops.h -- internal interface between the C API and the per-degree kernel
+// instantiations (one translation unit per polynomial degree N).
+#pragma once
+#include <cuda_runtime.h>
+
+namespace dg {
+
+struct PhysDev;
+
+struct OpArgs {
+  int N, K, F, n_interior, n_wall;
+  int fp32;                 // 0: double fluxes, 1: float fluxes (mixed form)
+  const void* Ja;           // [9][K n^3] in the flux type
+  const void* invJ;         // [K n^3] in the flux type
+  const double* fgeo;
+  const int* nbr;
+  const int* elem_face;
+  const int4* faces;
+  const int* ws_elem;
+  const double* ws_lag;
+  const double* D;          // host basis: D[n*n], w[n]
+  const double* w;
+  const double* Uin;        // state read by the operator
+  void* Rv;                 // scratch in the flux type
+  void* Gf;
+  void* Fs;
+  double* tau;              // wall shear per wall node (may be null)
+  int* status;
+  int mode;                 // 0: Ut -> Out; 1: LSERK4 stage on dU, Uout
+  double* Out;
+  double* dU;
+  double* Uout;
+  double A, B, dt;
+  int read_dU;
+  cudaEvent_t* ev;          // null, or 5 events recorded around lift, face, wall, volume
+};
+
+// Launches lift (if viscous), face, wall and volume kernels on the stream.
+int run_operator(const OpArgs& a, const PhysDev& ph, cudaStream_t s);
+
+#define DG_DECLARE_N(NN) int run_operator_n##NN(const OpArgs& a, const PhysDev& ph, cudaStream_t s);
+DG_DECLARE_N(1)
+DG_DECLARE_N(2)
+DG_DECLARE_N(3)
+DG_DECLARE_N(4)
+DG_DECLARE_N(5)
+DG_DECLARE_N(6)
+DG_DECLARE_N(7)
+DG_DECLARE_N(8)
+#undef DG_DECLARE_N
+
+}  // namespace dg

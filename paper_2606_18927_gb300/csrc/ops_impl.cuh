@@ -1,0 +1,76 @@
+// ops_impl.cuh -- host launch code for one polynomial degree (included by
+// op_n<N>.cu with DG_N defined).
+#pragma once
+#include "kernels.cuh"
+#include "ops.h"
+
+namespace dg {
+
+template <int N>
+static Tables<N> make_tables(const double* D, const double* w) {
+  constexpr int n = N + 1;
+  Tables<N> t;
+  for (int i = 0; i < n; ++i) {
+    t.iw[i] = 1.0 / w[i];
+    for (int m = 0; m < n; ++m) {
+      double dvs = 2.0 * D[i * n + m];
+      if (i == m && i == 0) dvs += 1.0 / w[0];
+      if (i == m && i == N) dvs -= 1.0 / w[N];
+      t.D[i * n + m] = D[i * n + m];
+      t.DVS8[i * n + m] = dvs / 8.0;
+      t.Dvisc[i * n + m] = w[m] / w[i] * D[m * n + i];
+    }
+  }
+  return t;
+}
+
+template <int N, typename R>
+static int run_typed(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {
+  constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
+  MeshDev<R> m;
+  m.K = a.K; m.F = a.F; m.n_interior = a.n_interior; m.n_wall = a.n_wall;
+  m.Ja = static_cast<const R*>(a.Ja); m.invJ = static_cast<const R*>(a.invJ);
+  m.fgeo = a.fgeo; m.nbr = a.nbr; m.elem_face = a.elem_face; m.faces = a.faces;
+  m.ws_elem = a.ws_elem; m.ws_lag = a.ws_lag;
+  const Tables<N> tab = make_tables<N>(a.D, a.w);
+  R* Rv = static_cast<R*>(a.Rv);
+  R* Gf = static_cast<R*>(a.Gf);
+  R* Fs = static_cast<R*>(a.Fs);
+  const size_t smem_lift = (size_t)(16 * n3 + 26 * n2 + n) * sizeof(R);
+  const size_t smem_vol = (size_t)(15 * n3 + n2 + n) * sizeof(R);
+  // per device and cheap: set on every call
+  cudaFuncSetAttribute(k_lift<N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_lift);
+  cudaFuncSetAttribute(k_volume<N, R, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_vol);
+  cudaFuncSetAttribute(k_volume<N, R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_vol);
+  if (a.ev) cudaEventRecord(a.ev[0], s);
+  if (ph.viscous) k_lift<N, R><<<a.K, n3, smem_lift, s>>>(a.Uin, m, ph, tab, Rv, Gf);
+  if (a.ev) cudaEventRecord(a.ev[1], s);
+  if (a.n_interior > 0) {
+    const int threads = 256;
+    const long long work = (long long)a.n_interior * n2;
+    k_face<N, R><<<(unsigned)((work + threads - 1) / threads), threads, 0, s>>>(a.Uin, m, ph, Gf, Fs);
+  }
+  if (a.ev) cudaEventRecord(a.ev[2], s);
+  if (a.n_wall > 0) {
+    const int threads = 128;
+    const long long work = (long long)a.n_wall * n2;
+    k_wall<N, R><<<(unsigned)((work + threads - 1) / threads), threads, 0, s>>>(a.Uin, m, ph, Fs, a.tau, a.status);
+  }
+  if (a.ev) cudaEventRecord(a.ev[3], s);
+  StageArgs st{a.A, a.B, a.dt, a.read_dU};
+  if (a.mode == 0)
+    k_volume<N, R, 0><<<a.K, n3, smem_vol, s>>>(a.Uin, m, ph, tab, Rv, Fs, a.Out, nullptr, nullptr, st, a.status);
+  else
+    k_volume<N, R, 1><<<a.K, n3, smem_vol, s>>>(a.Uin, m, ph, tab, Rv, Fs, nullptr, a.dU, a.Uout, st, a.status);
+  if (a.ev) cudaEventRecord(a.ev[4], s);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace dg
+
+#define DG_DEFINE_N(NN)                                                              \
+  namespace dg {                                                                     \
+  int run_operator_n##NN(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {      \
+    return a.fp32 ? run_typed<NN, float>(a, ph, s) : run_typed<NN, double>(a, ph, s); \
+  }                                                                                  \
+  }

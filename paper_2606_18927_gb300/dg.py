@@ -1,0 +1,220 @@
+"""Python binding of libdg_gb300.so (the C ABI declared in include/dg.h).
+
+Argument marshalling only: every step of the operator runs in the library's
+sm_103a kernels.  Device arrays are torch CUDA tensors (float64, contiguous,
+SoA layout [5][K][n^3]); the stream is torch's current stream unless one is
+given.  There is no CPU fallback: if the library cannot be loaded or a call
+fails, an exception is raised.
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+
+from . import build as _build
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+HEADER = os.path.join(_HERE, "..", "include", "dg.h")
+
+FP64, FP32_MIXED = 0, 1
+VOL_KEP_PIROZZOLI, VOL_KEP_KENNEDY_GRUBER = 0, 1
+SURF_CENTRAL, SURF_LLF, SURF_ROE = 0, 1, 2
+LAW_SPALDING, LAW_REICHARDT = 0, 1
+
+ERRORS = {
+    -1: "DG_ERR_ARG", -2: "DG_ERR_NOT_INIT", -3: "DG_ERR_MESH", -4: "DG_ERR_CUDA",
+    -5: "DG_ERR_NONFINITE", -6: "DG_ERR_WM_NOCONV", -7: "DG_ERR_DEVICE_BOUNDS",
+    -8: "DG_ERR_NOT_IMPLEMENTED", -9: "DG_ERR_OOM",
+}
+
+
+class DGError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (ERRORS.get(code, "?"), code, msg))
+        self.code = code
+
+
+class _MeshDesc(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("K", ctypes.c_int),
+                ("X", ctypes.POINTER(ctypes.c_double)), ("nbr", ctypes.POINTER(ctypes.c_int))]
+
+
+class _Phys(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_double), ("R", ctypes.c_double), ("mu", ctypes.c_double),
+                ("Pr", ctypes.c_double), ("force", ctypes.c_double * 3), ("kappa", ctypes.c_double),
+                ("B", ctypes.c_double), ("hwm", ctypes.c_double), ("law", ctypes.c_int)]
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("vol_flux", ctypes.c_int), ("surf_flux", ctypes.c_int),
+                ("viscous", ctypes.c_int)]
+
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def lib():
+    """Load (building first if needed) the shared library."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build()
+    L = ctypes.CDLL(path)
+    vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
+    c_int, c_double = ctypes.c_int, ctypes.c_double
+    sig = {
+        "dg_lgl_nodes": (c_int, [c_int, dp, dp]),
+        "dg_init_mesh": (c_int, [ctypes.POINTER(vp), ctypes.POINTER(_MeshDesc), ctypes.POINTER(_Phys),
+                                 ctypes.POINTER(_Options), vp]),
+        "dg_destroy": (c_int, [vp]),
+        "dg_last_error": (ctypes.c_char_p, [vp]),
+        "dg_set_stream": (c_int, [vp, vp]),
+        "dg_sizes": (c_int, [vp, ip, ip, ctypes.POINTER(ctypes.c_longlong)]),
+        "dg_set_state": (c_int, [vp, vp, c_int]),
+        "dg_get_state": (c_int, [vp, vp, c_int]),
+        "dg_time_derivative": (c_int, [vp, vp, vp, c_double, c_int]),
+        "dg_rk_stage": (c_int, [vp, c_int, c_double, c_double]),
+        "dg_rk_steps": (c_int, [vp, c_double, c_double, c_int]),
+        "dg_check_status": (c_int, [vp]),
+        "dg_get_metrics": (c_int, [vp, dp, dp]),
+        "dg_profile_enable": (c_int, [vp, c_int]),
+        "dg_profile_read": (c_int, [vp, dp, ip]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def header_functions():
+    """Names of every function declared in include/dg.h."""
+    with open(HEADER) as f:
+        txt = f.read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_]+\s*\**\s*(dg_[a-z0-9_]+)\s*\(", txt, re.M)))
+
+
+def lgl_nodes(N):
+    x = np.zeros(N + 1); w = np.zeros(N + 1)
+    rc = lib().dg_lgl_nodes(N, x.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                            w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    if rc != 0:
+        raise DGError(rc, lib().dg_last_error(None).decode())
+    return x, w
+
+
+def _ptr(t):
+    """Device or host address of a tensor / array, and whether it is on the device."""
+    if isinstance(t, np.ndarray):
+        assert t.dtype == np.float64 and t.flags.c_contiguous
+        return ctypes.c_void_p(t.ctypes.data), 0
+    assert t.dtype.is_floating_point and t.is_contiguous()
+    return ctypes.c_void_p(t.data_ptr()), 1 if t.is_cuda else 0
+
+
+def _stream_handle(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Operator:
+    """Ut = DG_Operator(U) and LSERK4 stages on one mesh (one GPU)."""
+
+    def __init__(self, N, X, nbr, phys, precision=FP64, vol_flux=VOL_KEP_PIROZZOLI, surf_flux=SURF_LLF,
+                 viscous=1, law=LAW_REICHARDT, stream=None):
+        L = lib()
+        self.N = int(N)
+        self.n3 = (self.N + 1) ** 3
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        nbr = np.ascontiguousarray(nbr, dtype=np.int32)
+        self.K = X.size // (3 * self.n3)
+        md = _MeshDesc(self.N, self.K, X.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                       nbr.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+        ph = _Phys(phys["gamma"], phys["R"], phys["mu"], phys["Pr"],
+                   (ctypes.c_double * 3)(phys.get("fx", 0.0), phys.get("fy", 0.0), phys.get("fz", 0.0)),
+                   phys.get("kappa", 0.41), phys.get("B", 5.2), phys.get("hwm", 0.1), int(law))
+        op = _Options(int(precision), int(vol_flux), int(surf_flux), int(viscous))
+        h = ctypes.c_void_p()
+        self._stream = _stream_handle(stream)
+        rc = L.dg_init_mesh(ctypes.byref(h), ctypes.byref(md), ctypes.byref(ph), ctypes.byref(op), self._stream)
+        if rc != 0:
+            raise DGError(rc, L.dg_last_error(None).decode())
+        self.h = h
+        self.shape = (5, self.K, self.n3)
+        self.numel = 5 * self.K * self.n3
+        self.dofs = self.K * self.n3
+        self.precision = precision
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().dg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != 0:
+            raise DGError(rc, lib().dg_last_error(self.h).decode())
+
+    def set_stream(self, stream):
+        self._stream = _stream_handle(stream)
+        self._check(lib().dg_set_stream(self.h, self._stream))
+
+    def set_state(self, U):
+        p, dev = _ptr(U)
+        count = U.numel() if hasattr(U, "numel") else U.size
+        if count != self.numel:
+            raise ValueError("state has %d values, expected %d" % (count, self.numel))
+        self._check(lib().dg_set_state(self.h, p, dev))
+
+    def get_state(self, out):
+        p, dev = _ptr(out)
+        self._check(lib().dg_get_state(self.h, p, dev))
+        return out
+
+    def time_derivative(self, Ut, U=None, t=0.0):
+        """Ut <- DG_Operator(U) (U None: the context's state).  Ut and U are
+        both device tensors or both host arrays."""
+        po, dev = _ptr(Ut)
+        pu = None
+        if U is not None:
+            pu, devu = _ptr(U)
+            assert devu == dev
+        self._check(lib().dg_time_derivative(self.h, pu, po, float(t), dev))
+        return Ut
+
+    def rk_stage(self, s, t, dt):
+        self._check(lib().dg_rk_stage(self.h, int(s), float(t), float(dt)))
+
+    def rk_steps(self, t, dt, nsteps):
+        self._check(lib().dg_rk_steps(self.h, float(t), float(dt), int(nsteps)))
+
+    def check_status(self):
+        self._check(lib().dg_check_status(self.h))
+
+    def profile_enable(self, on=True):
+        self._check(lib().dg_profile_enable(self.h, 1 if on else 0))
+
+    def profile_read(self):
+        """{kernel: (total ms, launches)} since the last read (lift, face, wall, volume)."""
+        ms = np.zeros(4); cnt = np.zeros(4, dtype=np.int32)
+        self._check(lib().dg_profile_read(self.h, ms.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                          cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_int))))
+        return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(("lift", "face", "wall", "volume"))}
+
+    def metrics(self):
+        Ja = np.zeros((self.K, self.n3, 3, 3)); J = np.zeros((self.K, self.n3))
+        self._check(lib().dg_get_metrics(self.h, Ja.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                         J.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return Ja, J

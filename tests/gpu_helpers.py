@@ -1,0 +1,45 @@
+"""Shared set-up of the GPU parity tests (no method arithmetic)."""
+import numpy as np
+
+from paper_2606_18927_gb300 import dg, inputs as I
+
+
+def torch_cuda():
+    import pytest
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def case(ora, spec, phys, surf_flux=1, vol_flux=0, viscous=1, law=1, precision=0, ic="tgv", rel=1e-3):
+    """Oracle and GPU operator on the same mesh nodes (the oracle's LGL
+    nodes) and the same seeded state."""
+    x, w, D = ora.lgl(spec.N)
+    X = I.node_coordinates(spec, x)
+    nbr = I.connectivity(spec)
+    o = ora.Oracle(spec.N, X, nbr, phys, vol_flux=vol_flux, surf_flux=surf_flux, viscous=viscous, law=law)
+    g = dg.Operator(spec.N, X, nbr, phys, precision=precision, vol_flux=vol_flux, surf_flux=surf_flux,
+                    viscous=viscous, law=law)
+    if ic == "tgv":
+        U = I.perturb(I.taylor_green(X, phys), rel=rel)
+    elif ic == "channel":
+        U = I.channel_profile(X, phys)
+    else:
+        U = I.free_stream(X, phys)
+    return o, g, X, U
+
+
+def gpu_ut(torch, g, U):
+    Ud = torch.from_numpy(U).cuda()
+    Ut = torch.empty_like(Ud)
+    g.time_derivative(Ut, Ud)
+    torch.cuda.synchronize()
+    g.check_status()
+    return Ut.cpu().numpy()
+
+
+def parity(a, ref):
+    """max over variables of max|a_v - ref_v| / max|ref_v|."""
+    a = a.reshape(5, -1); ref = ref.reshape(5, -1)
+    return max(float(np.abs(a[v] - ref[v]).max() / max(np.abs(ref[v]).max(), 1e-300)) for v in range(5))

@@ -1,0 +1,118 @@
+"""Parity of the sm_103a FP64 operator with the CPU oracle (paper Sec. 2.2 /
+Sec. 4 split-form DGSEM, Sec. 3 wall model), element by element on the same
+seeded inputs, through the C ABI.
+
+Tolerance: relative max-norm 1e-12 per variable (normalised by max|Ut_v| of
+the oracle), the FP64 parity target of the operator."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2606_18927_gb300 import inputs as I
+from gpu_helpers import case, gpu_ut, parity, torch_cuda
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+
+@pytest.mark.parametrize("label,spec,surf,vol,visc", [
+    ("tgv_n3_4^3_llf", I.BoxSpec(3, 4, 4, 4), 1, 0, 1),
+    ("n2_ragged_sine_roe", I.BoxSpec(2, 3, 2, 5, geometry="sine", amplitude=0.3), 2, 0, 1),
+    ("n4_central_kg", I.BoxSpec(4, 2, 3, 2, geometry="sine", amplitude=0.2), 0, 1, 1),
+    ("n5_roe_euler", I.BoxSpec(5, 2, 2, 3, geometry="sine", amplitude=0.2), 2, 0, 0),
+    ("n7_roe_sine", I.BoxSpec(7, 2, 2, 2, geometry="sine", amplitude=0.1), 2, 0, 1),
+    ("n1_llf", I.BoxSpec(1, 3, 3, 3), 1, 0, 1),
+    ("n6_llf_periodic_self", I.BoxSpec(6, 1, 2, 1), 1, 0, 1),
+    ("n8_roe", I.BoxSpec(8, 2, 1, 2, geometry="sine", amplitude=0.1), 2, 0, 1),
+])
+def test_time_derivative_matches_oracle(ora, label, spec, surf, vol, visc):
+    torch = torch_cuda()
+    phys = I.phys_params(Ma=0.1, Re=1600.0)
+    o, g, X, U = case(ora, spec, phys, surf_flux=surf, vol_flux=vol, viscous=visc)
+    ref = o.time_derivative(U)
+    out = gpu_ut(torch, g, U)
+    e = parity(out, ref)
+    print(label, "parity", e)
+    assert e <= TOL, e
+
+
+@pytest.mark.parametrize("law", [1, 0])
+def test_wall_model_channel_matches_oracle(ora, law):
+    torch = torch_cuda()
+    wl = I.workload("channel_n5", N=3, elems=(4, 4, 2))
+    o, g, X, U = case(ora, wl.spec, wl.phys, surf_flux=2, law=law, ic="channel")
+    ref = o.time_derivative(U)
+    out = gpu_ut(torch, g, U)
+    e = parity(out, ref)
+    print("channel law", law, "parity", e)
+    assert e <= TOL, e
+
+
+def test_channel_full_size_matches_oracle(ora):
+    """16 x 8 x 8 elements, N = 5 (221,184 DOF), Reichardt wall model."""
+    torch = torch_cuda()
+    wl = I.workload("channel_n5")
+    o, g, X, U = case(ora, wl.spec, wl.phys, surf_flux=2, law=1, ic="channel")
+    e = parity(gpu_ut(torch, g, U), o.time_derivative(U))
+    print("channel full parity", e)
+    assert e <= TOL, e
+
+
+def test_rk_step_matches_oracle(ora):
+    torch = torch_cuda()
+    phys = I.phys_params(Ma=0.1, Re=1600.0)
+    spec = I.BoxSpec(3, 4, 4, 4)
+    o, g, X, U = case(ora, spec, phys, surf_flux=1)
+    dt = o.dt(U, 0.9)
+    Ud = torch.from_numpy(U).cuda()
+    g.set_state(Ud)
+    nsteps = 2
+    g.rk_steps(0.0, dt, nsteps)
+    Ug = torch.empty_like(Ud)
+    g.get_state(Ug)
+    g.check_status()
+    Uo = o.rk_steps(U, dt, nsteps)
+    # compare the change of the state over the steps
+    e = parity(Ug.cpu().numpy() - U, Uo - U)
+    print("rk steps parity (increment)", e)
+    assert e <= TOL, e
+
+
+def test_single_stage_dU(ora):
+    torch = torch_cuda()
+    phys = I.phys_params(Ma=0.1, Re=1600.0)
+    spec = I.BoxSpec(4, 3, 2, 2, geometry="sine", amplitude=0.2)
+    o, g, X, U = case(ora, spec, phys, surf_flux=2)
+    dt = 1e-3
+    g.set_state(torch.from_numpy(U).cuda())
+    Uo = U.copy(); dUo = np.zeros_like(U)
+    for s in range(3):
+        g.rk_stage(s, 0.0, dt)
+        o.rk_stage(Uo, dUo, s, 0.0, dt)
+    Ug = torch.empty(U.shape, dtype=torch.float64, device="cuda")
+    g.get_state(Ug)
+    e = parity(Ug.cpu().numpy() - U, Uo - U)
+    assert e <= TOL, e
+
+
+def test_host_pointer_path(ora):
+    """dg_time_derivative with host arrays (upload, operator, download)."""
+    torch = torch_cuda()
+    phys = I.phys_params()
+    o, g, X, U = case(ora, I.BoxSpec(3, 2, 2, 2), phys)
+    Ut = np.zeros_like(U)
+    g.time_derivative(Ut, U)
+    assert parity(Ut, o.time_derivative(U)) <= TOL
+
+
+@pytest.mark.parametrize("N,ne", [(3, 8), (5, 4)])
+def test_free_stream_and_conservation_on_device(ora, N, ne):
+    torch = torch_cuda()
+    phys = I.phys_params(Ma=0.3)
+    spec = I.BoxSpec(N, ne, ne, ne, geometry="sine", amplitude=0.1)
+    o, g, X, U = case(ora, spec, phys, surf_flux=2, ic="free")
+    Ut = gpu_ut(torch, g, U)
+    ref = o.time_derivative(U)
+    # both at the roundoff floor, and of the same size
+    assert np.abs(Ut).max() < 1e-9 and np.abs(ref).max() < 1e-9
