@@ -82,12 +82,18 @@ typedef struct {
 /* Ideal gas and wall-model constants (paper Sec. 4: ideal gas; Sec. 3.2:
  * law of the wall).  mu is constant; kappa and B are the law's constants;
  * hwm the sampling distance of the wall model; force a constant body force
- * per unit volume entering momentum (and its work f.u the energy). */
+ * per unit volume entering momentum (and its work f.u the energy).
+ * p_ref: a constant subtracted from the pressure inside the momentum fluxes.
+ * A constant pressure integrates to zero over every element (discrete
+ * metric identities of the curl-form metrics), so the operator is unchanged
+ * in exact arithmetic; setting p_ref to the ambient pressure removes the
+ * cancellation of O(p_ref) terms at low Mach number (0 disables it). */
 typedef struct {
   double gamma, R, mu, Pr;
   double force[3];
   double kappa, B, hwm;
   int law; /* dg_wall_law */
+  double p_ref;
 } dg_phys;
 
 typedef struct {
@@ -137,6 +143,12 @@ int dg_rk_stage(dg_ctx* c, int s, double t, double dt);
 
 /* nsteps full LSERK4 steps from time t. */
 int dg_rk_steps(dg_ctx* c, double t, double dt, int nsteps);
+
+/* Copies the LSERK4 register dU (5 K n^3 doubles) out of / into the context
+ * (checkpoint and restart inside a step; between steps dU needs no saving
+ * because A_0 = 0). */
+int dg_get_rk_register(dg_ctx* c, double* dU, int on_device);
+int dg_set_rk_register(dg_ctx* c, const double* dU, int on_device);
 
 /* Reads and clears the device status flags.  Returns DG_OK,
  * DG_ERR_NONFINITE or DG_ERR_WM_NOCONV (synchronises the stream). */

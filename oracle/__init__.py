@@ -13,15 +13,15 @@ import numpy as np
 
 from . import build as _build
 
-_lib = None
+_libs = {}
 
 PHYS_KEYS = ("gamma", "R", "mu", "Pr", "fx", "fy", "fz", "kappa", "B", "hwm")
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        path = _build.build()
+def lib(extended=False):
+    """The FP64 oracle library, or its extended-precision build."""
+    if extended not in _libs:
+        path = _build.build(extended=extended)
         L = ctypes.CDLL(path)
         dp = ctypes.POINTER(ctypes.c_double)
         ip = ctypes.POINTER(ctypes.c_int)
@@ -51,8 +51,9 @@ def lib():
         L.ora_law_value.restype = ctypes.c_double
         L.ora_wall_flux.argtypes = [dp, ctypes.c_int, dp, dp, dp, dp]
         L.ora_riemann.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp]
-        _lib = L
-    return _lib
+        L.ora_real_digits.restype = ctypes.c_int
+        _libs[extended] = L
+    return _libs[extended]
 
 
 def _p(a):
@@ -94,9 +95,14 @@ def phys_array(phys):
 
 
 class Oracle:
-    """One mesh + parameter set.  U arrays are SoA [5][K][n^3] float64."""
+    """One mesh + parameter set.  U arrays are SoA [5][K][n^3] float64.
 
-    def __init__(self, N, X, nbr, phys, vol_flux=0, surf_flux=1, viscous=1, law=1):
+    extended=True evaluates everything (geometry included) in long double and
+    rounds the results to double: the parity reference."""
+
+    def __init__(self, N, X, nbr, phys, vol_flux=0, surf_flux=1, viscous=1, law=1, extended=False):
+        self.L = lib(extended)
+        self.extended = extended
         self.N = int(N)
         self.n = self.N + 1
         self.n3 = self.n ** 3
@@ -106,7 +112,7 @@ class Oracle:
         self._phys = phys_array(phys)
         opts = np.array([vol_flux, surf_flux, viscous, law], dtype=np.int32)
         err = ctypes.create_string_buffer(512)
-        self.h = lib().ora_create(self.N, self.K, _p(X), _ip(nbr), _p(self._phys), _ip(opts), err, 512)
+        self.h = self.L.ora_create(self.N, self.K, _p(X), _ip(nbr), _p(self._phys), _ip(opts), err, 512)
         if not self.h:
             raise ValueError("oracle mesh rejected: " + err.value.decode())
         self.shape = (5, self.K, self.n3)
@@ -114,23 +120,23 @@ class Oracle:
     def __del__(self):
         h = getattr(self, "h", None)
         if h:
-            lib().ora_destroy(h)
+            self.L.ora_destroy(h)
             self.h = None
 
     def metrics(self):
         Ja = np.zeros((self.K, self.n3, 3, 3)); J = np.zeros((self.K, self.n3))
-        lib().ora_get_metrics(self.h, _p(Ja), _p(J))
+        self.L.ora_get_metrics(self.h, _p(Ja), _p(J))
         return Ja, J
 
     def wall_samples(self):
-        nw = lib().ora_num_wall(self.h)
+        nw = self.L.ora_num_wall(self.h)
         el = np.zeros(nw, dtype=np.int32); ref = np.zeros((nw, 3))
-        lib().ora_get_wall_samples(self.h, _ip(el), _p(ref))
+        self.L.ora_get_wall_samples(self.h, _ip(el), _p(ref))
         return el, ref
 
     def time_derivative(self, U, t=0.0):
         U = _f64(U); Ut = np.zeros_like(U)
-        st = lib().ora_time_derivative(self.h, _p(U), float(t), _p(Ut))
+        st = self.L.ora_time_derivative(self.h, _p(U), float(t), _p(Ut))
         if st != 0:
             raise RuntimeError("oracle wall model did not converge")
         return Ut
@@ -140,7 +146,7 @@ class Oracle:
         dptr = None
         if dU is not None:
             dU = _f64(dU); dptr = _p(dU)
-        st = lib().ora_jvp(self.h, _p(U), dptr, float(dkappa), float(dB), float(t), _p(Ut), _p(dUt))
+        st = self.L.ora_jvp(self.h, _p(U), dptr, float(dkappa), float(dB), float(t), _p(Ut), _p(dUt))
         if st != 0:
             raise RuntimeError("oracle wall model did not converge")
         return Ut, dUt
@@ -149,21 +155,21 @@ class Oracle:
         """In-place LSERK4 stage on float64 arrays U, dU."""
         assert U.dtype == np.float64 and U.flags.c_contiguous
         assert dU.dtype == np.float64 and dU.flags.c_contiguous
-        return lib().ora_rk_stage(self.h, _p(U), _p(dU), int(s), float(t), float(dt))
+        return self.L.ora_rk_stage(self.h, _p(U), _p(dU), int(s), float(t), float(dt))
 
     def rk_steps(self, U, dt, nsteps, t0=0.0):
         U = _f64(U).copy()
-        lib().ora_rk_steps(self.h, _p(U), float(t0), float(dt), int(nsteps))
+        self.L.ora_rk_steps(self.h, _p(U), float(t0), float(dt), int(nsteps))
         return U
 
     def dt(self, U, cfl=0.9):
         U = _f64(U); out = np.zeros(1)
-        lib().ora_dt(self.h, _p(U), float(cfl), _p(out))
+        self.L.ora_dt(self.h, _p(U), float(cfl), _p(out))
         return float(out[0])
 
     def wall_shear(self, U):
         U = _f64(U); out = np.zeros(1)
-        st = lib().ora_wall_shear(self.h, _p(U), _p(out))
+        st = self.L.ora_wall_shear(self.h, _p(U), _p(out))
         if st != 0:
             raise RuntimeError("oracle wall model did not converge")
         return float(out[0])
@@ -174,7 +180,7 @@ class Oracle:
         dptr = None
         if dU0 is not None:
             dU0 = _f64(dU0); dptr = _p(dU0)
-        st = lib().ora_rollout_jvp(self.h, _p(U0), dptr, float(dkappa), float(dB), int(nsteps),
+        st = self.L.ora_rollout_jvp(self.h, _p(U0), dptr, float(dkappa), float(dB), int(nsteps),
                                    float(dt), _p(loss), _p(dl))
         if st != 0:
             raise RuntimeError("oracle wall model did not converge")
@@ -182,7 +188,7 @@ class Oracle:
 
     def kinetic_energy(self, U):
         U = _f64(U); out = np.zeros(1)
-        lib().ora_kinetic_energy(self.h, _p(U), _p(out))
+        self.L.ora_kinetic_energy(self.h, _p(U), _p(out))
         return float(out[0])
 
 

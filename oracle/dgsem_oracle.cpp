@@ -29,6 +29,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <limits>
 #include <string>
 #include <type_traits>
 #include <vector>
@@ -36,36 +37,45 @@
 #include <omp.h>
 #endif
 
+#ifndef ORA_REAL
+#define ORA_REAL double
+#endif
+
 namespace ora {
+
+// Base floating-point type of the whole oracle: double for the FP64 oracle
+// (the CPU baseline and every pin), long double for the extended-precision
+// build used as the parity reference.
+typedef ORA_REAL real;
 
 // ---------------------------------------------------------------------------
 // Forward-mode dual number (value, one directional derivative).
 // ---------------------------------------------------------------------------
 struct Dual {
-  double v, d;
-  Dual(double x = 0.0, double dx = 0.0) : v(x), d(dx) {}
+  real v, d;
+  Dual(real x = 0.0, real dx = 0.0) : v(x), d(dx) {}
 };
 inline Dual operator+(Dual a, Dual b) { return Dual(a.v + b.v, a.d + b.d); }
 inline Dual operator-(Dual a, Dual b) { return Dual(a.v - b.v, a.d - b.d); }
 inline Dual operator-(Dual a) { return Dual(-a.v, -a.d); }
 inline Dual operator*(Dual a, Dual b) { return Dual(a.v * b.v, a.d * b.v + a.v * b.d); }
 inline Dual operator/(Dual a, Dual b) {
-  double r = a.v / b.v;
+  real r = a.v / b.v;
   return Dual(r, (a.d - r * b.d) / b.v);
 }
 inline Dual& operator+=(Dual& a, Dual b) { a = a + b; return a; }
 inline Dual& operator-=(Dual& a, Dual b) { a = a - b; return a; }
 inline Dual& operator*=(Dual& a, Dual b) { a = a * b; return a; }
-inline Dual sqrt(Dual a) { double s = std::sqrt(a.v); return Dual(s, a.d / (2.0 * s)); }
-inline Dual exp(Dual a) { double e = std::exp(a.v); return Dual(e, a.d * e); }
+inline Dual sqrt(Dual a) { real s = std::sqrt(a.v); return Dual(s, a.d / (2.0 * s)); }
+inline Dual exp(Dual a) { real e = std::exp(a.v); return Dual(e, a.d * e); }
 inline Dual log(Dual a) { return Dual(std::log(a.v), a.d / a.v); }
 inline Dual asin(Dual a) { return Dual(std::asin(a.v), a.d / std::sqrt(1.0 - a.v * a.v)); }
 inline Dual fabs(Dual a) { return a.v < 0.0 ? -a : a; }
 
-inline double val(double x) { return x; }
-inline double val(const Dual& x) { return x.v; }
-inline double der(double) { return 0.0; }
-inline double der(const Dual& x) { return x.d; }
+inline real val(real x) { return x; }
+inline real val(const Dual& x) { return x.v; }
+inline real der(real) { return 0.0; }
+inline real der(const Dual& x) { return x.d; }
 
 using std::sqrt; using std::exp; using std::log; using std::asin; using std::fabs;
 
@@ -82,29 +92,29 @@ enum WallLaw { LAW_SPALDING = 0, LAW_REICHARDT = 1 };
 //    ODE).  Weights: w_i = 2 / (N (N+1) P_N(x_i)^2).
 //    D_ij = l_j'(x_i) from barycentric weights; D_ii = -sum_{j!=i} D_ij.
 // ---------------------------------------------------------------------------
-static void legendre(int N, double x, double* P, double* dP) {
+static void legendre(int N, real x, real* P, real* dP) {
   // P_N(x) and P_N'(x) by the three-term recurrence.
-  double p0 = 1.0, p1 = x, d0 = 0.0, d1 = 1.0;
+  real p0 = 1.0, p1 = x, d0 = 0.0, d1 = 1.0;
   if (N == 0) { *P = 1.0; *dP = 0.0; return; }
   for (int k = 2; k <= N; ++k) {
-    double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
-    double d2 = d0 + (2.0 * k - 1.0) * p1;  // P_k' = P_{k-2}' + (2k-1) P_{k-1}
+    real p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+    real d2 = d0 + (2.0 * k - 1.0) * p1;  // P_k' = P_{k-2}' + (2k-1) P_{k-1}
     p0 = p1; p1 = p2; d0 = d1; d1 = d2;
   }
   *P = p1; *dP = d1;
 }
 
-void lgl(int N, std::vector<double>& x, std::vector<double>& w, std::vector<double>& D) {
+void lgl(int N, std::vector<real>& x, std::vector<real>& w, std::vector<real>& D) {
   const int n = N + 1;
   x.assign(n, 0.0); w.assign(n, 0.0); D.assign(n * n, 0.0);
   x[0] = -1.0; x[N] = 1.0;
   for (int i = 1; i < N; ++i) {
-    double xi = -std::cos(M_PI * i / N);  // Chebyshev-Lobatto start
+    real xi = -std::cos(M_PI * i / N);  // Chebyshev-Lobatto start
     for (int it = 0; it < 100; ++it) {
-      double P, dP;
+      real P, dP;
       legendre(N, xi, &P, &dP);
-      double d2P = (2.0 * xi * dP - N * (N + 1.0) * P) / (1.0 - xi * xi);
-      double step = dP / d2P;
+      real d2P = (2.0 * xi * dP - N * (N + 1.0) * P) / (1.0 - xi * xi);
+      real step = dP / d2P;
       xi -= step;
       if (std::fabs(step) < 1e-16) break;
     }
@@ -112,21 +122,21 @@ void lgl(int N, std::vector<double>& x, std::vector<double>& w, std::vector<doub
   }
   // symmetrise (nodes are symmetric about 0)
   for (int i = 0; i < n / 2; ++i) {
-    double a = 0.5 * (x[N - i] - x[i]);
+    real a = 0.5 * (x[N - i] - x[i]);
     x[i] = -a; x[N - i] = a;
   }
   if (n % 2 == 1) x[N / 2] = 0.0;
   for (int i = 0; i < n; ++i) {
-    double P, dP;
+    real P, dP;
     legendre(N, x[i], &P, &dP);
     w[i] = 2.0 / (N * (N + 1.0) * P * P);
   }
-  std::vector<double> lam(n, 1.0);
+  std::vector<real> lam(n, 1.0);
   for (int j = 0; j < n; ++j)
     for (int k = 0; k < n; ++k)
       if (k != j) lam[j] /= (x[j] - x[k]);
   for (int i = 0; i < n; ++i) {
-    double s = 0.0;
+    real s = 0.0;
     for (int j = 0; j < n; ++j) {
       if (j == i) continue;
       D[i * n + j] = (lam[j] / lam[i]) / (x[i] - x[j]);
@@ -137,13 +147,13 @@ void lgl(int N, std::vector<double>& x, std::vector<double>& w, std::vector<doub
 }
 
 // Lagrange basis l_j(s) and l_j'(s) on the nodes x, by the product formula.
-static void lagrange(const std::vector<double>& x, double s, double* l, double* dl) {
+static void lagrange(const std::vector<real>& x, real s, real* l, real* dl) {
   const int n = (int)x.size();
   for (int j = 0; j < n; ++j) {
-    double p = 1.0, dp = 0.0;
+    real p = 1.0, dp = 0.0;
     for (int k = 0; k < n; ++k) {
       if (k == j) continue;
-      double f = (s - x[k]) / (x[j] - x[k]);
+      real f = (s - x[k]) / (x[j] - x[k]);
       dp = dp * f + p / (x[j] - x[k]);
       p *= f;
     }
@@ -154,16 +164,16 @@ static void lagrange(const std::vector<double>& x, double s, double* l, double* 
 
 // LSERK4: Carpenter & Kennedy (1994) five-stage, fourth-order 2N-storage
 // scheme (paper Sec. 4: "fourth-order low-storage Runge-Kutta").
-static const double RK_A[5] = {0.0, -567301805773.0 / 1357537059087.0,
+static const real RK_A[5] = {0.0, -567301805773.0 / 1357537059087.0,
                                -2404267990393.0 / 2016746695238.0,
                                -3550918686646.0 / 2091501179385.0,
                                -1275806237668.0 / 842570457699.0};
-static const double RK_B[5] = {1432997174477.0 / 9575080441755.0,
+static const real RK_B[5] = {1432997174477.0 / 9575080441755.0,
                                5161836677717.0 / 13612068292357.0,
                                1720146321549.0 / 2090206949498.0,
                                3134564353537.0 / 4481467310338.0,
                                2277821191437.0 / 14882151754819.0};
-static const double RK_C[5] = {0.0, 1432997174477.0 / 9575080441755.0,
+static const real RK_C[5] = {0.0, 1432997174477.0 / 9575080441755.0,
                                2526269341429.0 / 6820363962896.0,
                                2006345519317.0 / 3224310063776.0,
                                2802321613138.0 / 2924317926251.0};
@@ -173,10 +183,10 @@ static const double RK_C[5] = {0.0, 1432997174477.0 / 9575080441755.0,
 // ---------------------------------------------------------------------------
 template <class T>
 struct Phys {
-  double gamma = 1.4, R = 1.0, mu = 0.0, Pr = 0.72;
-  double f[3] = {0.0, 0.0, 0.0};  // constant body force per unit volume
+  real gamma = 1.4, R = 1.0, mu = 0.0, Pr = 0.72;
+  real f[3] = {0.0, 0.0, 0.0};  // constant body force per unit volume
   T kappa = 0.41, B = 5.2;        // wall-law constants
-  double hwm = 0.1;               // wall-model sampling distance
+  real hwm = 0.1;               // wall-model sampling distance
 };
 struct Opts {
   int vol_flux = VOL_KEP_PIROZZOLI;
@@ -193,16 +203,16 @@ struct Opts {
 // ---------------------------------------------------------------------------
 struct Mesh {
   int N = 0, n = 0, n2 = 0, n3 = 0, K = 0;
-  std::vector<double> xi, w, D;
-  std::vector<double> X;    // [3][K*n3]
+  std::vector<real> xi, w, D;
+  std::vector<real> X;    // [3][K*n3]
   std::vector<int> nbr;     // [K*6]
-  std::vector<double> Ja;   // [(e*n3+p)*9 + dir*3 + comp]
-  std::vector<double> J;    // [e*n3+p]
+  std::vector<real> Ja;   // [(e*n3+p)*9 + dir*3 + comp]
+  std::vector<real> J;    // [e*n3+p]
   // wall model: one slot per wall face node, ordered by (e, l, b, a)
   std::vector<int> wslot;   // [K*6] first slot of that face or -1
   std::vector<int> ws_elem; // sample element
-  std::vector<double> ws_ref;   // sample reference coordinates [slot*3]
-  std::vector<double> ws_l;     // Lagrange weights [slot*3*n]
+  std::vector<real> ws_ref;   // sample reference coordinates [slot*3]
+  std::vector<real> ws_l;     // Lagrange weights [slot*3*n]
   int nwall = 0;
 };
 
@@ -222,13 +232,13 @@ inline int face_node(const Mesh& M, int l, int a, int b) {
     default: return node(M, a, b, N);
   }
 }
-inline double face_sign(int l) { return (l & 1) ? 1.0 : -1.0; }
+inline real face_sign(int l) { return (l & 1) ? 1.0 : -1.0; }
 
 static bool build_metrics(Mesh& M, std::string& err) {
   const int n = M.n, n3 = M.n3, K = M.K;
   M.Ja.assign((size_t)K * n3 * 9, 0.0);
   M.J.assign((size_t)K * n3, 0.0);
-  std::vector<double> dX(9 * n3), v(3 * n3);
+  std::vector<real> dX(9 * n3), v(3 * n3);
   for (int e = 0; e < K; ++e) {
     // Coordinates relative to the element's first node: rows of D sum to
     // zero and curl(c grad X_m) = 0 for a constant c, so derivatives and the
@@ -242,7 +252,7 @@ static bool build_metrics(Mesh& M, std::string& err) {
     for (int c = 0; c < 3; ++c)
       for (int p = 0; p < n3; ++p) {
         int i, j, k; ijk(M, p, i, j, k);
-        double s0 = 0, s1 = 0, s2 = 0;
+        real s0 = 0, s1 = 0, s2 = 0;
         for (int m = 0; m < n; ++m) {
           s0 += M.D[i * n + m] * Xc(c, node(M, m, j, k));
           s1 += M.D[j * n + m] * Xc(c, node(M, i, m, k));
@@ -253,10 +263,10 @@ static bool build_metrics(Mesh& M, std::string& err) {
         dX[(c * 3 + 2) * n3 + p] = s2;
       }
     for (int p = 0; p < n3; ++p) {
-      double a[3][3];
+      real a[3][3];
       for (int c = 0; c < 3; ++c)
         for (int d = 0; d < 3; ++d) a[c][d] = dX[(c * 3 + d) * n3 + p];
-      double det = a[0][0] * (a[1][1] * a[2][2] - a[1][2] * a[2][1]) -
+      real det = a[0][0] * (a[1][1] * a[2][2] - a[1][2] * a[2][1]) -
                    a[0][1] * (a[1][0] * a[2][2] - a[1][2] * a[2][0]) +
                    a[0][2] * (a[1][0] * a[2][1] - a[1][1] * a[2][0]);
       M.J[(size_t)e * n3 + p] = det;
@@ -273,14 +283,14 @@ static bool build_metrics(Mesh& M, std::string& err) {
         for (int d = 0; d < 3; ++d) v[d * n3 + p] = Xc(ll, p) * dX[(mm * 3 + d) * n3 + p];
       for (int p = 0; p < n3; ++p) {
         int i, j, k; ijk(M, p, i, j, k);
-        double dv[3][3] = {{0}};  // dv[d][dir] = d v_d / d xi_dir
+        real dv[3][3] = {{0}};  // dv[d][dir] = d v_d / d xi_dir
         for (int d = 0; d < 3; ++d)
           for (int m = 0; m < n; ++m) {
             dv[d][0] += M.D[i * n + m] * v[d * n3 + node(M, m, j, k)];
             dv[d][1] += M.D[j * n + m] * v[d * n3 + node(M, i, m, k)];
             dv[d][2] += M.D[k * n + m] * v[d * n3 + node(M, i, j, m)];
           }
-        double* ja = &M.Ja[((size_t)e * n3 + p) * 9];
+        real* ja = &M.Ja[((size_t)e * n3 + p) * 9];
         ja[0 * 3 + nn] = -(dv[2][1] - dv[1][2]);
         ja[1 * 3 + nn] = -(dv[0][2] - dv[2][0]);
         ja[2 * 3 + nn] = -(dv[1][0] - dv[0][1]);
@@ -292,9 +302,9 @@ static bool build_metrics(Mesh& M, std::string& err) {
 
 static bool check_connectivity(const Mesh& M, std::string& err) {
   const int K = M.K, n3 = M.n3;
-  double scale = 0.0;
-  for (double x : M.X) scale = std::max(scale, std::fabs(x));
-  scale = std::max(scale, 1.0);
+  real scale = 0.0;
+  for (real x : M.X) scale = std::max(scale, std::fabs(x));
+  scale = std::max<real>(scale, 1.0);
   for (int e = 0; e < K; ++e)
     for (int l = 0; l < 6; ++l) {
       int nb = M.nbr[e * 6 + l];
@@ -302,12 +312,12 @@ static bool check_connectivity(const Mesh& M, std::string& err) {
       if (nb < 0) continue;
       if (M.nbr[nb * 6 + (l ^ 1)] != e) { err = "non-reciprocal connectivity"; return false; }
       // faces must coincide up to one translation (periodic image)
-      double shift[3];
+      real shift[3];
       for (int b = 0; b < M.n; ++b)
         for (int a = 0; a < M.n; ++a) {
           int p = face_node(M, l, a, b), q = face_node(M, l ^ 1, a, b);
           for (int c = 0; c < 3; ++c) {
-            double dx = M.X[(size_t)c * K * n3 + (size_t)nb * n3 + q] -
+            real dx = M.X[(size_t)c * K * n3 + (size_t)nb * n3 + q] -
                         M.X[(size_t)c * K * n3 + (size_t)e * n3 + p];
             if (a == 0 && b == 0) shift[c] = dx;
             else if (std::fabs(dx - shift[c]) > 1e-9 * scale) {
@@ -323,49 +333,50 @@ static bool check_connectivity(const Mesh& M, std::string& err) {
 // Wall-model sampling points (reading of Sec. 3.1: the wall model samples
 // the LES solution at distance h_wm from the wall): for every wall face node
 // the point x_w - h_wm * n_out is located by Newton on each candidate
-// element's polynomial mapping.  Among elements that contain it (max |xi|
-// <= 1 + 1e-10) the one with the smallest max |xi| wins, ties to the lower
-// element index.
-static bool locate_point(const Mesh& M, int e, const double xs[3], double ref[3]) {
+// element's polynomial mapping.  The lowest-index element that contains it
+// (max |xi| <= 1 + 1e-8) is used: points on a face shared by two elements
+// (e.g. above an edge node of the wall face) then get one well-defined
+// element although the DG solution is discontinuous there.
+static bool locate_point(const Mesh& M, int e, const real xs[3], real ref[3]) {
   const int n = M.n, n3 = M.n3, K = M.K;
-  double r[3] = {0.0, 0.0, 0.0};
-  std::vector<double> l0(n), l1(n), l2(n), d0(n), d1(n), d2(n);
+  real r[3] = {0.0, 0.0, 0.0};
+  std::vector<real> l0(n), l1(n), l2(n), d0(n), d1(n), d2(n);
   for (int it = 0; it < 60; ++it) {
     lagrange(M.xi, r[0], l0.data(), d0.data());
     lagrange(M.xi, r[1], l1.data(), d1.data());
     lagrange(M.xi, r[2], l2.data(), d2.data());
-    double x[3] = {0, 0, 0}, Jm[3][3] = {{0}};
+    real x[3] = {0, 0, 0}, Jm[3][3] = {{0}};
     for (int k = 0; k < n; ++k)
       for (int j = 0; j < n; ++j)
         for (int i = 0; i < n; ++i) {
           int p = node(M, i, j, k);
           for (int c = 0; c < 3; ++c) {
-            double Xv = M.X[(size_t)c * K * n3 + (size_t)e * n3 + p];
+            real Xv = M.X[(size_t)c * K * n3 + (size_t)e * n3 + p];
             x[c] += Xv * l0[i] * l1[j] * l2[k];
             Jm[c][0] += Xv * d0[i] * l1[j] * l2[k];
             Jm[c][1] += Xv * l0[i] * d1[j] * l2[k];
             Jm[c][2] += Xv * l0[i] * l1[j] * d2[k];
           }
         }
-    double res[3] = {xs[0] - x[0], xs[1] - x[1], xs[2] - x[2]};
+    real res[3] = {xs[0] - x[0], xs[1] - x[1], xs[2] - x[2]};
     // solve Jm * dr = res by Cramer's rule
-    double det = Jm[0][0] * (Jm[1][1] * Jm[2][2] - Jm[1][2] * Jm[2][1]) -
+    real det = Jm[0][0] * (Jm[1][1] * Jm[2][2] - Jm[1][2] * Jm[2][1]) -
                  Jm[0][1] * (Jm[1][0] * Jm[2][2] - Jm[1][2] * Jm[2][0]) +
                  Jm[0][2] * (Jm[1][0] * Jm[2][1] - Jm[1][1] * Jm[2][0]);
     if (det == 0.0) return false;
-    double dr[3];
+    real dr[3];
     for (int c = 0; c < 3; ++c) {
-      double A[3][3];
+      real A[3][3];
       for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) A[a][b] = (b == c) ? res[a] : Jm[a][b];
       dr[c] = (A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) -
                A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
                A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0])) / det;
     }
-    double step = 0.0;
+    real step = 0.0;
     for (int c = 0; c < 3; ++c) {
       r[c] += dr[c];
-      r[c] = std::max(-3.0, std::min(3.0, r[c]));
+      r[c] = std::max<real>(-3.0, std::min<real>(3.0, r[c]));
       step = std::max(step, std::fabs(dr[c]));
     }
     if (step < 1e-15) break;
@@ -374,7 +385,7 @@ static bool locate_point(const Mesh& M, int e, const double xs[3], double ref[3]
   return true;
 }
 
-static bool build_wall_samples(Mesh& M, double hwm, std::string& err) {
+static bool build_wall_samples(Mesh& M, real hwm, std::string& err) {
   const int n = M.n, n3 = M.n3, K = M.K;
   M.wslot.assign((size_t)K * 6, -1);
   int slots = 0;
@@ -387,11 +398,11 @@ static bool build_wall_samples(Mesh& M, double hwm, std::string& err) {
   M.ws_l.assign((size_t)slots * 3 * n, 0.0);
   if (slots == 0) return true;
   // element bounding boxes
-  std::vector<double> bmin((size_t)K * 3, 1e300), bmax((size_t)K * 3, -1e300);
+  std::vector<real> bmin((size_t)K * 3, 1e300), bmax((size_t)K * 3, -1e300);
   for (int e = 0; e < K; ++e)
     for (int p = 0; p < n3; ++p)
       for (int c = 0; c < 3; ++c) {
-        double x = M.X[(size_t)c * K * n3 + (size_t)e * n3 + p];
+        real x = M.X[(size_t)c * K * n3 + (size_t)e * n3 + p];
         bmin[e * 3 + c] = std::min(bmin[e * 3 + c], x);
         bmax[e * 3 + c] = std::max(bmax[e * 3 + c], x);
       }
@@ -403,27 +414,28 @@ static bool build_wall_samples(Mesh& M, double hwm, std::string& err) {
       for (int b = 0; b < n; ++b)
         for (int a = 0; a < n; ++a) {
           int p = face_node(M, l, a, b);
-          const double* ja = &M.Ja[((size_t)e * n3 + p) * 9 + dir * 3];
-          double s = std::sqrt(ja[0] * ja[0] + ja[1] * ja[1] + ja[2] * ja[2]);
-          double xs[3];
+          const real* ja = &M.Ja[((size_t)e * n3 + p) * 9 + dir * 3];
+          real s = std::sqrt(ja[0] * ja[0] + ja[1] * ja[1] + ja[2] * ja[2]);
+          real xs[3];
           for (int c = 0; c < 3; ++c) {
-            double nout = face_sign(l) * ja[c] / s;
+            real nout = face_sign(l) * ja[c] / s;
             xs[c] = M.X[(size_t)c * K * n3 + (size_t)e * n3 + p] - hwm * nout;
           }
-          int best = -1; double bestr = 1e300, bref[3] = {0, 0, 0};
+          int best = -1; real bestr = 1e300, bref[3] = {0, 0, 0};
           for (int c2 = 0; c2 < K; ++c2) {
             bool inside = true;
             for (int c = 0; c < 3; ++c) {
-              double marg = 0.05 * (bmax[c2 * 3 + c] - bmin[c2 * 3 + c]) + 1e-12;
+              real marg = 0.05 * (bmax[c2 * 3 + c] - bmin[c2 * 3 + c]) + 1e-12;
               if (xs[c] < bmin[c2 * 3 + c] - marg || xs[c] > bmax[c2 * 3 + c] + marg) inside = false;
             }
             if (!inside) continue;
-            double ref[3];
+            real ref[3];
             if (!locate_point(M, c2, xs, ref)) continue;
-            double rm = std::max(std::fabs(ref[0]), std::max(std::fabs(ref[1]), std::fabs(ref[2])));
-            if (rm <= 1.0 + 1e-10 && rm < bestr) {
+            real rm = std::max(std::fabs(ref[0]), std::max(std::fabs(ref[1]), std::fabs(ref[2])));
+            if (rm <= 1.0 + 1e-8) {  // first (lowest-index) element containing the point
               best = c2; bestr = rm;
               for (int c = 0; c < 3; ++c) bref[c] = ref[c];
+              break;
             }
           }
           if (best < 0) {
@@ -464,7 +476,7 @@ inline Prim<T> prim_of(const Phys<T>& P, const T U[5]) {
 // ---------------------------------------------------------------------------
 // Euler flux F(U) . a
 template <class T>
-void euler_flux(const Prim<T>& q, const T U[5], const double a[3], T F[5]) {
+void euler_flux(const Prim<T>& q, const T U[5], const real a[3], T F[5]) {
   T un = q.u[0] * a[0] + q.u[1] * a[1] + q.u[2] * a[2];
   F[0] = q.rho * un;
   for (int c = 0; c < 3; ++c) F[1 + c] = q.rho * un * q.u[c] + q.p * a[c];
@@ -476,7 +488,7 @@ void euler_flux(const Prim<T>& q, const T U[5], const double a[3], T F[5]) {
 //  Kennedy-Gruber:   {rho}{u.a},  {rho}{u.a}{u} + {p} a,  {rho}{u.a}{e} + {p}{u.a}
 template <class T>
 void twopoint_flux(int kind, const Prim<T>& L, const T UL[5], const Prim<T>& R, const T UR[5],
-                   const double a[3], T F[5]) {
+                   const real a[3], T F[5]) {
   T rho = 0.5 * (L.rho + R.rho);
   T u[3];
   for (int c = 0; c < 3; ++c) u[c] = 0.5 * (L.u[c] + R.u[c]);
@@ -497,10 +509,10 @@ void twopoint_flux(int kind, const Prim<T>& L, const T UL[5], const Prim<T>& R, 
 //   Fv_d = (0, tau_1d, tau_2d, tau_3d, tau_jd u_j + k dT/dx_d)
 //   tau_ij = mu (du_i/dx_j + du_j/dx_i) - 2/3 mu (div u) delta_ij
 template <class T>
-void viscous_flux(const Phys<T>& P, const Prim<T>& q, const T g[3][4], const double a[3], T F[5]) {
-  const double mu = P.mu;
-  const double cp = P.gamma * P.R / (P.gamma - 1.0);
-  const double kcond = mu * cp / P.Pr;
+void viscous_flux(const Phys<T>& P, const Prim<T>& q, const T g[3][4], const real a[3], T F[5]) {
+  const real mu = P.mu;
+  const real cp = P.gamma * P.R / (P.gamma - 1.0);
+  const real kcond = mu * cp / P.Pr;
   T div = g[0][0] + g[1][1] + g[2][2];
   T tau[3][3];
   for (int i = 0; i < 3; ++i)
@@ -526,10 +538,10 @@ void viscous_flux(const Phys<T>& P, const Prim<T>& q, const T g[3][4], const dou
 //           two acoustic waves.
 template <class T>
 void riemann(const Phys<T>& P, int vol_kind, int kind, const Prim<T>& L, const T UL[5],
-             const Prim<T>& R, const T UR[5], const double nh[3], T F[5]) {
+             const Prim<T>& R, const T UR[5], const real nh[3], T F[5]) {
   twopoint_flux(vol_kind, L, UL, R, UR, nh, F);
   if (kind == SURF_CENTRAL) return;
-  const double g = P.gamma;
+  const real g = P.gamma;
   if (kind == SURF_LLF) {
     T unL = L.u[0] * nh[0] + L.u[1] * nh[1] + L.u[2] * nh[2];
     T unR = R.u[0] * nh[0] + R.u[1] * nh[1] + R.u[2] * nh[2];
@@ -619,43 +631,43 @@ T law_residual(int law, const T& t, const T& lnRe, const T& kappa, const T& B) {
 }
 
 template <class T>
-int solve_utau(int law, const T& u, double h, const T& nu, const T& kappa, const T& B, T& ut) {
+int solve_utau(int law, const T& u, real h, const T& nu, const T& kappa, const T& B, T& ut) {
   if (!(val(u) > 0.0)) { ut = 0.0; return 0; }
-  const double lnRe = std::log(h * val(u) / val(nu));
+  const real lnRe = std::log(h * val(u) / val(nu));
   const Dual kD(val(kappa)), BD(val(B)), lnReD(lnRe);
-  auto F_of = [&](double t, double* dF) {
+  auto F_of = [&](real t, real* dF) {
     Dual F = law_residual(law, Dual(t, 1.0), lnReD, kD, BD);
     *dF = F.d;
     return F.v;
   };
-  double dF;
-  double lo = 0.5 * lnRe, hi = lo, stepb = 1.0;
+  real dF;
+  real lo = 0.5 * lnRe, hi = lo, stepb = 1.0;
   int it = 0;
   while (!(F_of(lo, &dF) < 0.0) && it < 200) { lo -= stepb; stepb *= 2.0; ++it; }
   stepb = 1.0;
   while (!(F_of(hi, &dF) > 0.0) && it < 200) { hi += stepb; stepb *= 2.0; ++it; }
-  double t = 0.5 * lnRe;
+  real t = 0.5 * lnRe;
   if (!(t > lo && t < hi)) t = 0.5 * (lo + hi);
   bool done = false;
   for (; it < 200; ++it) {
-    double Ft = F_of(t, &dF);
+    real Ft = F_of(t, &dF);
     if (Ft == 0.0) { done = true; ++it; break; }
     if (Ft < 0.0) lo = t; else hi = t;
-    double next = t - Ft / dF;
+    real next = t - Ft / dF;
     const bool newton = (next >= lo && next <= hi);
     if (!newton) next = 0.5 * (lo + hi);
-    double step = std::fabs(next - t);
+    real step = std::fabs(next - t);
     t = next;
-    const double scale = std::max(1.0, std::fabs(t));
+    const real scale = std::max<real>(1.0, std::fabs(t));
     // a Newton step of size d leaves an error of order d^2: 1e-12 suffices
     if ((newton && step <= 1e-12 * scale) || hi - lo <= 2e-15 * scale) { done = true; ++it; break; }
   }
   if (!done) { ut = 0.0; return -1; }
   T tT = t;
-  if (!std::is_same<T, double>::value) {
+  if (!std::is_same<T, real>::value) {
     // derivative of the root by the implicit function theorem:
     // dt = -(dF/dparams . dparams) / (dF/dt) at fixed t
-    double Ft_t;
+    real Ft_t;
     F_of(t, &Ft_t);
     T lnReT = log(h * u / nu);
     T FT = law_residual(law, T(t), lnReT, kappa, B);
@@ -669,9 +681,9 @@ int solve_utau(int law, const T& u, double h, const T& nu, const T& kappa, const
 // Wall-model viscous flux at a wall node: returns Fv*.n_out (momentum part)
 // and the wall shear vector tau_w * t (t = unit wall-parallel sample velocity).
 template <class T>
-int wall_flux(const Phys<T>& P, int law, const Prim<T>& s, const double nout[3], T fm[3], T tauvec[3]) {
-  const double cp = P.gamma * P.R / (P.gamma - 1.0);
-  const double r = std::cbrt(P.Pr);
+int wall_flux(const Phys<T>& P, int law, const Prim<T>& s, const real nout[3], T fm[3], T tauvec[3]) {
+  const real cp = P.gamma * P.R / (P.gamma - 1.0);
+  const real r = std::cbrt(P.Pr);
   T un = s.u[0] * nout[0] + s.u[1] * nout[1] + s.u[2] * nout[2];
   T upar[3];
   for (int c = 0; c < 3; ++c) upar[c] = s.u[c] - un * nout[c];
@@ -716,7 +728,7 @@ inline void load_U(const Mesh& M, const T* U, int e, int p, T u[5]) {
 
 // mirror state for a slip wall: normal velocity reversed
 template <class T>
-void mirror(const T U[5], const double nh[3], T Ub[5]) {
+void mirror(const T U[5], const real nh[3], T Ub[5]) {
   T mn = U[1] * nh[0] + U[2] * nh[1] + U[3] * nh[2];
   Ub[0] = U[0];
   for (int c = 0; c < 3; ++c) Ub[1 + c] = U[1 + c] - 2.0 * mn * nh[c];
@@ -724,21 +736,21 @@ void mirror(const T U[5], const double nh[3], T Ub[5]) {
 }
 
 // master side's unit normal and surface element of face l of e at node (a,b)
-static void face_geometry(const Mesh& M, int e, int l, int a, int b, double nh[3], double* s, bool* own_is_master) {
+static void face_geometry(const Mesh& M, int e, int l, int a, int b, real nh[3], real* s, bool* own_is_master) {
   int nb = M.nbr[e * 6 + l];
   int me = e, ml = l;
   bool master = true;
   if (nb >= 0 && (l & 1) == 0) { me = nb; ml = l ^ 1; master = false; }
   int p = face_node(M, ml, a, b);
-  const double* ja = &M.Ja[((size_t)me * M.n3 + p) * 9 + (ml / 2) * 3];
-  double ss = std::sqrt(ja[0] * ja[0] + ja[1] * ja[1] + ja[2] * ja[2]);
+  const real* ja = &M.Ja[((size_t)me * M.n3 + p) * 9 + (ml / 2) * 3];
+  real ss = std::sqrt(ja[0] * ja[0] + ja[1] * ja[1] + ja[2] * ja[2]);
   for (int c = 0; c < 3; ++c) nh[c] = face_sign(ml) * ja[c] / ss;
   *s = ss;
   *own_is_master = master;
 }
 
 template <class T>
-int time_derivative(const Mesh& M, const Phys<T>& P, const Opts& O, const T* U, double t, T* Ut,
+int time_derivative(const Mesh& M, const Phys<T>& P, const Opts& O, const T* U, real t, T* Ut,
                     Work<T>& W) {
   (void)t;
   const int n = M.n, n3 = M.n3, K = M.K;
@@ -758,8 +770,8 @@ int time_derivative(const Mesh& M, const Phys<T>& P, const Opts& O, const T* U, 
     for (int e = 0; e < K; ++e)
       for (int p = 0; p < n3; ++p) {
         int i, j, k; ijk(M, p, i, j, k);
-        const double* ja = &M.Ja[((size_t)e * n3 + p) * 9];
-        const double invJ = 1.0 / M.J[(size_t)e * n3 + p];
+        const real* ja = &M.Ja[((size_t)e * n3 + p) * 9];
+        const real invJ = 1.0 / M.J[(size_t)e * n3 + p];
         auto Wv = [&](int ee, int pp, int w) -> T {
           const Prim<T>& q = W.q[(size_t)ee * n3 + pp];
           return w < 3 ? q.u[w] : q.T_;
@@ -788,8 +800,8 @@ int time_derivative(const Mesh& M, const Phys<T>& P, const Opts& O, const T* U, 
           int l = fl[f], dir = l / 2;
           int a, b;
           if (dir == 0) { a = j; b = k; } else if (dir == 1) { a = i; b = k; } else { a = i; b = j; }
-          double wperp = M.w[dir == 0 ? i : (dir == 1 ? j : k)];
-          double ns[3];
+          real wperp = M.w[dir == 0 ? i : (dir == 1 ? j : k)];
+          real ns[3];
           for (int c = 0; c < 3; ++c) ns[c] = face_sign(l) * ja[dir * 3 + c];
           T Wo[4], Wn[4];
           for (int w = 0; w < 4; ++w) Wo[w] = Wv(e, p, w);
@@ -799,8 +811,8 @@ int time_derivative(const Mesh& M, const Phys<T>& P, const Opts& O, const T* U, 
             for (int w = 0; w < 4; ++w) Wn[w] = Wv(nb, q, w);
           } else {
             // slip wall: mirror state (normal velocity reversed, same T)
-            double ss = std::sqrt(ns[0] * ns[0] + ns[1] * ns[1] + ns[2] * ns[2]);
-            double nh[3] = {ns[0] / ss, ns[1] / ss, ns[2] / ss};
+            real ss = std::sqrt(ns[0] * ns[0] + ns[1] * ns[1] + ns[2] * ns[2]);
+            real nh[3] = {ns[0] / ss, ns[1] / ss, ns[2] / ss};
             T un = Wo[0] * nh[0] + Wo[1] * nh[1] + Wo[2] * nh[2];
             for (int c = 0; c < 3; ++c) Wn[c] = Wo[c] - 2.0 * un * nh[c];
             Wn[3] = Wo[3];
@@ -820,7 +832,7 @@ int time_derivative(const Mesh& M, const Phys<T>& P, const Opts& O, const T* U, 
         T g[3][4];
         for (int d = 0; d < 3; ++d)
           for (int w = 0; w < 4; ++w) g[d][w] = W.grad[((size_t)e * n3 + p) * 12 + d * 4 + w];
-        const double* ja = &M.Ja[((size_t)e * n3 + p) * 9];
+        const real* ja = &M.Ja[((size_t)e * n3 + p) * 9];
         for (int dir = 0; dir < 3; ++dir)
           viscous_flux(P, W.q[(size_t)e * n3 + p], g, &ja[dir * 3], &W.G[((size_t)e * n3 + p) * 15 + dir * 5]);
       }
@@ -839,19 +851,19 @@ int time_derivative(const Mesh& M, const Phys<T>& P, const Opts& O, const T* U, 
           for (int a = 0; a < n; ++a) {
             int slot = s0 + a + n * b;
             int es = M.ws_elem[slot];
-            const double* l0 = &M.ws_l[((size_t)slot * 3 + 0) * n];
-            const double* l1 = &M.ws_l[((size_t)slot * 3 + 1) * n];
-            const double* l2 = &M.ws_l[((size_t)slot * 3 + 2) * n];
+            const real* l0 = &M.ws_l[((size_t)slot * 3 + 0) * n];
+            const real* l1 = &M.ws_l[((size_t)slot * 3 + 1) * n];
+            const real* l2 = &M.ws_l[((size_t)slot * 3 + 2) * n];
             T Us[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
             for (int kk = 0; kk < n; ++kk)
               for (int jj = 0; jj < n; ++jj)
                 for (int ii = 0; ii < n; ++ii) {
                   T u[5]; load_U(M, U, es, node(M, ii, jj, kk), u);
-                  double lw = l0[ii] * l1[jj] * l2[kk];
+                  real lw = l0[ii] * l1[jj] * l2[kk];
                   for (int v = 0; v < 5; ++v) Us[v] += lw * u[v];
                 }
             Prim<T> qs = prim_of(P, Us);
-            double nh[3], s; bool own;
+            real nh[3], s; bool own;
             face_geometry(M, e, l, a, b, nh, &s, &own);
             T fm[3], tv[3];
             W.wstat[slot] = wall_flux(P, O.law, qs, nh, fm, tv);
@@ -870,14 +882,14 @@ int time_derivative(const Mesh& M, const Phys<T>& P, const Opts& O, const T* U, 
       const int idx[3] = {i, j, k};
       T Uo[5]; load_U(M, U, e, p, Uo);
       const Prim<T>& qo = W.q[(size_t)e * n3 + p];
-      const double* jao = &M.Ja[((size_t)e * n3 + p) * 9];
+      const real* jao = &M.Ja[((size_t)e * n3 + p) * 9];
       T V[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
       for (int dir = 0; dir < 3; ++dir)
         for (int m = 0; m < n; ++m) {
           int pm = dir == 0 ? node(M, m, j, k) : (dir == 1 ? node(M, i, m, k) : node(M, i, j, m));
-          const double Dim = M.D[idx[dir] * n + m];
-          const double* jam = &M.Ja[((size_t)e * n3 + pm) * 9];
-          double abar[3];
+          const real Dim = M.D[idx[dir] * n + m];
+          const real* jam = &M.Ja[((size_t)e * n3 + pm) * 9];
+          real abar[3];
           for (int c = 0; c < 3; ++c) abar[c] = 0.5 * (jao[dir * 3 + c] + jam[dir * 3 + c]);
           T Um[5]; load_U(M, U, e, pm, Um);
           T F[5];
@@ -898,8 +910,8 @@ int time_derivative(const Mesh& M, const Phys<T>& P, const Opts& O, const T* U, 
         int l = fl[f], dir = l / 2;
         int a, b;
         if (dir == 0) { a = j; b = k; } else if (dir == 1) { a = i; b = k; } else { a = i; b = j; }
-        double wperp = M.w[idx[dir]];
-        double nh[3], s; bool own_master;
+        real wperp = M.w[idx[dir]];
+        real nh[3], s; bool own_master;
         face_geometry(M, e, l, a, b, nh, &s, &own_master);
         int nb = M.nbr[e * 6 + l];
         // master / slave states
@@ -944,9 +956,9 @@ int time_derivative(const Mesh& M, const Phys<T>& P, const Opts& O, const T* U, 
             for (int c = 0; c < 3; ++c) Fv[1 + c] = W.wflux[(size_t)slot * 3 + c];
           }
         }
-        const double sg = own_master ? 1.0 : -1.0;
+        const real sg = own_master ? 1.0 : -1.0;
         // own flux along own outward metric normal
-        double ns[3];
+        real ns[3];
         for (int c = 0; c < 3; ++c) ns[c] = face_sign(l) * jao[dir * 3 + c];
         T Fo[5];
         euler_flux(qo, Uo, ns, Fo);
@@ -960,7 +972,7 @@ int time_derivative(const Mesh& M, const Phys<T>& P, const Opts& O, const T* U, 
         }
         for (int v = 0; v < 5; ++v) V[v] += (sg * (Fi[v] - Fv[v]) * s - Fo[v]) / wperp;
       }
-      const double invJ = 1.0 / M.J[(size_t)e * n3 + p];
+      const real invJ = 1.0 / M.J[(size_t)e * n3 + p];
       T src[5] = {0.0, P.f[0], P.f[1], P.f[2],
                   P.f[0] * qo.u[0] + P.f[1] * qo.u[1] + P.f[2] * qo.u[2]};
       for (int v = 0; v < 5; ++v) Ut[v * S + (size_t)e * n3 + p] = -V[v] * invJ + src[v];
@@ -976,16 +988,16 @@ T wall_shear_loss(const Mesh& M, const Phys<T>& P, const Opts& O, const T* U, Wo
   Opts o2 = O; o2.viscous = 1;
   std::vector<T> Ut((size_t)5 * M.K * M.n3);
   *status = time_derivative(M, P, o2, U, 0.0, Ut.data(), W);
-  T num = 0.0; double den = 0.0;
+  T num = 0.0; real den = 0.0;
   for (int e = 0; e < M.K; ++e)
     for (int l = 0; l < 6; ++l) {
       int s0 = M.wslot[e * 6 + l];
       if (s0 < 0) continue;
       for (int b = 0; b < M.n; ++b)
         for (int a = 0; a < M.n; ++a) {
-          double nh[3], s; bool own;
+          real nh[3], s; bool own;
           face_geometry(M, e, l, a, b, nh, &s, &own);
-          double wt = M.w[a] * M.w[b] * s;
+          real wt = M.w[a] * M.w[b] * s;
           num += wt * W.wtau[(size_t)(s0 + a + M.n * b) * 3 + 0];
           den += wt;
         }
@@ -995,18 +1007,18 @@ T wall_shear_loss(const Mesh& M, const Phys<T>& P, const Opts& O, const T* U, Wo
 }
 
 // explicit time step (reading: dt = CFL * 2/(2N+1) * min_p J / sum_dir(|u.Ja| + c |Ja|))
-static double time_step(const Mesh& M, const Phys<double>& P, const double* U, double cfl) {
-  double best = 1e300;
+static real time_step(const Mesh& M, const Phys<real>& P, const real* U, real cfl) {
+  real best = 1e300;
   for (int e = 0; e < M.K; ++e)
     for (int p = 0; p < M.n3; ++p) {
-      double u[5]; load_U(M, U, e, p, u);
-      Prim<double> q = prim_of(P, u);
-      double c = std::sqrt(P.gamma * q.p / q.rho);
-      const double* ja = &M.Ja[((size_t)e * M.n3 + p) * 9];
-      double lam = 0.0;
+      real u[5]; load_U(M, U, e, p, u);
+      Prim<real> q = prim_of(P, u);
+      real c = std::sqrt(P.gamma * q.p / q.rho);
+      const real* ja = &M.Ja[((size_t)e * M.n3 + p) * 9];
+      real lam = 0.0;
       for (int d = 0; d < 3; ++d) {
-        double un = q.u[0] * ja[d * 3] + q.u[1] * ja[d * 3 + 1] + q.u[2] * ja[d * 3 + 2];
-        double jn = std::sqrt(ja[d * 3] * ja[d * 3] + ja[d * 3 + 1] * ja[d * 3 + 1] + ja[d * 3 + 2] * ja[d * 3 + 2]);
+        real un = q.u[0] * ja[d * 3] + q.u[1] * ja[d * 3 + 1] + q.u[2] * ja[d * 3 + 2];
+        real jn = std::sqrt(ja[d * 3] * ja[d * 3] + ja[d * 3 + 1] * ja[d * 3 + 1] + ja[d * 3 + 2] * ja[d * 3 + 2]);
         lam += std::fabs(un) + c * jn;
       }
       best = std::min(best, M.J[(size_t)e * M.n3 + p] / lam);
@@ -1016,7 +1028,7 @@ static double time_step(const Mesh& M, const Phys<double>& P, const double* U, d
 
 // one LSERK4 stage: dU = A_s dU + dt Ut(U, t + c_s dt); U = U + B_s dU
 template <class T>
-int rk_stage(const Mesh& M, const Phys<T>& P, const Opts& O, T* U, T* dU, int s, double t, double dt,
+int rk_stage(const Mesh& M, const Phys<T>& P, const Opts& O, T* U, T* dU, int s, real t, real dt,
              Work<T>& W) {
   const size_t S5 = (size_t)5 * M.K * M.n3;
   std::vector<T> Ut(S5);
@@ -1030,9 +1042,9 @@ int rk_stage(const Mesh& M, const Phys<T>& P, const Opts& O, T* U, T* dU, int s,
 
 struct Ctx {
   Mesh M;
-  Phys<double> P;
+  Phys<real> P;
   Opts O;
-  Work<double> W;
+  Work<real> W;
   Work<Dual> WD;
   std::string err;
 };
@@ -1046,7 +1058,7 @@ struct Ctx {
 // ---------------------------------------------------------------------------
 using namespace ora;
 
-static Phys<Dual> dual_phys(const Phys<double>& P, double dk, double dB) {
+static Phys<Dual> dual_phys(const Phys<real>& P, real dk, real dB) {
   Phys<Dual> Q;
   Q.gamma = P.gamma; Q.R = P.R; Q.mu = P.mu; Q.Pr = P.Pr;
   for (int c = 0; c < 3; ++c) Q.f[c] = P.f[c];
@@ -1054,22 +1066,28 @@ static Phys<Dual> dual_phys(const Phys<double>& P, double dk, double dB) {
   return Q;
 }
 
+// conversions at the C boundary (the interface is double in both builds)
+static std::vector<real> to_real(const double* a, size_t n) { return std::vector<real>(a, a + n); }
+static void to_double(const std::vector<real>& a, double* out) {
+  for (size_t x = 0; x < a.size(); ++x) out[x] = (double)a[x];
+}
+
 extern "C" {
 
 int ora_lgl(int N, double* xi, double* w, double* D) {
   if (N < 1 || N > 32) return -1;
-  std::vector<double> x, ww, DD;
+  std::vector<real> x, ww, DD;
   lgl(N, x, ww, DD);
-  std::memcpy(xi, x.data(), sizeof(double) * (N + 1));
-  std::memcpy(w, ww.data(), sizeof(double) * (N + 1));
-  std::memcpy(D, DD.data(), sizeof(double) * (N + 1) * (N + 1));
+  to_double(x, xi); to_double(ww, w); to_double(DD, D);
   return 0;
 }
 
 int ora_lserk4(double* A, double* B, double* c) {
-  for (int s = 0; s < 5; ++s) { A[s] = RK_A[s]; B[s] = RK_B[s]; c[s] = RK_C[s]; }
+  for (int s = 0; s < 5; ++s) { A[s] = (double)RK_A[s]; B[s] = (double)RK_B[s]; c[s] = (double)RK_C[s]; }
   return 0;
 }
+
+int ora_real_digits(void) { return std::numeric_limits<real>::digits; }
 
 void ora_set_threads(int nt) {
 #ifdef _OPENMP
@@ -1093,7 +1111,7 @@ void* ora_create(int N, int K, const double* X, const int* nbr, const double* ph
   Mesh& M = c->M;
   M.N = N; M.n = N + 1; M.n2 = M.n * M.n; M.n3 = M.n2 * M.n; M.K = K;
   lgl(N, M.xi, M.w, M.D);
-  M.X.assign(X, X + (size_t)3 * K * M.n3);
+  M.X = to_real(X, (size_t)3 * K * M.n3);
   M.nbr.assign(nbr, nbr + (size_t)6 * K);
   c->P.gamma = phys[0]; c->P.R = phys[1]; c->P.mu = phys[2]; c->P.Pr = phys[3];
   c->P.f[0] = phys[4]; c->P.f[1] = phys[5]; c->P.f[2] = phys[6];
@@ -1113,8 +1131,8 @@ void ora_destroy(void* h) { delete (Ctx*)h; }
 
 int ora_get_metrics(void* h, double* Ja, double* J) {
   Ctx* c = (Ctx*)h;
-  std::memcpy(Ja, c->M.Ja.data(), sizeof(double) * c->M.Ja.size());
-  std::memcpy(J, c->M.J.data(), sizeof(double) * c->M.J.size());
+  to_double(c->M.Ja, Ja);
+  to_double(c->M.J, J);
   return 0;
 }
 
@@ -1124,57 +1142,70 @@ int ora_get_wall_samples(void* h, int* elem, double* ref) {
   Ctx* c = (Ctx*)h;
   for (int s = 0; s < c->M.nwall; ++s) {
     elem[s] = c->M.ws_elem[s];
-    for (int d = 0; d < 3; ++d) ref[s * 3 + d] = c->M.ws_ref[s * 3 + d];
+    for (int d = 0; d < 3; ++d) ref[s * 3 + d] = (double)c->M.ws_ref[s * 3 + d];
   }
   return 0;
 }
 
+static size_t state_size(const Ctx* c) { return (size_t)5 * c->M.K * c->M.n3; }
+
 int ora_time_derivative(void* h, const double* U, double t, double* Ut) {
   Ctx* c = (Ctx*)h;
-  return time_derivative(c->M, c->P, c->O, U, t, Ut, c->W);
+  const size_t S5 = state_size(c);
+  std::vector<real> u = to_real(U, S5), ut(S5);
+  int st = time_derivative(c->M, c->P, c->O, u.data(), t, ut.data(), c->W);
+  to_double(ut, Ut);
+  return st;
 }
 
 // Jacobian-vector product: dUt = (dUt/dU) dU + (dUt/dkappa) dk + (dUt/dB) dB
 int ora_jvp(void* h, const double* U, const double* dU, double dk, double dB, double t, double* Ut,
             double* dUt) {
   Ctx* c = (Ctx*)h;
-  const size_t S5 = (size_t)5 * c->M.K * c->M.n3;
+  const size_t S5 = state_size(c);
   std::vector<Dual> Ud(S5), Utd(S5);
   for (size_t x = 0; x < S5; ++x) Ud[x] = Dual(U[x], dU ? dU[x] : 0.0);
   Phys<Dual> P = dual_phys(c->P, dk, dB);
   int st = time_derivative(c->M, P, c->O, Ud.data(), t, Utd.data(), c->WD);
-  for (size_t x = 0; x < S5; ++x) { Ut[x] = Utd[x].v; dUt[x] = Utd[x].d; }
+  for (size_t x = 0; x < S5; ++x) { Ut[x] = (double)Utd[x].v; dUt[x] = (double)Utd[x].d; }
   return st;
 }
 
 int ora_rk_stage(void* h, double* U, double* dU, int s, double t, double dt) {
   Ctx* c = (Ctx*)h;
   if (s < 0 || s > 4) return -1;
-  return rk_stage(c->M, c->P, c->O, U, dU, s, t, dt, c->W);
+  const size_t S5 = state_size(c);
+  std::vector<real> u = to_real(U, S5), du = to_real(dU, S5);
+  int st = rk_stage(c->M, c->P, c->O, u.data(), du.data(), s, t, dt, c->W);
+  to_double(u, U); to_double(du, dU);
+  return st;
 }
 
 int ora_rk_steps(void* h, double* U, double t0, double dt, int nsteps) {
   Ctx* c = (Ctx*)h;
-  const size_t S5 = (size_t)5 * c->M.K * c->M.n3;
-  std::vector<double> dU(S5, 0.0);
+  const size_t S5 = state_size(c);
+  std::vector<real> u = to_real(U, S5), du(S5, 0.0);
   int st = 0;
   for (int it = 0; it < nsteps; ++it) {
-    std::fill(dU.begin(), dU.end(), 0.0);
-    for (int s = 0; s < 5; ++s) st |= rk_stage(c->M, c->P, c->O, U, dU.data(), s, t0 + it * dt, dt, c->W);
+    std::fill(du.begin(), du.end(), real(0.0));
+    for (int s = 0; s < 5; ++s) st |= rk_stage(c->M, c->P, c->O, u.data(), du.data(), s, t0 + it * dt, dt, c->W);
   }
+  to_double(u, U);
   return st;
 }
 
 int ora_dt(void* h, const double* U, double cfl, double* dt) {
   Ctx* c = (Ctx*)h;
-  *dt = time_step(c->M, c->P, U, cfl);
+  std::vector<real> u = to_real(U, state_size(c));
+  *dt = (double)time_step(c->M, c->P, u.data(), cfl);
   return 0;
 }
 
 int ora_wall_shear(void* h, const double* U, double* loss) {
   Ctx* c = (Ctx*)h;
   int st = 0;
-  *loss = wall_shear_loss(c->M, c->P, c->O, U, c->W, &st);
+  std::vector<real> u = to_real(U, state_size(c));
+  *loss = (double)wall_shear_loss(c->M, c->P, c->O, u.data(), c->W, &st);
   return st;
 }
 
@@ -1183,7 +1214,7 @@ int ora_wall_shear(void* h, const double* U, double* loss) {
 int ora_rollout_jvp(void* h, const double* U0, const double* dU0, double dk, double dB, int nsteps,
                     double dt, double* loss, double* dloss) {
   Ctx* c = (Ctx*)h;
-  const size_t S5 = (size_t)5 * c->M.K * c->M.n3;
+  const size_t S5 = state_size(c);
   std::vector<Dual> U(S5), dU(S5);
   for (size_t x = 0; x < S5; ++x) U[x] = Dual(U0[x], dU0 ? dU0[x] : 0.0);
   Phys<Dual> P = dual_phys(c->P, dk, dB);
@@ -1194,7 +1225,7 @@ int ora_rollout_jvp(void* h, const double* U0, const double* dU0, double dk, dou
   }
   int st2 = 0;
   Dual L = wall_shear_loss(c->M, P, c->O, U.data(), c->WD, &st2);
-  *loss = L.v; *dloss = L.d;
+  *loss = (double)L.v; *dloss = (double)L.d;
   return st | st2;
 }
 
@@ -1202,51 +1233,57 @@ int ora_rollout_jvp(void* h, const double* U0, const double* dU0, double dk, dou
 int ora_kinetic_energy(void* h, const double* U, double* ke) {
   Ctx* c = (Ctx*)h;
   const Mesh& M = c->M;
-  double num = 0.0, vol = 0.0;
+  real num = 0.0, vol = 0.0;
   for (int e = 0; e < M.K; ++e)
     for (int p = 0; p < M.n3; ++p) {
       int i, j, k; ijk(M, p, i, j, k);
-      double wJ = M.w[i] * M.w[j] * M.w[k] * M.J[(size_t)e * M.n3 + p];
-      double u[5]; load_U(M, U, e, p, u);
+      real wJ = M.w[i] * M.w[j] * M.w[k] * M.J[(size_t)e * M.n3 + p];
+      real u[5];
+      for (int v = 0; v < 5; ++v) u[v] = U[(size_t)v * M.K * M.n3 + (size_t)e * M.n3 + p];
       num += wJ * 0.5 * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) / u[0];
       vol += wJ;
     }
-  *ke = num / vol;
+  *ke = (double)(num / vol);
   return 0;
 }
 
 // Wall law solve for tests: returns u_tau and iterations (law pins).
 int ora_solve_utau(int law, double u, double h, double nu, double kappa, double B, double* ut) {
-  double x;
-  int it = solve_utau<double>(law, u, h, nu, kappa, B, x);
-  *ut = x;
+  real x;
+  int it = solve_utau<real>(law, u, h, nu, kappa, B, x);
+  *ut = (double)x;
   return it;
 }
 
 double ora_law_value(int law, double x, double kappa, double B) {
-  return law == LAW_REICHARDT ? reichardt<double>(x, kappa, B) : spalding<double>(x, kappa, B);
+  return (double)(law == LAW_REICHARDT ? reichardt<real>(x, kappa, B) : spalding<real>(x, kappa, B));
 }
 
 // Wall flux at one sample state (tests): U5 conservative, nout unit normal.
 int ora_wall_flux(const double* phys, int law, const double* U5, const double* nout, double* fm, double* tau) {
-  Phys<double> P;
+  Phys<real> P;
   P.gamma = phys[0]; P.R = phys[1]; P.mu = phys[2]; P.Pr = phys[3];
   P.kappa = phys[7]; P.B = phys[8]; P.hwm = phys[9];
-  double u[5];
+  real u[5], nh[3], f[3], t[3];
   for (int v = 0; v < 5; ++v) u[v] = U5[v];
-  Prim<double> q = prim_of(P, u);
-  return wall_flux(P, law, q, nout, fm, tau);
+  for (int c = 0; c < 3; ++c) nh[c] = nout[c];
+  Prim<real> q = prim_of(P, u);
+  int st = wall_flux(P, law, q, nh, f, t);
+  for (int c = 0; c < 3; ++c) { fm[c] = (double)f[c]; tau[c] = (double)t[c]; }
+  return st;
 }
 
 // Single numerical flux evaluation (tests): returns F*(UL, UR; nh).
 int ora_riemann(const double* phys, int vol_kind, int kind, const double* UL, const double* UR,
                 const double* nh, double* F) {
-  Phys<double> P;
+  Phys<real> P;
   P.gamma = phys[0]; P.R = phys[1];
-  double ul[5], ur[5];
+  real ul[5], ur[5], n3[3], f[5];
   for (int v = 0; v < 5; ++v) { ul[v] = UL[v]; ur[v] = UR[v]; }
-  Prim<double> L = prim_of(P, ul), R = prim_of(P, ur);
-  riemann(P, vol_kind, kind, L, ul, R, ur, nh, F);
+  for (int c = 0; c < 3; ++c) n3[c] = nh[c];
+  Prim<real> L = prim_of(P, ul), R = prim_of(P, ur);
+  riemann(P, vol_kind, kind, L, ul, R, ur, n3, f);
+  for (int v = 0; v < 5; ++v) F[v] = (double)f[v];
   return 0;
 }
 

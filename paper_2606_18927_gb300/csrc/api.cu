@@ -173,6 +173,7 @@ int dg_init_mesh(dg_ctx** out, const dg_mesh_desc* m, const dg_phys* p, const dg
   dg::PhysDev& ph = c->ph;
   ph.gamma = p->gamma; ph.gm1 = p->gamma - 1.0; ph.R = p->R; ph.mu = p->mu; ph.Pr = p->Pr;
   ph.cp = p->gamma * p->R / (p->gamma - 1.0); ph.kcond = p->mu * ph.cp / p->Pr; ph.rcp_R = 1.0 / p->R;
+  ph.p_ref = p->p_ref;
   for (int d = 0; d < 3; ++d) ph.f[d] = p->force[d];
   ph.kappa = p->kappa; ph.B = p->B; ph.hwm = p->hwm; ph.law = p->law;
   ph.vol_flux = o->vol_flux; ph.surf_flux = o->surf_flux; ph.viscous = o->viscous ? 1 : 0;
@@ -325,6 +326,24 @@ int dg_rk_steps(dg_ctx* c, double t, double dt, int nsteps) {
       int rc = dg_rk_stage(c, s, t + (it + kRkC[s]) * dt, dt);
       if (rc != DG_OK) return rc;
     }
+  return DG_OK;
+}
+
+int dg_get_rk_register(dg_ctx* c, double* dU, int on_device) {
+  if (!c || !dU) return c ? fail(c, DG_ERR_ARG, "dg_get_rk_register: null dU") : DG_ERR_ARG;
+  cudaError_t e = cudaMemcpyAsync(dU, c->dU, 5 * c->S * sizeof(double),
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "dg_get_rk_register");
+  return DG_OK;
+}
+
+int dg_set_rk_register(dg_ctx* c, const double* dU, int on_device) {
+  if (!c || !dU) return c ? fail(c, DG_ERR_ARG, "dg_set_rk_register: null dU") : DG_ERR_ARG;
+  cudaError_t e = cudaMemcpyAsync(c->dU, dU, 5 * c->S * sizeof(double),
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "dg_set_rk_register");
   return DG_OK;
 }
 

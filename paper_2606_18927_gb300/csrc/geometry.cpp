@@ -4,57 +4,136 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <functional>
+#include <thread>
 
 namespace dg {
 
-static void legendre_pair(int N, double x, double* PN, double* PNm1) {
-  double a = 1.0, b = x;  // P_0, P_1
-  if (N == 0) { *PN = 1.0; *PNm1 = 0.0; return; }
+// ---------------------------------------------------------------------------
+// Double-double arithmetic (Dekker / Knuth error-free transformations): the
+// nodes, the derivative matrix and the metric terms are computed with a
+// ~106-bit significand and rounded to double once.  The curl-form metrics
+// chain two derivative applications (entries up to N(N+1)/4) and lose
+// ~|D|^2 ulps in plain double; the kernels multiply them by O(p0) and O(h)
+// flux values at low Mach number.
+// ---------------------------------------------------------------------------
+struct dd {
+  double hi = 0.0, lo = 0.0;
+  dd() = default;
+  dd(double h) : hi(h), lo(0.0) {}
+  dd(double h, double l) : hi(h), lo(l) {}
+};
+static inline dd two_sum(double a, double b) {
+  const double s = a + b, bb = s - a;
+  return dd(s, (a - (s - bb)) + (b - bb));
+}
+static inline dd fast_two_sum(double a, double b) {
+  const double s = a + b;
+  return dd(s, b - (s - a));
+}
+static inline dd two_prod(double a, double b) {
+  const double p = a * b;
+  return dd(p, std::fma(a, b, -p));
+}
+static inline dd operator+(dd a, dd b) {
+  dd s = two_sum(a.hi, b.hi), t = two_sum(a.lo, b.lo);
+  s.lo += t.hi;
+  s = fast_two_sum(s.hi, s.lo);
+  s.lo += t.lo;
+  return fast_two_sum(s.hi, s.lo);
+}
+static inline dd operator-(dd a) { return dd(-a.hi, -a.lo); }
+static inline dd operator-(dd a, dd b) { return a + (-b); }
+static inline dd operator*(dd a, dd b) {
+  dd p = two_prod(a.hi, b.hi);
+  p.lo += a.hi * b.lo + a.lo * b.hi;
+  return fast_two_sum(p.hi, p.lo);
+}
+static inline dd operator/(dd a, dd b) {
+  const double q1 = a.hi / b.hi;
+  dd r = a - b * dd(q1);
+  const double q2 = r.hi / b.hi;
+  r = r - b * dd(q2);
+  const double q3 = r.hi / b.hi;
+  return fast_two_sum(q1, q2) + dd(q3);
+}
+static inline dd dd_sqrt(dd a) {
+  if (a.hi <= 0.0) return dd(0.0);
+  const double x = std::sqrt(a.hi);
+  const dd y(x);
+  return y + (a - y * y) / dd(2.0 * x);  // one Newton step
+}
+
+static void run_parallel(int count, const std::function<void(int, int)>& fn) {
+  unsigned hw = std::thread::hardware_concurrency();
+  int nt = (int)std::min<unsigned>(hw ? hw : 1, 64);
+  if (count < 64 || nt <= 1) { fn(0, count); return; }
+  std::vector<std::thread> pool;
+  const int chunk = (count + nt - 1) / nt;
+  for (int t = 0; t < nt; ++t) {
+    const int b = t * chunk, e = std::min(count, b + chunk);
+    if (b < e) pool.emplace_back(fn, b, e);
+  }
+  for (auto& th : pool) th.join();
+}
+
+static void legendre_pair(int N, dd x, dd* PN, dd* PNm1) {
+  dd a(1.0), b = x;  // P_0, P_1
+  if (N == 0) { *PN = dd(1.0); *PNm1 = dd(0.0); return; }
   for (int k = 2; k <= N; ++k) {
-    double c = ((2 * k - 1) * x * b - (k - 1) * a) / k;
+    dd c = (dd(2.0 * k - 1.0) * x * b - dd(k - 1.0) * a) / dd((double)k);
     a = b; b = c;
   }
   *PN = b; *PNm1 = a;
 }
 
-Basis make_basis(int N) {
-  Basis B;
-  B.N = N; B.n = N + 1;
-  const int n = B.n;
-  B.x.resize(n); B.w.resize(n); B.D.assign(n * n, 0.0);
+// nodes, weights and D in double-double (Dd) and rounded (x, w, D)
+static void make_basis_dd(int N, std::vector<dd>& x, std::vector<dd>& w, std::vector<dd>& D) {
+  const int n = N + 1;
+  x.assign(n, dd(0.0)); w.assign(n, dd(0.0)); D.assign(n * n, dd(0.0));
   // Chebyshev-Gauss-Lobatto start, then x <- x - (x P_N - P_{N-1}) / ((N+1) P_N)
   // (a Newton step on (1 - x^2) P_N'(x) written through the recurrence).
-  for (int i = 0; i < n; ++i) {
-    double x = std::cos(M_PI * (N - i) / N);
-    for (int it = 0; it < 200; ++it) {
-      double P, Q;
-      legendre_pair(N, x, &P, &Q);
-      double dx = (x * P - Q) / ((N + 1) * P);
-      x -= dx;
-      if (std::fabs(dx) <= 1e-17) break;
+  for (int i = 1; i < N; ++i) {
+    dd xi(std::cos(M_PI * (N - i) / N));
+    for (int it = 0; it < 100; ++it) {
+      dd P, Q;
+      legendre_pair(N, xi, &P, &Q);
+      dd dx = (xi * P - Q) / (dd(N + 1.0) * P);
+      xi = xi - dx;
+      if (std::fabs(dx.hi) <= 1e-32) break;
     }
-    B.x[i] = x;
+    x[i] = xi;
   }
-  B.x[0] = -1.0; B.x[N] = 1.0;
+  x[0] = dd(-1.0); x[N] = dd(1.0);
   for (int i = 0; i < n / 2; ++i) {  // exact symmetry
-    double m = 0.5 * (B.x[N - i] - B.x[i]);
-    B.x[i] = -m; B.x[N - i] = m;
+    dd m = (x[N - i] - x[i]) * dd(0.5);
+    x[i] = -m; x[N - i] = m;
   }
-  if (n % 2) B.x[N / 2] = 0.0;
-  std::vector<double> PN(n);
+  if (n % 2) x[N / 2] = dd(0.0);
+  std::vector<dd> PN(n);
   for (int i = 0; i < n; ++i) {
-    double P, Q;
-    legendre_pair(N, B.x[i], &P, &Q);
+    dd P, Q;
+    legendre_pair(N, x[i], &P, &Q);
     PN[i] = P;
-    B.w[i] = 2.0 / (N * (N + 1.0) * P * P);
+    w[i] = dd(2.0) / (dd(N * (N + 1.0)) * P * P);
   }
   // closed form: D_ij = P_N(x_i) / (P_N(x_j) (x_i - x_j)) for i != j,
   // D_00 = -N(N+1)/4, D_NN = N(N+1)/4, other diagonal entries 0
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j)
-      if (i != j) B.D[i * n + j] = PN[i] / (PN[j] * (B.x[i] - B.x[j]));
-  B.D[0] = -N * (N + 1.0) / 4.0;
-  B.D[N * n + N] = N * (N + 1.0) / 4.0;
+      if (i != j) D[i * n + j] = PN[i] / (PN[j] * (x[i] - x[j]));
+  D[0] = dd(-N * (N + 1.0) / 4.0);
+  D[N * n + N] = dd(N * (N + 1.0) / 4.0);
+}
+
+Basis make_basis(int N) {
+  Basis B;
+  B.N = N; B.n = N + 1;
+  std::vector<dd> x, w, D;
+  make_basis_dd(N, x, w, D);
+  B.x.resize(B.n); B.w.resize(B.n); B.D.resize(B.n * B.n);
+  for (int i = 0; i < B.n; ++i) { B.x[i] = x[i].hi; B.w[i] = w[i].hi; }
+  for (int i = 0; i < B.n * B.n; ++i) B.D[i] = D[i].hi;
   return B;
 }
 
@@ -81,60 +160,62 @@ void lagrange_at(const Basis& b, double s, double* l) {
 // --------------------------------------------------------------------------
 static bool metrics(Geometry& g, std::string& err) {
   const int n = g.n, n3 = g.n3, K = g.K;
-  const std::vector<double>& D = g.basis.D;
+  std::vector<dd> bx, bw, D;
+  make_basis_dd(g.N, bx, bw, D);
   g.Ja.assign((size_t)K * n3 * 9, 0.0);
   g.J.assign((size_t)K * n3, 0.0);
-  std::vector<double> xl(3 * n3), dx(9 * n3), v(3 * n3);
-  auto dxi = [&](const double* f, int dir, int p) {
-    const int i = p % n, j = (p / n) % n, k = p / (n * n);
-    double s = 0.0;
-    if (dir == 0) for (int m = 0; m < n; ++m) s += D[i * n + m] * f[m + n * (j + n * k)];
-    else if (dir == 1) for (int m = 0; m < n; ++m) s += D[j * n + m] * f[i + n * (m + n * k)];
-    else for (int m = 0; m < n; ++m) s += D[k * n + m] * f[i + n * (j + n * m)];
-    return s;
-  };
-  for (int e = 0; e < K; ++e) {
-    // element-local coordinates (relative to the element centroid): the curl
-    // form and the derivatives are unchanged by a constant shift, and the
-    // roundoff then does not grow with the distance from the origin
-    for (int c = 0; c < 3; ++c) {
-      double mean = 0.0;
-      for (int p = 0; p < n3; ++p) mean += g.X[(size_t)c * K * n3 + (size_t)e * n3 + p];
-      mean /= n3;
-      for (int p = 0; p < n3; ++p) xl[c * n3 + p] = g.X[(size_t)c * K * n3 + (size_t)e * n3 + p] - mean;
-    }
-    for (int c = 0; c < 3; ++c)
-      for (int d = 0; d < 3; ++d)
-        for (int p = 0; p < n3; ++p) dx[(c * 3 + d) * n3 + p] = dxi(&xl[c * n3], d, p);
-    for (int p = 0; p < n3; ++p) {
-      const double* a = &dx[0];
-      double m[3][3];
+  std::vector<int> bad(K, 0);
+  run_parallel(K, [&](int e0, int e1) {
+    std::vector<dd> xl(3 * n3), dx(9 * n3), v(3 * n3);
+    auto dxi = [&](const dd* f, int dir, int p) {
+      const int i = p % n, j = (p / n) % n, k = p / (n * n);
+      dd s(0.0);
+      if (dir == 0) for (int m = 0; m < n; ++m) s = s + D[i * n + m] * f[m + n * (j + n * k)];
+      else if (dir == 1) for (int m = 0; m < n; ++m) s = s + D[j * n + m] * f[i + n * (m + n * k)];
+      else for (int m = 0; m < n; ++m) s = s + D[k * n + m] * f[i + n * (j + n * m)];
+      return s;
+    };
+    for (int e = e0; e < e1; ++e) {
+      // element-local coordinates (relative to the element's first node): the
+      // curl form and the derivatives are unchanged by a constant shift
+      for (int c = 0; c < 3; ++c) {
+        const double x0 = g.X[(size_t)c * K * n3 + (size_t)e * n3];
+        for (int p = 0; p < n3; ++p) xl[c * n3 + p] = two_sum(g.X[(size_t)c * K * n3 + (size_t)e * n3 + p], -x0);
+      }
       for (int c = 0; c < 3; ++c)
-        for (int d = 0; d < 3; ++d) m[c][d] = a[(c * 3 + d) * n3 + p];
-      double det = m[0][0] * (m[1][1] * m[2][2] - m[2][1] * m[1][2]) -
-                   m[1][0] * (m[0][1] * m[2][2] - m[2][1] * m[0][2]) +
-                   m[2][0] * (m[0][1] * m[1][2] - m[1][1] * m[0][2]);
-      g.J[(size_t)e * n3 + p] = det;
-      if (!(det > 0.0)) {
-        char buf[128];
-        std::snprintf(buf, sizeof buf, "non-positive Jacobian %.3e in element %d", det, e);
-        err = buf;
-        return false;
-      }
-    }
-    // Ja^i_c = -(curl_xi (x_l grad_xi x_m))_i with (c, m, l) cyclic
-    for (int c = 0; c < 3; ++c) {
-      const int mm = (c + 1) % 3, ll = (c + 2) % 3;
-      for (int d = 0; d < 3; ++d)
-        for (int p = 0; p < n3; ++p) v[d * n3 + p] = xl[ll * n3 + p] * dx[(mm * 3 + d) * n3 + p];
+        for (int d = 0; d < 3; ++d)
+          for (int p = 0; p < n3; ++p) dx[(c * 3 + d) * n3 + p] = dxi(&xl[c * n3], d, p);
       for (int p = 0; p < n3; ++p) {
-        double* ja = &g.Ja[((size_t)e * n3 + p) * 9];
-        ja[0 * 3 + c] = dxi(&v[1 * n3], 2, p) - dxi(&v[2 * n3], 1, p);
-        ja[1 * 3 + c] = dxi(&v[2 * n3], 0, p) - dxi(&v[0 * n3], 2, p);
-        ja[2 * 3 + c] = dxi(&v[0 * n3], 1, p) - dxi(&v[1 * n3], 0, p);
+        dd m[3][3];
+        for (int c = 0; c < 3; ++c)
+          for (int d = 0; d < 3; ++d) m[c][d] = dx[(c * 3 + d) * n3 + p];
+        const dd det = m[0][0] * (m[1][1] * m[2][2] - m[2][1] * m[1][2]) -
+                       m[1][0] * (m[0][1] * m[2][2] - m[2][1] * m[0][2]) +
+                       m[2][0] * (m[0][1] * m[1][2] - m[1][1] * m[0][2]);
+        g.J[(size_t)e * n3 + p] = det.hi;
+        if (!(det.hi > 0.0)) bad[e] = 1;
+      }
+      // Ja^i_c = -(curl_xi (x_l grad_xi x_m))_i with (c, m, l) cyclic
+      for (int c = 0; c < 3; ++c) {
+        const int mm = (c + 1) % 3, ll = (c + 2) % 3;
+        for (int d = 0; d < 3; ++d)
+          for (int p = 0; p < n3; ++p) v[d * n3 + p] = xl[ll * n3 + p] * dx[(mm * 3 + d) * n3 + p];
+        for (int p = 0; p < n3; ++p) {
+          double* ja = &g.Ja[((size_t)e * n3 + p) * 9];
+          ja[0 * 3 + c] = (dxi(&v[1 * n3], 2, p) - dxi(&v[2 * n3], 1, p)).hi;
+          ja[1 * 3 + c] = (dxi(&v[2 * n3], 0, p) - dxi(&v[0 * n3], 2, p)).hi;
+          ja[2 * 3 + c] = (dxi(&v[0 * n3], 1, p) - dxi(&v[1 * n3], 0, p)).hi;
+        }
       }
     }
-  }
+  });
+  for (int e = 0; e < K; ++e)
+    if (bad[e]) {
+      char buf[128];
+      std::snprintf(buf, sizeof buf, "non-positive Jacobian in element %d", e);
+      err = buf;
+      return false;
+    }
   return true;
 }
 
@@ -190,9 +271,9 @@ static bool faces(Geometry& g, std::string& err) {
     for (int ab = 0; ab < n2; ++ab) {
       const int p = face_node(n, fc.lM, ab % n, ab / n);
       const double* ja = &g.Ja[((size_t)fc.eM * n3 + p) * 9 + (fc.lM / 2) * 3];
-      const double s = std::sqrt(ja[0] * ja[0] + ja[1] * ja[1] + ja[2] * ja[2]);
-      for (int c = 0; c < 3; ++c) g.fgeo[(size_t)c * F * n2 + f * n2 + ab] = sgn * ja[c] / s;
-      g.fgeo[3 * F * n2 + f * n2 + ab] = s;
+      const dd s = dd_sqrt(dd(ja[0]) * dd(ja[0]) + dd(ja[1]) * dd(ja[1]) + dd(ja[2]) * dd(ja[2]));
+      for (int c = 0; c < 3; ++c) g.fgeo[(size_t)c * F * n2 + f * n2 + ab] = sgn * (dd(ja[c]) / s).hi;
+      g.fgeo[3 * F * n2 + f * n2 + ab] = s.hi;
     }
   }
   return true;
@@ -287,8 +368,10 @@ static bool wall_samples(Geometry& g, double hwm, std::string& err) {
       double xs[3];
       for (int c = 0; c < 3; ++c)
         xs[c] = g.X[(size_t)c * K * n3 + (size_t)fc.eM * n3 + p] - hwm * g.fgeo[(size_t)c * F * n2 + (size_t)f * n2 + ab];
+      // the lowest-index element containing the point (within 1e-8 in the
+      // reference coordinates): points on a shared face get one element
       int best = -1;
-      double bestm = 0.0, br[3] = {0, 0, 0};
+      double br[3] = {0, 0, 0};
       for (int e : cand) {
         bool in = true;
         for (int c = 0; c < 3; ++c) {
@@ -299,9 +382,10 @@ static bool wall_samples(Geometry& g, double hwm, std::string& err) {
         double r[3];
         if (!invert_map(g, e, xs, r)) continue;
         const double mx = std::max(std::fabs(r[0]), std::max(std::fabs(r[1]), std::fabs(r[2])));
-        if (mx <= 1.0 + 1e-10 && (best < 0 || mx < bestm)) {
-          best = e; bestm = mx;
+        if (mx <= 1.0 + 1e-8) {
+          best = e;
           br[0] = r[0]; br[1] = r[1]; br[2] = r[2];
+          break;
         }
       }
       if (best < 0) {

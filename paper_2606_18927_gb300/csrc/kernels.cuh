@@ -25,6 +25,7 @@ enum { ST_NONFINITE = 1, ST_WM_NOCONV = 2 };
 
 struct PhysDev {
   double gamma, gm1, R, mu, Pr, cp, kcond, rcp_R;
+  double p_ref;  // constant removed from p in the momentum fluxes
   double f[3];
   double kappa, B, hwm;
   int law, vol_flux, surf_flux, viscous;
@@ -72,7 +73,10 @@ __device__ __forceinline__ bool finite_bits(double x) {
 
 // Primitive state in the flux type.  p is recovered in double from the
 // double state (p = (gamma-1)(E - rho |u|^2 / 2) cancels at low Mach number)
-// and only then rounded to R.
+// and stored as p - p_ref (the momentum fluxes see only the deviation from
+// the constant reference pressure; a constant pressure contributes nothing to
+// the element residual by the discrete metric identities).  h = (E + p)/rho
+// uses the full pressure.
 template <typename R>
 struct Prim {
   R rho, u, v, w, p, h;
@@ -85,7 +89,7 @@ __device__ __forceinline__ Prim<R> primitive(const double U0, const double U1, c
   const double ir = 1.0 / U0;
   const double u = U1 * ir, v = U2 * ir, w = U3 * ir;
   const double p = ph.gm1 * (U4 - 0.5 * (U1 * u + U2 * v + U3 * w));
-  q.rho = (R)U0; q.u = (R)u; q.v = (R)v; q.w = (R)w; q.p = (R)p;
+  q.rho = (R)U0; q.u = (R)u; q.v = (R)v; q.w = (R)w; q.p = (R)(p - ph.p_ref);
   q.h = (R)((U4 + p) * ir);
   return q;
 }
@@ -93,7 +97,7 @@ __device__ __forceinline__ Prim<R> primitive(const double U0, const double U1, c
 // Two-point KEP flux F#(L, R) . a (a need not be unit).
 template <typename R>
 __device__ __forceinline__ void twopoint(int kind, const Prim<R>& A, const Prim<R>& B, R a0, R a1, R a2,
-                                         R F[5]) {
+                                         R F[5], R pref) {
   const R rho = R(0.5) * (A.rho + B.rho);
   const R u = R(0.5) * (A.u + B.u), v = R(0.5) * (A.v + B.v), w = R(0.5) * (A.w + B.w);
   const R p = R(0.5) * (A.p + B.p);
@@ -105,9 +109,10 @@ __device__ __forceinline__ void twopoint(int kind, const Prim<R>& A, const Prim<
   F[3] = m * w + p * a2;
   if (kind == 0) {
     F[4] = m * (R(0.5) * (A.h + B.h));
-  } else {  // Kennedy-Gruber: {rho}{u.a}{e} + {p}{u.a}, e = E / rho = h - p / rho
-    const R eA = A.h - A.p / A.rho, eB = B.h - B.p / B.rho;
-    F[4] = m * (R(0.5) * (eA + eB)) + p * ua;
+  } else {  // Kennedy-Gruber: {rho}{u.a}{e} + {p}{u.a}, e = E / rho = h - p / rho (full p)
+    const R pA = A.p + pref, pB = B.p + pref;
+    const R eA = A.h - pA / A.rho, eB = B.h - pB / B.rho;
+    F[4] = m * (R(0.5) * (eA + eB)) + (p + pref) * ua;
   }
 }
 
@@ -115,10 +120,11 @@ __device__ __forceinline__ void twopoint(int kind, const Prim<R>& A, const Prim<
 template <typename R>
 __device__ __forceinline__ void riemann(const PhysDev& ph, const Prim<R>& A, const double UA[5],
                                         const Prim<R>& B, const double UB[5], R nx, R ny, R nz, R F[5]) {
-  twopoint<R>(ph.vol_flux, A, B, nx, ny, nz, F);
+  const R pref = (R)ph.p_ref;
+  twopoint<R>(ph.vol_flux, A, B, nx, ny, nz, F, pref);
   const R g = (R)ph.gamma;
-  if (ph.surf_flux == 1) {  // local Lax-Friedrichs
-    const R cA = sqrt(g * A.p / A.rho), cB = sqrt(g * B.p / B.rho);
+  if (ph.surf_flux == 1) {  // local Lax-Friedrichs (sound speed from the full pressure)
+    const R cA = sqrt(g * (A.p + pref) / A.rho), cB = sqrt(g * (B.p + pref) / B.rho);
     const R lA = fabs(A.u * nx + A.v * ny + A.w * nz) + cA;
     const R lB = fabs(B.u * nx + B.v * ny + B.w * nz) + cB;
     const R lam = R(0.5) * (lA >= lB ? lA : lB);
@@ -505,71 +511,153 @@ k_wall(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, R* __
 }
 
 // ---------------------------------------------------------------------------
-// k_volume: one CTA of n^3 threads per element.  MODE 0 writes Ut; MODE 1
-// applies the LSERK4 stage to U and dU in place.
+// k_volume: one CTA per element.  MODE 0 writes Ut; MODE 1 applies the LSERK4
+// stage to U and dU in place.
+//
+// Split-form volume integral with symmetric pairs: the two-point flux is
+// symmetric, F#(i, m) = F#(m, i), so each unordered pair of a line is
+// evaluated once.  A line of n nodes occupies n consecutive lanes of a warp
+// (32 / n lines per warp); at distance d lane i evaluates the pair
+// (i, i + d mod n), keeps DVS_{i,m} F and hands F to lane m by a shuffle,
+// which applies DVS_{m,i}.  One pass per direction; the three passes meet in
+// a shared-memory residual.  With per-node sums S_x = x_i + x_m the flux is
+// F0 * 8 = S_rho (S_u . S_a) and F1..4 * 16 = m S_u + S_p4 S_a, m S_h, so
+// the scale factors fold into the coefficient tables (DVS/8 and DVS/16).
 // ---------------------------------------------------------------------------
 struct StageArgs {
   double A, B, dt;
   int read_dU;
 };
 
+template <int N>
+struct VolShape {
+  static constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
+  static constexpr int LPW = 32 / n;                        // lines per warp
+  static constexpr int WARPS_LINES = (n2 + LPW - 1) / LPW;  // warps for one direction
+  static constexpr int WARPS_NODES = (n3 + 31) / 32;
+  static constexpr int THREADS = 32 * (WARPS_LINES > WARPS_NODES ? WARPS_LINES : WARPS_NODES);
+  // shared memory (in units of R): 7 prim slots, 9 metric, 5 residual per node,
+  // two coefficient tables, 1/w
+  static constexpr int SMEM_R = 21 * n3 + 2 * n2 + n;
+};
+
 template <int N, typename R, int MODE>
-__global__ void __launch_bounds__((N + 1) * (N + 1) * (N + 1))
+__global__ void __launch_bounds__(VolShape<N>::THREADS)
 k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, const Tables<N> tab,
          const R* __restrict__ Rv, const R* __restrict__ Fs, double* __restrict__ Out,
          double* __restrict__ dU, double* __restrict__ Uout, const StageArgs st, int* __restrict__ status) {
-  constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
+  using Sh = VolShape<N>;
+  constexpr int n = Sh::n, n2 = Sh::n2, n3 = Sh::n3, T = Sh::THREADS, LPW = Sh::LPW;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  R* sQ = reinterpret_cast<R*>(smem_raw);  // [6][n3]: rho u v w p h
-  R* sA = sQ + 6 * n3;                      // [9][n3]: Ja (dir*3+comp)
-  R* sDVS = sA + 9 * n3;                    // [n2]
-  R* siw = sDVS + n2;                       // [n]
-  const int e = blockIdx.x, p = threadIdx.x;
-  const int i = p % n, j = (p / n) % n, k = p / n2;
+  R* sQ = reinterpret_cast<R*>(smem_raw);  // [7][n3]: rho u v w 4p' h|e 2p (KG)
+  R* sA = sQ + 7 * n3;                      // [9][n3]: Ja (dir*3+comp)
+  R* sR = sA + 9 * n3;                      // [5][n3]: residual
+  R* sC8 = sR + 5 * n3;                     // [n2]: DVS / 8
+  R* sC16 = sC8 + n2;                       // [n2]: DVS / 16
+  R* siw = sC16 + n2;                       // [n]
+  const int e = blockIdx.x, t = threadIdx.x;
   const size_t S = (size_t)m.K * n3;
-  const size_t g = (size_t)e * n3 + p;
-  for (int t = p; t < n2; t += n3) sDVS[t] = (R)tab.DVS8[t];
-  if (p < n) siw[p] = (R)tab.iw[p];
+  const bool kg = ph.vol_flux == 1;
+  for (int x = t; x < n2; x += T) {
+    sC8[x] = (R)tab.DVS8[x];
+    sC16[x] = (R)(0.5 * tab.DVS8[x]);
+  }
+  if (t < n) siw[t] = (R)tab.iw[t];
+  // prologue: node t
   double Uo[5];
+  if (t < n3) {
+    const size_t g = (size_t)e * n3 + t;
 #pragma unroll
-  for (int v = 0; v < 5; ++v) Uo[v] = Uin[v * S + g];
-  const Prim<R> qo = primitive<R>(Uo[0], Uo[1], Uo[2], Uo[3], Uo[4], ph);
-  sQ[p] = qo.rho; sQ[n3 + p] = qo.u; sQ[2 * n3 + p] = qo.v; sQ[3 * n3 + p] = qo.w;
-  sQ[4 * n3 + p] = qo.p; sQ[5 * n3 + p] = qo.h;
+    for (int v = 0; v < 5; ++v) Uo[v] = Uin[v * S + g];
+    const Prim<R> q = primitive<R>(Uo[0], Uo[1], Uo[2], Uo[3], Uo[4], ph);
+    sQ[t] = q.rho; sQ[n3 + t] = q.u; sQ[2 * n3 + t] = q.v; sQ[3 * n3 + t] = q.w;
+    sQ[4 * n3 + t] = R(4) * q.p;
+    if (!kg) {
+      sQ[5 * n3 + t] = q.h;
+    } else {
+      const R pf = q.p + (R)ph.p_ref;
+      sQ[5 * n3 + t] = q.h - pf / q.rho;  // e = E / rho
+      sQ[6 * n3 + t] = R(2) * pf;
+    }
 #pragma unroll
-  for (int c = 0; c < 9; ++c) sA[c * n3 + p] = m.Ja[(size_t)c * S + g];
-  const R iJ = m.invJ[g];
+    for (int c = 0; c < 9; ++c) sA[c * n3 + t] = m.Ja[(size_t)c * S + g];
+  }
   __syncthreads();
-  R acc[5] = {0, 0, 0, 0, 0};
-  // split-form volume integral: sum_dir sum_m DVS_im F#(p, m) . {Ja^dir}
+  // three direction passes over the lines
+  {
+    const int warp = t >> 5, lane = t & 31;
+    const int seg = lane / n, pos = lane - seg * n;
+    const int L0 = warp * LPW + seg;
+    const bool active = (seg < LPW) && (L0 < n2);
+    const int L = active ? L0 : 0;
+    const int base = seg * n;  // first lane of the segment
+#pragma unroll 1
+    for (int dir = 0; dir < 3; ++dir) {
+      const int a = L % n, b = L / n;
+      auto node = [&](int q) {
+        return dir == 0 ? q + n * L : (dir == 1 ? a + n * q + n2 * b : L + n2 * q);
+      };
+      const int me = node(pos);
+      const R rho = sQ[me], u = sQ[n3 + me], v = sQ[2 * n3 + me], w = sQ[3 * n3 + me];
+      const R p4 = sQ[4 * n3 + me], hh = sQ[5 * n3 + me];
+      const R p2 = kg ? sQ[6 * n3 + me] : R(0);
+      const R a0 = sA[(dir * 3 + 0) * n3 + me], a1 = sA[(dir * 3 + 1) * n3 + me],
+              a2 = sA[(dir * 3 + 2) * n3 + me];
+      R acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0, acc4 = 0;
 #pragma unroll
-  for (int dir = 0; dir < 3; ++dir) {
-    const int idx = dir == 0 ? i : (dir == 1 ? j : k);
-    const int base = p - idx * (dir == 0 ? 1 : (dir == 1 ? n : n2));
-    const int stride = dir == 0 ? 1 : (dir == 1 ? n : n2);
-    const R a0 = sA[(dir * 3 + 0) * n3 + p], a1 = sA[(dir * 3 + 1) * n3 + p], a2 = sA[(dir * 3 + 2) * n3 + p];
-#pragma unroll
-    for (int mm = 0; mm < n; ++mm) {
-      if (mm == idx) continue;
-      const int q = base + mm * stride;
-      Prim<R> qm;
-      qm.rho = sQ[q]; qm.u = sQ[n3 + q]; qm.v = sQ[2 * n3 + q]; qm.w = sQ[3 * n3 + q];
-      qm.p = sQ[4 * n3 + q]; qm.h = sQ[5 * n3 + q];
-      R F[5];
-      // metric average {Ja} = (Ja_p + Ja_m) / 2; DVS8 carries 2D/8 so the
-      // flux is evaluated with 4 {Ja} ... folded below as (Ja_p + Ja_m) * 4
-      twopoint<R>(ph.vol_flux, qo, qm, a0 + sA[(dir * 3 + 0) * n3 + q], a1 + sA[(dir * 3 + 1) * n3 + q],
-                  a2 + sA[(dir * 3 + 2) * n3 + q], F);
-      const R c = R(4) * sDVS[idx * n + mm];
-#pragma unroll
-      for (int v = 0; v < 5; ++v) acc[v] += c * F[v];
+      for (int d = 1; d <= n / 2; ++d) {
+        const int pm = pos + d < n ? pos + d : pos + d - n;
+        const int q = node(pm);
+        const R Sr = rho + sQ[q], Su = u + sQ[n3 + q], Sv = v + sQ[2 * n3 + q], Sw = w + sQ[3 * n3 + q];
+        const R Sp = p4 + sQ[4 * n3 + q], Sh = hh + sQ[5 * n3 + q];
+        const R Sa0 = a0 + sA[(dir * 3 + 0) * n3 + q], Sa1 = a1 + sA[(dir * 3 + 1) * n3 + q],
+                Sa2 = a2 + sA[(dir * 3 + 2) * n3 + q];
+        const R ua = Su * Sa0 + Sv * Sa1 + Sw * Sa2;
+        const R mf = Sr * ua;                 // 8 F0
+        const R F1 = mf * Su + Sp * Sa0;      // 16 F1
+        const R F2 = mf * Sv + Sp * Sa1;
+        const R F3 = mf * Sw + Sp * Sa2;
+        R F4 = mf * Sh;                       // 16 F4
+        if (kg) F4 += (p2 + sQ[6 * n3 + q]) * ua;
+        const R c8 = sC8[pos * n + pm], c16 = sC16[pos * n + pm];
+        acc0 += c8 * mf; acc1 += c16 * F1; acc2 += c16 * F2; acc3 += c16 * F3; acc4 += c16 * F4;
+        if (2 * d != n) {
+          // hand the pair flux to the partner lane (pos + d); receive the one
+          // of lane (pos - d)
+          const int src = base + (pos - d >= 0 ? pos - d : pos - d + n);
+          const R g0 = __shfl_sync(0xffffffffu, mf, src);
+          const R g1 = __shfl_sync(0xffffffffu, F1, src);
+          const R g2 = __shfl_sync(0xffffffffu, F2, src);
+          const R g3 = __shfl_sync(0xffffffffu, F3, src);
+          const R g4 = __shfl_sync(0xffffffffu, F4, src);
+          const int ps = src - base;
+          const R r8 = sC8[pos * n + ps], r16 = sC16[pos * n + ps];
+          acc0 += r8 * g0; acc1 += r16 * g1; acc2 += r16 * g2; acc3 += r16 * g3; acc4 += r16 * g4;
+        }
+      }
+      if (active) {
+        if (dir == 0) {
+          sR[me] = acc0; sR[n3 + me] = acc1; sR[2 * n3 + me] = acc2; sR[3 * n3 + me] = acc3; sR[4 * n3 + me] = acc4;
+        } else {
+          sR[me] += acc0; sR[n3 + me] += acc1; sR[2 * n3 + me] += acc2; sR[3 * n3 + me] += acc3;
+          sR[4 * n3 + me] += acc4;
+        }
+      }
+      __syncthreads();
     }
   }
+  if (t >= n3) return;
+  // epilogue: node t
+  const int i = t % n, j = (t / n) % n, k = t / n2;
+  const size_t g = (size_t)e * n3 + t;
+  R acc[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) acc[v] = sR[v * n3 + t];
   if (ph.viscous) {
 #pragma unroll
     for (int v = 0; v < 4; ++v) acc[v + 1] += Rv[(size_t)v * S + g];
   }
-  // surface integral: + sgn * Fs / w_perp on the faces that touch p
+  // surface integral: + sgn * Fs / w_perp on the faces that touch the node
   auto surf = [&](int l, int ab, R iw) {
     const int code = m.elem_face[e * 6 + l];
     const int f = code >> 1;
@@ -585,10 +673,11 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
   if (k == 0) surf(4, i + n * j, siw[0]);
   if (k == N) surf(5, i + n * j, siw[N]);
   // Ut = -(1/J) acc + S, S = (0, f, f . u)
+  const R iJ = m.invJ[g];
   double Ut[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) Ut[v] = -(double)(iJ * acc[v]);
-  {
+  if (ph.f[0] != 0.0 || ph.f[1] != 0.0 || ph.f[2] != 0.0) {
     const double ir = 1.0 / Uo[0];
     Ut[1] += ph.f[0]; Ut[2] += ph.f[1]; Ut[3] += ph.f[2];
     Ut[4] += (ph.f[0] * Uo[1] + ph.f[1] * Uo[2] + ph.f[2] * Uo[3]) * ir;

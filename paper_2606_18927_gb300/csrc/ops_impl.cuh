@@ -37,7 +37,8 @@ static int run_typed(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {
   R* Gf = static_cast<R*>(a.Gf);
   R* Fs = static_cast<R*>(a.Fs);
   const size_t smem_lift = (size_t)(16 * n3 + 26 * n2 + n) * sizeof(R);
-  const size_t smem_vol = (size_t)(15 * n3 + n2 + n) * sizeof(R);
+  const size_t smem_vol = (size_t)VolShape<N>::SMEM_R * sizeof(R);
+  constexpr int vol_threads = VolShape<N>::THREADS;
   // per device and cheap: set on every call
   cudaFuncSetAttribute(k_lift<N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_lift);
   cudaFuncSetAttribute(k_volume<N, R, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_vol);
@@ -59,9 +60,9 @@ static int run_typed(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {
   if (a.ev) cudaEventRecord(a.ev[3], s);
   StageArgs st{a.A, a.B, a.dt, a.read_dU};
   if (a.mode == 0)
-    k_volume<N, R, 0><<<a.K, n3, smem_vol, s>>>(a.Uin, m, ph, tab, Rv, Fs, a.Out, nullptr, nullptr, st, a.status);
+    k_volume<N, R, 0><<<a.K, vol_threads, smem_vol, s>>>(a.Uin, m, ph, tab, Rv, Fs, a.Out, nullptr, nullptr, st, a.status);
   else
-    k_volume<N, R, 1><<<a.K, n3, smem_vol, s>>>(a.Uin, m, ph, tab, Rv, Fs, nullptr, a.dU, a.Uout, st, a.status);
+    k_volume<N, R, 1><<<a.K, vol_threads, smem_vol, s>>>(a.Uin, m, ph, tab, Rv, Fs, nullptr, a.dU, a.Uout, st, a.status);
   if (a.ev) cudaEventRecord(a.ev[4], s);
   return (int)cudaGetLastError();
 }

@@ -43,7 +43,8 @@ class _MeshDesc(ctypes.Structure):
 class _Phys(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("R", ctypes.c_double), ("mu", ctypes.c_double),
                 ("Pr", ctypes.c_double), ("force", ctypes.c_double * 3), ("kappa", ctypes.c_double),
-                ("B", ctypes.c_double), ("hwm", ctypes.c_double), ("law", ctypes.c_int)]
+                ("B", ctypes.c_double), ("hwm", ctypes.c_double), ("law", ctypes.c_int),
+                ("p_ref", ctypes.c_double)]
 
 
 class _Options(ctypes.Structure):
@@ -81,6 +82,8 @@ def lib():
         "dg_rk_stage": (c_int, [vp, c_int, c_double, c_double]),
         "dg_rk_steps": (c_int, [vp, c_double, c_double, c_int]),
         "dg_check_status": (c_int, [vp]),
+        "dg_get_rk_register": (c_int, [vp, vp, c_int]),
+        "dg_set_rk_register": (c_int, [vp, vp, c_int]),
         "dg_get_metrics": (c_int, [vp, dp, dp]),
         "dg_profile_enable": (c_int, [vp, c_int]),
         "dg_profile_read": (c_int, [vp, dp, ip]),
@@ -139,7 +142,8 @@ class Operator:
                        nbr.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
         ph = _Phys(phys["gamma"], phys["R"], phys["mu"], phys["Pr"],
                    (ctypes.c_double * 3)(phys.get("fx", 0.0), phys.get("fy", 0.0), phys.get("fz", 0.0)),
-                   phys.get("kappa", 0.41), phys.get("B", 5.2), phys.get("hwm", 0.1), int(law))
+                   phys.get("kappa", 0.41), phys.get("B", 5.2), phys.get("hwm", 0.1), int(law),
+                   phys.get("p_ref", phys.get("p0", 0.0)))
         op = _Options(int(precision), int(vol_flux), int(surf_flux), int(viscous))
         h = ctypes.c_void_p()
         self._stream = _stream_handle(stream)
@@ -179,18 +183,37 @@ class Operator:
         self._check(lib().dg_set_state(self.h, p, dev))
 
     def get_state(self, out):
+        if (out.numel() if hasattr(out, "numel") else out.size) != self.numel:
+            raise ValueError("array has the wrong size for this mesh")
         p, dev = _ptr(out)
         self._check(lib().dg_get_state(self.h, p, dev))
         return out
+
+    def get_rk_register(self, out):
+        if (out.numel() if hasattr(out, "numel") else out.size) != self.numel:
+            raise ValueError("array has the wrong size for this mesh")
+        p, dev = _ptr(out)
+        self._check(lib().dg_get_rk_register(self.h, p, dev))
+        return out
+
+    def set_rk_register(self, dU):
+        if (dU.numel() if hasattr(dU, "numel") else dU.size) != self.numel:
+            raise ValueError("array has the wrong size for this mesh")
+        p, dev = _ptr(dU)
+        self._check(lib().dg_set_rk_register(self.h, p, dev))
 
     def time_derivative(self, Ut, U=None, t=0.0):
         """Ut <- DG_Operator(U) (U None: the context's state).  Ut and U are
         both device tensors or both host arrays."""
         po, dev = _ptr(Ut)
         pu = None
+        for a in (Ut, U):
+            if a is not None and (a.numel() if hasattr(a, "numel") else a.size) != self.numel:
+                raise ValueError("array has the wrong size for this mesh")
         if U is not None:
             pu, devu = _ptr(U)
-            assert devu == dev
+            if devu != dev:
+                raise ValueError("U and Ut must both be on the device or both on the host")
         self._check(lib().dg_time_derivative(self.h, pu, po, float(t), dev))
         return Ut
 

@@ -126,37 +126,46 @@ def _unit_coords(spec: BoxSpec, xi):
     return sx, sy, sz
 
 
+def _quantize(w, spec):
+    """Round a displacement to a multiple of the ulp of the largest domain
+    coordinate, so that (period + w) and w differ by exactly the period."""
+    q = 2.0 ** (math.frexp(max(spec.lengths) + abs(spec.amplitude) + 1.0)[1] - 53)
+    return np.round(w / q) * q
+
+
 def node_coordinates(spec: BoxSpec, xi):
     """Physical node coordinates X[3][K][n^3] of the mapped box.
 
-    xi are the caller's reference nodes on [-1, 1] (Gauss-Lobatto)."""
+    xi are the caller's reference nodes on [-1, 1] (Gauss-Lobatto).  The
+    warps are evaluated on the unit coordinate wrapped into [0, 1) along
+    periodic axes and quantised to the ulp of the domain length, so the two
+    periodic images of a face are exact translations of each other."""
     sx, sy, sz = _unit_coords(spec, xi)
     Lx, Ly, Lz = spec.lengths
     a = spec.amplitude
+    wrap = [np.where(c >= 1.0, c - 1.0, c) if per else c
+            for c, per in zip((sx, sy, sz), spec.periodic)]
     if spec.geometry == "affine":
         X = (Lx * sx, Ly * sy, Lz * sz)
     elif spec.geometry == "sine":
         # x' = x + a sin(y) sin(z), cyclic over the axes
-        x, y, z = Lx * sx, Ly * sy, Lz * sz
-        X = (x + a * np.sin(y) * np.sin(z),
-             y + a * np.sin(z) * np.sin(x),
-             z + a * np.sin(x) * np.sin(y))
+        xw, yw, zw = Lx * wrap[0], Ly * wrap[1], Lz * wrap[2]
+        X = (Lx * sx + _quantize(a * np.sin(yw) * np.sin(zw), spec),
+             Ly * sy + _quantize(a * np.sin(zw) * np.sin(xw), spec),
+             Lz * sz + _quantize(a * np.sin(xw) * np.sin(yw), spec))
     elif spec.geometry == "channel":
         # y = 1 + tanh(beta (2 eta - 1)) / tanh(beta) on [0, 2], then every
         # coordinate += a sin(x) sin(pi y / 2) sin(2 z)
         beta = spec.stretch
-        x = Lx * sx
         y = 0.5 * Ly * (1.0 + np.tanh(beta * (2.0 * sy - 1.0)) / math.tanh(beta))
-        z = Lz * sz
-        wv = a * np.sin(x) * np.sin(math.pi * y / Ly) * np.sin(2.0 * z)
-        X = (x + wv, y + wv, z + wv)
+        wv = _quantize(a * np.sin(Lx * wrap[0]) * np.sin(math.pi * y / Ly) * np.sin(2.0 * Lz * wrap[2]), spec)
+        X = (Lx * sx + wv, y + wv, Lz * sz + wv)
     elif spec.geometry == "wavy":
         # periodic warp on [0, L]^3: x += a sin(2 pi y / L) sin(2 pi z / L), cyclic
-        x, y, z = Lx * sx, Ly * sy, Lz * sz
-        kx, ky, kz = 2 * math.pi / Lx, 2 * math.pi / Ly, 2 * math.pi / Lz
-        X = (x + a * np.sin(ky * y) * np.sin(kz * z),
-             y + a * np.sin(kz * z) * np.sin(kx * x),
-             z + a * np.sin(kx * x) * np.sin(ky * y))
+        tp = 2 * math.pi
+        X = (Lx * sx + _quantize(a * np.sin(tp * wrap[1]) * np.sin(tp * wrap[2]), spec),
+             Ly * sy + _quantize(a * np.sin(tp * wrap[2]) * np.sin(tp * wrap[0]), spec),
+             Lz * sz + _quantize(a * np.sin(tp * wrap[0]) * np.sin(tp * wrap[1]), spec))
     else:
         raise ValueError("unknown geometry " + spec.geometry)
     return np.ascontiguousarray(np.stack(X))
