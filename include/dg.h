@@ -163,6 +163,34 @@ int dg_check_status(dg_ctx* c);
 int dg_profile_enable(dg_ctx* c, int enable);
 int dg_profile_read(dg_ctx* c, double* ms, int* launches);
 
+/* Size in bytes of the static scratch array of dg_time_derivative_noalloc. */
+#define DG_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/* Ut = DG_Operator(U) like dg_time_derivative with device pointers, but
+ * without the context's scratch buffers: the intermediate arrays of the
+ * kernels come from one static device array of DG_NOALLOC_SCRATCH_BYTES
+ * (32 MiB), which every GPU that loads the library holds until the process
+ * exits.  The call allocates nothing.  The paper has no counterpart.
+ *
+ * It is meant for host programs that own all device memory through their
+ * own allocator and cannot let a library call cudaMalloc when it computes
+ * (as the paper's Fortran core does for its HIP kernels), and for callers
+ * that run many contexts but want one shared scratch area instead of one
+ * per context.  The mesh arrays still come from the context, which
+ * dg_init_mesh allocated during set-up.
+ *   U, Ut  device pointers, double[5][K][n^3]; U is read, Ut written.
+ *   Errors DG_ERR_ARG if the mesh needs more scratch than the static array
+ *   holds (the viscous FP64 operator needs about 84 bytes per DOF at N = 5
+ *   and 72 at N = 7, so about 4e5 DOF fit, e.g. the 221,184-DOF channel;
+ *   the message gives the bytes needed), DG_ERR_CUDA on a CUDA failure.
+ * The first call on a device looks up the array's device address (the host
+ * symbol is only a stand-in) and caches it; make that first call before any
+ * stream capture.  All calls share the array: calls whose kernels overlap on
+ * the GPU (different streams, different host threads) race on it.  Every
+ * scratch word is rewritten before it is read in each call, so nothing
+ * carries over from the previous call. */
+int dg_time_derivative_noalloc(dg_ctx* c, const double* U, double* Ut);
+
 /* Host copies of the geometry (for checking): Ja[K][n^3][3 dir][3 comp],
  * J[K][n^3]. */
 int dg_get_metrics(const dg_ctx* c, double* Ja, double* J);

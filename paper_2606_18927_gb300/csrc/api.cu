@@ -133,6 +133,30 @@ int run_operator(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {
 }
 }  // namespace dg
 
+namespace dg {
+// Operator arguments of a context for dg_time_derivative_noalloc (noalloc.cu):
+// everything except the scratch pointers, plus the scratch sizes in bytes.
+int noalloc_args(dg_ctx* c, const double* U, double* Ut, OpArgs* a, const PhysDev** ph, cudaStream_t* s,
+                 size_t* rv_bytes, size_t* gf_bytes, size_t* fs_bytes) {
+  const size_t rs = c->opts.precision == DG_FP32_MIXED ? sizeof(float) : sizeof(double);
+  *a = OpArgs{};
+  a->N = c->N; a->K = c->K; a->F = c->F; a->n_interior = c->geo.n_interior; a->n_wall = c->geo.n_wall;
+  a->fp32 = c->opts.precision == DG_FP32_MIXED;
+  a->Ja = c->Ja; a->invJ = c->invJ; a->fgeo = c->fgeo; a->nbr = c->nbr; a->elem_face = c->elem_face;
+  a->faces = c->faces; a->ws_elem = c->ws_elem; a->ws_lag = c->ws_lag;
+  a->D = c->geo.basis.D.data(); a->w = c->geo.basis.w.data();
+  a->Uin = U; a->status = c->status;
+  a->mode = 0; a->Out = Ut;
+  *ph = &c->ph;
+  *s = c->stream;
+  *rv_bytes = (c->opts.viscous ? 4 * c->S : 1) * rs;
+  *gf_bytes = (c->opts.viscous ? 24 * (size_t)c->K * c->n2 : 1) * rs;
+  *fs_bytes = 5 * (size_t)c->F * c->n2 * rs;
+  return DG_OK;
+}
+int noalloc_fail(dg_ctx* c, int code, const std::string& msg) { return fail(c, code, msg); }
+}  // namespace dg
+
 extern "C" {
 
 int dg_lgl_nodes(int N, double* xi, double* w) {

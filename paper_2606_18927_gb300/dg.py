@@ -85,6 +85,7 @@ def lib():
         "dg_get_rk_register": (c_int, [vp, vp, c_int]),
         "dg_set_rk_register": (c_int, [vp, vp, c_int]),
         "dg_get_metrics": (c_int, [vp, dp, dp]),
+        "dg_time_derivative_noalloc": (c_int, [vp, vp, vp]),
         "dg_profile_enable": (c_int, [vp, c_int]),
         "dg_profile_read": (c_int, [vp, dp, ip]),
     }
