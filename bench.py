@@ -120,9 +120,9 @@ def load_peaks():
         return {}
 
 
-def build_case(wl_name, precision, lgl):
+def build_case(wl_name, precision, lgl, elems=None):
     from paper_2606_18927_gb300 import inputs as I
-    wl = I.workload(wl_name)
+    wl = I.workload(wl_name, elems=elems)
     x, _ = lgl(wl.spec.N)
     X = I.node_coordinates(wl.spec, x)
     nbr = I.connectivity(wl.spec)
@@ -197,7 +197,8 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     precision = dg.FP32_MIXED if args.precision == "fp32" else dg.FP64
-    wl, X, nbr, U = build_case(args.workload, precision, dg.lgl_nodes)
+    wl, X, nbr, U = build_case(args.workload, precision, dg.lgl_nodes,
+                               elems=tuple(args.elems) if args.elems else None)
     stream = torch.cuda.current_stream()
     free0 = torch.cuda.mem_get_info()[0]
     op = dg.Operator(wl.spec.N, X, nbr, wl.phys, precision=precision, vol_flux=wl.vol_flux,
@@ -327,6 +328,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
     ap.add_argument("--workload", default="tgv_n7_32")
+    ap.add_argument("--elems", type=int, nargs=3, default=None,
+                    help="element counts of a smaller case of the same workload (profiling)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
