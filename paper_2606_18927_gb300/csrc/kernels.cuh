@@ -94,6 +94,43 @@ __device__ __forceinline__ Prim<R> primitive(const double U0, const double U1, c
   return q;
 }
 
+// Mixed form: everything in FP32 except the pressure recovery, whose
+// cancellation E - rho |u|^2 / 2 is taken in FP64 (two FP64 operations).
+template <>
+__device__ __forceinline__ Prim<float> primitive<float>(const double U0, const double U1, const double U2,
+                                                        const double U3, const double U4, const PhysDev& ph) {
+  Prim<float> q;
+  const float rho = (float)U0, ir = 1.0f / rho;
+  const float m1 = (float)U1, m2 = (float)U2, m3 = (float)U3;
+  q.rho = rho; q.u = m1 * ir; q.v = m2 * ir; q.w = m3 * ir;
+  const float ke = 0.5f * (m1 * q.u + m2 * q.v + m3 * q.w);
+  const double pr = fma(ph.gm1, U4 - (double)ke, -ph.p_ref);  // p - p_ref
+  q.p = (float)pr;
+  q.h = ((float)U4 + q.p + (float)ph.p_ref) * ir;
+  return q;
+}
+
+// (u, v, w, T) for the lifting, in the flux type (same pressure recovery).
+template <typename R>
+__device__ __forceinline__ void velocity_temperature(const double U0, const double U1, const double U2,
+                                                     const double U3, const double U4, const PhysDev& ph,
+                                                     R& u, R& v, R& w, R& T) {
+  const double ir = 1.0 / U0;
+  const double ud = U1 * ir, vd = U2 * ir, wd = U3 * ir;
+  const double pr = ph.gm1 * (U4 - 0.5 * U0 * (ud * ud + vd * vd + wd * wd));
+  u = (R)ud; v = (R)vd; w = (R)wd; T = (R)(pr * ph.rcp_R * ir);
+}
+
+template <>
+__device__ __forceinline__ void velocity_temperature<float>(const double U0, const double U1, const double U2,
+                                                            const double U3, const double U4,
+                                                            const PhysDev& ph, float& u, float& v, float& w,
+                                                            float& T) {
+  const Prim<float> q = primitive<float>(U0, U1, U2, U3, U4, ph);
+  u = q.u; v = q.v; w = q.w;
+  T = (q.p + (float)ph.p_ref) * (float)ph.rcp_R / q.rho;
+}
+
 // Two-point KEP flux F#(L, R) . a (a need not be unit).
 template <typename R>
 __device__ __forceinline__ void twopoint(int kind, const Prim<R>& A, const Prim<R>& B, R a0, R a1, R a2,
@@ -276,10 +313,9 @@ k_lift(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
   if (p < n) siw[p] = (R)tab.iw[p];
   // own primitives W = (u, v, w, T)
   {
-    const double U0 = U[g], ir = 1.0 / U0;
-    const double u = U[S + g] * ir, v = U[2 * S + g] * ir, w = U[3 * S + g] * ir;
-    const double pr = ph.gm1 * (U[4 * S + g] - 0.5 * U0 * (u * u + v * v + w * w));
-    sW[p] = (R)u; sW[n3 + p] = (R)v; sW[2 * n3 + p] = (R)w; sW[3 * n3 + p] = (R)(pr * ph.rcp_R * ir);
+    R u, v, w, T;
+    velocity_temperature<R>(U[g], U[S + g], U[2 * S + g], U[3 * S + g], U[4 * S + g], ph, u, v, w, T);
+    sW[p] = u; sW[n3 + p] = v; sW[2 * n3 + p] = w; sW[3 * n3 + p] = T;
   }
   // own metrics
   R ja[9];
@@ -297,11 +333,10 @@ k_lift(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
     R d0, d1, d2, d3;
     if (nb >= 0) {
       const size_t gn = (size_t)nb * n3 + fnode<N>(l ^ 1, a, b);
-      const double U0 = U[gn], ir = 1.0 / U0;
-      const double u = U[S + gn] * ir, v = U[2 * S + gn] * ir, w = U[3 * S + gn] * ir;
-      const double pr = ph.gm1 * (U[4 * S + gn] - 0.5 * U0 * (u * u + v * v + w * w));
-      d0 = R(0.5) * ((R)u - Wo0); d1 = R(0.5) * ((R)v - Wo1); d2 = R(0.5) * ((R)w - Wo2);
-      d3 = R(0.5) * ((R)(pr * ph.rcp_R * ir) - Wo3);
+      R u, v, w, T;
+      velocity_temperature<R>(U[gn], U[S + gn], U[2 * S + gn], U[3 * S + gn], U[4 * S + gn], ph, u, v, w, T);
+      d0 = R(0.5) * (u - Wo0); d1 = R(0.5) * (v - Wo1); d2 = R(0.5) * (w - Wo2);
+      d3 = R(0.5) * (T - Wo3);
     } else {
       // mirror: W* - W = -(u . n) n, T unchanged (n: own outward unit normal)
       const size_t gq = (size_t)e * n3 + q;
