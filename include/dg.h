@@ -144,6 +144,40 @@ int dg_rk_stage(dg_ctx* c, int s, double t, double dt);
 /* nsteps full LSERK4 steps from time t. */
 int dg_rk_steps(dg_ctx* c, double t, double dt, int nsteps);
 
+/* Vector-Jacobian product of the operator (the hand-written adjoint):
+ *   gU     = (dUt/dU)^T lam,
+ *   gtheta = (dUt/d(kappa, B))^T lam  (wall-law constants; zero without walls).
+ * U: device array or NULL for the context's state; lam, gU: device arrays
+ * double[5][K][n^3]; gtheta: device double[2] or NULL.  The transposed
+ * split-form volume integral, viscous flux, BR1 lifting and primitive
+ * recovery are written out by hand; the local Jacobians of the Riemann
+ * solver and of the wall model (with the implicit function theorem for the
+ * law of the wall, Sec. 3.2) come from forward-mode dual numbers.  FP64
+ * contexts with the Pirozzoli volume flux (else DG_ERR_NOT_IMPLEMENTED).
+ * The first call allocates the adjoint scratch of the context. */
+int dg_vjp(dg_ctx* c, const double* U, const double* lam, double* gU, double* gtheta);
+
+/* Sets the wall-law constants (kappa, B) used by later calls (Sec. 3.2). */
+int dg_set_params(dg_ctx* c, double kappa, double B);
+
+/* Mean wall shear: the surface-quadrature-weighted mean of tau_w t_x over
+ * all wall-modelled faces (t: unit wall-parallel sample velocity).  U: device
+ * array or NULL for the state; loss: host double.  Synchronises the stream.
+ * DG_ERR_ARG without wall-modelled walls. */
+int dg_wall_shear(dg_ctx* c, const double* U, double* loss);
+
+/* Rollout adjoint: runs nsteps LSERK4 steps of size dt from U0 (device),
+ * keeping one checkpoint of U per step (A_0 = 0, so U alone restarts a
+ * step; checkpoints take nsteps * 5 K n^3 doubles of device memory), takes
+ * L = mean wall shear of the final state, then sweeps the steps backwards,
+ * recomputing each step's five stage inputs from its checkpoint and applying
+ * the transposed 2N-storage recurrence with dg_vjp per stage.  Returns L
+ * (host double), gU0 = dL/dU0 (device array) and gtheta = dL/d(kappa, B)
+ * (device double[2] or NULL).  The context's state is not touched.
+ * FP64 contexts with the Pirozzoli flux and wall-modelled walls. */
+int dg_rollout_vjp(dg_ctx* c, const double* U0, int nsteps, double dt, double* loss, double* gU0,
+                   double* gtheta);
+
 /* Copies the LSERK4 register dU (5 K n^3 doubles) out of / into the context
  * (checkpoint and restart inside a step; between steps dU needs no saving
  * because A_0 = 0). */

@@ -1,0 +1,809 @@
+// adjoint.cuh -- vector-Jacobian product of the DGSEM operator (FP64).
+//
+// Given a cotangent lam of Ut = DG_Operator(U), computes gU = (dUt/dU)^T lam
+// and g_theta = (dUt/d(kappa, B))^T lam for the wall-law constants.  The
+// kernels run the forward operator's structure backwards:
+//   k_adj_face   interior face nodes: cotangent of the surface flux from the
+//                two sides' lam, transposed local Jacobian of the Riemann flux
+//                (by forward-mode duals over the 10 state components), and
+//                the cotangents of the two sides' viscous face fluxes;
+//   k_adj_wall   wall face nodes: the same through the mirror state, and the
+//                wall-model derivative (implicit function theorem for the law
+//                of the wall) with respect to the sample state and (kappa, B);
+//   k_adj_element one CTA per element: transposed split-form volume integral
+//                (hand-derived, symmetric pairs with shuffles), transposed
+//                viscous divergence and viscous flux, transposed BR1 lifting,
+//                transposed primitive recovery, source term;
+//   k_adj_gather  adds the per-face contributions of the face kernels and of
+//                the neighbours' lifting to every node;
+//   k_adj_scatter adds the wall-model sample cotangents to the sample
+//                elements (Lagrange weights; atomics).
+#pragma once
+#include "kernels.cuh"
+
+namespace dg {
+
+// ---------------------------------------------------------------------------
+// forward-mode dual number (value, one directional derivative)
+// ---------------------------------------------------------------------------
+struct DualD {
+  double v, d;
+  __device__ DualD() : v(0.0), d(0.0) {}
+  __device__ DualD(double x) : v(x), d(0.0) {}
+  __device__ DualD(double x, double dx) : v(x), d(dx) {}
+};
+__device__ __forceinline__ DualD operator+(DualD a, DualD b) { return DualD(a.v + b.v, a.d + b.d); }
+__device__ __forceinline__ DualD operator-(DualD a, DualD b) { return DualD(a.v - b.v, a.d - b.d); }
+__device__ __forceinline__ DualD operator-(DualD a) { return DualD(-a.v, -a.d); }
+__device__ __forceinline__ DualD operator*(DualD a, DualD b) { return DualD(a.v * b.v, a.d * b.v + a.v * b.d); }
+__device__ __forceinline__ DualD operator/(DualD a, DualD b) {
+  const double r = a.v / b.v;
+  return DualD(r, (a.d - r * b.d) / b.v);
+}
+__device__ __forceinline__ DualD operator+(DualD a, double b) { return DualD(a.v + b, a.d); }
+__device__ __forceinline__ DualD operator+(double a, DualD b) { return DualD(a + b.v, b.d); }
+__device__ __forceinline__ DualD operator-(DualD a, double b) { return DualD(a.v - b, a.d); }
+__device__ __forceinline__ DualD operator-(double a, DualD b) { return DualD(a - b.v, -b.d); }
+__device__ __forceinline__ DualD operator*(DualD a, double b) { return DualD(a.v * b, a.d * b); }
+__device__ __forceinline__ DualD operator*(double a, DualD b) { return DualD(a * b.v, a * b.d); }
+__device__ __forceinline__ DualD operator/(DualD a, double b) { return DualD(a.v / b, a.d / b); }
+__device__ __forceinline__ DualD operator/(double a, DualD b) {
+  const double r = a / b.v;
+  return DualD(r, -r * b.d / b.v);
+}
+__device__ __forceinline__ DualD& operator+=(DualD& a, DualD b) { a = a + b; return a; }
+__device__ __forceinline__ DualD& operator-=(DualD& a, DualD b) { a = a - b; return a; }
+__device__ __forceinline__ bool operator<(DualD a, DualD b) { return a.v < b.v; }
+__device__ __forceinline__ bool operator>=(DualD a, DualD b) { return a.v >= b.v; }
+__device__ __forceinline__ DualD sqrt(DualD a) {
+  const double s = ::sqrt(a.v);
+  return DualD(s, a.d / (2.0 * s));
+}
+__device__ __forceinline__ DualD fabs(DualD a) { return a.v < 0.0 ? -a : a; }
+__device__ __forceinline__ DualD asin(DualD a) { return DualD(::asin(a.v), a.d / ::sqrt(1.0 - a.v * a.v)); }
+
+// primitive state of a dual conservative state (same formula as primitive<double>)
+__device__ __forceinline__ Prim<DualD> primitive_dual(const DualD U[5], const PhysDev& ph) {
+  Prim<DualD> q;
+  const DualD ir = 1.0 / U[0];
+  q.rho = U[0];
+  q.u = U[1] * ir; q.v = U[2] * ir; q.w = U[3] * ir;
+  const DualD p = ph.gm1 * (U[4] - 0.5 * (U[1] * q.u + U[2] * q.v + U[3] * q.w));
+  q.p = p - ph.p_ref;
+  q.h = (U[4] + p) * ir;
+  return q;
+}
+
+// ---------------------------------------------------------------------------
+// wall-model JVP: tau (3) with its derivative along the duals of Us and
+// (dk, dB) for the law constants.  u_tau comes from the primal solver; its
+// derivative from the implicit function theorem on F(t) = t + ln L(e^t) -
+// ln Re_h = 0, Re_h = h u_VD / nu_w.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void law_param_derivs(int law, double w, double kap, double B, double* Lk,
+                                                 double* LB) {
+  if (law == 1) {
+    const double e1 = exp(-w / 11.0), e2 = exp(-0.33 * w);
+    const double brk = 1.0 - e1 - (w / 11.0) * e2;
+    const double dC = -(1.0 - log(kap)) / (kap * kap);
+    *Lk = (w / (1.0 + kap * w)) / kap - log1p(kap * w) / (kap * kap) + dC * brk;
+    *LB = brk;
+  } else {
+    const double x = kap * w, eb = exp(-kap * B), ex = exp(x);
+    const double x3 = x * x * x / 6.0;
+    const double P = ex - 1.0 - x - 0.5 * x * x - x3 - 0.25 * x * x3;
+    const double Pp = ex - 1.0 - x - 0.5 * x * x - x3;
+    *Lk = -B * eb * P + eb * Pp * w;
+    *LB = -kap * eb * P;
+  }
+}
+
+static __device__ void wall_stress_jvp(const PhysDev& ph, const DualD Us[5], double dk, double dB, double nx,
+                                double ny, double nz, DualD tau[3], bool* ok) {
+  const DualD rho = Us[0], ir = 1.0 / rho;
+  const DualD u = Us[1] * ir, v = Us[2] * ir, w = Us[3] * ir;
+  const DualD p = ph.gm1 * (Us[4] - 0.5 * rho * (u * u + v * v + w * w));
+  const DualD T = p * ph.rcp_R * ir;
+  const DualD un = u * nx + v * ny + w * nz;
+  const DualD ux = u - un * nx, uy = v - un * ny, uz = w - un * nz;
+  const DualD u2 = ux * ux + uy * uy + uz * uz;
+  tau[0] = tau[1] = tau[2] = DualD(0.0);
+  *ok = true;
+  if (!(u2.v > 0.0)) return;
+  const DualD um = sqrt(u2);
+  const double r = cbrt(ph.Pr);
+  const DualD Tw = T + r * u2 / (2.0 * ph.cp);
+  const DualD rhow = rho * T / Tw;
+  const DualD a = sqrt(r / (2.0 * ph.cp * Tw));
+  const DualD uvd = asin(a * um) / a;
+  const DualD nuw = ph.mu / rhow;
+  const double ut = solve_utau(ph.law, uvd.v, ph.hwm, nuw.v, ph.kappa, ph.B, ok);
+  // explicit variable of the law at the solution
+  const double wv = ph.law == 1 ? ut * ph.hwm / nuw.v : uvd.v / ut;
+  double L, wdL, Lk, LB;
+  law_eval(ph.law, wv, ph.kappa, ph.B, &L, &wdL);
+  law_param_derivs(ph.law, wv, ph.kappa, ph.B, &Lk, &LB);
+  const double Ft = 1.0 + wdL / L;
+  const double dlnRe = uvd.d / uvd.v - nuw.d / nuw.v;
+  const double dt = -((Lk * dk + LB * dB) / L - dlnRe) / Ft;
+  const double dut = ph.law == 1 ? ut * (dt + nuw.d / nuw.v) : ut * (uvd.d / uvd.v - dt);
+  const DualD utD(ut, dut);
+  const DualD tw = rhow * utD * utD / um;
+  tau[0] = tw * ux; tau[1] = tw * uy; tau[2] = tw * uz;
+}
+
+// ---------------------------------------------------------------------------
+// transposed primitive recoveries
+// ---------------------------------------------------------------------------
+// Q = (rho, u, v, w, p - p_ref, h): gU += (dQ/dU)^T gQ
+__device__ __forceinline__ void prim_vjp(const double U[5], const PhysDev& ph, const double gQ[6], double gU[5]) {
+  const double ir = 1.0 / U[0];
+  const double u = U[1] * ir, v = U[2] * ir, w = U[3] * ir;
+  const double q2 = u * u + v * v + w * w;
+  const double p = ph.gm1 * (U[4] - 0.5 * U[0] * q2);
+  const double h = (U[4] + p) * ir;
+  const double g1 = ph.gm1;
+  const double gp = gQ[4], gh = gQ[5];
+  gU[0] += gQ[0] - (gQ[1] * u + gQ[2] * v + gQ[3] * w) * ir + gp * 0.5 * g1 * q2 + gh * (0.5 * g1 * q2 - h) * ir;
+  gU[1] += gQ[1] * ir - gp * g1 * u - gh * g1 * u * ir;
+  gU[2] += gQ[2] * ir - gp * g1 * v - gh * g1 * v * ir;
+  gU[3] += gQ[3] * ir - gp * g1 * w - gh * g1 * w * ir;
+  gU[4] += gp * g1 + gh * (1.0 + g1) * ir;
+}
+
+// W = (u, v, w, T): gU += (dW/dU)^T gW
+__device__ __forceinline__ void vt_vjp(const double U[5], const PhysDev& ph, const double gW[4], double gU[5]) {
+  const double ir = 1.0 / U[0];
+  const double u = U[1] * ir, v = U[2] * ir, w = U[3] * ir;
+  const double q2 = u * u + v * v + w * w;
+  const double p = ph.gm1 * (U[4] - 0.5 * U[0] * q2);
+  const double T = p * ph.rcp_R * ir;
+  const double c = ph.gm1 * ph.rcp_R * ir;  // dT/dE
+  gU[0] += -(gW[0] * u + gW[1] * v + gW[2] * w) * ir + gW[3] * (0.5 * q2 * c - T * ir);
+  gU[1] += gW[0] * ir - gW[3] * c * u;
+  gU[2] += gW[1] * ir - gW[3] * c * v;
+  gU[3] += gW[2] * ir - gW[3] * c * w;
+  gU[4] += gW[3] * c;
+}
+
+// ---------------------------------------------------------------------------
+// k_adj_face: one thread per node of an interior face.
+// ---------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(128)
+k_adj_face(const double* __restrict__ U, const double* __restrict__ lam, const MeshDev<double> m,
+           const PhysDev ph, double iw, double* __restrict__ gUf, double* __restrict__ gGf) {
+  constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int f = tid / n2, ab = tid - f * n2;
+  if (f >= m.n_interior) return;
+  const int4 fc = m.faces[f];
+  const size_t S = (size_t)m.K * n3;
+  const size_t gM = (size_t)fc.x * n3 + fnode<N>(fc.y, ab % n, ab / n);
+  const size_t gS = (size_t)fc.z * n3 + fnode<N>(fc.w, ab % n, ab / n);
+  const double jM = m.invJ[gM], jS = m.invJ[gS];
+  double gFs[5], UA[5], UB[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    // Fs enters the bracket of the master with +1/w and of the slave with -1/w;
+    // the bracket's cotangent is -lam/J
+    gFs[v] = (-lam[v * S + gM] * jM + lam[v * S + gS] * jS) * iw;
+    UA[v] = U[v * S + gM];
+    UB[v] = U[v * S + gS];
+  }
+  const size_t FN = (size_t)m.F * n2, fg = (size_t)f * n2 + ab;
+  const double nx = m.fgeo[fg], ny = m.fgeo[FN + fg], nz = m.fgeo[2 * FN + fg], s = m.fgeo[3 * FN + fg];
+  if (ph.viscous) {
+    // Fs = F* s - (Gf_M - Gf_S) / 2
+    double* dM = gGf + ((size_t)fc.x * 6 + fc.y) * 4 * n2 + ab;
+    double* dS = gGf + ((size_t)fc.z * 6 + fc.w) * 4 * n2 + ab;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) { dM[v * n2] = -0.5 * gFs[v + 1]; dS[v * n2] = 0.5 * gFs[v + 1]; }
+  }
+  double g[10];
+#pragma unroll 1
+  for (int k = 0; k < 10; ++k) {
+    DualD A[5], B[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      A[v] = DualD(UA[v], k == v ? 1.0 : 0.0);
+      B[v] = DualD(UB[v], k == v + 5 ? 1.0 : 0.0);
+    }
+    const Prim<DualD> qa = primitive_dual(A, ph), qb = primitive_dual(B, ph);
+    DualD F[5];
+    riemann<DualD, DualD>(ph, qa, A, qb, B, DualD(nx), DualD(ny), DualD(nz), F);
+    double acc = 0.0;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) acc += F[v].d * gFs[v];
+    g[k] = acc * s;
+  }
+  double* oM = gUf + ((size_t)fc.x * 6 + fc.y) * 5 * n2 + ab;
+  double* oS = gUf + ((size_t)fc.z * 6 + fc.w) * 5 * n2 + ab;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) { oM[v * n2] = g[v]; oS[v * n2] = g[v + 5]; }
+}
+
+// ---------------------------------------------------------------------------
+// k_adj_wall: one thread per node of a wall face.  Also accumulates
+// g_theta = sum_nodes (dFs/dtheta)^T gFs.
+// ---------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(128)
+k_adj_wall(const double* __restrict__ U, const double* __restrict__ lam, const MeshDev<double> m,
+           const PhysDev ph, double iw, double* __restrict__ gUf, double* __restrict__ gGf,
+           double* __restrict__ gUs, double* __restrict__ gtheta, int* __restrict__ status) {
+  constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int wf = tid / n2, ab = tid - wf * n2;
+  double gk = 0.0, gb = 0.0;
+  if (wf < m.n_wall) {
+    const int f = m.n_interior + wf;
+    const int4 fc = m.faces[f];
+    const size_t S = (size_t)m.K * n3;
+    const size_t gM = (size_t)fc.x * n3 + fnode<N>(fc.y, ab % n, ab / n);
+    const double jM = m.invJ[gM];
+    double gFs[5], UA[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      gFs[v] = -lam[v * S + gM] * jM * iw;
+      UA[v] = U[v * S + gM];
+    }
+    const size_t FN = (size_t)m.F * n2, fg = (size_t)f * n2 + ab;
+    const double nx = m.fgeo[fg], ny = m.fgeo[FN + fg], nz = m.fgeo[2 * FN + fg], s = m.fgeo[3 * FN + fg];
+    if (ph.viscous) {
+      double* dM = gGf + ((size_t)fc.x * 6 + fc.y) * 4 * n2 + ab;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) dM[v * n2] = 0.0;
+    }
+    // inviscid flux through the mirror state
+    double g[5];
+#pragma unroll 1
+    for (int k = 0; k < 5; ++k) {
+      DualD A[5], B[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) A[v] = DualD(UA[v], k == v ? 1.0 : 0.0);
+      const DualD mn = A[1] * nx + A[2] * ny + A[3] * nz;
+      B[0] = A[0]; B[1] = A[1] - 2.0 * mn * nx; B[2] = A[2] - 2.0 * mn * ny; B[3] = A[3] - 2.0 * mn * nz;
+      B[4] = A[4];
+      const Prim<DualD> qa = primitive_dual(A, ph), qb = primitive_dual(B, ph);
+      DualD F[5];
+      riemann<DualD, DualD>(ph, qa, A, qb, B, DualD(nx), DualD(ny), DualD(nz), F);
+      double acc = 0.0;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) acc += F[v].d * gFs[v];
+      g[k] = acc * s;
+    }
+    double* oM = gUf + ((size_t)fc.x * 6 + fc.y) * 5 * n2 + ab;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) oM[v * n2] = g[v];
+    // wall model: Fs_mom += tau s
+    const size_t slot = (size_t)wf * n2 + ab;
+    if (ph.viscous) {
+      const int es = m.ws_elem[slot];
+      const double* L = m.ws_lag + slot * 3 * n;
+      double Us[5] = {0, 0, 0, 0, 0};
+      for (int kk = 0; kk < n; ++kk)
+        for (int jj = 0; jj < n; ++jj) {
+          const double ljk = L[n + jj] * L[2 * n + kk];
+          double row[5] = {0, 0, 0, 0, 0};
+          for (int ii = 0; ii < n; ++ii) {
+            const size_t gs = (size_t)es * n3 + ii + n * (jj + n * kk);
+#pragma unroll
+            for (int v = 0; v < 5; ++v) row[v] += L[ii] * U[v * S + gs];
+          }
+#pragma unroll
+          for (int v = 0; v < 5; ++v) Us[v] += ljk * row[v];
+        }
+      const double gt0 = gFs[1] * s, gt1 = gFs[2] * s, gt2 = gFs[3] * s;
+      bool ok = true;
+#pragma unroll 1
+      for (int k = 0; k < 7; ++k) {
+        DualD Ud[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) Ud[v] = DualD(Us[v], k == v ? 1.0 : 0.0);
+        DualD tau[3];
+        bool okk;
+        wall_stress_jvp(ph, Ud, k == 5 ? 1.0 : 0.0, k == 6 ? 1.0 : 0.0, nx, ny, nz, tau, &okk);
+        ok = ok && okk;
+        const double gdot = tau[0].d * gt0 + tau[1].d * gt1 + tau[2].d * gt2;
+        if (k < 5) gUs[slot * 5 + k] = gdot;
+        else if (k == 5) gk = gdot;
+        else gb = gdot;
+      }
+      if (!ok) atomicOr(status, ST_WM_NOCONV);
+    } else {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) gUs[slot * 5 + v] = 0.0;
+    }
+  }
+  // block reduction of the two parameter cotangents
+  if (gtheta) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      gk += __shfl_down_sync(0xffffffffu, gk, o);
+      gb += __shfl_down_sync(0xffffffffu, gb, o);
+    }
+    if ((threadIdx.x & 31) == 0 && (gk != 0.0 || gb != 0.0)) {
+      atomicAdd(&gtheta[0], gk);
+      atomicAdd(&gtheta[1], gb);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_adj_element: one CTA per element.  Writes the element's own part of gU
+// and, for every interior face, the lifting cotangent of the neighbour's
+// face nodes (gWf[e][l]: for the node across face l).
+// ---------------------------------------------------------------------------
+template <int N>
+struct AdjShape {
+  static constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
+  static constexpr int THREADS = VolShape<N>::THREADS;
+  // doubles per node: Q 6 (reused with 6 more for H 12 after the pair
+  // phase), lam~ 5, Ja 9, W 4, gQ 6; 24 n2 face corrections; D, DVS, Dvisc
+  // tables, 1/w
+  static constexpr int SMEM_D = 36 * n3 + 24 * n2 + 3 * n2 + n;
+};
+
+template <int N>
+__global__ void __launch_bounds__(AdjShape<N>::THREADS)
+k_adj_element(const double* __restrict__ U, const double* __restrict__ lam, const MeshDev<double> m,
+              const PhysDev ph, const Tables<N> tab, const double* __restrict__ gGf, double* __restrict__ gU,
+              double* __restrict__ gWf) {
+  using Sh = AdjShape<N>;
+  constexpr int n = Sh::n, n2 = Sh::n2, n3 = Sh::n3, T = Sh::THREADS, LPW = VolShape<N>::LPW;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* sQ = reinterpret_cast<double*>(smem_raw);  // [6][n3] (pair phase)
+  double* sH = sQ;                                     // [3][4][n3] (viscous phase, reuses Q)
+  double* sL = sQ + 12 * n3;                           // [5][n3] lam~ = -lam / J
+  double* sA = sL + 5 * n3;                            // [9][n3]
+  double* sW = sA + 9 * n3;                            // [4][n3] u v w T
+  double* sGQ = sW + 4 * n3;                           // [6][n3]
+  double* sC = sGQ + 6 * n3;                           // [6][4][n2]
+  double* sD = sC + 24 * n2;                           // [n2]
+  double* sDVS = sD + n2;                              // [n2]
+  double* sDv = sDVS + n2;                             // [n2]
+  double* siw = sDv + n2;                              // [n]
+  const int e = blockIdx.x, t = threadIdx.x;
+  const size_t S = (size_t)m.K * n3;
+  for (int x = t; x < n2; x += T) {
+    sD[x] = tab.D[x];
+    sDVS[x] = 8.0 * tab.DVS8[x];
+    sDv[x] = tab.Dvisc[x];
+  }
+  if (t < n) siw[t] = tab.iw[t];
+  if (t < n3) {
+    const size_t g = (size_t)e * n3 + t;
+    double Uo[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) Uo[v] = U[v * S + g];
+    const Prim<double> q = primitive<double>(Uo[0], Uo[1], Uo[2], Uo[3], Uo[4], ph);
+    sQ[t] = q.rho; sQ[n3 + t] = q.u; sQ[2 * n3 + t] = q.v; sQ[3 * n3 + t] = q.w;
+    sQ[4 * n3 + t] = q.p; sQ[5 * n3 + t] = q.h;
+    const double iJ = m.invJ[g];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) sL[v * n3 + t] = -lam[v * S + g] * iJ;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) sA[c * n3 + t] = m.Ja[(size_t)c * S + g];
+    double uu, vv, ww, TT;
+    velocity_temperature<double>(Uo[0], Uo[1], Uo[2], Uo[3], Uo[4], ph, uu, vv, ww, TT);
+    sW[t] = uu; sW[n3 + t] = vv; sW[2 * n3 + t] = ww; sW[3 * n3 + t] = TT;
+  }
+  __syncthreads();
+  // ---- transposed split-form volume integral (symmetric pairs)
+  {
+    const int warp = t >> 5, lane = t & 31;
+    const int seg = lane / n, pos = lane - seg * n;
+    const int L0 = warp * LPW + seg;
+    const bool active = (seg < LPW) && (L0 < n2);
+    const int L = active ? L0 : 0;
+    const int base = seg * n;
+#pragma unroll 1
+    for (int dir = 0; dir < 3; ++dir) {
+      const int a = L % n, b = L / n;
+      auto node = [&](int q) {
+        return dir == 0 ? q + n * L : (dir == 1 ? a + n * q + n2 * b : L + n2 * q);
+      };
+      const int me = node(pos);
+      double g0 = 0, g1 = 0, g2 = 0, g3 = 0, g4 = 0, g5 = 0;
+#pragma unroll
+      for (int d = 1; d <= n / 2; ++d) {
+        const int pm = pos + d < n ? pos + d : pos + d - n;
+        const int q = node(pm);
+        const double rb = 0.5 * (sQ[me] + sQ[q]);
+        const double ub = 0.5 * (sQ[n3 + me] + sQ[n3 + q]), vb = 0.5 * (sQ[2 * n3 + me] + sQ[2 * n3 + q]),
+                     wb = 0.5 * (sQ[3 * n3 + me] + sQ[3 * n3 + q]);
+        const double hb = 0.5 * (sQ[5 * n3 + me] + sQ[5 * n3 + q]);
+        const double a0 = 0.5 * (sA[(dir * 3 + 0) * n3 + me] + sA[(dir * 3 + 0) * n3 + q]);
+        const double a1 = 0.5 * (sA[(dir * 3 + 1) * n3 + me] + sA[(dir * 3 + 1) * n3 + q]);
+        const double a2 = 0.5 * (sA[(dir * 3 + 2) * n3 + me] + sA[(dir * 3 + 2) * n3 + q]);
+        const double cim = sDVS[pos * n + pm], cmi = sDVS[pm * n + pos];
+        double mu[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) mu[v] = cim * sL[v * n3 + me] + cmi * sL[v * n3 + q];
+        // F0 = rb qa, Fk = rb qa uk + pb ak, F4 = rb qa hb, qa = ub.a
+        const double qa = ub * a0 + vb * a1 + wb * a2;
+        const double tt = mu[0] + mu[1] * ub + mu[2] * vb + mu[3] * wb + mu[4] * hb;
+        const double rq = rb * qa;
+        // half of the average's cotangent goes to each node
+        const double h0 = 0.5 * qa * tt;
+        const double h1 = 0.5 * (rb * tt * a0 + rq * mu[1]);
+        const double h2 = 0.5 * (rb * tt * a1 + rq * mu[2]);
+        const double h3 = 0.5 * (rb * tt * a2 + rq * mu[3]);
+        const double h4 = 0.5 * (mu[1] * a0 + mu[2] * a1 + mu[3] * a2);
+        const double h5 = 0.5 * rq * mu[4];
+        g0 += h0; g1 += h1; g2 += h2; g3 += h3; g4 += h4; g5 += h5;
+        if (2 * d != n) {
+          const int src = base + (pos - d >= 0 ? pos - d : pos - d + n);
+          g0 += __shfl_sync(0xffffffffu, h0, src);
+          g1 += __shfl_sync(0xffffffffu, h1, src);
+          g2 += __shfl_sync(0xffffffffu, h2, src);
+          g3 += __shfl_sync(0xffffffffu, h3, src);
+          g4 += __shfl_sync(0xffffffffu, h4, src);
+          g5 += __shfl_sync(0xffffffffu, h5, src);
+        }
+      }
+      if (active) {
+        if (dir == 0) {
+          sGQ[me] = g0; sGQ[n3 + me] = g1; sGQ[2 * n3 + me] = g2; sGQ[3 * n3 + me] = g3;
+          sGQ[4 * n3 + me] = g4; sGQ[5 * n3 + me] = g5;
+        } else {
+          sGQ[me] += g0; sGQ[n3 + me] += g1; sGQ[2 * n3 + me] += g2; sGQ[3 * n3 + me] += g3;
+          sGQ[4 * n3 + me] += g4; sGQ[5 * n3 + me] += g5;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // ---- viscous part: recompute the lifted gradients, then transpose
+  double gWo[4] = {0, 0, 0, 0};
+  if (ph.viscous) {
+    // W* - W at the faces (as in the forward lifting)
+    for (int x = t; x < 6 * n2; x += T) {
+      const int l = x / n2, ab = x - l * n2, a = ab % n, b = ab / n;
+      const int q = fnode<N>(l, a, b);
+      const int nb = m.nbr[e * 6 + l];
+      double d[4];
+      if (nb >= 0) {
+        const size_t gn = (size_t)nb * n3 + fnode<N>(l ^ 1, a, b);
+        double un, vn, wn, Tn;
+        velocity_temperature<double>(U[gn], U[S + gn], U[2 * S + gn], U[3 * S + gn], U[4 * S + gn], ph, un, vn,
+                                     wn, Tn);
+        d[0] = 0.5 * (un - sW[q]); d[1] = 0.5 * (vn - sW[n3 + q]); d[2] = 0.5 * (wn - sW[2 * n3 + q]);
+        d[3] = 0.5 * (Tn - sW[3 * n3 + q]);
+      } else {
+        const int dir = l >> 1;
+        const double a0 = sA[(dir * 3 + 0) * n3 + q], a1 = sA[(dir * 3 + 1) * n3 + q], a2 = sA[(dir * 3 + 2) * n3 + q];
+        const double is = 1.0 / ::sqrt(a0 * a0 + a1 * a1 + a2 * a2);
+        const double nx = a0 * is, ny = a1 * is, nz = a2 * is;
+        const double un = sW[q] * nx + sW[n3 + q] * ny + sW[2 * n3 + q] * nz;
+        d[0] = -un * nx; d[1] = -un * ny; d[2] = -un * nz; d[3] = 0.0;
+      }
+#pragma unroll
+      for (int v = 0; v < 4; ++v) sC[(l * 4 + v) * n2 + ab] = d[v];
+    }
+    __syncthreads();
+    if (t < n3) {
+      const int i = t % n, j = (t / n) % n, k = t / n2;
+      const size_t g = (size_t)e * n3 + t;
+      double ja[9];
+#pragma unroll
+      for (int c = 0; c < 9; ++c) ja[c] = sA[c * n3 + t];
+      const double iJ = m.invJ[g];
+      // forward gradients q[d][v]
+      double q[3][4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        double s0 = 0, s1 = 0, s2 = 0;
+#pragma unroll
+        for (int mm = 0; mm < n; ++mm) {
+          s0 += sD[i * n + mm] * sW[v * n3 + mm + n * (j + n * k)];
+          s1 += sD[j * n + mm] * sW[v * n3 + i + n * (mm + n * k)];
+          s2 += sD[k * n + mm] * sW[v * n3 + i + n * (j + n * mm)];
+        }
+#pragma unroll
+        for (int d = 0; d < 3; ++d) q[d][v] = ja[0 * 3 + d] * s0 + ja[1 * 3 + d] * s1 + ja[2 * 3 + d] * s2;
+      }
+      auto surf = [&](int l, int ab, double sgn_iw) {
+        const int dir = l >> 1;
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) q[d][v] += sgn_iw * ja[dir * 3 + d] * sC[(l * 4 + v) * n2 + ab];
+      };
+      if (i == 0) surf(0, j + n * k, -siw[0]);
+      if (i == N) surf(1, j + n * k, siw[N]);
+      if (j == 0) surf(2, i + n * k, -siw[0]);
+      if (j == N) surf(3, i + n * k, siw[N]);
+      if (k == 0) surf(4, i + n * j, -siw[0]);
+      if (k == N) surf(5, i + n * j, siw[N]);
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) q[d][v] *= iJ;
+      // cotangent of the contravariant viscous flux G^dir at this node:
+      // from R_v = sum_i Dvisc_i,m G_m (transposed) and from the face fluxes
+      double gG[3][4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        double s0 = 0, s1 = 0, s2 = 0;
+#pragma unroll
+        for (int ii = 0; ii < n; ++ii) {
+          s0 += sDv[ii * n + i] * sL[(v + 1) * n3 + ii + n * (j + n * k)];
+          s1 += sDv[ii * n + j] * sL[(v + 1) * n3 + i + n * (ii + n * k)];
+          s2 += sDv[ii * n + k] * sL[(v + 1) * n3 + i + n * (j + n * ii)];
+        }
+        gG[0][v] = s0; gG[1][v] = s1; gG[2][v] = s2;
+      }
+      auto gface = [&](int l, int ab, double sgn) {
+        const double* src = gGf + ((size_t)e * 6 + l) * 4 * n2 + ab;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) gG[l >> 1][v] += sgn * src[v * n2];
+      };
+      if (i == 0) gface(0, j + n * k, -1.0);
+      if (i == N) gface(1, j + n * k, 1.0);
+      if (j == 0) gface(2, i + n * k, -1.0);
+      if (j == N) gface(3, i + n * k, 1.0);
+      if (k == 0) gface(4, i + n * j, -1.0);
+      if (k == N) gface(5, i + n * j, 1.0);
+      // G^dir = sum_d Ja^dir_d Fv_d  ->  gFv_d = sum_dir Ja^dir_d gG^dir
+      double gF[3][4];
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) gF[d][v] = ja[0 * 3 + d] * gG[0][v] + ja[1 * 3 + d] * gG[1][v] + ja[2 * 3 + d] * gG[2][v];
+      // viscous flux Fv_d = (tau_0d, tau_1d, tau_2d, tau_jd u_j + k q[d][T])
+      const double mu = ph.mu, kc = ph.kcond;
+      const double div = q[0][0] + q[1][1] + q[2][2];
+      double tau[3][3];
+#pragma unroll
+      for (int aa = 0; aa < 3; ++aa)
+#pragma unroll
+        for (int bb = 0; bb < 3; ++bb) tau[aa][bb] = mu * (q[bb][aa] + q[aa][bb]) - (aa == bb ? 2.0 / 3.0 * mu * div : 0.0);
+      const double uvw[3] = {sW[t], sW[n3 + t], sW[2 * n3 + t]};
+      double gq[3][4] = {{0}};
+      double gtau[3][3];
+#pragma unroll
+      for (int jj = 0; jj < 3; ++jj)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) gtau[jj][d] = gF[d][jj] + gF[d][3] * uvw[jj];
+#pragma unroll
+      for (int jj = 0; jj < 3; ++jj) gWo[jj] += tau[jj][0] * gF[0][3] + tau[jj][1] * gF[1][3] + tau[jj][2] * gF[2][3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) gq[d][3] += kc * gF[d][3];
+      double gdiv = 0.0;
+#pragma unroll
+      for (int aa = 0; aa < 3; ++aa) {
+#pragma unroll
+        for (int bb = 0; bb < 3; ++bb) {
+          gq[bb][aa] += mu * gtau[aa][bb];
+          gq[aa][bb] += mu * gtau[aa][bb];
+        }
+        gdiv -= 2.0 / 3.0 * mu * gtau[aa][aa];
+      }
+      gq[0][0] += gdiv; gq[1][1] += gdiv; gq[2][2] += gdiv;
+      // lifting transposed: q = (1/J)(sum_dir Ja^dir dW_dir + surface)
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) gq[d][v] *= iJ;
+#pragma unroll
+      for (int dir = 0; dir < 3; ++dir)
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+          sH[(dir * 4 + v) * n3 + t] = ja[dir * 3 + 0] * gq[0][v] + ja[dir * 3 + 1] * gq[1][v] + ja[dir * 3 + 2] * gq[2][v];
+      // surface terms: (W* - W) (n s)_d / w_perp with n s = +-Ja^dir
+      auto surf_t = [&](int l, int ab, double sgn_iw) {
+        const int dir = l >> 1;
+        double tv[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+          tv[v] = sgn_iw * (ja[dir * 3 + 0] * gq[0][v] + ja[dir * 3 + 1] * gq[1][v] + ja[dir * 3 + 2] * gq[2][v]);
+        const int nb = m.nbr[e * 6 + l];
+        if (nb >= 0) {
+          // W* - W = (W_nbr - W) / 2
+#pragma unroll
+          for (int v = 0; v < 4; ++v) gWo[v] -= 0.5 * tv[v];
+          double* dst = gWf + ((size_t)e * 6 + l) * 4 * n2 + ab;
+#pragma unroll
+          for (int v = 0; v < 4; ++v) dst[v * n2] = 0.5 * tv[v];
+        } else {
+          // W* - W = -(u . n) n (mirror), T unchanged
+          const double a0 = ja[dir * 3 + 0], a1 = ja[dir * 3 + 1], a2 = ja[dir * 3 + 2];
+          const double is = 1.0 / ::sqrt(a0 * a0 + a1 * a1 + a2 * a2);
+          const double nx = a0 * is, ny = a1 * is, nz = a2 * is;
+          const double tn = tv[0] * nx + tv[1] * ny + tv[2] * nz;
+          gWo[0] -= tn * nx; gWo[1] -= tn * ny; gWo[2] -= tn * nz;
+        }
+      };
+      if (i == 0) surf_t(0, j + n * k, -siw[0]);
+      if (i == N) surf_t(1, j + n * k, siw[N]);
+      if (j == 0) surf_t(2, i + n * k, -siw[0]);
+      if (j == N) surf_t(3, i + n * k, siw[N]);
+      if (k == 0) surf_t(4, i + n * j, -siw[0]);
+      if (k == N) surf_t(5, i + n * j, siw[N]);
+    }
+    __syncthreads();
+    if (t < n3) {
+      // gW_m += sum_dir sum_i D_{i, m} H^dir_i along the lines through m
+      const int i = t % n, j = (t / n) % n, k = t / n2;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        double s = 0;
+#pragma unroll
+        for (int ii = 0; ii < n; ++ii) {
+          s += sD[ii * n + i] * sH[(0 * 4 + v) * n3 + ii + n * (j + n * k)];
+          s += sD[ii * n + j] * sH[(1 * 4 + v) * n3 + i + n * (ii + n * k)];
+          s += sD[ii * n + k] * sH[(2 * 4 + v) * n3 + i + n * (j + n * ii)];
+        }
+        gWo[v] += s;
+      }
+    }
+  }
+  if (t >= n3) return;
+  // ---- own part of gU: primitives, lifting variables and the source term
+  const size_t g = (size_t)e * n3 + t;
+  double Uo[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) Uo[v] = U[v * S + g];
+  double gQ[6];
+#pragma unroll
+  for (int v = 0; v < 6; ++v) gQ[v] = sGQ[v * n3 + t];
+  double out[5] = {0, 0, 0, 0, 0};
+  prim_vjp(Uo, ph, gQ, out);
+  if (ph.viscous) vt_vjp(Uo, ph, gWo, out);
+  if (ph.f[0] != 0.0 || ph.f[1] != 0.0 || ph.f[2] != 0.0) {
+    // S_E = f . m / rho
+    const double l4 = lam[4 * S + g], ir = 1.0 / Uo[0];
+    out[0] -= l4 * (ph.f[0] * Uo[1] + ph.f[1] * Uo[2] + ph.f[2] * Uo[3]) * ir * ir;
+    out[1] += l4 * ph.f[0] * ir; out[2] += l4 * ph.f[1] * ir; out[3] += l4 * ph.f[2] * ir;
+  }
+#pragma unroll
+  for (int v = 0; v < 5; ++v) gU[v * S + g] = out[v];
+}
+
+// ---------------------------------------------------------------------------
+// k_adj_gather: one thread per node; adds the face kernels' state cotangents
+// and the neighbours' lifting cotangents (through W(U) of this node).
+// ---------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(256)
+k_adj_gather(const double* __restrict__ U, const MeshDev<double> m, const PhysDev ph,
+             const double* __restrict__ gUf, const double* __restrict__ gWf, double* __restrict__ gU) {
+  constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
+  const size_t S = (size_t)m.K * n3;
+  const size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= S) return;
+  const int e = (int)(g / n3), t = (int)(g - (size_t)e * n3);
+  const int i = t % n, j = (t / n) % n, k = t / n2;
+  double add[5] = {0, 0, 0, 0, 0}, gW[4] = {0, 0, 0, 0};
+  bool any_w = false;
+  auto face = [&](int l, int ab) {
+    const double* src = gUf + ((size_t)e * 6 + l) * 5 * n2 + ab;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) add[v] += src[v * n2];
+    const int nb = m.nbr[e * 6 + l];
+    if (ph.viscous && nb >= 0) {
+      const double* w = gWf + ((size_t)nb * 6 + (l ^ 1)) * 4 * n2 + ab;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) gW[v] += w[v * n2];
+      any_w = true;
+    }
+  };
+  if (i == 0) face(0, j + n * k);
+  if (i == N) face(1, j + n * k);
+  if (j == 0) face(2, i + n * k);
+  if (j == N) face(3, i + n * k);
+  if (k == 0) face(4, i + n * j);
+  if (k == N) face(5, i + n * j);
+  if (any_w) {
+    double Uo[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) Uo[v] = U[v * S + g];
+    vt_vjp(Uo, ph, gW, add);
+  }
+#pragma unroll
+  for (int v = 0; v < 5; ++v) gU[v * S + g] += add[v];
+}
+
+// ---------------------------------------------------------------------------
+// k_adj_scatter: wall-model sample cotangents to the sample element's nodes.
+// ---------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(128)
+k_adj_scatter(const MeshDev<double> m, const double* __restrict__ gUs, double* __restrict__ gU) {
+  constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
+  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= m.n_wall * n2) return;
+  const size_t S = (size_t)m.K * n3;
+  const int es = m.ws_elem[slot];
+  const double* L = m.ws_lag + (size_t)slot * 3 * n;
+  double gs[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) gs[v] = gUs[(size_t)slot * 5 + v];
+  if (gs[0] == 0.0 && gs[1] == 0.0 && gs[2] == 0.0 && gs[3] == 0.0 && gs[4] == 0.0) return;
+  for (int kk = 0; kk < n; ++kk)
+    for (int jj = 0; jj < n; ++jj)
+      for (int ii = 0; ii < n; ++ii) {
+        const double wgt = L[ii] * L[n + jj] * L[2 * n + kk];
+        const size_t gn = (size_t)es * n3 + ii + n * (jj + n * kk);
+#pragma unroll
+        for (int v = 0; v < 5; ++v) atomicAdd(&gU[v * S + gn], wgt * gs[v]);
+      }
+}
+
+// ---------------------------------------------------------------------------
+// k_wall_loss: mean wall shear L = sum_slots wq tau_x / sum wq (wq: surface
+// quadrature weight w_a w_b s of the wall node), accumulated into loss[0].
+// With grad != 0 also dL/dUs per slot (into gUs, for k_adj_scatter) and
+// dL/d(kappa, B) (into gtheta).
+// ---------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(128)
+k_wall_loss(const double* __restrict__ U, const MeshDev<double> m, const PhysDev ph, const double* __restrict__ wq,
+            double inv_total, int grad, double* __restrict__ loss, double* __restrict__ gUs,
+            double* __restrict__ gtheta, int* __restrict__ status) {
+  constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
+  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+  double lv = 0.0, gk = 0.0, gb = 0.0;
+  if (slot < m.n_wall * n2) {
+    const int f = m.n_interior + slot / n2;
+    const int ab = slot % n2;
+    const size_t S = (size_t)m.K * n3;
+    const size_t FN = (size_t)m.F * n2, fg = (size_t)f * n2 + ab;
+    const double nx = m.fgeo[fg], ny = m.fgeo[FN + fg], nz = m.fgeo[2 * FN + fg];
+    const int es = m.ws_elem[slot];
+    const double* L = m.ws_lag + (size_t)slot * 3 * n;
+    double Us[5] = {0, 0, 0, 0, 0};
+    for (int kk = 0; kk < n; ++kk)
+      for (int jj = 0; jj < n; ++jj) {
+        const double ljk = L[n + jj] * L[2 * n + kk];
+        double row[5] = {0, 0, 0, 0, 0};
+        for (int ii = 0; ii < n; ++ii) {
+          const size_t gs = (size_t)es * n3 + ii + n * (jj + n * kk);
+#pragma unroll
+          for (int v = 0; v < 5; ++v) row[v] += L[ii] * U[v * S + gs];
+        }
+#pragma unroll
+        for (int v = 0; v < 5; ++v) Us[v] += ljk * row[v];
+      }
+    const double wgt = wq[slot] * inv_total;
+    bool ok = true;
+    const int seeds = grad ? 7 : 1;
+#pragma unroll 1
+    for (int k = 0; k < seeds; ++k) {
+      DualD Ud[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) Ud[v] = DualD(Us[v], grad && k == v ? 1.0 : 0.0);
+      DualD tau[3];
+      bool okk;
+      wall_stress_jvp(ph, Ud, grad && k == 5 ? 1.0 : 0.0, grad && k == 6 ? 1.0 : 0.0, nx, ny, nz, tau, &okk);
+      ok = ok && okk;
+      if (k == 0) lv = wgt * tau[0].v;
+      if (grad) {
+        if (k < 5) gUs[(size_t)slot * 5 + k] = wgt * tau[0].d;
+        else if (k == 5) gk = wgt * tau[0].d;
+        else gb = wgt * tau[0].d;
+      }
+    }
+    if (!ok) atomicOr(status, ST_WM_NOCONV);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lv += __shfl_down_sync(0xffffffffu, lv, o);
+    gk += __shfl_down_sync(0xffffffffu, gk, o);
+    gb += __shfl_down_sync(0xffffffffu, gb, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(loss, lv);
+    if (grad && gtheta) { atomicAdd(&gtheta[0], gk); atomicAdd(&gtheta[1], gb); }
+  }
+}
+
+// y = a x + b y over n doubles
+static __global__ void k_axpby(long long n, double a, const double* __restrict__ x, double b, double* __restrict__ y) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = (b == 0.0 ? 0.0 : b * y[i]) + a * x[i];
+}
+
+}  // namespace dg

@@ -1,6 +1,7 @@
 // api.cu -- C ABI of the GB300 DGSEM library (declared in include/dg.h).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -51,6 +52,21 @@ struct dg_ctx {
   int* status = nullptr;
   bool state_set = false;
   std::string err;
+  // wall-node surface quadrature weights w_a w_b s and their sum
+  double* wq = nullptr;
+  double wq_total = 0.0;
+  // rollout buffers (allocated on the first dg_rollout_vjp, grown on demand)
+  double* ro_ckpt = nullptr;
+  int ro_cap = 0;
+  double* ro_stage = nullptr;  // 5 stage inputs
+  double* ro_work = nullptr;   // Uw, dUw, gA, gD, gT, lam
+  double* ro_scalar = nullptr; // loss
+  // adjoint scratch (allocated on the first dg_vjp)
+  double* gUf = nullptr;
+  double* gGf = nullptr;
+  double* gWf = nullptr;
+  double* gUs = nullptr;
+  double* gtheta = nullptr;
   // optional per-kernel timing: 5 events per operator evaluation
   bool profiling = false;
   std::vector<cudaEvent_t> events;
@@ -81,13 +97,15 @@ void free_all(dg_ctx* c) {
   for (cudaEvent_t ev : c->events) cudaEventDestroy(ev);
   c->events.clear();
   void* ptrs[] = {c->U, c->dU, c->io, c->io2, c->Ja, c->invJ, c->fgeo, c->nbr, c->elem_face, c->faces,
-                  c->ws_elem, c->ws_lag, c->Rv, c->Gf, c->Fs, c->tau, c->status};
+                  c->ws_elem, c->ws_lag, c->Rv, c->Gf, c->Fs, c->tau, c->status,
+                  c->gUf, c->gGf, c->gWf, c->gUs, c->gtheta, c->wq, c->ro_ckpt, c->ro_stage, c->ro_work,
+                  c->ro_scalar};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
 
 int launch(dg_ctx* c, const double* Uin, int mode, double* Out, double A, double B, double dt, int read_dU,
-           double* Uout) {
+           double* Uout, double* dU = nullptr) {
   dg::OpArgs a{};
   a.N = c->N; a.K = c->K; a.F = c->F; a.n_interior = c->geo.n_interior; a.n_wall = c->geo.n_wall;
   a.fp32 = c->opts.precision == DG_FP32_MIXED;
@@ -95,7 +113,7 @@ int launch(dg_ctx* c, const double* Uin, int mode, double* Out, double A, double
   a.faces = c->faces; a.ws_elem = c->ws_elem; a.ws_lag = c->ws_lag;
   a.D = c->geo.basis.D.data(); a.w = c->geo.basis.w.data();
   a.Uin = Uin; a.Rv = c->Rv; a.Gf = c->Gf; a.Fs = c->Fs; a.tau = c->tau; a.status = c->status;
-  a.mode = mode; a.Out = Out; a.dU = c->dU; a.Uout = Uout;
+  a.mode = mode; a.Out = Out; a.dU = dU ? dU : c->dU; a.Uout = Uout;
   a.A = A; a.B = B; a.dt = dt; a.read_dU = read_dU;
   a.ev = nullptr;
   if (c->profiling) {
@@ -128,6 +146,41 @@ int run_operator(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {
     case 6: return run_operator_n6(a, ph, s);
     case 7: return run_operator_n7(a, ph, s);
     case 8: return run_operator_n8(a, ph, s);
+    default: return (int)cudaErrorInvalidValue;
+  }
+}
+__global__ void k_axpby_api(long long n, double a, const double* __restrict__ x, double b, double* __restrict__ y) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = (b == 0.0 ? 0.0 : b * y[i]) + (a == 0.0 ? 0.0 : a * x[i]);
+}
+int run_axpby(long long n, double a, const double* x, double b, double* y, cudaStream_t s) {
+  k_axpby_api<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, a, x, b, y);
+  return (int)cudaGetLastError();
+}
+int run_wall_loss(const OpArgs& a, const PhysDev& ph, const double* wq, double inv_total, int grad, double* loss,
+                  cudaStream_t s) {
+  switch (a.N) {
+    case 1: return run_wall_loss_n1(a, ph, wq, inv_total, grad, loss, s);
+    case 2: return run_wall_loss_n2(a, ph, wq, inv_total, grad, loss, s);
+    case 3: return run_wall_loss_n3(a, ph, wq, inv_total, grad, loss, s);
+    case 4: return run_wall_loss_n4(a, ph, wq, inv_total, grad, loss, s);
+    case 5: return run_wall_loss_n5(a, ph, wq, inv_total, grad, loss, s);
+    case 6: return run_wall_loss_n6(a, ph, wq, inv_total, grad, loss, s);
+    case 7: return run_wall_loss_n7(a, ph, wq, inv_total, grad, loss, s);
+    case 8: return run_wall_loss_n8(a, ph, wq, inv_total, grad, loss, s);
+    default: return (int)cudaErrorInvalidValue;
+  }
+}
+int run_vjp(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {
+  switch (a.N) {
+    case 1: return run_vjp_n1(a, ph, s);
+    case 2: return run_vjp_n2(a, ph, s);
+    case 3: return run_vjp_n3(a, ph, s);
+    case 4: return run_vjp_n4(a, ph, s);
+    case 5: return run_vjp_n5(a, ph, s);
+    case 6: return run_vjp_n6(a, ph, s);
+    case 7: return run_vjp_n7(a, ph, s);
+    case 8: return run_vjp_n8(a, ph, s);
     default: return (int)cudaErrorInvalidValue;
   }
 }
@@ -258,6 +311,20 @@ int dg_init_mesh(dg_ctx** out, const dg_mesh_desc* m, const dg_phys* p, const dg
     chk(cudaMemcpy(c->ws_elem, c->geo.ws_elem.data(), c->geo.ws_elem.size() * sizeof(int), cudaMemcpyHostToDevice));
     chk(cudaMemcpy(c->ws_lag, c->geo.ws_lag.data(), c->geo.ws_lag.size() * sizeof(double), cudaMemcpyHostToDevice));
   }
+  if (c->geo.n_wall) {
+    // surface quadrature weight of every wall node (mean wall shear)
+    std::vector<double> wq((size_t)c->geo.n_wall * n2);
+    const size_t FN = (size_t)c->F * n2;
+    for (int wf = 0; wf < c->geo.n_wall; ++wf)
+      for (size_t ab = 0; ab < n2; ++ab) {
+        const size_t f = (size_t)(c->geo.n_interior + wf);
+        const double sface = c->geo.fgeo[3 * FN + f * n2 + ab];
+        wq[wf * n2 + ab] = c->geo.basis.w[ab % c->n] * c->geo.basis.w[ab / c->n] * sface;
+        c->wq_total += wq[wf * n2 + ab];
+      }
+    chk(alloc(&c->wq, wq.size()));
+    chk(cudaMemcpy(c->wq, wq.data(), wq.size() * sizeof(double), cudaMemcpyHostToDevice));
+  }
   chk(cudaMemset(c->status, 0, sizeof(int)));
   chk(cudaMemset(c->dU, 0, 5 * S * sizeof(double)));
   if (e != cudaSuccess) { free_all(c); delete c; return cuda_fail(nullptr, e, "dg_init_mesh: upload"); }
@@ -350,6 +417,158 @@ int dg_rk_steps(dg_ctx* c, double t, double dt, int nsteps) {
       int rc = dg_rk_stage(c, s, t + (it + kRkC[s]) * dt, dt);
       if (rc != DG_OK) return rc;
     }
+  return DG_OK;
+}
+
+int dg_set_params(dg_ctx* c, double kappa, double B) {
+  if (!c) return DG_ERR_ARG;
+  if (!(kappa > 0.0)) return fail(c, DG_ERR_ARG, "dg_set_params: kappa must be positive");
+  c->phys.kappa = kappa; c->phys.B = B;
+  c->ph.kappa = kappa; c->ph.B = B;
+  return DG_OK;
+}
+
+static int ensure_adjoint_scratch(dg_ctx* c) {
+  if (c->gUf) return DG_OK;
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+  const size_t kn2 = (size_t)c->K * 6 * c->n2;
+  chk(alloc(&c->gUf, 5 * kn2));
+  chk(alloc(&c->gGf, 4 * kn2));
+  chk(alloc(&c->gWf, 4 * kn2));
+  chk(alloc(&c->gUs, (size_t)c->geo.n_wall * c->n2 * 5 + 1));
+  chk(alloc(&c->gtheta, 2));
+  chk(alloc(&c->ro_scalar, 1));
+  if (e != cudaSuccess) return cuda_fail(c, e, "adjoint scratch allocation");
+  return DG_OK;
+}
+
+static dg::OpArgs adjoint_args(dg_ctx* c, const double* U, const double* lam, double* gU, double* gth) {
+  dg::OpArgs a{};
+  a.N = c->N; a.K = c->K; a.F = c->F; a.n_interior = c->geo.n_interior; a.n_wall = c->geo.n_wall;
+  a.Ja = c->Ja; a.invJ = c->invJ; a.fgeo = c->fgeo; a.nbr = c->nbr; a.elem_face = c->elem_face;
+  a.faces = c->faces; a.ws_elem = c->ws_elem; a.ws_lag = c->ws_lag;
+  a.D = c->geo.basis.D.data(); a.w = c->geo.basis.w.data();
+  a.Uin = U; a.status = c->status;
+  a.lam = lam; a.gU = gU; a.gUf = c->gUf; a.gGf = c->gGf; a.gWf = c->gWf; a.gUs = c->gUs; a.gtheta = gth;
+  return a;
+}
+
+static int check_adjoint_options(dg_ctx* c, const char* who) {
+  if (c->opts.precision != DG_FP64)
+    return fail(c, DG_ERR_NOT_IMPLEMENTED, std::string(who) + ": the adjoint is available for FP64 contexts");
+  if (c->opts.vol_flux != DG_VOL_KEP_PIROZZOLI)
+    return fail(c, DG_ERR_NOT_IMPLEMENTED, std::string(who) + ": the adjoint needs the Pirozzoli volume flux");
+  return DG_OK;
+}
+
+int dg_wall_shear(dg_ctx* c, const double* U, double* loss) {
+  if (!c || !loss) return c ? fail(c, DG_ERR_ARG, "dg_wall_shear: null loss") : DG_ERR_ARG;
+  if (c->geo.n_wall == 0 || !c->opts.viscous) return fail(c, DG_ERR_ARG, "dg_wall_shear: no wall-modelled walls");
+  const double* Uin = U ? U : c->U;
+  if (!U && !c->state_set) return fail(c, DG_ERR_NOT_INIT, "dg_wall_shear: state not set");
+  int rc = ensure_adjoint_scratch(c);
+  if (rc != DG_OK) return rc;
+  cudaError_t e = cudaMemsetAsync(c->ro_scalar, 0, sizeof(double), c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "dg_wall_shear");
+  dg::OpArgs a = adjoint_args(c, Uin, nullptr, nullptr, nullptr);
+  rc = dg::run_wall_loss(a, c->ph, c->wq, 1.0 / c->wq_total, 0, c->ro_scalar, c->stream);
+  if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "dg_wall_shear launch");
+  e = cudaMemcpyAsync(loss, c->ro_scalar, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "dg_wall_shear");
+  return DG_OK;
+}
+
+int dg_rollout_vjp(dg_ctx* c, const double* U0, int nsteps, double dt, double* loss, double* gU0, double* gtheta) {
+  if (!c) return DG_ERR_ARG;
+  if (!U0 || !loss || !gU0 || nsteps < 0) return fail(c, DG_ERR_ARG, "dg_rollout_vjp: bad argument");
+  int rc = check_adjoint_options(c, "dg_rollout_vjp");
+  if (rc != DG_OK) return rc;
+  if (c->geo.n_wall == 0 || !c->opts.viscous)
+    return fail(c, DG_ERR_ARG, "dg_rollout_vjp: the loss needs wall-modelled walls");
+  rc = ensure_adjoint_scratch(c);
+  if (rc != DG_OK) return rc;
+  const size_t S5 = 5 * c->S, bytes = S5 * sizeof(double);
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+  if (nsteps > c->ro_cap || !c->ro_ckpt) {
+    if (c->ro_ckpt) cudaFree(c->ro_ckpt);
+    c->ro_ckpt = nullptr;
+    chk(alloc(&c->ro_ckpt, S5 * (size_t)std::max(nsteps, 1)));
+    c->ro_cap = std::max(nsteps, 1);
+  }
+  if (!c->ro_stage) chk(alloc(&c->ro_stage, 5 * S5));
+  if (!c->ro_work) chk(alloc(&c->ro_work, 6 * S5));
+  if (e != cudaSuccess) return cuda_fail(c, e, "dg_rollout_vjp: buffers");
+  double *Uw = c->ro_work, *dUw = Uw + S5, *gA = dUw + S5, *gD = gA + S5, *gT = gD + S5, *lamS = gT + S5;
+  double* gth = gtheta ? gtheta : c->gtheta;
+  cudaStream_t st = c->stream;
+  chk(cudaMemsetAsync(gth, 0, 2 * sizeof(double), st));
+  chk(cudaMemsetAsync(c->ro_scalar, 0, sizeof(double), st));
+  chk(cudaMemcpyAsync(Uw, U0, bytes, cudaMemcpyDeviceToDevice, st));
+  if (e != cudaSuccess) return cuda_fail(c, e, "dg_rollout_vjp");
+  // forward, one checkpoint per step (A_0 = 0: U alone restarts a step)
+  for (int k = 0; k < nsteps; ++k) {
+    chk(cudaMemcpyAsync(c->ro_ckpt + (size_t)k * S5, Uw, bytes, cudaMemcpyDeviceToDevice, st));
+    for (int s = 0; s < 5; ++s) {
+      rc = launch(c, Uw, 1, nullptr, kRkA[s], kRkB[s], dt, s > 0, Uw, dUw);
+      if (rc != DG_OK) return rc;
+    }
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "dg_rollout_vjp: forward");
+  // loss at the final state and its gradient
+  dg::OpArgs la = adjoint_args(c, Uw, nullptr, gA, gth);
+  rc = dg::run_wall_loss(la, c->ph, c->wq, 1.0 / c->wq_total, 1, c->ro_scalar, st);
+  if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "dg_rollout_vjp: loss");
+  // reverse sweep through the 2N-storage recurrence
+  for (int k = nsteps - 1; k >= 0; --k) {
+    chk(cudaMemcpyAsync(Uw, c->ro_ckpt + (size_t)k * S5, bytes, cudaMemcpyDeviceToDevice, st));
+    for (int s = 0; s < 5; ++s) {
+      chk(cudaMemcpyAsync(c->ro_stage + (size_t)s * S5, Uw, bytes, cudaMemcpyDeviceToDevice, st));
+      if (s < 4) {
+        rc = launch(c, Uw, 1, nullptr, kRkA[s], kRkB[s], dt, s > 0, Uw, dUw);
+        if (rc != DG_OK) return rc;
+      }
+    }
+    chk(cudaMemsetAsync(gD, 0, bytes, st));
+    for (int s = 4; s >= 0; --s) {
+      // gD += B_s gA;  lam = dt gD;  gA += J^T lam (and gtheta);  gD = A_s gD
+      rc = dg::run_axpby((long long)S5, kRkB[s], gA, 1.0, gD, st);
+      if (rc == 0) rc = dg::run_axpby((long long)S5, dt, gD, 0.0, lamS, st);
+      if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "dg_rollout_vjp: axpby");
+      dg::OpArgs va = adjoint_args(c, c->ro_stage + (size_t)s * S5, lamS, gT, gth);
+      rc = dg::run_vjp(va, c->ph, st);
+      if (rc == 0) rc = dg::run_axpby((long long)S5, 1.0, gT, 1.0, gA, st);
+      if (rc == 0) rc = dg::run_axpby((long long)S5, 0.0, gD, kRkA[s], gD, st);
+      if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "dg_rollout_vjp: reverse");
+    }
+  }
+  chk(cudaMemcpyAsync(gU0, gA, bytes, cudaMemcpyDeviceToDevice, st));
+  chk(cudaMemcpyAsync(loss, c->ro_scalar, sizeof(double), cudaMemcpyDeviceToHost, st));
+  chk(cudaStreamSynchronize(st));
+  if (e != cudaSuccess) return cuda_fail(c, e, "dg_rollout_vjp");
+  return DG_OK;
+}
+
+int dg_vjp(dg_ctx* c, const double* U, const double* lam, double* gU, double* gtheta) {
+  if (!c) return DG_ERR_ARG;
+  if (!lam || !gU) return fail(c, DG_ERR_ARG, "dg_vjp: null lam or gU");
+  int rc = check_adjoint_options(c, "dg_vjp");
+  if (rc != DG_OK) return rc;
+  const double* Uin = U;
+  if (!Uin) {
+    if (!c->state_set) return fail(c, DG_ERR_NOT_INIT, "dg_vjp: state not set");
+    Uin = c->U;
+  }
+  rc = ensure_adjoint_scratch(c);
+  if (rc != DG_OK) return rc;
+  double* gth = gtheta ? gtheta : c->gtheta;
+  cudaError_t e = cudaMemsetAsync(gth, 0, 2 * sizeof(double), c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "dg_vjp");
+  dg::OpArgs a = adjoint_args(c, Uin, lam, gU, gth);
+  rc = dg::run_vjp(a, c->ph, c->stream);
+  if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "dg_vjp launch");
   return DG_OK;
 }
 

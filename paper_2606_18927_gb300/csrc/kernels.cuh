@@ -154,9 +154,9 @@ __device__ __forceinline__ void twopoint(int kind, const Prim<R>& A, const Prim<
 }
 
 // Numerical inviscid flux along the unit normal (nx, ny, nz), side A = master.
-template <typename R>
-__device__ __forceinline__ void riemann(const PhysDev& ph, const Prim<R>& A, const double UA[5],
-                                        const Prim<R>& B, const double UB[5], R nx, R ny, R nz, R F[5]) {
+template <typename R, typename S>
+__device__ __forceinline__ void riemann(const PhysDev& ph, const Prim<R>& A, const S UA[5],
+                                        const Prim<R>& B, const S UB[5], R nx, R ny, R nz, R F[5]) {
   const R pref = (R)ph.p_ref;
   twopoint<R>(ph.vol_flux, A, B, nx, ny, nz, F, pref);
   const R g = (R)ph.gamma;
@@ -468,7 +468,7 @@ k_face(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
   const size_t FN = (size_t)m.F * n2, fg = (size_t)f * n2 + ab;
   const R nx = (R)m.fgeo[fg], ny = (R)m.fgeo[FN + fg], nz = (R)m.fgeo[2 * FN + fg], s = (R)m.fgeo[3 * FN + fg];
   R F[5];
-  riemann<R>(ph, A, UA, B, UB, nx, ny, nz, F);
+  riemann<R, double>(ph, A, UA, B, UB, nx, ny, nz, F);
   R* out = Fs + (size_t)f * 5 * n2 + ab;
   out[0] = F[0] * s;
   if (ph.viscous) {
@@ -508,7 +508,7 @@ k_wall(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, R* __
   const Prim<R> A = primitive<R>(UA[0], UA[1], UA[2], UA[3], UA[4], ph);
   const Prim<R> B = primitive<R>(UB[0], UB[1], UB[2], UB[3], UB[4], ph);
   R F[5];
-  riemann<R>(ph, A, UA, B, UB, (R)nxd, (R)nyd, (R)nzd, F);
+  riemann<R, double>(ph, A, UA, B, UB, (R)nxd, (R)nyd, (R)nzd, F);
   double tau[3] = {0.0, 0.0, 0.0};
   if (ph.viscous) {
     // sample state at h_wm: tensor-product Lagrange interpolation of U

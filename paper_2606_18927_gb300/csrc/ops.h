@@ -33,12 +33,34 @@ struct OpArgs {
   double A, B, dt;
   int read_dU;
   cudaEvent_t* ev;          // null, or 5 events recorded around lift, face, wall, volume
+  // adjoint (FP64): cotangent lam of Ut, output gU, and scratch
+  const double* lam;
+  double* gU;
+  double* gUf;              // [K][6][5][n2] face-kernel state cotangents
+  double* gGf;              // [K][6][4][n2] cotangents of the own face viscous fluxes
+  double* gWf;              // [K][6][4][n2] lifting cotangents for the neighbour's face nodes
+  double* gUs;              // [n_wall n2][5] wall-model sample cotangents
+  double* gtheta;           // [2] (kappa, B), accumulated
 };
+
+// Vector-Jacobian product (FP64 contexts): gU = (dUt/dU)^T lam, gtheta += ...
+int run_vjp(const OpArgs& a, const PhysDev& ph, cudaStream_t s);
+
+// Mean wall shear of U (accumulated into loss[0]); with grad also gU
+// (= dL/dU, overwritten) and gtheta (accumulated).  Uses a.Uin, a.gU, a.gUs,
+// a.gtheta, a.status.
+int run_wall_loss(const OpArgs& a, const PhysDev& ph, const double* wq, double inv_total, int grad,
+                  double* loss, cudaStream_t s);
+// y = a x + b y
+int run_axpby(long long n, double a, const double* x, double b, double* y, cudaStream_t s);
 
 // Launches lift (if viscous), face, wall and volume kernels on the stream.
 int run_operator(const OpArgs& a, const PhysDev& ph, cudaStream_t s);
 
-#define DG_DECLARE_N(NN) int run_operator_n##NN(const OpArgs& a, const PhysDev& ph, cudaStream_t s);
+#define DG_DECLARE_N(NN) int run_operator_n##NN(const OpArgs& a, const PhysDev& ph, cudaStream_t s); \
+  int run_vjp_n##NN(const OpArgs& a, const PhysDev& ph, cudaStream_t s);                           \
+  int run_wall_loss_n##NN(const OpArgs& a, const PhysDev& ph, const double* wq, double inv_total, int grad, \
+                          double* loss, cudaStream_t s);
 DG_DECLARE_N(1)
 DG_DECLARE_N(2)
 DG_DECLARE_N(3)

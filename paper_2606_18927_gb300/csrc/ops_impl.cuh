@@ -1,6 +1,7 @@
 // ops_impl.cuh -- host launch code for one polynomial degree (included by
 // op_n<N>.cu with DG_N defined).
 #pragma once
+#include "adjoint.cuh"
 #include "kernels.cuh"
 #include "ops.h"
 
@@ -67,11 +68,70 @@ static int run_typed(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {
   return (int)cudaGetLastError();
 }
 
+template <int N>
+static int run_vjp_typed(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {
+  constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
+  MeshDev<double> m;
+  m.K = a.K; m.F = a.F; m.n_interior = a.n_interior; m.n_wall = a.n_wall;
+  m.Ja = static_cast<const double*>(a.Ja); m.invJ = static_cast<const double*>(a.invJ);
+  m.fgeo = a.fgeo; m.nbr = a.nbr; m.elem_face = a.elem_face; m.faces = a.faces;
+  m.ws_elem = a.ws_elem; m.ws_lag = a.ws_lag;
+  const Tables<N> tab = make_tables<N>(a.D, a.w);
+  const double iw = tab.iw[0];
+  const size_t smem = (size_t)AdjShape<N>::SMEM_D * sizeof(double);
+  cudaFuncSetAttribute(k_adj_element<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (a.n_interior > 0) {
+    const long long work = (long long)a.n_interior * n2;
+    k_adj_face<N><<<(unsigned)((work + 127) / 128), 128, 0, s>>>(a.Uin, a.lam, m, ph, iw, a.gUf, a.gGf);
+  }
+  if (a.n_wall > 0) {
+    const long long work = (long long)a.n_wall * n2;
+    k_adj_wall<N><<<(unsigned)((work + 127) / 128), 128, 0, s>>>(a.Uin, a.lam, m, ph, iw, a.gUf, a.gGf, a.gUs,
+                                                                 a.gtheta, a.status);
+  }
+  k_adj_element<N><<<a.K, AdjShape<N>::THREADS, smem, s>>>(a.Uin, a.lam, m, ph, tab, a.gGf, a.gU, a.gWf);
+  const long long S = (long long)a.K * n3;
+  k_adj_gather<N><<<(unsigned)((S + 255) / 256), 256, 0, s>>>(a.Uin, m, ph, a.gUf, a.gWf, a.gU);
+  if (a.n_wall > 0 && ph.viscous) {
+    const long long work = (long long)a.n_wall * n2;
+    k_adj_scatter<N><<<(unsigned)((work + 127) / 128), 128, 0, s>>>(m, a.gUs, a.gU);
+  }
+  return (int)cudaGetLastError();
+}
+
+template <int N>
+static int run_wall_loss_typed(const OpArgs& a, const PhysDev& ph, const double* wq, double inv_total, int grad,
+                               double* loss, cudaStream_t s) {
+  constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
+  MeshDev<double> m;
+  m.K = a.K; m.F = a.F; m.n_interior = a.n_interior; m.n_wall = a.n_wall;
+  m.Ja = static_cast<const double*>(a.Ja); m.invJ = static_cast<const double*>(a.invJ);
+  m.fgeo = a.fgeo; m.nbr = a.nbr; m.elem_face = a.elem_face; m.faces = a.faces;
+  m.ws_elem = a.ws_elem; m.ws_lag = a.ws_lag;
+  if (a.n_wall == 0) return 0;
+  const long long work = (long long)a.n_wall * n2;
+  k_wall_loss<N><<<(unsigned)((work + 127) / 128), 128, 0, s>>>(a.Uin, m, ph, wq, inv_total, grad, loss, a.gUs,
+                                                                a.gtheta, a.status);
+  if (grad) {
+    const long long S = 5LL * a.K * n3;
+    k_axpby<<<(unsigned)((S + 255) / 256), 256, 0, s>>>(S, 0.0, a.gU, 0.0, a.gU);
+    k_adj_scatter<N><<<(unsigned)((work + 127) / 128), 128, 0, s>>>(m, a.gUs, a.gU);
+  }
+  return (int)cudaGetLastError();
+}
+
 }  // namespace dg
 
 #define DG_DEFINE_N(NN)                                                              \
   namespace dg {                                                                     \
   int run_operator_n##NN(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {      \
     return a.fp32 ? run_typed<NN, float>(a, ph, s) : run_typed<NN, double>(a, ph, s); \
+  }                                                                                  \
+  int run_vjp_n##NN(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {           \
+    return run_vjp_typed<NN>(a, ph, s);                                              \
+  }                                                                                  \
+  int run_wall_loss_n##NN(const OpArgs& a, const PhysDev& ph, const double* wq, double inv_total, int grad, \
+                          double* loss, cudaStream_t s) {                            \
+    return run_wall_loss_typed<NN>(a, ph, wq, inv_total, grad, loss, s);             \
   }                                                                                  \
   }

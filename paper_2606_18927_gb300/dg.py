@@ -86,6 +86,10 @@ def lib():
         "dg_set_rk_register": (c_int, [vp, vp, c_int]),
         "dg_get_metrics": (c_int, [vp, dp, dp]),
         "dg_time_derivative_noalloc": (c_int, [vp, vp, vp]),
+        "dg_vjp": (c_int, [vp, vp, vp, vp, vp]),
+        "dg_set_params": (c_int, [vp, c_double, c_double]),
+        "dg_wall_shear": (c_int, [vp, vp, dp]),
+        "dg_rollout_vjp": (c_int, [vp, vp, c_int, c_double, dp, vp, vp]),
         "dg_profile_enable": (c_int, [vp, c_int]),
         "dg_profile_read": (c_int, [vp, dp, ip]),
     }
@@ -218,6 +222,35 @@ class Operator:
         self._check(lib().dg_time_derivative(self.h, pu, po, float(t), dev))
         return Ut
 
+    def vjp(self, lam, gU, U=None, gtheta=None):
+        """gU <- (dUt/dU)^T lam; gtheta (device tensor of 2) <- (dUt/d(kappa, B))^T lam."""
+        for a in (lam, gU, U):
+            if a is not None and a.numel() != self.numel:
+                raise ValueError("array has the wrong size for this mesh")
+        pl, _ = _ptr(lam)
+        pg, _ = _ptr(gU)
+        pu = _ptr(U)[0] if U is not None else None
+        pt = _ptr(gtheta)[0] if gtheta is not None else None
+        self._check(lib().dg_vjp(self.h, pu, pl, pg, pt))
+        return gU
+
+    def set_params(self, kappa, B):
+        self._check(lib().dg_set_params(self.h, float(kappa), float(B)))
+
+    def wall_shear(self, U=None):
+        out = ctypes.c_double(0.0)
+        pu = _ptr(U)[0] if U is not None else None
+        self._check(lib().dg_wall_shear(self.h, pu, ctypes.byref(out)))
+        return out.value
+
+    def rollout_vjp(self, U0, nsteps, dt, gU0, gtheta=None):
+        """Loss (mean wall shear after nsteps steps) and its gradients, see dg.h."""
+        out = ctypes.c_double(0.0)
+        pt = _ptr(gtheta)[0] if gtheta is not None else None
+        self._check(lib().dg_rollout_vjp(self.h, _ptr(U0)[0], int(nsteps), float(dt), ctypes.byref(out),
+                                         _ptr(gU0)[0], pt))
+        return out.value
+
     def rk_stage(self, s, t, dt):
         self._check(lib().dg_rk_stage(self.h, int(s), float(t), float(dt)))
 
@@ -242,3 +275,60 @@ class Operator:
         self._check(lib().dg_get_metrics(self.h, Ja.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                          J.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
         return Ja, J
+
+
+# ---------------------------------------------------------------------------
+# torch.autograd bindings (the backward passes call the library's adjoint)
+# ---------------------------------------------------------------------------
+def _autograd():
+    import torch
+
+    class DGOperatorFunction(torch.autograd.Function):
+        """Ut = DG_Operator(U) with its hand-written VJP as backward."""
+
+        @staticmethod
+        def forward(ctx, U, op):
+            Ut = torch.empty_like(U)
+            op.time_derivative(Ut, U.contiguous())
+            ctx.save_for_backward(U)
+            ctx.op = op
+            return Ut
+
+        @staticmethod
+        def backward(ctx, g):
+            (U,) = ctx.saved_tensors
+            gU = torch.empty_like(U)
+            ctx.op.vjp(g.contiguous(), gU, U.contiguous())
+            return gU, None
+
+    class WallShearRollout(torch.autograd.Function):
+        """Mean wall shear after nsteps LSERK4 steps from U0, differentiable in
+        U0 and theta = (kappa, B); the gradients come from dg_rollout_vjp
+        (per-step checkpoints, reverse sweep) computed during forward."""
+
+        @staticmethod
+        def forward(ctx, U0, theta, op, nsteps, dt):
+            th = theta.detach().double().cpu()
+            op.set_params(float(th[0]), float(th[1]))
+            gU0 = torch.empty_like(U0)
+            gth = torch.zeros(2, dtype=torch.float64, device=U0.device)
+            loss = op.rollout_vjp(U0.contiguous(), nsteps, dt, gU0, gth)
+            ctx.save_for_backward(gU0, gth.to(theta.device, theta.dtype))
+            return torch.tensor(loss, dtype=torch.float64, device=U0.device)
+
+        @staticmethod
+        def backward(ctx, g):
+            gU0, gth = ctx.saved_tensors
+            return g * gU0, g * gth, None, None, None
+
+    return DGOperatorFunction, WallShearRollout
+
+
+def dg_operator(U, op):
+    """Differentiable Ut = DG_Operator(U) for torch CUDA float64 tensors."""
+    return _autograd()[0].apply(U, op)
+
+
+def wall_shear_rollout(U0, theta, op, nsteps, dt):
+    """Differentiable mean wall shear after nsteps LSERK4 steps."""
+    return _autograd()[1].apply(U0, theta, op, nsteps, dt)
