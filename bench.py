@@ -35,6 +35,11 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP64 pipe of a GB300 SM: 2 DFMA per clock per SM (1 instruction/clock per
 # 16 lanes); 152 SMs at the 2070 MHz maximum clock: 152 * 2 * 2 * 2.07e9.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# DRAM bytes (read + write) of one launch of the dominant kernel, from an ncu
+# capture of the same kernel build on a 16^3-element case, scaled to the
+# launch size by the DOF count (traffic is proportional to the DOF count);
+# see profiles/k_volume_n7_16cubed_fp64.md.
+NCU_TRAFFIC_PER_DOF = {("k_volume", "fp64", 7): 486.6e6 / 2097152}
 
 
 def algorithmic_flops_per_dof(N, kernel, viscous=True, surf="roe"):
@@ -183,6 +188,55 @@ def run_reference(args):
     return 0
 
 
+def measure_variants(args, wl, X, nbr, U, op64, stream, dt):
+    """FP32-mixed form on the same workload (throughput and its Ut error
+    against the FP64 path), and the time of one FP64 VJP."""
+    import torch
+    from paper_2606_18927_gb300 import dg
+    out = {}
+    Ud = torch.from_numpy(U).cuda()
+    ref = torch.empty_like(Ud)
+    op64.time_derivative(ref, Ud)
+    # VJP of the operator (FP64, hand-written adjoint)
+    lam = torch.ones_like(Ud)
+    gU = torch.empty_like(Ud)
+    op64.vjp(lam, gU, Ud)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(3):
+        op64.vjp(lam, gU, Ud)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    out["vjp_fp64"] = {"ms_per_call": e0.elapsed_time(e1) / 3}
+    # FP32-mixed form
+    opm = dg.Operator(wl.spec.N, X, nbr, wl.phys, precision=dg.FP32_MIXED, vol_flux=wl.vol_flux,
+                      surf_flux=wl.surf_flux, viscous=wl.viscous, law=wl.law, stream=stream)
+    utm = torch.empty_like(Ud)
+    opm.time_derivative(utm, Ud)
+    a = utm.view(5, -1); b = ref.view(5, -1)
+    rel = [float(torch.linalg.norm(a[v] - b[v]) / torch.linalg.norm(b[v])) for v in range(5)]
+    rel_all = float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+    opm.set_state(Ud)
+    for s in range(args.warmup):
+        opm.rk_stage(s % 5, 0.0, dt)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for s in range(args.steps):
+        opm.rk_stage(s % 5, 0.0, dt)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    opm.check_status()
+    dofs = wl.spec.dofs
+    out["fp32_mixed"] = {"value": dofs / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "pid_ns": ms * 1e6 / dofs,
+                         "ut_rel_l2_vs_fp64_per_var": rel, "ut_rel_l2_vs_fp64": rel_all,
+                         "dtype": "f32 fluxes, f64 state / RK / pressure recovery"}
+    opm.close()
+    del utm, ref, gU, lam
+    return out
+
+
 def run_ours(args):
     import torch
     from paper_2606_18927_gb300 import dg
@@ -268,6 +322,10 @@ def run_ours(args):
             dist.destroy_process_group()
         return 0
 
+    variants = {}
+    if world == 1 and precision == dg.FP64 and not args.no_variants:
+        variants = measure_variants(args, wl, X, nbr, U, op, stream, dt)
+
     # ---- roofline of the dominant kernel
     kernels = {}
     for k, (ms, cnt) in prof.items():
@@ -281,9 +339,10 @@ def run_ours(args):
     peaks = load_peaks()
     if precision == dg.FP64:
         achieved = kernels[dom]["achieved_tflops"]
+        tpd = NCU_TRAFFIC_PER_DOF.get(("k_" + dom, "fp64", wl.spec.N))
         roof = {"bound": "alu", "kernel": "k_" + dom, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS if achieved else None,
-                "traffic": None,
+                "traffic": tpd * dofs if tpd else None,
                 "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 pipe)"}
     else:
         hbm = peaks.get("hbm_gbs", 6800.0)
@@ -313,6 +372,7 @@ def run_ours(args):
                 "steps": e2e_steps},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
+        "variants": variants,
     }
     print(json.dumps(line))
     if dist:
@@ -332,6 +392,8 @@ def main():
                     help="element counts of a smaller case of the same workload (profiling)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the FP32-mixed and VJP measurements appended to the line")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

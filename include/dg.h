@@ -160,6 +160,11 @@ int dg_vjp(dg_ctx* c, const double* U, const double* lam, double* gU, double* gt
 /* Sets the wall-law constants (kappa, B) used by later calls (Sec. 3.2). */
 int dg_set_params(dg_ctx* c, double kappa, double B);
 
+/* Volume-averaged kinetic energy (1/|Omega|) sum_nodes w_i w_j w_k J rho|u|^2/2
+ * (the Taylor-Green diagnostic).  U: device array or NULL for the state; ke:
+ * host double.  Synchronises the stream. */
+int dg_kinetic_energy(dg_ctx* c, const double* U, double* ke);
+
 /* Mean wall shear: the surface-quadrature-weighted mean of tau_w t_x over
  * all wall-modelled faces (t: unit wall-parallel sample velocity).  U: device
  * array or NULL for the state; loss: host double.  Synchronises the stream.

@@ -32,6 +32,9 @@ def lib(extended=False):
         L.ora_max_threads.restype = ctypes.c_int
         L.ora_create.argtypes = [ctypes.c_int, ctypes.c_int, dp, ip, dp, ip, ctypes.c_char_p, ctypes.c_int]
         L.ora_create.restype = vp
+        L.ora_create_subset.argtypes = [ctypes.c_int, ctypes.c_int, dp, ip, dp, ip, ctypes.c_int, ip,
+                                        ctypes.c_char_p, ctypes.c_int]
+        L.ora_create_subset.restype = vp
         L.ora_destroy.argtypes = [vp]
         L.ora_get_metrics.argtypes = [vp, dp, dp]
         L.ora_num_wall.argtypes = [vp]
@@ -98,9 +101,12 @@ class Oracle:
     """One mesh + parameter set.  U arrays are SoA [5][K][n^3] float64.
 
     extended=True evaluates everything (geometry included) in long double and
-    rounds the results to double: the parity reference."""
+    rounds the results to double: the parity reference.  subset: element
+    indices; Ut is then evaluated on those elements only (the rest of the
+    output is 0), which lets the oracle sample meshes too large to evaluate
+    whole."""
 
-    def __init__(self, N, X, nbr, phys, vol_flux=0, surf_flux=1, viscous=1, law=1, extended=False):
+    def __init__(self, N, X, nbr, phys, vol_flux=0, surf_flux=1, viscous=1, law=1, extended=False, subset=None):
         self.L = lib(extended)
         self.extended = extended
         self.N = int(N)
@@ -112,7 +118,12 @@ class Oracle:
         self._phys = phys_array(phys)
         opts = np.array([vol_flux, surf_flux, viscous, law], dtype=np.int32)
         err = ctypes.create_string_buffer(512)
-        self.h = self.L.ora_create(self.N, self.K, _p(X), _ip(nbr), _p(self._phys), _ip(opts), err, 512)
+        if subset is None:
+            self.h = self.L.ora_create(self.N, self.K, _p(X), _ip(nbr), _p(self._phys), _ip(opts), err, 512)
+        else:
+            sel = np.ascontiguousarray(subset, dtype=np.int32)
+            self.h = self.L.ora_create_subset(self.N, self.K, _p(X), _ip(nbr), _p(self._phys), _ip(opts),
+                                              int(sel.size), _ip(sel), err, 512)
         if not self.h:
             raise ValueError("oracle mesh rejected: " + err.value.decode())
         self.shape = (5, self.K, self.n3)

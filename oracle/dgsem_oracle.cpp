@@ -214,7 +214,14 @@ struct Mesh {
   std::vector<real> ws_ref;   // sample reference coordinates [slot*3]
   std::vector<real> ws_l;     // Lagrange weights [slot*3*n]
   int nwall = 0;
+  // Optional evaluation subset (empty: every element).  Ut is computed for
+  // the elements in mask_out only; the lifting for those and their
+  // neighbours (mask_grad); primitives and metrics for one more ring
+  // (mask_q).  Used to sample meshes too large to evaluate whole.
+  std::vector<char> mask_out, mask_grad, mask_q;
 };
+
+inline bool in_mask(const std::vector<char>& m, int e) { return m.empty() || m[e]; }
 
 inline int node(const Mesh& M, int i, int j, int k) { return i + M.n * (j + M.n * k); }
 inline void ijk(const Mesh& M, int p, int& i, int& j, int& k) {
@@ -240,6 +247,7 @@ static bool build_metrics(Mesh& M, std::string& err) {
   M.J.assign((size_t)K * n3, 0.0);
   std::vector<real> dX(9 * n3), v(3 * n3);
   for (int e = 0; e < K; ++e) {
+    if (!in_mask(M.mask_q, e)) continue;
     // Coordinates relative to the element's first node: rows of D sum to
     // zero and curl(c grad X_m) = 0 for a constant c, so derivatives and the
     // curl form are unchanged in exact arithmetic, while the roundoff no
@@ -409,7 +417,7 @@ static bool build_wall_samples(Mesh& M, real hwm, std::string& err) {
   for (int e = 0; e < K; ++e)
     for (int l = 0; l < 6; ++l) {
       int s0 = M.wslot[e * 6 + l];
-      if (s0 < 0) continue;
+      if (s0 < 0 || !in_mask(M.mask_q, e)) continue;
       const int dir = l / 2;
       for (int b = 0; b < n; ++b)
         for (int a = 0; a < n; ++a) {
@@ -421,7 +429,7 @@ static bool build_wall_samples(Mesh& M, real hwm, std::string& err) {
             real nout = face_sign(l) * ja[c] / s;
             xs[c] = M.X[(size_t)c * K * n3 + (size_t)e * n3 + p] - hwm * nout;
           }
-          int best = -1; real bestr = 1e300, bref[3] = {0, 0, 0};
+          int best = -1; real bref[3] = {0, 0, 0};
           for (int c2 = 0; c2 < K; ++c2) {
             bool inside = true;
             for (int c = 0; c < 3; ++c) {
@@ -433,7 +441,7 @@ static bool build_wall_samples(Mesh& M, real hwm, std::string& err) {
             if (!locate_point(M, c2, xs, ref)) continue;
             real rm = std::max(std::fabs(ref[0]), std::max(std::fabs(ref[1]), std::fabs(ref[2])));
             if (rm <= 1.0 + 1e-8) {  // first (lowest-index) element containing the point
-              best = c2; bestr = rm;
+              best = c2;
               for (int c = 0; c < 3; ++c) bref[c] = ref[c];
               break;
             }
@@ -759,6 +767,7 @@ int time_derivative(const Mesh& M, const Phys<T>& P, const Opts& O, const T* U, 
   // 3. primitives
 #pragma omp parallel for schedule(static)
   for (int e = 0; e < K; ++e)
+    if (in_mask(M.mask_q, e))
     for (int p = 0; p < n3; ++p) {
       T u[5]; load_U(M, U, e, p, u);
       W.q[(size_t)e * n3 + p] = prim_of(P, u);
@@ -768,6 +777,7 @@ int time_derivative(const Mesh& M, const Phys<T>& P, const Opts& O, const T* U, 
     W.grad.assign(S * 12, T(0.0));
 #pragma omp parallel for schedule(static)
     for (int e = 0; e < K; ++e)
+      if (in_mask(M.mask_grad, e))
       for (int p = 0; p < n3; ++p) {
         int i, j, k; ijk(M, p, i, j, k);
         const real* ja = &M.Ja[((size_t)e * n3 + p) * 9];
@@ -828,6 +838,7 @@ int time_derivative(const Mesh& M, const Phys<T>& P, const Opts& O, const T* U, 
     W.G.assign(S * 15, T(0.0));
 #pragma omp parallel for schedule(static)
     for (int e = 0; e < K; ++e)
+      if (in_mask(M.mask_grad, e))
       for (int p = 0; p < n3; ++p) {
         T g[3][4];
         for (int d = 0; d < 3; ++d)
@@ -844,6 +855,7 @@ int time_derivative(const Mesh& M, const Phys<T>& P, const Opts& O, const T* U, 
   if (O.viscous && M.nwall > 0) {
 #pragma omp parallel for schedule(static)
     for (int e = 0; e < K; ++e)
+      if (in_mask(M.mask_out, e))
       for (int l = 0; l < 6; ++l) {
         int s0 = M.wslot[e * 6 + l];
         if (s0 < 0) continue;
@@ -877,6 +889,7 @@ int time_derivative(const Mesh& M, const Phys<T>& P, const Opts& O, const T* U, 
   // 6-8. volume integral, surface integral, Jacobian scaling, source
 #pragma omp parallel for schedule(static)
   for (int e = 0; e < K; ++e)
+    if (in_mask(M.mask_out, e))
     for (int p = 0; p < n3; ++p) {
       int i, j, k; ijk(M, p, i, j, k);
       const int idx[3] = {i, j, k};
@@ -1105,14 +1118,30 @@ int ora_max_threads(void) {
 #endif
 }
 
-void* ora_create(int N, int K, const double* X, const int* nbr, const double* phys, const int* opts,
-                 char* err, int errlen) {
+static void* create_impl(int N, int K, const double* X, const int* nbr, const double* phys, const int* opts,
+                         int n_sel, const int* sel, char* err, int errlen) {
   Ctx* c = new Ctx();
   Mesh& M = c->M;
   M.N = N; M.n = N + 1; M.n2 = M.n * M.n; M.n3 = M.n2 * M.n; M.K = K;
   lgl(N, M.xi, M.w, M.D);
   M.X = to_real(X, (size_t)3 * K * M.n3);
   M.nbr.assign(nbr, nbr + (size_t)6 * K);
+  if (n_sel > 0) {
+    // the selected elements, their neighbours, and one more ring
+    M.mask_out.assign(K, 0); M.mask_grad.assign(K, 0); M.mask_q.assign(K, 0);
+    for (int x = 0; x < n_sel; ++x)
+      if (sel[x] >= 0 && sel[x] < K) M.mask_out[sel[x]] = 1;
+    auto grow = [&](const std::vector<char>& a, std::vector<char>& b) {
+      for (int e = 0; e < K; ++e)
+        if (a[e]) {
+          b[e] = 1;
+          for (int l = 0; l < 6; ++l)
+            if (M.nbr[e * 6 + l] >= 0) b[M.nbr[e * 6 + l]] = 1;
+        }
+    };
+    grow(M.mask_out, M.mask_grad);
+    grow(M.mask_grad, M.mask_q);
+  }
   c->P.gamma = phys[0]; c->P.R = phys[1]; c->P.mu = phys[2]; c->P.Pr = phys[3];
   c->P.f[0] = phys[4]; c->P.f[1] = phys[5]; c->P.f[2] = phys[6];
   c->P.kappa = phys[7]; c->P.B = phys[8]; c->P.hwm = phys[9];
@@ -1125,6 +1154,18 @@ void* ora_create(int N, int K, const double* X, const int* nbr, const double* ph
     return nullptr;
   }
   return c;
+}
+
+void* ora_create(int N, int K, const double* X, const int* nbr, const double* phys, const int* opts,
+                 char* err, int errlen) {
+  return create_impl(N, K, X, nbr, phys, opts, 0, nullptr, err, errlen);
+}
+
+// As ora_create, but Ut is evaluated only on the n_sel selected elements
+// (other entries of the output stay 0).
+void* ora_create_subset(int N, int K, const double* X, const int* nbr, const double* phys, const int* opts,
+                        int n_sel, const int* sel, char* err, int errlen) {
+  return create_impl(N, K, X, nbr, phys, opts, n_sel, sel, err, errlen);
 }
 
 void ora_destroy(void* h) { delete (Ctx*)h; }

@@ -61,6 +61,8 @@ struct dg_ctx {
   double* ro_stage = nullptr;  // 5 stage inputs
   double* ro_work = nullptr;   // Uw, dUw, gA, gD, gT, lam
   double* ro_scalar = nullptr; // loss
+  double* wJ = nullptr;        // w_i w_j w_k J per node (kinetic-energy integral)
+  double vol = 0.0;
   // adjoint scratch (allocated on the first dg_vjp)
   double* gUf = nullptr;
   double* gGf = nullptr;
@@ -99,7 +101,7 @@ void free_all(dg_ctx* c) {
   void* ptrs[] = {c->U, c->dU, c->io, c->io2, c->Ja, c->invJ, c->fgeo, c->nbr, c->elem_face, c->faces,
                   c->ws_elem, c->ws_lag, c->Rv, c->Gf, c->Fs, c->tau, c->status,
                   c->gUf, c->gGf, c->gWf, c->gUs, c->gtheta, c->wq, c->ro_ckpt, c->ro_stage, c->ro_work,
-                  c->ro_scalar};
+                  c->ro_scalar, c->wJ};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -148,6 +150,17 @@ int run_operator(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {
     case 8: return run_operator_n8(a, ph, s);
     default: return (int)cudaErrorInvalidValue;
   }
+}
+// sum over nodes of wJ * |m|^2 / (2 rho), block reduction + one atomic per warp
+__global__ void k_kinetic_energy(long long S, const double* __restrict__ U, const double* __restrict__ wJ,
+                                 double* __restrict__ out) {
+  double acc = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < S; i += (long long)gridDim.x * blockDim.x) {
+    const double r = U[i], m1 = U[S + i], m2 = U[2 * S + i], m3 = U[3 * S + i];
+    acc += wJ[i] * 0.5 * (m1 * m1 + m2 * m2 + m3 * m3) / r;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
 }
 __global__ void k_axpby_api(long long n, double a, const double* __restrict__ x, double b, double* __restrict__ y) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -459,6 +472,37 @@ static int check_adjoint_options(dg_ctx* c, const char* who) {
     return fail(c, DG_ERR_NOT_IMPLEMENTED, std::string(who) + ": the adjoint is available for FP64 contexts");
   if (c->opts.vol_flux != DG_VOL_KEP_PIROZZOLI)
     return fail(c, DG_ERR_NOT_IMPLEMENTED, std::string(who) + ": the adjoint needs the Pirozzoli volume flux");
+  return DG_OK;
+}
+
+int dg_kinetic_energy(dg_ctx* c, const double* U, double* ke) {
+  if (!c || !ke) return c ? fail(c, DG_ERR_ARG, "dg_kinetic_energy: null ke") : DG_ERR_ARG;
+  const double* Uin = U ? U : c->U;
+  if (!U && !c->state_set) return fail(c, DG_ERR_NOT_INIT, "dg_kinetic_energy: state not set");
+  cudaError_t e = cudaSuccess;
+  if (!c->wJ) {
+    std::vector<double> w(c->S);
+    const std::vector<double>& bw = c->geo.basis.w;
+    c->vol = 0.0;
+    for (size_t x = 0; x < c->S; ++x) {
+      const int p = (int)(x % c->n3);
+      w[x] = bw[p % c->n] * bw[(p / c->n) % c->n] * bw[p / c->n2] * c->geo.J[x];
+      c->vol += w[x];
+    }
+    e = alloc(&c->wJ, c->S);
+    if (e == cudaSuccess) e = cudaMemcpy(c->wJ, w.data(), c->S * sizeof(double), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(c, e, "dg_kinetic_energy: weights");
+  }
+  int rc = ensure_adjoint_scratch(c);
+  if (rc != DG_OK) return rc;
+  e = cudaMemsetAsync(c->ro_scalar, 0, sizeof(double), c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "dg_kinetic_energy");
+  dg::k_kinetic_energy<<<152 * 8, 256, 0, c->stream>>>((long long)c->S, Uin, c->wJ, c->ro_scalar);
+  double sum = 0.0;
+  e = cudaMemcpyAsync(&sum, c->ro_scalar, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "dg_kinetic_energy");
+  *ke = sum / c->vol;
   return DG_OK;
 }
 

@@ -89,6 +89,7 @@ def lib():
         "dg_vjp": (c_int, [vp, vp, vp, vp, vp]),
         "dg_set_params": (c_int, [vp, c_double, c_double]),
         "dg_wall_shear": (c_int, [vp, vp, dp]),
+        "dg_kinetic_energy": (c_int, [vp, vp, dp]),
         "dg_rollout_vjp": (c_int, [vp, vp, c_int, c_double, dp, vp, vp]),
         "dg_profile_enable": (c_int, [vp, c_int]),
         "dg_profile_read": (c_int, [vp, dp, ip]),
@@ -237,6 +238,12 @@ class Operator:
     def set_params(self, kappa, B):
         self._check(lib().dg_set_params(self.h, float(kappa), float(B)))
 
+    def kinetic_energy(self, U=None):
+        out = ctypes.c_double(0.0)
+        pu = _ptr(U)[0] if U is not None else None
+        self._check(lib().dg_kinetic_energy(self.h, pu, ctypes.byref(out)))
+        return out.value
+
     def wall_shear(self, U=None):
         out = ctypes.c_double(0.0)
         pu = _ptr(U)[0] if U is not None else None
@@ -313,13 +320,15 @@ def _autograd():
             gU0 = torch.empty_like(U0)
             gth = torch.zeros(2, dtype=torch.float64, device=U0.device)
             loss = op.rollout_vjp(U0.contiguous(), nsteps, dt, gU0, gth)
-            ctx.save_for_backward(gU0, gth.to(theta.device, theta.dtype))
+            ctx.save_for_backward(gU0, gth)
+            ctx.theta_device, ctx.theta_dtype = theta.device, theta.dtype
             return torch.tensor(loss, dtype=torch.float64, device=U0.device)
 
         @staticmethod
         def backward(ctx, g):
             gU0, gth = ctx.saved_tensors
-            return g * gU0, g * gth, None, None, None
+            g = g.to(gU0.device)
+            return g * gU0, (g * gth).to(ctx.theta_device, ctx.theta_dtype), None, None, None
 
     return DGOperatorFunction, WallShearRollout
 

@@ -1,0 +1,77 @@
+"""Parity at the full benchmark size, in the bench's launch configuration.
+
+Taylor-Green, N = 7, 32^3 elements (16.8M DOF, Roe, BR1): the GPU operator
+and one fused LSERK4 stage are compared with the extended-precision oracle
+on a seeded sample of elements (the oracle evaluates those elements and the
+two neighbour rings they depend on).  The 48^3 sine-mapped case (56.6M DOF)
+runs when DG_FULLSIZE_LARGE=1 (it needs ~40 GB of host memory)."""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2606_18927_gb300 import dg, inputs as I
+from gpu_helpers import parity_per_var, torch_cuda
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+
+def _sample(K, count, seed):
+    z = I.splitmix64(count, seed=seed)
+    return np.unique((z % np.uint64(K)).astype(np.int64))
+
+
+def _full_case(ora, name, count=12):
+    torch = torch_cuda()
+    wl = I.workload(name)
+    x, w, D = ora.lgl(wl.spec.N)
+    X = I.node_coordinates(wl.spec, x)
+    nbr = I.connectivity(wl.spec)
+    U = I.initial_state(wl, X)
+    sel = _sample(wl.spec.K, count, seed=99)
+    o = ora.Oracle(wl.spec.N, X, nbr, wl.phys, vol_flux=wl.vol_flux, surf_flux=wl.surf_flux, extended=True,
+                   subset=sel)
+    return torch, wl, X, nbr, U, sel, o
+
+
+def _check(torch, wl, X, nbr, U, sel, o, precision, tol):
+    g = dg.Operator(wl.spec.N, X, nbr, wl.phys, precision=precision, vol_flux=wl.vol_flux,
+                    surf_flux=wl.surf_flux)
+    Ud = torch.from_numpy(U).cuda()
+    Ut = torch.empty_like(Ud)
+    g.time_derivative(Ut, Ud)
+    ref = o.time_derivative(U)
+    got = Ut.cpu().numpy()[:, sel]
+    e = parity_per_var(got, ref[:, sel])
+    print(wl.name, "precision", precision, "sampled Ut parity", ["%.1e" % v for v in e])
+    if precision == dg.FP64:
+        assert max(e) <= tol
+        # one fused LSERK4 stage (the benchmarked kernel): compare the register
+        dt = 1e-4
+        g.set_state(Ud)
+        g.rk_stage(0, 0.0, dt)
+        dUg = torch.empty_like(Ud)
+        g.get_rk_register(dUg)
+        g.check_status()
+        e2 = parity_per_var(dUg.cpu().numpy()[:, sel], dt * ref[:, sel])
+        print(wl.name, "sampled stage register parity", ["%.1e" % v for v in e2])
+        assert max(e2) <= tol
+    else:
+        a = got.reshape(5, -1); b = ref[:, sel].reshape(5, -1)
+        l2 = [float(np.linalg.norm(a[v] - b[v]) / np.linalg.norm(b[v])) for v in range(5)]
+        print(wl.name, "mixed sampled rel L2", ["%.1e" % v for v in l2])
+        assert max(l2) <= tol
+    g.close()
+
+
+def test_tgv_n7_32_full_size(ora):
+    torch, wl, X, nbr, U, sel, o = _full_case(ora, "tgv_n7_32")
+    _check(torch, wl, X, nbr, U, sel, o, dg.FP64, TOL)
+    _check(torch, wl, X, nbr, U, sel, o, dg.FP32_MIXED, 1e-3)
+
+
+@pytest.mark.skipif(os.environ.get("DG_FULLSIZE_LARGE") != "1", reason="set DG_FULLSIZE_LARGE=1 (56.6M DOF)")
+def test_tgv_sine_n7_48_full_size(ora):
+    torch, wl, X, nbr, U, sel, o = _full_case(ora, "tgv_sine_n7_48", count=8)
+    _check(torch, wl, X, nbr, U, sel, o, dg.FP64, TOL)
