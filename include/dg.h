@@ -160,6 +160,12 @@ int dg_vjp(dg_ctx* c, const double* U, const double* lam, double* gU, double* gt
 /* Sets the wall-law constants (kappa, B) used by later calls (Sec. 3.2). */
 int dg_set_params(dg_ctx* c, double kappa, double B);
 
+/* Explicit time step dt = cfl * 2/(2N+1) * min_nodes J / sum_dir(|u . Ja^dir|
+ * + c |Ja^dir|) (CFL-based step of the explicit LSERK4, paper Sec. 4 uses
+ * CFL 0.9).  U: device array or NULL for the state; dt: host double.
+ * Synchronises the stream. */
+int dg_time_step(dg_ctx* c, const double* U, double cfl, double* dt);
+
 /* Volume-averaged kinetic energy (1/|Omega|) sum_nodes w_i w_j w_k J rho|u|^2/2
  * (the Taylor-Green diagnostic).  U: device array or NULL for the state; ke:
  * host double.  Synchronises the stream. */

@@ -162,6 +162,27 @@ __global__ void k_kinetic_energy(long long S, const double* __restrict__ U, cons
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
 }
+// max over nodes of sum_dir (|u . Ja^dir| + c |Ja^dir|) / J (positive doubles
+// order like their bit patterns, so the maximum is an integer atomicMax)
+template <typename R>
+__global__ void k_wave_speed(long long S, const double* __restrict__ U, const R* __restrict__ Ja,
+                             const R* __restrict__ invJ, double gamma, unsigned long long* __restrict__ out) {
+  double mx = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < S; i += (long long)gridDim.x * blockDim.x) {
+    const double r = U[i], u = U[S + i] / r, v = U[2 * S + i] / r, w = U[3 * S + i] / r;
+    const double p = (gamma - 1.0) * (U[4 * S + i] - 0.5 * r * (u * u + v * v + w * w));
+    const double c = sqrt(gamma * p / r);
+    double lam = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      const double a0 = Ja[(size_t)(d * 3) * S + i], a1 = Ja[(size_t)(d * 3 + 1) * S + i],
+                   a2 = Ja[(size_t)(d * 3 + 2) * S + i];
+      lam += fabs(u * a0 + v * a1 + w * a2) + c * sqrt(a0 * a0 + a1 * a1 + a2 * a2);
+    }
+    mx = fmax(mx, lam * (double)invJ[i]);
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(mx));
+}
 __global__ void k_axpby_api(long long n, double a, const double* __restrict__ x, double b, double* __restrict__ y) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) y[i] = (b == 0.0 ? 0.0 : b * y[i]) + (a == 0.0 ? 0.0 : a * x[i]);
@@ -472,6 +493,30 @@ static int check_adjoint_options(dg_ctx* c, const char* who) {
     return fail(c, DG_ERR_NOT_IMPLEMENTED, std::string(who) + ": the adjoint is available for FP64 contexts");
   if (c->opts.vol_flux != DG_VOL_KEP_PIROZZOLI)
     return fail(c, DG_ERR_NOT_IMPLEMENTED, std::string(who) + ": the adjoint needs the Pirozzoli volume flux");
+  return DG_OK;
+}
+
+int dg_time_step(dg_ctx* c, const double* U, double cfl, double* dt) {
+  if (!c || !dt || !(cfl > 0.0)) return c ? fail(c, DG_ERR_ARG, "dg_time_step: bad argument") : DG_ERR_ARG;
+  const double* Uin = U ? U : c->U;
+  if (!U && !c->state_set) return fail(c, DG_ERR_NOT_INIT, "dg_time_step: state not set");
+  int rc = ensure_adjoint_scratch(c);
+  if (rc != DG_OK) return rc;
+  unsigned long long* slot = reinterpret_cast<unsigned long long*>(c->ro_scalar);
+  cudaError_t e = cudaMemsetAsync(slot, 0, sizeof(double), c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "dg_time_step");
+  if (c->opts.precision == DG_FP32_MIXED)
+    dg::k_wave_speed<float><<<152 * 8, 256, 0, c->stream>>>((long long)c->S, Uin, static_cast<const float*>(c->Ja),
+                                                             static_cast<const float*>(c->invJ), c->phys.gamma, slot);
+  else
+    dg::k_wave_speed<double><<<152 * 8, 256, 0, c->stream>>>((long long)c->S, Uin, static_cast<const double*>(c->Ja),
+                                                              static_cast<const double*>(c->invJ), c->phys.gamma, slot);
+  double mx = 0.0;
+  e = cudaMemcpyAsync(&mx, slot, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "dg_time_step");
+  if (!(mx > 0.0)) return fail(c, DG_ERR_NONFINITE, "dg_time_step: no finite wave speed");
+  *dt = cfl * 2.0 / (2.0 * c->N + 1.0) / mx;
   return DG_OK;
 }
 

@@ -90,6 +90,7 @@ def lib():
         "dg_set_params": (c_int, [vp, c_double, c_double]),
         "dg_wall_shear": (c_int, [vp, vp, dp]),
         "dg_kinetic_energy": (c_int, [vp, vp, dp]),
+        "dg_time_step": (c_int, [vp, vp, c_double, dp]),
         "dg_rollout_vjp": (c_int, [vp, vp, c_int, c_double, dp, vp, vp]),
         "dg_profile_enable": (c_int, [vp, c_int]),
         "dg_profile_read": (c_int, [vp, dp, ip]),
@@ -237,6 +238,12 @@ class Operator:
 
     def set_params(self, kappa, B):
         self._check(lib().dg_set_params(self.h, float(kappa), float(B)))
+
+    def time_step(self, cfl=0.9, U=None):
+        out = ctypes.c_double(0.0)
+        pu = _ptr(U)[0] if U is not None else None
+        self._check(lib().dg_time_step(self.h, pu, float(cfl), ctypes.byref(out)))
+        return out.value
 
     def kinetic_energy(self, U=None):
         out = ctypes.c_double(0.0)

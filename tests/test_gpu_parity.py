@@ -127,3 +127,16 @@ def test_free_stream_and_conservation_on_device(ora, N, ne):
     ref = o.time_derivative(U)
     # both at the roundoff floor, and of the same size
     assert np.abs(Ut).max() < 1e-9 and np.abs(ref).max() < 1e-9
+
+
+def test_time_step_and_kinetic_energy(ora):
+    """CFL time step (reading R9) and the volume-averaged kinetic energy on
+    the GPU against the oracle's definitions."""
+    torch = torch_cuda()
+    phys = I.phys_params(Ma=0.1, Re=1600.0)
+    o, g, X, U = case(ora, I.BoxSpec(4, 3, 2, 2, geometry="sine", amplitude=0.2), phys, surf_flux=2)
+    Ud = torch.from_numpy(U).cuda()
+    dt = g.time_step(0.9, Ud)
+    ke = g.kinetic_energy(Ud)
+    assert abs(dt - o.dt(U, 0.9)) <= 1e-13 * dt
+    assert abs(ke - o.kinetic_energy(U)) <= 1e-13 * ke
