@@ -188,6 +188,23 @@ def run_reference(args):
     return 0
 
 
+def max_over_ranks(value, dist=None, device=None):
+    """Maximum of a per-rank float over all ranks (the slowest rank's time)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(dofs_per_rank, steps, world, max_ms):
+    """Whole-job DOF-stage updates per second: every rank advances its own
+    replica, so the job processes world * dofs * steps in the slowest rank's
+    time."""
+    return world * dofs_per_rank * steps / (max_ms * 1e-3)
+
+
 def measure_variants(args, wl, X, nbr, U, op64, stream, dt):
     """FP32-mixed form on the same workload (throughput and its Ut error
     against the FP64 path), and the time of one FP64 VJP."""
@@ -200,18 +217,35 @@ def measure_variants(args, wl, X, nbr, U, op64, stream, dt):
     # VJP of the operator (FP64, hand-written adjoint)
     lam = torch.ones_like(Ud)
     gU = torch.empty_like(Ud)
+    free0 = torch.cuda.mem_get_info()[0]
     op64.vjp(lam, gU, Ud)
     torch.cuda.synchronize()
+    vjp_scratch = free0 - torch.cuda.mem_get_info()[0]
     e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(3):
         op64.vjp(lam, gU, Ud)
     e1.record(stream)
     torch.cuda.synchronize()
-    out["vjp_fp64"] = {"ms_per_call": e0.elapsed_time(e1) / 3}
+    out["vjp_fp64"] = {"ms_per_call": e0.elapsed_time(e1) / 3, "scratch_gb": vjp_scratch / 1e9}
+    if wl.spec.periodic[1] is False or not all(wl.spec.periodic):
+        # wall-modelled channel: 20-step rollout VJP of the mean wall shear
+        gth = torch.zeros(2, dtype=torch.float64, device="cuda")
+        op64.rollout_vjp(Ud, 2, dt, gU, gth)
+        torch.cuda.synchronize()
+        free1 = torch.cuda.mem_get_info()[0]
+        e0.record(stream)
+        loss = op64.rollout_vjp(Ud, 20, dt, gU, gth)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out["rollout_vjp_20_steps"] = {"ms": e0.elapsed_time(e1), "loss": loss,
+                                       "dloss_dkappa": float(gth[0]), "dloss_dB": float(gth[1]),
+                                       "checkpoint_gb": (free1 - torch.cuda.mem_get_info()[0]) / 1e9}
     # FP32-mixed form
+    free2 = torch.cuda.mem_get_info()[0]
     opm = dg.Operator(wl.spec.N, X, nbr, wl.phys, precision=dg.FP32_MIXED, vol_flux=wl.vol_flux,
                       surf_flux=wl.surf_flux, viscous=wl.viscous, law=wl.law, stream=stream)
+    mixed_footprint = free2 - torch.cuda.mem_get_info()[0]
     utm = torch.empty_like(Ud)
     opm.time_derivative(utm, Ud)
     a = utm.view(5, -1); b = ref.view(5, -1)
@@ -231,7 +265,8 @@ def measure_variants(args, wl, X, nbr, U, op64, stream, dt):
     dofs = wl.spec.dofs
     out["fp32_mixed"] = {"value": dofs / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "pid_ns": ms * 1e6 / dofs,
                          "ut_rel_l2_vs_fp64_per_var": rel, "ut_rel_l2_vs_fp64": rel_all,
-                         "dtype": "f32 fluxes, f64 state / RK / pressure recovery"}
+                         "dtype": "f32 fluxes, f64 state / RK / pressure recovery",
+                         "footprint_gb": mixed_footprint / 1e9}
     opm.close()
     del utm, ref, gU, lam
     return out
@@ -261,8 +296,8 @@ def run_ours(args):
     op.set_state(Ud)
     footprint = free0 - torch.cuda.mem_get_info()[0]
     dofs = wl.spec.dofs
-    # explicit time step from the CFL rule (value irrelevant to throughput)
-    dt = 1e-4
+    # explicit time step from the CFL rule (CFL 0.9, paper Sec. 4)
+    dt = op.time_step(0.9)
     for s in range(args.warmup):
         op.rk_stage(s % 5, 0.0, dt)
     torch.cuda.synchronize()
@@ -289,11 +324,8 @@ def run_ours(args):
     op.profile_enable(False)
     clk = clocks.stop()
     op.check_status()
-    if dist:
-        t = torch.tensor([ms_total], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
-    value = world * dofs * args.steps / (ms_total * 1e-3)
+    ms_total = max_over_ranks(ms_total, dist, "cuda")
+    value = job_throughput(dofs, args.steps, world, ms_total)
 
     # ---- end to end through the public API with host buffers
     Uh = torch.from_numpy(U).pin_memory()
@@ -310,11 +342,8 @@ def run_ours(args):
         op.get_state(Uh.numpy())       # device -> host copy of the step's result
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * dofs * e2e_steps / e2e_s
+    e2e_s = max_over_ranks(e2e_s, dist, "cuda")
+    e2e_value = job_throughput(dofs, e2e_steps, world, e2e_s * 1e3)
     nbytes = U.nbytes
 
     if rank != 0:
