@@ -29,7 +29,10 @@
  *   - Stream: every device operation of a context is enqueued on the stream
  *     given to dg_init_mesh / dg_set_stream (a cudaStream_t, 0 = legacy
  *     default stream).  Calls that return results to the host synchronise
- *     that stream; the others are asynchronous.
+ *     that stream; the others are asynchronous.  With dg_set_overlap the
+ *     wall-model kernel may run on a side stream that forks from and joins
+ *     back into that stream within each call, so the ordering seen by the
+ *     caller is that of the one stream.
  *   - Errors never trap or hang the GPU: device-side failures (non-finite
  *     state, wall-model Newton without convergence) set flags that the host
  *     reads with dg_check_status().
@@ -55,7 +58,11 @@ enum dg_status_code {
 };
 
 enum dg_precision { DG_FP64 = 0, DG_FP32_MIXED = 1 };
-enum dg_vol_flux { DG_VOL_KEP_PIROZZOLI = 0, DG_VOL_KEP_KENNEDY_GRUBER = 1 };
+/* Volume two-point fluxes: the kinetic-energy-preserving split forms of
+ * Pirozzoli and of Kennedy-Gruber (Sec. 2.2), and Chandrashekar's entropy-
+ * conserving and kinetic-energy-preserving flux (Sec. 4, the production
+ * scheme).  The central surface flux uses the same two-point flux. */
+enum dg_vol_flux { DG_VOL_KEP_PIROZZOLI = 0, DG_VOL_KEP_KENNEDY_GRUBER = 1, DG_VOL_EC_CHANDRASHEKAR = 2 };
 enum dg_surf_flux { DG_SURF_CENTRAL = 0, DG_SURF_LLF = 1, DG_SURF_ROE = 2 };
 enum dg_wall_law { DG_LAW_SPALDING = 0, DG_LAW_REICHARDT = 1 };
 
@@ -79,8 +86,12 @@ typedef struct {
   const int* nbr;
 } dg_mesh_desc;
 
-/* Ideal gas and wall-model constants (paper Sec. 4: ideal gas; Sec. 3.2:
- * law of the wall).  mu is constant; kappa and B are the law's constants;
+/* Ideal gas and wall-model constants (paper Sec. 4: ideal gas with
+ * Sutherland's law; Sec. 3.2: law of the wall).  mu is the viscosity:
+ * constant when suth_S <= 0, else the reference value of Sutherland's law
+ * mu(T) = mu (T / T_ref)^(3/2) (T_ref + suth_S) / (T + suth_S) (T_ref > 0
+ * required), which then also sets the conductivity mu(T) cp / Pr and the
+ * wall-model viscosity at the wall temperature; kappa and B are the law's constants;
  * hwm the sampling distance of the wall model; force a constant body force
  * per unit volume entering momentum (and its work f.u the energy).
  * p_ref: a constant subtracted from the pressure inside the momentum fluxes.
@@ -94,6 +105,7 @@ typedef struct {
   double kappa, B, hwm;
   int law; /* dg_wall_law */
   double p_ref;
+  double suth_S, T_ref; /* Sutherland's law (suth_S <= 0: constant mu) */
 } dg_phys;
 
 typedef struct {
@@ -121,6 +133,18 @@ int dg_destroy(dg_ctx* c);
 const char* dg_last_error(const dg_ctx* c);
 
 int dg_set_stream(dg_ctx* c, void* stream);
+
+/* Meshes with wall-modelled walls: enable = 1 runs the wall-model kernel
+ * (which reads only the state and writes only the wall faces' fluxes) on a
+ * side stream of the highest priority, beside the lifting and the
+ * interior-face kernel, rejoining the caller's stream before the volume
+ * kernel (the prioritised streams and events of the paper's Sec. 2.3).
+ * enable = 0 (the default) launches it in line on the caller's stream:
+ * measured on GB300 the wall kernel, sharing the SMs with the FP64-bound
+ * lifting, then takes longer than the two together.  Results are bitwise the
+ * same either way; a CUDA graph captured by dg_rk_steps_graph records the
+ * fork and join of the setting in force when it is captured. */
+int dg_set_overlap(dg_ctx* c, int enable);
 
 /* Sizes: number of elements, nodes per element and total doubles of U. */
 int dg_sizes(const dg_ctx* c, int* N, int* K, long long* n_state);
@@ -153,7 +177,8 @@ int dg_rk_steps(dg_ctx* c, double t, double dt, int nsteps);
  * recovery are written out by hand; the local Jacobians of the Riemann
  * solver and of the wall model (with the implicit function theorem for the
  * law of the wall, Sec. 3.2) come from forward-mode dual numbers.  FP64
- * contexts with the Pirozzoli volume flux (else DG_ERR_NOT_IMPLEMENTED).
+ * contexts with the Pirozzoli volume flux and a constant viscosity (else
+ * DG_ERR_NOT_IMPLEMENTED).
  * The first call allocates the adjoint scratch of the context. */
 int dg_vjp(dg_ctx* c, const double* U, const double* lam, double* gU, double* gtheta);
 
@@ -188,6 +213,13 @@ int dg_wall_shear(dg_ctx* c, const double* U, double* loss);
  * FP64 contexts with the Pirozzoli flux and wall-modelled walls. */
 int dg_rollout_vjp(dg_ctx* c, const double* U0, int nsteps, double dt, double* loss, double* gU0,
                    double* gtheta);
+
+/* As dg_rk_steps, but replays a CUDA graph of one full step (the fifteen
+ * kernel launches of the five stages), captured on an internal stream at
+ * the first call and again whenever dt changes; the replays run on the
+ * context's stream.  Results are identical to dg_rk_steps.  Per-kernel
+ * profiling does not see graph replays. */
+int dg_rk_steps_graph(dg_ctx* c, double t, double dt, int nsteps);
 
 /* Copies the LSERK4 register dU (5 K n^3 doubles) out of / into the context
  * (checkpoint and restart inside a step; between steps dU needs no saving

@@ -15,7 +15,8 @@ from . import build as _build
 
 _libs = {}
 
-PHYS_KEYS = ("gamma", "R", "mu", "Pr", "fx", "fy", "fz", "kappa", "B", "hwm")
+PHYS_KEYS = ("gamma", "R", "mu", "Pr", "fx", "fy", "fz", "kappa", "B", "hwm", "suth_S", "T_ref")
+PHYS_DEFAULTS = {"suth_S": 0.0, "T_ref": 1.0}
 
 
 def lib(extended=False):
@@ -26,6 +27,8 @@ def lib(extended=False):
         dp = ctypes.POINTER(ctypes.c_double)
         ip = ctypes.POINTER(ctypes.c_int)
         vp = ctypes.c_void_p
+        L.ora_viscosity.argtypes = [dp, ctypes.c_double]
+        L.ora_viscosity.restype = ctypes.c_double
         L.ora_lgl.argtypes = [ctypes.c_int, dp, dp, dp]
         L.ora_lserk4.argtypes = [dp, dp, dp]
         L.ora_set_threads.argtypes = [ctypes.c_int]
@@ -94,7 +97,7 @@ def max_threads():
 
 
 def phys_array(phys):
-    return np.array([float(phys[k]) for k in PHYS_KEYS], dtype=np.float64)
+    return np.array([float(phys.get(k, PHYS_DEFAULTS.get(k, 0.0))) for k in PHYS_KEYS], dtype=np.float64)
 
 
 class Oracle:
@@ -219,6 +222,10 @@ def wall_flux(phys, law, U5, nout):
     fm = np.zeros(3); tau = np.zeros(3)
     st = lib().ora_wall_flux(_p(pa), int(law), _p(U5), _p(nout), _p(fm), _p(tau))
     return fm, tau, st
+
+
+def viscosity(phys, T):
+    return lib().ora_viscosity(_p(phys_array(phys)), float(T))
 
 
 def riemann(phys, vol_kind, kind, UL, UR, nh):

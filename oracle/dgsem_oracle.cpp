@@ -69,6 +69,7 @@ inline Dual& operator*=(Dual& a, Dual b) { a = a * b; return a; }
 inline Dual sqrt(Dual a) { real s = std::sqrt(a.v); return Dual(s, a.d / (2.0 * s)); }
 inline Dual exp(Dual a) { real e = std::exp(a.v); return Dual(e, a.d * e); }
 inline Dual log(Dual a) { return Dual(std::log(a.v), a.d / a.v); }
+inline Dual log1p(Dual a) { return Dual(std::log1p(a.v), a.d / (1.0 + a.v)); }
 inline Dual asin(Dual a) { return Dual(std::asin(a.v), a.d / std::sqrt(1.0 - a.v * a.v)); }
 inline Dual fabs(Dual a) { return a.v < 0.0 ? -a : a; }
 
@@ -77,12 +78,12 @@ inline real val(const Dual& x) { return x.v; }
 inline real der(real) { return 0.0; }
 inline real der(const Dual& x) { return x.d; }
 
-using std::sqrt; using std::exp; using std::log; using std::asin; using std::fabs;
+using std::sqrt; using std::exp; using std::log; using std::log1p; using std::asin; using std::fabs;
 
 // ---------------------------------------------------------------------------
 // Enumerations (same numeric values as the public C ABI documents).
 // ---------------------------------------------------------------------------
-enum VolFlux { VOL_KEP_PIROZZOLI = 0, VOL_KEP_KENNEDY_GRUBER = 1 };
+enum VolFlux { VOL_KEP_PIROZZOLI = 0, VOL_KEP_KENNEDY_GRUBER = 1, VOL_EC_CHANDRASHEKAR = 2 };
 enum SurfFlux { SURF_CENTRAL = 0, SURF_LLF = 1, SURF_ROE = 2 };
 enum WallLaw { LAW_SPALDING = 0, LAW_REICHARDT = 1 };
 
@@ -186,6 +187,7 @@ struct Phys {
   real gamma = 1.4, R = 1.0, mu = 0.0, Pr = 0.72;
   real f[3] = {0.0, 0.0, 0.0};  // constant body force per unit volume
   T kappa = 0.41, B = 5.2;        // wall-law constants
+  real suth_S = 0.0, T_ref = 1.0;  // Sutherland constant and reference temperature (S <= 0: constant mu)
   real hwm = 0.1;               // wall-model sampling distance
 };
 struct Opts {
@@ -491,16 +493,40 @@ void euler_flux(const Prim<T>& q, const T U[5], const real a[3], T F[5]) {
   F[4] = (U[4] + q.p) * un;
 }
 
-// Two-point kinetic-energy-preserving flux F#(UL, UR) . a.
-//  Pirozzoli:        {rho}{u.a},  {rho}{u.a}{u} + {p} a,  {rho}{u.a}{h}
-//  Kennedy-Gruber:   {rho}{u.a},  {rho}{u.a}{u} + {p} a,  {rho}{u.a}{e} + {p}{u.a}
+// Logarithmic mean (a - b) / ln(a / b), written as (a - b) / log1p((a - b) / b)
+// so that it stays accurate when a and b are close; a == b gives a.
 template <class T>
-void twopoint_flux(int kind, const Prim<T>& L, const T UL[5], const Prim<T>& R, const T UR[5],
+T logmean(const T& a, const T& b) {
+  if (val(a) == val(b)) return 0.5 * (a + b);
+  T d = a - b;
+  return d / log1p(d / b);
+}
+
+// Two-point flux F#(UL, UR) . a.
+//  Pirozzoli (KEP):      {rho}{u.a},  {rho}{u.a}{u} + {p} a,  {rho}{u.a}{h}
+//  Kennedy-Gruber (KEP): {rho}{u.a},  {rho}{u.a}{u} + {p} a,  {rho}{u.a}{e} + {p}{u.a}
+//  Chandrashekar (entropy conserving and KEP, the paper's Sec. 4 scheme):
+//    beta = rho / (2 p), rho^ = ln-mean(rho), beta^ = ln-mean(beta),
+//    p~ = {rho} / (2 {beta}),  F_rho = rho^ {u}.a,  F_m = p~ a + {u} F_rho,
+//    F_E = F_rho (1 / (2 (gamma - 1) beta^) - {|u|^2} / 2) + {u} . F_m
+template <class T>
+void twopoint_flux(int kind, real gamma, const Prim<T>& L, const T UL[5], const Prim<T>& R, const T UR[5],
                    const real a[3], T F[5]) {
-  T rho = 0.5 * (L.rho + R.rho);
   T u[3];
   for (int c = 0; c < 3; ++c) u[c] = 0.5 * (L.u[c] + R.u[c]);
   T ua = u[0] * a[0] + u[1] * a[1] + u[2] * a[2];
+  if (kind == VOL_EC_CHANDRASHEKAR) {
+    T bL = L.rho / (2.0 * L.p), bR = R.rho / (2.0 * R.p);
+    T rho_ln = logmean(L.rho, R.rho), b_ln = logmean(bL, bR);
+    T pt = 0.5 * (L.rho + R.rho) / (bL + bR);
+    T u2 = 0.5 * (L.u[0] * L.u[0] + L.u[1] * L.u[1] + L.u[2] * L.u[2] +
+                  R.u[0] * R.u[0] + R.u[1] * R.u[1] + R.u[2] * R.u[2]);
+    F[0] = rho_ln * ua;
+    for (int c = 0; c < 3; ++c) F[1 + c] = pt * a[c] + u[c] * F[0];
+    F[4] = F[0] * (1.0 / (2.0 * (gamma - 1.0) * b_ln) - 0.5 * u2) + u[0] * F[1] + u[1] * F[2] + u[2] * F[3];
+    return;
+  }
+  T rho = 0.5 * (L.rho + R.rho);
   T p = 0.5 * (L.p + R.p);
   F[0] = rho * ua;
   for (int c = 0; c < 3; ++c) F[1 + c] = rho * ua * u[c] + p * a[c];
@@ -513,14 +539,22 @@ void twopoint_flux(int kind, const Prim<T>& L, const T UL[5], const Prim<T>& R, 
   }
 }
 
+// dynamic viscosity: constant, or Sutherland mu (T / T_ref)^(3/2) (T_ref + S) / (T + S)
+template <class T>
+T viscosity(const Phys<T>& P, const T& Tt) {
+  if (!(P.suth_S > 0.0)) return T(P.mu);
+  T x = Tt / P.T_ref;
+  return P.mu * x * sqrt(x) * (P.T_ref + P.suth_S) / (Tt + P.suth_S);
+}
+
 // Viscous flux Fv(U, grad W) . a  with grad W = g[d][w], W = (u, v, w, T).
 //   Fv_d = (0, tau_1d, tau_2d, tau_3d, tau_jd u_j + k dT/dx_d)
 //   tau_ij = mu (du_i/dx_j + du_j/dx_i) - 2/3 mu (div u) delta_ij
 template <class T>
 void viscous_flux(const Phys<T>& P, const Prim<T>& q, const T g[3][4], const real a[3], T F[5]) {
-  const real mu = P.mu;
+  const T mu = viscosity(P, q.T_);
   const real cp = P.gamma * P.R / (P.gamma - 1.0);
-  const real kcond = mu * cp / P.Pr;
+  const T kcond = mu * cp / P.Pr;
   T div = g[0][0] + g[1][1] + g[2][2];
   T tau[3][3];
   for (int i = 0; i < 3; ++i)
@@ -547,7 +581,7 @@ void viscous_flux(const Phys<T>& P, const Prim<T>& q, const T g[3][4], const rea
 template <class T>
 void riemann(const Phys<T>& P, int vol_kind, int kind, const Prim<T>& L, const T UL[5],
              const Prim<T>& R, const T UR[5], const real nh[3], T F[5]) {
-  twopoint_flux(vol_kind, L, UL, R, UR, nh, F);
+  twopoint_flux(vol_kind, P.gamma, L, UL, R, UR, nh, F);
   if (kind == SURF_CENTRAL) return;
   const real g = P.gamma;
   if (kind == SURF_LLF) {
@@ -703,7 +737,7 @@ int wall_flux(const Phys<T>& P, int law, const Prim<T>& s, const real nout[3], T
   T rhow = s.rho * s.T_ / Tw;
   T a = sqrt(r / (2.0 * cp * Tw));
   T uvd = asin(a * umag) / a;
-  T nuw = P.mu / rhow;
+  T nuw = viscosity(P, Tw) / rhow;
   T ut;
   int it = solve_utau(law, uvd, P.hwm, nuw, P.kappa, P.B, ut);
   T tw = rhow * ut * ut;
@@ -906,7 +940,7 @@ int time_derivative(const Mesh& M, const Phys<T>& P, const Opts& O, const T* U, 
           for (int c = 0; c < 3; ++c) abar[c] = 0.5 * (jao[dir * 3 + c] + jam[dir * 3 + c]);
           T Um[5]; load_U(M, U, e, pm, Um);
           T F[5];
-          twopoint_flux(O.vol_flux, qo, Uo, W.q[(size_t)e * n3 + pm], Um, abar, F);
+          twopoint_flux(O.vol_flux, P.gamma, qo, Uo, W.q[(size_t)e * n3 + pm], Um, abar, F);
           for (int v = 0; v < 5; ++v) V[v] += 2.0 * Dim * F[v];
           if (O.viscous)
             for (int v = 0; v < 5; ++v) V[v] -= Dim * W.G[((size_t)e * n3 + pm) * 15 + dir * 5 + v];
@@ -1076,6 +1110,7 @@ static Phys<Dual> dual_phys(const Phys<real>& P, real dk, real dB) {
   Q.gamma = P.gamma; Q.R = P.R; Q.mu = P.mu; Q.Pr = P.Pr;
   for (int c = 0; c < 3; ++c) Q.f[c] = P.f[c];
   Q.kappa = Dual(P.kappa, dk); Q.B = Dual(P.B, dB); Q.hwm = P.hwm;
+  Q.suth_S = P.suth_S; Q.T_ref = P.T_ref;
   return Q;
 }
 
@@ -1145,6 +1180,7 @@ static void* create_impl(int N, int K, const double* X, const int* nbr, const do
   c->P.gamma = phys[0]; c->P.R = phys[1]; c->P.mu = phys[2]; c->P.Pr = phys[3];
   c->P.f[0] = phys[4]; c->P.f[1] = phys[5]; c->P.f[2] = phys[6];
   c->P.kappa = phys[7]; c->P.B = phys[8]; c->P.hwm = phys[9];
+  c->P.suth_S = phys[10]; c->P.T_ref = phys[11];
   c->O.vol_flux = opts[0]; c->O.surf_flux = opts[1]; c->O.viscous = opts[2]; c->O.law = opts[3];
   std::string e;
   bool ok = check_connectivity(M, e) && build_metrics(M, e) && build_wall_samples(M, c->P.hwm, e);
@@ -1305,6 +1341,7 @@ int ora_wall_flux(const double* phys, int law, const double* U5, const double* n
   Phys<real> P;
   P.gamma = phys[0]; P.R = phys[1]; P.mu = phys[2]; P.Pr = phys[3];
   P.kappa = phys[7]; P.B = phys[8]; P.hwm = phys[9];
+  P.suth_S = phys[10]; P.T_ref = phys[11];
   real u[5], nh[3], f[3], t[3];
   for (int v = 0; v < 5; ++v) u[v] = U5[v];
   for (int c = 0; c < 3; ++c) nh[c] = nout[c];
@@ -1312,6 +1349,13 @@ int ora_wall_flux(const double* phys, int law, const double* U5, const double* n
   int st = wall_flux(P, law, q, nh, f, t);
   for (int c = 0; c < 3; ++c) { fm[c] = (double)f[c]; tau[c] = (double)t[c]; }
   return st;
+}
+
+// Dynamic viscosity at temperature T (tests).
+double ora_viscosity(const double* phys, double T) {
+  Phys<real> P;
+  P.mu = phys[2]; P.suth_S = phys[10]; P.T_ref = phys[11];
+  return (double)viscosity(P, (real)T);
 }
 
 // Single numerical flux evaluation (tests): returns F*(UL, UR; nh).

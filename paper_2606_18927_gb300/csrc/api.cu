@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -31,6 +32,11 @@ struct dg_ctx {
   dg::PhysDev ph{};
   cudaStream_t stream = nullptr;
   int device = 0;
+  // side stream (highest priority) for the wall-model kernel, forked from and
+  // joined back into the caller's stream around each operator evaluation
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+  bool overlap = false;
   dg::Geometry geo;
   // device storage
   double* U = nullptr;
@@ -69,6 +75,10 @@ struct dg_ctx {
   double* gWf = nullptr;
   double* gUs = nullptr;
   double* gtheta = nullptr;
+  // CUDA graph of one full LSERK4 step (five stages), captured for a given dt
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t step_graph = nullptr;
+  double step_graph_dt = 0.0;
   // optional per-kernel timing: 5 events per operator evaluation
   bool profiling = false;
   std::vector<cudaEvent_t> events;
@@ -98,6 +108,15 @@ cudaError_t alloc(T** p, size_t count) {
 void free_all(dg_ctx* c) {
   for (cudaEvent_t ev : c->events) cudaEventDestroy(ev);
   c->events.clear();
+  if (c->step_graph) cudaGraphExecDestroy(c->step_graph);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  c->step_graph = nullptr;
+  c->cap_stream = nullptr;
+  if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+  if (c->join_ev) cudaEventDestroy(c->join_ev);
+  if (c->side) cudaStreamDestroy(c->side);
+  c->fork_ev = c->join_ev = nullptr;
+  c->side = nullptr;
   void* ptrs[] = {c->U, c->dU, c->io, c->io2, c->Ja, c->invJ, c->fgeo, c->nbr, c->elem_face, c->faces,
                   c->ws_elem, c->ws_lag, c->Rv, c->Gf, c->Fs, c->tau, c->status,
                   c->gUf, c->gGf, c->gWf, c->gUs, c->gtheta, c->wq, c->ro_ckpt, c->ro_stage, c->ro_work,
@@ -105,6 +124,9 @@ void free_all(dg_ctx* c) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
+
+// profiling events per operator evaluation (see OpArgs::ev)
+constexpr size_t kEventsPerLaunch = 7;
 
 int launch(dg_ctx* c, const double* Uin, int mode, double* Out, double A, double B, double dt, int read_dU,
            double* Uout, double* dU = nullptr) {
@@ -118,9 +140,10 @@ int launch(dg_ctx* c, const double* Uin, int mode, double* Out, double A, double
   a.mode = mode; a.Out = Out; a.dU = dU ? dU : c->dU; a.Uout = Uout;
   a.A = A; a.B = B; a.dt = dt; a.read_dU = read_dU;
   a.ev = nullptr;
+  if (c->overlap && c->side) { a.side = c->side; a.fork = c->fork_ev; a.join = c->join_ev; }
   if (c->profiling) {
-    if (c->events_used + 5 > c->events.size()) {
-      for (int x = 0; x < 5 * 64; ++x) {
+    if (c->events_used + kEventsPerLaunch > c->events.size()) {
+      for (int x = 0; x < kEventsPerLaunch * 64; ++x) {
         cudaEvent_t ev;
         cudaError_t e = cudaEventCreate(&ev);
         if (e != cudaSuccess) return cuda_fail(c, e, "profiling events");
@@ -128,7 +151,7 @@ int launch(dg_ctx* c, const double* Uin, int mode, double* Out, double A, double
       }
     }
     a.ev = &c->events[c->events_used];
-    c->events_used += 5;
+    c->events_used += kEventsPerLaunch;
   }
   int rc = dg::run_operator(a, c->ph, c->stream);
   if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "kernel launch");
@@ -263,7 +286,9 @@ int dg_init_mesh(dg_ctx** out, const dg_mesh_desc* m, const dg_phys* p, const dg
   if (m->K < 1 || !m->X || !m->nbr) return fail(nullptr, DG_ERR_ARG, "dg_init_mesh: empty mesh");
   if (o->precision != DG_FP64 && o->precision != DG_FP32_MIXED)
     return fail(nullptr, DG_ERR_ARG, "dg_init_mesh: bad precision");
-  if (o->vol_flux < 0 || o->vol_flux > 1) return fail(nullptr, DG_ERR_ARG, "dg_init_mesh: bad vol_flux");
+  if (o->vol_flux < 0 || o->vol_flux > 2) return fail(nullptr, DG_ERR_ARG, "dg_init_mesh: bad vol_flux");
+  if (p->suth_S > 0.0 && !(p->T_ref > 0.0))
+    return fail(nullptr, DG_ERR_ARG, "dg_init_mesh: Sutherland's law needs T_ref > 0");
   if (o->surf_flux < 0 || o->surf_flux > 2) return fail(nullptr, DG_ERR_ARG, "dg_init_mesh: bad surf_flux");
   if (p->law < 0 || p->law > 1) return fail(nullptr, DG_ERR_ARG, "dg_init_mesh: bad wall law");
   if (!(p->gamma > 1.0) || !(p->R > 0.0) || !(p->mu >= 0.0) || !(p->Pr > 0.0))
@@ -284,6 +309,9 @@ int dg_init_mesh(dg_ctx** out, const dg_mesh_desc* m, const dg_phys* p, const dg
   dg::PhysDev& ph = c->ph;
   ph.gamma = p->gamma; ph.gm1 = p->gamma - 1.0; ph.R = p->R; ph.mu = p->mu; ph.Pr = p->Pr;
   ph.cp = p->gamma * p->R / (p->gamma - 1.0); ph.kcond = p->mu * ph.cp / p->Pr; ph.rcp_R = 1.0 / p->R;
+  ph.rgm1 = 1.0 / (p->gamma - 1.0); ph.cp_Pr = ph.cp / p->Pr;
+  ph.suth_S = p->suth_S > 0.0 ? p->suth_S : 0.0;
+  ph.suth_C = ph.suth_S > 0.0 ? p->mu * (p->T_ref + p->suth_S) / (p->T_ref * std::sqrt(p->T_ref)) : 0.0;
   ph.p_ref = p->p_ref;
   for (int d = 0; d < 3; ++d) ph.f[d] = p->force[d];
   ph.kappa = p->kappa; ph.B = p->B; ph.hwm = p->hwm; ph.law = p->law;
@@ -359,6 +387,14 @@ int dg_init_mesh(dg_ctx** out, const dg_mesh_desc* m, const dg_phys* p, const dg
     chk(alloc(&c->wq, wq.size()));
     chk(cudaMemcpy(c->wq, wq.data(), wq.size() * sizeof(double), cudaMemcpyHostToDevice));
   }
+  if (c->geo.n_wall) {
+    // the wall-model kernel's side stream, at the device's highest priority
+    int least = 0, greatest = 0;
+    chk(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    chk(cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, greatest));
+    chk(cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming));
+    chk(cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming));
+  }
   chk(cudaMemset(c->status, 0, sizeof(int)));
   chk(cudaMemset(c->dU, 0, 5 * S * sizeof(double)));
   if (e != cudaSuccess) { free_all(c); delete c; return cuda_fail(nullptr, e, "dg_init_mesh: upload"); }
@@ -377,6 +413,12 @@ int dg_destroy(dg_ctx* c) {
 int dg_set_stream(dg_ctx* c, void* stream) {
   if (!c) return DG_ERR_ARG;
   c->stream = static_cast<cudaStream_t>(stream);
+  return DG_OK;
+}
+
+int dg_set_overlap(dg_ctx* c, int enable) {
+  if (!c) return DG_ERR_ARG;
+  c->overlap = enable != 0;
   return DG_OK;
 }
 
@@ -462,8 +504,18 @@ int dg_set_params(dg_ctx* c, double kappa, double B) {
   return DG_OK;
 }
 
+// the device scalar of the reductions (time step, kinetic energy, losses)
+static int ensure_scalar(dg_ctx* c) {
+  if (c->ro_scalar) return DG_OK;
+  cudaError_t e = alloc(&c->ro_scalar, 1);
+  if (e != cudaSuccess) return cuda_fail(c, e, "reduction scalar allocation");
+  return DG_OK;
+}
+
 static int ensure_adjoint_scratch(dg_ctx* c) {
   if (c->gUf) return DG_OK;
+  int rc = ensure_scalar(c);
+  if (rc != DG_OK) return rc;
   cudaError_t e = cudaSuccess;
   auto chk = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
   const size_t kn2 = (size_t)c->K * 6 * c->n2;
@@ -472,7 +524,6 @@ static int ensure_adjoint_scratch(dg_ctx* c) {
   chk(alloc(&c->gWf, 4 * kn2));
   chk(alloc(&c->gUs, (size_t)c->geo.n_wall * c->n2 * 5 + 1));
   chk(alloc(&c->gtheta, 2));
-  chk(alloc(&c->ro_scalar, 1));
   if (e != cudaSuccess) return cuda_fail(c, e, "adjoint scratch allocation");
   return DG_OK;
 }
@@ -493,6 +544,8 @@ static int check_adjoint_options(dg_ctx* c, const char* who) {
     return fail(c, DG_ERR_NOT_IMPLEMENTED, std::string(who) + ": the adjoint is available for FP64 contexts");
   if (c->opts.vol_flux != DG_VOL_KEP_PIROZZOLI)
     return fail(c, DG_ERR_NOT_IMPLEMENTED, std::string(who) + ": the adjoint needs the Pirozzoli volume flux");
+  if (c->phys.suth_S > 0.0)
+    return fail(c, DG_ERR_NOT_IMPLEMENTED, std::string(who) + ": the adjoint needs a constant viscosity");
   return DG_OK;
 }
 
@@ -500,7 +553,7 @@ int dg_time_step(dg_ctx* c, const double* U, double cfl, double* dt) {
   if (!c || !dt || !(cfl > 0.0)) return c ? fail(c, DG_ERR_ARG, "dg_time_step: bad argument") : DG_ERR_ARG;
   const double* Uin = U ? U : c->U;
   if (!U && !c->state_set) return fail(c, DG_ERR_NOT_INIT, "dg_time_step: state not set");
-  int rc = ensure_adjoint_scratch(c);
+  int rc = ensure_scalar(c);
   if (rc != DG_OK) return rc;
   unsigned long long* slot = reinterpret_cast<unsigned long long*>(c->ro_scalar);
   cudaError_t e = cudaMemsetAsync(slot, 0, sizeof(double), c->stream);
@@ -538,7 +591,7 @@ int dg_kinetic_energy(dg_ctx* c, const double* U, double* ke) {
     if (e == cudaSuccess) e = cudaMemcpy(c->wJ, w.data(), c->S * sizeof(double), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(c, e, "dg_kinetic_energy: weights");
   }
-  int rc = ensure_adjoint_scratch(c);
+  int rc = ensure_scalar(c);
   if (rc != DG_OK) return rc;
   e = cudaMemsetAsync(c->ro_scalar, 0, sizeof(double), c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "dg_kinetic_energy");
@@ -556,7 +609,7 @@ int dg_wall_shear(dg_ctx* c, const double* U, double* loss) {
   if (c->geo.n_wall == 0 || !c->opts.viscous) return fail(c, DG_ERR_ARG, "dg_wall_shear: no wall-modelled walls");
   const double* Uin = U ? U : c->U;
   if (!U && !c->state_set) return fail(c, DG_ERR_NOT_INIT, "dg_wall_shear: state not set");
-  int rc = ensure_adjoint_scratch(c);
+  int rc = ensure_scalar(c);
   if (rc != DG_OK) return rc;
   cudaError_t e = cudaMemsetAsync(c->ro_scalar, 0, sizeof(double), c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "dg_wall_shear");
@@ -679,6 +732,49 @@ int dg_set_rk_register(dg_ctx* c, const double* dU, int on_device) {
   return DG_OK;
 }
 
+int dg_rk_steps_graph(dg_ctx* c, double t, double dt, int nsteps) {
+  (void)t;  // the operator is autonomous
+  if (!c || nsteps < 0) return c ? fail(c, DG_ERR_ARG, "dg_rk_steps_graph: nsteps < 0") : DG_ERR_ARG;
+  if (!c->state_set) return fail(c, DG_ERR_NOT_INIT, "dg_rk_steps_graph: state not set");
+  cudaError_t e = cudaSuccess;
+  if (!c->step_graph || c->step_graph_dt != dt) {
+    if (!c->cap_stream) {
+      e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+      if (e != cudaSuccess) return cuda_fail(c, e, "dg_rk_steps_graph: stream");
+    }
+    // the capture stream must see the caller's pending work on the state
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "dg_rk_steps_graph");
+    const bool prof = c->profiling;
+    cudaStream_t user = c->stream;
+    c->profiling = false;
+    c->stream = c->cap_stream;
+    e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+    int rc = DG_OK;
+    if (e == cudaSuccess)
+      for (int s = 0; s < 5 && rc == DG_OK; ++s)
+        rc = launch(c, c->U, 1, nullptr, kRkA[s], kRkB[s], dt, s > 0 ? 1 : 0, c->U);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &graph);
+    c->stream = user;
+    c->profiling = prof;
+    if (e == cudaSuccess) e = e2;
+    if (rc != DG_OK) { if (graph) cudaGraphDestroy(graph); return rc; }
+    if (e != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return cuda_fail(c, e, "dg_rk_steps_graph: capture"); }
+    if (c->step_graph) cudaGraphExecDestroy(c->step_graph);
+    c->step_graph = nullptr;
+    e = cudaGraphInstantiate(&c->step_graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) { c->step_graph = nullptr; return cuda_fail(c, e, "dg_rk_steps_graph: instantiate"); }
+    c->step_graph_dt = dt;
+  }
+  for (int it = 0; it < nsteps; ++it) {
+    e = cudaGraphLaunch(c->step_graph, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "dg_rk_steps_graph: launch");
+  }
+  return DG_OK;
+}
+
 int dg_check_status(dg_ctx* c) {
   if (!c) return DG_ERR_ARG;
   int h = 0;
@@ -705,10 +801,12 @@ int dg_profile_read(dg_ctx* c, double* ms, int* launches) {
   if (e != cudaSuccess) return cuda_fail(c, e, "dg_profile_read");
   const bool visc = c->opts.viscous != 0;
   const bool work[4] = {visc, c->geo.n_interior > 0, c->geo.n_wall > 0, true};
-  for (size_t b = 0; b + 5 <= c->events_used; b += 5)
+  // lift [0,1], face [1,2], wall [3,4], volume [5,6]
+  const int from[4] = {0, 1, 3, 5}, to[4] = {1, 2, 4, 6};
+  for (size_t b = 0; b + kEventsPerLaunch <= c->events_used; b += kEventsPerLaunch)
     for (int k = 0; k < 4; ++k) {
       float t = 0.0f;
-      e = cudaEventElapsedTime(&t, c->events[b + k], c->events[b + k + 1]);
+      e = cudaEventElapsedTime(&t, c->events[b + from[k]], c->events[b + to[k]]);
       if (e != cudaSuccess) return cuda_fail(c, e, "dg_profile_read");
       ms[k] += t;
       if (work[k]) launches[k] += 1;

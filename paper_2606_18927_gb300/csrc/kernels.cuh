@@ -19,13 +19,19 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 namespace dg {
 
 enum { ST_NONFINITE = 1, ST_WM_NOCONV = 2 };
 
 struct PhysDev {
   double gamma, gm1, R, mu, Pr, cp, kcond, rcp_R;
-  double p_ref;  // constant removed from p in the momentum fluxes
+  double rgm1;    // 1 / (gamma - 1)
+  double cp_Pr;   // cp / Pr: conductivity per unit viscosity
+  double suth_S;  // Sutherland constant (> 0: mu(T) = suth_C T^(3/2) / (T + S))
+  double suth_C;  // mu_ref (T_ref + S) / T_ref^(3/2)
+  double p_ref;   // constant removed from p in the momentum fluxes
   double f[3];
   double kappa, B, hwm;
   int law, vol_flux, surf_flux, viscous;
@@ -76,6 +82,71 @@ __device__ __forceinline__ double rcp_pos(double x) {
   return r;
 }
 
+template <typename R>
+__device__ __forceinline__ R rcp_t(R x);
+template <>
+__device__ __forceinline__ double rcp_t<double>(double x) { return rcp_pos(x); }
+template <>
+__device__ __forceinline__ float rcp_t<float>(float x) { return __frcp_rn(x); }
+
+// Dynamic viscosity at temperature T: constant mu, or Sutherland's law
+// mu_ref (T / T_ref)^(3/2) (T_ref + S) / (T + S) (the paper's Sec. 4 gas model).
+template <typename R>
+__device__ __forceinline__ R sutherland(const PhysDev& ph, R T) {
+  return (R)ph.suth_C * T * sqrt(T) / (T + (R)ph.suth_S);
+}
+
+// Logarithmic mean L(a, b) = (a - b) / ln(a / b) of two positive numbers,
+// needed by the entropy-conserving flux, written through s = a + b and
+// u = ((a - b) / (a + b))^2.  With f = (a - b) / (a + b), ln(a / b) =
+// 2 artanh(f) = 2 f (1 + u/3 + u^2/5 + u^3/7 + ...), so
+//   L = (s / 2) g(u),  g = f / artanh(f) = 1 - u/3 - 4u^2/45 - 44u^3/945 - ...
+//   1 / L = (2 / s) P(u),  P = artanh(f) / f = 1 + u/3 + u^2/5 + u^3/7 + ...
+// Truncated after u^3 the series are exact to rounding for u below LOGMEAN_CUT
+// (next terms 0.03 u^4 and u^4 / 9); above it the logarithm is evaluated.
+template <typename R>
+struct LogMeanCut;
+template <>
+struct LogMeanCut<double> { static constexpr double v = 1e-4; };
+template <>
+struct LogMeanCut<float> { static constexpr float v = 1e-2f; };
+
+template <typename R>
+__device__ __forceinline__ R logmean_g(R u) {  // f / artanh(f)
+  return R(1) - u * (R(1.0 / 3.0) + u * (R(4.0 / 45.0) + u * R(44.0 / 945.0)));
+}
+template <typename R>
+__device__ __forceinline__ R logmean_P(R u) {  // artanh(f) / f
+  return R(1) + u * (R(1.0 / 3.0) + u * (R(1.0 / 5.0) + u * R(1.0 / 7.0)));
+}
+
+// ln(a / b) / (2 f) for the slow branch: artanh(f) / f from the logarithm
+template <typename R>
+__device__ __forceinline__ R logmean_P_slow(R a, R b) {
+  const R d = a - b;
+  return log1p(d / b) * (a + b) / (R(2) * d);
+}
+
+// The volume kernel evaluates the same means without a division per pair,
+// through t = (a - b)^2 / (4 a b) = sinh^2(l / 2), l = ln(a / b), formed from
+// per-node reciprocals.  With s = asinh(sqrt(t)):
+//   L = ((a + b) / 2) G(t),        G = tanh(s) / s
+//   1 / L = ((1/a + 1/b) / 2) Q(t), Q = 2 s / sinh(2 s)
+//   1 / (a + b) = ((1/a + 1/b) / 4) / (1 + t)
+// Series through t^4 (the t^5 terms are below 0.4 t^5).
+template <typename R>
+__device__ __forceinline__ R logmean_G(R t) {
+  return R(1) + t * (R(-1.0 / 3.0) + t * (R(11.0 / 45.0) + t * (R(-191.0 / 945.0) + t * R(2497.0 / 14175.0))));
+}
+template <typename R>
+__device__ __forceinline__ R logmean_Q(R t) {
+  return R(1) + t * (R(-2.0 / 3.0) + t * (R(8.0 / 15.0) + t * (R(-16.0 / 35.0) + t * R(128.0 / 315.0))));
+}
+template <typename R>
+__device__ __forceinline__ R inv_one_plus(R t) {
+  return R(1) + t * (R(-1) + t * (R(1) + t * (R(-1) + t)));
+}
+
 __device__ __forceinline__ bool finite_bits(double x) {
   const unsigned hi = (unsigned)(__double_as_longlong(x) >> 32);
   return (hi & 0x7ff00000u) != 0x7ff00000u;
@@ -106,6 +177,8 @@ __device__ __forceinline__ Prim<R> primitive(const double U0, const double U1, c
 
 // Mixed form: everything in FP32 except the pressure recovery, whose
 // cancellation E - rho |u|^2 / 2 is taken in FP64 (two FP64 operations).
+// (Forming the velocity in FP64 and rounding it once lowers the Ut error by
+// only ~4 % and costs 40 % of the mixed path's time: not done.)
 template <>
 __device__ __forceinline__ Prim<float> primitive<float>(const double U0, const double U1, const double U2,
                                                         const double U3, const double U4, const PhysDev& ph) {
@@ -141,10 +214,49 @@ __device__ __forceinline__ void velocity_temperature<float>(const double U0, con
   T = (q.p + (float)ph.p_ref) * (float)ph.rcp_R / q.rho;
 }
 
-// Two-point KEP flux F#(L, R) . a (a need not be unit).
+// Entropy-conserving two-point flux of Chandrashekar (the paper's Sec. 4
+// volume flux) along a (a need not be unit), with beta = rho / (2 p):
+//   F_rho = ln-mean(rho) {u}.a,  F_m = p~ a + {u} F_rho,
+//   F_E = F_rho (1 / (2 (gamma - 1) ln-mean(beta)) - {|u|^2} / 2) + {u} . F_m,
+//   p~ = {rho} / (2 {beta}).
+// The momentum flux carries p~ - p_ref = (bA p'A + bB p'B) / (bA + bB)
+// (p' = p - p_ref), the same value without the O(p_ref) cancellation.
+template <typename R>
+__device__ __forceinline__ void twopoint_ec(const Prim<R>& A, const Prim<R>& B, R a0, R a1, R a2, R F[5],
+                                            const PhysDev& ph) {
+  const R pref = (R)ph.p_ref;
+  const R bA = A.rho * rcp_t<R>(R(2) * (A.p + pref)), bB = B.rho * rcp_t<R>(R(2) * (B.p + pref));
+  const R sr = A.rho + B.rho, dr = A.rho - B.rho, sb = bA + bB, db = bA - bB;
+  const R rr = rcp_t<R>(sr), rb = rcp_t<R>(sb);
+  const R ur = (dr * rr) * (dr * rr), ub = (db * rb) * (db * rb);
+  const R rho_ln = ur < LogMeanCut<R>::v ? R(0.5) * sr * logmean_g<R>(ur) : dr / log1p(dr / B.rho);
+  const R Pb = ub < LogMeanCut<R>::v ? logmean_P<R>(ub) : logmean_P_slow<R>(bA, bB);
+  const R u = R(0.5) * (A.u + B.u), v = R(0.5) * (A.v + B.v), w = R(0.5) * (A.w + B.w);
+  const R ua = u * a0 + v * a1 + w * a2;
+  const R pt = (bA * A.p + bB * B.p) * rb;  // p~ - p_ref
+  const R f0 = rho_ln * ua;
+  F[0] = f0;
+  F[1] = f0 * u + pt * a0;
+  F[2] = f0 * v + pt * a1;
+  F[3] = f0 * w + pt * a2;
+  const R k2 = R(0.25) * (A.u * A.u + A.v * A.v + A.w * A.w + B.u * B.u + B.v * B.v + B.w * B.w);
+  // 1 / (2 (gamma - 1) beta_ln) = rb P / (gamma - 1)
+  F[4] = f0 * (rb * Pb * (R)ph.rgm1 + (u * u + v * v + w * w) - k2) + (pt + pref) * ua;
+}
+
+// Two-point KEP flux F#(L, R) . a (a need not be unit); kind 2 is the
+// entropy-conserving flux above (FP64 and FP32 only: the adjoint covers the
+// KEP fluxes).
 template <typename R>
 __device__ __forceinline__ void twopoint(int kind, const Prim<R>& A, const Prim<R>& B, R a0, R a1, R a2,
-                                         R F[5], R pref) {
+                                         R F[5], const PhysDev& ph) {
+  if constexpr (std::is_same<R, double>::value || std::is_same<R, float>::value) {
+    if (kind == 2) {
+      twopoint_ec<R>(A, B, a0, a1, a2, F, ph);
+      return;
+    }
+  }
+  const R pref = (R)ph.p_ref;
   const R rho = R(0.5) * (A.rho + B.rho);
   const R u = R(0.5) * (A.u + B.u), v = R(0.5) * (A.v + B.v), w = R(0.5) * (A.w + B.w);
   const R p = R(0.5) * (A.p + B.p);
@@ -168,7 +280,7 @@ template <typename R, typename S>
 __device__ __forceinline__ void riemann(const PhysDev& ph, const Prim<R>& A, const S UA[5],
                                         const Prim<R>& B, const S UB[5], R nx, R ny, R nz, R F[5]) {
   const R pref = (R)ph.p_ref;
-  twopoint<R>(ph.vol_flux, A, B, nx, ny, nz, F, pref);
+  twopoint<R>(ph.vol_flux, A, B, nx, ny, nz, F, ph);
   const R g = (R)ph.gamma;
   if (ph.surf_flux == 1) {  // local Lax-Friedrichs (sound speed from the full pressure)
     const R cA = sqrt(g * (A.p + pref) / A.rho), cB = sqrt(g * (B.p + pref) / B.rho);
@@ -295,7 +407,8 @@ static __device__ void wall_stress(const PhysDev& ph, const double Us[5], double
   const double rhow = rho * T / Tw;
   const double a = sqrt(r / (2.0 * ph.cp * Tw));
   const double uvd = asin(a * um) / a;
-  const double ut = solve_utau(ph.law, uvd, ph.hwm, ph.mu / rhow, ph.kappa, ph.B, ok);
+  const double muw = ph.suth_S > 0.0 ? sutherland<double>(ph, Tw) : ph.mu;
+  const double ut = solve_utau(ph.law, uvd, ph.hwm, muw / rhow, ph.kappa, ph.B, ok);
   const double tw = rhow * ut * ut / um;
   tau[0] = tw * ux; tau[1] = tw * uy; tau[2] = tw * uz;
 }
@@ -402,7 +515,11 @@ k_lift(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
 #pragma unroll
     for (int v = 0; v < 4; ++v) q[d][v] *= iJ;
   // viscous flux Fv_d = (0, tau_1d, tau_2d, tau_3d, tau_jd u_j + k dT/dx_d)
-  const R mu = (R)ph.mu, kc = (R)ph.kcond;
+  R mu = (R)ph.mu, kc = (R)ph.kcond;
+  if (ph.suth_S > 0.0) {
+    mu = sutherland<R>(ph, sW[3 * n3 + p]);
+    kc = mu * (R)ph.cp_Pr;
+  }
   const R div = q[0][0] + q[1][1] + q[2][2];
   R tau[3][3];
 #pragma unroll
@@ -568,6 +685,9 @@ k_wall(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, R* __
 // a shared-memory residual.  With per-node sums S_x = x_i + x_m the flux is
 // F0 * 8 = S_rho (S_u . S_a) and F1..4 * 16 = m S_u + S_p4 S_a, m S_h, so
 // the scale factors fold into the coefficient tables (DVS/8 and DVS/16).
+// EC selects the entropy-conserving flux; its nodes hold (rho, u, v, w,
+// 8 beta p', beta, |u|^2, 1 / beta, 1 / rho) and each pair takes two
+// logarithmic means (series in t, or the logarithm for far-apart values).
 // ---------------------------------------------------------------------------
 struct StageArgs {
   double A, B, dt;
@@ -581,12 +701,13 @@ struct VolShape {
   static constexpr int WARPS_LINES = (n2 + LPW - 1) / LPW;  // warps for one direction
   static constexpr int WARPS_NODES = (n3 + 31) / 32;
   static constexpr int THREADS = 32 * (WARPS_LINES > WARPS_NODES ? WARPS_LINES : WARPS_NODES);
-  // shared memory (in units of R): 7 prim slots, 9 metric, 5 residual per node,
-  // two coefficient tables, 1/w
+  // shared memory (in units of R): 7 prim slots (9 with the entropy-
+  // conserving flux), 9 metric, 5 residual per node, two coefficient tables, 1/w
   static constexpr int SMEM_R = 21 * n3 + 2 * n2 + n;
+  static constexpr int SMEM_R_EC = 23 * n3 + 2 * n2 + n;
 };
 
-template <int N, typename R, int MODE>
+template <int N, typename R, int MODE, bool EC>
 __global__ void __launch_bounds__(VolShape<N>::THREADS)
 k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, const Tables<N> tab,
          const R* __restrict__ Rv, const R* __restrict__ Fs, double* __restrict__ Out,
@@ -594,8 +715,9 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
   using Sh = VolShape<N>;
   constexpr int n = Sh::n, n2 = Sh::n2, n3 = Sh::n3, T = Sh::THREADS, LPW = Sh::LPW;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  R* sQ = reinterpret_cast<R*>(smem_raw);  // [7][n3]: rho u v w 4p' h|e 2p (KG)
-  R* sA = sQ + 7 * n3;                      // [9][n3]: Ja (dir*3+comp)
+  constexpr int QS = EC ? 9 : 7;
+  R* sQ = reinterpret_cast<R*>(smem_raw);  // [QS][n3]: rho u v w 4p' h|e 2p (KG); EC see above
+  R* sA = sQ + QS * n3;                     // [9][n3]: Ja (dir*3+comp)
   R* sR = sA + 9 * n3;                      // [5][n3]: residual
   R* sC8 = sR + 5 * n3;                     // [n2]: DVS / 8
   R* sC16 = sC8 + n2;                       // [n2]: DVS / 16
@@ -617,7 +739,16 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
     const Prim<R> q = primitive<R>(Uo[0], Uo[1], Uo[2], Uo[3], Uo[4], ph);
     sQ[t] = q.rho; sQ[n3 + t] = q.u; sQ[2 * n3 + t] = q.v; sQ[3 * n3 + t] = q.w;
     sQ[4 * n3 + t] = R(4) * q.p;
-    if (!kg) {
+    if constexpr (EC) {
+      const R pf = q.p + (R)ph.p_ref;
+      const R beta = R(0.5) * q.rho * rcp_t<R>(pf);
+      const R irho = rcp_t<R>(q.rho);
+      sQ[4 * n3 + t] = R(8) * beta * q.p;
+      sQ[5 * n3 + t] = beta;
+      sQ[6 * n3 + t] = q.u * q.u + q.v * q.v + q.w * q.w;
+      sQ[7 * n3 + t] = R(2) * pf * irho;  // 1 / beta
+      sQ[8 * n3 + t] = irho;
+    } else if (!kg) {
       sQ[5 * n3 + t] = q.h;
     } else {
       const R pf = q.p + (R)ph.p_ref;
@@ -645,7 +776,8 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
       const int me = node(pos);
       const R rho = sQ[me], u = sQ[n3 + me], v = sQ[2 * n3 + me], w = sQ[3 * n3 + me];
       const R p4 = sQ[4 * n3 + me], hh = sQ[5 * n3 + me];
-      const R p2 = kg ? sQ[6 * n3 + me] : R(0);
+      const R p2 = (kg || EC) ? sQ[6 * n3 + me] : R(0);
+      const R ib = EC ? sQ[7 * n3 + me] : R(0), irh = EC ? sQ[8 * n3 + me] : R(0);
       const R a0 = sA[(dir * 3 + 0) * n3 + me], a1 = sA[(dir * 3 + 1) * n3 + me],
               a2 = sA[(dir * 3 + 2) * n3 + me];
       R acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0, acc4 = 0;
@@ -653,17 +785,45 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
       for (int d = 1; d <= n / 2; ++d) {
         const int pm = pos + d < n ? pos + d : pos + d - n;
         const int q = node(pm);
-        const R Sr = rho + sQ[q], Su = u + sQ[n3 + q], Sv = v + sQ[2 * n3 + q], Sw = w + sQ[3 * n3 + q];
-        const R Sp = p4 + sQ[4 * n3 + q], Sh = hh + sQ[5 * n3 + q];
+        const R rq = sQ[q];
+        const R Sr = rho + rq, Su = u + sQ[n3 + q], Sv = v + sQ[2 * n3 + q], Sw = w + sQ[3 * n3 + q];
+        const R Sp = p4 + sQ[4 * n3 + q];
         const R Sa0 = a0 + sA[(dir * 3 + 0) * n3 + q], Sa1 = a1 + sA[(dir * 3 + 1) * n3 + q],
                 Sa2 = a2 + sA[(dir * 3 + 2) * n3 + q];
-        const R ua = Su * Sa0 + Sv * Sa1 + Sw * Sa2;
-        const R mf = Sr * ua;                 // 8 F0
-        const R F1 = mf * Su + Sp * Sa0;      // 16 F1
-        const R F2 = mf * Sv + Sp * Sa1;
-        const R F3 = mf * Sw + Sp * Sa2;
-        R F4 = mf * Sh;                       // 16 F4
-        if (kg) F4 += (p2 + sQ[6 * n3 + q]) * ua;
+        const R ua = Su * Sa0 + Sv * Sa1 + Sw * Sa2;  // 4 {u}.{a}
+        R mf, F1, F2, F3, F4;
+        if constexpr (EC) {
+          // rho_ln = Sr G / 2; 1 / beta_ln = Sib Q / 2; 1 / (bA + bB) = Sib Rb / 4
+          const R bq = sQ[5 * n3 + q], ibq = sQ[7 * n3 + q];
+          const R Dr = rho - rq, Db = hh - bq, Sib = ib + ibq;
+          const R tr = R(0.25) * Dr * Dr * (irh * sQ[8 * n3 + q]);
+          const R tb = R(0.25) * Db * Db * (ib * ibq);
+          const R G = tr < LogMeanCut<R>::v ? logmean_G<R>(tr) : R(2) * Dr / (Sr * log1p(Dr / rq));
+          R Q, Rb;
+          if (tb < LogMeanCut<R>::v) {
+            Q = logmean_Q<R>(tb);
+            Rb = inv_one_plus<R>(tb);
+          } else {
+            Q = R(2) * log1p(Db / bq) / (Db * Sib);
+            Rb = R(4) / (Sib * (hh + bq));
+          }
+          mf = Sr * G * ua;                    // 8 F_rho
+          const R Spt = R(0.25) * Sib * Rb * Sp;  // 8 (p~ - p_ref)
+          F1 = mf * Su + Spt * Sa0;            // 16 F_m
+          F2 = mf * Sv + Spt * Sa1;
+          F3 = mf * Sw + Spt * Sa2;
+          // 16 F_E = 2 mf (1 / (2 (gamma-1) beta_ln) + |{u}|^2 - {|u|^2} / 2) + 4 p~ (4 {u}.{a})
+          const R X = R(0.25) * (Sib * Q * (R)ph.rgm1 + Su * Su + Sv * Sv + Sw * Sw - p2 - sQ[6 * n3 + q]);
+          F4 = R(2) * mf * X + (R(0.5) * Spt + R(4) * (R)ph.p_ref) * ua;
+        } else {
+          const R Sh = hh + sQ[5 * n3 + q];
+          mf = Sr * ua;                        // 8 F0
+          F1 = mf * Su + Sp * Sa0;             // 16 F1
+          F2 = mf * Sv + Sp * Sa1;
+          F3 = mf * Sw + Sp * Sa2;
+          F4 = mf * Sh;                        // 16 F4
+          if (kg) F4 += (p2 + sQ[6 * n3 + q]) * ua;
+        }
         const R c8 = sC8[pos * n + pm], c16 = sC16[pos * n + pm];
         acc0 += c8 * mf; acc1 += c16 * F1; acc2 += c16 * F2; acc3 += c16 * F3; acc4 += c16 * F4;
         if (2 * d != n) {

@@ -32,7 +32,12 @@ struct OpArgs {
   double* Uout;
   double A, B, dt;
   int read_dU;
-  cudaEvent_t* ev;          // null, or 5 events recorded around lift, face, wall, volume
+  cudaEvent_t* ev;          // null, or 7 events: lift [0,1], face [1,2], wall [3,4], volume [5,6]
+  // optional side stream for the wall-model kernel: it forks from the main
+  // stream before the lifting and joins it before the volume kernel (the
+  // paper's prioritised boundary work, Sec. 2.3); null side: one stream
+  cudaStream_t side;
+  cudaEvent_t fork, join;
   // adjoint (FP64): cotangent lam of Ut, output gU, and scratch
   const double* lam;
   double* gU;

@@ -38,12 +38,36 @@ static int run_typed(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {
   R* Gf = static_cast<R*>(a.Gf);
   R* Fs = static_cast<R*>(a.Fs);
   const size_t smem_lift = (size_t)(16 * n3 + 26 * n2 + n) * sizeof(R);
-  const size_t smem_vol = (size_t)VolShape<N>::SMEM_R * sizeof(R);
+  const size_t smem_vol = (size_t)(ph.vol_flux == 2 ? VolShape<N>::SMEM_R_EC : VolShape<N>::SMEM_R) * sizeof(R);
   constexpr int vol_threads = VolShape<N>::THREADS;
   // per device and cheap: set on every call
   cudaFuncSetAttribute(k_lift<N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_lift);
-  cudaFuncSetAttribute(k_volume<N, R, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_vol);
-  cudaFuncSetAttribute(k_volume<N, R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_vol);
+  const bool ec = ph.vol_flux == 2;
+  if (ec) {
+    cudaFuncSetAttribute(k_volume<N, R, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_vol);
+    cudaFuncSetAttribute(k_volume<N, R, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_vol);
+  } else {
+    cudaFuncSetAttribute(k_volume<N, R, 0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_vol);
+    cudaFuncSetAttribute(k_volume<N, R, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_vol);
+  }
+  // the wall kernel reads only U and writes only the wall faces' fluxes, so
+  // it may run beside the lifting and the interior faces
+  const bool fork = a.side != nullptr && a.n_wall > 0;
+  const cudaStream_t ws = fork ? a.side : s;
+  auto wall = [&]() {
+    if (a.n_wall == 0) return;
+    const int threads = 128;
+    const long long work = (long long)a.n_wall * n2;
+    k_wall<N, R><<<(unsigned)((work + threads - 1) / threads), threads, 0, ws>>>(a.Uin, m, ph, Fs, a.tau, a.status);
+  };
+  if (fork) {
+    cudaEventRecord(a.fork, s);
+    cudaStreamWaitEvent(a.side, a.fork, 0);
+    if (a.ev) cudaEventRecord(a.ev[3], ws);
+    wall();
+    if (a.ev) cudaEventRecord(a.ev[4], ws);
+    cudaEventRecord(a.join, a.side);
+  }
   if (a.ev) cudaEventRecord(a.ev[0], s);
   if (ph.viscous) k_lift<N, R><<<a.K, n3, smem_lift, s>>>(a.Uin, m, ph, tab, Rv, Gf);
   if (a.ev) cudaEventRecord(a.ev[1], s);
@@ -53,18 +77,28 @@ static int run_typed(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {
     k_face<N, R><<<(unsigned)((work + threads - 1) / threads), threads, 0, s>>>(a.Uin, m, ph, Gf, Fs);
   }
   if (a.ev) cudaEventRecord(a.ev[2], s);
-  if (a.n_wall > 0) {
-    const int threads = 128;
-    const long long work = (long long)a.n_wall * n2;
-    k_wall<N, R><<<(unsigned)((work + threads - 1) / threads), threads, 0, s>>>(a.Uin, m, ph, Fs, a.tau, a.status);
+  if (fork) {
+    cudaStreamWaitEvent(s, a.join, 0);
+  } else {
+    if (a.ev) cudaEventRecord(a.ev[3], s);
+    wall();
+    if (a.ev) cudaEventRecord(a.ev[4], s);
   }
-  if (a.ev) cudaEventRecord(a.ev[3], s);
+  if (a.ev) cudaEventRecord(a.ev[5], s);
   StageArgs st{a.A, a.B, a.dt, a.read_dU};
-  if (a.mode == 0)
-    k_volume<N, R, 0><<<a.K, vol_threads, smem_vol, s>>>(a.Uin, m, ph, tab, Rv, Fs, a.Out, nullptr, nullptr, st, a.status);
+  if (a.mode == 0 && !ec)
+    k_volume<N, R, 0, false><<<a.K, vol_threads, smem_vol, s>>>(a.Uin, m, ph, tab, Rv, Fs, a.Out, nullptr, nullptr,
+                                                                st, a.status);
+  else if (a.mode == 0)
+    k_volume<N, R, 0, true><<<a.K, vol_threads, smem_vol, s>>>(a.Uin, m, ph, tab, Rv, Fs, a.Out, nullptr, nullptr,
+                                                               st, a.status);
+  else if (!ec)
+    k_volume<N, R, 1, false><<<a.K, vol_threads, smem_vol, s>>>(a.Uin, m, ph, tab, Rv, Fs, nullptr, a.dU, a.Uout,
+                                                                st, a.status);
   else
-    k_volume<N, R, 1><<<a.K, vol_threads, smem_vol, s>>>(a.Uin, m, ph, tab, Rv, Fs, nullptr, a.dU, a.Uout, st, a.status);
-  if (a.ev) cudaEventRecord(a.ev[4], s);
+    k_volume<N, R, 1, true><<<a.K, vol_threads, smem_vol, s>>>(a.Uin, m, ph, tab, Rv, Fs, nullptr, a.dU, a.Uout,
+                                                               st, a.status);
+  if (a.ev) cudaEventRecord(a.ev[6], s);
   return (int)cudaGetLastError();
 }
 

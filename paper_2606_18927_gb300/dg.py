@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 HEADER = os.path.join(_HERE, "..", "include", "dg.h")
 
 FP64, FP32_MIXED = 0, 1
-VOL_KEP_PIROZZOLI, VOL_KEP_KENNEDY_GRUBER = 0, 1
+VOL_KEP_PIROZZOLI, VOL_KEP_KENNEDY_GRUBER, VOL_EC_CHANDRASHEKAR = 0, 1, 2
 SURF_CENTRAL, SURF_LLF, SURF_ROE = 0, 1, 2
 LAW_SPALDING, LAW_REICHARDT = 0, 1
 
@@ -44,7 +44,7 @@ class _Phys(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("R", ctypes.c_double), ("mu", ctypes.c_double),
                 ("Pr", ctypes.c_double), ("force", ctypes.c_double * 3), ("kappa", ctypes.c_double),
                 ("B", ctypes.c_double), ("hwm", ctypes.c_double), ("law", ctypes.c_int),
-                ("p_ref", ctypes.c_double)]
+                ("p_ref", ctypes.c_double), ("suth_S", ctypes.c_double), ("T_ref", ctypes.c_double)]
 
 
 class _Options(ctypes.Structure):
@@ -81,6 +81,7 @@ def lib():
         "dg_time_derivative": (c_int, [vp, vp, vp, c_double, c_int]),
         "dg_rk_stage": (c_int, [vp, c_int, c_double, c_double]),
         "dg_rk_steps": (c_int, [vp, c_double, c_double, c_int]),
+        "dg_rk_steps_graph": (c_int, [vp, c_double, c_double, c_int]),
         "dg_check_status": (c_int, [vp]),
         "dg_get_rk_register": (c_int, [vp, vp, c_int]),
         "dg_set_rk_register": (c_int, [vp, vp, c_int]),
@@ -93,6 +94,7 @@ def lib():
         "dg_time_step": (c_int, [vp, vp, c_double, dp]),
         "dg_rollout_vjp": (c_int, [vp, vp, c_int, c_double, dp, vp, vp]),
         "dg_profile_enable": (c_int, [vp, c_int]),
+        "dg_set_overlap": (c_int, [vp, c_int]),
         "dg_profile_read": (c_int, [vp, dp, ip]),
     }
     for name, (res, args) in sig.items():
@@ -150,7 +152,7 @@ class Operator:
         ph = _Phys(phys["gamma"], phys["R"], phys["mu"], phys["Pr"],
                    (ctypes.c_double * 3)(phys.get("fx", 0.0), phys.get("fy", 0.0), phys.get("fz", 0.0)),
                    phys.get("kappa", 0.41), phys.get("B", 5.2), phys.get("hwm", 0.1), int(law),
-                   phys.get("p_ref", phys.get("p0", 0.0)))
+                   phys.get("p_ref", phys.get("p0", 0.0)), phys.get("suth_S", 0.0), phys.get("T_ref", 1.0))
         op = _Options(int(precision), int(vol_flux), int(surf_flux), int(viscous))
         h = ctypes.c_void_p()
         self._stream = _stream_handle(stream)
@@ -271,8 +273,16 @@ class Operator:
     def rk_steps(self, t, dt, nsteps):
         self._check(lib().dg_rk_steps(self.h, float(t), float(dt), int(nsteps)))
 
+    def rk_steps_graph(self, t, dt, nsteps):
+        """LSERK4 steps replayed from a CUDA graph of one step."""
+        self._check(lib().dg_rk_steps_graph(self.h, float(t), float(dt), int(nsteps)))
+
     def check_status(self):
         self._check(lib().dg_check_status(self.h))
+
+    def set_overlap(self, on=True):
+        """Wall-model kernel on its own high-priority stream, or in line (default)."""
+        self._check(lib().dg_set_overlap(self.h, 1 if on else 0))
 
     def profile_enable(self, on=True):
         self._check(lib().dg_profile_enable(self.h, 1 if on else 0))

@@ -175,11 +175,19 @@ def node_coordinates(spec: BoxSpec, xi):
 # Physical parameters and initial conditions
 # ---------------------------------------------------------------------------
 def phys_params(Ma=0.1, Re=1600.0, Pr=0.72, gamma=1.4, force=(0.0, 0.0, 0.0),
-                kappa=0.41, B=5.2, hwm=0.1, inviscid=False):
-    """Non-dimensional parameters: rho0 = U0 = L = R = 1, mu = 1/Re."""
-    return dict(gamma=gamma, R=1.0, mu=0.0 if inviscid else 1.0 / Re, Pr=Pr,
-                fx=force[0], fy=force[1], fz=force[2], kappa=kappa, B=B, hwm=hwm,
-                Ma=Ma, p0=1.0 / (gamma * Ma * Ma))
+                kappa=0.41, B=5.2, hwm=0.1, inviscid=False, sutherland=False):
+    """Non-dimensional parameters: rho0 = U0 = L = R = 1, mu = 1/Re.
+
+    sutherland: viscosity by Sutherland's law for air, mu = 1/Re at the
+    reference temperature T_ref = p0 / (rho0 R) (taken as 288.15 K) and
+    S = 110.4 K in the same scale."""
+    p0 = 1.0 / (gamma * Ma * Ma)
+    d = dict(gamma=gamma, R=1.0, mu=0.0 if inviscid else 1.0 / Re, Pr=Pr,
+             fx=force[0], fy=force[1], fz=force[2], kappa=kappa, B=B, hwm=hwm,
+             Ma=Ma, p0=p0)
+    if sutherland:
+        d.update(T_ref=p0, suth_S=p0 * 110.4 / 288.15)
+    return d
 
 
 def conservative(rho, u, v, w, p, gamma):

@@ -140,3 +140,55 @@ def test_time_step_and_kinetic_energy(ora):
     ke = g.kinetic_energy(Ud)
     assert abs(dt - o.dt(U, 0.9)) <= 1e-13 * dt
     assert abs(ke - o.kinetic_energy(U)) <= 1e-13 * ke
+
+
+def test_graph_replay_equals_stream_launches(ora):
+    """A CUDA-graph replay of whole LSERK4 steps gives bitwise the state of
+    the same steps launched kernel by kernel."""
+    torch = torch_cuda()
+    phys = I.phys_params(Ma=0.1, Re=1600.0)
+    o, g, X, U = case(ora, I.BoxSpec(3, 4, 4, 4), phys, surf_flux=1)
+    Ud = torch.from_numpy(U).cuda()
+    dt = g.time_step(0.9, Ud)
+    g.set_state(Ud)
+    g.rk_steps(0.0, dt, 3)
+    a = torch.empty_like(Ud)
+    g.get_state(a)
+    g.set_state(Ud)
+    g.rk_steps_graph(0.0, dt, 3)
+    b = torch.empty_like(Ud)
+    g.get_state(b)
+    g.check_status()
+    assert torch.equal(a, b)
+
+
+def test_wall_side_stream_and_graph_on_channel(ora):
+    """Wall-modelled channel: the wall-model kernel on its side stream gives
+    bitwise the result of the in-line launch, also when whole steps are
+    replayed from a CUDA graph (the fork and join are captured), and the
+    step still matches the oracle."""
+    torch = torch_cuda()
+    wl = I.workload("channel_n5", N=3, elems=(4, 4, 2))
+    o, g, X, U = case(ora, wl.spec, wl.phys, surf_flux=2, law=1, ic="channel")
+    Ud = torch.from_numpy(U).cuda()
+    dt = g.time_step(0.9, Ud)
+    out = []
+    for overlap, graph in ((False, False), (True, False), (True, True)):
+        g.set_overlap(overlap)
+        g.set_state(Ud)
+        (g.rk_steps_graph if graph else g.rk_steps)(0.0, dt, 2)
+        r = torch.empty_like(Ud)
+        g.get_state(r)
+        g.check_status()
+        out.append(r)
+    assert torch.equal(out[0], out[1]) and torch.equal(out[0], out[2])
+    e = parity(out[1].cpu().numpy() - U, o.rk_steps(U, dt, 2) - U)
+    print("channel side-stream steps parity (increment)", e)
+    assert e <= TOL, e
+    # per-kernel timing sees the wall kernel on its stream
+    g.set_overlap(True)
+    g.profile_enable(True)
+    g.rk_stage(0, 0.0, dt)
+    prof = g.profile_read()
+    g.profile_enable(False)
+    assert prof["wall"][1] == 1 and prof["wall"][0] > 0.0

@@ -5,8 +5,11 @@
 * Free-stream preservation on deformed meshes (the split-form DGSEM of
   paper Sec. 2.2 / Sec. 4 with curl-form metrics keeps a uniform state).
 * Discrete conservation of mass, momentum and energy on periodic meshes.
-* Kinetic-energy preservation of the KEP split form with a central surface
-  flux at constant pressure.
+* Kinetic-energy preservation of the KEP split forms (and of Chandrashekar's
+  flux) with a central surface flux at constant pressure.
+* Semi-discrete entropy conservation of the split form with Chandrashekar's
+  entropy-conserving flux in the volume and at the faces (paper Sec. 4).
+* Sutherland's law reduces to constant viscosity at uniform temperature.
 Each is a property of the mathematics, not of the code: a dropped metric
 term, a wrong sign in the surface correction or a transposed index breaks
 one of them."""
@@ -107,7 +110,7 @@ def test_discrete_conservation(ora, viscous, surf):
         assert abs(tot) <= 1e-13 * mag, (v, tot, mag)
 
 
-@pytest.mark.parametrize("vol", [0, 1])
+@pytest.mark.parametrize("vol", [0, 1, 2])
 def test_kinetic_energy_preservation(ora, vol):
     # constant pressure, random density and velocity, inviscid, central surface flux
     phys = I.phys_params(Ma=0.3)
@@ -129,3 +132,58 @@ def test_kinetic_energy_preservation(ora, vol):
     Ut2 = o2.time_derivative(U).reshape(5, o.K, o.n3)
     dke2 = (wJ * ((u * Ut2[1:4]).sum(0) - 0.5 * (u * u).sum(0) * Ut2[0])).sum()
     assert dke2 < -1e-6 * scale
+
+
+def _entropy_variables(U, gamma):
+    rho = U[0]; u = U[1:4] / rho
+    p = (gamma - 1) * (U[4] - 0.5 * rho * (u * u).sum(0))
+    s = np.log(p) - gamma * np.log(rho)
+    return np.concatenate([((gamma - s) / (gamma - 1) - 0.5 * rho * (u * u).sum(0) / p)[None],
+                           rho * u / p, (-rho / p)[None]])
+
+
+@pytest.mark.parametrize("N", [3, 4])
+def test_entropy_conservation(ora, N):
+    # With the entropy-conserving two-point flux in the volume and at the
+    # faces, inviscid and periodic, the split-form DGSEM on a curvilinear mesh
+    # conserves the total entropy: sum_nodes wJ w(U) . Ut = 0.  With Roe's
+    # flux at the faces it must produce entropy decay instead.
+    phys = I.phys_params(Ma=0.3)
+    spec = I.BoxSpec(N, 3, 2, 2, geometry="sine", amplitude=0.4)
+    o, X, nbr = oracle_case(ora, spec, phys, vol_flux=2, surf_flux=0, viscous=0)
+    U = I.perturb(I.taylor_green(X, phys), rel=0.2)
+    Ut = o.time_derivative(U).reshape(5, o.K, o.n3)
+    W = _entropy_variables(U.reshape(5, o.K, o.n3), phys["gamma"])
+    wJ = quad_weights(ora, o)
+    ds = (wJ * (W * Ut).sum(0)).sum()
+    scale = (wJ * np.abs(W * Ut).sum(0)).sum()
+    assert abs(ds) < 1e-13 * scale, (ds, scale)
+    o2, _, _ = oracle_case(ora, spec, phys, vol_flux=2, surf_flux=2, viscous=0)
+    Ut2 = o2.time_derivative(U).reshape(5, o.K, o.n3)
+    ds2 = (wJ * (W * Ut2).sum(0)).sum()
+    assert ds2 < -1e-6 * scale
+
+
+def test_sutherland_uniform_temperature(ora):
+    # at a uniform temperature T0 Sutherland's law is the constant viscosity
+    # mu(T0): the whole operator (viscous fluxes, lifting, wall-free periodic
+    # mesh) must match the constant-viscosity run with that mu
+    phys = I.phys_params(Re=200.0)
+    spec = I.BoxSpec(3, 2, 2, 2, geometry="sine", amplitude=0.3)
+    x, w, D = ora.lgl(spec.N)
+    X = I.node_coordinates(spec, x)
+    nbr = I.connectivity(spec)
+    shape = X[0].shape
+    rho = 1.0 + 0.3 * I.uniform(X[0].size, 0, 1, seed=21).reshape(shape)
+    vel = I.uniform(3 * X[0].size, -1, 1, seed=22).reshape(3, *shape)
+    T0 = 1.3
+    p = rho * phys["R"] * T0
+    U = I.conservative(rho, vel[0], vel[1], vel[2], p, phys["gamma"])
+    ps = dict(phys, suth_S=0.4, T_ref=0.9)
+    mu0 = ora.viscosity(ps, T0)
+    assert mu0 == pytest.approx(phys["mu"] * (T0 / 0.9) ** 1.5 * (0.9 + 0.4) / (T0 + 0.4), rel=1e-14)
+    a = ora.Oracle(spec.N, X, nbr, ps, surf_flux=2).time_derivative(U)
+    b = ora.Oracle(spec.N, X, nbr, dict(phys, mu=mu0), surf_flux=2).time_derivative(U)
+    assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max()
+    c = ora.Oracle(spec.N, X, nbr, phys, surf_flux=2).time_derivative(U)
+    assert np.abs(a - c).max() > 1e-6 * np.abs(b).max()
