@@ -66,8 +66,18 @@ enum dg_vol_flux { DG_VOL_KEP_PIROZZOLI = 0, DG_VOL_KEP_KENNEDY_GRUBER = 1, DG_V
 enum dg_surf_flux { DG_SURF_CENTRAL = 0, DG_SURF_LLF = 1, DG_SURF_ROE = 2 };
 enum dg_wall_law { DG_LAW_SPALDING = 0, DG_LAW_REICHARDT = 1 };
 
-/* Neighbour code of a wall-modelled slip wall in dg_mesh_desc.nbr. */
+/* Neighbour codes of boundary faces in dg_mesh_desc.nbr.
+ *   DG_BC_WALL     slip wall with the equilibrium wall model (Sec. 3.2);
+ *   DG_BC_INFLOW   Dirichlet inflow: the exterior state is dg_phys.U_in;
+ *   DG_BC_OUTFLOW  subsonic pressure outflow: the exterior state has the
+ *                  interior density and velocity and pressure dg_phys.p_out
+ *                  (the cascade boundaries of Sec. 4).
+ * At inflow and outflow faces the inviscid flux is the selected Riemann
+ * solver between the interior trace and the exterior state, the BR1 lifting
+ * averages with the exterior state, and the viscous flux is the interior one. */
 #define DG_BC_WALL (-1)
+#define DG_BC_INFLOW (-2)
+#define DG_BC_OUTFLOW (-3)
 
 typedef struct dg_ctx dg_ctx;
 
@@ -77,8 +87,9 @@ typedef struct dg_ctx dg_ctx;
  *   nbr host, int[K][6]: neighbour across local face l (0 -xi, 1 +xi, 2 -eta,
  *       3 +eta, 4 -zeta, 5 +zeta).  A neighbour e' must list e across face
  *       l^1 and share its face nodes in the same order (faces may differ by
- *       one translation: periodic images).  DG_BC_WALL marks a slip wall
- *       with the wall model.  Copied during dg_init_mesh. */
+ *       one translation: periodic images).  Negative entries are boundary
+ *       codes (DG_BC_WALL, DG_BC_INFLOW, DG_BC_OUTFLOW).  Copied during
+ *       dg_init_mesh. */
 typedef struct {
   int N;
   int K;
@@ -106,6 +117,8 @@ typedef struct {
   int law; /* dg_wall_law */
   double p_ref;
   double suth_S, T_ref; /* Sutherland's law (suth_S <= 0: constant mu) */
+  double U_in[5];       /* inflow state (conservative), used by DG_BC_INFLOW faces */
+  double p_out;         /* outflow pressure, used by DG_BC_OUTFLOW faces */
 } dg_phys;
 
 typedef struct {
@@ -134,15 +147,13 @@ const char* dg_last_error(const dg_ctx* c);
 
 int dg_set_stream(dg_ctx* c, void* stream);
 
-/* Meshes with wall-modelled walls: enable = 1 runs the wall-model kernel
- * (which reads only the state and writes only the wall faces' fluxes) on a
- * side stream of the highest priority, beside the lifting and the
- * interior-face kernel, rejoining the caller's stream before the volume
- * kernel (the prioritised streams and events of the paper's Sec. 2.3).
- * enable = 0 (the default) launches it in line on the caller's stream:
- * measured on GB300 the wall kernel, sharing the SMs with the FP64-bound
- * lifting, then takes longer than the two together.  Results are bitwise the
- * same either way; a CUDA graph captured by dg_rk_steps_graph records the
+/* Meshes with wall-modelled walls: enable = 1 (the default) runs the
+ * wall-model kernel (which reads only the state and writes only the wall
+ * faces' fluxes) on a side stream of the highest priority, beside the lifting
+ * and the interior-face kernels, rejoining the caller's stream before the
+ * volume kernel (the prioritised streams and events of the paper's Sec. 2.3).
+ * enable = 0 launches it in line on the caller's stream.  Results are bitwise
+ * the same either way; a CUDA graph captured by dg_rk_steps_graph records the
  * fork and join of the setting in force when it is captured. */
 int dg_set_overlap(dg_ctx* c, int enable);
 
@@ -177,8 +188,8 @@ int dg_rk_steps(dg_ctx* c, double t, double dt, int nsteps);
  * recovery are written out by hand; the local Jacobians of the Riemann
  * solver and of the wall model (with the implicit function theorem for the
  * law of the wall, Sec. 3.2) come from forward-mode dual numbers.  FP64
- * contexts with the Pirozzoli volume flux and a constant viscosity (else
- * DG_ERR_NOT_IMPLEMENTED).
+ * contexts with the Pirozzoli volume flux, a constant viscosity and no
+ * inflow or outflow faces (else DG_ERR_NOT_IMPLEMENTED).
  * The first call allocates the adjoint scratch of the context. */
 int dg_vjp(dg_ctx* c, const double* U, const double* lam, double* gU, double* gtheta);
 

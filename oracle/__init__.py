@@ -15,8 +15,9 @@ from . import build as _build
 
 _libs = {}
 
-PHYS_KEYS = ("gamma", "R", "mu", "Pr", "fx", "fy", "fz", "kappa", "B", "hwm", "suth_S", "T_ref")
-PHYS_DEFAULTS = {"suth_S": 0.0, "T_ref": 1.0}
+PHYS_KEYS = ("gamma", "R", "mu", "Pr", "fx", "fy", "fz", "kappa", "B", "hwm", "suth_S", "T_ref",
+             "U_in0", "U_in1", "U_in2", "U_in3", "U_in4", "p_out")
+PHYS_DEFAULTS = {"suth_S": 0.0, "T_ref": 1.0, "U_in0": 1.0, "U_in4": 1.0, "p_out": 1.0}
 
 
 def lib(extended=False):
@@ -97,7 +98,13 @@ def max_threads():
 
 
 def phys_array(phys):
-    return np.array([float(phys.get(k, PHYS_DEFAULTS.get(k, 0.0))) for k in PHYS_KEYS], dtype=np.float64)
+    """Parameter vector of the C interface; the inflow state comes from
+    phys["U_in"] (5 conservative values)."""
+    d = dict(phys)
+    if "U_in" in d:
+        for v in range(5):
+            d["U_in%d" % v] = float(d["U_in"][v])
+    return np.array([float(d.get(k, PHYS_DEFAULTS.get(k, 0.0))) for k in PHYS_KEYS], dtype=np.float64)
 
 
 class Oracle:

@@ -86,6 +86,9 @@ using std::sqrt; using std::exp; using std::log; using std::log1p; using std::as
 enum VolFlux { VOL_KEP_PIROZZOLI = 0, VOL_KEP_KENNEDY_GRUBER = 1, VOL_EC_CHANDRASHEKAR = 2 };
 enum SurfFlux { SURF_CENTRAL = 0, SURF_LLF = 1, SURF_ROE = 2 };
 enum WallLaw { LAW_SPALDING = 0, LAW_REICHARDT = 1 };
+// neighbour codes of boundary faces: slip wall with the wall model (Sec. 3),
+// Dirichlet inflow and subsonic pressure outflow (Sec. 4's cascade boundaries)
+enum BoundaryCode { BC_WALL = -1, BC_INFLOW = -2, BC_OUTFLOW = -3 };
 
 // ---------------------------------------------------------------------------
 // 1. Legendre-Gauss-Lobatto nodes/weights and the nodal derivative matrix.
@@ -188,6 +191,8 @@ struct Phys {
   real f[3] = {0.0, 0.0, 0.0};  // constant body force per unit volume
   T kappa = 0.41, B = 5.2;        // wall-law constants
   real suth_S = 0.0, T_ref = 1.0;  // Sutherland constant and reference temperature (S <= 0: constant mu)
+  real U_in[5] = {1.0, 0.0, 0.0, 0.0, 1.0};  // Dirichlet inflow state (conservative)
+  real p_out = 1.0;                          // outflow pressure
   real hwm = 0.1;               // wall-model sampling distance
 };
 struct Opts {
@@ -318,7 +323,7 @@ static bool check_connectivity(const Mesh& M, std::string& err) {
   for (int e = 0; e < K; ++e)
     for (int l = 0; l < 6; ++l) {
       int nb = M.nbr[e * 6 + l];
-      if (nb < -1 || nb >= K) { err = "bad neighbour id"; return false; }
+      if (nb < BC_OUTFLOW || nb >= K) { err = "bad neighbour id"; return false; }
       if (nb < 0) continue;
       if (M.nbr[nb * 6 + (l ^ 1)] != e) { err = "non-reciprocal connectivity"; return false; }
       // faces must coincide up to one translation (periodic image)
@@ -401,7 +406,7 @@ static bool build_wall_samples(Mesh& M, real hwm, std::string& err) {
   int slots = 0;
   for (int e = 0; e < K; ++e)
     for (int l = 0; l < 6; ++l)
-      if (M.nbr[e * 6 + l] < 0) { M.wslot[e * 6 + l] = slots; slots += M.n2; }
+      if (M.nbr[e * 6 + l] == BC_WALL) { M.wslot[e * 6 + l] = slots; slots += M.n2; }
   M.nwall = slots;
   M.ws_elem.assign(slots, -1);
   M.ws_ref.assign((size_t)slots * 3, 0.0);
@@ -777,6 +782,21 @@ void mirror(const T U[5], const real nh[3], T Ub[5]) {
   Ub[4] = U[4];
 }
 
+// exterior (ghost) state of a boundary face: the wall's mirror state, the
+// prescribed inflow state, or the interior density and velocity with the
+// prescribed outflow pressure
+template <class T>
+void ghost_state(const Phys<T>& P, int code, const T U[5], const real nh[3], T Ub[5]) {
+  if (code == BC_WALL) {
+    mirror(U, nh, Ub);
+  } else if (code == BC_INFLOW) {
+    for (int v = 0; v < 5; ++v) Ub[v] = T(P.U_in[v]);
+  } else {
+    for (int v = 0; v < 4; ++v) Ub[v] = U[v];
+    Ub[4] = P.p_out / (P.gamma - 1.0) + 0.5 * (U[1] * U[1] + U[2] * U[2] + U[3] * U[3]) / U[0];
+  }
+}
+
 // master side's unit normal and surface element of face l of e at node (a,b)
 static void face_geometry(const Mesh& M, int e, int l, int a, int b, real nh[3], real* s, bool* own_is_master) {
   int nb = M.nbr[e * 6 + l];
@@ -853,13 +873,23 @@ int time_derivative(const Mesh& M, const Phys<T>& P, const Opts& O, const T* U, 
           if (nb >= 0) {
             int q = face_node(M, l ^ 1, a, b);
             for (int w = 0; w < 4; ++w) Wn[w] = Wv(nb, q, w);
-          } else {
+          } else if (nb == BC_WALL) {
             // slip wall: mirror state (normal velocity reversed, same T)
             real ss = std::sqrt(ns[0] * ns[0] + ns[1] * ns[1] + ns[2] * ns[2]);
             real nh[3] = {ns[0] / ss, ns[1] / ss, ns[2] / ss};
             T un = Wo[0] * nh[0] + Wo[1] * nh[1] + Wo[2] * nh[2];
             for (int c = 0; c < 3; ++c) Wn[c] = Wo[c] - 2.0 * un * nh[c];
             Wn[3] = Wo[3];
+          } else {
+            // inflow / outflow: W of the exterior state
+            real ss = std::sqrt(ns[0] * ns[0] + ns[1] * ns[1] + ns[2] * ns[2]);
+            real nh[3] = {ns[0] / ss, ns[1] / ss, ns[2] / ss};
+            T u[5], ub[5];
+            load_U(M, U, e, p, u);
+            ghost_state(P, nb, u, nh, ub);
+            Prim<T> qb = prim_of(P, ub);
+            for (int c = 0; c < 3; ++c) Wn[c] = qb.u[c];
+            Wn[3] = qb.T_;
           }
           for (int w = 0; w < 4; ++w) {
             T Ws = 0.5 * (Wo[w] + Wn[w]);
@@ -986,7 +1016,7 @@ int time_derivative(const Mesh& M, const Phys<T>& P, const Opts& O, const T* U, 
               }
         } else {
           for (int v = 0; v < 5; ++v) Um[v] = Uo[v];
-          mirror(Uo, nh, Us);
+          ghost_state(P, nb, Uo, nh, Us);
           qm = qo; qs = prim_of(P, Us);
         }
         T Fi[5];
@@ -998,9 +1028,15 @@ int time_derivative(const Mesh& M, const Phys<T>& P, const Opts& O, const T* U, 
             viscous_flux(P, qm, gm, nh, Fa);
             viscous_flux(P, qs, gs, nh, Fb);
             for (int v = 0; v < 5; ++v) Fv[v] = 0.5 * (Fa[v] + Fb[v]);
-          } else {
+          } else if (nb == BC_WALL) {
             int slot = M.wslot[e * 6 + l] + a + n * b;
             for (int c = 0; c < 3; ++c) Fv[1 + c] = W.wflux[(size_t)slot * 3 + c];
+          } else {
+            // inflow / outflow: the interior viscous flux
+            T go[3][4];
+            for (int d = 0; d < 3; ++d)
+              for (int w = 0; w < 4; ++w) go[d][w] = W.grad[((size_t)e * n3 + p) * 12 + d * 4 + w];
+            viscous_flux(P, qo, go, nh, Fv);
           }
         }
         const real sg = own_master ? 1.0 : -1.0;
@@ -1111,6 +1147,8 @@ static Phys<Dual> dual_phys(const Phys<real>& P, real dk, real dB) {
   for (int c = 0; c < 3; ++c) Q.f[c] = P.f[c];
   Q.kappa = Dual(P.kappa, dk); Q.B = Dual(P.B, dB); Q.hwm = P.hwm;
   Q.suth_S = P.suth_S; Q.T_ref = P.T_ref;
+  for (int v = 0; v < 5; ++v) Q.U_in[v] = P.U_in[v];
+  Q.p_out = P.p_out;
   return Q;
 }
 
@@ -1181,6 +1219,8 @@ static void* create_impl(int N, int K, const double* X, const int* nbr, const do
   c->P.f[0] = phys[4]; c->P.f[1] = phys[5]; c->P.f[2] = phys[6];
   c->P.kappa = phys[7]; c->P.B = phys[8]; c->P.hwm = phys[9];
   c->P.suth_S = phys[10]; c->P.T_ref = phys[11];
+  for (int v = 0; v < 5; ++v) c->P.U_in[v] = phys[12 + v];
+  c->P.p_out = phys[17];
   c->O.vol_flux = opts[0]; c->O.surf_flux = opts[1]; c->O.viscous = opts[2]; c->O.law = opts[3];
   std::string e;
   bool ok = check_connectivity(M, e) && build_metrics(M, e) && build_wall_samples(M, c->P.hwm, e);

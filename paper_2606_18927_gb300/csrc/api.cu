@@ -36,7 +36,10 @@ struct dg_ctx {
   // joined back into the caller's stream around each operator evaluation
   cudaStream_t side = nullptr;
   cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
-  bool overlap = false;
+  bool overlap = true;
+  // FP32-mixed form: FP32 primitives [6][S]; w32_of_U says they are those of U
+  float* W32 = nullptr;
+  bool w32_of_U = false;
   dg::Geometry geo;
   // device storage
   double* U = nullptr;
@@ -120,7 +123,7 @@ void free_all(dg_ctx* c) {
   void* ptrs[] = {c->U, c->dU, c->io, c->io2, c->Ja, c->invJ, c->fgeo, c->nbr, c->elem_face, c->faces,
                   c->ws_elem, c->ws_lag, c->Rv, c->Gf, c->Fs, c->tau, c->status,
                   c->gUf, c->gGf, c->gWf, c->gUs, c->gtheta, c->wq, c->ro_ckpt, c->ro_stage, c->ro_work,
-                  c->ro_scalar, c->wJ};
+                  c->ro_scalar, c->wJ, c->W32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -132,6 +135,7 @@ int launch(dg_ctx* c, const double* Uin, int mode, double* Out, double A, double
            double* Uout, double* dU = nullptr) {
   dg::OpArgs a{};
   a.N = c->N; a.K = c->K; a.F = c->F; a.n_interior = c->geo.n_interior; a.n_wall = c->geo.n_wall;
+  a.n_bc = c->geo.n_bc;
   a.fp32 = c->opts.precision == DG_FP32_MIXED;
   a.Ja = c->Ja; a.invJ = c->invJ; a.fgeo = c->fgeo; a.nbr = c->nbr; a.elem_face = c->elem_face;
   a.faces = c->faces; a.ws_elem = c->ws_elem; a.ws_lag = c->ws_lag;
@@ -153,8 +157,27 @@ int launch(dg_ctx* c, const double* Uin, int mode, double* Out, double A, double
     a.ev = &c->events[c->events_used];
     c->events_used += kEventsPerLaunch;
   }
+  a.W32 = c->W32;
+  a.w32_valid = (a.fp32 && Uin == c->U && c->w32_of_U) ? 1 : 0;
   int rc = dg::run_operator(a, c->ph, c->stream);
-  if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "kernel launch");
+  if (rc != 0) {
+    c->w32_of_U = false;
+    return cuda_fail(c, (cudaError_t)rc, "kernel launch");
+  }
+  // the FP32 primitives now belong to the stage's output (mode 1) or input
+  if (a.fp32) c->w32_of_U = mode == 1 ? (Uout == c->U) : (Uin == c->U);
+  return DG_OK;
+}
+
+// FP32-mixed form: form the primitives of the context's state if they are stale
+int refresh_w32(dg_ctx* c) {
+  if (c->opts.precision != DG_FP32_MIXED || c->w32_of_U) return DG_OK;
+  const long long S = (long long)c->S;
+  dg::k_prim32<<<(unsigned)std::min<long long>((S + 255) / 256, 152 * 16), 256, 0, c->stream>>>(S, c->U, c->ph,
+                                                                                                 c->W32);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "primitive refresh");
+  c->w32_of_U = true;
   return DG_OK;
 }
 
@@ -251,6 +274,7 @@ int noalloc_args(dg_ctx* c, const double* U, double* Ut, OpArgs* a, const PhysDe
   const size_t rs = c->opts.precision == DG_FP32_MIXED ? sizeof(float) : sizeof(double);
   *a = OpArgs{};
   a->N = c->N; a->K = c->K; a->F = c->F; a->n_interior = c->geo.n_interior; a->n_wall = c->geo.n_wall;
+  a->n_bc = c->geo.n_bc;
   a->fp32 = c->opts.precision == DG_FP32_MIXED;
   a->Ja = c->Ja; a->invJ = c->invJ; a->fgeo = c->fgeo; a->nbr = c->nbr; a->elem_face = c->elem_face;
   a->faces = c->faces; a->ws_elem = c->ws_elem; a->ws_lag = c->ws_lag;
@@ -262,6 +286,11 @@ int noalloc_args(dg_ctx* c, const double* U, double* Ut, OpArgs* a, const PhysDe
   *rv_bytes = (c->opts.viscous ? 4 * c->S : 1) * rs;
   *gf_bytes = (c->opts.viscous ? 24 * (size_t)c->K * c->n2 : 1) * rs;
   *fs_bytes = 5 * (size_t)c->F * c->n2 * rs;
+  // FP32-mixed form: the primitives go to the context's own W32 array
+  // (allocated with the context); they are formed afresh from U
+  a->W32 = c->W32;
+  a->w32_valid = 0;
+  if (a->fp32) c->w32_of_U = (U == c->U);
   return DG_OK;
 }
 int noalloc_fail(dg_ctx* c, int code, const std::string& msg) { return fail(c, code, msg); }
@@ -305,6 +334,20 @@ int dg_init_mesh(dg_ctx** out, const dg_mesh_desc* m, const dg_phys* p, const dg
     return fail(nullptr, DG_ERR_ARG, "dg_init_mesh: wall faces need hwm > 0");
   }
   c->F = (int)c->geo.faces.size();
+  if (c->geo.n_bc > 0) {
+    bool has_in = false, has_out = false;
+    for (int f = c->geo.n_interior + c->geo.n_wall; f < c->F; ++f) {
+      has_in |= c->geo.faces[f].eS == dg::BC_CODE_INFLOW;
+      has_out |= c->geo.faces[f].eS == dg::BC_CODE_OUTFLOW;
+    }
+    const double* ui = p->U_in;
+    const double pin = (p->gamma - 1.0) * (ui[4] - 0.5 * (ui[1] * ui[1] + ui[2] * ui[2] + ui[3] * ui[3]) / ui[0]);
+    if ((has_in && !(ui[0] > 0.0 && pin > 0.0)) || (has_out && !(p->p_out > 0.0))) {
+      delete c;
+      return fail(nullptr, DG_ERR_ARG, "dg_init_mesh: inflow faces need U_in with positive density and pressure, "
+                                       "outflow faces a positive p_out");
+    }
+  }
   // physics constants for the kernels
   dg::PhysDev& ph = c->ph;
   ph.gamma = p->gamma; ph.gm1 = p->gamma - 1.0; ph.R = p->R; ph.mu = p->mu; ph.Pr = p->Pr;
@@ -316,6 +359,13 @@ int dg_init_mesh(dg_ctx** out, const dg_mesh_desc* m, const dg_phys* p, const dg
   for (int d = 0; d < 3; ++d) ph.f[d] = p->force[d];
   ph.kappa = p->kappa; ph.B = p->B; ph.hwm = p->hwm; ph.law = p->law;
   ph.vol_flux = o->vol_flux; ph.surf_flux = o->surf_flux; ph.viscous = o->viscous ? 1 : 0;
+  for (int v = 0; v < 5; ++v) ph.U_in[v] = p->U_in[v];
+  ph.p_out = p->p_out;
+  ph.sutherland = ph.suth_S > 0.0 ? 1 : 0;
+  ph.has_force = (ph.f[0] != 0.0 || ph.f[1] != 0.0 || ph.f[2] != 0.0) ? 1 : 0;
+  ph.f32c.p_ref = (float)ph.p_ref; ph.f32c.rcp_R = (float)ph.rcp_R; ph.f32c.rgm1 = (float)ph.rgm1;
+  ph.f32c.gamma = (float)ph.gamma; ph.f32c.mu = (float)ph.mu; ph.f32c.kcond = (float)ph.kcond;
+  ph.f32c.cp_Pr = (float)ph.cp_Pr; ph.f32c.suth_C = (float)ph.suth_C; ph.f32c.suth_S = (float)ph.suth_S;
   cudaGetDevice(&c->device);
   // device storage
   const size_t S = c->S, n2 = c->n2;
@@ -339,6 +389,7 @@ int dg_init_mesh(dg_ctx** out, const dg_mesh_desc* m, const dg_phys* p, const dg
   chk(cudaMalloc(&c->Rv, (o->viscous ? 4 * S : 1) * rs));
   chk(cudaMalloc(&c->Gf, (o->viscous ? 24 * (size_t)c->K * n2 : 1) * rs));
   chk(cudaMalloc(&c->Fs, 5 * (size_t)c->F * n2 * rs));
+  if (f32) chk(alloc(&c->W32, 6 * S));
   chk(alloc(&c->status, 1));
   if (e != cudaSuccess) { free_all(c); delete c; return cuda_fail(nullptr, e, "dg_init_mesh: allocation"); }
   // uploads (metrics transposed to [9][S], comp-major for coalesced loads)
@@ -440,6 +491,7 @@ int dg_set_state(dg_ctx* c, const double* U, int on_device) {
     if (e != cudaSuccess) return cuda_fail(c, e, "dg_set_state");
   }
   c->state_set = true;
+  c->w32_of_U = false;
   return DG_OK;
 }
 
@@ -531,6 +583,7 @@ static int ensure_adjoint_scratch(dg_ctx* c) {
 static dg::OpArgs adjoint_args(dg_ctx* c, const double* U, const double* lam, double* gU, double* gth) {
   dg::OpArgs a{};
   a.N = c->N; a.K = c->K; a.F = c->F; a.n_interior = c->geo.n_interior; a.n_wall = c->geo.n_wall;
+  a.n_bc = c->geo.n_bc;
   a.Ja = c->Ja; a.invJ = c->invJ; a.fgeo = c->fgeo; a.nbr = c->nbr; a.elem_face = c->elem_face;
   a.faces = c->faces; a.ws_elem = c->ws_elem; a.ws_lag = c->ws_lag;
   a.D = c->geo.basis.D.data(); a.w = c->geo.basis.w.data();
@@ -546,6 +599,8 @@ static int check_adjoint_options(dg_ctx* c, const char* who) {
     return fail(c, DG_ERR_NOT_IMPLEMENTED, std::string(who) + ": the adjoint needs the Pirozzoli volume flux");
   if (c->phys.suth_S > 0.0)
     return fail(c, DG_ERR_NOT_IMPLEMENTED, std::string(who) + ": the adjoint needs a constant viscosity");
+  if (c->geo.n_bc > 0)
+    return fail(c, DG_ERR_NOT_IMPLEMENTED, std::string(who) + ": the adjoint covers periodic and wall faces only");
   return DG_OK;
 }
 
@@ -736,6 +791,8 @@ int dg_rk_steps_graph(dg_ctx* c, double t, double dt, int nsteps) {
   (void)t;  // the operator is autonomous
   if (!c || nsteps < 0) return c ? fail(c, DG_ERR_ARG, "dg_rk_steps_graph: nsteps < 0") : DG_ERR_ARG;
   if (!c->state_set) return fail(c, DG_ERR_NOT_INIT, "dg_rk_steps_graph: state not set");
+  int rc0 = refresh_w32(c);
+  if (rc0 != DG_OK) return rc0;
   cudaError_t e = cudaSuccess;
   if (!c->step_graph || c->step_graph_dt != dt) {
     if (!c->cap_stream) {

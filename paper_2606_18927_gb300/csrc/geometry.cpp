@@ -226,7 +226,7 @@ static bool faces(Geometry& g, std::string& err) {
   for (int e = 0; e < K; ++e)
     for (int l = 0; l < 6; ++l) {
       const int nb = g.nbr[e * 6 + l];
-      if (nb < -1 || nb >= K) { err = "neighbour index out of range"; return false; }
+      if (nb < BC_CODE_MIN || nb >= K) { err = "neighbour index out of range"; return false; }
       if (nb < 0) continue;
       if (g.nbr[nb * 6 + (l ^ 1)] != e) { err = "connectivity is not reciprocal"; return false; }
       // the two sides must coincide up to a single translation
@@ -255,14 +255,25 @@ static bool faces(Geometry& g, std::string& err) {
       g.elem_face[nb * 6 + (l ^ 1)] = 2 * id + 1;
     }
   g.n_interior = (int)g.faces.size();
+  // boundary faces: walls first, then inflow / outflow faces (eS = the code)
   for (int e = 0; e < K; ++e)
     for (int l = 0; l < 6; ++l)
-      if (g.nbr[e * 6 + l] < 0) {
+      if (g.nbr[e * 6 + l] == BC_CODE_WALL) {
         const int id = (int)g.faces.size();
-        g.faces.push_back({e, l, -1, -1});
+        g.faces.push_back({e, l, BC_CODE_WALL, -1});
         g.elem_face[e * 6 + l] = 2 * id;
       }
   g.n_wall = (int)g.faces.size() - g.n_interior;
+  for (int e = 0; e < K; ++e)
+    for (int l = 0; l < 6; ++l) {
+      const int nb = g.nbr[e * 6 + l];
+      if (nb < 0 && nb != BC_CODE_WALL) {
+        const int id = (int)g.faces.size();
+        g.faces.push_back({e, l, nb, -1});
+        g.elem_face[e * 6 + l] = 2 * id;
+      }
+    }
+  g.n_bc = (int)g.faces.size() - g.n_interior - g.n_wall;
   const size_t F = g.faces.size();
   g.fgeo.assign(4 * F * n2, 0.0);
   for (size_t f = 0; f < F; ++f) {

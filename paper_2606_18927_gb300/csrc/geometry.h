@@ -27,9 +27,12 @@ Basis make_basis(int N);
 // Lagrange basis l_j(s) (barycentric form) on the basis nodes.
 void lagrange_at(const Basis& b, double s, double* l);
 
+// neighbour codes of boundary faces (dg.h: DG_BC_WALL, DG_BC_INFLOW, DG_BC_OUTFLOW)
+constexpr int BC_CODE_WALL = -1, BC_CODE_INFLOW = -2, BC_CODE_OUTFLOW = -3, BC_CODE_MIN = -3;
+
 struct Face {
   int eM, lM;  // master element and its local face
-  int eS, lS;  // slave element and local face, or -1 for a wall
+  int eS, lS;  // slave element and local face; boundary faces: eS = the code, lS = -1
 };
 
 struct Geometry {
@@ -39,8 +42,8 @@ struct Geometry {
   std::vector<double> X;         // [3][K*n3]
   std::vector<double> Ja;        // [K*n3][3 dir][3 comp]
   std::vector<double> J;         // [K*n3]
-  std::vector<Face> faces;       // interior faces first, then wall faces
-  int n_interior = 0, n_wall = 0;
+  std::vector<Face> faces;       // interior faces, then wall faces, then inflow / outflow faces
+  int n_interior = 0, n_wall = 0, n_bc = 0;
   std::vector<int> elem_face;    // [K*6] = 2 * face id + side (0 master, 1 slave)
   std::vector<double> fgeo;      // [4][F*n2]: unit normal (master outward) and s
   std::vector<int> ws_elem;      // [n_wall*n2] element containing the sample point

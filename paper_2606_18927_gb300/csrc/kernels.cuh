@@ -35,12 +35,31 @@ struct PhysDev {
   double f[3];
   double kappa, B, hwm;
   int law, vol_flux, surf_flux, viscous;
+  int sutherland, has_force;  // suth_S > 0; f != 0
+  double U_in[5], p_out;      // inflow state (conservative) and outflow pressure
+  // FP32 copies of the constants the FP32 kernels use (a double-to-float
+  // conversion is an FP64-pipe instruction)
+  struct {
+    float p_ref, rcp_R, rgm1, gamma, mu, kcond, cp_Pr, suth_C, suth_S;
+  } f32c;
 };
+
+// a PhysDev constant in the flux type R
+template <typename R>
+__device__ __forceinline__ R cR(double d, float f) {
+  if constexpr (std::is_same<R, float>::value) {
+    (void)d;
+    return f;
+  } else {
+    (void)f;
+    return (R)d;
+  }
+}
 
 // device-side views of the context's arrays
 template <typename R>
 struct MeshDev {
-  int K, F, n_interior, n_wall;
+  int K, F, n_interior, n_wall, n_bc;  // faces: interior, walls, inflow / outflow
   const R* Ja;           // [9][K*n3] (dir*3+comp)
   const R* invJ;         // [K*n3]
   const double* fgeo;    // [4][F*n2]
@@ -49,6 +68,7 @@ struct MeshDev {
   const int4* faces;     // [F]
   const int* ws_elem;    // [n_wall*n2]
   const double* ws_lag;  // [n_wall*n2*3*n]
+  float* W32;            // FP32-mixed form: [6][K*n3] primitives of the input state (null in FP64)
 };
 
 template <int N>
@@ -93,7 +113,7 @@ __device__ __forceinline__ float rcp_t<float>(float x) { return __frcp_rn(x); }
 // mu_ref (T / T_ref)^(3/2) (T_ref + S) / (T + S) (the paper's Sec. 4 gas model).
 template <typename R>
 __device__ __forceinline__ R sutherland(const PhysDev& ph, R T) {
-  return (R)ph.suth_C * T * sqrt(T) / (T + (R)ph.suth_S);
+  return cR<R>(ph.suth_C, ph.f32c.suth_C) * T * sqrt(T) / (T + cR<R>(ph.suth_S, ph.f32c.suth_S));
 }
 
 // Logarithmic mean L(a, b) = (a - b) / ln(a / b) of two positive numbers,
@@ -147,6 +167,19 @@ __device__ __forceinline__ R inv_one_plus(R t) {
   return R(1) + t * (R(-1) + t * (R(1) + t * (R(-1) + t)));
 }
 
+// exterior state of an inflow (code -2: the prescribed state) or outflow
+// (code -3: interior density and velocity, prescribed pressure) face node
+__device__ __forceinline__ void ghost_state(const PhysDev& ph, int code, const double U[5], double Ub[5]) {
+  if (code == -2) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) Ub[v] = ph.U_in[v];
+  } else {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) Ub[v] = U[v];
+    Ub[4] = fma(ph.p_out, ph.rgm1, 0.5 * (U[1] * U[1] + U[2] * U[2] + U[3] * U[3]) / U[0]);
+  }
+}
+
 __device__ __forceinline__ bool finite_bits(double x) {
   const unsigned hi = (unsigned)(__double_as_longlong(x) >> 32);
   return (hi & 0x7ff00000u) != 0x7ff00000u;
@@ -189,7 +222,7 @@ __device__ __forceinline__ Prim<float> primitive<float>(const double U0, const d
   const float ke = 0.5f * (m1 * q.u + m2 * q.v + m3 * q.w);
   const double pr = fma(ph.gm1, U4 - (double)ke, -ph.p_ref);  // p - p_ref
   q.p = (float)pr;
-  q.h = ((float)U4 + q.p + (float)ph.p_ref) * ir;
+  q.h = ((float)U4 + q.p + ph.f32c.p_ref) * ir;
   return q;
 }
 
@@ -211,7 +244,7 @@ __device__ __forceinline__ void velocity_temperature<float>(const double U0, con
                                                             float& T) {
   const Prim<float> q = primitive<float>(U0, U1, U2, U3, U4, ph);
   u = q.u; v = q.v; w = q.w;
-  T = (q.p + (float)ph.p_ref) * (float)ph.rcp_R / q.rho;
+  T = (q.p + ph.f32c.p_ref) * ph.f32c.rcp_R / q.rho;
 }
 
 // Entropy-conserving two-point flux of Chandrashekar (the paper's Sec. 4
@@ -224,7 +257,7 @@ __device__ __forceinline__ void velocity_temperature<float>(const double U0, con
 template <typename R>
 __device__ __forceinline__ void twopoint_ec(const Prim<R>& A, const Prim<R>& B, R a0, R a1, R a2, R F[5],
                                             const PhysDev& ph) {
-  const R pref = (R)ph.p_ref;
+  const R pref = cR<R>(ph.p_ref, ph.f32c.p_ref);
   const R bA = A.rho * rcp_t<R>(R(2) * (A.p + pref)), bB = B.rho * rcp_t<R>(R(2) * (B.p + pref));
   const R sr = A.rho + B.rho, dr = A.rho - B.rho, sb = bA + bB, db = bA - bB;
   const R rr = rcp_t<R>(sr), rb = rcp_t<R>(sb);
@@ -241,7 +274,13 @@ __device__ __forceinline__ void twopoint_ec(const Prim<R>& A, const Prim<R>& B, 
   F[3] = f0 * w + pt * a2;
   const R k2 = R(0.25) * (A.u * A.u + A.v * A.v + A.w * A.w + B.u * B.u + B.v * B.v + B.w * B.w);
   // 1 / (2 (gamma - 1) beta_ln) = rb P / (gamma - 1)
-  F[4] = f0 * (rb * Pb * (R)ph.rgm1 + (u * u + v * v + w * w) - k2) + (pt + pref) * ua;
+  F[4] = f0 * (rb * Pb * cR<R>(ph.rgm1, ph.f32c.rgm1) + (u * u + v * v + w * w) - k2) + (pt + pref) * ua;
+}
+
+__device__ __forceinline__ void velocity_temperature32(const Prim<float>& q, const PhysDev& ph, float& u, float& v,
+                                                       float& w, float& T) {
+  u = q.u; v = q.v; w = q.w;
+  T = (q.p + ph.f32c.p_ref) * ph.f32c.rcp_R / q.rho;
 }
 
 // Two-point KEP flux F#(L, R) . a (a need not be unit); kind 2 is the
@@ -256,7 +295,7 @@ __device__ __forceinline__ void twopoint(int kind, const Prim<R>& A, const Prim<
       return;
     }
   }
-  const R pref = (R)ph.p_ref;
+  const R pref = cR<R>(ph.p_ref, ph.f32c.p_ref);
   const R rho = R(0.5) * (A.rho + B.rho);
   const R u = R(0.5) * (A.u + B.u), v = R(0.5) * (A.v + B.v), w = R(0.5) * (A.w + B.w);
   const R p = R(0.5) * (A.p + B.p);
@@ -275,20 +314,21 @@ __device__ __forceinline__ void twopoint(int kind, const Prim<R>& A, const Prim<
   }
 }
 
-// Numerical inviscid flux along the unit normal (nx, ny, nz), side A = master.
-template <typename R, typename S>
-__device__ __forceinline__ void riemann(const PhysDev& ph, const Prim<R>& A, const S UA[5],
-                                        const Prim<R>& B, const S UB[5], R nx, R ny, R nz, R F[5]) {
-  const R pref = (R)ph.p_ref;
+// Numerical inviscid flux along the unit normal (nx, ny, nz), side A = master;
+// dU = U_B - U_A (conservative) for the Lax-Friedrichs dissipation.
+template <typename R>
+__device__ __forceinline__ void riemann_d(const PhysDev& ph, const Prim<R>& A, const Prim<R>& B, const R dU[5],
+                                          R nx, R ny, R nz, R F[5]) {
+  const R pref = cR<R>(ph.p_ref, ph.f32c.p_ref);
   twopoint<R>(ph.vol_flux, A, B, nx, ny, nz, F, ph);
-  const R g = (R)ph.gamma;
+  const R g = cR<R>(ph.gamma, ph.f32c.gamma);
   if (ph.surf_flux == 1) {  // local Lax-Friedrichs (sound speed from the full pressure)
     const R cA = sqrt(g * (A.p + pref) / A.rho), cB = sqrt(g * (B.p + pref) / B.rho);
     const R lA = fabs(A.u * nx + A.v * ny + A.w * nz) + cA;
     const R lB = fabs(B.u * nx + B.v * ny + B.w * nz) + cB;
     const R lam = R(0.5) * (lA >= lB ? lA : lB);
 #pragma unroll
-    for (int v = 0; v < 5; ++v) F[v] -= lam * (R)(UB[v] - UA[v]);
+    for (int v = 0; v < 5; ++v) F[v] -= lam * dU[v];
   } else if (ph.surf_flux == 2) {  // Roe with Harten's entropy fix on the acoustic waves
     const R sA = sqrt(A.rho), sB = sqrt(B.rho);
     const R is = R(1) / (sA + sB);
@@ -323,21 +363,60 @@ __device__ __forceinline__ void riemann(const PhysDev& ph, const Prim<R>& A, con
   }
 }
 
+template <typename R, typename S>
+__device__ __forceinline__ void riemann(const PhysDev& ph, const Prim<R>& A, const S UA[5],
+                                        const Prim<R>& B, const S UB[5], R nx, R ny, R nz, R F[5]) {
+  R dU[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) dU[v] = (R)(UB[v] - UA[v]);
+  riemann_d<R>(ph, A, B, dU, nx, ny, nz, F);
+}
+
+// ---------------------------------------------------------------------------
+// FP32-mixed form: the FP32 primitives (rho, u, v, w, p - p_ref, h) of every
+// node, W[6][K n^3], formed once per stage from the FP64 state (by k_prim32,
+// or by the previous stage's volume epilogue from the updated state) and read
+// by the lifting, face and volume kernels.  The FP64 work of the primitive
+// recovery (and of the double-to-float conversions) is then done once per node
+// and stage instead of once per use.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void store_prim32(float* __restrict__ W, size_t S, size_t g, const Prim<float>& q) {
+  W[g] = q.rho; W[S + g] = q.u; W[2 * S + g] = q.v; W[3 * S + g] = q.w; W[4 * S + g] = q.p; W[5 * S + g] = q.h;
+}
+
+__device__ __forceinline__ Prim<float> load_prim32(const float* __restrict__ W, size_t S, size_t g) {
+  Prim<float> q;
+  q.rho = W[g]; q.u = W[S + g]; q.v = W[2 * S + g]; q.w = W[3 * S + g]; q.p = W[4 * S + g]; q.h = W[5 * S + g];
+  return q;
+}
+
+static __global__ void k_prim32(long long S, const double* __restrict__ U, const PhysDev ph, float* __restrict__ W) {
+  for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < S; x += (long long)gridDim.x * blockDim.x) {
+    const Prim<float> q = primitive<float>(U[x], U[S + x], U[2 * S + x], U[3 * S + x], U[4 * S + x], ph);
+    store_prim32(W, (size_t)S, (size_t)x, q);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Wall model (paper Sec. 3.2, Algorithms 1-2), always in double.
 // ---------------------------------------------------------------------------
 // law L(w) and w L'(w) / L(w) for w = y+ (Reichardt, L = u+) or w = u+
-// (Spalding, L = y+)
-__device__ __forceinline__ void law_eval(int law, double w, double kap, double B, double* L, double* wdL) {
+// (Spalding, L = y+).  cst is the law's constant part: C = B - ln(kappa) /
+// kappa (Reichardt) or e^(-kappa B) (Spalding), see law_const.
+__device__ __forceinline__ double law_const(int law, double kap, double B) {
+  return law == 1 ? B - log(kap) / kap : exp(-kap * B);
+}
+
+__device__ __forceinline__ void law_eval_c(int law, double w, double kap, double cst, double* L, double* wdL) {
   if (law == 1) {
-    const double C = B - log(kap) / kap;
+    const double C = cst;
     const double e1 = exp(-w / 11.0), e2 = exp(-0.33 * w);
     const double Lv = log1p(kap * w) / kap + C * (1.0 - e1 - (w / 11.0) * e2);
     const double dL = 1.0 / (1.0 + kap * w) + C * (e1 / 11.0 - e2 / 11.0 + 0.33 * (w / 11.0) * e2);
     *L = Lv; *wdL = w * dL;
   } else {
     const double ku = kap * w;
-    const double eb = exp(-kap * B), ek = exp(ku);
+    const double eb = cst, ek = exp(ku);
     const double t3 = ku * ku * ku / 6.0;
     const double Lv = w + eb * (ek - 1.0 - ku - 0.5 * ku * ku - t3 - 0.25 * ku * t3);
     const double dL = 1.0 + eb * kap * (ek - 1.0 - ku - 0.5 * ku * ku - t3);
@@ -345,27 +424,37 @@ __device__ __forceinline__ void law_eval(int law, double w, double kap, double B
   }
 }
 
+__device__ __forceinline__ void law_eval(int law, double w, double kap, double B, double* L, double* wdL) {
+  law_eval_c(law, w, kap, law_const(law, kap, B), L, wdL);
+}
+
 // Solve t + ln L(e^t) = ln Re_h (Re_h = h u / nu = u+ y+): bracket by growing
 // steps from the laminar estimate t = ln(Re_h)/2, then Newton with bisection
-// whenever a step would leave the bracket.  Returns u_tau (and *ok).
+// whenever a step would leave the bracket.  Returns u_tau (and *ok).  F is
+// increasing in t; its value at the starting point is evaluated once.
 static __device__ double solve_utau(int law, double u, double h, double nu, double kap, double B, bool* ok) {
   *ok = true;
   if (!(u > 0.0)) return 0.0;
   const double lnRe = log(h * u / nu);
+  const double cst = law_const(law, kap, B);
   auto F = [&](double t, double* dF) {
     const double w = exp(t);
     double L, wdL;
-    law_eval(law, w, kap, B, &L, &wdL);
+    law_eval_c(law, w, kap, cst, &L, &wdL);
     *dF = 1.0 + wdL / L;
     return t + log(L) - lnRe;
   };
   double dF;
-  double lo = 0.5 * lnRe, hi = lo, st = 1.0;
+  const double t0 = 0.5 * lnRe;
+  const double F0 = F(t0, &dF);
+  double lo = t0, hi = t0, st = 1.0;
   int it = 0;
-  while (!(F(lo, &dF) < 0.0) && it < 200) { lo -= st; st *= 2.0; ++it; }
+  double Flo = F0;
+  while (!(Flo < 0.0) && it < 200) { lo -= st; st *= 2.0; ++it; Flo = F(lo, &dF); }
   st = 1.0;
-  while (!(F(hi, &dF) > 0.0) && it < 200) { hi += st; st *= 2.0; ++it; }
-  double t = 0.5 * lnRe;
+  double Fhi = F0;
+  while (!(Fhi > 0.0) && it < 200) { hi += st; st *= 2.0; ++it; Fhi = F(hi, &dF); }
+  double t = t0;
   if (!(t > lo && t < hi)) t = 0.5 * (lo + hi);
   bool done = false;
   for (; it < 200; ++it) {
@@ -407,7 +496,7 @@ static __device__ void wall_stress(const PhysDev& ph, const double Us[5], double
   const double rhow = rho * T / Tw;
   const double a = sqrt(r / (2.0 * ph.cp * Tw));
   const double uvd = asin(a * um) / a;
-  const double muw = ph.suth_S > 0.0 ? sutherland<double>(ph, Tw) : ph.mu;
+  const double muw = ph.sutherland ? sutherland<double>(ph, Tw) : ph.mu;
   const double ut = solve_utau(ph.law, uvd, ph.hwm, muw / rhow, ph.kappa, ph.B, ok);
   const double tw = rhow * ut * ut / um;
   tau[0] = tw * ux; tau[1] = tw * uy; tau[2] = tw * uz;
@@ -417,7 +506,7 @@ static __device__ void wall_stress(const PhysDev& ph, const double Us[5], double
 // k_lift: one CTA of n^3 threads per element.
 // ---------------------------------------------------------------------------
 template <int N, typename R>
-__global__ void __launch_bounds__((N + 1) * (N + 1) * (N + 1))
+__global__ void __launch_bounds__((N + 1) * (N + 1) * (N + 1), ((N + 1) * (N + 1) * (N + 1) <= 512 ? 2 : 1))
 k_lift(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const Tables<N> tab,
        R* __restrict__ Rv, R* __restrict__ Gf) {
   constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
@@ -437,7 +526,10 @@ k_lift(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
   // own primitives W = (u, v, w, T)
   {
     R u, v, w, T;
-    velocity_temperature<R>(U[g], U[S + g], U[2 * S + g], U[3 * S + g], U[4 * S + g], ph, u, v, w, T);
+    if constexpr (std::is_same<R, float>::value)
+      velocity_temperature32(load_prim32(m.W32, S, g), ph, u, v, w, T);
+    else
+      velocity_temperature<R>(U[g], U[S + g], U[2 * S + g], U[3 * S + g], U[4 * S + g], ph, u, v, w, T);
     sW[p] = u; sW[n3 + p] = v; sW[2 * n3 + p] = w; sW[3 * n3 + p] = T;
   }
   // own metrics
@@ -457,7 +549,21 @@ k_lift(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
     if (nb >= 0) {
       const size_t gn = (size_t)nb * n3 + fnode<N>(l ^ 1, a, b);
       R u, v, w, T;
-      velocity_temperature<R>(U[gn], U[S + gn], U[2 * S + gn], U[3 * S + gn], U[4 * S + gn], ph, u, v, w, T);
+      if constexpr (std::is_same<R, float>::value)
+        velocity_temperature32(load_prim32(m.W32, S, gn), ph, u, v, w, T);
+      else
+        velocity_temperature<R>(U[gn], U[S + gn], U[2 * S + gn], U[3 * S + gn], U[4 * S + gn], ph, u, v, w, T);
+      d0 = R(0.5) * (u - Wo0); d1 = R(0.5) * (v - Wo1); d2 = R(0.5) * (w - Wo2);
+      d3 = R(0.5) * (T - Wo3);
+    } else if (nb != -1) {
+      // inflow / outflow: W* - W = (W(exterior) - W) / 2
+      const size_t gq = (size_t)e * n3 + q;
+      double Ui[5], Ub[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) Ui[v] = U[v * S + gq];
+      ghost_state(ph, nb, Ui, Ub);
+      R u, v, w, T;
+      velocity_temperature<R>(Ub[0], Ub[1], Ub[2], Ub[3], Ub[4], ph, u, v, w, T);
       d0 = R(0.5) * (u - Wo0); d1 = R(0.5) * (v - Wo1); d2 = R(0.5) * (w - Wo2);
       d3 = R(0.5) * (T - Wo3);
     } else {
@@ -515,10 +621,10 @@ k_lift(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
 #pragma unroll
     for (int v = 0; v < 4; ++v) q[d][v] *= iJ;
   // viscous flux Fv_d = (0, tau_1d, tau_2d, tau_3d, tau_jd u_j + k dT/dx_d)
-  R mu = (R)ph.mu, kc = (R)ph.kcond;
-  if (ph.suth_S > 0.0) {
+  R mu = cR<R>(ph.mu, ph.f32c.mu), kc = cR<R>(ph.kcond, ph.f32c.kcond);
+  if (ph.sutherland) {
     mu = sutherland<R>(ph, sW[3 * n3 + p]);
-    kc = mu * (R)ph.cp_Pr;
+    kc = mu * cR<R>(ph.cp_Pr, ph.f32c.cp_Pr);
   }
   const R div = q[0][0] + q[1][1] + q[2][2];
   R tau[3][3];
@@ -587,15 +693,27 @@ k_face(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
   const size_t S = (size_t)m.K * n3;
   const size_t gM = (size_t)fc.x * n3 + fnode<N>(fc.y, ab % n, ab / n);
   const size_t gS = (size_t)fc.z * n3 + fnode<N>(fc.w, ab % n, ab / n);
-  double UA[5], UB[5];
-#pragma unroll
-  for (int v = 0; v < 5; ++v) { UA[v] = U[v * S + gM]; UB[v] = U[v * S + gS]; }
-  const Prim<R> A = primitive<R>(UA[0], UA[1], UA[2], UA[3], UA[4], ph);
-  const Prim<R> B = primitive<R>(UB[0], UB[1], UB[2], UB[3], UB[4], ph);
   const size_t FN = (size_t)m.F * n2, fg = (size_t)f * n2 + ab;
   const R nx = (R)m.fgeo[fg], ny = (R)m.fgeo[FN + fg], nz = (R)m.fgeo[2 * FN + fg], s = (R)m.fgeo[3 * FN + fg];
   R F[5];
-  riemann<R, double>(ph, A, UA, B, UB, nx, ny, nz, F);
+  if constexpr (std::is_same<R, float>::value) {
+    const Prim<float> A = load_prim32(m.W32, S, gM), B = load_prim32(m.W32, S, gS);
+    // U_B - U_A for the Lax-Friedrichs dissipation, differenced in FP64 (from
+    // rounded FP32 states the difference would carry an error of eps |U|)
+    float dU[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    if (ph.surf_flux == 1) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) dU[v] = (float)(U[v * S + gS] - U[v * S + gM]);
+    }
+    riemann_d<float>(ph, A, B, dU, nx, ny, nz, F);
+  } else {
+    double UA[5], UB[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) { UA[v] = U[v * S + gM]; UB[v] = U[v * S + gS]; }
+    const Prim<R> A = primitive<R>(UA[0], UA[1], UA[2], UA[3], UA[4], ph);
+    const Prim<R> B = primitive<R>(UB[0], UB[1], UB[2], UB[3], UB[4], ph);
+    riemann<R, double>(ph, A, UA, B, UB, nx, ny, nz, F);
+  }
   R* out = Fs + (size_t)f * 5 * n2 + ab;
   out[0] = F[0] * s;
   if (ph.viscous) {
@@ -610,10 +728,54 @@ k_face(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
 }
 
 // ---------------------------------------------------------------------------
-// k_wall: one thread per node of a wall face (slip wall + wall model).
+// k_bc: one thread per node of an inflow or outflow face: the Riemann flux
+// between the interior trace and the exterior state, and the interior viscous
+// flux (the BR1 average with an exterior side that carries the same flux).
 // ---------------------------------------------------------------------------
 template <int N, typename R>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(256)
+k_bc(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const R* __restrict__ Gf,
+     R* __restrict__ Fs) {
+  constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int bf = tid / n2, ab = tid - bf * n2;
+  if (bf >= m.n_bc) return;
+  const int f = m.n_interior + m.n_wall + bf;
+  const int4 fc = m.faces[f];
+  const size_t S = (size_t)m.K * n3;
+  const size_t gM = (size_t)fc.x * n3 + fnode<N>(fc.y, ab % n, ab / n);
+  double UA[5], UB[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) UA[v] = U[v * S + gM];
+  ghost_state(ph, fc.z, UA, UB);
+  const Prim<R> A = primitive<R>(UA[0], UA[1], UA[2], UA[3], UA[4], ph);
+  const Prim<R> B = primitive<R>(UB[0], UB[1], UB[2], UB[3], UB[4], ph);
+  const size_t FN = (size_t)m.F * n2, fg = (size_t)f * n2 + ab;
+  const R nx = (R)m.fgeo[fg], ny = (R)m.fgeo[FN + fg], nz = (R)m.fgeo[2 * FN + fg], s = (R)m.fgeo[3 * FN + fg];
+  R F[5];
+  riemann<R, double>(ph, A, UA, B, UB, nx, ny, nz, F);
+  R* out = Fs + (size_t)f * 5 * n2 + ab;
+  out[0] = F[0] * s;
+  if (ph.viscous) {
+    const R* gA = Gf + ((size_t)fc.x * 6 + fc.y) * 4 * n2 + ab;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) out[(v + 1) * n2] = F[v + 1] * s - gA[v * n2];
+  } else {
+#pragma unroll
+    for (int v = 1; v < 5; ++v) out[v * n2] = F[v] * s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_wall: one thread per node of a wall face (slip wall + wall model).
+// The work per node is long (sample interpolation over n^3 nodes, Newton
+// iterations of transcendental functions) and the nodes are few, so blocks
+// are one warp: the launch spreads over all SMs instead of filling a few.
+// ---------------------------------------------------------------------------
+constexpr int WALL_THREADS = 32;
+
+template <int N, typename R>
+__global__ void __launch_bounds__(WALL_THREADS)
 k_wall(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, R* __restrict__ Fs,
        double* __restrict__ tau_out, int* __restrict__ status) {
   constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
@@ -692,6 +854,7 @@ k_wall(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, R* __
 struct StageArgs {
   double A, B, dt;
   int read_dU;
+  int write_w32;  // FP32-mixed form: store the updated state's primitives into W32
 };
 
 template <int N>
@@ -707,8 +870,17 @@ struct VolShape {
   static constexpr int SMEM_R_EC = 23 * n3 + 2 * n2 + n;
 };
 
+// Resident CTAs per SM asked of the register allocator: two for the KEP
+// kernels of up to 512 threads (64 registers; measured 5 % faster at N = 7 in
+// FP64 than one CTA at 106 registers), one for the entropy-conserving kernel
+// (about 126 registers) and for larger CTAs.
+template <int N, bool EC>
+constexpr int vol_min_blocks() {
+  return (!EC && VolShape<N>::THREADS * 64 * 2 <= 65536) ? 2 : 1;
+}
+
 template <int N, typename R, int MODE, bool EC>
-__global__ void __launch_bounds__(VolShape<N>::THREADS)
+__global__ void __launch_bounds__(VolShape<N>::THREADS, (vol_min_blocks<N, EC>()))
 k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, const Tables<N> tab,
          const R* __restrict__ Rv, const R* __restrict__ Fs, double* __restrict__ Out,
          double* __restrict__ dU, double* __restrict__ Uout, const StageArgs st, int* __restrict__ status) {
@@ -730,17 +902,24 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
     sC16[x] = (R)(0.5 * tab.DVS8[x]);
   }
   if (t < n) siw[t] = (R)tab.iw[t];
-  // prologue: node t
+  // prologue: node t (the FP32-mixed form reads the stage's FP32 primitives
+  // and loads the FP64 state only in the epilogue)
+  constexpr bool F32 = std::is_same<R, float>::value;
   double Uo[5];
   if (t < n3) {
     const size_t g = (size_t)e * n3 + t;
+    Prim<R> q;
+    if constexpr (F32) {
+      q = load_prim32(m.W32, S, g);
+    } else {
 #pragma unroll
-    for (int v = 0; v < 5; ++v) Uo[v] = Uin[v * S + g];
-    const Prim<R> q = primitive<R>(Uo[0], Uo[1], Uo[2], Uo[3], Uo[4], ph);
+      for (int v = 0; v < 5; ++v) Uo[v] = Uin[v * S + g];
+      q = primitive<R>(Uo[0], Uo[1], Uo[2], Uo[3], Uo[4], ph);
+    }
     sQ[t] = q.rho; sQ[n3 + t] = q.u; sQ[2 * n3 + t] = q.v; sQ[3 * n3 + t] = q.w;
     sQ[4 * n3 + t] = R(4) * q.p;
     if constexpr (EC) {
-      const R pf = q.p + (R)ph.p_ref;
+      const R pf = q.p + cR<R>(ph.p_ref, ph.f32c.p_ref);
       const R beta = R(0.5) * q.rho * rcp_t<R>(pf);
       const R irho = rcp_t<R>(q.rho);
       sQ[4 * n3 + t] = R(8) * beta * q.p;
@@ -751,7 +930,7 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
     } else if (!kg) {
       sQ[5 * n3 + t] = q.h;
     } else {
-      const R pf = q.p + (R)ph.p_ref;
+      const R pf = q.p + cR<R>(ph.p_ref, ph.f32c.p_ref);
       sQ[5 * n3 + t] = q.h - pf / q.rho;  // e = E / rho
       sQ[6 * n3 + t] = R(2) * pf;
     }
@@ -813,8 +992,8 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
           F2 = mf * Sv + Spt * Sa1;
           F3 = mf * Sw + Spt * Sa2;
           // 16 F_E = 2 mf (1 / (2 (gamma-1) beta_ln) + |{u}|^2 - {|u|^2} / 2) + 4 p~ (4 {u}.{a})
-          const R X = R(0.25) * (Sib * Q * (R)ph.rgm1 + Su * Su + Sv * Sv + Sw * Sw - p2 - sQ[6 * n3 + q]);
-          F4 = R(2) * mf * X + (R(0.5) * Spt + R(4) * (R)ph.p_ref) * ua;
+          const R X = R(0.25) * (Sib * Q * cR<R>(ph.rgm1, ph.f32c.rgm1) + Su * Su + Sv * Sv + Sw * Sw - p2 - sQ[6 * n3 + q]);
+          F4 = R(2) * mf * X + (R(0.5) * Spt + R(4) * cR<R>(ph.p_ref, ph.f32c.p_ref)) * ua;
         } else {
           const R Sh = hh + sQ[5 * n3 + q];
           mf = Sr * ua;                        // 8 F0
@@ -855,6 +1034,10 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
   // epilogue: node t
   const int i = t % n, j = (t / n) % n, k = t / n2;
   const size_t g = (size_t)e * n3 + t;
+  if constexpr (F32) {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) Uo[v] = Uin[v * S + g];
+  }
   R acc[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) acc[v] = sR[v * n3 + t];
@@ -879,7 +1062,7 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
   if (k == N) surf(5, i + n * j, siw[N]);
   // Ut = -(1/J) acc + S, S = (0, f, f . u)
   const R iJ = m.invJ[g];
-  const bool force = ph.f[0] != 0.0 || ph.f[1] != 0.0 || ph.f[2] != 0.0;
+  const bool force = ph.has_force != 0;
   double src[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
   if (force) {
     const double ir = 1.0 / Uo[0];
@@ -891,19 +1074,27 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
     for (int v = 0; v < 5; ++v) Out[v * S + g] = -(double)(iJ * acc[v]) + src[v];
   } else {
     // dU = A dU + dt Ut = A dU + (-dt / J) acc + dt S;  U = U + B dU
+    // (the FP32-mixed form forms the increment dt Ut in FP32, the accuracy of
+    // its Ut, and keeps the register update in FP64)
     const double c = -st.dt * (double)iJ;
+    const R cf = F32 ? (R)(-st.dt) * iJ : R(0);
     bool bad = false;
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
-      double d = c * (double)acc[v];
+      double d = F32 ? (double)(cf * acc[v]) : c * (double)acc[v];
       if (force) d = fma(st.dt, src[v], d);
       if (st.read_dU) d = fma(st.A, dU[v * S + g], d);
       const double un = fma(st.B, d, Uo[v]);
       dU[v * S + g] = d;
       Uout[v * S + g] = un;
+      Uo[v] = un;
       bad |= !finite_bits(un);
     }
     if (bad) atomicOr(status, ST_NONFINITE);
+    // the next stage's FP32 primitives, from the updated FP64 state
+    if constexpr (F32) {
+      if (st.write_w32) store_prim32(m.W32, S, g, primitive<float>(Uo[0], Uo[1], Uo[2], Uo[3], Uo[4], ph));
+    }
   }
 }
 

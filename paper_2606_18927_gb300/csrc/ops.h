@@ -8,7 +8,7 @@ namespace dg {
 struct PhysDev;
 
 struct OpArgs {
-  int N, K, F, n_interior, n_wall;
+  int N, K, F, n_interior, n_wall, n_bc;
   int fp32;                 // 0: double fluxes, 1: float fluxes (mixed form)
   const void* Ja;           // [9][K n^3] in the flux type
   const void* invJ;         // [K n^3] in the flux type
@@ -38,6 +38,11 @@ struct OpArgs {
   // paper's prioritised boundary work, Sec. 2.3); null side: one stream
   cudaStream_t side;
   cudaEvent_t fork, join;
+  // FP32-mixed form: [6][K n^3] FP32 primitives of Uin; w32_valid = 1 when they
+  // are already those of Uin (else the operator forms them first).  A stage
+  // (mode 1) leaves the primitives of Uout in W32.
+  float* W32;
+  int w32_valid;
   // adjoint (FP64): cotangent lam of Ut, output gU, and scratch
   const double* lam;
   double* gU;

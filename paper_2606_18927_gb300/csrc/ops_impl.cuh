@@ -1,6 +1,9 @@
 // ops_impl.cuh -- host launch code for one polynomial degree (included by
 // op_n<N>.cu with DG_N defined).
 #pragma once
+#include <algorithm>
+#include <type_traits>
+
 #include "adjoint.cuh"
 #include "kernels.cuh"
 #include "ops.h"
@@ -29,10 +32,11 @@ template <int N, typename R>
 static int run_typed(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {
   constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
   MeshDev<R> m;
-  m.K = a.K; m.F = a.F; m.n_interior = a.n_interior; m.n_wall = a.n_wall;
+  m.K = a.K; m.F = a.F; m.n_interior = a.n_interior; m.n_wall = a.n_wall; m.n_bc = a.n_bc;
   m.Ja = static_cast<const R*>(a.Ja); m.invJ = static_cast<const R*>(a.invJ);
   m.fgeo = a.fgeo; m.nbr = a.nbr; m.elem_face = a.elem_face; m.faces = a.faces;
   m.ws_elem = a.ws_elem; m.ws_lag = a.ws_lag;
+  m.W32 = std::is_same<R, float>::value ? a.W32 : nullptr;
   const Tables<N> tab = make_tables<N>(a.D, a.w);
   R* Rv = static_cast<R*>(a.Rv);
   R* Gf = static_cast<R*>(a.Gf);
@@ -56,7 +60,7 @@ static int run_typed(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {
   const cudaStream_t ws = fork ? a.side : s;
   auto wall = [&]() {
     if (a.n_wall == 0) return;
-    const int threads = 128;
+    const int threads = WALL_THREADS;
     const long long work = (long long)a.n_wall * n2;
     k_wall<N, R><<<(unsigned)((work + threads - 1) / threads), threads, 0, ws>>>(a.Uin, m, ph, Fs, a.tau, a.status);
   };
@@ -68,6 +72,10 @@ static int run_typed(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {
     if (a.ev) cudaEventRecord(a.ev[4], ws);
     cudaEventRecord(a.join, a.side);
   }
+  if (std::is_same<R, float>::value && !a.w32_valid) {
+    const long long S = (long long)a.K * n3;
+    k_prim32<<<(unsigned)std::min<long long>((S + 255) / 256, 152 * 16), 256, 0, s>>>(S, a.Uin, ph, a.W32);
+  }
   if (a.ev) cudaEventRecord(a.ev[0], s);
   if (ph.viscous) k_lift<N, R><<<a.K, n3, smem_lift, s>>>(a.Uin, m, ph, tab, Rv, Gf);
   if (a.ev) cudaEventRecord(a.ev[1], s);
@@ -75,6 +83,11 @@ static int run_typed(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {
     const int threads = 256;
     const long long work = (long long)a.n_interior * n2;
     k_face<N, R><<<(unsigned)((work + threads - 1) / threads), threads, 0, s>>>(a.Uin, m, ph, Gf, Fs);
+  }
+  if (a.n_bc > 0) {
+    const int threads = 256;
+    const long long work = (long long)a.n_bc * n2;
+    k_bc<N, R><<<(unsigned)((work + threads - 1) / threads), threads, 0, s>>>(a.Uin, m, ph, Gf, Fs);
   }
   if (a.ev) cudaEventRecord(a.ev[2], s);
   if (fork) {
@@ -85,7 +98,7 @@ static int run_typed(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {
     if (a.ev) cudaEventRecord(a.ev[4], s);
   }
   if (a.ev) cudaEventRecord(a.ev[5], s);
-  StageArgs st{a.A, a.B, a.dt, a.read_dU};
+  StageArgs st{a.A, a.B, a.dt, a.read_dU, std::is_same<R, float>::value && a.mode == 1 ? 1 : 0};
   if (a.mode == 0 && !ec)
     k_volume<N, R, 0, false><<<a.K, vol_threads, smem_vol, s>>>(a.Uin, m, ph, tab, Rv, Fs, a.Out, nullptr, nullptr,
                                                                 st, a.status);
@@ -106,7 +119,7 @@ template <int N>
 static int run_vjp_typed(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {
   constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
   MeshDev<double> m;
-  m.K = a.K; m.F = a.F; m.n_interior = a.n_interior; m.n_wall = a.n_wall;
+  m.K = a.K; m.F = a.F; m.n_interior = a.n_interior; m.n_wall = a.n_wall; m.n_bc = a.n_bc;
   m.Ja = static_cast<const double*>(a.Ja); m.invJ = static_cast<const double*>(a.invJ);
   m.fgeo = a.fgeo; m.nbr = a.nbr; m.elem_face = a.elem_face; m.faces = a.faces;
   m.ws_elem = a.ws_elem; m.ws_lag = a.ws_lag;
@@ -120,7 +133,7 @@ static int run_vjp_typed(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {
   }
   if (a.n_wall > 0) {
     const long long work = (long long)a.n_wall * n2;
-    k_adj_wall<N><<<(unsigned)((work + 127) / 128), 128, 0, s>>>(a.Uin, a.lam, m, ph, iw, a.gUf, a.gGf, a.gUs,
+    k_adj_wall<N><<<(unsigned)((work + WALL_THREADS - 1) / WALL_THREADS), WALL_THREADS, 0, s>>>(a.Uin, a.lam, m, ph, iw, a.gUf, a.gGf, a.gUs,
                                                                  a.gtheta, a.status);
   }
   k_adj_element<N><<<a.K, AdjShape<N>::THREADS, smem, s>>>(a.Uin, a.lam, m, ph, tab, a.gGf, a.gU, a.gWf);
@@ -138,13 +151,13 @@ static int run_wall_loss_typed(const OpArgs& a, const PhysDev& ph, const double*
                                double* loss, cudaStream_t s) {
   constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
   MeshDev<double> m;
-  m.K = a.K; m.F = a.F; m.n_interior = a.n_interior; m.n_wall = a.n_wall;
+  m.K = a.K; m.F = a.F; m.n_interior = a.n_interior; m.n_wall = a.n_wall; m.n_bc = a.n_bc;
   m.Ja = static_cast<const double*>(a.Ja); m.invJ = static_cast<const double*>(a.invJ);
   m.fgeo = a.fgeo; m.nbr = a.nbr; m.elem_face = a.elem_face; m.faces = a.faces;
   m.ws_elem = a.ws_elem; m.ws_lag = a.ws_lag;
   if (a.n_wall == 0) return 0;
   const long long work = (long long)a.n_wall * n2;
-  k_wall_loss<N><<<(unsigned)((work + 127) / 128), 128, 0, s>>>(a.Uin, m, ph, wq, inv_total, grad, loss, a.gUs,
+  k_wall_loss<N><<<(unsigned)((work + WALL_THREADS - 1) / WALL_THREADS), WALL_THREADS, 0, s>>>(a.Uin, m, ph, wq, inv_total, grad, loss, a.gUs,
                                                                 a.gtheta, a.status);
   if (grad) {
     const long long S = 5LL * a.K * n3;

@@ -44,7 +44,8 @@ class _Phys(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("R", ctypes.c_double), ("mu", ctypes.c_double),
                 ("Pr", ctypes.c_double), ("force", ctypes.c_double * 3), ("kappa", ctypes.c_double),
                 ("B", ctypes.c_double), ("hwm", ctypes.c_double), ("law", ctypes.c_int),
-                ("p_ref", ctypes.c_double), ("suth_S", ctypes.c_double), ("T_ref", ctypes.c_double)]
+                ("p_ref", ctypes.c_double), ("suth_S", ctypes.c_double), ("T_ref", ctypes.c_double),
+                ("U_in", ctypes.c_double * 5), ("p_out", ctypes.c_double)]
 
 
 class _Options(ctypes.Structure):
@@ -152,7 +153,9 @@ class Operator:
         ph = _Phys(phys["gamma"], phys["R"], phys["mu"], phys["Pr"],
                    (ctypes.c_double * 3)(phys.get("fx", 0.0), phys.get("fy", 0.0), phys.get("fz", 0.0)),
                    phys.get("kappa", 0.41), phys.get("B", 5.2), phys.get("hwm", 0.1), int(law),
-                   phys.get("p_ref", phys.get("p0", 0.0)), phys.get("suth_S", 0.0), phys.get("T_ref", 1.0))
+                   phys.get("p_ref", phys.get("p0", 0.0)), phys.get("suth_S", 0.0), phys.get("T_ref", 1.0),
+                   (ctypes.c_double * 5)(*[float(x) for x in phys.get("U_in", (1.0, 0.0, 0.0, 0.0, 1.0))]),
+                   float(phys.get("p_out", 1.0)))
         op = _Options(int(precision), int(vol_flux), int(surf_flux), int(viscous))
         h = ctypes.c_void_p()
         self._stream = _stream_handle(stream)
@@ -281,7 +284,7 @@ class Operator:
         self._check(lib().dg_check_status(self.h))
 
     def set_overlap(self, on=True):
-        """Wall-model kernel on its own high-priority stream, or in line (default)."""
+        """Wall-model kernel on its own high-priority stream (default), or in line."""
         self._check(lib().dg_set_overlap(self.h, 1 if on else 0))
 
     def profile_enable(self, on=True):

@@ -48,7 +48,9 @@ def uniform(count, lo, hi, seed=SEED, offset=0):
 # ---------------------------------------------------------------------------
 # Meshes
 # ---------------------------------------------------------------------------
-WALL = -1  # neighbour code of a wall-modelled slip wall
+WALL = -1     # neighbour code of a wall-modelled slip wall
+INFLOW = -2   # Dirichlet inflow (prescribed exterior state)
+OUTFLOW = -3  # subsonic pressure outflow (prescribed exterior pressure)
 
 
 @dataclass
@@ -58,7 +60,8 @@ class BoxSpec:
     geometry: 'affine' | 'sine' (x += a sin(y) sin(z), cyclic) |
               'channel' (tanh stretching in y + sinusoidal warp) |
               'wavy' (periodic sine warp on [0, L]^3 used for convergence)
-    periodic: per-axis flags; non-periodic axes end in wall-modelled walls.
+    periodic: per-axis flags; non-periodic axes end in the boundary codes of
+    `boundary` ((lo, hi) per axis), wall-modelled walls by default.
     """
     N: int
     nx: int
@@ -69,6 +72,7 @@ class BoxSpec:
     amplitude: float = 0.0
     stretch: float = 1.5
     periodic: tuple = (True, True, True)
+    boundary: tuple = ((WALL, WALL), (WALL, WALL), (WALL, WALL))
 
     @property
     def K(self):
@@ -88,7 +92,7 @@ def connectivity(spec: BoxSpec):
 
     Local faces: 0 -x, 1 +x, 2 -y, 3 +y, 4 -z, 5 +z.  A neighbour shares
     the opposite local face with identical face-node ordering; non-periodic
-    box ends are walls (code -1)."""
+    box ends carry the spec's boundary codes (walls, -1, by default)."""
     nx, ny, nz = spec.nx, spec.ny, spec.nz
     e = np.arange(spec.K)
     ex = e % nx; ey = (e // nx) % ny; ez = e // (nx * ny)
@@ -104,7 +108,7 @@ def connectivity(spec: BoxSpec):
                 c[axis] %= dims[axis]
                 e = c[0] + nx * (c[1] + ny * c[2])
             else:
-                e = np.where(out, WALL, (c[0] % nx) + nx * ((c[1] % ny) + ny * (c[2] % nz)))
+                e = np.where(out, spec.boundary[axis][side], (c[0] % nx) + nx * ((c[1] % ny) + ny * (c[2] % nz)))
             nbr[:, 2 * axis + side] = e
     return nbr
 

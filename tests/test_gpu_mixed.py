@@ -65,3 +65,44 @@ def test_mixed_rk_stages(ora):
     e = rel_l2(dUg.cpu().numpy(), dUo)
     print("mixed stage register rel L2", ["%.1e" % x for x in e])
     assert max(e) <= 5 * TOL_L2
+
+
+def test_mixed_primitive_buffer_follows_the_state(ora):
+    """The FP32 primitives are formed once per stage (by the previous stage's
+    epilogue) and re-formed whenever the state changed outside a stage.
+    Interleaving evaluations at other states, set_state calls and graph
+    replays must leave the stage sequence bitwise unchanged."""
+    torch = torch_cuda()
+    phys = I.phys_params(Ma=0.1, Re=1600.0)
+    spec = I.BoxSpec(3, 3, 2, 2, geometry="sine", amplitude=0.2)
+    o, g, X, U = case(ora, spec, phys, surf_flux=1, precision=dg.FP32_MIXED)
+    Ud = torch.from_numpy(U).cuda()
+    U2 = torch.from_numpy(I.perturb(U, rel=1e-2, seed=99)).cuda()
+    dt = 1e-3
+    g.set_state(Ud)
+    g.rk_steps(0.0, dt, 2)
+    ref = torch.empty_like(Ud)
+    g.get_state(ref)
+    # same steps, stage by stage, with foreign evaluations in between
+    ut_a = torch.empty_like(Ud); ut_b = torch.empty_like(Ud)
+    g.set_state(U2)
+    g.time_derivative(ut_a)              # primitives of U2
+    g.set_state(Ud)
+    for k in range(10):
+        g.rk_stage(k % 5, 0.0, dt)
+        if k % 3 == 1:
+            g.time_derivative(ut_b, U2)  # primitives of a foreign state
+    out = torch.empty_like(Ud)
+    g.get_state(out)
+    assert torch.equal(out, ref)
+    # a time derivative at U2 equals the one of a fresh context
+    g2 = dg.Operator(spec.N, X, I.connectivity(spec), phys, precision=dg.FP32_MIXED, surf_flux=1)
+    ut_c = torch.empty_like(Ud)
+    g2.time_derivative(ut_c, U2)
+    assert torch.equal(ut_a, ut_c) and torch.equal(ut_b, ut_c)
+    # graph replay of whole steps
+    g.set_state(Ud)
+    g.rk_steps_graph(0.0, dt, 2)
+    g.get_state(out)
+    g.check_status()
+    assert torch.equal(out, ref)
