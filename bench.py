@@ -39,7 +39,12 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # capture of the same kernel build on a 16^3-element case, scaled to the
 # launch size by the DOF count (traffic is proportional to the DOF count);
 # see profiles/k_volume_n7_16cubed_fp64.md.
-NCU_TRAFFIC_PER_DOF = {("k_volume", "fp64", 7): 486.6e6 / 2097152}
+NCU_TRAFFIC_PER_DOF = {("k_volume", "fp64", 7): 485.8e6 / 2097152,
+                       ("k_volume", "fp32", 7): 518.4e6 / 2097152}
+# algorithmic HBM bytes per DOF of the FP32-mixed volume kernel (stage form):
+# U read 40 and written 40, dU read and written 80, FP32 primitives read 24 and
+# written 24, Ja + 1/J 40, R_v 16, surface fluxes 3 n^2 / n^3 x 5 x 4 B x 2 sides
+MIXED_VOLUME_BYTES_PER_DOF = lambda N: 40 + 40 + 80 + 24 + 24 + 40 + 16 + 3.0 / (N + 1) * 5 * 4 * 2
 
 
 def algorithmic_flops_per_dof(N, kernel, viscous=True, surf="roe"):
@@ -284,18 +289,27 @@ def measure_variants(args, wl, X, nbr, U, op64, stream, dt):
     for s in range(args.warmup):
         opm.rk_stage(s % 5, 0.0, dt)
     torch.cuda.synchronize()
+    opm.profile_enable(True)
     e0.record(stream)
     for s in range(args.steps):
         opm.rk_stage(s % 5, 0.0, dt)
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
+    prof = opm.profile_read()
+    opm.profile_enable(False)
     opm.check_status()
     dofs = wl.spec.dofs
+    kms = {k: (v[0] / v[1] if v[1] else None) for k, v in prof.items()}
+    hbm = load_peaks().get("hbm_gbs", 6800.0)
+    vol_gbs = MIXED_VOLUME_BYTES_PER_DOF(wl.spec.N) * dofs / (kms["volume"] * 1e-3) / 1e9 if kms["volume"] else None
     out["fp32_mixed"] = {"value": dofs / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "pid_ns": ms * 1e6 / dofs,
                          "ut_rel_l2_vs_fp64_per_var": rel, "ut_rel_l2_vs_fp64": rel_all,
                          "dtype": "f32 fluxes, f64 state / RK / pressure recovery",
-                         "footprint_gb": mixed_footprint / 1e9}
+                         "footprint_gb": mixed_footprint / 1e9, "kernels_ms_per_launch": kms,
+                         "volume_roofline": {"bound": "hbm", "achieved": vol_gbs, "peak": hbm, "unit": "GB/s",
+                                             "frac": vol_gbs / hbm if vol_gbs else None,
+                                             "bytes_per_dof": MIXED_VOLUME_BYTES_PER_DOF(wl.spec.N)}}
     opm.close()
     # the production scheme of Sec. 4: entropy-conserving volume flux, Roe +
     # Harten at the faces, Sutherland viscosity (same mesh and state)
@@ -429,9 +443,14 @@ def run_ours(args):
                 "traffic": tpd * dofs if tpd else None,
                 "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 pipe)"}
     else:
+        # the mixed form's dominant kernel is the volume kernel, against HBM
         hbm = peaks.get("hbm_gbs", 6800.0)
-        roof = {"bound": "hbm", "kernel": "k_" + dom, "achieved": None, "peak": hbm, "unit": "GB/s",
-                "frac": None, "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
+        vol = kernels.get("volume")
+        ach = (MIXED_VOLUME_BYTES_PER_DOF(wl.spec.N) * dofs / (vol["ms_per_launch"] * 1e-3) / 1e9) if vol else None
+        tpd = NCU_TRAFFIC_PER_DOF.get(("k_volume", "fp32", wl.spec.N))
+        roof = {"bound": "hbm", "kernel": "k_volume", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm if ach else None, "traffic": tpd * dofs if tpd else None,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
     launches_per_step = sum(1 for k in kernels)
     # CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only)
     cpu = None

@@ -78,6 +78,10 @@ enum dg_wall_law { DG_LAW_SPALDING = 0, DG_LAW_REICHARDT = 1 };
 #define DG_BC_WALL (-1)
 #define DG_BC_INFLOW (-2)
 #define DG_BC_OUTFLOW (-3)
+/* Halo face h of a partitioned mesh (the neighbour lives on another rank):
+ * neighbour code DG_BC_HALO_BASE - h, h = 0 .. n_halo-1, each once.  See the
+ * partitioning section below. */
+#define DG_BC_HALO_BASE (-16)
 
 typedef struct dg_ctx dg_ctx;
 
@@ -241,6 +245,60 @@ int dg_set_rk_register(dg_ctx* c, const double* dU, int on_device);
 /* Reads and clears the device status flags.  Returns DG_OK,
  * DG_ERR_NONFINITE or DG_ERR_WM_NOCONV (synchronises the stream). */
 int dg_check_status(dg_ctx* c);
+
+/* ---------------------------------------------------------------------------
+ * Partitioned meshes (Sec. 2.3: non-overlapping subdomains along a
+ * space-filling curve, one per rank and GPU).  Host functions need no GPU.
+ *
+ * dg_partition_sfc: part[K] (host) <- the rank of every element: elements
+ *   ordered by the Morton key of their node-average centroid in the mesh's
+ *   bounding box (21 bits per axis), cut into nranks contiguous runs of
+ *   floor(K / nranks) or one more elements.  1 <= nranks <= K.
+ *   X: host double[3][K][n^3] as in dg_mesh_desc.
+ * dg_partition_local: the local mesh of `rank`: K_local elements (its own,
+ *   in ascending global order; l2g[K_local] their global ids), nbr_local
+ *   [K_local][6] with local neighbours, the global boundary codes, and
+ *   DG_BC_HALO_BASE - h for the h-th face shared with another rank.
+ *   halo[n_halo][4] (peer rank, local element, local face, 1 if the local
+ *   element is the face's master, i.e. it is its +xi/+eta/+zeta face).  The
+ *   halo faces are ordered by peer, then by (global master element, master
+ *   face), so two ranks list the faces they share in the same order and their
+ *   halo buffers line up.  Call once with NULL arrays to get K_local and
+ *   n_halo, then with arrays of those sizes.
+ *
+ * A context built from a local mesh (dg_init_mesh with nbr_local) owns halo
+ * buffers: recv_U/send_U double[n_halo][5][n^2] (state traces at the halo
+ * faces' nodes, in the local face's node order, which the neighbour shares)
+ * and recv_G/send_G [n_halo][4][n^2] in the flux type (float in the
+ * FP32-mixed form): each side's outward viscous flux there.  The caller moves
+ * send_* of one rank into recv_* of the peer (the rows of the faces they
+ * share, in the same order) between the phases of an evaluation:
+ *   phase 1  packs send_U;                 then exchange U traces,
+ *   phase 2  lifting, packs send_G;        then exchange viscous traces,
+ *   phase 4  face fluxes (a halo face's flux is evaluated by both ranks from
+ *            the same master and slave data) and the volume kernel.
+ * Before the first evaluation the slave side of each halo face must receive
+ * the master's normals: dg_halo_geometry writes the context's halo-face
+ * geometry [n_halo][4][n^2] (unit normal of the master, surface element) to a
+ * host array; send it to the peer, whose dg_halo_set_geometry installs the
+ * rows of the faces where its element is the slave.  The fused calls
+ * (dg_time_derivative, dg_rk_stage, ...) refuse partitioned contexts with
+ * DG_ERR_ARG, and the adjoint with DG_ERR_NOT_IMPLEMENTED.  Wall-model sample
+ * points must lie in local elements (else dg_init_mesh fails, DG_ERR_MESH).
+ * Results equal those of the unpartitioned mesh bitwise.
+ * ------------------------------------------------------------------------- */
+int dg_partition_sfc(int N, int K, const double* X, int nranks, int* part);
+int dg_partition_local(int K, const int* nbr, const int* part, int rank, int* K_local, int* l2g, int* nbr_local,
+                       int* n_halo, int* halo);
+int dg_halo_buffers(dg_ctx* c, int* n_halo, void** send_U, void** recv_U, void** send_G, void** recv_G);
+int dg_halo_geometry(dg_ctx* c, double* fgeo);
+int dg_halo_set_geometry(dg_ctx* c, const double* fgeo);
+/* One LSERK4 stage s (0..4) of the context's state, in phases 1, 2, 4 (in
+ * that order, halo exchanges between them). */
+int dg_stage_phase(dg_ctx* c, int phase, int s, double t, double dt);
+/* Ut = DG_Operator(U) in phases 1, 2, 4; U (device, or NULL for the
+ * context's state) and Ut (device) must be the same in the three calls. */
+int dg_time_derivative_phase(dg_ctx* c, int phase, const double* U, double* Ut);
 
 /* Per-kernel timing with CUDA events on the context's stream (tracing).
  * dg_profile_enable(c, 1) records events around the lift, face, wall and

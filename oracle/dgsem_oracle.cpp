@@ -437,7 +437,21 @@ static bool build_wall_samples(Mesh& M, real hwm, std::string& err) {
             xs[c] = M.X[(size_t)c * K * n3 + (size_t)e * n3 + p] - hwm * nout;
           }
           int best = -1; real bref[3] = {0, 0, 0};
-          for (int c2 = 0; c2 < K; ++c2) {
+          // first the wall element's column: the wall element, then its
+          // neighbours across the faces opposite the wall (up to 3 layers)
+          for (int c2 = e, layer = 0; c2 >= 0 && layer < 4 && best < 0; ++layer) {
+            real ref[3];
+            if (locate_point(M, c2, xs, ref)) {
+              real rm = std::max(std::fabs(ref[0]), std::max(std::fabs(ref[1]), std::fabs(ref[2])));
+              if (rm <= 1.0 + 1e-8) {
+                best = c2;
+                for (int c = 0; c < 3; ++c) bref[c] = ref[c];
+              }
+            }
+            c2 = M.nbr[c2 * 6 + (l ^ 1)];
+          }
+          // else the lowest-index element containing the point
+          for (int c2 = 0; c2 < K && best < 0; ++c2) {
             bool inside = true;
             for (int c = 0; c < 3; ++c) {
               real marg = 0.05 * (bmax[c2 * 3 + c] - bmin[c2 * 3 + c]) + 1e-12;

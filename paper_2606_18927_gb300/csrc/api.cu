@@ -40,6 +40,12 @@ struct dg_ctx {
   // FP32-mixed form: FP32 primitives [6][S]; w32_of_U says they are those of U
   float* W32 = nullptr;
   bool w32_of_U = false;
+  // partitioned meshes: halo buffers [n_halo][5][n2] (state traces, FP64) and
+  // [n_halo][4][n2] (viscous-flux traces, flux type), received and sent
+  double* halo_U = nullptr;
+  double* send_U = nullptr;
+  void* halo_G = nullptr;
+  void* send_G = nullptr;
   dg::Geometry geo;
   // device storage
   double* U = nullptr;
@@ -123,7 +129,7 @@ void free_all(dg_ctx* c) {
   void* ptrs[] = {c->U, c->dU, c->io, c->io2, c->Ja, c->invJ, c->fgeo, c->nbr, c->elem_face, c->faces,
                   c->ws_elem, c->ws_lag, c->Rv, c->Gf, c->Fs, c->tau, c->status,
                   c->gUf, c->gGf, c->gWf, c->gUs, c->gtheta, c->wq, c->ro_ckpt, c->ro_stage, c->ro_work,
-                  c->ro_scalar, c->wJ, c->W32};
+                  c->ro_scalar, c->wJ, c->W32, c->halo_U, c->send_U, c->halo_G, c->send_G};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -132,7 +138,10 @@ void free_all(dg_ctx* c) {
 constexpr size_t kEventsPerLaunch = 7;
 
 int launch(dg_ctx* c, const double* Uin, int mode, double* Out, double A, double B, double dt, int read_dU,
-           double* Uout, double* dU = nullptr) {
+           double* Uout, double* dU = nullptr, int phase = 7) {
+  if (phase == 7 && c->geo.n_halo > 0)
+    return fail(c, DG_ERR_ARG, "a partitioned context evaluates in phases around its halo exchanges "
+                               "(dg_stage_phase, dg_time_derivative_phase)");
   dg::OpArgs a{};
   a.N = c->N; a.K = c->K; a.F = c->F; a.n_interior = c->geo.n_interior; a.n_wall = c->geo.n_wall;
   a.n_bc = c->geo.n_bc;
@@ -145,7 +154,10 @@ int launch(dg_ctx* c, const double* Uin, int mode, double* Out, double A, double
   a.A = A; a.B = B; a.dt = dt; a.read_dU = read_dU;
   a.ev = nullptr;
   if (c->overlap && c->side) { a.side = c->side; a.fork = c->fork_ev; a.join = c->join_ev; }
-  if (c->profiling) {
+  a.phase = phase;
+  a.n_halo = c->geo.n_halo;
+  a.halo_U = c->halo_U; a.halo_G = c->halo_G; a.send_U = c->send_U; a.send_G = c->send_G;
+  if (c->profiling && phase == 7) {
     if (c->events_used + kEventsPerLaunch > c->events.size()) {
       for (int x = 0; x < kEventsPerLaunch * 64; ++x) {
         cudaEvent_t ev;
@@ -165,7 +177,8 @@ int launch(dg_ctx* c, const double* Uin, int mode, double* Out, double A, double
     return cuda_fail(c, (cudaError_t)rc, "kernel launch");
   }
   // the FP32 primitives now belong to the stage's output (mode 1) or input
-  if (a.fp32) c->w32_of_U = mode == 1 ? (Uout == c->U) : (Uin == c->U);
+  if (a.fp32 && (phase & 4)) c->w32_of_U = mode == 1 ? (Uout == c->U) : (Uin == c->U);
+  else if (a.fp32 && (phase & 2)) c->w32_of_U = (Uin == c->U);
   return DG_OK;
 }
 
@@ -275,6 +288,7 @@ int noalloc_args(dg_ctx* c, const double* U, double* Ut, OpArgs* a, const PhysDe
   *a = OpArgs{};
   a->N = c->N; a->K = c->K; a->F = c->F; a->n_interior = c->geo.n_interior; a->n_wall = c->geo.n_wall;
   a->n_bc = c->geo.n_bc;
+  a->n_halo = c->geo.n_halo;
   a->fp32 = c->opts.precision == DG_FP32_MIXED;
   a->Ja = c->Ja; a->invJ = c->invJ; a->fgeo = c->fgeo; a->nbr = c->nbr; a->elem_face = c->elem_face;
   a->faces = c->faces; a->ws_elem = c->ws_elem; a->ws_lag = c->ws_lag;
@@ -390,6 +404,13 @@ int dg_init_mesh(dg_ctx** out, const dg_mesh_desc* m, const dg_phys* p, const dg
   chk(cudaMalloc(&c->Gf, (o->viscous ? 24 * (size_t)c->K * n2 : 1) * rs));
   chk(cudaMalloc(&c->Fs, 5 * (size_t)c->F * n2 * rs));
   if (f32) chk(alloc(&c->W32, 6 * S));
+  if (c->geo.n_halo > 0) {
+    const size_t nh = (size_t)c->geo.n_halo;
+    chk(alloc(&c->halo_U, nh * 5 * n2));
+    chk(alloc(&c->send_U, nh * 5 * n2));
+    chk(cudaMalloc(&c->halo_G, nh * 4 * n2 * rs));
+    chk(cudaMalloc(&c->send_G, nh * 4 * n2 * rs));
+  }
   chk(alloc(&c->status, 1));
   if (e != cudaSuccess) { free_all(c); delete c; return cuda_fail(nullptr, e, "dg_init_mesh: allocation"); }
   // uploads (metrics transposed to [9][S], comp-major for coalesced loads)
@@ -548,6 +569,60 @@ int dg_rk_steps(dg_ctx* c, double t, double dt, int nsteps) {
   return DG_OK;
 }
 
+int dg_halo_buffers(dg_ctx* c, int* n_halo, void** send_U, void** recv_U, void** send_G, void** recv_G) {
+  if (!c || !n_halo) return c ? fail(c, DG_ERR_ARG, "dg_halo_buffers: null n_halo") : DG_ERR_ARG;
+  *n_halo = c->geo.n_halo;
+  if (send_U) *send_U = c->send_U;
+  if (recv_U) *recv_U = c->halo_U;
+  if (send_G) *send_G = c->send_G;
+  if (recv_G) *recv_G = c->halo_G;
+  return DG_OK;
+}
+
+int dg_halo_geometry(dg_ctx* c, double* fgeo) {
+  if (!c || !fgeo) return c ? fail(c, DG_ERR_ARG, "dg_halo_geometry: null output") : DG_ERR_ARG;
+  const size_t n2 = c->n2, F = (size_t)c->F, f0 = F - (size_t)c->geo.n_halo;
+  for (size_t h = 0; h < (size_t)c->geo.n_halo; ++h)
+    for (int k = 0; k < 4; ++k)
+      std::memcpy(fgeo + (h * 4 + k) * n2, c->geo.fgeo.data() + k * F * n2 + (f0 + h) * n2, n2 * sizeof(double));
+  return DG_OK;
+}
+
+int dg_halo_set_geometry(dg_ctx* c, const double* fgeo) {
+  if (!c || !fgeo) return c ? fail(c, DG_ERR_ARG, "dg_halo_set_geometry: null input") : DG_ERR_ARG;
+  const size_t n2 = c->n2, F = (size_t)c->F, f0 = F - (size_t)c->geo.n_halo;
+  for (size_t h = 0; h < (size_t)c->geo.n_halo; ++h) {
+    if (c->geo.faces[f0 + h].lS) continue;  // the local element is the master: keep its own
+    for (int k = 0; k < 4; ++k)
+      std::memcpy(c->geo.fgeo.data() + k * F * n2 + (f0 + h) * n2, fgeo + (h * 4 + k) * n2, n2 * sizeof(double));
+  }
+  cudaError_t e = cudaMemcpy(c->fgeo, c->geo.fgeo.data(), c->geo.fgeo.size() * sizeof(double),
+                             cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(c, e, "dg_halo_set_geometry");
+  return DG_OK;
+}
+
+int dg_stage_phase(dg_ctx* c, int phase, int s, double t, double dt) {
+  (void)t;
+  if (!c) return DG_ERR_ARG;
+  if (s < 0 || s > 4) return fail(c, DG_ERR_ARG, "dg_stage_phase: stage must be 0..4");
+  if (phase != 1 && phase != 2 && phase != 4) return fail(c, DG_ERR_ARG, "dg_stage_phase: phase must be 1, 2 or 4");
+  if (!c->state_set) return fail(c, DG_ERR_NOT_INIT, "dg_stage_phase: state not set");
+  return launch(c, c->U, 1, nullptr, kRkA[s], kRkB[s], dt, s > 0 ? 1 : 0, c->U, nullptr, phase);
+}
+
+int dg_time_derivative_phase(dg_ctx* c, int phase, const double* U, double* Ut) {
+  if (!c || !Ut) return c ? fail(c, DG_ERR_ARG, "dg_time_derivative_phase: null Ut") : DG_ERR_ARG;
+  if (phase != 1 && phase != 2 && phase != 4)
+    return fail(c, DG_ERR_ARG, "dg_time_derivative_phase: phase must be 1, 2 or 4");
+  const double* Uin = U;
+  if (!U) {
+    if (!c->state_set) return fail(c, DG_ERR_NOT_INIT, "dg_time_derivative_phase: state not set");
+    Uin = c->U;
+  }
+  return launch(c, Uin, 0, Ut, 0, 0, 0, 0, nullptr, nullptr, phase);
+}
+
 int dg_set_params(dg_ctx* c, double kappa, double B) {
   if (!c) return DG_ERR_ARG;
   if (!(kappa > 0.0)) return fail(c, DG_ERR_ARG, "dg_set_params: kappa must be positive");
@@ -599,7 +674,7 @@ static int check_adjoint_options(dg_ctx* c, const char* who) {
     return fail(c, DG_ERR_NOT_IMPLEMENTED, std::string(who) + ": the adjoint needs the Pirozzoli volume flux");
   if (c->phys.suth_S > 0.0)
     return fail(c, DG_ERR_NOT_IMPLEMENTED, std::string(who) + ": the adjoint needs a constant viscosity");
-  if (c->geo.n_bc > 0)
+  if (c->geo.n_bc > 0 || c->geo.n_halo > 0)
     return fail(c, DG_ERR_NOT_IMPLEMENTED, std::string(who) + ": the adjoint covers periodic and wall faces only");
   return DG_OK;
 }

@@ -226,7 +226,7 @@ static bool faces(Geometry& g, std::string& err) {
   for (int e = 0; e < K; ++e)
     for (int l = 0; l < 6; ++l) {
       const int nb = g.nbr[e * 6 + l];
-      if (nb < BC_CODE_MIN || nb >= K) { err = "neighbour index out of range"; return false; }
+      if ((nb < BC_CODE_MIN && nb > HALO_BASE) || nb >= K) { err = "neighbour index out of range"; return false; }
       if (nb < 0) continue;
       if (g.nbr[nb * 6 + (l ^ 1)] != e) { err = "connectivity is not reciprocal"; return false; }
       // the two sides must coincide up to a single translation
@@ -267,18 +267,40 @@ static bool faces(Geometry& g, std::string& err) {
   for (int e = 0; e < K; ++e)
     for (int l = 0; l < 6; ++l) {
       const int nb = g.nbr[e * 6 + l];
-      if (nb < 0 && nb != BC_CODE_WALL) {
+      if (nb < 0 && nb != BC_CODE_WALL && nb > HALO_BASE) {
         const int id = (int)g.faces.size();
         g.faces.push_back({e, l, nb, -1});
         g.elem_face[e * 6 + l] = 2 * id;
       }
     }
   g.n_bc = (int)g.faces.size() - g.n_interior - g.n_wall;
+  // halo faces, in halo-index order; the local element is the face's master
+  // when the face is its +xi / +eta / +zeta face, as for interior faces
+  {
+    std::vector<int> hid;
+    for (int e = 0; e < K; ++e)
+      for (int l = 0; l < 6; ++l)
+        if (g.nbr[e * 6 + l] <= HALO_BASE) hid.push_back(e * 6 + l);
+    std::sort(hid.begin(), hid.end(), [&](int a, int b) { return g.nbr[a] > g.nbr[b]; });
+    for (size_t i = 0; i < hid.size(); ++i) {
+      const int e = hid[i] / 6, l = hid[i] % 6, h = HALO_BASE - g.nbr[hid[i]];
+      if (h != (int)i) { err = "halo face indices must be 0 .. n_halo-1, each once"; return false; }
+      const int id = (int)g.faces.size();
+      const int master = (l & 1) ? 1 : 0;
+      g.faces.push_back({e, l, h, master});
+      g.elem_face[e * 6 + l] = 2 * id + (master ? 0 : 1);
+    }
+    g.n_halo = (int)hid.size();
+  }
   const size_t F = g.faces.size();
   g.fgeo.assign(4 * F * n2, 0.0);
+  const size_t F_halo0 = F - (size_t)g.n_halo;
   for (size_t f = 0; f < F; ++f) {
     const Face& fc = g.faces[f];
-    const double sgn = (fc.lM & 1) ? 1.0 : -1.0;
+    // the master's outward normal; a halo face whose local element is the
+    // slave takes the negated own normal until the master's is installed
+    double sgn = (fc.lM & 1) ? 1.0 : -1.0;
+    if (f >= F_halo0 && fc.lS == 0) sgn = -sgn;
     for (int ab = 0; ab < n2; ++ab) {
       const int p = face_node(n, fc.lM, ab % n, ab / n);
       const double* ja = &g.Ja[((size_t)fc.eM * n3 + p) * 9 + (fc.lM / 2) * 3];
@@ -374,16 +396,27 @@ static bool wall_samples(Geometry& g, double hwm, std::string& err) {
         }
     }
     std::sort(cand.begin(), cand.end());
+    // search order: the wall element's column first (the wall element, then
+    // its neighbours across the faces opposite the wall, up to 3 layers; a
+    // choice that does not depend on element numbering or partitioning), then
+    // the remaining candidates by ascending index
+    std::vector<int> order;
+    for (int c = fc.eM, layer = 0; c >= 0 && layer < 4; ++layer) {
+      order.push_back(c);
+      c = g.nbr[c * 6 + (fc.lM ^ 1)];
+    }
+    for (int c : cand)
+      if (std::find(order.begin(), order.end(), c) == order.end()) order.push_back(c);
     for (int ab = 0; ab < n2; ++ab) {
       const int p = face_node(n, fc.lM, ab % n, ab / n);
       double xs[3];
       for (int c = 0; c < 3; ++c)
         xs[c] = g.X[(size_t)c * K * n3 + (size_t)fc.eM * n3 + p] - hwm * g.fgeo[(size_t)c * F * n2 + (size_t)f * n2 + ab];
-      // the lowest-index element containing the point (within 1e-8 in the
-      // reference coordinates): points on a shared face get one element
+      // the first element in that order containing the point (within 1e-8 in
+      // the reference coordinates): points on a shared face get one element
       int best = -1;
       double br[3] = {0, 0, 0};
-      for (int e : cand) {
+      for (int e : order) {
         bool in = true;
         for (int c = 0; c < 3; ++c) {
           const double pad = 0.05 * (hi[e * 3 + c] - lo[e * 3 + c]) + 1e-12;

@@ -29,10 +29,13 @@ void lagrange_at(const Basis& b, double s, double* l);
 
 // neighbour codes of boundary faces (dg.h: DG_BC_WALL, DG_BC_INFLOW, DG_BC_OUTFLOW)
 constexpr int BC_CODE_WALL = -1, BC_CODE_INFLOW = -2, BC_CODE_OUTFLOW = -3, BC_CODE_MIN = -3;
+// halo face h of a partitioned mesh: neighbour code HALO_BASE - h (dg.h: DG_BC_HALO_BASE)
+constexpr int HALO_BASE = -16;
 
 struct Face {
   int eM, lM;  // master element and its local face
-  int eS, lS;  // slave element and local face; boundary faces: eS = the code, lS = -1
+  int eS, lS;  // slave element and local face; boundary faces: eS = the code, lS = -1;
+               // halo faces: eS = the halo index, lS = 1 if the local element is the master
 };
 
 struct Geometry {
@@ -42,8 +45,8 @@ struct Geometry {
   std::vector<double> X;         // [3][K*n3]
   std::vector<double> Ja;        // [K*n3][3 dir][3 comp]
   std::vector<double> J;         // [K*n3]
-  std::vector<Face> faces;       // interior faces, then wall faces, then inflow / outflow faces
-  int n_interior = 0, n_wall = 0, n_bc = 0;
+  std::vector<Face> faces;       // interior, wall, inflow / outflow, then halo faces
+  int n_interior = 0, n_wall = 0, n_bc = 0, n_halo = 0;
   std::vector<int> elem_face;    // [K*6] = 2 * face id + side (0 master, 1 slave)
   std::vector<double> fgeo;      // [4][F*n2]: unit normal (master outward) and s
   std::vector<int> ws_elem;      // [n_wall*n2] element containing the sample point

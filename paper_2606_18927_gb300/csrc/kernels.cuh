@@ -59,7 +59,10 @@ __device__ __forceinline__ R cR(double d, float f) {
 // device-side views of the context's arrays
 template <typename R>
 struct MeshDev {
-  int K, F, n_interior, n_wall, n_bc;  // faces: interior, walls, inflow / outflow
+  int K, F, n_interior, n_wall, n_bc;  // faces: interior, walls, inflow / outflow, then halo
+  int n_halo;                          // halo faces of a partitioned mesh (the last n_halo faces)
+  const double* halo_U;                // [n_halo][5][n2] remote traces of the state
+  const R* halo_G;                     // [n_halo][4][n2] remote outward viscous fluxes
   const R* Ja;           // [9][K*n3] (dir*3+comp)
   const R* invJ;         // [K*n3]
   const double* fgeo;    // [4][F*n2]
@@ -555,6 +558,13 @@ k_lift(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
         velocity_temperature<R>(U[gn], U[S + gn], U[2 * S + gn], U[3 * S + gn], U[4 * S + gn], ph, u, v, w, T);
       d0 = R(0.5) * (u - Wo0); d1 = R(0.5) * (v - Wo1); d2 = R(0.5) * (w - Wo2);
       d3 = R(0.5) * (T - Wo3);
+    } else if (nb <= -16) {
+      // halo face: the remote element's trace from the halo buffer
+      const double* src = m.halo_U + (size_t)(-16 - nb) * 5 * n2 + ab;
+      R u, v, w, T;
+      velocity_temperature<R>(src[0], src[n2], src[2 * n2], src[3 * n2], src[4 * n2], ph, u, v, w, T);
+      d0 = R(0.5) * (u - Wo0); d1 = R(0.5) * (v - Wo1); d2 = R(0.5) * (w - Wo2);
+      d3 = R(0.5) * (T - Wo3);
     } else if (nb != -1) {
       // inflow / outflow: W* - W = (W(exterior) - W) / 2
       const size_t gq = (size_t)e * n3 + q;
@@ -728,6 +738,78 @@ k_face(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
 }
 
 // ---------------------------------------------------------------------------
+// Halo faces of a partitioned mesh.  Both ranks of a shared face evaluate its
+// flux from the same master and slave traces (one side from the halo buffer)
+// with the master's normal, so both get the value a single-domain run gets.
+// ---------------------------------------------------------------------------
+template <int N, typename R>
+__global__ void __launch_bounds__(256)
+k_halo_face(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const R* __restrict__ Gf,
+            R* __restrict__ Fs) {
+  constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int h = tid / n2, ab = tid - h * n2;
+  if (h >= m.n_halo) return;
+  const int f = m.F - m.n_halo + h;
+  const int4 fc = m.faces[f];  // (local element, local face, halo index, local is master)
+  const size_t S = (size_t)m.K * n3;
+  const size_t gL = (size_t)fc.x * n3 + fnode<N>(fc.y, ab % n, ab / n);
+  const double* rU = m.halo_U + (size_t)h * 5 * n2 + ab;
+  const bool master = fc.w != 0;
+  double UA[5], UB[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    const double loc = U[v * S + gL], rem = rU[v * n2];
+    UA[v] = master ? loc : rem;
+    UB[v] = master ? rem : loc;
+  }
+  const size_t FN = (size_t)m.F * n2, fg = (size_t)f * n2 + ab;
+  const R nx = (R)m.fgeo[fg], ny = (R)m.fgeo[FN + fg], nz = (R)m.fgeo[2 * FN + fg], s = (R)m.fgeo[3 * FN + fg];
+  const Prim<R> A = primitive<R>(UA[0], UA[1], UA[2], UA[3], UA[4], ph);
+  const Prim<R> B = primitive<R>(UB[0], UB[1], UB[2], UB[3], UB[4], ph);
+  R F[5];
+  riemann<R, double>(ph, A, UA, B, UB, nx, ny, nz, F);
+  R* out = Fs + (size_t)f * 5 * n2 + ab;
+  out[0] = F[0] * s;
+  if (ph.viscous) {
+    const R* gl = Gf + ((size_t)fc.x * 6 + fc.y) * 4 * n2 + ab;
+    const R* gr = m.halo_G + (size_t)h * 4 * n2 + ab;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const R gA = master ? gl[v * n2] : gr[v * n2], gB = master ? gr[v * n2] : gl[v * n2];
+      out[(v + 1) * n2] = F[v + 1] * s - R(0.5) * (gA - gB);
+    }
+  } else {
+#pragma unroll
+    for (int v = 1; v < 5; ++v) out[v * n2] = F[v] * s;
+  }
+}
+
+// the local traces of the halo faces: state (before the lifting) and own
+// outward viscous flux (after it), in the halo-buffer layout
+template <int N, typename R>
+__global__ void __launch_bounds__(256)
+k_halo_pack(const double* __restrict__ U, const MeshDev<R> m, const R* __restrict__ Gf, double* __restrict__ sendU,
+            R* __restrict__ sendG) {
+  constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int h = tid / n2, ab = tid - h * n2;
+  if (h >= m.n_halo) return;
+  const int4 fc = m.faces[m.F - m.n_halo + h];
+  if (sendU) {
+    const size_t S = (size_t)m.K * n3;
+    const size_t gL = (size_t)fc.x * n3 + fnode<N>(fc.y, ab % n, ab / n);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) sendU[((size_t)h * 5 + v) * n2 + ab] = U[v * S + gL];
+  }
+  if (sendG) {
+    const R* gl = Gf + ((size_t)fc.x * 6 + fc.y) * 4 * n2 + ab;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) sendG[((size_t)h * 4 + v) * n2 + ab] = gl[v * n2];
+  }
+}
+
+// ---------------------------------------------------------------------------
 // k_bc: one thread per node of an inflow or outflow face: the Riemann flux
 // between the interior trace and the exterior state, and the interior viscous
 // flux (the BR1 average with an exterior side that carries the same flux).
@@ -870,17 +952,18 @@ struct VolShape {
   static constexpr int SMEM_R_EC = 23 * n3 + 2 * n2 + n;
 };
 
-// Resident CTAs per SM asked of the register allocator: two for the KEP
-// kernels of up to 512 threads (64 registers; measured 5 % faster at N = 7 in
-// FP64 than one CTA at 106 registers), one for the entropy-conserving kernel
-// (about 126 registers) and for larger CTAs.
-template <int N, bool EC>
+// Resident CTAs per SM asked of the register allocator: two for CTAs of up to
+// 512 threads (64 registers; measured 5 % faster at N = 7 in FP64 than one CTA
+// at 106 registers, and 1.6x faster for the FP32 entropy-conserving kernel
+// than one CTA at 104), except the FP64 entropy-conserving kernel (about 126
+// registers, one CTA).
+template <int N, typename R, bool EC>
 constexpr int vol_min_blocks() {
-  return (!EC && VolShape<N>::THREADS * 64 * 2 <= 65536) ? 2 : 1;
+  return ((!EC || std::is_same<R, float>::value) && VolShape<N>::THREADS * 64 * 2 <= 65536) ? 2 : 1;
 }
 
 template <int N, typename R, int MODE, bool EC>
-__global__ void __launch_bounds__(VolShape<N>::THREADS, (vol_min_blocks<N, EC>()))
+__global__ void __launch_bounds__(VolShape<N>::THREADS, (vol_min_blocks<N, R, EC>()))
 k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, const Tables<N> tab,
          const R* __restrict__ Rv, const R* __restrict__ Fs, double* __restrict__ Out,
          double* __restrict__ dU, double* __restrict__ Uout, const StageArgs st, int* __restrict__ status) {

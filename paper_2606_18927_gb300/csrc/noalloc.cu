@@ -60,6 +60,8 @@ extern "C" int dg_time_derivative_noalloc(dg_ctx* c, const double* U, double* Ut
   size_t rv = 0, gf = 0, fs = 0;
   int rc = dg::noalloc_args(c, U, Ut, &a, &ph, &stream, &rv, &gf, &fs);
   if (rc != DG_OK) return rc;
+  if (a.n_halo > 0)
+    return dg::noalloc_fail(c, DG_ERR_ARG, "dg_time_derivative_noalloc: not for partitioned contexts");
   const size_t need = align256(rv) + align256(gf) + align256(fs);
   if (need > (size_t)DG_NOALLOC_SCRATCH_BYTES)
     return dg::noalloc_fail(c, DG_ERR_ARG,

@@ -43,6 +43,16 @@ struct OpArgs {
   // (mode 1) leaves the primitives of Uout in W32.
   float* W32;
   int w32_valid;
+  // partitioned meshes: n_halo halo faces (the last faces), remote traces in
+  // halo_U / halo_G, local traces packed into send_U / send_G.  phase selects
+  // part of an evaluation: 1 packs the state traces, 2 runs the lifting and
+  // packs the viscous-flux traces, 4 the faces and the volume kernel (7: all)
+  int n_halo;
+  const double* halo_U;
+  const void* halo_G;
+  double* send_U;
+  void* send_G;
+  int phase;
   // adjoint (FP64): cotangent lam of Ut, output gU, and scratch
   const double* lam;
   double* gU;

@@ -37,6 +37,7 @@ static int run_typed(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {
   m.fgeo = a.fgeo; m.nbr = a.nbr; m.elem_face = a.elem_face; m.faces = a.faces;
   m.ws_elem = a.ws_elem; m.ws_lag = a.ws_lag;
   m.W32 = std::is_same<R, float>::value ? a.W32 : nullptr;
+  m.n_halo = a.n_halo; m.halo_U = a.halo_U; m.halo_G = static_cast<const R*>(a.halo_G);
   const Tables<N> tab = make_tables<N>(a.D, a.w);
   R* Rv = static_cast<R*>(a.Rv);
   R* Gf = static_cast<R*>(a.Gf);
@@ -54,6 +55,11 @@ static int run_typed(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {
     cudaFuncSetAttribute(k_volume<N, R, 0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_vol);
     cudaFuncSetAttribute(k_volume<N, R, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_vol);
   }
+  const int phase = a.phase ? a.phase : 7;
+  const unsigned halo_blocks = (unsigned)(((long long)a.n_halo * n2 + 255) / 256);
+  if ((phase & 1) && a.n_halo > 0 && a.send_U)
+    k_halo_pack<N, R><<<halo_blocks, 256, 0, s>>>(a.Uin, m, Gf, a.send_U, nullptr);
+  if (!(phase & 6)) return (int)cudaGetLastError();
   // the wall kernel reads only U and writes only the wall faces' fluxes, so
   // it may run beside the lifting and the interior faces
   const bool fork = a.side != nullptr && a.n_wall > 0;
@@ -64,21 +70,26 @@ static int run_typed(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {
     const long long work = (long long)a.n_wall * n2;
     k_wall<N, R><<<(unsigned)((work + threads - 1) / threads), threads, 0, ws>>>(a.Uin, m, ph, Fs, a.tau, a.status);
   };
-  if (fork) {
-    cudaEventRecord(a.fork, s);
-    cudaStreamWaitEvent(a.side, a.fork, 0);
-    if (a.ev) cudaEventRecord(a.ev[3], ws);
-    wall();
-    if (a.ev) cudaEventRecord(a.ev[4], ws);
-    cudaEventRecord(a.join, a.side);
+  if (phase & 2) {
+    if (fork) {
+      cudaEventRecord(a.fork, s);
+      cudaStreamWaitEvent(a.side, a.fork, 0);
+      if (a.ev) cudaEventRecord(a.ev[3], ws);
+      wall();
+      if (a.ev) cudaEventRecord(a.ev[4], ws);
+      cudaEventRecord(a.join, a.side);
+    }
+    if (std::is_same<R, float>::value && !a.w32_valid) {
+      const long long S = (long long)a.K * n3;
+      k_prim32<<<(unsigned)std::min<long long>((S + 255) / 256, 152 * 16), 256, 0, s>>>(S, a.Uin, ph, a.W32);
+    }
+    if (a.ev) cudaEventRecord(a.ev[0], s);
+    if (ph.viscous) k_lift<N, R><<<a.K, n3, smem_lift, s>>>(a.Uin, m, ph, tab, Rv, Gf);
+    if (a.ev) cudaEventRecord(a.ev[1], s);
+    if (a.n_halo > 0 && a.send_G && ph.viscous)
+      k_halo_pack<N, R><<<halo_blocks, 256, 0, s>>>(a.Uin, m, Gf, nullptr, static_cast<R*>(a.send_G));
   }
-  if (std::is_same<R, float>::value && !a.w32_valid) {
-    const long long S = (long long)a.K * n3;
-    k_prim32<<<(unsigned)std::min<long long>((S + 255) / 256, 152 * 16), 256, 0, s>>>(S, a.Uin, ph, a.W32);
-  }
-  if (a.ev) cudaEventRecord(a.ev[0], s);
-  if (ph.viscous) k_lift<N, R><<<a.K, n3, smem_lift, s>>>(a.Uin, m, ph, tab, Rv, Gf);
-  if (a.ev) cudaEventRecord(a.ev[1], s);
+  if (!(phase & 4)) return (int)cudaGetLastError();
   if (a.n_interior > 0) {
     const int threads = 256;
     const long long work = (long long)a.n_interior * n2;
@@ -89,6 +100,7 @@ static int run_typed(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {
     const long long work = (long long)a.n_bc * n2;
     k_bc<N, R><<<(unsigned)((work + threads - 1) / threads), threads, 0, s>>>(a.Uin, m, ph, Gf, Fs);
   }
+  if (a.n_halo > 0) k_halo_face<N, R><<<halo_blocks, 256, 0, s>>>(a.Uin, m, ph, Gf, Fs);
   if (a.ev) cudaEventRecord(a.ev[2], s);
   if (fork) {
     cudaStreamWaitEvent(s, a.join, 0);

@@ -19,6 +19,7 @@ HEADER = os.path.join(_HERE, "..", "include", "dg.h")
 
 FP64, FP32_MIXED = 0, 1
 VOL_KEP_PIROZZOLI, VOL_KEP_KENNEDY_GRUBER, VOL_EC_CHANDRASHEKAR = 0, 1, 2
+DG_BC_WALL, DG_BC_INFLOW, DG_BC_OUTFLOW, DG_BC_HALO_BASE = -1, -2, -3, -16
 SURF_CENTRAL, SURF_LLF, SURF_ROE = 0, 1, 2
 LAW_SPALDING, LAW_REICHARDT = 0, 1
 
@@ -97,6 +98,14 @@ def lib():
         "dg_profile_enable": (c_int, [vp, c_int]),
         "dg_set_overlap": (c_int, [vp, c_int]),
         "dg_profile_read": (c_int, [vp, dp, ip]),
+        "dg_partition_sfc": (c_int, [c_int, c_int, dp, c_int, ip]),
+        "dg_partition_local": (c_int, [c_int, ip, ip, c_int, ip, ip, ip, ip, ip]),
+        "dg_halo_buffers": (c_int, [vp, ip, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                    ctypes.POINTER(vp)]),
+        "dg_halo_geometry": (c_int, [vp, dp]),
+        "dg_halo_set_geometry": (c_int, [vp, dp]),
+        "dg_stage_phase": (c_int, [vp, c_int, c_int, c_double, c_double]),
+        "dg_time_derivative_phase": (c_int, [vp, c_int, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -129,6 +138,51 @@ def _ptr(t):
         return ctypes.c_void_p(t.ctypes.data), 0
     assert t.dtype.is_floating_point and t.is_contiguous()
     return ctypes.c_void_p(t.data_ptr()), 1 if t.is_cuda else 0
+
+
+class _DeviceView:
+    """A device array described through __cuda_array_interface__, so that
+    torch.as_tensor views library-owned device memory without copying."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 3, "strides": None}
+
+
+def partition_sfc(N, X, nranks):
+    """Rank of every element along the Morton curve of the centroids (dg_partition_sfc)."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    n3 = (N + 1) ** 3
+    K = X.size // (3 * n3)
+    part = np.zeros(K, dtype=np.int32)
+    rc = lib().dg_partition_sfc(int(N), int(K), X.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(nranks),
+                                part.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+    if rc != 0:
+        raise DGError(rc, "dg_partition_sfc failed")
+    return part
+
+
+def partition_local(nbr, part, rank):
+    """(l2g, nbr_local, halo[n_halo, 4]) of one rank (dg_partition_local)."""
+    nbr = np.ascontiguousarray(nbr, dtype=np.int32)
+    part = np.ascontiguousarray(part, dtype=np.int32)
+    K = part.size
+    ip = ctypes.POINTER(ctypes.c_int)
+    Kl, nh = ctypes.c_int(), ctypes.c_int()
+    L = lib()
+    rc = L.dg_partition_local(K, nbr.ctypes.data_as(ip), part.ctypes.data_as(ip), int(rank), ctypes.byref(Kl),
+                              None, None, ctypes.byref(nh), None)
+    if rc != 0:
+        raise DGError(rc, "dg_partition_local failed")
+    l2g = np.zeros(Kl.value, dtype=np.int32)
+    nbl = np.zeros((Kl.value, 6), dtype=np.int32)
+    halo = np.zeros((max(nh.value, 1), 4), dtype=np.int32)
+    rc = L.dg_partition_local(K, nbr.ctypes.data_as(ip), part.ctypes.data_as(ip), int(rank), ctypes.byref(Kl),
+                              l2g.ctypes.data_as(ip), nbl.ctypes.data_as(ip), ctypes.byref(nh),
+                              halo.ctypes.data_as(ip))
+    if rc != 0:
+        raise DGError(rc, "dg_partition_local failed")
+    return l2g, nbl, halo[: nh.value]
 
 
 def _stream_handle(stream):
@@ -282,6 +336,43 @@ class Operator:
 
     def check_status(self):
         self._check(lib().dg_check_status(self.h))
+
+    # -- partitioned meshes (see halo.py) ---------------------------------
+    def halo_buffers(self):
+        """Device views (torch) of the halo buffers: send_U, recv_U
+        [n_halo, 5, n2] float64 and send_G, recv_G [n_halo, 4, n2] in the flux
+        type.  Empty dict for an unpartitioned context."""
+        import torch
+        nh = ctypes.c_int()
+        ptrs = [ctypes.c_void_p() for _ in range(4)]
+        self._check(lib().dg_halo_buffers(self.h, ctypes.byref(nh), *[ctypes.byref(q) for q in ptrs]))
+        if nh.value == 0:
+            return {}
+        n2 = (self.N + 1) ** 2
+        gdt = "<f4" if self.precision == FP32_MIXED else "<f8"
+        out = {}
+        for name, q, rows, dt in (("send_U", ptrs[0], 5, "<f8"), ("recv_U", ptrs[1], 5, "<f8"),
+                                  ("send_G", ptrs[2], 4, gdt), ("recv_G", ptrs[3], 4, gdt)):
+            out[name] = torch.as_tensor(_DeviceView(q.value, (nh.value, rows, n2), dt), device="cuda")
+        return out
+
+    def halo_geometry(self):
+        nh = ctypes.c_int()
+        self._check(lib().dg_halo_buffers(self.h, ctypes.byref(nh), None, None, None, None))
+        out = np.zeros((nh.value, 4, (self.N + 1) ** 2))
+        self._check(lib().dg_halo_geometry(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out
+
+    def set_halo_geometry(self, fgeo):
+        fgeo = np.ascontiguousarray(fgeo, dtype=np.float64)
+        self._check(lib().dg_halo_set_geometry(self.h, fgeo.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+
+    def stage_phase(self, phase, s, t, dt):
+        self._check(lib().dg_stage_phase(self.h, int(phase), int(s), float(t), float(dt)))
+
+    def time_derivative_phase(self, phase, Ut, U=None):
+        pu = _ptr(U)[0] if U is not None else None
+        self._check(lib().dg_time_derivative_phase(self.h, int(phase), pu, _ptr(Ut)[0]))
 
     def set_overlap(self, on=True):
         """Wall-model kernel on its own high-priority stream (default), or in line."""

@@ -1,0 +1,125 @@
+"""Partitioned meshes on one GPU: the ranks of a space-filling-curve
+partition (paper Sec. 2.3) as contexts in one process, their halo exchanges
+done by device copies between the phases.  Every stage must reproduce the
+unpartitioned context bitwise; the time derivative likewise."""
+import numpy as np
+import pytest
+
+from paper_2606_18927_gb300 import dg, halo, inputs as I
+from gpu_helpers import tgv_with_offset, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def _setup(spec, phys, **opts):
+    x, w = dg.lgl_nodes(spec.N)
+    X = I.node_coordinates(spec, x)
+    nbr = I.connectivity(spec)
+    U = I.perturb(tgv_with_offset(X, phys, offset=(0.3, 0.1, 0.05)), rel=1e-3)
+    return X, nbr, U
+
+
+def _compare(torch, spec, phys, P, nsteps=2, **opts):
+    X, nbr, U = _setup(spec, phys)
+    Ud = torch.from_numpy(U).cuda()
+    g = dg.Operator(spec.N, X, nbr, phys, **opts)
+    dt = g.time_step(0.9, Ud)
+    g.set_state(Ud)
+    g.rk_steps(0.0, dt, nsteps)
+    ref = torch.empty_like(Ud)
+    g.get_state(ref)
+    g.check_status()
+    ranks = halo.LocalRanks(spec.N, X, nbr, phys, P, **opts)
+    ranks.set_state(Ud)
+    ranks.steps(0.0, dt, nsteps)
+    out = torch.empty_like(Ud)
+    ranks.get_state(out)
+    ranks.check_status()
+    # time derivative through the phases
+    ut_ref = torch.empty_like(Ud)
+    g.time_derivative(ut_ref, Ud)
+    ut = torch.empty_like(Ud)
+    ranks.time_derivative(ut, Ud)
+    torch.cuda.synchronize()
+    nh = [len(h) for h in ranks.halo]
+    ranks.close(); g.close()
+    return ref, out, ut_ref, ut, nh
+
+
+@pytest.mark.parametrize("P", [2, 3, 5])
+def test_partitioned_tgv_bitwise(P):
+    torch = torch_cuda()
+    phys = I.phys_params(Ma=0.1, Re=1600.0)
+    spec = I.BoxSpec(3, 4, 4, 3, geometry="sine", amplitude=0.2)
+    ref, out, ut_ref, ut, nh = _compare(torch, spec, phys, P, surf_flux=2)
+    print("TGV P", P, "halo faces", nh)
+    assert min(nh) > 0
+    assert torch.equal(out, ref)
+    assert torch.equal(ut, ut_ref)
+
+
+@pytest.mark.parametrize("P", [2, 5])
+def test_partitioned_tgv_mixed(P):
+    # the FP32 flux arithmetic of a halo face runs in another kernel than that
+    # of an interior face, where the compiler may contract it differently:
+    # agreement to FP32 rounding of the fluxes, not bitwise
+    torch = torch_cuda()
+    phys = I.phys_params(Ma=0.1, Re=1600.0)
+    spec = I.BoxSpec(3, 4, 4, 3, geometry="sine", amplitude=0.2)
+    X, nbr, U = _setup(spec, phys)
+    U0 = torch.from_numpy(U).cuda()
+    ref, out, ut_ref, ut, nh = _compare(torch, spec, phys, P, precision=dg.FP32_MIXED, surf_flux=2)
+    e_state = float((out - ref).abs().max() / (ref - U0).abs().max())
+    e_ut = max(float((ut[v] - ut_ref[v]).abs().max() / ut_ref[v].abs().max()) for v in range(5))
+    print("mixed P", P, "state increment diff", e_state, "Ut diff", e_ut, "bitwise", torch.equal(out, ref))
+    assert e_state <= 1e-5 and e_ut <= 1e-5
+
+
+def test_partitioned_production_scheme_with_inflow_outflow_bitwise():
+    torch = torch_cuda()
+    phys = I.phys_params(Ma=0.3, Re=400.0, sutherland=True)
+    g0, p0 = phys["gamma"], phys["p0"]
+    phys.update(U_in=np.array([1.0, 0.5, 0.0, 0.0, p0 / (g0 - 1) + 0.125]), p_out=0.99 * p0)
+    spec = I.BoxSpec(4, 5, 2, 3, geometry="sine", amplitude=0.1, periodic=(False, True, True),
+                     boundary=((I.INFLOW, I.OUTFLOW), (I.WALL, I.WALL), (I.WALL, I.WALL)))
+    ref, out, ut_ref, ut, nh = _compare(torch, spec, phys, 3, vol_flux=dg.VOL_EC_CHANDRASHEKAR, surf_flux=2)
+    assert torch.equal(out, ref) and torch.equal(ut, ut_ref)
+
+
+@pytest.mark.parametrize("P", [2, 4])
+def test_partitioned_wall_modelled_channel_bitwise(P):
+    torch = torch_cuda()
+    wl = I.workload("channel_n5", N=3, elems=(8, 4, 4))
+    X, nbr, U = _setup(wl.spec, wl.phys)
+    U = I.channel_profile(X, wl.phys)
+    Ud = torch.from_numpy(U).cuda()
+    g = dg.Operator(wl.spec.N, X, nbr, wl.phys, surf_flux=2, law=1)
+    dt = g.time_step(0.9, Ud)
+    g.set_state(Ud)
+    g.rk_steps(0.0, dt, 2)
+    ref = torch.empty_like(Ud)
+    g.get_state(ref)
+    ranks = halo.LocalRanks(wl.spec.N, X, nbr, wl.phys, P, surf_flux=2, law=1)
+    ranks.set_state(Ud)
+    ranks.steps(0.0, dt, 2)
+    out = torch.empty_like(Ud)
+    ranks.get_state(out)
+    ranks.check_status()
+    assert torch.equal(out, ref)
+
+
+def test_fused_calls_refuse_partitioned_contexts():
+    torch = torch_cuda()
+    phys = I.phys_params()
+    spec = I.BoxSpec(2, 4, 2, 2)
+    X, nbr, U = _setup(spec, phys)
+    ranks = halo.LocalRanks(spec.N, X, nbr, phys, 2)
+    op = ranks.ops[0]
+    Ul = torch.from_numpy(halo.local_state(U, ranks.l2g[0])).cuda()
+    op.set_state(Ul)
+    with pytest.raises(dg.DGError) as ei:
+        op.rk_stage(0, 0.0, 1e-3)
+    assert ei.value.code == -1
+    with pytest.raises(dg.DGError) as ei:
+        op.vjp(torch.ones_like(Ul), torch.empty_like(Ul), U=Ul)
+    assert ei.value.code in (-1, -8)
