@@ -299,7 +299,7 @@ int noalloc_args(dg_ctx* c, const double* U, double* Ut, OpArgs* a, const PhysDe
   *s = c->stream;
   *rv_bytes = (c->opts.viscous ? 4 * c->S : 1) * rs;
   *gf_bytes = (c->opts.viscous ? 24 * (size_t)c->K * c->n2 : 1) * rs;
-  *fs_bytes = 5 * (size_t)c->F * c->n2 * rs;
+  *fs_bytes = (c->ph.fs_diff ? 10 : 5) * (size_t)c->F * c->n2 * rs;
   // FP32-mixed form: the primitives go to the context's own W32 array
   // (allocated with the context); they are formed afresh from U
   a->W32 = c->W32;
@@ -376,6 +376,7 @@ int dg_init_mesh(dg_ctx** out, const dg_mesh_desc* m, const dg_phys* p, const dg
   for (int v = 0; v < 5; ++v) ph.U_in[v] = p->U_in[v];
   ph.p_out = p->p_out;
   ph.sutherland = ph.suth_S > 0.0 ? 1 : 0;
+  ph.fs_diff = (o->precision == DG_FP32_MIXED && o->vol_flux == DG_VOL_KEP_PIROZZOLI) ? 1 : 0;
   ph.has_force = (ph.f[0] != 0.0 || ph.f[1] != 0.0 || ph.f[2] != 0.0) ? 1 : 0;
   ph.f32c.p_ref = (float)ph.p_ref; ph.f32c.rcp_R = (float)ph.rcp_R; ph.f32c.rgm1 = (float)ph.rgm1;
   ph.f32c.gamma = (float)ph.gamma; ph.f32c.mu = (float)ph.mu; ph.f32c.kcond = (float)ph.kcond;
@@ -402,7 +403,7 @@ int dg_init_mesh(dg_ctx** out, const dg_mesh_desc* m, const dg_phys* p, const dg
   chk(alloc(&c->tau, (size_t)c->geo.n_wall * n2 * 3));
   chk(cudaMalloc(&c->Rv, (o->viscous ? 4 * S : 1) * rs));
   chk(cudaMalloc(&c->Gf, (o->viscous ? 24 * (size_t)c->K * n2 : 1) * rs));
-  chk(cudaMalloc(&c->Fs, 5 * (size_t)c->F * n2 * rs));
+  chk(cudaMalloc(&c->Fs, (ph.fs_diff ? 10 : 5) * (size_t)c->F * n2 * rs));
   if (f32) chk(alloc(&c->W32, 6 * S));
   if (c->geo.n_halo > 0) {
     const size_t nh = (size_t)c->geo.n_halo;

@@ -36,6 +36,7 @@ struct PhysDev {
   double kappa, B, hwm;
   int law, vol_flux, surf_flux, viscous;
   int sutherland, has_force;  // suth_S > 0; f != 0
+  int fs_diff;                // FP32 Pirozzoli form: surface fluxes stored per side as F* - F(U_side)
   double U_in[5], p_out;      // inflow state (conservative) and outflow pressure
   // FP32 copies of the constants the FP32 kernels use (a double-to-float
   // conversion is an FP64-pipe instruction)
@@ -319,11 +320,11 @@ __device__ __forceinline__ void twopoint(int kind, const Prim<R>& A, const Prim<
 
 // Numerical inviscid flux along the unit normal (nx, ny, nz), side A = master;
 // dU = U_B - U_A (conservative) for the Lax-Friedrichs dissipation.
+// subtracts the dissipation of the selected Riemann solver from F
 template <typename R>
-__device__ __forceinline__ void riemann_d(const PhysDev& ph, const Prim<R>& A, const Prim<R>& B, const R dU[5],
-                                          R nx, R ny, R nz, R F[5]) {
+__device__ __forceinline__ void riemann_dissipation(const PhysDev& ph, const Prim<R>& A, const Prim<R>& B,
+                                                    const R dU[5], R nx, R ny, R nz, R F[5]) {
   const R pref = cR<R>(ph.p_ref, ph.f32c.p_ref);
-  twopoint<R>(ph.vol_flux, A, B, nx, ny, nz, F, ph);
   const R g = cR<R>(ph.gamma, ph.f32c.gamma);
   if (ph.surf_flux == 1) {  // local Lax-Friedrichs (sound speed from the full pressure)
     const R cA = sqrt(g * (A.p + pref) / A.rho), cB = sqrt(g * (B.p + pref) / B.rho);
@@ -363,6 +364,78 @@ __device__ __forceinline__ void riemann_d(const PhysDev& ph, const Prim<R>& A, c
                  ws * (u * du + v * dv + w * dw - un * dun);
     F[0] -= R(0.5) * D0; F[1] -= R(0.5) * D1; F[2] -= R(0.5) * D2;
     F[3] -= R(0.5) * D3; F[4] -= R(0.5) * D4;
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void riemann_d(const PhysDev& ph, const Prim<R>& A, const Prim<R>& B, const R dU[5],
+                                          R nx, R ny, R nz, R F[5]) {
+  twopoint<R>(ph.vol_flux, A, B, nx, ny, nz, F, ph);
+  riemann_dissipation<R>(ph, A, B, dU, nx, ny, nz, F);
+}
+
+// FP32-mixed form with the Pirozzoli flux: two-point flux differences
+//   G(i -> m) = F#(U_i, U_m; {a}) - F(U_i) . a_i
+// formed from the differences of the two nodes' primitives (x_m = x_i + dx,
+// {x} = x_i + dx / 2), so that their FP32 rounding error scales with the
+// difference, not with the flux itself:
+//   {u}.{a} - u_i.a_i = du/2 . {a} + u_i . da/2 =: dua
+//   G_rho = rho_i dua + drho/2 ({u}.{a})
+//   G_m   = G_rho {u} + rho_i (u_i.a_i) du/2 + dp/2 {a} + p_i da/2   (p = p - p_ref)
+//   G_E   = G_rho {h} + rho_i (u_i.a_i) dh/2
+// The split-form volume term is sum_m DVS_im G(i -> m) (the F(U_i) part sums to
+// the boundary rows' -B/w F(U_i), which the surface term carries in the same
+// difference form, F* - F(U_i)).
+struct NodeF {
+  float rho, u, v, w, p, h;
+};
+
+__device__ __forceinline__ void flux_delta(const NodeF& i, const NodeF& m, float ai0, float ai1, float ai2, float da0,
+                                           float da1, float da2, float G[5]) {
+  const float du = m.u - i.u, dv = m.v - i.v, dw = m.w - i.w;
+  const float dr = m.rho - i.rho, dp = m.p - i.p, dh = m.h - i.h;
+  const float ab0 = fmaf(0.5f, da0, ai0), ab1 = fmaf(0.5f, da1, ai1), ab2 = fmaf(0.5f, da2, ai2);
+  const float uia = i.u * ai0 + i.v * ai1 + i.w * ai2;
+  const float dua = 0.5f * (du * ab0 + dv * ab1 + dw * ab2 + i.u * da0 + i.v * da1 + i.w * da2);
+  const float g0 = i.rho * dua + 0.5f * dr * (uia + dua);
+  const float ruia = i.rho * uia;
+  G[0] = g0;
+  G[1] = g0 * fmaf(0.5f, du, i.u) + 0.5f * (ruia * du + dp * ab0 + i.p * da0);
+  G[2] = g0 * fmaf(0.5f, dv, i.v) + 0.5f * (ruia * dv + dp * ab1 + i.p * da1);
+  G[3] = g0 * fmaf(0.5f, dw, i.w) + 0.5f * (ruia * dw + dp * ab2 + i.p * da2);
+  G[4] = g0 * fmaf(0.5f, dh, i.h) + 0.5f * ruia * dh;
+}
+
+__device__ __forceinline__ NodeF nodef(const Prim<float>& q) { return NodeF{q.rho, q.u, q.v, q.w, q.p, q.h}; }
+
+// face flux differences for both sides: D_A = F* - F(U_A).n, D_B = F* - F(U_B).n
+__device__ __forceinline__ void face_flux_delta(const PhysDev& ph, const Prim<float>& A, const Prim<float>& B,
+                                                const float dU[5], float nx, float ny, float nz, float DA[5],
+                                                float DB[5]) {
+  float Z[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  riemann_dissipation<float>(ph, A, B, dU, nx, ny, nz, Z);
+  flux_delta(nodef(A), nodef(B), nx, ny, nz, 0.f, 0.f, 0.f, DA);
+  flux_delta(nodef(B), nodef(A), nx, ny, nz, 0.f, 0.f, 0.f, DB);
+#pragma unroll
+  for (int v = 0; v < 5; ++v) { DA[v] += Z[v]; DB[v] += Z[v]; }
+}
+
+// FP32 difference form: writes the master's (and, with both, the slave's)
+// F* s - F(U_side).(n s) minus the viscous flux vis_w (gA - gB) (gB null: gA)
+// into out (master) and out + 5 n2 (slave)
+__device__ __forceinline__ void store_face_delta(const PhysDev& ph, const Prim<float>& A, const Prim<float>& B,
+                                                 const float dU[5], float nx, float ny, float nz, float s,
+                                                 const float* gA, const float* gB, float vis_w, float* out, int n2,
+                                                 bool both) {
+  float DA[5], DB[5];
+  face_flux_delta(ph, A, B, dU, nx, ny, nz, DA, DB);
+  out[0] = DA[0] * s;
+  if (both) out[5 * n2] = DB[0] * s;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const float vis = ph.viscous ? vis_w * (gB ? gA[v * n2] - gB[v * n2] : gA[v * n2]) : 0.f;
+    out[(v + 1) * n2] = DA[v + 1] * s - vis;
+    if (both) out[(v + 6) * n2] = DB[v + 1] * s - vis;
   }
 }
 
@@ -715,6 +788,12 @@ k_face(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
 #pragma unroll
       for (int v = 0; v < 5; ++v) dU[v] = (float)(U[v * S + gS] - U[v * S + gM]);
     }
+    if (ph.fs_diff) {
+      const R* gA = Gf + ((size_t)fc.x * 6 + fc.y) * 4 * n2 + ab;
+      const R* gB = Gf + ((size_t)fc.z * 6 + fc.w) * 4 * n2 + ab;
+      store_face_delta(ph, A, B, dU, nx, ny, nz, s, gA, gB, R(0.5), Fs + (size_t)f * 10 * n2 + ab, n2, true);
+      return;
+    }
     riemann_d<float>(ph, A, B, dU, nx, ny, nz, F);
   } else {
     double UA[5], UB[5];
@@ -767,6 +846,18 @@ k_halo_face(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, 
   const R nx = (R)m.fgeo[fg], ny = (R)m.fgeo[FN + fg], nz = (R)m.fgeo[2 * FN + fg], s = (R)m.fgeo[3 * FN + fg];
   const Prim<R> A = primitive<R>(UA[0], UA[1], UA[2], UA[3], UA[4], ph);
   const Prim<R> B = primitive<R>(UB[0], UB[1], UB[2], UB[3], UB[4], ph);
+  if constexpr (std::is_same<R, float>::value) {
+    if (ph.fs_diff) {
+      float dU[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) dU[v] = (float)(UB[v] - UA[v]);
+      const R* gl = Gf + ((size_t)fc.x * 6 + fc.y) * 4 * n2 + ab;
+      const R* gr = m.halo_G + (size_t)h * 4 * n2 + ab;
+      store_face_delta(ph, A, B, dU, nx, ny, nz, s, master ? gl : gr, master ? gr : gl, 0.5f,
+                       Fs + (size_t)f * 10 * n2 + ab, n2, true);
+      return;
+    }
+  }
   R F[5];
   riemann<R, double>(ph, A, UA, B, UB, nx, ny, nz, F);
   R* out = Fs + (size_t)f * 5 * n2 + ab;
@@ -834,6 +925,16 @@ k_bc(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const R
   const Prim<R> B = primitive<R>(UB[0], UB[1], UB[2], UB[3], UB[4], ph);
   const size_t FN = (size_t)m.F * n2, fg = (size_t)f * n2 + ab;
   const R nx = (R)m.fgeo[fg], ny = (R)m.fgeo[FN + fg], nz = (R)m.fgeo[2 * FN + fg], s = (R)m.fgeo[3 * FN + fg];
+  if constexpr (std::is_same<R, float>::value) {
+    if (ph.fs_diff) {
+      float dU[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) dU[v] = (float)(UB[v] - UA[v]);
+      store_face_delta(ph, A, B, dU, nx, ny, nz, s, Gf + ((size_t)fc.x * 6 + fc.y) * 4 * n2 + ab, nullptr, 1.f,
+                       Fs + (size_t)f * 10 * n2 + ab, n2, false);
+      return;
+    }
+  }
   R F[5];
   riemann<R, double>(ph, A, UA, B, UB, nx, ny, nz, F);
   R* out = Fs + (size_t)f * 5 * n2 + ab;
@@ -879,7 +980,17 @@ k_wall(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, R* __
   const Prim<R> A = primitive<R>(UA[0], UA[1], UA[2], UA[3], UA[4], ph);
   const Prim<R> B = primitive<R>(UB[0], UB[1], UB[2], UB[3], UB[4], ph);
   R F[5];
-  riemann<R, double>(ph, A, UA, B, UB, (R)nxd, (R)nyd, (R)nzd, F);
+  int fss = 5;  // surface-flux values per face node (10: FP32 difference form)
+  if constexpr (std::is_same<R, float>::value) {
+    if (ph.fs_diff) {
+      float dU[5], DB[5];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) dU[v] = (float)(UB[v] - UA[v]);
+      face_flux_delta(ph, A, B, dU, (R)nxd, (R)nyd, (R)nzd, F, DB);
+      fss = 10;
+    }
+  }
+  if (fss == 5) riemann<R, double>(ph, A, UA, B, UB, (R)nxd, (R)nyd, (R)nzd, F);
   double tau[3] = {0.0, 0.0, 0.0};
   if (ph.viscous) {
     // sample state at h_wm: tensor-product Lagrange interpolation of U
@@ -907,7 +1018,7 @@ k_wall(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, R* __
     }
   }
   // viscous wall flux Fv . n = (0, -tau_w t, 0): the wall decelerates the flow
-  R* out = Fs + (size_t)f * 5 * n2 + ab;
+  R* out = Fs + (size_t)f * fss * n2 + ab;
   const R s = (R)sd;
   out[0] = F[0] * s;
   out[n2] = F[1] * s + (R)(tau[0] * sd);
@@ -947,9 +1058,9 @@ struct VolShape {
   static constexpr int WARPS_NODES = (n3 + 31) / 32;
   static constexpr int THREADS = 32 * (WARPS_LINES > WARPS_NODES ? WARPS_LINES : WARPS_NODES);
   // shared memory (in units of R): 7 prim slots (9 with the entropy-
-  // conserving flux), 9 metric, 5 residual per node, two coefficient tables, 1/w
-  static constexpr int SMEM_R = 21 * n3 + 2 * n2 + n;
-  static constexpr int SMEM_R_EC = 23 * n3 + 2 * n2 + n;
+  // conserving flux), 9 metric, 5 residual per node, three coefficient tables, 1/w
+  static constexpr int SMEM_R = 21 * n3 + 3 * n2 + n;
+  static constexpr int SMEM_R_EC = 23 * n3 + 3 * n2 + n;
 };
 
 // Resident CTAs per SM asked of the register allocator: two for CTAs of up to
@@ -976,13 +1087,18 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
   R* sR = sA + 9 * n3;                      // [5][n3]: residual
   R* sC8 = sR + 5 * n3;                     // [n2]: DVS / 8
   R* sC16 = sC8 + n2;                       // [n2]: DVS / 16
-  R* siw = sC16 + n2;                       // [n]
+  R* sC1 = sC16 + n2;                       // [n2]: DVS
+  R* siw = sC1 + n2;                        // [n]
   const int e = blockIdx.x, t = threadIdx.x;
   const size_t S = (size_t)m.K * n3;
   const bool kg = ph.vol_flux == 1;
+  // FP32 Pirozzoli form: flux differences G(i -> m) and per-side surface
+  // differences F* - F(U_i) (see flux_delta)
+  const bool dif = std::is_same<R, float>::value && !EC && ph.fs_diff;
   for (int x = t; x < n2; x += T) {
     sC8[x] = (R)tab.DVS8[x];
     sC16[x] = (R)(0.5 * tab.DVS8[x]);
+    sC1[x] = (R)(8.0 * tab.DVS8[x]);
   }
   if (t < n) siw[t] = (R)tab.iw[t];
   // prologue: node t (the FP32-mixed form reads the stage's FP32 primitives
@@ -1000,7 +1116,7 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
       q = primitive<R>(Uo[0], Uo[1], Uo[2], Uo[3], Uo[4], ph);
     }
     sQ[t] = q.rho; sQ[n3 + t] = q.u; sQ[2 * n3 + t] = q.v; sQ[3 * n3 + t] = q.w;
-    sQ[4 * n3 + t] = R(4) * q.p;
+    sQ[4 * n3 + t] = dif ? q.p : R(4) * q.p;
     if constexpr (EC) {
       const R pf = q.p + cR<R>(ph.p_ref, ph.f32c.p_ref);
       const R beta = R(0.5) * q.rho * rcp_t<R>(pf);
@@ -1052,6 +1168,31 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
         const R Sp = p4 + sQ[4 * n3 + q];
         const R Sa0 = a0 + sA[(dir * 3 + 0) * n3 + q], Sa1 = a1 + sA[(dir * 3 + 1) * n3 + q],
                 Sa2 = a2 + sA[(dir * 3 + 2) * n3 + q];
+        if constexpr (std::is_same<R, float>::value && !EC) {
+          if (dif) {
+            const NodeF mi{rho, u, v, w, p4, hh};
+            const NodeF mq{rq, sQ[n3 + q], sQ[2 * n3 + q], sQ[3 * n3 + q], sQ[4 * n3 + q], sQ[5 * n3 + q]};
+            const float aq0 = sA[(dir * 3 + 0) * n3 + q], aq1 = sA[(dir * 3 + 1) * n3 + q],
+                        aq2 = sA[(dir * 3 + 2) * n3 + q];
+            float G[5];
+            flux_delta(mi, mq, a0, a1, a2, aq0 - a0, aq1 - a1, aq2 - a2, G);
+            const float c1 = sC1[pos * n + pm];
+            acc0 += c1 * G[0]; acc1 += c1 * G[1]; acc2 += c1 * G[2]; acc3 += c1 * G[3]; acc4 += c1 * G[4];
+            if (2 * d != n) {
+              // G(q -> i) for the partner lane (pos + d); receive G(i -> pos - d)
+              flux_delta(mq, mi, aq0, aq1, aq2, a0 - aq0, a1 - aq1, a2 - aq2, G);
+              const int src = base + (pos - d >= 0 ? pos - d : pos - d + n);
+              const float g0 = __shfl_sync(0xffffffffu, G[0], src);
+              const float g1 = __shfl_sync(0xffffffffu, G[1], src);
+              const float g2 = __shfl_sync(0xffffffffu, G[2], src);
+              const float g3 = __shfl_sync(0xffffffffu, G[3], src);
+              const float g4 = __shfl_sync(0xffffffffu, G[4], src);
+              const float r1 = sC1[pos * n + (src - base)];
+              acc0 += r1 * g0; acc1 += r1 * g1; acc2 += r1 * g2; acc3 += r1 * g3; acc4 += r1 * g4;
+            }
+            continue;
+          }
+        }
         const R ua = Su * Sa0 + Sv * Sa1 + Sw * Sa2;  // 4 {u}.{a}
         R mf, F1, F2, F3, F4;
         if constexpr (EC) {
@@ -1133,7 +1274,8 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
     const int code = m.elem_face[e * 6 + l];
     const int f = code >> 1;
     const R sg = (code & 1) ? -iw : iw;
-    const R* src = Fs + (size_t)f * 5 * n2 + ab;
+    // difference form: the face's own side, F* - F(U_side), in rows 5 n2 apart
+    const R* src = dif ? Fs + (size_t)f * 10 * n2 + ((code & 1) ? 5 * n2 : 0) + ab : Fs + (size_t)f * 5 * n2 + ab;
 #pragma unroll
     for (int v = 0; v < 5; ++v) acc[v] += sg * src[v * n2];
   };

@@ -3,12 +3,14 @@ LSERK4 register update and the pressure recovery p = (gamma-1)(E - rho|u|^2/2)
 in FP64.  Its error against the oracle is stated as the relative L2 norm of
 Ut per variable.
 
-Bound: FP32 rounding of the O(1) velocity (and of curved-mesh metrics) is
-amplified by the divergence operator, |D| |Ja| / J ~ N^2 / h, while the
-Mach 0.1 Taylor-Green flow is nearly divergence free, so rho_t and E_t are
-small differences: the floor is ~1e-5 (N = 3) to ~1e-4 (N = 7, curved) in
-relative L2.  The tests assert 1e-4 and print the per-variable errors; the
-1e-5 goal is met only by part of the cases."""
+With the Pirozzoli flux the volume and surface terms are summed as flux
+differences F#(U_i, U_m) - F(U_i) formed from the differences of the nodes'
+primitives, whose FP32 rounding scales with the difference.  What remains is
+the FP32 rounding of the inputs (velocity, density, and on curved meshes the
+metrics), amplified by the divergence operator |D| |Ja| / J ~ N^2 / h against
+a nearly divergence-free Mach 0.1 flow.  Bounds per case: 1e-5 on affine
+meshes, 5e-5 on curved ones (metric rounding); 1e-4 for the other fluxes,
+which keep the direct form."""
 import numpy as np
 import pytest
 
@@ -24,18 +26,29 @@ def rel_l2(a, ref):
     return [float(np.linalg.norm(a[v] - ref[v]) / np.linalg.norm(ref[v])) for v in range(5)]
 
 
-@pytest.mark.parametrize("label,spec,surf,ma", [
-    ("tgv_n3_4^3_llf", I.BoxSpec(3, 4, 4, 4), 1, 0.1),
-    ("tgv_n7_4^3_roe", I.BoxSpec(7, 4, 4, 4), 2, 0.1),
-    ("sine_n7_roe_ma03", I.BoxSpec(7, 3, 2, 2, geometry="sine", amplitude=0.1), 2, 0.3),
-    ("n5_central", I.BoxSpec(5, 2, 3, 2, geometry="sine", amplitude=0.2), 0, 0.1),
+@pytest.mark.parametrize("label,spec,surf,ma,bound", [
+    ("tgv_n3_4^3_llf", I.BoxSpec(3, 4, 4, 4), 1, 0.1, 1e-5),
+    ("tgv_n7_4^3_roe", I.BoxSpec(7, 4, 4, 4), 2, 0.1, 1e-5),
+    ("sine_n7_roe_ma03", I.BoxSpec(7, 3, 2, 2, geometry="sine", amplitude=0.1), 2, 0.3, 5e-5),
+    ("n5_central", I.BoxSpec(5, 2, 3, 2, geometry="sine", amplitude=0.2), 0, 0.1, 5e-5),
 ])
-def test_mixed_time_derivative_error(ora, label, spec, surf, ma):
+def test_mixed_time_derivative_error(ora, label, spec, surf, ma, bound):
     torch = torch_cuda()
     phys = I.phys_params(Ma=ma, Re=1600.0)
     o, g, X, U = case(ora, spec, phys, surf_flux=surf, precision=dg.FP32_MIXED)
     e = rel_l2(gpu_ut(torch, g, U), o.time_derivative(U))
     print(label, "mixed rel L2", ["%.1e" % x for x in e])
+    assert max(e) <= bound, e
+
+
+def test_mixed_kennedy_gruber_direct_form(ora):
+    # the other KEP flux keeps the direct FP32 form (no flux differences)
+    torch = torch_cuda()
+    phys = I.phys_params(Ma=0.1, Re=1600.0)
+    o, g, X, U = case(ora, I.BoxSpec(5, 3, 2, 2), phys, surf_flux=2, vol_flux=dg.VOL_KEP_KENNEDY_GRUBER,
+                      precision=dg.FP32_MIXED)
+    e = rel_l2(gpu_ut(torch, g, U), o.time_derivative(U))
+    print("kennedy-gruber mixed rel L2", ["%.1e" % x for x in e])
     assert max(e) <= TOL_L2, e
 
 
@@ -45,7 +58,7 @@ def test_mixed_wall_model_channel(ora):
     o, g, X, U = case(ora, wl.spec, wl.phys, surf_flux=2, law=1, ic="channel", precision=dg.FP32_MIXED)
     e = rel_l2(gpu_ut(torch, g, U), o.time_derivative(U))
     print("channel mixed rel L2", ["%.1e" % x for x in e])
-    assert max(e) <= TOL_L2, e
+    assert max(e) <= 1e-5, e
 
 
 def test_mixed_rk_stages(ora):
