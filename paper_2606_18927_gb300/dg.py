@@ -186,6 +186,10 @@ def partition_local(nbr, part, rank):
 
 
 def _stream_handle(stream):
+    """cudaStream_t of a torch stream (None: torch's current stream; 0: the
+    legacy default stream, which needs no torch CUDA state)."""
+    if isinstance(stream, int) and stream == 0:
+        return ctypes.c_void_p(0)
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
     return ctypes.c_void_p(s.cuda_stream)
