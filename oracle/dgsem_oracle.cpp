@@ -12,17 +12,21 @@
 // Algorithms 1 and 2):
 //   Ut = DG_Operator(U) for the 3D compressible Navier-Stokes equations in
 //   strong form on curvilinear hexahedra, followed by the LSERK4 update.
-// The paper gives no operator equations; the textbook DGSEM written out here
-// (step by step, one loop per definition, no symmetry tricks, no fusion) and
-// every reading of a point the paper leaves open is listed in the design doc.
+// The paper gives no operator equations; this is the textbook DGSEM written
+// out step by step (one loop per definition, no symmetry tricks, no fusion).
+// Where the paper leaves a point open (lifted variables, flux forms, boundary
+// states, the wall model's sampling and Newton stopping rule, the logarithmic
+// mean, Sutherland constants), the reading taken is stated at the function
+// that implements it; the library implements the same readings independently.
 //
 // Everything is templated on the scalar type T so that a forward-mode dual
 // number gives exact Jacobian-vector products (used to check the adjoint).
 //
 // Parity status of each function: pinned by tests/test_oracle_*.py against
 // closed forms, identities (SBP, metric identities, free-stream, conservation,
-// kinetic-energy preservation), a manufactured solution and finite
-// differences.  Nothing here is "parity unpinned".
+// kinetic-energy and entropy conservation, boundary flux balances), tabulated
+// data (Spalding's printed constants, air viscosities), a manufactured
+// solution and finite differences.  Nothing here is "parity unpinned".
 
 #include <algorithm>
 #include <cmath>
