@@ -123,6 +123,10 @@ typedef struct {
   double suth_S, T_ref; /* Sutherland's law (suth_S <= 0: constant mu) */
   double U_in[5];       /* inflow state (conservative), used by DG_BC_INFLOW faces */
   double p_out;         /* outflow pressure, used by DG_BC_OUTFLOW faces */
+  double T_wall;        /* > 0: isothermal wall-modelled walls at this temperature
+                           (Crocco-Busemann in the Van Driest transform, wall heat
+                           flux q_w = -(cp/Pr) tau_w (T_aw - T_w) / u_s into the
+                           energy equation); <= 0: adiabatic walls */
 } dg_phys;
 
 typedef struct {
@@ -192,8 +196,8 @@ int dg_rk_steps(dg_ctx* c, double t, double dt, int nsteps);
  * recovery are written out by hand; the local Jacobians of the Riemann
  * solver and of the wall model (with the implicit function theorem for the
  * law of the wall, Sec. 3.2) come from forward-mode dual numbers.  FP64
- * contexts with the Pirozzoli volume flux, a constant viscosity and no
- * inflow or outflow faces (else DG_ERR_NOT_IMPLEMENTED).
+ * contexts with the Pirozzoli volume flux, a constant viscosity, adiabatic
+ * walls and no inflow, outflow or halo faces (else DG_ERR_NOT_IMPLEMENTED).
  * The first call allocates the adjoint scratch of the context. */
 int dg_vjp(dg_ctx* c, const double* U, const double* lam, double* gU, double* gtheta);
 

@@ -16,7 +16,7 @@ from . import build as _build
 _libs = {}
 
 PHYS_KEYS = ("gamma", "R", "mu", "Pr", "fx", "fy", "fz", "kappa", "B", "hwm", "suth_S", "T_ref",
-             "U_in0", "U_in1", "U_in2", "U_in3", "U_in4", "p_out")
+             "U_in0", "U_in1", "U_in2", "U_in3", "U_in4", "p_out", "T_wall")
 PHYS_DEFAULTS = {"suth_S": 0.0, "T_ref": 1.0, "U_in0": 1.0, "U_in4": 1.0, "p_out": 1.0}
 
 
@@ -44,6 +44,7 @@ def lib(extended=False):
         L.ora_num_wall.argtypes = [vp]
         L.ora_get_wall_samples.argtypes = [vp, ip, dp]
         L.ora_time_derivative.argtypes = [vp, dp, ctypes.c_double, dp]
+        L.ora_wall_heat.argtypes = [vp, dp, dp]
         L.ora_jvp.argtypes = [vp, dp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp]
         L.ora_rk_stage.argtypes = [vp, dp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double]
         L.ora_rk_steps.argtypes = [vp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_int]
@@ -56,7 +57,7 @@ def lib(extended=False):
                                      ctypes.c_double, ctypes.c_double, dp]
         L.ora_law_value.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double]
         L.ora_law_value.restype = ctypes.c_double
-        L.ora_wall_flux.argtypes = [dp, ctypes.c_int, dp, dp, dp, dp]
+        L.ora_wall_flux.argtypes = [dp, ctypes.c_int, dp, dp, dp, dp, dp]
         L.ora_riemann.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp]
         L.ora_real_digits.restype = ctypes.c_int
         _libs[extended] = L
@@ -162,6 +163,15 @@ class Oracle:
             raise RuntimeError("oracle wall model did not converge")
         return Ut
 
+    def wall_heat(self, U):
+        """Wall heat flux q_w into the fluid per wall slot (face-major, n^2 per face)."""
+        U = _f64(U)
+        out = np.zeros(self.L.ora_num_wall(self.h))
+        st = self.L.ora_wall_heat(self.h, _p(U), _p(out))
+        if st != 0:
+            raise RuntimeError("oracle wall model did not converge")
+        return out
+
     def jvp(self, U, dU=None, dkappa=0.0, dB=0.0, t=0.0):
         U = _f64(U); Ut = np.zeros_like(U); dUt = np.zeros_like(U)
         dptr = None
@@ -223,12 +233,13 @@ def law_value(law, x, kappa, B):
     return lib().ora_law_value(int(law), float(x), float(kappa), float(B))
 
 
-def wall_flux(phys, law, U5, nout):
+def wall_flux(phys, law, U5, nout, heat=False):
+    """(momentum flux, wall shear vector, status[, wall heat flux q_w])."""
     pa = phys_array(phys)
     U5 = _f64(U5); nout = _f64(nout)
-    fm = np.zeros(3); tau = np.zeros(3)
-    st = lib().ora_wall_flux(_p(pa), int(law), _p(U5), _p(nout), _p(fm), _p(tau))
-    return fm, tau, st
+    fm = np.zeros(3); tau = np.zeros(3); qw = np.zeros(1)
+    st = lib().ora_wall_flux(_p(pa), int(law), _p(U5), _p(nout), _p(fm), _p(tau), _p(qw))
+    return (fm, tau, st, float(qw[0])) if heat else (fm, tau, st)
 
 
 def viscosity(phys, T):

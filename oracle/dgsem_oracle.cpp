@@ -197,6 +197,7 @@ struct Phys {
   real suth_S = 0.0, T_ref = 1.0;  // Sutherland constant and reference temperature (S <= 0: constant mu)
   real U_in[5] = {1.0, 0.0, 0.0, 0.0, 1.0};  // Dirichlet inflow state (conservative)
   real p_out = 1.0;                          // outflow pressure
+  real T_wall = 0.0;                         // isothermal wall temperature (<= 0: adiabatic walls)
   real hwm = 0.1;               // wall-model sampling distance
 };
 struct Opts {
@@ -745,8 +746,21 @@ int solve_utau(int law, const T& u, real h, const T& nu, const T& kappa, const T
 
 // Wall-model viscous flux at a wall node: returns Fv*.n_out (momentum part)
 // and the wall shear vector tau_w * t (t = unit wall-parallel sample velocity).
+//
+// Isothermal wall (T_wall > 0; Sec. 3.1 names the wall heat flux q_w, the
+// model is a reading): the Crocco-Busemann relation through the wall layer,
+//   T(u) = T_w + (T_aw - T_w) u / u_s - r u^2 / (2 cp),  T_aw = T_s + r u_s^2 / (2 cp),
+// which meets T_w at the wall and T_s at the sample.  The Van Driest velocity
+// u_VD = int_0^{u_s} sqrt(T_w / T(u)) du, with T / T_w = 1 + b u - a^2 u^2,
+// b = (T_aw - T_w) / (T_w u_s), a^2 = r / (2 cp T_w), integrates to
+//   u_VD = [asin((2 a^2 u_s - b) / q) + asin(b / q)] / a,  q = sqrt(b^2 + 4 a^2),
+// (b = 0: the adiabatic asin(a u_s) / a), and the wall heat flux into the
+// fluid is q_w = -k_w dT/dy = -k_w (dT/du)(0) tau_w / mu_w
+//   = -(cp / Pr) tau_w (T_aw - T_w) / u_s.
+// qw receives q_w (0 for adiabatic walls); it is the energy component of the
+// viscous flux along the outward normal.
 template <class T>
-int wall_flux(const Phys<T>& P, int law, const Prim<T>& s, const real nout[3], T fm[3], T tauvec[3]) {
+int wall_flux(const Phys<T>& P, int law, const Prim<T>& s, const real nout[3], T fm[3], T tauvec[3], T* qw) {
   const real cp = P.gamma * P.R / (P.gamma - 1.0);
   const real r = std::cbrt(P.Pr);
   T un = s.u[0] * nout[0] + s.u[1] * nout[1] + s.u[2] * nout[2];
@@ -754,12 +768,24 @@ int wall_flux(const Phys<T>& P, int law, const Prim<T>& s, const real nout[3], T
   for (int c = 0; c < 3; ++c) upar[c] = s.u[c] - un * nout[c];
   T u2 = upar[0] * upar[0] + upar[1] * upar[1] + upar[2] * upar[2];
   for (int c = 0; c < 3; ++c) { fm[c] = 0.0; tauvec[c] = 0.0; }
+  *qw = T(0.0);
   if (!(val(u2) > 0.0)) return 0;
   T umag = sqrt(u2);
-  T Tw = s.T_ + r * u2 / (2.0 * cp);
+  T Tw, uvd;
+  T Taw = s.T_ + r * u2 / (2.0 * cp);
+  if (P.T_wall > 0.0) {
+    Tw = T(P.T_wall);
+    T b = (Taw - Tw) / (Tw * umag);
+    T a2 = r / (2.0 * cp * Tw);
+    T a = sqrt(a2);
+    T q = sqrt(b * b + 4.0 * a2);
+    uvd = (asin((2.0 * a2 * umag - b) / q) + asin(b / q)) / a;
+  } else {
+    Tw = Taw;  // adiabatic: the wall takes the recovery temperature
+    T a = sqrt(r / (2.0 * cp * Tw));
+    uvd = asin(a * umag) / a;
+  }
   T rhow = s.rho * s.T_ / Tw;
-  T a = sqrt(r / (2.0 * cp * Tw));
-  T uvd = asin(a * umag) / a;
   T nuw = viscosity(P, Tw) / rhow;
   T ut;
   int it = solve_utau(law, uvd, P.hwm, nuw, P.kappa, P.B, ut);
@@ -769,6 +795,7 @@ int wall_flux(const Phys<T>& P, int law, const Prim<T>& s, const real nout[3], T
     tauvec[c] = tw * tc;
     fm[c] = -tw * tc;
   }
+  if (P.T_wall > 0.0) *qw = -(cp / P.Pr) * tw * (Taw - Tw) / umag;
   return it < 0 ? -1 : 0;
 }
 
@@ -782,6 +809,7 @@ struct Work {
   std::vector<T> G;              // contravariant viscous flux [(e*n3+p)*15 + dir*5 + v]
   std::vector<T> wflux;          // wall-model momentum flux [slot*3]
   std::vector<T> wtau;           // wall shear vector [slot*3]
+  std::vector<T> wq;             // wall heat flux into the fluid [slot]
   std::vector<int> wstat;
 };
 
@@ -933,6 +961,7 @@ int time_derivative(const Mesh& M, const Phys<T>& P, const Opts& O, const T* U, 
   // 12. wall model at every wall face node
   W.wflux.assign((size_t)M.nwall * 3, T(0.0));
   W.wtau.assign((size_t)M.nwall * 3, T(0.0));
+  W.wq.assign((size_t)M.nwall, T(0.0));
   W.wstat.assign(M.nwall, 0);
   if (O.viscous && M.nwall > 0) {
 #pragma omp parallel for schedule(static)
@@ -959,8 +988,9 @@ int time_derivative(const Mesh& M, const Phys<T>& P, const Opts& O, const T* U, 
             Prim<T> qs = prim_of(P, Us);
             real nh[3], s; bool own;
             face_geometry(M, e, l, a, b, nh, &s, &own);
-            T fm[3], tv[3];
-            W.wstat[slot] = wall_flux(P, O.law, qs, nh, fm, tv);
+            T fm[3], tv[3], qwv;
+            W.wstat[slot] = wall_flux(P, O.law, qs, nh, fm, tv, &qwv);
+            W.wq[slot] = qwv;
             for (int c = 0; c < 3; ++c) {
               W.wflux[(size_t)slot * 3 + c] = fm[c];
               W.wtau[(size_t)slot * 3 + c] = tv[c];
@@ -1049,6 +1079,7 @@ int time_derivative(const Mesh& M, const Phys<T>& P, const Opts& O, const T* U, 
           } else if (nb == BC_WALL) {
             int slot = M.wslot[e * 6 + l] + a + n * b;
             for (int c = 0; c < 3; ++c) Fv[1 + c] = W.wflux[(size_t)slot * 3 + c];
+            Fv[4] = W.wq[slot];
           } else {
             // inflow / outflow: the interior viscous flux
             T go[3][4];
@@ -1167,6 +1198,7 @@ static Phys<Dual> dual_phys(const Phys<real>& P, real dk, real dB) {
   Q.suth_S = P.suth_S; Q.T_ref = P.T_ref;
   for (int v = 0; v < 5; ++v) Q.U_in[v] = P.U_in[v];
   Q.p_out = P.p_out;
+  Q.T_wall = P.T_wall;
   return Q;
 }
 
@@ -1239,6 +1271,7 @@ static void* create_impl(int N, int K, const double* X, const int* nbr, const do
   c->P.suth_S = phys[10]; c->P.T_ref = phys[11];
   for (int v = 0; v < 5; ++v) c->P.U_in[v] = phys[12 + v];
   c->P.p_out = phys[17];
+  c->P.T_wall = phys[18];
   c->O.vol_flux = opts[0]; c->O.surf_flux = opts[1]; c->O.viscous = opts[2]; c->O.law = opts[3];
   std::string e;
   bool ok = check_connectivity(M, e) && build_metrics(M, e) && build_wall_samples(M, c->P.hwm, e);
@@ -1290,6 +1323,16 @@ int ora_time_derivative(void* h, const double* U, double t, double* Ut) {
   std::vector<real> u = to_real(U, S5), ut(S5);
   int st = time_derivative(c->M, c->P, c->O, u.data(), t, ut.data(), c->W);
   to_double(ut, Ut);
+  return st;
+}
+
+// Wall heat flux q_w into the fluid at every wall slot for state U (tests).
+int ora_wall_heat(void* h, const double* U, double* qw) {
+  Ctx* c = (Ctx*)h;
+  const size_t S5 = state_size(c);
+  std::vector<real> u = to_real(U, S5), ut(S5);
+  int st = time_derivative(c->M, c->P, c->O, u.data(), 0.0, ut.data(), c->W);
+  for (int s2 = 0; s2 < c->M.nwall; ++s2) qw[s2] = (double)c->W.wq[s2];
   return st;
 }
 
@@ -1395,17 +1438,19 @@ double ora_law_value(int law, double x, double kappa, double B) {
 }
 
 // Wall flux at one sample state (tests): U5 conservative, nout unit normal.
-int ora_wall_flux(const double* phys, int law, const double* U5, const double* nout, double* fm, double* tau) {
+int ora_wall_flux(const double* phys, int law, const double* U5, const double* nout, double* fm, double* tau,
+                  double* qw) {
   Phys<real> P;
   P.gamma = phys[0]; P.R = phys[1]; P.mu = phys[2]; P.Pr = phys[3];
   P.kappa = phys[7]; P.B = phys[8]; P.hwm = phys[9];
-  P.suth_S = phys[10]; P.T_ref = phys[11];
-  real u[5], nh[3], f[3], t[3];
+  P.suth_S = phys[10]; P.T_ref = phys[11]; P.T_wall = phys[18];
+  real u[5], nh[3], f[3], t[3], q_w;
   for (int v = 0; v < 5; ++v) u[v] = U5[v];
   for (int c = 0; c < 3; ++c) nh[c] = nout[c];
   Prim<real> q = prim_of(P, u);
-  int st = wall_flux(P, law, q, nh, f, t);
+  int st = wall_flux(P, law, q, nh, f, t, &q_w);
   for (int c = 0; c < 3; ++c) { fm[c] = (double)f[c]; tau[c] = (double)t[c]; }
+  if (qw) *qw = (double)q_w;
   return st;
 }
 

@@ -375,6 +375,7 @@ int dg_init_mesh(dg_ctx** out, const dg_mesh_desc* m, const dg_phys* p, const dg
   ph.vol_flux = o->vol_flux; ph.surf_flux = o->surf_flux; ph.viscous = o->viscous ? 1 : 0;
   for (int v = 0; v < 5; ++v) ph.U_in[v] = p->U_in[v];
   ph.p_out = p->p_out;
+  ph.T_wall = p->T_wall;
   ph.sutherland = ph.suth_S > 0.0 ? 1 : 0;
   ph.fs_diff = (o->precision == DG_FP32_MIXED && o->vol_flux == DG_VOL_KEP_PIROZZOLI) ? 1 : 0;
   ph.has_force = (ph.f[0] != 0.0 || ph.f[1] != 0.0 || ph.f[2] != 0.0) ? 1 : 0;
@@ -677,6 +678,8 @@ static int check_adjoint_options(dg_ctx* c, const char* who) {
     return fail(c, DG_ERR_NOT_IMPLEMENTED, std::string(who) + ": the adjoint needs a constant viscosity");
   if (c->geo.n_bc > 0 || c->geo.n_halo > 0)
     return fail(c, DG_ERR_NOT_IMPLEMENTED, std::string(who) + ": the adjoint covers periodic and wall faces only");
+  if (c->phys.T_wall > 0.0)
+    return fail(c, DG_ERR_NOT_IMPLEMENTED, std::string(who) + ": the adjoint covers adiabatic walls only");
   return DG_OK;
 }
 
@@ -738,6 +741,7 @@ int dg_kinetic_energy(dg_ctx* c, const double* U, double* ke) {
 int dg_wall_shear(dg_ctx* c, const double* U, double* loss) {
   if (!c || !loss) return c ? fail(c, DG_ERR_ARG, "dg_wall_shear: null loss") : DG_ERR_ARG;
   if (c->geo.n_wall == 0 || !c->opts.viscous) return fail(c, DG_ERR_ARG, "dg_wall_shear: no wall-modelled walls");
+  if (c->phys.T_wall > 0.0) return fail(c, DG_ERR_NOT_IMPLEMENTED, "dg_wall_shear: adiabatic walls only");
   const double* Uin = U ? U : c->U;
   if (!U && !c->state_set) return fail(c, DG_ERR_NOT_INIT, "dg_wall_shear: state not set");
   int rc = ensure_scalar(c);

@@ -44,6 +44,7 @@ struct PhysDev {
   int sutherland, has_force;  // suth_S > 0; f != 0
   int fs_diff;                // FP32 Pirozzoli form: surface fluxes stored per side as F* - F(U_side)
   double U_in[5], p_out;      // inflow state (conservative) and outflow pressure
+  double T_wall;              // isothermal wall temperature (<= 0: adiabatic walls)
   // FP32 copies of the constants the FP32 kernels use (a double-to-float
   // conversion is an FP64-pipe instruction)
   struct {
@@ -555,13 +556,18 @@ static __device__ double solve_utau(int law, double u, double h, double nu, doub
   return law == 1 ? exp(t) * nu / h : u / exp(t);
 }
 
-// Wall shear stress from the sample state: Van Driest transform for an
-// adiabatic wall (Crocco-Busemann: T_w = T + r u^2 / (2 cp), rho_w = rho T / T_w,
-// u_VD = asin(a u) / a with a = sqrt(r / (2 cp T_w)), r = Pr^(1/3)), then the
-// law of the wall for u_tau, tau_w = rho_w u_tau^2 along the sample's
-// wall-parallel velocity.
+// Wall shear stress (and, at an isothermal wall, the heat flux into the fluid)
+// from the sample state.  Adiabatic wall: Van Driest transform with the wall at
+// the recovery temperature (Crocco-Busemann: T_w = T + r u^2 / (2 cp), rho_w =
+// rho T / T_w, u_VD = asin(a u) / a with a = sqrt(r / (2 cp T_w)), r = Pr^(1/3)).
+// Isothermal wall (ph.T_wall > 0): the Crocco-Busemann relation T(u) = T_w +
+// (T_aw - T_w) u / u_s - r u^2 / (2 cp) in the transform,
+//   u_VD = [asin((2 a^2 u_s - b) / q) + asin(b / q)] / a,
+//   b = (T_aw - T_w) / (T_w u_s), a^2 = r / (2 cp T_w), q = sqrt(b^2 + 4 a^2),
+// and q_w = -(cp / Pr) tau_w (T_aw - T_w) / u_s.  Then the law of the wall for
+// u_tau, tau_w = rho_w u_tau^2 along the sample's wall-parallel velocity.
 static __device__ void wall_stress(const PhysDev& ph, const double Us[5], double nx, double ny, double nz,
-                            double tau[3], bool* ok) {
+                            double tau[3], double* qw, bool* ok) {
   const double rho = Us[0], ir = 1.0 / rho;
   const double u = Us[1] * ir, v = Us[2] * ir, w = Us[3] * ir;
   const double p = ph.gm1 * (Us[4] - 0.5 * rho * (u * u + v * v + w * w));
@@ -570,18 +576,31 @@ static __device__ void wall_stress(const PhysDev& ph, const double Us[5], double
   const double ux = u - un * nx, uy = v - un * ny, uz = w - un * nz;
   const double u2 = ux * ux + uy * uy + uz * uz;
   tau[0] = tau[1] = tau[2] = 0.0;
+  *qw = 0.0;
   *ok = true;
   if (!(u2 > 0.0)) return;
   const double um = sqrt(u2);
   const double r = cbrt(ph.Pr);
-  const double Tw = T + r * u2 / (2.0 * ph.cp);
+  const double Taw = T + r * u2 / (2.0 * ph.cp);
+  double Tw, uvd;
+  if (ph.T_wall > 0.0) {
+    Tw = ph.T_wall;
+    const double b = (Taw - Tw) / (Tw * um);
+    const double a2 = r / (2.0 * ph.cp * Tw);
+    const double a = sqrt(a2);
+    const double q = sqrt(b * b + 4.0 * a2);
+    uvd = (asin((2.0 * a2 * um - b) / q) + asin(b / q)) / a;
+  } else {
+    Tw = Taw;
+    const double a = sqrt(r / (2.0 * ph.cp * Tw));
+    uvd = asin(a * um) / a;
+  }
   const double rhow = rho * T / Tw;
-  const double a = sqrt(r / (2.0 * ph.cp * Tw));
-  const double uvd = asin(a * um) / a;
   const double muw = ph.sutherland ? sutherland<double>(ph, Tw) : ph.mu;
   const double ut = solve_utau(ph.law, uvd, ph.hwm, muw / rhow, ph.kappa, ph.B, ok);
   const double tw = rhow * ut * ut / um;
   tau[0] = tw * ux; tau[1] = tw * uy; tau[2] = tw * uz;
+  if (ph.T_wall > 0.0) *qw = -(ph.cp / ph.Pr) * (rhow * ut * ut) * (Taw - Tw) / um;
 }
 
 // ---------------------------------------------------------------------------
@@ -997,7 +1016,7 @@ k_wall(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, R* __
     }
   }
   if (fss == 5) riemann<R, double>(ph, A, UA, B, UB, (R)nxd, (R)nyd, (R)nzd, F);
-  double tau[3] = {0.0, 0.0, 0.0};
+  double tau[3] = {0.0, 0.0, 0.0}, qw = 0.0;
   if (ph.viscous) {
     // sample state at h_wm: tensor-product Lagrange interpolation of U
     const size_t slot = (size_t)wf * n2 + ab;
@@ -1017,7 +1036,7 @@ k_wall(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, R* __
         for (int v = 0; v < 5; ++v) Us[v] += ljk * row[v];
       }
     bool ok;
-    wall_stress(ph, Us, nxd, nyd, nzd, tau, &ok);
+    wall_stress(ph, Us, nxd, nyd, nzd, tau, &qw, &ok);
     if (!ok) atomicOr(status, ST_WM_NOCONV);
     if (tau_out) {
       tau_out[slot * 3 + 0] = tau[0]; tau_out[slot * 3 + 1] = tau[1]; tau_out[slot * 3 + 2] = tau[2];
@@ -1030,7 +1049,7 @@ k_wall(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, R* __
   out[n2] = F[1] * s + (R)(tau[0] * sd);
   out[2 * n2] = F[2] * s + (R)(tau[1] * sd);
   out[3 * n2] = F[3] * s + (R)(tau[2] * sd);
-  out[4 * n2] = F[4] * s;
+  out[4 * n2] = F[4] * s - (R)(qw * sd);  // viscous energy flux along the outward normal: q_w
 }
 
 // ---------------------------------------------------------------------------

@@ -256,3 +256,78 @@ def test_sutherland_air_table(ora):
     assert ora.viscosity(phys, 273.15) == pytest.approx(1.716e-5, rel=1e-15)
     phys["suth_S"] = 0.0
     assert ora.viscosity(phys, 400.0) == 1.716e-5
+
+
+@pytest.mark.parametrize("law", [0, 1])
+@pytest.mark.parametrize("Ma", [0.1, 0.8])
+def test_isothermal_wall_model(ora, law, Ma):
+    """Isothermal wall (reading of Sec. 3.1's wall heat flux): Van Driest by
+    quadrature of sqrt(T_w / T(u)) with the Crocco-Busemann temperature
+    T(u) = T_w + (T_aw - T_w) u/u_s - r u^2/(2 c_p), the law by bracketing, and
+    q_w = -k_w (dT/du)(0) tau_w / mu_w with dT/du from a finite difference of T(u)."""
+    phys = I.phys_params(Ma=Ma, Re=20000.0, kappa=0.41, B=5.2, hwm=0.1)
+    g, R, mu, Pr = phys["gamma"], phys["R"], phys["mu"], phys["Pr"]
+    cp = g * R / (g - 1); r = Pr ** (1 / 3)
+    nout = np.array([0.0, -1.0, 0.0])
+    rng = np.random.default_rng(5)
+    for _ in range(6):
+        vel = np.array([rng.uniform(0.2, 1.5), rng.uniform(-0.3, 0.3), rng.uniform(-0.5, 0.5)])
+        rho = rng.uniform(0.9, 1.1); p = phys["p0"] * rng.uniform(0.95, 1.05)
+        T = p / (rho * R)
+        Tw = T * rng.uniform(0.8, 1.3)
+        phys["T_wall"] = Tw
+        fm, tau, st, qw = ora.wall_flux(phys, law, _state(rho, vel, p), nout, heat=True)
+        assert st == 0
+        upar = vel - (vel @ nout) * nout
+        um = np.linalg.norm(upar)
+        Taw = T + r * um ** 2 / (2 * cp)
+        Tu = lambda s: Tw + (Taw - Tw) * s / um - r * s * s / (2 * cp)
+        assert abs(Tu(um) - T) < 1e-12 * T
+        uvd = integrate.quad(lambda s: math.sqrt(Tw / Tu(s)), 0.0, um, epsabs=0, epsrel=2e-14)[0]
+        rhow = rho * T / Tw
+        nuw = mu / rhow
+        if law == 1:
+            gf = lambda x: uvd / x - ora.law_value(1, 0.1 * x / nuw, 0.41, 5.2)
+        else:
+            gf = lambda x: 0.1 * x / nuw - ora.law_value(0, uvd / x, 0.41, 5.2)
+        ut = optimize.brentq(gf, 1e-12, 1e3, xtol=1e-300, rtol=1e-15)
+        tw = rhow * ut * ut
+        assert np.allclose(tau, tw * upar / um, rtol=1e-11, atol=1e-16)
+        h = 1e-6 * um
+        dTdu = (Tu(h) - Tu(-h)) / (2 * h)
+        qref = -(mu * cp / Pr) * dTdu * tw / mu
+        assert abs(qw - qref) <= 1e-7 * abs(qref)
+        # heat flows into the fluid from a wall hotter than the recovery temperature
+        assert (qw > 0) == (Tw > Taw)
+
+
+def test_isothermal_wall_at_recovery_temperature_is_adiabatic(ora):
+    phys = I.phys_params(Ma=0.5, Re=20000.0)
+    g, R, Pr = phys["gamma"], phys["R"], phys["Pr"]
+    cp = g * R / (g - 1); r = Pr ** (1 / 3)
+    nout = np.array([0.0, 1.0, 0.0])
+    rho, vel, p = 1.02, np.array([0.9, 0.1, -0.2]), phys["p0"]
+    U = _state(rho, vel, p)
+    fa, ta, _, qa = ora.wall_flux(phys, 1, U, nout, heat=True)
+    upar = vel - (vel @ nout) * nout
+    phys["T_wall"] = p / (rho * R) + r * (upar @ upar) / (2 * cp)
+    fi, ti, _, qi = ora.wall_flux(phys, 1, U, nout, heat=True)
+    assert qa == 0.0 and abs(qi) < 1e-12 * abs(ti).max() * cp
+    assert np.allclose(ti, ta, rtol=1e-12)
+
+
+def test_isothermal_wall_laminar_conduction_limit(ora):
+    # low Mach, sample in the viscous sublayer (y+ << 1) and T_s close to T_w:
+    # tau_w -> mu_w u_s / h and q_w -> -k_w (T_s - T_w) / h (Fourier across h)
+    phys = I.phys_params(Ma=0.05, Re=50.0, hwm=0.01)
+    g, R, mu, Pr = phys["gamma"], phys["R"], phys["mu"], phys["Pr"]
+    cp = g * R / (g - 1)
+    rho, p = 1.0, phys["p0"]
+    T = p / (rho * R)
+    phys["T_wall"] = T * (1 - 1e-4)
+    vel = np.array([1e-3, 0.0, 0.0])
+    fm, tau, st, qw = ora.wall_flux(phys, 1, _state(rho, vel, p), np.array([0.0, -1.0, 0.0]), heat=True)
+    k = mu * cp / Pr
+    q_fourier = -k * (T - phys["T_wall"]) / 0.01
+    assert abs(qw - q_fourier) < 2e-3 * abs(q_fourier)
+    assert abs(tau[0] - mu * 1e-3 / 0.01) < 2e-3 * mu * 1e-3 / 0.01

@@ -187,3 +187,47 @@ def test_sutherland_uniform_temperature(ora):
     assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max()
     c = ora.Oracle(spec.N, X, nbr, phys, surf_flux=2).time_derivative(U)
     assert np.abs(a - c).max() > 1e-6 * np.abs(b).max()
+
+
+def test_energy_balance_with_isothermal_walls(ora):
+    # periodic in x and z, isothermal wall-modelled walls in y, no body force:
+    # the total energy changes only through the walls, by the inviscid wall
+    # flux (slip, mirror state) minus the wall heat flux q_w into the fluid
+    wl = I.workload("channel_n5", N=3, elems=(4, 4, 2))
+    spec = I.BoxSpec(wl.spec.N, wl.spec.nx, wl.spec.ny, wl.spec.nz, lengths=wl.spec.lengths,
+                     geometry="channel", amplitude=0.0, periodic=wl.spec.periodic)
+    phys = dict(wl.phys)
+    phys.update(fx=0.0, fy=0.0, fz=0.0)
+    phys["T_wall"] = 1.1 * phys["p0"] / phys["R"]
+    x, w, D = ora.lgl(spec.N)
+    X = I.node_coordinates(spec, x)
+    nbr = I.connectivity(spec)
+    o = ora.Oracle(spec.N, X, nbr, phys, surf_flux=2, viscous=1, law=1)
+    U = I.channel_profile(X, phys)
+    Ut = o.time_derivative(U).reshape(5, o.K, o.n3)
+    wJ = quad_weights(ora, o)
+    lhs = (wJ * Ut[4]).sum()
+    qw = o.wall_heat(U)
+    n = spec.N + 1
+    s = (spec.lengths[0] / spec.nx / 2) * (spec.lengths[2] / spec.nz / 2)
+    Ur = U.reshape(5, o.K, o.n3)
+    rhs = 0.0
+    slot = 0
+    for e in range(o.K):
+        for l in range(6):
+            if nbr[e, l] != I.WALL:
+                continue
+            nout = np.array([0.0, -1.0 if l == 2 else 1.0, 0.0])
+            for b in range(n):
+                for a in range(n):
+                    p = [None, None, a + n * n * b, a + n * ((n - 1) + n * b)][l]
+                    Um = Ur[:, e, p]
+                    mn = Um[1:4] @ nout
+                    Ub = Um.copy(); Ub[1:4] = Um[1:4] - 2 * mn * nout
+                    F = ora.riemann(phys, 0, 2, Um, Ub, nout)
+                    rhs -= w[a] * w[b] * s * (F[4] - qw[slot + a + n * b])
+            slot += n * n
+    heat = sum(w[a] * w[b] * s * qw[k * n * n + a + n * b] for k in range(len(qw) // (n * n))
+               for b in range(n) for a in range(n))
+    assert abs(heat) > 1e-6 * abs(lhs) + 1e-12     # the walls do exchange heat
+    assert abs(lhs - rhs) <= 1e-11 * (abs(rhs) + abs(heat)), (lhs, rhs, heat)
