@@ -556,6 +556,102 @@ static __device__ double solve_utau(int law, double u, double h, double nu, doub
   return law == 1 ? exp(t) * nu / h : u / exp(t);
 }
 
+// FP32 form of the wall model for the FP32-mixed kernels: the same steps in
+// FP32 arithmetic, with the Newton stopping tolerances scaled to FP32
+// rounding (a step below 1e-6 of max(1, |t|), or a bracket below 4e-7 of it).
+__device__ __forceinline__ void law_eval_cf(int law, float w, float kap, float cst, float* L, float* wdL) {
+  if (law == 1) {
+    const float C = cst;
+    const float e1 = expf(-w / 11.0f), e2 = expf(-0.33f * w);
+    const float Lv = log1pf(kap * w) / kap + C * (1.0f - e1 - (w / 11.0f) * e2);
+    const float dL = 1.0f / (1.0f + kap * w) + C * (e1 / 11.0f - e2 / 11.0f + 0.33f * (w / 11.0f) * e2);
+    *L = Lv; *wdL = w * dL;
+  } else {
+    const float ku = kap * w;
+    const float eb = cst, ek = expf(ku);
+    const float t3 = ku * ku * ku / 6.0f;
+    const float Lv = w + eb * (ek - 1.0f - ku - 0.5f * ku * ku - t3 - 0.25f * ku * t3);
+    const float dL = 1.0f + eb * kap * (ek - 1.0f - ku - 0.5f * ku * ku - t3);
+    *L = Lv; *wdL = w * dL;
+  }
+}
+
+static __device__ float solve_utau_f(int law, float u, float h, float nu, float kap, float B, bool* ok) {
+  *ok = true;
+  if (!(u > 0.0f)) return 0.0f;
+  const float lnRe = logf(h * u / nu);
+  const float cst = law == 1 ? B - logf(kap) / kap : expf(-kap * B);
+  auto F = [&](float t, float* dF) {
+    const float w = expf(t);
+    float L, wdL;
+    law_eval_cf(law, w, kap, cst, &L, &wdL);
+    *dF = 1.0f + wdL / L;
+    return t + logf(L) - lnRe;
+  };
+  float dF;
+  const float t0 = 0.5f * lnRe;
+  const float F0 = F(t0, &dF);
+  float lo = t0, hi = t0, st = 1.0f;
+  int it = 0;
+  float Flo = F0;
+  while (!(Flo < 0.0f) && it < 200) { lo -= st; st *= 2.0f; ++it; Flo = F(lo, &dF); }
+  st = 1.0f;
+  float Fhi = F0;
+  while (!(Fhi > 0.0f) && it < 200) { hi += st; st *= 2.0f; ++it; Fhi = F(hi, &dF); }
+  float t = t0;
+  if (!(t > lo && t < hi)) t = 0.5f * (lo + hi);
+  bool done = false;
+  for (; it < 200; ++it) {
+    const float Ft = F(t, &dF);
+    if (Ft == 0.0f) { done = true; break; }
+    if (Ft < 0.0f) lo = t; else hi = t;
+    float nt = t - Ft / dF;
+    const bool newton = (nt >= lo && nt <= hi);
+    if (!newton) nt = 0.5f * (lo + hi);
+    const float step = fabsf(nt - t);
+    t = nt;
+    const float sc = fmaxf(1.0f, fabsf(t));
+    if ((newton && step <= 1e-6f * sc) || hi - lo <= 4e-7f * sc) { done = true; break; }
+  }
+  *ok = done;
+  return law == 1 ? expf(t) * nu / h : u / expf(t);
+}
+
+// wall_stress below in FP32, from the sample's primitives
+static __device__ void wall_stress_f(const PhysDev& ph, float rho, float u, float v, float w, float T, float nx,
+                                     float ny, float nz, float tau[3], float* qw, bool* ok) {
+  const float un = u * nx + v * ny + w * nz;
+  const float ux = u - un * nx, uy = v - un * ny, uz = w - un * nz;
+  const float u2 = ux * ux + uy * uy + uz * uz;
+  tau[0] = tau[1] = tau[2] = 0.0f;
+  *qw = 0.0f;
+  *ok = true;
+  if (!(u2 > 0.0f)) return;
+  const float cp = (float)ph.cp, Pr = (float)ph.Pr;
+  const float um = sqrtf(u2);
+  const float r = cbrtf(Pr);
+  const float Taw = T + r * u2 / (2.0f * cp);
+  float Tw, uvd;
+  if (ph.T_wall > 0.0) {
+    Tw = (float)ph.T_wall;
+    const float b = (Taw - Tw) / (Tw * um);
+    const float a2 = r / (2.0f * cp * Tw);
+    const float a = sqrtf(a2);
+    const float q = sqrtf(b * b + 4.0f * a2);
+    uvd = (asinf((2.0f * a2 * um - b) / q) + asinf(b / q)) / a;
+  } else {
+    Tw = Taw;
+    const float a = sqrtf(r / (2.0f * cp * Tw));
+    uvd = asinf(a * um) / a;
+  }
+  const float rhow = rho * T / Tw;
+  const float muw = ph.sutherland ? sutherland<float>(ph, Tw) : ph.f32c.mu;
+  const float ut = solve_utau_f(ph.law, uvd, (float)ph.hwm, muw / rhow, (float)ph.kappa, (float)ph.B, ok);
+  const float tw = rhow * ut * ut / um;
+  tau[0] = tw * ux; tau[1] = tw * uy; tau[2] = tw * uz;
+  if (ph.T_wall > 0.0) *qw = -(cp / Pr) * (rhow * ut * ut) * (Taw - Tw) / um;
+}
+
 // Wall shear stress (and, at an isothermal wall, the heat flux into the fluid)
 // from the sample state.  Adiabatic wall: Van Driest transform with the wall at
 // the recovery temperature (Crocco-Busemann: T_w = T + r u^2 / (2 cp), rho_w =
@@ -1017,7 +1113,50 @@ k_wall(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, R* __
   }
   if (fss == 5) riemann<R, double>(ph, A, UA, B, UB, (R)nxd, (R)nyd, (R)nzd, F);
   double tau[3] = {0.0, 0.0, 0.0}, qw = 0.0;
-  if (ph.viscous) {
+  if constexpr (std::is_same<R, float>::value) {
+    if (ph.viscous) {
+      // FP32 form: interpolation of the conservative state formed from the
+      // stage's FP32 primitives, with the energy taken relative to
+      // p_ref / (gamma - 1) (the interpolation weights sum to one), then the
+      // FP32 wall model
+      const size_t slot = (size_t)wf * n2 + ab;
+      const int es = m.ws_elem[slot];
+      const double* Ld = m.ws_lag + slot * 3 * n;
+      float L[3 * n];
+#pragma unroll
+      for (int x = 0; x < 3 * n; ++x) L[x] = (float)Ld[x];
+      const float rg = ph.f32c.rgm1;
+      float Us[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+      for (int kk = 0; kk < n; ++kk)
+        for (int jj = 0; jj < n; ++jj) {
+          const float ljk = L[n + jj] * L[2 * n + kk];
+          float row[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+          for (int ii = 0; ii < n; ++ii) {
+            const Prim<float> q = load_prim32(m.W32, S, (size_t)es * n3 + ii + n * (jj + n * kk));
+            const float li = L[ii];
+            row[0] += li * q.rho;
+            row[1] += li * (q.rho * q.u);
+            row[2] += li * (q.rho * q.v);
+            row[3] += li * (q.rho * q.w);
+            row[4] += li * (q.p * rg + 0.5f * q.rho * (q.u * q.u + q.v * q.v + q.w * q.w));
+          }
+#pragma unroll
+          for (int v = 0; v < 5; ++v) Us[v] += ljk * row[v];
+        }
+      const float ir = 1.0f / Us[0];
+      const float u = Us[1] * ir, v = Us[2] * ir, w = Us[3] * ir;
+      const float pp = (float)ph.gm1 * (Us[4] - 0.5f * Us[0] * (u * u + v * v + w * w));  // p - p_ref
+      const float Ts = (pp + ph.f32c.p_ref) * ph.f32c.rcp_R * ir;
+      float tf[3], qf;
+      bool ok;
+      wall_stress_f(ph, Us[0], u, v, w, Ts, (float)nxd, (float)nyd, (float)nzd, tf, &qf, &ok);
+      if (!ok) atomicOr(status, ST_WM_NOCONV);
+      tau[0] = tf[0]; tau[1] = tf[1]; tau[2] = tf[2]; qw = qf;
+      if (tau_out) {
+        tau_out[slot * 3 + 0] = tau[0]; tau_out[slot * 3 + 1] = tau[1]; tau_out[slot * 3 + 2] = tau[2];
+      }
+    }
+  } else if (ph.viscous) {
     // sample state at h_wm: tensor-product Lagrange interpolation of U
     const size_t slot = (size_t)wf * n2 + ab;
     const int es = m.ws_elem[slot];

@@ -71,6 +71,11 @@ static int run_typed(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {
     k_wall<N, R><<<(unsigned)((work + threads - 1) / threads), threads, 0, ws>>>(a.Uin, m, ph, Fs, a.tau, a.status);
   };
   if (phase & 2) {
+    // the FP32 primitives first: the FP32 wall kernel reads them
+    if (std::is_same<R, float>::value && !a.w32_valid) {
+      const long long S = (long long)a.K * n3;
+      k_prim32<<<(unsigned)std::min<long long>((S + 255) / 256, 152 * 16), 256, 0, s>>>(S, a.Uin, ph, a.W32);
+    }
     if (fork) {
       cudaEventRecord(a.fork, s);
       cudaStreamWaitEvent(a.side, a.fork, 0);
@@ -78,10 +83,6 @@ static int run_typed(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {
       wall();
       if (a.ev) cudaEventRecord(a.ev[4], ws);
       cudaEventRecord(a.join, a.side);
-    }
-    if (std::is_same<R, float>::value && !a.w32_valid) {
-      const long long S = (long long)a.K * n3;
-      k_prim32<<<(unsigned)std::min<long long>((S + 255) / 256, 152 * 16), 256, 0, s>>>(S, a.Uin, ph, a.W32);
     }
     if (a.ev) cudaEventRecord(a.ev[0], s);
     if (ph.viscous) k_lift<N, R><<<a.K, n3, smem_lift, s>>>(a.Uin, m, ph, tab, Rv, Gf);
