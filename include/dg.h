@@ -168,7 +168,12 @@ int dg_set_overlap(dg_ctx* c, int enable);
 /* Sizes: number of elements, nodes per element and total doubles of U. */
 int dg_sizes(const dg_ctx* c, int* N, int* K, long long* n_state);
 
-/* Copies U (5 K n^3 doubles) into / out of the context's state. */
+/* Copies U (5 K n^3 doubles) into / out of the context's state.
+ * dg_set_state also clears the wall model's warm starts: each wall node's
+ * law-of-the-wall solve starts from its previous solution (a few Newton steps,
+ * the bracketed solve from scratch if they do not converge, Sec. 3.2 Alg. 1),
+ * so results depend on the evaluations since the last dg_set_state, to the
+ * solve's stopping tolerance (a Newton step below 1e-12 of max(1, |ln w|)). */
 int dg_set_state(dg_ctx* c, const double* U, int on_device);
 int dg_get_state(dg_ctx* c, double* U, int on_device);
 

@@ -40,6 +40,7 @@ struct dg_ctx {
   // FP32-mixed form: FP32 primitives [6][S]; w32_of_U says they are those of U
   float* W32 = nullptr;
   bool w32_of_U = false;
+  double* wm_t = nullptr;  // wall-law warm start per wall node (NaN: none yet)
   // partitioned meshes: halo buffers [n_halo][5][n2] (state traces, FP64) and
   // [n_halo][4][n2] (viscous-flux traces, flux type), received and sent
   double* halo_U = nullptr;
@@ -129,7 +130,7 @@ void free_all(dg_ctx* c) {
   void* ptrs[] = {c->U, c->dU, c->io, c->io2, c->Ja, c->invJ, c->fgeo, c->nbr, c->elem_face, c->faces,
                   c->ws_elem, c->ws_lag, c->Rv, c->Gf, c->Fs, c->tau, c->status,
                   c->gUf, c->gGf, c->gWf, c->gUs, c->gtheta, c->wq, c->ro_ckpt, c->ro_stage, c->ro_work,
-                  c->ro_scalar, c->wJ, c->W32, c->halo_U, c->send_U, c->halo_G, c->send_G};
+                  c->ro_scalar, c->wJ, c->W32, c->halo_U, c->send_U, c->halo_G, c->send_G, c->wm_t};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -171,6 +172,7 @@ int launch(dg_ctx* c, const double* Uin, int mode, double* Out, double A, double
   }
   a.W32 = c->W32;
   a.w32_valid = (a.fp32 && Uin == c->U && c->w32_of_U) ? 1 : 0;
+  a.wm_t = c->wm_t;
   int rc = dg::run_operator(a, c->ph, c->stream);
   if (rc != 0) {
     c->w32_of_U = false;
@@ -406,6 +408,10 @@ int dg_init_mesh(dg_ctx** out, const dg_mesh_desc* m, const dg_phys* p, const dg
   chk(cudaMalloc(&c->Gf, (o->viscous ? 24 * (size_t)c->K * n2 : 1) * rs));
   chk(cudaMalloc(&c->Fs, (ph.fs_diff ? 10 : 5) * (size_t)c->F * n2 * rs));
   if (f32) chk(alloc(&c->W32, 6 * S));
+  if (c->geo.n_wall > 0) {
+    chk(alloc(&c->wm_t, (size_t)c->geo.n_wall * n2));
+    chk(cudaMemset(c->wm_t, 0xff, (size_t)c->geo.n_wall * n2 * sizeof(double)));  // NaN: no guess yet
+  }
   if (c->geo.n_halo > 0) {
     const size_t nh = (size_t)c->geo.n_halo;
     chk(alloc(&c->halo_U, nh * 5 * n2));
@@ -515,6 +521,12 @@ int dg_set_state(dg_ctx* c, const double* U, int on_device) {
   }
   c->state_set = true;
   c->w32_of_U = false;
+  // a new state starts the wall-law solves afresh (results then depend only
+  // on the sequence of evaluations since the last dg_set_state)
+  if (c->wm_t) {
+    e = cudaMemsetAsync(c->wm_t, 0xff, (size_t)c->geo.n_wall * c->n2 * sizeof(double), c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "dg_set_state");
+  }
   return DG_OK;
 }
 

@@ -80,6 +80,7 @@ struct MeshDev {
   const int* ws_elem;    // [n_wall*n2]
   const double* ws_lag;  // [n_wall*n2*3*n]
   float* W32;            // FP32-mixed form: [6][K*n3] primitives of the input state (null in FP64)
+  double* wm_t;          // [n_wall*n2] last wall-law solution per wall node (warm start; may be null)
 };
 
 template <int N>
@@ -556,6 +557,38 @@ static __device__ double solve_utau(int law, double u, double h, double nu, doub
   return law == 1 ? exp(t) * nu / h : u / exp(t);
 }
 
+// Warm-started solve: up to four Newton steps from t_prev (the node's solution
+// at its previous evaluation, NaN if none), stopping by the same rule as the
+// bracketed solve; if they do not converge, the bracketed solve from scratch.
+// *t_out receives the converged t.  The state changes little between stages, so
+// one or two evaluations of F usually suffice instead of about eight.
+static __device__ double solve_utau_warm(int law, double u, double h, double nu, double kap, double B,
+                                         double t_prev, double* t_out, bool* ok) {
+  *ok = true;
+  if (!(u > 0.0)) { *t_out = t_prev; return 0.0; }
+  if (t_prev == t_prev && fabs(t_prev) < 1e3) {
+    const double lnRe = log(h * u / nu);
+    const double cst = law_const(law, kap, B);
+    double t = t_prev;
+    for (int k = 0; k < 4; ++k) {
+      const double w = exp(t);
+      double L, wdL;
+      law_eval_c(law, w, kap, cst, &L, &wdL);
+      const double Ft = t + log(L) - lnRe;
+      const double dF = 1.0 + wdL / L;
+      if (Ft == 0.0) { *t_out = t; return law == 1 ? exp(t) * nu / h : u / exp(t); }
+      const double nt = t - Ft / dF;
+      if (!(nt == nt) || !(dF > 0.0)) break;
+      const double step = fabs(nt - t);
+      t = nt;
+      if (step <= 1e-12 * fmax(1.0, fabs(t))) { *t_out = t; return law == 1 ? exp(t) * nu / h : u / exp(t); }
+    }
+  }
+  const double ut = solve_utau(law, u, h, nu, kap, B, ok);
+  *t_out = law == 1 ? log(ut * h / nu) : log(u / ut);
+  return ut;
+}
+
 // FP32 form of the wall model for the FP32-mixed kernels: the same steps in
 // FP32 arithmetic, with the Newton stopping tolerances scaled to FP32
 // rounding (a step below 1e-6 of max(1, |t|), or a bracket below 4e-7 of it).
@@ -663,7 +696,7 @@ static __device__ void wall_stress_f(const PhysDev& ph, float rho, float u, floa
 // and q_w = -(cp / Pr) tau_w (T_aw - T_w) / u_s.  Then the law of the wall for
 // u_tau, tau_w = rho_w u_tau^2 along the sample's wall-parallel velocity.
 static __device__ void wall_stress(const PhysDev& ph, const double Us[5], double nx, double ny, double nz,
-                            double tau[3], double* qw, bool* ok) {
+                            double tau[3], double* qw, bool* ok, double* t_warm = nullptr) {
   const double rho = Us[0], ir = 1.0 / rho;
   const double u = Us[1] * ir, v = Us[2] * ir, w = Us[3] * ir;
   const double p = ph.gm1 * (Us[4] - 0.5 * rho * (u * u + v * v + w * w));
@@ -693,7 +726,8 @@ static __device__ void wall_stress(const PhysDev& ph, const double Us[5], double
   }
   const double rhow = rho * T / Tw;
   const double muw = ph.sutherland ? sutherland<double>(ph, Tw) : ph.mu;
-  const double ut = solve_utau(ph.law, uvd, ph.hwm, muw / rhow, ph.kappa, ph.B, ok);
+  const double ut = t_warm ? solve_utau_warm(ph.law, uvd, ph.hwm, muw / rhow, ph.kappa, ph.B, *t_warm, t_warm, ok)
+                           : solve_utau(ph.law, uvd, ph.hwm, muw / rhow, ph.kappa, ph.B, ok);
   const double tw = rhow * ut * ut / um;
   tau[0] = tw * ux; tau[1] = tw * uy; tau[2] = tw * uz;
   if (ph.T_wall > 0.0) *qw = -(ph.cp / ph.Pr) * (rhow * ut * ut) * (Taw - Tw) / um;
@@ -1175,7 +1209,13 @@ k_wall(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, R* __
         for (int v = 0; v < 5; ++v) Us[v] += ljk * row[v];
       }
     bool ok;
-    wall_stress(ph, Us, nxd, nyd, nzd, tau, &qw, &ok);
+    if (m.wm_t) {
+      double tw = m.wm_t[slot];
+      wall_stress(ph, Us, nxd, nyd, nzd, tau, &qw, &ok, &tw);
+      m.wm_t[slot] = tw;
+    } else {
+      wall_stress(ph, Us, nxd, nyd, nzd, tau, &qw, &ok);
+    }
     if (!ok) atomicOr(status, ST_WM_NOCONV);
     if (tau_out) {
       tau_out[slot * 3 + 0] = tau[0]; tau_out[slot * 3 + 1] = tau[1]; tau_out[slot * 3 + 2] = tau[2];

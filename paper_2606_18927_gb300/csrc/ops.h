@@ -43,6 +43,7 @@ struct OpArgs {
   // (mode 1) leaves the primitives of Uout in W32.
   float* W32;
   int w32_valid;
+  double* wm_t;  // wall-law warm-start values per wall node (null: cold solves)
   // partitioned meshes: n_halo halo faces (the last faces), remote traces in
   // halo_U / halo_G, local traces packed into send_U / send_G.  phase selects
   // part of an evaluation: 1 packs the state traces, 2 runs the lifting and

@@ -31,12 +31,13 @@ static Tables<N> make_tables(const double* D, const double* w) {
 template <int N, typename R>
 static int run_typed(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {
   constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
-  MeshDev<R> m;
+  MeshDev<R> m{};
   m.K = a.K; m.F = a.F; m.n_interior = a.n_interior; m.n_wall = a.n_wall; m.n_bc = a.n_bc;
   m.Ja = static_cast<const R*>(a.Ja); m.invJ = static_cast<const R*>(a.invJ);
   m.fgeo = a.fgeo; m.nbr = a.nbr; m.elem_face = a.elem_face; m.faces = a.faces;
   m.ws_elem = a.ws_elem; m.ws_lag = a.ws_lag;
   m.W32 = std::is_same<R, float>::value ? a.W32 : nullptr;
+  m.wm_t = a.wm_t;
   m.n_halo = a.n_halo; m.halo_U = a.halo_U; m.halo_G = static_cast<const R*>(a.halo_G);
   const Tables<N> tab = make_tables<N>(a.D, a.w);
   R* Rv = static_cast<R*>(a.Rv);
@@ -131,7 +132,7 @@ static int run_typed(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {
 template <int N>
 static int run_vjp_typed(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {
   constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
-  MeshDev<double> m;
+  MeshDev<double> m{};
   m.K = a.K; m.F = a.F; m.n_interior = a.n_interior; m.n_wall = a.n_wall; m.n_bc = a.n_bc;
   m.Ja = static_cast<const double*>(a.Ja); m.invJ = static_cast<const double*>(a.invJ);
   m.fgeo = a.fgeo; m.nbr = a.nbr; m.elem_face = a.elem_face; m.faces = a.faces;
@@ -163,7 +164,7 @@ template <int N>
 static int run_wall_loss_typed(const OpArgs& a, const PhysDev& ph, const double* wq, double inv_total, int grad,
                                double* loss, cudaStream_t s) {
   constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
-  MeshDev<double> m;
+  MeshDev<double> m{};
   m.K = a.K; m.F = a.F; m.n_interior = a.n_interior; m.n_wall = a.n_wall; m.n_bc = a.n_bc;
   m.Ja = static_cast<const double*>(a.Ja); m.invJ = static_cast<const double*>(a.invJ);
   m.fgeo = a.fgeo; m.nbr = a.nbr; m.elem_face = a.elem_face; m.faces = a.faces;
