@@ -734,6 +734,52 @@ static __device__ void wall_stress(const PhysDev& ph, const double Us[5], double
 }
 
 // ---------------------------------------------------------------------------
+// Even/odd form of a line contraction y_q = sum_m M_qm x_m whose matrix is
+// centro-antisymmetric (M_{N-q,N-m} = -M_qm; the LGL derivative matrix D and
+// (w_m / w_q) D_mq are).  With xe_m = x_m + x_{N-m} and xo_m = x_m - x_{N-m}
+// for m < n/2,
+//   E_q = sum_m (M_qm + M_q,N-m) / 2 xe_m,   O_q = sum_m (M_qm - M_q,N-m) / 2 xo_m,
+//   y_q = E_q + O_q,   y_{N-q} = O_q - E_q          (q < n/2, n even),
+// n/2 products per output instead of n.  The node at line position q < n/2
+// forms E_q, its mirror node N - q forms O_q, and the two swap them with a
+// shuffle: used with N = 7 in the warp layout of k_lift, where the mirror
+// node along xi, eta, zeta is lane ^ 7, ^ 8, ^ 16.
+// ---------------------------------------------------------------------------
+template <int N>
+struct LineEO {
+  static constexpr int n = N + 1, h = n / 2;
+  static_assert(n % 2 == 0, "even/odd form needs an even number of nodes");
+  // table [n][h]: rows q < h hold (M_qm + M_q,N-m) / 2, rows q >= h hold
+  // (M_q'm - M_q',N-m) / 2 with q' = N - q
+  __device__ static double coef(const double* M, int t) {
+    const int q = t / h, mm = t % h;
+    const int r = q < h ? q : N - q;
+    const double a = M[r * n + mm], b = M[r * n + N - mm];
+    return q < h ? 0.5 * (a + b) : 0.5 * (a - b);
+  }
+  // node at line position pos on the line along dir through node p (at q)
+  __device__ static int at(int p, int dir, int q, int pos) {
+    return p + (pos - q) * (dir == 0 ? 1 : (dir == 1 ? n : n * n));
+  }
+  // the value a node stores at its line position: xe_q (q < h) or xo_{N-q}
+  template <class R>
+  __device__ static R half(int q, R x, R x_mirror) { return fma(q < h ? R(1) : R(-1), x, x_mirror); }
+  template <class R>
+  __device__ static R mirror(R x, int dir) {
+    return __shfl_xor_sync(0xffffffffu, x, dir == 0 ? 7 : (dir == 1 ? 8 : 16));
+  }
+  // y at this node from the stored halves sH of the line and the table sM
+  template <class R>
+  __device__ static R apply(const R* sM, const R* sH, int p, int dir, int q) {
+    const bool lo = q < h;
+    R P = 0;
+#pragma unroll
+    for (int mm = 0; mm < h; ++mm) P = fma(sM[q * h + mm], sH[at(p, dir, q, lo ? mm : N - mm)], P);
+    return fma(lo ? R(1) : R(-1), mirror(P, dir), P);
+  }
+};
+
+// ---------------------------------------------------------------------------
 // k_lift: one CTA of n^3 threads per element.
 // ---------------------------------------------------------------------------
 template <int N, typename R>
@@ -741,19 +787,41 @@ __global__ void __launch_bounds__((N + 1) * (N + 1) * (N + 1), ((N + 1) * (N + 1
 k_lift(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const Tables<N> tab,
        R* __restrict__ Rv, R* __restrict__ Gf) {
   constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
+  // FP64, N = 7: line contractions in even/odd form (LineEO), with the thread
+  // of each node sharing a warp with its three mirror nodes (the FP32 kernel is
+  // not bound by its multiply-adds: the extra barriers and shuffles cost more)
+  constexpr bool EO = (n == 8) && std::is_same<R, double>::value;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* sW = reinterpret_cast<R*>(smem_raw);      // [4][n3]
   R* sC = sW + 4 * n3;                          // [6][4][n2]
   R* sG = sC + 24 * n2;                         // [3][4][n3]
-  R* sD = sG + 12 * n3;                         // [n2]
-  R* sDv = sD + n2;                             // [n2]
+  R* sD = sG + 12 * n3;                         // [n2]  (EO: [n][n/2] even/odd rows of D)
+  R* sDv = sD + n2;                             // [n2]  (EO: the same for Dvisc)
   R* siw = sDv + n2;                            // [n]
-  const int e = blockIdx.x, p = threadIdx.x;
-  const int i = p % n, j = (p / n) % n, k = p / n2;
+  const int e = blockIdx.x, tid = threadIdx.x;
+  int i, j, k;
+  if constexpr (EO) {
+    // warp w = a + 4 b holds the xi-lines i = 0..7 at j in {a, N - a} and
+    // k in {b, N - b}: the mirror node along xi, eta, zeta is lane ^ 7, ^ 8, ^ 16
+    const int lane = tid & 31, w = tid >> 5, a = w & 3, b = w >> 2;
+    i = lane & 7;
+    j = (lane & 8) ? N - a : a;
+    k = (lane & 16) ? N - b : b;
+  } else {
+    i = tid % n; j = (tid / n) % n; k = tid / n2;
+  }
+  const int p = i + n * (j + n * k);  // this thread's node
   const size_t S = (size_t)m.K * n3;
   const size_t g = (size_t)e * n3 + p;
-  for (int t = p; t < n2; t += n3) { sD[t] = (R)tab.D[t]; sDv[t] = (R)tab.Dvisc[t]; }
-  if (p < n) siw[p] = (R)tab.iw[p];
+  if constexpr (EO) {
+    if (tid < n * (n / 2)) {
+      sD[tid] = (R)LineEO<N>::coef(tab.D, tid);
+      sDv[tid] = (R)LineEO<N>::coef(tab.Dvisc, tid);
+    }
+  } else {
+    for (int t = tid; t < n2; t += n3) { sD[t] = (R)tab.D[t]; sDv[t] = (R)tab.Dvisc[t]; }
+  }
+  if (tid < n) siw[tid] = (R)tab.iw[tid];
   // own primitives W = (u, v, w, T)
   {
     R u, v, w, T;
@@ -763,15 +831,10 @@ k_lift(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
       velocity_temperature<R>(U[g], U[S + g], U[2 * S + g], U[3 * S + g], U[4 * S + g], ph, u, v, w, T);
     sW[p] = u; sW[n3 + p] = v; sW[2 * n3 + p] = w; sW[3 * n3 + p] = T;
   }
-  // own metrics
-  R ja[9];
-#pragma unroll
-  for (int c = 0; c < 9; ++c) ja[c] = m.Ja[(size_t)c * S + g];
-  const R iJ = m.invJ[g];
   __syncthreads();
   // W* - W at the six faces (BR1 average with the neighbour, or the mirror
   // state at a slip wall)
-  for (int t = p; t < 6 * n2; t += n3) {
+  for (int t = tid; t < 6 * n2; t += n3) {
     const int l = t / n2, ab = t - l * n2, a = ab % n, b = ab / n;
     const int q = fnode<N>(l, a, b);
     const int nb = m.nbr[e * 6 + l];
@@ -821,43 +884,59 @@ k_lift(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
   __syncthreads();
   // gradients in reference space
   R dW[3][4];
+  if constexpr (EO) {
+    const int qd[3] = {i, j, k};
 #pragma unroll
-  for (int v = 0; v < 4; ++v) {
-    R s0 = 0, s1 = 0, s2 = 0;
+    for (int dir = 0; dir < 3; ++dir)
 #pragma unroll
-    for (int mm = 0; mm < n; ++mm) {
-      s0 += sD[i * n + mm] * sW[v * n3 + mm + n * (j + n * k)];
-      s1 += sD[j * n + mm] * sW[v * n3 + i + n * (mm + n * k)];
-      s2 += sD[k * n + mm] * sW[v * n3 + i + n * (j + n * mm)];
+      for (int v = 0; v < 4; ++v)
+        sG[(dir * 4 + v) * n3 + p] = LineEO<N>::half(qd[dir], sW[v * n3 + p],
+                                                      sW[v * n3 + LineEO<N>::at(p, dir, qd[dir], N - qd[dir])]);
+    __syncthreads();
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+#pragma unroll
+      for (int dir = 0; dir < 3; ++dir)
+        dW[dir][v] = LineEO<N>::apply(sD, sG + (dir * 4 + v) * n3, p, dir, qd[dir]);
+  } else {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      R s0 = 0, s1 = 0, s2 = 0;
+#pragma unroll
+      for (int mm = 0; mm < n; ++mm) {
+        s0 += sD[i * n + mm] * sW[v * n3 + mm + n * (j + n * k)];
+        s1 += sD[j * n + mm] * sW[v * n3 + i + n * (mm + n * k)];
+        s2 += sD[k * n + mm] * sW[v * n3 + i + n * (j + n * mm)];
+      }
+      dW[0][v] = s0; dW[1][v] = s1; dW[2][v] = s2;
     }
-    dW[0][v] = s0; dW[1][v] = s1; dW[2][v] = s2;
   }
-  // physical gradients q[d][v] = (1/J) (sum_dir Ja^dir_d dW_dir + surface terms)
+  // surface corrections of the reference-space gradient: (W* - W) (+-1 / w)
+  // at the first and last node of each line (with n s = +-Ja^dir they give
+  // the (W* - W) (n s)_d / w terms of the physical gradient)
+  auto surf = [&](int dir, int l, int ab, R sgn_iw) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) dW[dir][v] += sgn_iw * sC[(l * 4 + v) * n2 + ab];
+  };
+  // (one branch per direction: a warp holds nodes of both end faces of the
+  // lines along xi, and the masked lanes of a branch cost as much as active ones)
+  if (i == 0 || i == N) surf(0, i == 0 ? 0 : 1, j + n * k, i == 0 ? -siw[0] : siw[N]);
+  if (j == 0 || j == N) surf(1, j == 0 ? 2 : 3, i + n * k, j == 0 ? -siw[0] : siw[N]);
+  if (k == 0 || k == N) surf(2, k == 0 ? 4 : 5, i + n * j, k == 0 ? -siw[0] : siw[N]);
+  // own metrics (loaded here, after the contractions, to keep them out of
+  // the registers live across those)
+  R ja[9];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) ja[c] = m.Ja[(size_t)c * S + g];
+  const R iJ = m.invJ[g];
+  // physical gradients q[d][v] = (1/J) sum_dir Ja^dir_d dW_dir
   R q[3][4];
 #pragma unroll
-  for (int d = 0; d < 3; ++d)
+  for (int d = 0; d < 3; ++d) {
+    const R j0 = iJ * ja[0 * 3 + d], j1 = iJ * ja[1 * 3 + d], j2 = iJ * ja[2 * 3 + d];
 #pragma unroll
-    for (int v = 0; v < 4; ++v) q[d][v] = ja[0 * 3 + d] * dW[0][v] + ja[1 * 3 + d] * dW[1][v] + ja[2 * 3 + d] * dW[2][v];
-  // surface corrections: (W* - W) (n s)_d / w_perp with n s = +-Ja^dir
-  auto surf = [&](int l, int ab, R sgn_iw) {
-    const int dir = l >> 1;
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const R f = sgn_iw * ja[dir * 3 + d];
-#pragma unroll
-      for (int v = 0; v < 4; ++v) q[d][v] += f * sC[(l * 4 + v) * n2 + ab];
-    }
-  };
-  if (i == 0) surf(0, j + n * k, -siw[0]);
-  if (i == N) surf(1, j + n * k, siw[N]);
-  if (j == 0) surf(2, i + n * k, -siw[0]);
-  if (j == N) surf(3, i + n * k, siw[N]);
-  if (k == 0) surf(4, i + n * j, -siw[0]);
-  if (k == N) surf(5, i + n * j, siw[N]);
-#pragma unroll
-  for (int d = 0; d < 3; ++d)
-#pragma unroll
-    for (int v = 0; v < 4; ++v) q[d][v] *= iJ;
+    for (int v = 0; v < 4; ++v) q[d][v] = j0 * dW[0][v] + j1 * dW[1][v] + j2 * dW[2][v];
+  }
   // viscous flux Fv_d = (0, tau_1d, tau_2d, tau_3d, tau_jd u_j + k dT/dx_d)
   R mu = cR<R>(ph.mu, ph.f32c.mu), kc = cR<R>(ph.kcond, ph.f32c.kcond);
   if (ph.sutherland) {
@@ -885,10 +964,8 @@ k_lift(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
 #pragma unroll
   for (int dir = 0; dir < 3; ++dir)
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
+    for (int v = 0; v < 4; ++v)
       G[dir][v] = ja[dir * 3 + 0] * Fv[0][v] + ja[dir * 3 + 1] * Fv[1][v] + ja[dir * 3 + 2] * Fv[2][v];
-      sG[(dir * 4 + v) * n3 + p] = G[dir][v];
-    }
   // own outward viscous flux at face nodes: Gf[e][l][v][ab] = +-G^{l/2}
   auto gface = [&](int l, int ab, R sgn) {
     R* dst = Gf + ((size_t)e * 6 + l) * 4 * n2 + ab;
@@ -901,18 +978,40 @@ k_lift(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
   if (j == N) gface(3, i + n * k, R(1));
   if (k == 0) gface(4, i + n * j, R(-1));
   if (k == N) gface(5, i + n * j, R(1));
-  __syncthreads();
   // weak-form viscous volume term R_v = sum_dir sum_m (w_m / w_i) D_mi G^dir_m
+  if constexpr (EO) {
+    const int qd[3] = {i, j, k};
+    __syncthreads();  // the gradient contractions have read sG
 #pragma unroll
-  for (int v = 0; v < 4; ++v) {
-    R s = 0;
+    for (int dir = 0; dir < 3; ++dir)
 #pragma unroll
-    for (int mm = 0; mm < n; ++mm) {
-      s += sDv[i * n + mm] * sG[(0 * 4 + v) * n3 + mm + n * (j + n * k)];
-      s += sDv[j * n + mm] * sG[(1 * 4 + v) * n3 + i + n * (mm + n * k)];
-      s += sDv[k * n + mm] * sG[(2 * 4 + v) * n3 + i + n * (j + n * mm)];
+      for (int v = 0; v < 4; ++v)
+        sG[(dir * 4 + v) * n3 + p] = LineEO<N>::half(qd[dir], G[dir][v], LineEO<N>::mirror(G[dir][v], dir));
+    __syncthreads();
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      R s = 0;
+#pragma unroll
+      for (int dir = 0; dir < 3; ++dir) s += LineEO<N>::apply(sDv, sG + (dir * 4 + v) * n3, p, dir, qd[dir]);
+      Rv[(size_t)v * S + g] = s;
     }
-    Rv[(size_t)v * S + g] = s;
+  } else {
+#pragma unroll
+    for (int dir = 0; dir < 3; ++dir)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) sG[(dir * 4 + v) * n3 + p] = G[dir][v];
+    __syncthreads();
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      R s = 0;
+#pragma unroll
+      for (int mm = 0; mm < n; ++mm) {
+        s += sDv[i * n + mm] * sG[(0 * 4 + v) * n3 + mm + n * (j + n * k)];
+        s += sDv[j * n + mm] * sG[(1 * 4 + v) * n3 + i + n * (mm + n * k)];
+        s += sDv[k * n + mm] * sG[(2 * 4 + v) * n3 + i + n * (j + n * mm)];
+      }
+      Rv[(size_t)v * S + g] = s;
+    }
   }
 }
 
@@ -1254,6 +1353,12 @@ struct StageArgs {
   int write_w32;  // FP32-mixed form: store the updated state's primitives into W32
 };
 
+// the values of one node that the two-point flux of a direction reads
+template <class R>
+struct VolNode {
+  R rho, u, v, w, p4, hh, p2, ib, irh, a0, a1, a2;
+};
+
 template <int N>
 struct VolShape {
   static constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
@@ -1349,110 +1454,152 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
     const bool active = (seg < LPW) && (L0 < n2);
     const int L = active ? L0 : 0;
     const int base = seg * n;  // first lane of the segment
+    const int la = L % n, lb = L / n;
+    // node at position q of this lane's line along dir (a warp holds the same
+    // lines L in every direction)
+    auto node_at = [&](int dir, int q) {
+      return dir == 0 ? q + n * L : (dir == 1 ? la + n * q + n2 * lb : L + n2 * q);
+    };
+    auto load_node = [&](int node, int dir) {
+      VolNode<R> X;
+      X.rho = sQ[node]; X.u = sQ[n3 + node]; X.v = sQ[2 * n3 + node]; X.w = sQ[3 * n3 + node];
+      X.p4 = sQ[4 * n3 + node]; X.hh = sQ[5 * n3 + node];
+      X.p2 = (kg || EC) ? sQ[6 * n3 + node] : R(0);
+      X.ib = EC ? sQ[7 * n3 + node] : R(0);
+      X.irh = EC ? sQ[8 * n3 + node] : R(0);
+      X.a0 = sA[(dir * 3 + 0) * n3 + node]; X.a1 = sA[(dir * 3 + 1) * n3 + node];
+      X.a2 = sA[(dir * 3 + 2) * n3 + node];
+      return X;
+    };
+    // symmetric two-point flux F#(A, B) . 4 {Ja} in the scaled form of the
+    // coefficient tables (mass row against DVS / 8, the others against DVS / 16)
+    auto sym_flux = [&](const VolNode<R>& A, const VolNode<R>& B, R F[5]) {
+      const R Sr = A.rho + B.rho, Su = A.u + B.u, Sv = A.v + B.v, Sw = A.w + B.w;
+      const R Sp = A.p4 + B.p4;
+      const R Sa0 = A.a0 + B.a0, Sa1 = A.a1 + B.a1, Sa2 = A.a2 + B.a2;
+      const R ua = Su * Sa0 + Sv * Sa1 + Sw * Sa2;  // 4 {u}.{a}
+      if constexpr (EC) {
+        // rho_ln = Sr G / 2; 1 / beta_ln = Sib Q / 2; 1 / (bA + bB) = Sib Rb / 4
+        const R Dr = A.rho - B.rho, Db = A.hh - B.hh, Sib = A.ib + B.ib;
+        const R tr = R(0.25) * Dr * Dr * (A.irh * B.irh);
+        const R tb = R(0.25) * Db * Db * (A.ib * B.ib);
+        const R G = tr < LogMeanCut<R>::v ? logmean_G<R>(tr) : R(2) * Dr / (Sr * log1p(Dr / B.rho));
+        R Q, Rb;
+        if (tb < LogMeanCut<R>::v) {
+          Q = logmean_Q<R>(tb);
+          Rb = inv_one_plus<R>(tb);
+        } else {
+          Q = R(2) * log1p(Db / B.hh) / (Db * Sib);
+          Rb = R(4) / (Sib * (A.hh + B.hh));
+        }
+        const R mf = Sr * G * ua;                 // 8 F_rho
+        const R Spt = R(0.25) * Sib * Rb * Sp;    // 8 (p~ - p_ref)
+        F[0] = mf;
+        F[1] = mf * Su + Spt * Sa0;               // 16 F_m
+        F[2] = mf * Sv + Spt * Sa1;
+        F[3] = mf * Sw + Spt * Sa2;
+        // 16 F_E = 2 mf (1 / (2 (gamma-1) beta_ln) + |{u}|^2 - {|u|^2} / 2) + 4 p~ (4 {u}.{a})
+        const R X = R(0.25) * (Sib * Q * cR<R>(ph.rgm1, ph.f32c.rgm1) + Su * Su + Sv * Sv + Sw * Sw - A.p2 - B.p2);
+        F[4] = R(2) * mf * X + (R(0.5) * Spt + R(4) * cR<R>(ph.p_ref, ph.f32c.p_ref)) * ua;
+      } else {
+        const R mf = Sr * ua;                     // 8 F0
+        F[0] = mf;
+        F[1] = mf * Su + Sp * Sa0;                // 16 F1
+        F[2] = mf * Sv + Sp * Sa1;
+        F[3] = mf * Sw + Sp * Sa2;
+        F[4] = mf * (A.hh + B.hh);                // 16 F4
+        if (kg) F[4] += (A.p2 + B.p2) * ua;
+      }
+    };
+    // FP64, N = 7: the n/2 pairs at distance n/2 of a line would be formed twice
+    // (once in each lane); instead the distance-n/2 step of the xi pass forms
+    // the xi pairs in lanes pos < n/2 and the eta pairs in lanes pos >= n/2
+    // (swapped by a shuffle), the one of the eta pass forms the zeta pairs,
+    // and a lane carries the result for its next pass's node in `carry`.
+    constexpr bool HALF = std::is_same<R, double>::value && n == 8;
+    constexpr int DMAX = HALF ? n / 2 - 1 : n / 2;
+    R carry[5] = {R(0), R(0), R(0), R(0), R(0)};
 #pragma unroll 1
     for (int dir = 0; dir < 3; ++dir) {
-      const int a = L % n, b = L / n;
-      auto node = [&](int q) {
-        return dir == 0 ? q + n * L : (dir == 1 ? a + n * q + n2 * b : L + n2 * q);
-      };
-      const int me = node(pos);
-      const R rho = sQ[me], u = sQ[n3 + me], v = sQ[2 * n3 + me], w = sQ[3 * n3 + me];
-      const R p4 = sQ[4 * n3 + me], hh = sQ[5 * n3 + me];
-      const R p2 = (kg || EC) ? sQ[6 * n3 + me] : R(0);
-      const R ib = EC ? sQ[7 * n3 + me] : R(0), irh = EC ? sQ[8 * n3 + me] : R(0);
-      const R a0 = sA[(dir * 3 + 0) * n3 + me], a1 = sA[(dir * 3 + 1) * n3 + me],
-              a2 = sA[(dir * 3 + 2) * n3 + me];
-      R acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0, acc4 = 0;
+      const int me = node_at(dir, pos);
+      const VolNode<R> A = load_node(me, dir);
+      R acc[5];
 #pragma unroll
-      for (int d = 1; d <= n / 2; ++d) {
+      for (int v = 0; v < 5; ++v) acc[v] = carry[v];
+#pragma unroll
+      for (int d = 1; d <= DMAX; ++d) {
         const int pm = pos + d < n ? pos + d : pos + d - n;
-        const int q = node(pm);
-        const R rq = sQ[q];
-        const R Sr = rho + rq, Su = u + sQ[n3 + q], Sv = v + sQ[2 * n3 + q], Sw = w + sQ[3 * n3 + q];
-        const R Sp = p4 + sQ[4 * n3 + q];
-        const R Sa0 = a0 + sA[(dir * 3 + 0) * n3 + q], Sa1 = a1 + sA[(dir * 3 + 1) * n3 + q],
-                Sa2 = a2 + sA[(dir * 3 + 2) * n3 + q];
+        const int q = node_at(dir, pm);
         if constexpr (std::is_same<R, float>::value && !EC) {
           if (dif) {
-            const NodeF mi{rho, u, v, w, p4, hh};
-            const NodeF mq{rq, sQ[n3 + q], sQ[2 * n3 + q], sQ[3 * n3 + q], sQ[4 * n3 + q], sQ[5 * n3 + q]};
+            const NodeF mi{A.rho, A.u, A.v, A.w, A.p4, A.hh};
+            const NodeF mq{sQ[q], sQ[n3 + q], sQ[2 * n3 + q], sQ[3 * n3 + q], sQ[4 * n3 + q], sQ[5 * n3 + q]};
             const float aq0 = sA[(dir * 3 + 0) * n3 + q], aq1 = sA[(dir * 3 + 1) * n3 + q],
                         aq2 = sA[(dir * 3 + 2) * n3 + q];
             float G[5];
-            flux_delta(mi, mq, a0, a1, a2, aq0 - a0, aq1 - a1, aq2 - a2, G);
+            flux_delta(mi, mq, A.a0, A.a1, A.a2, aq0 - A.a0, aq1 - A.a1, aq2 - A.a2, G);
             const float c1 = sC1[pos * n + pm];
-            acc0 += c1 * G[0]; acc1 += c1 * G[1]; acc2 += c1 * G[2]; acc3 += c1 * G[3]; acc4 += c1 * G[4];
+#pragma unroll
+            for (int v = 0; v < 5; ++v) acc[v] += c1 * G[v];
             if (2 * d != n) {
               // G(q -> i) for the partner lane (pos + d); receive G(i -> pos - d)
-              flux_delta(mq, mi, aq0, aq1, aq2, a0 - aq0, a1 - aq1, a2 - aq2, G);
+              flux_delta(mq, mi, aq0, aq1, aq2, A.a0 - aq0, A.a1 - aq1, A.a2 - aq2, G);
               const int src = base + (pos - d >= 0 ? pos - d : pos - d + n);
-              const float g0 = __shfl_sync(0xffffffffu, G[0], src);
-              const float g1 = __shfl_sync(0xffffffffu, G[1], src);
-              const float g2 = __shfl_sync(0xffffffffu, G[2], src);
-              const float g3 = __shfl_sync(0xffffffffu, G[3], src);
-              const float g4 = __shfl_sync(0xffffffffu, G[4], src);
               const float r1 = sC1[pos * n + (src - base)];
-              acc0 += r1 * g0; acc1 += r1 * g1; acc2 += r1 * g2; acc3 += r1 * g3; acc4 += r1 * g4;
+#pragma unroll
+              for (int v = 0; v < 5; ++v) acc[v] += r1 * __shfl_sync(0xffffffffu, G[v], src);
             }
             continue;
           }
         }
-        const R ua = Su * Sa0 + Sv * Sa1 + Sw * Sa2;  // 4 {u}.{a}
-        R mf, F1, F2, F3, F4;
-        if constexpr (EC) {
-          // rho_ln = Sr G / 2; 1 / beta_ln = Sib Q / 2; 1 / (bA + bB) = Sib Rb / 4
-          const R bq = sQ[5 * n3 + q], ibq = sQ[7 * n3 + q];
-          const R Dr = rho - rq, Db = hh - bq, Sib = ib + ibq;
-          const R tr = R(0.25) * Dr * Dr * (irh * sQ[8 * n3 + q]);
-          const R tb = R(0.25) * Db * Db * (ib * ibq);
-          const R G = tr < LogMeanCut<R>::v ? logmean_G<R>(tr) : R(2) * Dr / (Sr * log1p(Dr / rq));
-          R Q, Rb;
-          if (tb < LogMeanCut<R>::v) {
-            Q = logmean_Q<R>(tb);
-            Rb = inv_one_plus<R>(tb);
-          } else {
-            Q = R(2) * log1p(Db / bq) / (Db * Sib);
-            Rb = R(4) / (Sib * (hh + bq));
-          }
-          mf = Sr * G * ua;                    // 8 F_rho
-          const R Spt = R(0.25) * Sib * Rb * Sp;  // 8 (p~ - p_ref)
-          F1 = mf * Su + Spt * Sa0;            // 16 F_m
-          F2 = mf * Sv + Spt * Sa1;
-          F3 = mf * Sw + Spt * Sa2;
-          // 16 F_E = 2 mf (1 / (2 (gamma-1) beta_ln) + |{u}|^2 - {|u|^2} / 2) + 4 p~ (4 {u}.{a})
-          const R X = R(0.25) * (Sib * Q * cR<R>(ph.rgm1, ph.f32c.rgm1) + Su * Su + Sv * Sv + Sw * Sw - p2 - sQ[6 * n3 + q]);
-          F4 = R(2) * mf * X + (R(0.5) * Spt + R(4) * cR<R>(ph.p_ref, ph.f32c.p_ref)) * ua;
-        } else {
-          const R Sh = hh + sQ[5 * n3 + q];
-          mf = Sr * ua;                        // 8 F0
-          F1 = mf * Su + Sp * Sa0;             // 16 F1
-          F2 = mf * Sv + Sp * Sa1;
-          F3 = mf * Sw + Sp * Sa2;
-          F4 = mf * Sh;                        // 16 F4
-          if (kg) F4 += (p2 + sQ[6 * n3 + q]) * ua;
-        }
+        R F[5];
+        sym_flux(A, load_node(q, dir), F);
         const R c8 = sC8[pos * n + pm], c16 = sC16[pos * n + pm];
-        acc0 += c8 * mf; acc1 += c16 * F1; acc2 += c16 * F2; acc3 += c16 * F3; acc4 += c16 * F4;
+        acc[0] += c8 * F[0];
+#pragma unroll
+        for (int v = 1; v < 5; ++v) acc[v] += c16 * F[v];
         if (2 * d != n) {
           // hand the pair flux to the partner lane (pos + d); receive the one
           // of lane (pos - d)
           const int src = base + (pos - d >= 0 ? pos - d : pos - d + n);
-          const R g0 = __shfl_sync(0xffffffffu, mf, src);
-          const R g1 = __shfl_sync(0xffffffffu, F1, src);
-          const R g2 = __shfl_sync(0xffffffffu, F2, src);
-          const R g3 = __shfl_sync(0xffffffffu, F3, src);
-          const R g4 = __shfl_sync(0xffffffffu, F4, src);
           const int ps = src - base;
           const R r8 = sC8[pos * n + ps], r16 = sC16[pos * n + ps];
-          acc0 += r8 * g0; acc1 += r16 * g1; acc2 += r16 * g2; acc3 += r16 * g3; acc4 += r16 * g4;
+          acc[0] += r8 * __shfl_sync(0xffffffffu, F[0], src);
+#pragma unroll
+          for (int v = 1; v < 5; ++v) acc[v] += r16 * __shfl_sync(0xffffffffu, F[v], src);
+        }
+      }
+      if constexpr (HALF) {
+        constexpr int h = n / 2;
+        const int px = pos ^ h;  // partner at distance n/2
+        const R c8 = sC8[pos * n + px], c16 = sC16[pos * n + px];
+        if (dir == 0) {
+          const bool lo = pos < h;
+          const int dd = lo ? 0 : 1, pa = pos & (h - 1);
+          R F[5];
+          sym_flux(load_node(node_at(dd, pa), dd), load_node(node_at(dd, pa + h), dd), F);
+#pragma unroll
+          for (int v = 0; v < 5; ++v) {
+            const R Fx = __shfl_xor_sync(0xffffffffu, F[v], h);
+            const R cv = v == 0 ? c8 : c16;
+            acc[v] += cv * (lo ? F[v] : Fx);
+            carry[v] = cv * (lo ? Fx : F[v]);
+          }
+        } else if (dir == 1) {
+          R F[5];
+          sym_flux(load_node(node_at(2, pos), 2), load_node(node_at(2, px), 2), F);
+          carry[0] = c8 * F[0];
+#pragma unroll
+          for (int v = 1; v < 5; ++v) carry[v] = c16 * F[v];
         }
       }
       if (active) {
         if (dir == 0) {
-          sR[me] = acc0; sR[n3 + me] = acc1; sR[2 * n3 + me] = acc2; sR[3 * n3 + me] = acc3; sR[4 * n3 + me] = acc4;
+#pragma unroll
+          for (int v = 0; v < 5; ++v) sR[v * n3 + me] = acc[v];
         } else {
-          sR[me] += acc0; sR[n3 + me] += acc1; sR[2 * n3 + me] += acc2; sR[3 * n3 + me] += acc3;
-          sR[4 * n3 + me] += acc4;
+#pragma unroll
+          for (int v = 0; v < 5; ++v) sR[v * n3 + me] += acc[v];
         }
       }
       __syncthreads();
@@ -1483,12 +1630,10 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
 #pragma unroll
     for (int v = 0; v < 5; ++v) acc[v] += sg * src[v * n2];
   };
-  if (i == 0) surf(0, j + n * k, siw[0]);
-  if (i == N) surf(1, j + n * k, siw[N]);
-  if (j == 0) surf(2, i + n * k, siw[0]);
-  if (j == N) surf(3, i + n * k, siw[N]);
-  if (k == 0) surf(4, i + n * j, siw[0]);
-  if (k == N) surf(5, i + n * j, siw[N]);
+  // one branch per direction (masked lanes of a branch cost as much as active ones)
+  if (i == 0 || i == N) surf(i == 0 ? 0 : 1, j + n * k, i == 0 ? siw[0] : siw[N]);
+  if (j == 0 || j == N) surf(j == 0 ? 2 : 3, i + n * k, j == 0 ? siw[0] : siw[N]);
+  if (k == 0 || k == N) surf(k == 0 ? 4 : 5, i + n * j, k == 0 ? siw[0] : siw[N]);
   // Ut = -(1/J) acc + S, S = (0, f, f . u)
   const R iJ = m.invJ[g];
   const bool force = ph.has_force != 0;
