@@ -1514,15 +1514,30 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
     // FP64, N = 7: the n/2 pairs at distance n/2 of a line would be formed twice
     // (once in each lane); instead the distance-n/2 step of the xi pass forms
     // the xi pairs in lanes pos < n/2 and the eta pairs in lanes pos >= n/2
-    // (swapped by a shuffle), the one of the eta pass forms the zeta pairs,
-    // and a lane carries the result for its next pass's node in `carry`.
-    constexpr bool HALF = std::is_same<R, double>::value && n == 8;
+    // (swapped by a shuffle), and the one of the eta pass, in the first half
+    // of the warps, the zeta pairs of its own lines (lanes pos < n/2) and of
+    // the lines of warp + WARPS_LINES/2 (lanes pos >= n/2, through shared
+    // memory: the xi metrics, no longer read after the xi pass).  A lane
+    // carries the result for its next pass's node in `carry`.
+    constexpr bool HALF = std::is_same<R, double>::value && n == 8 && Sh::WARPS_LINES % 2 == 0;
     constexpr int DMAX = HALF ? n / 2 - 1 : n / 2;
+    constexpr int HW = Sh::WARPS_LINES / 2, NX = HW * LPW * (n / 2);
+    R* sX = sA;  // [5][NX] zeta pair fluxes handed to the second half of the warps
     R carry[5] = {R(0), R(0), R(0), R(0), R(0)};
 #pragma unroll 1
     for (int dir = 0; dir < 3; ++dir) {
       const int me = node_at(dir, pos);
       const VolNode<R> A = load_node(me, dir);
+      if constexpr (HALF) {
+        if (dir == 2 && warp >= HW) {
+          const int px = pos ^ (n / 2);
+          const R c8 = sC8[pos * n + px], c16 = sC16[pos * n + px];
+          const int x = ((warp - HW) * LPW + seg) * (n / 2) + (pos & (n / 2 - 1));
+          carry[0] = c8 * sX[x];
+#pragma unroll
+          for (int v = 1; v < 5; ++v) carry[v] = c16 * sX[v * NX + x];
+        }
+      }
       R acc[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) acc[v] = carry[v];
@@ -1585,12 +1600,19 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
             acc[v] += cv * (lo ? F[v] : Fx);
             carry[v] = cv * (lo ? Fx : F[v]);
           }
-        } else if (dir == 1) {
+        } else if (dir == 1 && warp < HW) {
+          const bool lo = pos < h;
+          const int pa = pos & (h - 1);
+          const int Lz = lo ? L : L + HW * LPW;  // zeta line of this warp or of warp + HW
           R F[5];
-          sym_flux(load_node(node_at(2, pos), 2), load_node(node_at(2, px), 2), F);
-          carry[0] = c8 * F[0];
+          sym_flux(load_node(Lz + n2 * pa, 2), load_node(Lz + n2 * (pa + h), 2), F);
+          const int x = (warp * LPW + seg) * h + pa;
 #pragma unroll
-          for (int v = 1; v < 5; ++v) carry[v] = c16 * F[v];
+          for (int v = 0; v < 5; ++v) {
+            const R Fx = __shfl_xor_sync(0xffffffffu, F[v], h);
+            carry[v] = (v == 0 ? c8 : c16) * (lo ? F[v] : Fx);
+            if (!lo) sX[v * NX + x] = F[v];
+          }
         }
       }
       if (active) {
