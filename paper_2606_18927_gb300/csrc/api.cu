@@ -40,6 +40,9 @@ struct dg_ctx {
   // FP32-mixed form: FP32 primitives [6][S]; w32_of_U says they are those of U
   float* W32 = nullptr;
   bool w32_of_U = false;
+  // FP64 viscous form: primitives [6][S] formed by the lifting kernel for the
+  // face and volume kernels of the same evaluation
+  double* W64 = nullptr;
   double* wm_t = nullptr;  // wall-law warm start per wall node (NaN: none yet)
   // partitioned meshes: halo buffers [n_halo][5][n2] (state traces, FP64) and
   // [n_halo][4][n2] (viscous-flux traces, flux type), received and sent
@@ -130,7 +133,7 @@ void free_all(dg_ctx* c) {
   void* ptrs[] = {c->U, c->dU, c->io, c->io2, c->Ja, c->invJ, c->fgeo, c->nbr, c->elem_face, c->faces,
                   c->ws_elem, c->ws_lag, c->Rv, c->Gf, c->Fs, c->tau, c->status,
                   c->gUf, c->gGf, c->gWf, c->gUs, c->gtheta, c->wq, c->ro_ckpt, c->ro_stage, c->ro_work,
-                  c->ro_scalar, c->wJ, c->W32, c->halo_U, c->send_U, c->halo_G, c->send_G, c->wm_t};
+                  c->ro_scalar, c->wJ, c->W32, c->W64, c->halo_U, c->send_U, c->halo_G, c->send_G, c->wm_t};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -172,6 +175,7 @@ int launch(dg_ctx* c, const double* Uin, int mode, double* Out, double A, double
   }
   a.W32 = c->W32;
   a.w32_valid = (a.fp32 && Uin == c->U && c->w32_of_U) ? 1 : 0;
+  a.W64 = c->W64;
   a.wm_t = c->wm_t;
   int rc = dg::run_operator(a, c->ph, c->stream);
   if (rc != 0) {
@@ -408,6 +412,7 @@ int dg_init_mesh(dg_ctx** out, const dg_mesh_desc* m, const dg_phys* p, const dg
   chk(cudaMalloc(&c->Gf, (o->viscous ? 24 * (size_t)c->K * n2 : 1) * rs));
   chk(cudaMalloc(&c->Fs, (ph.fs_diff ? 10 : 5) * (size_t)c->F * n2 * rs));
   if (f32) chk(alloc(&c->W32, 6 * S));
+  if (!f32 && o->viscous) chk(alloc(&c->W64, 6 * S));
   if (c->geo.n_wall > 0) {
     chk(alloc(&c->wm_t, (size_t)c->geo.n_wall * n2));
     chk(cudaMemset(c->wm_t, 0xff, (size_t)c->geo.n_wall * n2 * sizeof(double)));  // NaN: no guess yet

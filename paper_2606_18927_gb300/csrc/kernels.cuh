@@ -80,6 +80,8 @@ struct MeshDev {
   const int* ws_elem;    // [n_wall*n2]
   const double* ws_lag;  // [n_wall*n2*3*n]
   float* W32;            // FP32-mixed form: [6][K*n3] primitives of the input state (null in FP64)
+  double* W64;           // FP64 viscous form: [6][K*n3] primitives (rho, u, v, w, p - p_ref, h) of the
+                         // input state, written by k_lift, read by k_face and k_volume (null: formed per use)
   double* wm_t;          // [n_wall*n2] last wall-law solution per wall node (warm start; may be null)
 };
 
@@ -239,6 +241,27 @@ __device__ __forceinline__ Prim<float> primitive<float>(const double U0, const d
 }
 
 // (u, v, w, T) for the lifting, in the flux type (same pressure recovery).
+// FP64 primitives and the temperature T = p / (rho R) (from the unshifted p).
+// Not inlined: one compiled body serves the lifting kernel, which stores its
+// result for the face and volume kernels, and the halo-face kernel, which
+// forms the same values for a remote trace; they then agree bitwise whatever
+// the surrounding code lets the compiler contract.
+static __device__ __noinline__ Prim<double> primitive_T(const double U0, const double U1, const double U2,
+                                                 const double U3, const double U4, const PhysDev& ph, double& T) {
+  Prim<double> q;
+  const double ir = rcp_pos(U0);
+  const double u = U1 * ir, v = U2 * ir, w = U3 * ir;
+  const double p = ph.gm1 * (U4 - 0.5 * (U1 * u + U2 * v + U3 * w));
+  q.rho = U0; q.u = u; q.v = v; q.w = w; q.p = p - ph.p_ref;
+  q.h = (U4 + p) * ir;
+  T = p * ph.rcp_R * ir;
+  return q;
+}
+
+__device__ __forceinline__ Prim<double> load_prim64(const double* __restrict__ W, size_t S, size_t g) {
+  return Prim<double>{W[g], W[S + g], W[2 * S + g], W[3 * S + g], W[4 * S + g], W[5 * S + g]};
+}
+
 template <typename R>
 __device__ __forceinline__ void velocity_temperature(const double U0, const double U1, const double U2,
                                                      const double U3, const double U4, const PhysDev& ph,
@@ -825,10 +848,18 @@ k_lift(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
   // own primitives W = (u, v, w, T)
   {
     R u, v, w, T;
-    if constexpr (std::is_same<R, float>::value)
+    if constexpr (std::is_same<R, float>::value) {
       velocity_temperature32(load_prim32(m.W32, S, g), ph, u, v, w, T);
-    else
+    } else if (m.W64) {
+      // the FP64 primitives of the node, kept for the face and volume kernels
+      double Td;
+      const Prim<double> q = primitive_T(U[g], U[S + g], U[2 * S + g], U[3 * S + g], U[4 * S + g], ph, Td);
+      m.W64[g] = q.rho; m.W64[S + g] = q.u; m.W64[2 * S + g] = q.v; m.W64[3 * S + g] = q.w;
+      m.W64[4 * S + g] = q.p; m.W64[5 * S + g] = q.h;
+      u = q.u; v = q.v; w = q.w; T = Td;
+    } else {
       velocity_temperature<R>(U[g], U[S + g], U[2 * S + g], U[3 * S + g], U[4 * S + g], ph, u, v, w, T);
+    }
     sW[p] = u; sW[n3 + p] = v; sW[2 * n3 + p] = w; sW[3 * n3 + p] = T;
   }
   __syncthreads();
@@ -1016,24 +1047,34 @@ k_lift(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
 }
 
 // ---------------------------------------------------------------------------
-// k_face: one thread per node of an interior face.
+// k_face: one thread per node of an interior face.  In FP64 the halo faces of
+// a partitioned mesh follow the interior faces in the same launch, so that one
+// code path forms the flux of both kinds (and a halo face's flux equals,
+// bitwise, the one a single-domain run forms for the same face).
 // ---------------------------------------------------------------------------
 template <int N, typename R>
 __global__ void __launch_bounds__(256)
 k_face(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const R* __restrict__ Gf,
        R* __restrict__ Fs) {
   constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
+  constexpr bool D = std::is_same<R, double>::value;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-  const int f = tid / n2, ab = tid - f * n2;
-  if (f >= m.n_interior) return;
+  const int f0 = tid / n2, ab = tid - f0 * n2;
+  if (f0 >= m.n_interior + (D ? m.n_halo : 0)) return;
+  const bool is_halo = D && f0 >= m.n_interior;
+  const int f = is_halo ? m.F - m.n_halo + (f0 - m.n_interior) : f0;
   const int4 fc = m.faces[f];
   const size_t S = (size_t)m.K * n3;
-  const size_t gM = (size_t)fc.x * n3 + fnode<N>(fc.y, ab % n, ab / n);
-  const size_t gS = (size_t)fc.z * n3 + fnode<N>(fc.w, ab % n, ab / n);
   const size_t FN = (size_t)m.F * n2, fg = (size_t)f * n2 + ab;
   const R nx = (R)m.fgeo[fg], ny = (R)m.fgeo[FN + fg], nz = (R)m.fgeo[2 * FN + fg], s = (R)m.fgeo[3 * FN + fg];
   R F[5];
-  if constexpr (std::is_same<R, float>::value) {
+  const R* gA;
+  const R* gB;
+  if constexpr (!D) {
+    const size_t gM = (size_t)fc.x * n3 + fnode<N>(fc.y, ab % n, ab / n);
+    const size_t gS = (size_t)fc.z * n3 + fnode<N>(fc.w, ab % n, ab / n);
+    gA = Gf + ((size_t)fc.x * 6 + fc.y) * 4 * n2 + ab;
+    gB = Gf + ((size_t)fc.z * 6 + fc.w) * 4 * n2 + ab;
     const Prim<float> A = load_prim32(m.W32, S, gM), B = load_prim32(m.W32, S, gS);
     // U_B - U_A for the Lax-Friedrichs dissipation, differenced in FP64 (from
     // rounded FP32 states the difference would carry an error of eps |U|)
@@ -1043,25 +1084,62 @@ k_face(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
       for (int v = 0; v < 5; ++v) dU[v] = (float)(U[v * S + gS] - U[v * S + gM]);
     }
     if (ph.fs_diff) {
-      const R* gA = Gf + ((size_t)fc.x * 6 + fc.y) * 4 * n2 + ab;
-      const R* gB = Gf + ((size_t)fc.z * 6 + fc.w) * 4 * n2 + ab;
       store_face_delta(ph, A, B, dU, nx, ny, nz, s, gA, gB, R(0.5), Fs + (size_t)f * 10 * n2 + ab, n2, true);
       return;
     }
     riemann_d<float>(ph, A, B, dU, nx, ny, nz, F);
   } else {
-    double UA[5], UB[5];
+    // both sides' FP64 primitives: from the lifting kernel's array where it
+    // ran, else (and for a remote trace) by primitive_T, whose one compiled
+    // body also wrote that array
+    Prim<double> A, B;
+    double dU[5] = {0.0, 0.0, 0.0, 0.0, 0.0}, T;
+    const bool llf = ph.surf_flux == 1;
+    if (!is_halo) {
+      const size_t gM = (size_t)fc.x * n3 + fnode<N>(fc.y, ab % n, ab / n);
+      const size_t gS = (size_t)fc.z * n3 + fnode<N>(fc.w, ab % n, ab / n);
+      gA = Gf + ((size_t)fc.x * 6 + fc.y) * 4 * n2 + ab;
+      gB = Gf + ((size_t)fc.z * 6 + fc.w) * 4 * n2 + ab;
+      if (m.W64) {
+        A = load_prim64(m.W64, S, gM);
+        B = load_prim64(m.W64, S, gS);
+      } else {
+        A = primitive_T(U[gM], U[S + gM], U[2 * S + gM], U[3 * S + gM], U[4 * S + gM], ph, T);
+        B = primitive_T(U[gS], U[S + gS], U[2 * S + gS], U[3 * S + gS], U[4 * S + gS], ph, T);
+      }
+      if (llf) {
 #pragma unroll
-    for (int v = 0; v < 5; ++v) { UA[v] = U[v * S + gM]; UB[v] = U[v * S + gS]; }
-    const Prim<R> A = primitive<R>(UA[0], UA[1], UA[2], UA[3], UA[4], ph);
-    const Prim<R> B = primitive<R>(UB[0], UB[1], UB[2], UB[3], UB[4], ph);
-    riemann<R, double>(ph, A, UA, B, UB, nx, ny, nz, F);
+        for (int v = 0; v < 5; ++v) dU[v] = U[v * S + gS] - U[v * S + gM];
+      }
+    } else {
+      // fc = (local element, local face, halo index, local side is master)
+      const int h = f0 - m.n_interior;
+      const size_t gL = (size_t)fc.x * n3 + fnode<N>(fc.y, ab % n, ab / n);
+      const double* rU = m.halo_U + (size_t)h * 5 * n2 + ab;
+      const bool master = fc.w != 0;
+      const Prim<double> loc =
+          m.W64 ? load_prim64(m.W64, S, gL)
+                : primitive_T(U[gL], U[S + gL], U[2 * S + gL], U[3 * S + gL], U[4 * S + gL], ph, T);
+      const Prim<double> rem = primitive_T(rU[0], rU[n2], rU[2 * n2], rU[3 * n2], rU[4 * n2], ph, T);
+      A = master ? loc : rem;
+      B = master ? rem : loc;
+      const R* gl = Gf + ((size_t)fc.x * 6 + fc.y) * 4 * n2 + ab;
+      const R* gr = m.halo_G + (size_t)h * 4 * n2 + ab;
+      gA = master ? gl : gr;
+      gB = master ? gr : gl;
+      if (llf) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) {
+          const double d = rU[v * n2] - U[v * S + gL];
+          dU[v] = master ? d : -d;
+        }
+      }
+    }
+    riemann_d<double>(ph, A, B, dU, nx, ny, nz, F);
   }
   R* out = Fs + (size_t)f * 5 * n2 + ab;
   out[0] = F[0] * s;
   if (ph.viscous) {
-    const R* gA = Gf + ((size_t)fc.x * 6 + fc.y) * 4 * n2 + ab;
-    const R* gB = Gf + ((size_t)fc.z * 6 + fc.w) * 4 * n2 + ab;
 #pragma unroll
     for (int v = 0; v < 4; ++v) out[(v + 1) * n2] = F[v + 1] * s - R(0.5) * (gA[v * n2] - gB[v * n2]);
   } else {
@@ -1071,9 +1149,9 @@ k_face(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
 }
 
 // ---------------------------------------------------------------------------
-// Halo faces of a partitioned mesh.  Both ranks of a shared face evaluate its
-// flux from the same master and slave traces (one side from the halo buffer)
-// with the master's normal, so both get the value a single-domain run gets.
+// Halo faces of a partitioned mesh, FP32-mixed form (FP64: in k_face).  Both
+// ranks of a shared face evaluate its flux from the same master and slave
+// traces (one side from the halo buffer) with the master's normal.
 // ---------------------------------------------------------------------------
 template <int N, typename R>
 __global__ void __launch_bounds__(256)
@@ -1098,8 +1176,21 @@ k_halo_face(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, 
   }
   const size_t FN = (size_t)m.F * n2, fg = (size_t)f * n2 + ab;
   const R nx = (R)m.fgeo[fg], ny = (R)m.fgeo[FN + fg], nz = (R)m.fgeo[2 * FN + fg], s = (R)m.fgeo[3 * FN + fg];
-  const Prim<R> A = primitive<R>(UA[0], UA[1], UA[2], UA[3], UA[4], ph);
-  const Prim<R> B = primitive<R>(UB[0], UB[1], UB[2], UB[3], UB[4], ph);
+  Prim<R> A, B;
+  if constexpr (std::is_same<R, double>::value) {
+    if (m.W64) {
+      // the values k_face takes from the lifting kernel's array (on both ranks)
+      double T;
+      A = primitive_T(UA[0], UA[1], UA[2], UA[3], UA[4], ph, T);
+      B = primitive_T(UB[0], UB[1], UB[2], UB[3], UB[4], ph, T);
+    } else {
+      A = primitive<R>(UA[0], UA[1], UA[2], UA[3], UA[4], ph);
+      B = primitive<R>(UB[0], UB[1], UB[2], UB[3], UB[4], ph);
+    }
+  } else {
+    A = primitive<R>(UA[0], UA[1], UA[2], UA[3], UA[4], ph);
+    B = primitive<R>(UB[0], UB[1], UB[2], UB[3], UB[4], ph);
+  }
   if constexpr (std::is_same<R, float>::value) {
     if (ph.fs_diff) {
       float dU[5];
@@ -1419,10 +1510,10 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
     Prim<R> q;
     if constexpr (F32) {
       q = load_prim32(m.W32, S, g);
+    } else if (m.W64) {
+      q = load_prim64(m.W64, S, g);
     } else {
-#pragma unroll
-      for (int v = 0; v < 5; ++v) Uo[v] = Uin[v * S + g];
-      q = primitive<R>(Uo[0], Uo[1], Uo[2], Uo[3], Uo[4], ph);
+      q = primitive<R>(Uin[g], Uin[S + g], Uin[2 * S + g], Uin[3 * S + g], Uin[4 * S + g], ph);
     }
     sQ[t] = q.rho; sQ[n3 + t] = q.u; sQ[2 * n3 + t] = q.v; sQ[3 * n3 + t] = q.w;
     sQ[4 * n3 + t] = dif ? q.p : R(4) * q.p;
@@ -1631,10 +1722,10 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
   // epilogue: node t
   const int i = t % n, j = (t / n) % n, k = t / n2;
   const size_t g = (size_t)e * n3 + t;
-  if constexpr (F32) {
+  // the element's own state, for the register update (read again here rather
+  // than kept in registers through the passes)
 #pragma unroll
-    for (int v = 0; v < 5; ++v) Uo[v] = Uin[v * S + g];
-  }
+  for (int v = 0; v < 5; ++v) Uo[v] = Uin[v * S + g];
   R acc[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) acc[v] = sR[v * n3 + t];

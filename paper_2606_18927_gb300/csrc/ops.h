@@ -43,6 +43,9 @@ struct OpArgs {
   // (mode 1) leaves the primitives of Uout in W32.
   float* W32;
   int w32_valid;
+  // FP64 viscous form: [6][K n^3] primitives of Uin, written by the lifting
+  // kernel for the face and volume kernels (null: each kernel forms its own)
+  double* W64;
   double* wm_t;  // wall-law warm-start values per wall node (null: cold solves)
   // partitioned meshes: n_halo halo faces (the last faces), remote traces in
   // halo_U / halo_G, local traces packed into send_U / send_G.  phase selects

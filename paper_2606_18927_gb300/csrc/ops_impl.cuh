@@ -37,6 +37,8 @@ static int run_typed(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {
   m.fgeo = a.fgeo; m.nbr = a.nbr; m.elem_face = a.elem_face; m.faces = a.faces;
   m.ws_elem = a.ws_elem; m.ws_lag = a.ws_lag;
   m.W32 = std::is_same<R, float>::value ? a.W32 : nullptr;
+  // written by the lifting kernel, so only when it runs
+  m.W64 = std::is_same<R, double>::value && ph.viscous ? a.W64 : nullptr;
   m.wm_t = a.wm_t;
   m.n_halo = a.n_halo; m.halo_U = a.halo_U; m.halo_G = static_cast<const R*>(a.halo_G);
   const Tables<N> tab = make_tables<N>(a.D, a.w);
@@ -92,17 +94,19 @@ static int run_typed(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {
       k_halo_pack<N, R><<<halo_blocks, 256, 0, s>>>(a.Uin, m, Gf, nullptr, static_cast<R*>(a.send_G));
   }
   if (!(phase & 4)) return (int)cudaGetLastError();
-  if (a.n_interior > 0) {
+  // FP64: k_face also takes the halo faces (after the interior ones)
+  constexpr bool halo_in_face = std::is_same<R, double>::value;
+  const long long face_work = (long long)(a.n_interior + (halo_in_face ? a.n_halo : 0)) * n2;
+  if (face_work > 0) {
     const int threads = 256;
-    const long long work = (long long)a.n_interior * n2;
-    k_face<N, R><<<(unsigned)((work + threads - 1) / threads), threads, 0, s>>>(a.Uin, m, ph, Gf, Fs);
+    k_face<N, R><<<(unsigned)((face_work + threads - 1) / threads), threads, 0, s>>>(a.Uin, m, ph, Gf, Fs);
   }
   if (a.n_bc > 0) {
     const int threads = 256;
     const long long work = (long long)a.n_bc * n2;
     k_bc<N, R><<<(unsigned)((work + threads - 1) / threads), threads, 0, s>>>(a.Uin, m, ph, Gf, Fs);
   }
-  if (a.n_halo > 0) k_halo_face<N, R><<<halo_blocks, 256, 0, s>>>(a.Uin, m, ph, Gf, Fs);
+  if (!halo_in_face && a.n_halo > 0) k_halo_face<N, R><<<halo_blocks, 256, 0, s>>>(a.Uin, m, ph, Gf, Fs);
   if (a.ev) cudaEventRecord(a.ev[2], s);
   if (fork) {
     cudaStreamWaitEvent(s, a.join, 0);
