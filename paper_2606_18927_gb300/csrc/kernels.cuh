@@ -1719,16 +1719,27 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
     }
   }
   if (t >= n3) return;
-  // epilogue: node t
-  const int i = t % n, j = (t / n) % n, k = t / n2;
-  const size_t g = (size_t)e * n3 + t;
+  // epilogue: one node per thread.  At N = 7 the two warps of a zeta layer
+  // hold the eta rows {0, N, 1, 2} and {3, 4, 5, 6}, so that only the first
+  // runs the (masked) eta-face branch of the surface integral
+  int i, j, k;
+  if constexpr (n == 8 && T == n3) {
+    const int w = t >> 5, r = (t >> 3) & 3;
+    i = t & 7;
+    k = w >> 1;
+    j = (w & 1) ? 3 + r : (r == 0 ? 0 : (r == 1 ? N : r - 1));
+  } else {
+    i = t % n; j = (t / n) % n; k = t / n2;
+  }
+  const int nd = i + n * (j + n * k);
+  const size_t g = (size_t)e * n3 + nd;
   // the element's own state, for the register update (read again here rather
   // than kept in registers through the passes)
 #pragma unroll
   for (int v = 0; v < 5; ++v) Uo[v] = Uin[v * S + g];
   R acc[5];
 #pragma unroll
-  for (int v = 0; v < 5; ++v) acc[v] = sR[v * n3 + t];
+  for (int v = 0; v < 5; ++v) acc[v] = sR[v * n3 + nd];
   if (ph.viscous) {
 #pragma unroll
     for (int v = 0; v < 4; ++v) acc[v + 1] += Rv[(size_t)v * S + g];
