@@ -38,8 +38,8 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) of one launch of the dominant kernel, from an ncu
 # capture of the same kernel build on a 16^3-element case, scaled to the
 # launch size by the DOF count (traffic is proportional to the DOF count).
-NCU_TRAFFIC_PER_DOF = {("k_volume", "fp64", 7): 488.6e6 / 2097152,
-                       ("k_volume", "fp32", 7): 450.3e6 / 2097152}
+NCU_TRAFFIC_PER_DOF = {("k_volume", "fp64", 7): 593.2e6 / 2097152,
+                       ("k_volume", "fp32", 7): 452.1e6 / 2097152}
 # algorithmic HBM bytes per DOF of the FP32-mixed volume kernel (stage form):
 # U read 40 and written 40, dU read and written 80, FP32 primitives read 24 and
 # written 24, Ja + 1/J 40, R_v 16, surface fluxes 3 n^2 / n^3 x 5 x 4 B x 2 sides
@@ -62,7 +62,13 @@ def algorithmic_flops_per_dof(N, kernel, viscous=True, surf="roe"):
     if kernel == "lift":
         if not viscous:
             return 0.0
-        return 13 + (6.0 / n) * 13 + 24 * n + 60 + (6.0 / n) * 24 + 12 + 50 + 60 + 24 * n
+        # 12 line contractions of the gradient and 12 of the weak divergence
+        # per node; with an even node count in their even/odd form (D is
+        # centro-antisymmetric): n/2 FMA, one addition forming the half-sums,
+        # one combining the halves, instead of n FMA; the divergence adds the
+        # three directions (8)
+        contr = 12 * (n + 2) if n % 2 == 0 else 24 * n
+        return 13 + (6.0 / n) * 13 + contr + 60 + (6.0 / n) * 24 + 12 + 50 + 60 + contr + (8 if n % 2 == 0 else 0)
     if kernel == "face":
         per_node = 26 + 25 + (80 if surf == "roe" else 12) + 8 + 10
         return (3.0 / n) * per_node
