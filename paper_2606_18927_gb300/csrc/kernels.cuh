@@ -1444,6 +1444,32 @@ struct StageArgs {
   int write_w32;  // FP32-mixed form: store the updated state's primitives into W32
 };
 
+// Shared-memory slot of a node in the volume kernel's per-node arrays.  A
+// direction pass gives each line of n nodes n consecutive lanes; in natural
+// order the 8 lanes of a zeta line at N = 7 read addresses 64 apart, all in one
+// bank (8-way conflicts), and those of an eta line conflict 2-way.  At N = 7
+// the nodes are swizzled (XOR of index bits) so that the lanes of every
+// direction's loads and of the thread-per-node prologue and epilogue hit
+// distinct banks: 32 four-byte banks per warp for FP32, 16 eight-byte bank
+// pairs per half warp for FP64.
+template <int N, class R>
+__device__ __forceinline__ int vslot(int node) {
+  if constexpr (N != 7) {
+    return node;
+  } else {
+    const int i = node & 7, j = (node >> 3) & 7, k = node >> 6;
+    if constexpr (sizeof(R) == 4) {
+      // bank bits (i0, i1, i2^j2^k2, j0^k0, j1^k1); row (j2, k)
+      const int bank = (i & 3) | ((((i ^ j ^ k) >> 2) & 1) << 2) | (((j ^ k) & 3) << 3);
+      return (((j >> 2) | (k << 1)) << 5) | bank;
+    } else {
+      // bank-pair bits (i0, i1^j1^k1, i2^j2^k2, j0^k0); row (j1, j2, k)
+      const int bank = (i & 1) | ((i ^ j ^ k) & 6) | (((j ^ k) & 1) << 3);
+      return ((((j >> 1) & 3) | (k << 2)) << 4) | bank;
+    }
+  }
+}
+
 // the values of one node that the two-point flux of a direction reads
 template <class R>
 struct VolNode {
@@ -1515,26 +1541,27 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
     } else {
       q = primitive<R>(Uin[g], Uin[S + g], Uin[2 * S + g], Uin[3 * S + g], Uin[4 * S + g], ph);
     }
-    sQ[t] = q.rho; sQ[n3 + t] = q.u; sQ[2 * n3 + t] = q.v; sQ[3 * n3 + t] = q.w;
-    sQ[4 * n3 + t] = dif ? q.p : R(4) * q.p;
+    const int ts = vslot<N, R>(t);
+    sQ[ts] = q.rho; sQ[n3 + ts] = q.u; sQ[2 * n3 + ts] = q.v; sQ[3 * n3 + ts] = q.w;
+    sQ[4 * n3 + ts] = dif ? q.p : R(4) * q.p;
     if constexpr (EC) {
       const R pf = q.p + cR<R>(ph.p_ref, ph.f32c.p_ref);
       const R beta = R(0.5) * q.rho * rcp_t<R>(pf);
       const R irho = rcp_t<R>(q.rho);
-      sQ[4 * n3 + t] = R(8) * beta * q.p;
-      sQ[5 * n3 + t] = beta;
-      sQ[6 * n3 + t] = q.u * q.u + q.v * q.v + q.w * q.w;
-      sQ[7 * n3 + t] = R(2) * pf * irho;  // 1 / beta
-      sQ[8 * n3 + t] = irho;
+      sQ[4 * n3 + ts] = R(8) * beta * q.p;
+      sQ[5 * n3 + ts] = beta;
+      sQ[6 * n3 + ts] = q.u * q.u + q.v * q.v + q.w * q.w;
+      sQ[7 * n3 + ts] = R(2) * pf * irho;  // 1 / beta
+      sQ[8 * n3 + ts] = irho;
     } else if (!kg) {
-      sQ[5 * n3 + t] = q.h;
+      sQ[5 * n3 + ts] = q.h;
     } else {
       const R pf = q.p + cR<R>(ph.p_ref, ph.f32c.p_ref);
-      sQ[5 * n3 + t] = q.h - pf / q.rho;  // e = E / rho
-      sQ[6 * n3 + t] = R(2) * pf;
+      sQ[5 * n3 + ts] = q.h - pf / q.rho;  // e = E / rho
+      sQ[6 * n3 + ts] = R(2) * pf;
     }
 #pragma unroll
-    for (int c = 0; c < 9; ++c) sA[c * n3 + t] = m.Ja[(size_t)c * S + g];
+    for (int c = 0; c < 9; ++c) sA[c * n3 + ts] = m.Ja[(size_t)c * S + g];
   }
   __syncthreads();
   // three direction passes over the lines
@@ -1551,7 +1578,8 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
     auto node_at = [&](int dir, int q) {
       return dir == 0 ? q + n * L : (dir == 1 ? la + n * q + n2 * lb : L + n2 * q);
     };
-    auto load_node = [&](int node, int dir) {
+    auto load_node = [&](int nd, int dir) {
+      const int node = vslot<N, R>(nd);
       VolNode<R> X;
       X.rho = sQ[node]; X.u = sQ[n3 + node]; X.v = sQ[2 * n3 + node]; X.w = sQ[3 * n3 + node];
       X.p4 = sQ[4 * n3 + node]; X.hh = sQ[5 * n3 + node];
@@ -1639,9 +1667,10 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
         if constexpr (std::is_same<R, float>::value && !EC) {
           if (dif) {
             const NodeF mi{A.rho, A.u, A.v, A.w, A.p4, A.hh};
-            const NodeF mq{sQ[q], sQ[n3 + q], sQ[2 * n3 + q], sQ[3 * n3 + q], sQ[4 * n3 + q], sQ[5 * n3 + q]};
-            const float aq0 = sA[(dir * 3 + 0) * n3 + q], aq1 = sA[(dir * 3 + 1) * n3 + q],
-                        aq2 = sA[(dir * 3 + 2) * n3 + q];
+            const int qs = vslot<N, R>(q);
+            const NodeF mq{sQ[qs], sQ[n3 + qs], sQ[2 * n3 + qs], sQ[3 * n3 + qs], sQ[4 * n3 + qs], sQ[5 * n3 + qs]};
+            const float aq0 = sA[(dir * 3 + 0) * n3 + qs], aq1 = sA[(dir * 3 + 1) * n3 + qs],
+                        aq2 = sA[(dir * 3 + 2) * n3 + qs];
             float G[5];
             flux_delta(mi, mq, A.a0, A.a1, A.a2, aq0 - A.a0, aq1 - A.a1, aq2 - A.a2, G);
             const float c1 = sC1[pos * n + pm];
@@ -1707,12 +1736,13 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
         }
       }
       if (active) {
+        const int ms = vslot<N, R>(me);
         if (dir == 0) {
 #pragma unroll
-          for (int v = 0; v < 5; ++v) sR[v * n3 + me] = acc[v];
+          for (int v = 0; v < 5; ++v) sR[v * n3 + ms] = acc[v];
         } else {
 #pragma unroll
-          for (int v = 0; v < 5; ++v) sR[v * n3 + me] += acc[v];
+          for (int v = 0; v < 5; ++v) sR[v * n3 + ms] += acc[v];
         }
       }
       __syncthreads();
@@ -1739,7 +1769,7 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
   for (int v = 0; v < 5; ++v) Uo[v] = Uin[v * S + g];
   R acc[5];
 #pragma unroll
-  for (int v = 0; v < 5; ++v) acc[v] = sR[v * n3 + nd];
+  for (int v = 0; v < 5; ++v) acc[v] = sR[v * n3 + vslot<N, R>(nd)];
   if (ph.viscous) {
 #pragma unroll
     for (int v = 0; v < 4; ++v) acc[v + 1] += Rv[(size_t)v * S + g];
