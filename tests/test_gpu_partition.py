@@ -58,6 +58,19 @@ def test_partitioned_tgv_bitwise(P):
     assert torch.equal(ut, ut_ref)
 
 
+def test_partitioned_tgv_n7_bitwise():
+    # N = 7 runs the even/odd lifting contractions, the once-formed
+    # half-distance pairs and the swizzled shared-memory layout of the volume
+    # kernel; the halo faces take the FP64 primitives the lifting kernel keeps
+    torch = torch_cuda()
+    phys = I.phys_params(Ma=0.1, Re=1600.0)
+    spec = I.BoxSpec(7, 4, 2, 2, geometry="sine", amplitude=0.1)
+    ref, out, ut_ref, ut, nh = _compare(torch, spec, phys, 3, surf_flux=2)
+    assert min(nh) > 0
+    assert torch.equal(out, ref)
+    assert torch.equal(ut, ut_ref)
+
+
 @pytest.mark.parametrize("P", [2, 5])
 def test_partitioned_tgv_mixed(P):
     # the FP32 flux arithmetic of a halo face runs in another kernel than that
