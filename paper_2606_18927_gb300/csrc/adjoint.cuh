@@ -167,6 +167,150 @@ __device__ __forceinline__ void vt_vjp(const double U[5], const PhysDev& ph, con
 }
 
 // ---------------------------------------------------------------------------
+// Reverse mode of the inviscid interface flux F*(U_A, U_B; n) (two-point
+// Pirozzoli flux plus the central / Lax-Friedrichs / Roe-Harten dissipation,
+// as riemann<double> forms it): gUA += (dF*/dU_A)^T gF, gUB += (dF*/dU_B)^T gF.
+// One forward sweep keeps the intermediates, one backward sweep applies the
+// chain rule to them in reverse order (about three flux evaluations, against
+// ten forward-mode dual sweeps).  |x| takes the derivative sign(x) with
+// sign(0) = +1, as the dual numbers do.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double sgn1(double x) { return x < 0.0 ? -1.0 : 1.0; }
+
+static __device__ void face_flux_vjp(const PhysDev& ph, const double UA[5], const double UB[5], double nx,
+                                     double ny, double nz, const double gF[5], double gUA[5], double gUB[5]) {
+  const Prim<double> A = primitive<double>(UA[0], UA[1], UA[2], UA[3], UA[4], ph);
+  const Prim<double> B = primitive<double>(UB[0], UB[1], UB[2], UB[3], UB[4], ph);
+  // cotangents of the primitives (rho, u, v, w, p - p_ref, h) of each side
+  double qA[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, qB[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  {
+    // two-point flux: m = {rho} ({u}.n); F = (m, m {u} + {p} n, m {h})
+    const double rho = 0.5 * (A.rho + B.rho), u = 0.5 * (A.u + B.u), v = 0.5 * (A.v + B.v), w = 0.5 * (A.w + B.w);
+    const double hb = 0.5 * (A.h + B.h);
+    const double un = u * nx + v * ny + w * nz, m = rho * un;
+    const double gm = gF[0] + gF[1] * u + gF[2] * v + gF[3] * w + gF[4] * hb;
+    const double gun = gm * rho;
+    const double g[6] = {gm * un, gF[1] * m + gun * nx, gF[2] * m + gun * ny, gF[3] * m + gun * nz,
+                         gF[1] * nx + gF[2] * ny + gF[3] * nz, gF[4] * m};
+#pragma unroll
+    for (int x = 0; x < 6; ++x) { qA[x] += 0.5 * g[x]; qB[x] += 0.5 * g[x]; }
+  }
+  if (ph.surf_flux == 1) {
+    // F -= lam (U_B - U_A), lam = max(|u_n| + c) / 2 over the sides
+    const double pref = ph.p_ref, gam = ph.gamma;
+    const double cA = ::sqrt(gam * (A.p + pref) / A.rho), cB = ::sqrt(gam * (B.p + pref) / B.rho);
+    const double unA = A.u * nx + A.v * ny + A.w * nz, unB = B.u * nx + B.v * ny + B.w * nz;
+    const double lA = ::fabs(unA) + cA, lB = ::fabs(unB) + cB;
+    const double lam = 0.5 * (lA >= lB ? lA : lB);
+    double glam = 0.0;
+#pragma unroll
+    for (int x = 0; x < 5; ++x) {
+      glam -= gF[x] * (UB[x] - UA[x]);
+      gUA[x] += lam * gF[x];
+      gUB[x] -= lam * gF[x];
+    }
+    const bool a_side = lA >= lB;
+    double* q = a_side ? qA : qB;
+    const double un = a_side ? unA : unB, c = a_side ? cA : cB;
+    const Prim<double>& X = a_side ? A : B;
+    const double gl = 0.5 * glam, gn = gl * sgn1(un);
+    q[1] += gn * nx; q[2] += gn * ny; q[3] += gn * nz;
+    // c = sqrt(gamma (p + p_ref) / rho)
+    q[4] += gl * gam / (2.0 * c * X.rho);
+    q[0] -= gl * c / (2.0 * X.rho);
+  } else if (ph.surf_flux == 2) {
+    // forward sweep of the Roe dissipation with Harten's fix (F -= D / 2)
+    const double gam = ph.gamma;
+    const double sA = ::sqrt(A.rho), sB = ::sqrt(B.rho);
+    const double is = 1.0 / (sA + sB);
+    const double rt = sA * sB;
+    const double Nu = sA * A.u + sB * B.u, Nv = sA * A.v + sB * B.v, Nw = sA * A.w + sB * B.w;
+    const double NH = sA * A.h + sB * B.h;
+    const double u = Nu * is, v = Nv * is, w = Nw * is, H = NH * is;
+    const double q2 = u * u + v * v + w * w;
+    const double c2 = (gam - 1.0) * (H - 0.5 * q2);
+    const double c = ::sqrt(c2);
+    const double un = u * nx + v * ny + w * nz;
+    const double dr = B.rho - A.rho, dp = B.p - A.p;
+    const double du = B.u - A.u, dv = B.v - A.v, dw = B.w - A.w;
+    const double dun = du * nx + dv * ny + dw * nz;
+    const double i2c2 = 0.5 / c2;
+    const double P1 = dp - rt * c * dun, P5 = dp + rt * c * dun;
+    const double a1 = P1 * i2c2, a2 = dr - dp / c2, a5 = P5 * i2c2;
+    const double l1o = ::fabs(un - c), l2 = ::fabs(un), l5o = ::fabs(un + c);
+    const double del = 0.1 * c;
+    const bool h1 = l1o < del, h5 = l5o < del;
+    const double l1 = h1 ? (l1o * l1o + del * del) / (2.0 * del) : l1o;
+    const double l5 = h5 ? (l5o * l5o + del * del) / (2.0 * del) : l5o;
+    const double w1 = l1 * a1, w2 = l2 * a2, w5 = l5 * a5, ws = l2 * rt;
+    const double dut = du - dun * nx, dvt = dv - dun * ny, dwt = dw - dun * nz;
+    const double X4 = u * du + v * dv + w * dw - un * dun;
+    // backward sweep
+    const double g0 = -0.5 * gF[0], g1 = -0.5 * gF[1], g2 = -0.5 * gF[2], g3 = -0.5 * gF[3], g4 = -0.5 * gF[4];
+    const double g13 = g1 * nx + g2 * ny + g3 * nz;  // sum_d gD_d n_d
+    double gw1 = g0 + g1 * (u - c * nx) + g2 * (v - c * ny) + g3 * (w - c * nz) + g4 * (H - c * un);
+    double gw2 = g0 + g1 * u + g2 * v + g3 * w + g4 * (0.5 * q2);
+    double gw5 = g0 + g1 * (u + c * nx) + g2 * (v + c * ny) + g3 * (w + c * nz) + g4 * (H + c * un);
+    const double gws = g1 * dut + g2 * dvt + g3 * dwt + g4 * X4;
+    const double wsum = w1 + w2 + w5;
+    double gu = g1 * wsum + g4 * ws * du, gv = g2 * wsum + g4 * ws * dv, gw = g3 * wsum + g4 * ws * dw;
+    double gc = g13 * (w5 - w1) + g4 * un * (w5 - w1);
+    double gun = g4 * c * (w5 - w1) - g4 * ws * dun;
+    double gH = g4 * (w1 + w5);
+    double gq2 = g4 * 0.5 * w2;
+    double gdu = g1 * ws + g4 * ws * u, gdv = g2 * ws + g4 * ws * v, gdw = g3 * ws + g4 * ws * w;
+    double gdun = -ws * g13 - g4 * ws * un;
+    // ws = l2 rt; w_k = l_k a_k
+    double gl2 = gws * rt + gw2 * a2, grt = gws * l2;
+    double gl1 = gw1 * a1, gl5 = gw5 * a5;
+    const double ga1 = gw1 * l1, ga2 = gw2 * l2, ga5 = gw5 * l5;
+    // Harten: l = (l_o^2 + del^2) / (2 del) below del
+    double gdel = 0.0;
+    if (h1) { gdel += gl1 * (0.5 - l1o * l1o / (2.0 * del * del)); gl1 *= l1o / del; }
+    if (h5) { gdel += gl5 * (0.5 - l5o * l5o / (2.0 * del * del)); gl5 *= l5o / del; }
+    gc += 0.1 * gdel;
+    // l1 = |un - c|, l2 = |un|, l5 = |un + c|
+    const double s1 = sgn1(un - c), s5 = sgn1(un + c);
+    gun += gl1 * s1 + gl2 * sgn1(un) + gl5 * s5;
+    gc += -gl1 * s1 + gl5 * s5;
+    // a1 = P1 i2c2, a5 = P5 i2c2, a2 = dr - dp / c2
+    double gdp = (ga1 + ga5) * i2c2 - ga2 / c2;
+    const double gdr = ga2;
+    const double gP = (ga5 - ga1) * i2c2;  // d/d(rt c dun) of P5 and -P1
+    grt += gP * c * dun;
+    gc += gP * rt * dun;
+    gdun += gP * rt * c;
+    const double gi2c2 = ga1 * P1 + ga5 * P5;
+    double gc2 = ga2 * dp / (c2 * c2) - gi2c2 * 0.5 / (c2 * c2);
+    // dun, un
+    gdu += gdun * nx; gdv += gdun * ny; gdw += gdun * nz;
+    gu += gun * nx; gv += gun * ny; gw += gun * nz;
+    // c = sqrt(c2), c2 = (gamma - 1)(H - q2 / 2), q2 = |u|^2
+    gc2 += gc / (2.0 * c);
+    gH += gc2 * (gam - 1.0);
+    gq2 -= 0.5 * (gam - 1.0) * gc2;
+    gu += 2.0 * u * gq2; gv += 2.0 * v * gq2; gw += 2.0 * w * gq2;
+    // Roe averages x = N_x is, N_x = sA x_A + sB x_B
+    const double gis = gu * Nu + gv * Nv + gw * Nw + gH * NH;
+    double gsA = (gu * A.u + gv * A.v + gw * A.w + gH * A.h) * is + grt * sB - gis * is * is;
+    double gsB = (gu * B.u + gv * B.v + gw * B.w + gH * B.h) * is + grt * sA - gis * is * is;
+    qA[1] += gu * sA * is; qA[2] += gv * sA * is; qA[3] += gw * sA * is; qA[5] += gH * sA * is;
+    qB[1] += gu * sB * is; qB[2] += gv * sB * is; qB[3] += gw * sB * is; qB[5] += gH * sB * is;
+    // jumps
+    qB[0] += gdr; qA[0] -= gdr;
+    qB[4] += gdp; qA[4] -= gdp;
+    qB[1] += gdu; qA[1] -= gdu;
+    qB[2] += gdv; qA[2] -= gdv;
+    qB[3] += gdw; qA[3] -= gdw;
+    // s = sqrt(rho)
+    qA[0] += gsA / (2.0 * sA);
+    qB[0] += gsB / (2.0 * sB);
+  }
+  prim_vjp(UA, ph, qA, gUA);
+  prim_vjp(UB, ph, qB, gUB);
+}
+
+// ---------------------------------------------------------------------------
 // k_adj_face: one thread per node of an interior face.
 // ---------------------------------------------------------------------------
 template <int N>
@@ -200,27 +344,14 @@ k_adj_face(const double* __restrict__ U, const double* __restrict__ lam, const M
 #pragma unroll
     for (int v = 0; v < 4; ++v) { dM[v * n2] = -0.5 * gFs[v + 1]; dS[v * n2] = 0.5 * gFs[v + 1]; }
   }
-  double g[10];
-#pragma unroll 1
-  for (int k = 0; k < 10; ++k) {
-    DualD A[5], B[5];
+  double gF[5], gA[5] = {0.0, 0.0, 0.0, 0.0, 0.0}, gB[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
 #pragma unroll
-    for (int v = 0; v < 5; ++v) {
-      A[v] = DualD(UA[v], k == v ? 1.0 : 0.0);
-      B[v] = DualD(UB[v], k == v + 5 ? 1.0 : 0.0);
-    }
-    const Prim<DualD> qa = primitive_dual(A, ph), qb = primitive_dual(B, ph);
-    DualD F[5];
-    riemann<DualD, DualD>(ph, qa, A, qb, B, DualD(nx), DualD(ny), DualD(nz), F);
-    double acc = 0.0;
-#pragma unroll
-    for (int v = 0; v < 5; ++v) acc += F[v].d * gFs[v];
-    g[k] = acc * s;
-  }
+  for (int v = 0; v < 5; ++v) gF[v] = gFs[v] * s;
+  face_flux_vjp(ph, UA, UB, nx, ny, nz, gF, gA, gB);
   double* oM = gUf + ((size_t)fc.x * 6 + fc.y) * 5 * n2 + ab;
   double* oS = gUf + ((size_t)fc.z * 6 + fc.w) * 5 * n2 + ab;
 #pragma unroll
-  for (int v = 0; v < 5; ++v) { oM[v * n2] = g[v]; oS[v * n2] = g[v + 5]; }
+  for (int v = 0; v < 5; ++v) { oM[v * n2] = gA[v]; oS[v * n2] = gB[v]; }
 }
 
 // ---------------------------------------------------------------------------
@@ -255,23 +386,19 @@ k_adj_wall(const double* __restrict__ U, const double* __restrict__ lam, const M
 #pragma unroll
       for (int v = 0; v < 4; ++v) dM[v * n2] = 0.0;
     }
-    // inviscid flux through the mirror state
-    double g[5];
-#pragma unroll 1
-    for (int k = 0; k < 5; ++k) {
-      DualD A[5], B[5];
+    // inviscid flux through the mirror state U_B = (rho, m - 2 (m.n) n, E):
+    // gU = gA + (dU_B/dU)^T gB
+    double g[5] = {0.0, 0.0, 0.0, 0.0, 0.0}, gB[5] = {0.0, 0.0, 0.0, 0.0, 0.0}, gF[5], UB[5];
+    {
+      const double mn = UA[1] * nx + UA[2] * ny + UA[3] * nz;
+      UB[0] = UA[0]; UB[1] = UA[1] - 2.0 * mn * nx; UB[2] = UA[2] - 2.0 * mn * ny; UB[3] = UA[3] - 2.0 * mn * nz;
+      UB[4] = UA[4];
 #pragma unroll
-      for (int v = 0; v < 5; ++v) A[v] = DualD(UA[v], k == v ? 1.0 : 0.0);
-      const DualD mn = A[1] * nx + A[2] * ny + A[3] * nz;
-      B[0] = A[0]; B[1] = A[1] - 2.0 * mn * nx; B[2] = A[2] - 2.0 * mn * ny; B[3] = A[3] - 2.0 * mn * nz;
-      B[4] = A[4];
-      const Prim<DualD> qa = primitive_dual(A, ph), qb = primitive_dual(B, ph);
-      DualD F[5];
-      riemann<DualD, DualD>(ph, qa, A, qb, B, DualD(nx), DualD(ny), DualD(nz), F);
-      double acc = 0.0;
-#pragma unroll
-      for (int v = 0; v < 5; ++v) acc += F[v].d * gFs[v];
-      g[k] = acc * s;
+      for (int v = 0; v < 5; ++v) gF[v] = gFs[v] * s;
+      face_flux_vjp(ph, UA, UB, nx, ny, nz, gF, g, gB);
+      const double gbn = gB[1] * nx + gB[2] * ny + gB[3] * nz;
+      g[0] += gB[0]; g[4] += gB[4];
+      g[1] += gB[1] - 2.0 * gbn * nx; g[2] += gB[2] - 2.0 * gbn * ny; g[3] += gB[3] - 2.0 * gbn * nz;
     }
     double* oM = gUf + ((size_t)fc.x * 6 + fc.y) * 5 * n2 + ab;
 #pragma unroll

@@ -30,6 +30,11 @@ def case(ora, spec, phys, surf_flux=1, vol_flux=0, viscous=1, law=1, precision=0
         U = I.perturb(I.taylor_green(X, phys), rel=rel)
     elif ic == "tgv_shift":
         U = I.perturb(tgv_with_offset(X, phys), rel=rel)
+    elif ic == "tgv_sonic":
+        # mean flow at the speed of sound along x: |u_n - c| < c / 10 on part
+        # of the xi faces, where Harten's entropy fix replaces |u_n - c|
+        c0 = np.sqrt(phys["gamma"] * phys["p0"])
+        U = I.perturb(tgv_with_offset(X, phys, offset=(c0, 0.4, 0.3)), rel=rel)
     elif ic == "channel":
         U = I.channel_profile(X, phys)
     else:

@@ -32,6 +32,8 @@ CASES = [
     ("tgv_n3_llf", I.BoxSpec(3, 3, 2, 2), 1, 1, "tgv_shift"),
     ("sine_n4_roe", I.BoxSpec(4, 2, 2, 3, geometry="sine", amplitude=0.2), 2, 1, "tgv_shift"),
     ("sine_n5_central_euler", I.BoxSpec(5, 2, 2, 2, geometry="sine", amplitude=0.2), 0, 0, "tgv_shift"),
+    ("sine_n4_roe_sonic", I.BoxSpec(4, 3, 2, 2, geometry="sine", amplitude=0.2), 2, 1, "tgv_sonic"),
+    ("tgv_n3_llf_sonic", I.BoxSpec(3, 3, 2, 2), 1, 1, "tgv_sonic"),
 ]
 
 
@@ -39,7 +41,7 @@ CASES = [
 def test_dot_product_against_oracle_jvp(ora, label, spec, surf, visc, ic):
     torch = torch_cuda()
     phys = I.phys_params(Ma=0.3, Re=200.0)
-    o, g, X, U = case(ora, spec, phys, surf_flux=surf, viscous=visc, rel=1e-2)
+    o, g, X, U = case(ora, spec, phys, surf_flux=surf, viscous=visc, rel=1e-2, ic=ic)
     lam = I.random_direction(U.shape, seed=3)
     gU, _ = _vjp(torch, g, U, lam)
     for seed in (4, 5):
