@@ -127,6 +127,14 @@ typedef struct {
                            (Crocco-Busemann in the Van Driest transform, wall heat
                            flux q_w = -(cp/Pr) tau_w (T_aw - T_w) / u_s into the
                            energy equation); <= 0: adiabatic walls */
+  double rho_ref;       /* FP32-mixed form only (>= 0; 0 disables): its FP32
+                           primitives hold rho - rho_ref and h - h_ref,
+                           h_ref = gamma p_ref / ((gamma - 1) rho_ref), formed
+                           from the FP64 state, so that the differences of
+                           neighbouring nodes in its flux-difference form carry
+                           the FP32 rounding of the deviations from the reference
+                           state instead of that of the values (the reference
+                           density of the flow, e.g. 1 in units of rho0) */
 } dg_phys;
 
 typedef struct {

@@ -339,6 +339,7 @@ int dg_init_mesh(dg_ctx** out, const dg_mesh_desc* m, const dg_phys* p, const dg
   if (p->suth_S > 0.0 && !(p->T_ref > 0.0))
     return fail(nullptr, DG_ERR_ARG, "dg_init_mesh: Sutherland's law needs T_ref > 0");
   if (o->surf_flux < 0 || o->surf_flux > 2) return fail(nullptr, DG_ERR_ARG, "dg_init_mesh: bad surf_flux");
+  if (!(p->rho_ref >= 0.0)) return fail(nullptr, DG_ERR_ARG, "dg_init_mesh: rho_ref must be >= 0");
   if (p->law < 0 || p->law > 1) return fail(nullptr, DG_ERR_ARG, "dg_init_mesh: bad wall law");
   if (!(p->gamma > 1.0) || !(p->R > 0.0) || !(p->mu >= 0.0) || !(p->Pr > 0.0))
     return fail(nullptr, DG_ERR_ARG, "dg_init_mesh: bad gas constants");
@@ -376,6 +377,8 @@ int dg_init_mesh(dg_ctx** out, const dg_mesh_desc* m, const dg_phys* p, const dg
   ph.suth_S = p->suth_S > 0.0 ? p->suth_S : 0.0;
   ph.suth_C = ph.suth_S > 0.0 ? p->mu * (p->T_ref + p->suth_S) / (p->T_ref * std::sqrt(p->T_ref)) : 0.0;
   ph.p_ref = p->p_ref;
+  ph.rho_ref = p->rho_ref;
+  ph.h_ref = p->rho_ref > 0.0 ? p->gamma / (p->gamma - 1.0) * p->p_ref / p->rho_ref : 0.0;
   for (int d = 0; d < 3; ++d) ph.f[d] = p->force[d];
   ph.kappa = p->kappa; ph.B = p->B; ph.hwm = p->hwm; ph.law = p->law;
   ph.vol_flux = o->vol_flux; ph.surf_flux = o->surf_flux; ph.viscous = o->viscous ? 1 : 0;
@@ -388,6 +391,10 @@ int dg_init_mesh(dg_ctx** out, const dg_mesh_desc* m, const dg_phys* p, const dg
   ph.f32c.p_ref = (float)ph.p_ref; ph.f32c.rcp_R = (float)ph.rcp_R; ph.f32c.rgm1 = (float)ph.rgm1;
   ph.f32c.gamma = (float)ph.gamma; ph.f32c.mu = (float)ph.mu; ph.f32c.kcond = (float)ph.kcond;
   ph.f32c.cp_Pr = (float)ph.cp_Pr; ph.f32c.suth_C = (float)ph.suth_C; ph.f32c.suth_S = (float)ph.suth_S;
+  ph.f32c.rho_ref = (float)ph.rho_ref; ph.f32c.h_ref = (float)ph.h_ref;
+  ph.f32c.g_gm1 = (float)(p->gamma / (p->gamma - 1.0));
+  ph.f32c.h_p = p->rho_ref > 0.0 ? 0.0f : (float)p->p_ref;
+  ph.f32c.h_r = p->rho_ref > 0.0 ? (float)(p->p_ref / p->rho_ref) : 0.0f;
   cudaGetDevice(&c->device);
   // device storage
   const size_t S = c->S, n2 = c->n2;

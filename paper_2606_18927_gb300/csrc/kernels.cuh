@@ -38,6 +38,7 @@ struct PhysDev {
   double suth_S;  // Sutherland constant (> 0: mu(T) = suth_C T^(3/2) / (T + S))
   double suth_C;  // mu_ref (T_ref + S) / T_ref^(3/2)
   double p_ref;   // constant removed from p in the momentum fluxes
+  double rho_ref, h_ref;  // FP32-mixed form: reference density and enthalpy removed from its FP32 primitives
   double f[3];
   double kappa, B, hwm;
   int law, vol_flux, surf_flux, viscous;
@@ -48,7 +49,8 @@ struct PhysDev {
   // FP32 copies of the constants the FP32 kernels use (a double-to-float
   // conversion is an FP64-pipe instruction)
   struct {
-    float p_ref, rcp_R, rgm1, gamma, mu, kcond, cp_Pr, suth_C, suth_S;
+    float p_ref, rcp_R, rgm1, gamma, mu, kcond, cp_Pr, suth_C, suth_S, rho_ref, h_ref;
+    float g_gm1, h_p, h_r;  // gamma / (gamma - 1); p_ref (rho_ref = 0) or 0; p_ref / rho_ref or 0
   } f32c;
 };
 
@@ -240,6 +242,34 @@ __device__ __forceinline__ Prim<float> primitive<float>(const double U0, const d
   return q;
 }
 
+// FP32-mixed storage form: (rho - rho_ref, u, v, w, p - p_ref, h - h_ref), the
+// shifted density and pressure formed in FP64 before rounding, so that the
+// difference of two nodes' values carries the rounding of their deviations
+// from the reference state.  The shifted enthalpy follows from those two in
+// FP32 (ideal gas, E = p / (gamma - 1) + rho |u|^2 / 2):
+//   h - h_ref = (gamma / (gamma - 1) (p' - (p_ref / rho_ref) rho') + rho |u|^2 / 2) / rho
+// (rho_ref = 0: h = (gamma / (gamma - 1) (p' + p_ref) + rho |u|^2 / 2) / rho)
+__device__ __forceinline__ Prim<float> prim32_shifted(const double U0, const double U1, const double U2,
+                                                      const double U3, const double U4, const PhysDev& ph) {
+  Prim<float> q;
+  q.rho = (float)(U0 - ph.rho_ref);
+  const float ir = 1.0f / (ph.f32c.rho_ref + q.rho);
+  const float m1 = (float)U1, m2 = (float)U2, m3 = (float)U3;
+  q.u = m1 * ir; q.v = m2 * ir; q.w = m3 * ir;
+  const float ke = 0.5f * (m1 * q.u + m2 * q.v + m3 * q.w);
+  const double pr = fma(ph.gm1, U4 - (double)ke, -ph.p_ref);  // p - p_ref
+  q.p = (float)pr;
+  q.h = fmaf(ph.f32c.g_gm1, q.p + ph.f32c.h_p - ph.f32c.h_r * q.rho, ke) * ir;
+  return q;
+}
+
+// full values from the storage form
+__device__ __forceinline__ Prim<float> unshift32(Prim<float> q, const PhysDev& ph) {
+  q.rho += ph.f32c.rho_ref;
+  q.h += ph.f32c.h_ref;
+  return q;
+}
+
 // (u, v, w, T) for the lifting, in the flux type (same pressure recovery).
 // FP64 primitives and the temperature T = p / (rho R) (from the unshifted p).
 // Not inlined: one compiled body serves the lifting kernel, which stores its
@@ -351,10 +381,12 @@ __device__ __forceinline__ void twopoint(int kind, const Prim<R>& A, const Prim<
 
 // Numerical inviscid flux along the unit normal (nx, ny, nz), side A = master;
 // dU = U_B - U_A (conservative) for the Lax-Friedrichs dissipation.
-// subtracts the dissipation of the selected Riemann solver from F
+// subtracts the dissipation of the selected Riemann solver from F (drho: the
+// density jump B - A when the caller has it more accurately than the values)
 template <typename R>
 __device__ __forceinline__ void riemann_dissipation(const PhysDev& ph, const Prim<R>& A, const Prim<R>& B,
-                                                    const R dU[5], R nx, R ny, R nz, R F[5]) {
+                                                    const R dU[5], R nx, R ny, R nz, R F[5],
+                                                    const R* drho = nullptr) {
   const R pref = cR<R>(ph.p_ref, ph.f32c.p_ref);
   const R g = cR<R>(ph.gamma, ph.f32c.gamma);
   if (ph.surf_flux == 1) {  // local Lax-Friedrichs (sound speed from the full pressure)
@@ -374,7 +406,7 @@ __device__ __forceinline__ void riemann_dissipation(const PhysDev& ph, const Pri
     const R c2 = (g - R(1)) * (H - R(0.5) * q2);
     const R c = sqrt(c2);
     const R un = u * nx + v * ny + w * nz;
-    const R dr = B.rho - A.rho, dp = B.p - A.p;
+    const R dr = drho ? *drho : B.rho - A.rho, dp = B.p - A.p;
     const R du = B.u - A.u, dv = B.v - A.v, dw = B.w - A.w;
     const R dun = du * nx + dv * ny + dw * nz;
     const R i2c2 = R(0.5) / c2;
@@ -421,32 +453,40 @@ struct NodeF {
   float rho, u, v, w, p, h;
 };
 
+// i, m in the storage form of the FP32 primitives (rho, h shifted by
+// rho_ref, h_ref): the differences come from the shifted values, the full
+// density and enthalpy of node i are rebuilt where they multiply
 __device__ __forceinline__ void flux_delta(const NodeF& i, const NodeF& m, float ai0, float ai1, float ai2, float da0,
-                                           float da1, float da2, float G[5]) {
+                                           float da1, float da2, float rho_ref, float h_ref, float G[5]) {
   const float du = m.u - i.u, dv = m.v - i.v, dw = m.w - i.w;
   const float dr = m.rho - i.rho, dp = m.p - i.p, dh = m.h - i.h;
+  const float ri = rho_ref + i.rho;
   const float ab0 = fmaf(0.5f, da0, ai0), ab1 = fmaf(0.5f, da1, ai1), ab2 = fmaf(0.5f, da2, ai2);
   const float uia = i.u * ai0 + i.v * ai1 + i.w * ai2;
   const float dua = 0.5f * (du * ab0 + dv * ab1 + dw * ab2 + i.u * da0 + i.v * da1 + i.w * da2);
-  const float g0 = i.rho * dua + 0.5f * dr * (uia + dua);
-  const float ruia = i.rho * uia;
+  const float g0 = ri * dua + 0.5f * dr * (uia + dua);
+  const float ruia = ri * uia;
   G[0] = g0;
   G[1] = g0 * fmaf(0.5f, du, i.u) + 0.5f * (ruia * du + dp * ab0 + i.p * da0);
   G[2] = g0 * fmaf(0.5f, dv, i.v) + 0.5f * (ruia * dv + dp * ab1 + i.p * da1);
   G[3] = g0 * fmaf(0.5f, dw, i.w) + 0.5f * (ruia * dw + dp * ab2 + i.p * da2);
-  G[4] = g0 * fmaf(0.5f, dh, i.h) + 0.5f * ruia * dh;
+  G[4] = g0 * (h_ref + fmaf(0.5f, dh, i.h)) + 0.5f * ruia * dh;
 }
 
 __device__ __forceinline__ NodeF nodef(const Prim<float>& q) { return NodeF{q.rho, q.u, q.v, q.w, q.p, q.h}; }
 
-// face flux differences for both sides: D_A = F* - F(U_A).n, D_B = F* - F(U_B).n
+// face flux differences for both sides: D_A = F* - F(U_A).n, D_B = F* - F(U_B).n;
+// A, B in the storage form (the dissipation takes the full values and the
+// density jump of the shifted ones)
 __device__ __forceinline__ void face_flux_delta(const PhysDev& ph, const Prim<float>& A, const Prim<float>& B,
                                                 const float dU[5], float nx, float ny, float nz, float DA[5],
                                                 float DB[5]) {
   float Z[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-  riemann_dissipation<float>(ph, A, B, dU, nx, ny, nz, Z);
-  flux_delta(nodef(A), nodef(B), nx, ny, nz, 0.f, 0.f, 0.f, DA);
-  flux_delta(nodef(B), nodef(A), nx, ny, nz, 0.f, 0.f, 0.f, DB);
+  const float drho = B.rho - A.rho;
+  riemann_dissipation<float>(ph, unshift32(A, ph), unshift32(B, ph), dU, nx, ny, nz, Z, &drho);
+  const float rr = ph.f32c.rho_ref, hr = ph.f32c.h_ref;
+  flux_delta(nodef(A), nodef(B), nx, ny, nz, 0.f, 0.f, 0.f, rr, hr, DA);
+  flux_delta(nodef(B), nodef(A), nx, ny, nz, 0.f, 0.f, 0.f, rr, hr, DB);
 #pragma unroll
   for (int v = 0; v < 5; ++v) { DA[v] += Z[v]; DB[v] += Z[v]; }
 }
@@ -491,15 +531,22 @@ __device__ __forceinline__ void store_prim32(float* __restrict__ W, size_t S, si
   W[g] = q.rho; W[S + g] = q.u; W[2 * S + g] = q.v; W[3 * S + g] = q.w; W[4 * S + g] = q.p; W[5 * S + g] = q.h;
 }
 
+// storage form (rho - rho_ref, u, v, w, p - p_ref, h - h_ref)
 __device__ __forceinline__ Prim<float> load_prim32(const float* __restrict__ W, size_t S, size_t g) {
   Prim<float> q;
   q.rho = W[g]; q.u = W[S + g]; q.v = W[2 * S + g]; q.w = W[3 * S + g]; q.p = W[4 * S + g]; q.h = W[5 * S + g];
   return q;
 }
 
+// full values (rho, u, v, w, p - p_ref, h)
+__device__ __forceinline__ Prim<float> load_prim32_full(const float* __restrict__ W, size_t S, size_t g,
+                                                        const PhysDev& ph) {
+  return unshift32(load_prim32(W, S, g), ph);
+}
+
 static __global__ void k_prim32(long long S, const double* __restrict__ U, const PhysDev ph, float* __restrict__ W) {
   for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < S; x += (long long)gridDim.x * blockDim.x) {
-    const Prim<float> q = primitive<float>(U[x], U[S + x], U[2 * S + x], U[3 * S + x], U[4 * S + x], ph);
+    const Prim<float> q = prim32_shifted(U[x], U[S + x], U[2 * S + x], U[3 * S + x], U[4 * S + x], ph);
     store_prim32(W, (size_t)S, (size_t)x, q);
   }
 }
@@ -849,7 +896,7 @@ k_lift(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
   {
     R u, v, w, T;
     if constexpr (std::is_same<R, float>::value) {
-      velocity_temperature32(load_prim32(m.W32, S, g), ph, u, v, w, T);
+      velocity_temperature32(load_prim32_full(m.W32, S, g, ph), ph, u, v, w, T);
     } else if (m.W64) {
       // the FP64 primitives of the node, kept for the face and volume kernels
       double Td;
@@ -875,7 +922,7 @@ k_lift(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
       const size_t gn = (size_t)nb * n3 + fnode<N>(l ^ 1, a, b);
       R u, v, w, T;
       if constexpr (std::is_same<R, float>::value)
-        velocity_temperature32(load_prim32(m.W32, S, gn), ph, u, v, w, T);
+        velocity_temperature32(load_prim32_full(m.W32, S, gn, ph), ph, u, v, w, T);
       else
         velocity_temperature<R>(U[gn], U[S + gn], U[2 * S + gn], U[3 * S + gn], U[4 * S + gn], ph, u, v, w, T);
       d0 = R(0.5) * (u - Wo0); d1 = R(0.5) * (v - Wo1); d2 = R(0.5) * (w - Wo2);
@@ -1087,7 +1134,7 @@ k_face(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
       store_face_delta(ph, A, B, dU, nx, ny, nz, s, gA, gB, R(0.5), Fs + (size_t)f * 10 * n2 + ab, n2, true);
       return;
     }
-    riemann_d<float>(ph, A, B, dU, nx, ny, nz, F);
+    riemann_d<float>(ph, unshift32(A, ph), unshift32(B, ph), dU, nx, ny, nz, F);
   } else {
     // both sides' FP64 primitives: from the lifting kernel's array where it
     // ran, else (and for a remote trace) by primitive_T, whose one compiled
@@ -1198,7 +1245,9 @@ k_halo_face(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, 
       for (int v = 0; v < 5; ++v) dU[v] = (float)(UB[v] - UA[v]);
       const R* gl = Gf + ((size_t)fc.x * 6 + fc.y) * 4 * n2 + ab;
       const R* gr = m.halo_G + (size_t)h * 4 * n2 + ab;
-      store_face_delta(ph, A, B, dU, nx, ny, nz, s, master ? gl : gr, master ? gr : gl, 0.5f,
+      // the storage form of the FP32 primitives (shifted rho, h)
+      const Prim<float> As = prim32_shifted(UA[0], UA[1], UA[2], UA[3], UA[4], ph), Bs = prim32_shifted(UB[0], UB[1], UB[2], UB[3], UB[4], ph);
+      store_face_delta(ph, As, Bs, dU, nx, ny, nz, s, master ? gl : gr, master ? gr : gl, 0.5f,
                        Fs + (size_t)f * 10 * n2 + ab, n2, true);
       return;
     }
@@ -1275,7 +1324,8 @@ k_bc(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const R
       float dU[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) dU[v] = (float)(UB[v] - UA[v]);
-      store_face_delta(ph, A, B, dU, nx, ny, nz, s, Gf + ((size_t)fc.x * 6 + fc.y) * 4 * n2 + ab, nullptr, 1.f,
+      const Prim<float> As = prim32_shifted(UA[0], UA[1], UA[2], UA[3], UA[4], ph), Bs = prim32_shifted(UB[0], UB[1], UB[2], UB[3], UB[4], ph);
+      store_face_delta(ph, As, Bs, dU, nx, ny, nz, s, Gf + ((size_t)fc.x * 6 + fc.y) * 4 * n2 + ab, nullptr, 1.f,
                        Fs + (size_t)f * 10 * n2 + ab, n2, false);
       return;
     }
@@ -1331,7 +1381,8 @@ k_wall(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, R* __
       float dU[5], DB[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) dU[v] = (float)(UB[v] - UA[v]);
-      face_flux_delta(ph, A, B, dU, (R)nxd, (R)nyd, (R)nzd, F, DB);
+      const Prim<float> As = prim32_shifted(UA[0], UA[1], UA[2], UA[3], UA[4], ph), Bs = prim32_shifted(UB[0], UB[1], UB[2], UB[3], UB[4], ph);
+      face_flux_delta(ph, As, Bs, dU, (R)nxd, (R)nyd, (R)nzd, F, DB);
       fss = 10;
     }
   }
@@ -1356,7 +1407,7 @@ k_wall(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, R* __
           const float ljk = L[n + jj] * L[2 * n + kk];
           float row[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
           for (int ii = 0; ii < n; ++ii) {
-            const Prim<float> q = load_prim32(m.W32, S, (size_t)es * n3 + ii + n * (jj + n * kk));
+            const Prim<float> q = load_prim32_full(m.W32, S, (size_t)es * n3 + ii + n * (jj + n * kk), ph);
             const float li = L[ii];
             row[0] += li * q.rho;
             row[1] += li * (q.rho * q.u);
@@ -1535,7 +1586,8 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
     const size_t g = (size_t)e * n3 + t;
     Prim<R> q;
     if constexpr (F32) {
-      q = load_prim32(m.W32, S, g);
+      // the difference form works on the storage form (shifted rho, h)
+      q = dif ? load_prim32(m.W32, S, g) : load_prim32_full(m.W32, S, g, ph);
     } else if (m.W64) {
       q = load_prim64(m.W64, S, g);
     } else {
@@ -1672,13 +1724,15 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
             const float aq0 = sA[(dir * 3 + 0) * n3 + qs], aq1 = sA[(dir * 3 + 1) * n3 + qs],
                         aq2 = sA[(dir * 3 + 2) * n3 + qs];
             float G[5];
-            flux_delta(mi, mq, A.a0, A.a1, A.a2, aq0 - A.a0, aq1 - A.a1, aq2 - A.a2, G);
+            flux_delta(mi, mq, A.a0, A.a1, A.a2, aq0 - A.a0, aq1 - A.a1, aq2 - A.a2, ph.f32c.rho_ref, ph.f32c.h_ref,
+                       G);
             const float c1 = sC1[pos * n + pm];
 #pragma unroll
             for (int v = 0; v < 5; ++v) acc[v] += c1 * G[v];
             if (2 * d != n) {
               // G(q -> i) for the partner lane (pos + d); receive G(i -> pos - d)
-              flux_delta(mq, mi, aq0, aq1, aq2, A.a0 - aq0, A.a1 - aq1, A.a2 - aq2, G);
+              flux_delta(mq, mi, aq0, aq1, aq2, A.a0 - aq0, A.a1 - aq1, A.a2 - aq2, ph.f32c.rho_ref, ph.f32c.h_ref,
+                         G);
               const int src = base + (pos - d >= 0 ? pos - d : pos - d + n);
               const float r1 = sC1[pos * n + (src - base)];
 #pragma unroll
@@ -1821,7 +1875,7 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
     if (bad) atomicOr(status, ST_NONFINITE);
     // the next stage's FP32 primitives, from the updated FP64 state
     if constexpr (F32) {
-      if (st.write_w32) store_prim32(m.W32, S, g, primitive<float>(Uo[0], Uo[1], Uo[2], Uo[3], Uo[4], ph));
+      if (st.write_w32) store_prim32(m.W32, S, g, prim32_shifted(Uo[0], Uo[1], Uo[2], Uo[3], Uo[4], ph));
     }
   }
 }

@@ -46,7 +46,8 @@ class _Phys(ctypes.Structure):
                 ("Pr", ctypes.c_double), ("force", ctypes.c_double * 3), ("kappa", ctypes.c_double),
                 ("B", ctypes.c_double), ("hwm", ctypes.c_double), ("law", ctypes.c_int),
                 ("p_ref", ctypes.c_double), ("suth_S", ctypes.c_double), ("T_ref", ctypes.c_double),
-                ("U_in", ctypes.c_double * 5), ("p_out", ctypes.c_double), ("T_wall", ctypes.c_double)]
+                ("U_in", ctypes.c_double * 5), ("p_out", ctypes.c_double), ("T_wall", ctypes.c_double),
+                ("rho_ref", ctypes.c_double)]
 
 
 class _Options(ctypes.Structure):
@@ -213,7 +214,8 @@ class Operator:
                    phys.get("kappa", 0.41), phys.get("B", 5.2), phys.get("hwm", 0.1), int(law),
                    phys.get("p_ref", phys.get("p0", 0.0)), phys.get("suth_S", 0.0), phys.get("T_ref", 1.0),
                    (ctypes.c_double * 5)(*[float(x) for x in phys.get("U_in", (1.0, 0.0, 0.0, 0.0, 1.0))]),
-                   float(phys.get("p_out", 1.0)), float(phys.get("T_wall", 0.0)))
+                   float(phys.get("p_out", 1.0)), float(phys.get("T_wall", 0.0)),
+                   float(phys.get("rho_ref", 1.0)))
         op = _Options(int(precision), int(vol_flux), int(surf_flux), int(viscous))
         h = ctypes.c_void_p()
         self._stream = _stream_handle(stream)

@@ -188,7 +188,7 @@ def phys_params(Ma=0.1, Re=1600.0, Pr=0.72, gamma=1.4, force=(0.0, 0.0, 0.0),
     p0 = 1.0 / (gamma * Ma * Ma)
     d = dict(gamma=gamma, R=1.0, mu=0.0 if inviscid else 1.0 / Re, Pr=Pr,
              fx=force[0], fy=force[1], fz=force[2], kappa=kappa, B=B, hwm=hwm,
-             Ma=Ma, p0=p0)
+             Ma=Ma, p0=p0, rho_ref=1.0)
     if sutherland:
         d.update(T_ref=p0, suth_S=p0 * 110.4 / 288.15)
     return d

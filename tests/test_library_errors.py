@@ -67,6 +67,12 @@ def test_sutherland_needs_a_reference_temperature():
     assert _init(spec.N, X, nbr, phys)[0] == ARG
 
 
+def test_reference_density_must_not_be_negative():
+    spec, X, nbr = _mesh()
+    phys = I.phys_params(); phys["rho_ref"] = -1.0
+    assert _init(spec.N, X, nbr, phys, precision=dg.FP32_MIXED)[0] == ARG
+
+
 def test_inflow_and_outflow_states_must_be_physical():
     spec, X, nbr = _mesh(periodic=(False, True, True),
                          boundary=((I.INFLOW, I.OUTFLOW), (I.WALL, I.WALL), (I.WALL, I.WALL)))
