@@ -532,33 +532,39 @@ k_adj_element(const double* __restrict__ U, const double* __restrict__ lam, cons
         return dir == 0 ? q + n * L : (dir == 1 ? a + n * q + n2 * b : L + n2 * q);
       };
       const int me = node(pos);
+      // the pair terms below carry constant factors (1/8 for rho, u, v, w,
+      // 1/4 for p, 1/16 for h) that are applied once per node after the sums
       double g0 = 0, g1 = 0, g2 = 0, g3 = 0, g4 = 0, g5 = 0;
 #pragma unroll
       for (int d = 1; d <= n / 2; ++d) {
         const int pm = pos + d < n ? pos + d : pos + d - n;
         const int q = node(pm);
-        const double rb = 0.5 * (sQ[me] + sQ[q]);
-        const double ub = 0.5 * (sQ[n3 + me] + sQ[n3 + q]), vb = 0.5 * (sQ[2 * n3 + me] + sQ[2 * n3 + q]),
-                     wb = 0.5 * (sQ[3 * n3 + me] + sQ[3 * n3 + q]);
-        const double hb = 0.5 * (sQ[5 * n3 + me] + sQ[5 * n3 + q]);
-        const double a0 = 0.5 * (sA[(dir * 3 + 0) * n3 + me] + sA[(dir * 3 + 0) * n3 + q]);
-        const double a1 = 0.5 * (sA[(dir * 3 + 1) * n3 + me] + sA[(dir * 3 + 1) * n3 + q]);
-        const double a2 = 0.5 * (sA[(dir * 3 + 2) * n3 + me] + sA[(dir * 3 + 2) * n3 + q]);
+        // sums of the two nodes' values: {x} = Sx / 2
+        const double Sr = sQ[me] + sQ[q];
+        const double Su = sQ[n3 + me] + sQ[n3 + q], Sv = sQ[2 * n3 + me] + sQ[2 * n3 + q],
+                     Sw = sQ[3 * n3 + me] + sQ[3 * n3 + q];
+        const double Sh = sQ[5 * n3 + me] + sQ[5 * n3 + q];
+        const double Sa0 = sA[(dir * 3 + 0) * n3 + me] + sA[(dir * 3 + 0) * n3 + q];
+        const double Sa1 = sA[(dir * 3 + 1) * n3 + me] + sA[(dir * 3 + 1) * n3 + q];
+        const double Sa2 = sA[(dir * 3 + 2) * n3 + me] + sA[(dir * 3 + 2) * n3 + q];
         const double cim = sDVS[pos * n + pm], cmi = sDVS[pm * n + pos];
         double mu[5];
 #pragma unroll
         for (int v = 0; v < 5; ++v) mu[v] = cim * sL[v * n3 + me] + cmi * sL[v * n3 + q];
-        // F0 = rb qa, Fk = rb qa uk + pb ak, F4 = rb qa hb, qa = ub.a
-        const double qa = ub * a0 + vb * a1 + wb * a2;
-        const double tt = mu[0] + mu[1] * ub + mu[2] * vb + mu[3] * wb + mu[4] * hb;
-        const double rq = rb * qa;
-        // half of the average's cotangent goes to each node
-        const double h0 = 0.5 * qa * tt;
-        const double h1 = 0.5 * (rb * tt * a0 + rq * mu[1]);
-        const double h2 = 0.5 * (rb * tt * a1 + rq * mu[2]);
-        const double h3 = 0.5 * (rb * tt * a2 + rq * mu[3]);
-        const double h4 = 0.5 * (mu[1] * a0 + mu[2] * a1 + mu[3] * a2);
-        const double h5 = 0.5 * rq * mu[4];
+        // F0 = {rho} qa, Fk = {rho} qa {u_k} + {p} {a_k}, F4 = {rho} qa {h}, qa = {u}.{a} = Q / 4;
+        // tt = mu . dF/d({rho} qa) = mu0 + (mu1 Su + mu2 Sv + mu3 Sw + mu4 Sh) / 2;
+        // half of each average's cotangent goes to each node:
+        //   g_rho = Q tt / 8, g_u_k = Sr (tt Sa_k + Q mu_k / 2) / 8, g_p = (mu . Sa) / 4,
+        //   g_h = Sr Q mu4 / 16
+        const double Q = Su * Sa0 + Sv * Sa1 + Sw * Sa2;
+        const double tt = fma(0.5, mu[1] * Su + mu[2] * Sv + mu[3] * Sw + mu[4] * Sh, mu[0]);
+        const double hQ = 0.5 * Q;
+        const double h0 = Q * tt;
+        const double h1 = Sr * fma(tt, Sa0, hQ * mu[1]);
+        const double h2 = Sr * fma(tt, Sa1, hQ * mu[2]);
+        const double h3 = Sr * fma(tt, Sa2, hQ * mu[3]);
+        const double h4 = mu[1] * Sa0 + mu[2] * Sa1 + mu[3] * Sa2;
+        const double h5 = Sr * Q * mu[4];
         g0 += h0; g1 += h1; g2 += h2; g3 += h3; g4 += h4; g5 += h5;
         if (2 * d != n) {
           const int src = base + (pos - d >= 0 ? pos - d : pos - d + n);
@@ -570,6 +576,7 @@ k_adj_element(const double* __restrict__ U, const double* __restrict__ lam, cons
           g5 += __shfl_sync(0xffffffffu, h5, src);
         }
       }
+      g0 *= 0.125; g1 *= 0.125; g2 *= 0.125; g3 *= 0.125; g4 *= 0.25; g5 *= 0.0625;
       if (active) {
         if (dir == 0) {
           sGQ[me] = g0; sGQ[n3 + me] = g1; sGQ[2 * n3 + me] = g2; sGQ[3 * n3 + me] = g3;
@@ -617,8 +624,9 @@ k_adj_element(const double* __restrict__ U, const double* __restrict__ lam, cons
 #pragma unroll
       for (int c = 0; c < 9; ++c) ja[c] = sA[c * n3 + t];
       const double iJ = m.invJ[g];
-      // forward gradients q[d][v]
-      double q[3][4];
+      // forward gradients q[d][v]: reference-space derivatives, the BR1
+      // surface corrections on them, then the metric transform
+      double dW[3][4];
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
         double s0 = 0, s1 = 0, s2 = 0;
@@ -628,26 +636,22 @@ k_adj_element(const double* __restrict__ U, const double* __restrict__ lam, cons
           s1 += sD[j * n + mm] * sW[v * n3 + i + n * (mm + n * k)];
           s2 += sD[k * n + mm] * sW[v * n3 + i + n * (j + n * mm)];
         }
-#pragma unroll
-        for (int d = 0; d < 3; ++d) q[d][v] = ja[0 * 3 + d] * s0 + ja[1 * 3 + d] * s1 + ja[2 * 3 + d] * s2;
+        dW[0][v] = s0; dW[1][v] = s1; dW[2][v] = s2;
       }
-      auto surf = [&](int l, int ab, double sgn_iw) {
-        const int dir = l >> 1;
+      auto surf = [&](int dir, int l, int ab, double sgn_iw) {
 #pragma unroll
-        for (int d = 0; d < 3; ++d)
-#pragma unroll
-          for (int v = 0; v < 4; ++v) q[d][v] += sgn_iw * ja[dir * 3 + d] * sC[(l * 4 + v) * n2 + ab];
+        for (int v = 0; v < 4; ++v) dW[dir][v] += sgn_iw * sC[(l * 4 + v) * n2 + ab];
       };
-      if (i == 0) surf(0, j + n * k, -siw[0]);
-      if (i == N) surf(1, j + n * k, siw[N]);
-      if (j == 0) surf(2, i + n * k, -siw[0]);
-      if (j == N) surf(3, i + n * k, siw[N]);
-      if (k == 0) surf(4, i + n * j, -siw[0]);
-      if (k == N) surf(5, i + n * j, siw[N]);
+      if (i == 0 || i == N) surf(0, i == 0 ? 0 : 1, j + n * k, i == 0 ? -siw[0] : siw[N]);
+      if (j == 0 || j == N) surf(1, j == 0 ? 2 : 3, i + n * k, j == 0 ? -siw[0] : siw[N]);
+      if (k == 0 || k == N) surf(2, k == 0 ? 4 : 5, i + n * j, k == 0 ? -siw[0] : siw[N]);
+      double q[3][4];
 #pragma unroll
-      for (int d = 0; d < 3; ++d)
+      for (int d = 0; d < 3; ++d) {
+        const double j0 = iJ * ja[0 * 3 + d], j1 = iJ * ja[1 * 3 + d], j2 = iJ * ja[2 * 3 + d];
 #pragma unroll
-        for (int v = 0; v < 4; ++v) q[d][v] *= iJ;
+        for (int v = 0; v < 4; ++v) q[d][v] = j0 * dW[0][v] + j1 * dW[1][v] + j2 * dW[2][v];
+      }
       // cotangent of the contravariant viscous flux G^dir at this node:
       // from R_v = sum_i Dvisc_i,m G_m (transposed) and from the face fluxes
       double gG[3][4];
@@ -714,18 +718,21 @@ k_adj_element(const double* __restrict__ U, const double* __restrict__ lam, cons
       for (int d = 0; d < 3; ++d)
 #pragma unroll
         for (int v = 0; v < 4; ++v) gq[d][v] *= iJ;
+      // cotangent of the reference-space gradient: H^dir = Ja^dir . gq
+      double H[3][4];
 #pragma unroll
       for (int dir = 0; dir < 3; ++dir)
 #pragma unroll
-        for (int v = 0; v < 4; ++v)
-          sH[(dir * 4 + v) * n3 + t] = ja[dir * 3 + 0] * gq[0][v] + ja[dir * 3 + 1] * gq[1][v] + ja[dir * 3 + 2] * gq[2][v];
-      // surface terms: (W* - W) (n s)_d / w_perp with n s = +-Ja^dir
+        for (int v = 0; v < 4; ++v) {
+          H[dir][v] = ja[dir * 3 + 0] * gq[0][v] + ja[dir * 3 + 1] * gq[1][v] + ja[dir * 3 + 2] * gq[2][v];
+          sH[(dir * 4 + v) * n3 + t] = H[dir][v];
+        }
+      // surface terms: dW_dir += (W* - W) (+-1 / w) at the line ends
       auto surf_t = [&](int l, int ab, double sgn_iw) {
         const int dir = l >> 1;
         double tv[4];
 #pragma unroll
-        for (int v = 0; v < 4; ++v)
-          tv[v] = sgn_iw * (ja[dir * 3 + 0] * gq[0][v] + ja[dir * 3 + 1] * gq[1][v] + ja[dir * 3 + 2] * gq[2][v]);
+        for (int v = 0; v < 4; ++v) tv[v] = sgn_iw * H[dir][v];
         const int nb = m.nbr[e * 6 + l];
         if (nb >= 0) {
           // W* - W = (W_nbr - W) / 2
@@ -743,12 +750,9 @@ k_adj_element(const double* __restrict__ U, const double* __restrict__ lam, cons
           gWo[0] -= tn * nx; gWo[1] -= tn * ny; gWo[2] -= tn * nz;
         }
       };
-      if (i == 0) surf_t(0, j + n * k, -siw[0]);
-      if (i == N) surf_t(1, j + n * k, siw[N]);
-      if (j == 0) surf_t(2, i + n * k, -siw[0]);
-      if (j == N) surf_t(3, i + n * k, siw[N]);
-      if (k == 0) surf_t(4, i + n * j, -siw[0]);
-      if (k == N) surf_t(5, i + n * j, siw[N]);
+      if (i == 0 || i == N) surf_t(i == 0 ? 0 : 1, j + n * k, i == 0 ? -siw[0] : siw[N]);
+      if (j == 0 || j == N) surf_t(j == 0 ? 2 : 3, i + n * k, j == 0 ? -siw[0] : siw[N]);
+      if (k == 0 || k == N) surf_t(k == 0 ? 4 : 5, i + n * j, k == 0 ? -siw[0] : siw[N]);
     }
     __syncthreads();
     if (t < n3) {
