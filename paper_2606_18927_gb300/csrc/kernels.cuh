@@ -544,6 +544,19 @@ __device__ __forceinline__ Prim<float> load_prim32_full(const float* __restrict_
   return unshift32(load_prim32(W, S, g), ph);
 }
 
+// the primitives a boundary or halo face kernel forms from a conservative
+// trace: FP64 directly; FP32 in the storage form (*st, for the flux-difference
+// form) with the full values rebuilt from it
+template <typename R>
+__device__ __forceinline__ Prim<R> trace_prims(const double Ut[5], const PhysDev& ph, Prim<R>* st) {
+  if constexpr (std::is_same<R, float>::value) {
+    *st = prim32_shifted(Ut[0], Ut[1], Ut[2], Ut[3], Ut[4], ph);
+    return unshift32(*st, ph);
+  } else {
+    return primitive<R>(Ut[0], Ut[1], Ut[2], Ut[3], Ut[4], ph);
+  }
+}
+
 static __global__ void k_prim32(long long S, const double* __restrict__ U, const PhysDev ph, float* __restrict__ W) {
   for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < S; x += (long long)gridDim.x * blockDim.x) {
     const Prim<float> q = prim32_shifted(U[x], U[S + x], U[2 * S + x], U[3 * S + x], U[4 * S + x], ph);
@@ -1223,21 +1236,8 @@ k_halo_face(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, 
   }
   const size_t FN = (size_t)m.F * n2, fg = (size_t)f * n2 + ab;
   const R nx = (R)m.fgeo[fg], ny = (R)m.fgeo[FN + fg], nz = (R)m.fgeo[2 * FN + fg], s = (R)m.fgeo[3 * FN + fg];
-  Prim<R> A, B;
-  if constexpr (std::is_same<R, double>::value) {
-    if (m.W64) {
-      // the values k_face takes from the lifting kernel's array (on both ranks)
-      double T;
-      A = primitive_T(UA[0], UA[1], UA[2], UA[3], UA[4], ph, T);
-      B = primitive_T(UB[0], UB[1], UB[2], UB[3], UB[4], ph, T);
-    } else {
-      A = primitive<R>(UA[0], UA[1], UA[2], UA[3], UA[4], ph);
-      B = primitive<R>(UB[0], UB[1], UB[2], UB[3], UB[4], ph);
-    }
-  } else {
-    A = primitive<R>(UA[0], UA[1], UA[2], UA[3], UA[4], ph);
-    B = primitive<R>(UB[0], UB[1], UB[2], UB[3], UB[4], ph);
-  }
+  Prim<R> As, Bs;
+  const Prim<R> A = trace_prims<R>(UA, ph, &As), B = trace_prims<R>(UB, ph, &Bs);
   if constexpr (std::is_same<R, float>::value) {
     if (ph.fs_diff) {
       float dU[5];
@@ -1245,8 +1245,6 @@ k_halo_face(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, 
       for (int v = 0; v < 5; ++v) dU[v] = (float)(UB[v] - UA[v]);
       const R* gl = Gf + ((size_t)fc.x * 6 + fc.y) * 4 * n2 + ab;
       const R* gr = m.halo_G + (size_t)h * 4 * n2 + ab;
-      // the storage form of the FP32 primitives (shifted rho, h)
-      const Prim<float> As = prim32_shifted(UA[0], UA[1], UA[2], UA[3], UA[4], ph), Bs = prim32_shifted(UB[0], UB[1], UB[2], UB[3], UB[4], ph);
       store_face_delta(ph, As, Bs, dU, nx, ny, nz, s, master ? gl : gr, master ? gr : gl, 0.5f,
                        Fs + (size_t)f * 10 * n2 + ab, n2, true);
       return;
@@ -1315,8 +1313,8 @@ k_bc(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const R
 #pragma unroll
   for (int v = 0; v < 5; ++v) UA[v] = U[v * S + gM];
   ghost_state(ph, fc.z, UA, UB);
-  const Prim<R> A = primitive<R>(UA[0], UA[1], UA[2], UA[3], UA[4], ph);
-  const Prim<R> B = primitive<R>(UB[0], UB[1], UB[2], UB[3], UB[4], ph);
+  Prim<R> As, Bs;  // FP32: the storage form, for the flux-difference form
+  const Prim<R> A = trace_prims<R>(UA, ph, &As), B = trace_prims<R>(UB, ph, &Bs);
   const size_t FN = (size_t)m.F * n2, fg = (size_t)f * n2 + ab;
   const R nx = (R)m.fgeo[fg], ny = (R)m.fgeo[FN + fg], nz = (R)m.fgeo[2 * FN + fg], s = (R)m.fgeo[3 * FN + fg];
   if constexpr (std::is_same<R, float>::value) {
@@ -1324,7 +1322,6 @@ k_bc(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const R
       float dU[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) dU[v] = (float)(UB[v] - UA[v]);
-      const Prim<float> As = prim32_shifted(UA[0], UA[1], UA[2], UA[3], UA[4], ph), Bs = prim32_shifted(UB[0], UB[1], UB[2], UB[3], UB[4], ph);
       store_face_delta(ph, As, Bs, dU, nx, ny, nz, s, Gf + ((size_t)fc.x * 6 + fc.y) * 4 * n2 + ab, nullptr, 1.f,
                        Fs + (size_t)f * 10 * n2 + ab, n2, false);
       return;
@@ -1372,8 +1369,8 @@ k_wall(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, R* __
   const double mn = UA[1] * nxd + UA[2] * nyd + UA[3] * nzd;
   UB[0] = UA[0]; UB[1] = UA[1] - 2.0 * mn * nxd; UB[2] = UA[2] - 2.0 * mn * nyd;
   UB[3] = UA[3] - 2.0 * mn * nzd; UB[4] = UA[4];
-  const Prim<R> A = primitive<R>(UA[0], UA[1], UA[2], UA[3], UA[4], ph);
-  const Prim<R> B = primitive<R>(UB[0], UB[1], UB[2], UB[3], UB[4], ph);
+  Prim<R> As, Bs;  // FP32: the storage form, for the flux-difference form
+  const Prim<R> A = trace_prims<R>(UA, ph, &As), B = trace_prims<R>(UB, ph, &Bs);
   R F[5];
   int fss = 5;  // surface-flux values per face node (10: FP32 difference form)
   if constexpr (std::is_same<R, float>::value) {
@@ -1381,7 +1378,6 @@ k_wall(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, R* __
       float dU[5], DB[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) dU[v] = (float)(UB[v] - UA[v]);
-      const Prim<float> As = prim32_shifted(UA[0], UA[1], UA[2], UA[3], UA[4], ph), Bs = prim32_shifted(UB[0], UB[1], UB[2], UB[3], UB[4], ph);
       face_flux_delta(ph, As, Bs, dU, (R)nxd, (R)nyd, (R)nzd, F, DB);
       fss = 10;
     }
