@@ -4,12 +4,13 @@
 // and g_theta = (dUt/d(kappa, B))^T lam for the wall-law constants.  The
 // kernels run the forward operator's structure backwards:
 //   k_adj_face   interior face nodes: cotangent of the surface flux from the
-//                two sides' lam, transposed local Jacobian of the Riemann flux
-//                (by forward-mode duals over the 10 state components), and
-//                the cotangents of the two sides' viscous face fluxes;
+//                two sides' lam, the Riemann flux in hand-written reverse mode
+//                (face_flux_vjp), and the cotangents of the two sides'
+//                viscous face fluxes;
 //   k_adj_wall   wall face nodes: the same through the mirror state, and the
-//                wall-model derivative (implicit function theorem for the law
-//                of the wall) with respect to the sample state and (kappa, B);
+//                wall-model derivative (forward-mode duals over the sample
+//                state; implicit function theorem for the law of the wall)
+//                with respect to the sample state and (kappa, B);
 //   k_adj_element one CTA per element: transposed split-form volume integral
 //                (hand-derived, symmetric pairs with shuffles), transposed
 //                viscous divergence and viscous flux, transposed BR1 lifting,
@@ -61,18 +62,6 @@ __device__ __forceinline__ DualD sqrt(DualD a) {
 }
 __device__ __forceinline__ DualD fabs(DualD a) { return a.v < 0.0 ? -a : a; }
 __device__ __forceinline__ DualD asin(DualD a) { return DualD(::asin(a.v), a.d / ::sqrt(1.0 - a.v * a.v)); }
-
-// primitive state of a dual conservative state (same formula as primitive<double>)
-__device__ __forceinline__ Prim<DualD> primitive_dual(const DualD U[5], const PhysDev& ph) {
-  Prim<DualD> q;
-  const DualD ir = 1.0 / U[0];
-  q.rho = U[0];
-  q.u = U[1] * ir; q.v = U[2] * ir; q.w = U[3] * ir;
-  const DualD p = ph.gm1 * (U[4] - 0.5 * (U[1] * q.u + U[2] * q.v + U[3] * q.w));
-  q.p = p - ph.p_ref;
-  q.h = (U[4] + p) * ir;
-  return q;
-}
 
 // ---------------------------------------------------------------------------
 // wall-model JVP: tau (3) with its derivative along the duals of Us and

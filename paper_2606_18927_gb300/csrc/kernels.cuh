@@ -2,25 +2,30 @@
 //
 // One operator evaluation (paper Sec. 2.2 / Sec. 4: split-form DGSEM on LGL
 // nodes; Sec. 3: equilibrium wall model) launches:
-//   k_lift      one CTA per element: primitives, BR1 lifting of grad(u,v,w,T),
-//               viscous flux, its weak-form volume divergence R_v, and the
-//               element's own outward viscous flux at its six faces;
+//   k_lift      one CTA per element: primitives (in FP64 kept for the face
+//               and volume kernels), BR1 lifting of grad(u,v,w,T), viscous
+//               flux, its weak-form volume divergence R_v, and the element's
+//               own outward viscous flux at its six faces (FP64, N = 7: line
+//               contractions in even/odd form, LineEO);
 //   k_face      one thread per interior face node: Riemann flux (central /
 //               LLF / Roe with Harten's entropy fix) plus the BR1 average of
-//               the viscous flux;
+//               the viscous flux (FP64: also the halo faces of a partitioned
+//               mesh);
 //   k_bc        inflow / outflow face nodes (exterior-state Riemann flux);
-//   k_halo_face faces shared with another rank of a partitioned mesh;
+//   k_halo_face FP32: faces shared with another rank of a partitioned mesh;
 //   k_wall      wall face nodes: mirror state and the wall-stress model (may
 //               run on a side stream beside k_lift and k_face);
 //   k_volume    one CTA per element: two-point flux differencing (KEP or
 //               entropy-conserving) with the split-form matrix DVS = 2D - B/w
 //               (zero corners), the surface integral, 1/J scaling, body force,
-//               and either Ut or the LSERK4 register update of U and dU.
+//               and either Ut or the LSERK4 register update of U and dU (N = 7:
+//               swizzled shared-memory node slots, vslot; FP64: each pair at
+//               distance n/2 formed once).
 // R is the arithmetic type of the fluxes and their sums (double, or float in
 // the mixed form); the state U, dU, the pressure recovery and the RK update
 // are always double.  The FP32 form also keeps per-stage FP32 primitives
-// (k_prim32 / the stage epilogue) and, with the Pirozzoli flux, sums flux
-// differences (flux_delta) instead of fluxes.
+// relative to a reference state (k_prim32 / the stage epilogue) and, with the
+// Pirozzoli flux, sums flux differences (flux_delta) instead of fluxes.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
