@@ -22,6 +22,10 @@ TOL = 1e-12
     ("n4_central_kg", I.BoxSpec(4, 2, 3, 2, geometry="sine", amplitude=0.2), 0, 1, 1),
     ("n5_roe_euler", I.BoxSpec(5, 2, 2, 3, geometry="sine", amplitude=0.2), 2, 0, 0),
     ("n7_roe_sine", I.BoxSpec(7, 2, 2, 2, geometry="sine", amplitude=0.1), 2, 0, 1),
+    # N = 7 without viscous terms (primitives formed by the face and volume
+    # kernels themselves) and with the Kennedy-Gruber flux
+    ("n7_llf_kg_euler", I.BoxSpec(7, 2, 3, 2, geometry="sine", amplitude=0.1), 1, 1, 0),
+    ("n7_central_kg", I.BoxSpec(7, 3, 2, 2, geometry="sine", amplitude=0.1), 0, 1, 1),
     ("n1_llf", I.BoxSpec(1, 3, 3, 3), 1, 0, 1),
     ("n6_llf_periodic_self", I.BoxSpec(6, 1, 2, 1), 1, 0, 1),
     ("n8_roe", I.BoxSpec(8, 2, 1, 2, geometry="sine", amplitude=0.1), 2, 0, 1),
