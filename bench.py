@@ -438,7 +438,11 @@ def run_ours(args):
             kernels[k] = {"ms_per_launch": avg, "launches": cnt, "share": ms / max(ms_total, 1e-30),
                           "flops_per_dof": flops,
                           "achieved_tflops": flops * dofs / (avg * 1e-3) / 1e12 if flops else None}
-    dom = max(kernels, key=lambda k: kernels[k]["ms_per_launch"] * kernels[k]["launches"])
+    # the dominant kernel among those with a flop model (the wall-model kernel,
+    # whose work depends on its Newton iterations, runs beside them on a side
+    # stream and its event time stretches with the overlap)
+    modelled = [k for k in kernels if kernels[k]["flops_per_dof"]] or list(kernels)
+    dom = max(modelled, key=lambda k: kernels[k]["ms_per_launch"] * kernels[k]["launches"])
     peaks = load_peaks()
     if precision == dg.FP64:
         achieved = kernels[dom]["achieved_tflops"]
