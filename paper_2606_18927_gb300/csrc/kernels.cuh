@@ -1542,13 +1542,13 @@ struct VolShape {
 };
 
 // Resident CTAs per SM asked of the register allocator: two for CTAs of up to
-// 512 threads (64 registers; measured 5 % faster at N = 7 in FP64 than one CTA
-// at 106 registers, and 1.6x faster for the FP32 entropy-conserving kernel
-// than one CTA at 104), except the FP64 entropy-conserving kernel (about 126
-// registers, one CTA).
+// 512 threads (64 registers at N = 7; measured 5 % faster in FP64 than one CTA
+// at 106 registers, 1.6x faster for the FP32 entropy-conserving kernel than one
+// CTA at 104, and 1.3 % faster for the FP64 entropy-conserving kernel than one
+// CTA at 126 registers, in spite of its spills).
 template <int N, typename R, bool EC>
 constexpr int vol_min_blocks() {
-  return ((!EC || std::is_same<R, float>::value) && VolShape<N>::THREADS * 64 * 2 <= 65536) ? 2 : 1;
+  return (VolShape<N>::THREADS * 64 * 2 <= 65536) ? 2 : 1;
 }
 
 template <int N, typename R, int MODE, bool EC>
