@@ -392,6 +392,14 @@ int dg_init_mesh(dg_ctx** out, const dg_mesh_desc* m, const dg_phys* p, const dg
   ph.f32c.gamma = (float)ph.gamma; ph.f32c.mu = (float)ph.mu; ph.f32c.kcond = (float)ph.kcond;
   ph.f32c.cp_Pr = (float)ph.cp_Pr; ph.f32c.suth_C = (float)ph.suth_C; ph.f32c.suth_S = (float)ph.suth_S;
   ph.f32c.rho_ref = (float)ph.rho_ref; ph.f32c.h_ref = (float)ph.h_ref;
+  {
+    // Q(t) = 1 - 2t/3 + 8t^2/15 - 16t^3/35 + 128t^4/315, times 2 / (gamma - 1)
+    const double qc[5] = {1.0, -2.0 / 3.0, 8.0 / 15.0, -16.0 / 35.0, 128.0 / 315.0};
+    for (int c = 0; c < 5; ++c) {
+      ph.ec_q[c] = 2.0 * ph.rgm1 * qc[c];
+      ph.f32c.ec_q[c] = (float)ph.ec_q[c];
+    }
+  }
   ph.f32c.g_gm1 = (float)(p->gamma / (p->gamma - 1.0));
   ph.f32c.h_p = p->rho_ref > 0.0 ? 0.0f : (float)p->p_ref;
   ph.f32c.h_r = p->rho_ref > 0.0 ? (float)(p->p_ref / p->rho_ref) : 0.0f;

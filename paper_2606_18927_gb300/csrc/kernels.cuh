@@ -44,6 +44,7 @@ struct PhysDev {
   double suth_C;  // mu_ref (T_ref + S) / T_ref^(3/2)
   double p_ref;   // constant removed from p in the momentum fluxes
   double rho_ref, h_ref;  // FP32-mixed form: reference density and enthalpy removed from its FP32 primitives
+  double ec_q[5];  // 2 (gamma - 1)^-1 times the t^k coefficients of Q(t) = 2 s / sinh 2s (entropy-conserving flux)
   double f[3];
   double kappa, B, hwm;
   int law, vol_flux, surf_flux, viscous;
@@ -56,6 +57,7 @@ struct PhysDev {
   struct {
     float p_ref, rcp_R, rgm1, gamma, mu, kcond, cp_Pr, suth_C, suth_S, rho_ref, h_ref;
     float g_gm1, h_p, h_r;  // gamma / (gamma - 1); p_ref (rho_ref = 0) or 0; p_ref / rho_ref or 0
+    float ec_q[5];
   } f32c;
 };
 
@@ -174,18 +176,13 @@ __device__ __forceinline__ R logmean_P_slow(R a, R b) {
 //   L = ((a + b) / 2) G(t),        G = tanh(s) / s
 //   1 / L = ((1/a + 1/b) / 2) Q(t), Q = 2 s / sinh(2 s)
 //   1 / (a + b) = ((1/a + 1/b) / 4) / (1 + t)
-// Series through t^4 (the t^5 terms are below 0.4 t^5).
+// Series through t^4 (the t^5 terms are below 0.4 t^5):
+//   G = 1 - t/3 + 11t^2/45 - 191t^3/945 + 2497t^4/14175,
+//   Q = 1 - 2t/3 + 8t^2/15 - 16t^3/35 + 128t^4/315 (the volume kernel takes it
+//   times 2 / (gamma - 1) from PhysDev::ec_q), 1 / (1 + t) = 1 - t + t^2 - t^3 + t^4.
 template <typename R>
 __device__ __forceinline__ R logmean_G(R t) {
   return R(1) + t * (R(-1.0 / 3.0) + t * (R(11.0 / 45.0) + t * (R(-191.0 / 945.0) + t * R(2497.0 / 14175.0))));
-}
-template <typename R>
-__device__ __forceinline__ R logmean_Q(R t) {
-  return R(1) + t * (R(-2.0 / 3.0) + t * (R(8.0 / 15.0) + t * (R(-16.0 / 35.0) + t * R(128.0 / 315.0))));
-}
-template <typename R>
-__device__ __forceinline__ R inv_one_plus(R t) {
-  return R(1) + t * (R(-1) + t * (R(1) + t * (R(-1) + t)));
 }
 
 // exterior state of an inflow (code -2: the prescribed state) or outflow
@@ -1604,8 +1601,8 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
       sQ[4 * n3 + ts] = R(8) * beta * q.p;
       sQ[5 * n3 + ts] = beta;
       sQ[6 * n3 + ts] = q.u * q.u + q.v * q.v + q.w * q.w;
-      sQ[7 * n3 + ts] = R(2) * pf * irho;  // 1 / beta
-      sQ[8 * n3 + ts] = irho;
+      sQ[7 * n3 + ts] = pf * irho;      // 1 / (2 beta)
+      sQ[8 * n3 + ts] = R(0.5) * irho;  // 1 / (2 rho)
     } else if (!kg) {
       sQ[5 * n3 + ts] = q.h;
     } else {
@@ -1651,28 +1648,33 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
       const R Sa0 = A.a0 + B.a0, Sa1 = A.a1 + B.a1, Sa2 = A.a2 + B.a2;
       const R ua = Su * Sa0 + Sv * Sa1 + Sw * Sa2;  // 4 {u}.{a}
       if constexpr (EC) {
-        // rho_ln = Sr G / 2; 1 / beta_ln = Sib Q / 2; 1 / (bA + bB) = Sib Rb / 4
-        const R Dr = A.rho - B.rho, Db = A.hh - B.hh, Sib = A.ib + B.ib;
-        const R tr = R(0.25) * Dr * Dr * (A.irh * B.irh);
-        const R tb = R(0.25) * Db * Db * (A.ib * B.ib);
+        // nodes hold ib = 1 / (2 beta) and irh = 1 / (2 rho), so that with
+        // Sh = ib_A + ib_B (half the sum of the inverse temperatures):
+        //   rho_ln = Sr G / 2;  rgm1 / beta_ln = Sh Qg / 2 (Qg = 2 rgm1 Q);
+        //   1 / (bA + bB) = Sh Rh / 2 (Rh = Rb / 2)
+        const R Dr = A.rho - B.rho, Db = A.hh - B.hh, Sh = A.ib + B.ib;
+        const R tr = Dr * Dr * (A.irh * B.irh);
+        const R tb = Db * Db * (A.ib * B.ib);
         const R G = tr < LogMeanCut<R>::v ? logmean_G<R>(tr) : R(2) * Dr / (Sr * log1p(Dr / B.rho));
-        R Q, Rb;
+        R Qg, Rh;
         if (tb < LogMeanCut<R>::v) {
-          Q = logmean_Q<R>(tb);
-          Rb = inv_one_plus<R>(tb);
+          auto qc = [&](int c) { return cR<R>(ph.ec_q[c], ph.f32c.ec_q[c]); };
+          Qg = qc(0) + tb * (qc(1) + tb * (qc(2) + tb * (qc(3) + tb * qc(4))));
+          Rh = R(0.5) + tb * (R(-0.5) + tb * (R(0.5) + tb * (R(-0.5) + tb * R(0.5))));
         } else {
-          Q = R(2) * log1p(Db / B.hh) / (Db * Sib);
-          Rb = R(4) / (Sib * (A.hh + B.hh));
+          Qg = R(2) * cR<R>(ph.rgm1, ph.f32c.rgm1) * log1p(Db / B.hh) / (Db * Sh);
+          Rh = R(1) / (Sh * (A.hh + B.hh));
         }
         const R mf = Sr * G * ua;                 // 8 F_rho
-        const R Spt = R(0.25) * Sib * Rb * Sp;    // 8 (p~ - p_ref)
+        const R Spt = Sh * Rh * Sp;               // 8 (p~ - p_ref)
         F[0] = mf;
         F[1] = mf * Su + Spt * Sa0;               // 16 F_m
         F[2] = mf * Sv + Spt * Sa1;
         F[3] = mf * Sw + Spt * Sa2;
         // 16 F_E = 2 mf (1 / (2 (gamma-1) beta_ln) + |{u}|^2 - {|u|^2} / 2) + 4 p~ (4 {u}.{a})
-        const R X = R(0.25) * (Sib * Q * cR<R>(ph.rgm1, ph.f32c.rgm1) + Su * Su + Sv * Sv + Sw * Sw - A.p2 - B.p2);
-        F[4] = R(2) * mf * X + (R(0.5) * Spt + R(4) * cR<R>(ph.p_ref, ph.f32c.p_ref)) * ua;
+        //        = mf X / 2 + (Spt / 2 + 4 p_ref) (4 {u}.{a})
+        const R X = Sh * Qg + Su * Su + Sv * Sv + Sw * Sw - A.p2 - B.p2;
+        F[4] = R(0.5) * mf * X + (R(0.5) * Spt + R(4) * cR<R>(ph.p_ref, ph.f32c.p_ref)) * ua;
       } else {
         const R mf = Sr * ua;                     // 8 F0
         F[0] = mf;
