@@ -925,8 +925,9 @@ k_lift(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
     sW[p] = u; sW[n3 + p] = v; sW[2 * n3 + p] = w; sW[3 * n3 + p] = T;
   }
   __syncthreads();
-  // W* - W at the six faces (BR1 average with the neighbour, or the mirror
-  // state at a slip wall)
+  // 2 (W* - W) at the six faces (BR1 average with the neighbour, or the
+  // mirror state at a slip wall); the factor 1/2 goes with the 1/w of the
+  // surface correction
   for (int t = tid; t < 6 * n2; t += n3) {
     const int l = t / n2, ab = t - l * n2, a = ab % n, b = ab / n;
     const int q = fnode<N>(l, a, b);
@@ -940,17 +941,15 @@ k_lift(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
         velocity_temperature32(load_prim32_full(m.W32, S, gn, ph), ph, u, v, w, T);
       else
         velocity_temperature<R>(U[gn], U[S + gn], U[2 * S + gn], U[3 * S + gn], U[4 * S + gn], ph, u, v, w, T);
-      d0 = R(0.5) * (u - Wo0); d1 = R(0.5) * (v - Wo1); d2 = R(0.5) * (w - Wo2);
-      d3 = R(0.5) * (T - Wo3);
+      d0 = u - Wo0; d1 = v - Wo1; d2 = w - Wo2; d3 = T - Wo3;
     } else if (nb <= -16) {
       // halo face: the remote element's trace from the halo buffer
       const double* src = m.halo_U + (size_t)(-16 - nb) * 5 * n2 + ab;
       R u, v, w, T;
       velocity_temperature<R>(src[0], src[n2], src[2 * n2], src[3 * n2], src[4 * n2], ph, u, v, w, T);
-      d0 = R(0.5) * (u - Wo0); d1 = R(0.5) * (v - Wo1); d2 = R(0.5) * (w - Wo2);
-      d3 = R(0.5) * (T - Wo3);
+      d0 = u - Wo0; d1 = v - Wo1; d2 = w - Wo2; d3 = T - Wo3;
     } else if (nb != -1) {
-      // inflow / outflow: W* - W = (W(exterior) - W) / 2
+      // inflow / outflow: 2 (W* - W) = W(exterior) - W
       const size_t gq = (size_t)e * n3 + q;
       double Ui[5], Ub[5];
 #pragma unroll
@@ -958,18 +957,17 @@ k_lift(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
       ghost_state(ph, nb, Ui, Ub);
       R u, v, w, T;
       velocity_temperature<R>(Ub[0], Ub[1], Ub[2], Ub[3], Ub[4], ph, u, v, w, T);
-      d0 = R(0.5) * (u - Wo0); d1 = R(0.5) * (v - Wo1); d2 = R(0.5) * (w - Wo2);
-      d3 = R(0.5) * (T - Wo3);
+      d0 = u - Wo0; d1 = v - Wo1; d2 = w - Wo2; d3 = T - Wo3;
     } else {
-      // mirror: W* - W = -(u . n) n, T unchanged (n: own outward unit normal)
+      // mirror: 2 (W* - W) = -2 (u . n) n, T unchanged (n: own outward unit normal)
       const size_t gq = (size_t)e * n3 + q;
       const int dir = l >> 1;
       const R a0 = m.Ja[(size_t)(dir * 3 + 0) * S + gq], a1 = m.Ja[(size_t)(dir * 3 + 1) * S + gq],
               a2 = m.Ja[(size_t)(dir * 3 + 2) * S + gq];
       const R is = R(1) / sqrt(a0 * a0 + a1 * a1 + a2 * a2);
       const R nx = a0 * is, ny = a1 * is, nz = a2 * is;  // sign irrelevant: (u.n) n
-      const R un = Wo0 * nx + Wo1 * ny + Wo2 * nz;
-      d0 = -un * nx; d1 = -un * ny; d2 = -un * nz; d3 = R(0);
+      const R un2 = R(-2) * (Wo0 * nx + Wo1 * ny + Wo2 * nz);
+      d0 = un2 * nx; d1 = un2 * ny; d2 = un2 * nz; d3 = R(0);
     }
     sC[(l * 4 + 0) * n2 + ab] = d0; sC[(l * 4 + 1) * n2 + ab] = d1;
     sC[(l * 4 + 2) * n2 + ab] = d2; sC[(l * 4 + 3) * n2 + ab] = d3;
@@ -1006,16 +1004,18 @@ k_lift(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
   }
   // surface corrections of the reference-space gradient: (W* - W) (+-1 / w)
   // at the first and last node of each line (with n s = +-Ja^dir they give
-  // the (W* - W) (n s)_d / w terms of the physical gradient)
+  // the (W* - W) (n s)_d / w terms of the physical gradient); sC holds
+  // 2 (W* - W), so the weights are shw = 1 / (2 w)
+  const R shw0 = R(0.5) * siw[0], shwN = R(0.5) * siw[N];
   auto surf = [&](int dir, int l, int ab, R sgn_iw) {
 #pragma unroll
     for (int v = 0; v < 4; ++v) dW[dir][v] += sgn_iw * sC[(l * 4 + v) * n2 + ab];
   };
   // (one branch per direction: a warp holds nodes of both end faces of the
   // lines along xi, and the masked lanes of a branch cost as much as active ones)
-  if (i == 0 || i == N) surf(0, i == 0 ? 0 : 1, j + n * k, i == 0 ? -siw[0] : siw[N]);
-  if (j == 0 || j == N) surf(1, j == 0 ? 2 : 3, i + n * k, j == 0 ? -siw[0] : siw[N]);
-  if (k == 0 || k == N) surf(2, k == 0 ? 4 : 5, i + n * j, k == 0 ? -siw[0] : siw[N]);
+  if (i == 0 || i == N) surf(0, i == 0 ? 0 : 1, j + n * k, i == 0 ? -shw0 : shwN);
+  if (j == 0 || j == N) surf(1, j == 0 ? 2 : 3, i + n * k, j == 0 ? -shw0 : shwN);
+  if (k == 0 || k == N) surf(2, k == 0 ? 4 : 5, i + n * j, k == 0 ? -shw0 : shwN);
   // own metrics (loaded here, after the contractions, to keep them out of
   // the registers live across those)
   R ja[9];
@@ -1036,15 +1036,16 @@ k_lift(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
     mu = sutherland<R>(ph, sW[3 * n3 + p]);
     kc = mu * cR<R>(ph.cp_Pr, ph.f32c.cp_Pr);
   }
+  // symmetric stress: tau_ab = mu (q_ba + q_ab) - (2/3) mu div delta_ab
   const R div = q[0][0] + q[1][1] + q[2][2];
+  const R mdiv = R(2.0 / 3.0) * mu * div, mu2 = R(2) * mu;
   R tau[3][3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b) tau[a][b] = mu * (q[b][a] + q[a][b]);
-  tau[0][0] -= R(2.0 / 3.0) * mu * div;
-  tau[1][1] -= R(2.0 / 3.0) * mu * div;
-  tau[2][2] -= R(2.0 / 3.0) * mu * div;
+  tau[0][0] = mu2 * q[0][0] - mdiv;
+  tau[1][1] = mu2 * q[1][1] - mdiv;
+  tau[2][2] = mu2 * q[2][2] - mdiv;
+  tau[0][1] = tau[1][0] = mu * (q[0][1] + q[1][0]);
+  tau[0][2] = tau[2][0] = mu * (q[0][2] + q[2][0]);
+  tau[1][2] = tau[2][1] = mu * (q[1][2] + q[2][1]);
   const R uu = sW[p], vv = sW[n3 + p], ww = sW[2 * n3 + p];
   R Fv[3][4];
 #pragma unroll
