@@ -42,7 +42,10 @@ struct dg_ctx {
   bool w32_of_U = false;
   // FP64 viscous form: primitives [6][S] formed by the lifting kernel for the
   // face and volume kernels of the same evaluation
-  double* W64 = nullptr;
+  double* W64 = nullptr;  // FP64 viscous form: primitives [7][S]; w64_of_U says they are those of U
+  bool w64_of_U = false;
+  double* JaJ = nullptr;  // FP64 viscous: [9][S] Ja / J
+  double* Mj = nullptr;   // FP64 viscous: [6][S] (Ja Ja^T) / J
   double* wm_t = nullptr;  // wall-law warm start per wall node (NaN: none yet)
   // partitioned meshes: halo buffers [n_halo][5][n2] (state traces, FP64) and
   // [n_halo][4][n2] (viscous-flux traces, flux type), received and sent
@@ -133,7 +136,7 @@ void free_all(dg_ctx* c) {
   void* ptrs[] = {c->U, c->dU, c->io, c->io2, c->Ja, c->invJ, c->fgeo, c->nbr, c->elem_face, c->faces,
                   c->ws_elem, c->ws_lag, c->Rv, c->Gf, c->Fs, c->tau, c->status,
                   c->gUf, c->gGf, c->gWf, c->gUs, c->gtheta, c->wq, c->ro_ckpt, c->ro_stage, c->ro_work,
-                  c->ro_scalar, c->wJ, c->W32, c->W64, c->halo_U, c->send_U, c->halo_G, c->send_G, c->wm_t};
+                  c->ro_scalar, c->wJ, c->W32, c->W64, c->JaJ, c->Mj, c->halo_U, c->send_U, c->halo_G, c->send_G, c->wm_t};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -176,15 +179,24 @@ int launch(dg_ctx* c, const double* Uin, int mode, double* Out, double A, double
   a.W32 = c->W32;
   a.w32_valid = (a.fp32 && Uin == c->U && c->w32_of_U) ? 1 : 0;
   a.W64 = c->W64;
+  a.w64_valid = (c->W64 && !a.fp32 && Uin == c->U && c->w64_of_U) ? 1 : 0;
+  a.JaJ = c->JaJ; a.Mj = c->Mj;
   a.wm_t = c->wm_t;
   int rc = dg::run_operator(a, c->ph, c->stream);
   if (rc != 0) {
     c->w32_of_U = false;
+    c->w64_of_U = false;
     return cuda_fail(c, (cudaError_t)rc, "kernel launch");
   }
   // the FP32 primitives now belong to the stage's output (mode 1) or input
   if (a.fp32 && (phase & 4)) c->w32_of_U = mode == 1 ? (Uout == c->U) : (Uin == c->U);
   else if (a.fp32 && (phase & 2)) c->w32_of_U = (Uin == c->U);
+  // the FP64 primitives: those of the input once phase 2 ran, stale once a
+  // stage has updated the state in place
+  if (!a.fp32 && c->W64 && c->opts.viscous) {
+    if ((phase & 4) && mode == 1 && Uout == c->U) c->w64_of_U = false;
+    else if (phase & 2) c->w64_of_U = (Uin == c->U);
+  }
   return DG_OK;
 }
 
@@ -297,6 +309,7 @@ int noalloc_args(dg_ctx* c, const double* U, double* Ut, OpArgs* a, const PhysDe
   a->n_halo = c->geo.n_halo;
   a->fp32 = c->opts.precision == DG_FP32_MIXED;
   a->Ja = c->Ja; a->invJ = c->invJ; a->fgeo = c->fgeo; a->nbr = c->nbr; a->elem_face = c->elem_face;
+  a->JaJ = c->JaJ; a->Mj = c->Mj;  // geometry, owned by the context
   a->faces = c->faces; a->ws_elem = c->ws_elem; a->ws_lag = c->ws_lag;
   a->D = c->geo.basis.D.data(); a->w = c->geo.basis.w.data();
   a->Uin = U; a->status = c->status;
@@ -427,7 +440,11 @@ int dg_init_mesh(dg_ctx** out, const dg_mesh_desc* m, const dg_phys* p, const dg
   chk(cudaMalloc(&c->Gf, (o->viscous ? 24 * (size_t)c->K * n2 : 1) * rs));
   chk(cudaMalloc(&c->Fs, (ph.fs_diff ? 10 : 5) * (size_t)c->F * n2 * rs));
   if (f32) chk(alloc(&c->W32, 6 * S));
-  if (!f32 && o->viscous) chk(alloc(&c->W64, 6 * S));
+  if (!f32 && o->viscous) {
+    chk(alloc(&c->W64, 7 * S));
+    chk(alloc(&c->JaJ, 9 * S));
+    chk(alloc(&c->Mj, 6 * S));
+  }
   if (c->geo.n_wall > 0) {
     chk(alloc(&c->wm_t, (size_t)c->geo.n_wall * n2));
     chk(cudaMemset(c->wm_t, 0xff, (size_t)c->geo.n_wall * n2 * sizeof(double)));  // NaN: no guess yet
@@ -455,6 +472,25 @@ int dg_init_mesh(dg_ctx** out, const dg_mesh_desc* m, const dg_phys* p, const dg
     } else {
       chk(cudaMemcpy(c->Ja, ja.data(), ja.size() * sizeof(double), cudaMemcpyHostToDevice));
       chk(cudaMemcpy(c->invJ, ij.data(), ij.size() * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    if (c->JaJ) {
+      // the lifting kernel's metric products: Ja^n_d / J (reference to
+      // physical gradient) and the symmetric (Ja^n . Ja^m) / J (the heat flux
+      // projected on Ja^n straight from the reference-space gradient of T),
+      // M in the order 00, 11, 22, 01, 02, 12
+      std::vector<double> jj(9 * S), mj(6 * S);
+      static const int mn[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+      for (size_t x = 0; x < S; ++x) {
+        for (int cc = 0; cc < 9; ++cc) jj[cc * S + x] = ja[cc * S + x] * ij[x];
+        for (int r = 0; r < 6; ++r) {
+          const int a = mn[r][0], b = mn[r][1];
+          double dot = 0.0;
+          for (int d = 0; d < 3; ++d) dot += ja[(a * 3 + d) * S + x] * ja[(b * 3 + d) * S + x];
+          mj[r * S + x] = dot * ij[x];
+        }
+      }
+      chk(cudaMemcpy(c->JaJ, jj.data(), jj.size() * sizeof(double), cudaMemcpyHostToDevice));
+      chk(cudaMemcpy(c->Mj, mj.data(), mj.size() * sizeof(double), cudaMemcpyHostToDevice));
     }
   }
   chk(cudaMemcpy(c->fgeo, c->geo.fgeo.data(), c->geo.fgeo.size() * sizeof(double), cudaMemcpyHostToDevice));
@@ -541,6 +577,7 @@ int dg_set_state(dg_ctx* c, const double* U, int on_device) {
   }
   c->state_set = true;
   c->w32_of_U = false;
+  c->w64_of_U = false;
   // a new state starts the wall-law solves afresh (results then depend only
   // on the sequence of evaluations since the last dg_set_state)
   if (c->wm_t) {
@@ -918,6 +955,9 @@ int dg_rk_steps_graph(dg_ctx* c, double t, double dt, int nsteps) {
     cudaStream_t user = c->stream;
     c->profiling = false;
     c->stream = c->cap_stream;
+    // every replay starts from a state its previous step updated: the first
+    // stage must form the FP64 primitives
+    c->w64_of_U = false;
     e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
     int rc = DG_OK;
     if (e == cudaSuccess)
@@ -941,6 +981,7 @@ int dg_rk_steps_graph(dg_ctx* c, double t, double dt, int nsteps) {
     e = cudaGraphLaunch(c->step_graph, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "dg_rk_steps_graph: launch");
   }
+  if (nsteps > 0) c->w64_of_U = false;  // the state changed under the stored primitives
   return DG_OK;
 }
 

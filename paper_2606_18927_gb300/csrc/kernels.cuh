@@ -2,8 +2,10 @@
 //
 // One operator evaluation (paper Sec. 2.2 / Sec. 4: split-form DGSEM on LGL
 // nodes; Sec. 3: equilibrium wall model) launches:
-//   k_lift      one CTA per element: primitives (in FP64 kept for the face
-//               and volume kernels), BR1 lifting of grad(u,v,w,T), viscous
+//   k_prim64    FP64 viscous form: the primitives (rho, u, v, w, p', h, T) of
+//               the input state, stored for the three kernels below;
+//   k_lift      one CTA per element: primitives (FP64: read from k_prim64's
+//               array), BR1 lifting of grad(u,v,w,T), viscous
 //               flux, its weak-form volume divergence R_v, and the element's
 //               own outward viscous flux at its six faces (FP64, N = 7: line
 //               contractions in even/odd form, LineEO);
@@ -89,8 +91,11 @@ struct MeshDev {
   const int* ws_elem;    // [n_wall*n2]
   const double* ws_lag;  // [n_wall*n2*3*n]
   float* W32;            // FP32-mixed form: [6][K*n3] primitives of the input state (null in FP64)
-  double* W64;           // FP64 viscous form: [6][K*n3] primitives (rho, u, v, w, p - p_ref, h) of the
-                         // input state, written by k_lift, read by k_face and k_volume (null: formed per use)
+  double* W64;           // FP64 viscous form: [7][K*n3] primitives (rho, u, v, w, p - p_ref, h, T) of the
+                         // input state, stored by k_prim64, read by k_lift, k_face and k_volume (null: formed
+                         // per use)
+  const double* JaJ;     // FP64 viscous form: [9][K*n3] Ja / J (dir*3+comp)
+  const double* Mj;      // FP64 viscous form: [6][K*n3] (Ja Ja^T) / J (00, 11, 22, 01, 02, 12)
   double* wm_t;          // [n_wall*n2] last wall-law solution per wall node (warm start; may be null)
 };
 
@@ -272,12 +277,11 @@ __device__ __forceinline__ Prim<float> unshift32(Prim<float> q, const PhysDev& p
   return q;
 }
 
-// (u, v, w, T) for the lifting, in the flux type (same pressure recovery).
 // FP64 primitives and the temperature T = p / (rho R) (from the unshifted p).
-// Not inlined: one compiled body serves the lifting kernel, which stores its
-// result for the face and volume kernels, and the halo-face kernel, which
-// forms the same values for a remote trace; they then agree bitwise whatever
-// the surrounding code lets the compiler contract.
+// Not inlined: one compiled body serves k_prim64, which stores them for the
+// lifting, face and volume kernels, and the kernels that form them for a
+// remote trace (or, without the stored array, per use); all then agree
+// bitwise whatever the surrounding code lets the compiler contract.
 static __device__ __noinline__ Prim<double> primitive_T(const double U0, const double U1, const double U2,
                                                  const double U3, const double U4, const PhysDev& ph, double& T) {
   Prim<double> q;
@@ -292,6 +296,22 @@ static __device__ __noinline__ Prim<double> primitive_T(const double U0, const d
 
 __device__ __forceinline__ Prim<double> load_prim64(const double* __restrict__ W, size_t S, size_t g) {
   return Prim<double>{W[g], W[S + g], W[2 * S + g], W[3 * S + g], W[4 * S + g], W[5 * S + g]};
+}
+
+__device__ __forceinline__ void store_prim64(double* __restrict__ W, size_t S, size_t g, const Prim<double>& q,
+                                             double T) {
+  W[g] = q.rho; W[S + g] = q.u; W[2 * S + g] = q.v; W[3 * S + g] = q.w;
+  W[4 * S + g] = q.p; W[5 * S + g] = q.h; W[6 * S + g] = T;
+}
+
+// the primitives of the input state, stored for the operator's kernels (FP64
+// viscous form); run before the lifting kernel whenever they are stale
+static __global__ void k_prim64(long long S, const double* __restrict__ U, const PhysDev ph, double* __restrict__ W) {
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < S; g += (long long)gridDim.x * blockDim.x) {
+    double T;
+    const Prim<double> q = primitive_T(U[g], U[S + g], U[2 * S + g], U[3 * S + g], U[4 * S + g], ph, T);
+    store_prim64(W, (size_t)S, (size_t)g, q, T);
+  }
 }
 
 template <typename R>
@@ -913,12 +933,8 @@ k_lift(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
     if constexpr (std::is_same<R, float>::value) {
       velocity_temperature32(load_prim32_full(m.W32, S, g, ph), ph, u, v, w, T);
     } else if (m.W64) {
-      // the FP64 primitives of the node, kept for the face and volume kernels
-      double Td;
-      const Prim<double> q = primitive_T(U[g], U[S + g], U[2 * S + g], U[3 * S + g], U[4 * S + g], ph, Td);
-      m.W64[g] = q.rho; m.W64[S + g] = q.u; m.W64[2 * S + g] = q.v; m.W64[3 * S + g] = q.w;
-      m.W64[4 * S + g] = q.p; m.W64[5 * S + g] = q.h;
-      u = q.u; v = q.v; w = q.w; T = Td;
+      // the FP64 primitives k_prim64 stored for this evaluation
+      u = m.W64[S + g]; v = m.W64[2 * S + g]; w = m.W64[3 * S + g]; T = m.W64[6 * S + g];
     } else {
       velocity_temperature<R>(U[g], U[S + g], U[2 * S + g], U[3 * S + g], U[4 * S + g], ph, u, v, w, T);
     }
@@ -937,16 +953,29 @@ k_lift(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
     if (nb >= 0) {
       const size_t gn = (size_t)nb * n3 + fnode<N>(l ^ 1, a, b);
       R u, v, w, T;
-      if constexpr (std::is_same<R, float>::value)
+      if constexpr (std::is_same<R, float>::value) {
         velocity_temperature32(load_prim32_full(m.W32, S, gn, ph), ph, u, v, w, T);
-      else
+      } else if (m.W64) {
+        u = m.W64[S + gn]; v = m.W64[2 * S + gn]; w = m.W64[3 * S + gn]; T = m.W64[6 * S + gn];
+      } else {
         velocity_temperature<R>(U[gn], U[S + gn], U[2 * S + gn], U[3 * S + gn], U[4 * S + gn], ph, u, v, w, T);
+      }
       d0 = u - Wo0; d1 = v - Wo1; d2 = w - Wo2; d3 = T - Wo3;
     } else if (nb <= -16) {
       // halo face: the remote element's trace from the halo buffer
       const double* src = m.halo_U + (size_t)(-16 - nb) * 5 * n2 + ab;
       R u, v, w, T;
-      velocity_temperature<R>(src[0], src[n2], src[2 * n2], src[3 * n2], src[4 * n2], ph, u, v, w, T);
+      if constexpr (std::is_same<R, double>::value) {
+        if (m.W64) {
+          // as the remote element's stored primitives (same function)
+          const Prim<double> q = primitive_T(src[0], src[n2], src[2 * n2], src[3 * n2], src[4 * n2], ph, T);
+          u = q.u; v = q.v; w = q.w;
+        } else {
+          velocity_temperature<R>(src[0], src[n2], src[2 * n2], src[3 * n2], src[4 * n2], ph, u, v, w, T);
+        }
+      } else {
+        velocity_temperature<R>(src[0], src[n2], src[2 * n2], src[3 * n2], src[4 * n2], ph, u, v, w, T);
+      }
       d0 = u - Wo0; d1 = v - Wo1; d2 = w - Wo2; d3 = T - Wo3;
     } else if (nb != -1) {
       // inflow / outflow: 2 (W* - W) = W(exterior) - W
@@ -1016,50 +1045,89 @@ k_lift(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
   if (i == 0 || i == N) surf(0, i == 0 ? 0 : 1, j + n * k, i == 0 ? -shw0 : shwN);
   if (j == 0 || j == N) surf(1, j == 0 ? 2 : 3, i + n * k, j == 0 ? -shw0 : shwN);
   if (k == 0 || k == N) surf(2, k == 0 ? 4 : 5, i + n * j, k == 0 ? -shw0 : shwN);
-  // own metrics (loaded here, after the contractions, to keep them out of
-  // the registers live across those)
-  R ja[9];
-#pragma unroll
-  for (int c = 0; c < 9; ++c) ja[c] = m.Ja[(size_t)c * S + g];
-  const R iJ = m.invJ[g];
-  // physical gradients q[d][v] = (1/J) sum_dir Ja^dir_d dW_dir
-  R q[3][4];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const R j0 = iJ * ja[0 * 3 + d], j1 = iJ * ja[1 * 3 + d], j2 = iJ * ja[2 * 3 + d];
-#pragma unroll
-    for (int v = 0; v < 4; ++v) q[d][v] = j0 * dW[0][v] + j1 * dW[1][v] + j2 * dW[2][v];
-  }
   // viscous flux Fv_d = (0, tau_1d, tau_2d, tau_3d, tau_jd u_j + k dT/dx_d)
   R mu = cR<R>(ph.mu, ph.f32c.mu), kc = cR<R>(ph.kcond, ph.f32c.kcond);
   if (ph.sutherland) {
     mu = sutherland<R>(ph, sW[3 * n3 + p]);
     kc = mu * cR<R>(ph.cp_Pr, ph.f32c.cp_Pr);
   }
-  // symmetric stress: tau_ab = mu (q_ba + q_ab) - (2/3) mu div delta_ab
-  const R div = q[0][0] + q[1][1] + q[2][2];
-  const R mdiv = R(2.0 / 3.0) * mu * div, mu2 = R(2) * mu;
-  R tau[3][3];
-  tau[0][0] = mu2 * q[0][0] - mdiv;
-  tau[1][1] = mu2 * q[1][1] - mdiv;
-  tau[2][2] = mu2 * q[2][2] - mdiv;
-  tau[0][1] = tau[1][0] = mu * (q[0][1] + q[1][0]);
-  tau[0][2] = tau[2][0] = mu * (q[0][2] + q[2][0]);
-  tau[1][2] = tau[2][1] = mu * (q[1][2] + q[2][1]);
   const R uu = sW[p], vv = sW[n3 + p], ww = sW[2 * n3 + p];
-  R Fv[3][4];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    Fv[d][0] = tau[0][d]; Fv[d][1] = tau[1][d]; Fv[d][2] = tau[2][d];
-    Fv[d][3] = tau[0][d] * uu + tau[1][d] * vv + tau[2][d] * ww + kc * q[d][3];
-  }
   // contravariant G^dir = sum_d Ja^dir_d Fv_d
   R G[3][4];
+  // symmetric stress: tau_ab = mu (q_ba + q_ab) - (2/3) mu div delta_ab
+  auto stress = [&](const R q[3][4], R tau[3][3]) {
+    const R div = q[0][0] + q[1][1] + q[2][2];
+    const R mdiv = R(2.0 / 3.0) * mu * div, mu2 = R(2) * mu;
+    tau[0][0] = mu2 * q[0][0] - mdiv;
+    tau[1][1] = mu2 * q[1][1] - mdiv;
+    tau[2][2] = mu2 * q[2][2] - mdiv;
+    tau[0][1] = tau[1][0] = mu * (q[0][1] + q[1][0]);
+    tau[0][2] = tau[2][0] = mu * (q[0][2] + q[2][0]);
+    tau[1][2] = tau[2][1] = mu * (q[1][2] + q[2][1]);
+  };
+  if constexpr (std::is_same<R, double>::value) {
+    // FP64: the metric products come precomputed (metrics are fixed, the
+    // FP64 pipe is the bound).  Velocity gradients q[d][c] = du_c/dx_d =
+    // sum_dir (Ja^dir_d / J) dW_dir; the energy row as
+    //   G^dir_E = sum_c u_c G^dir_c + k (Ja^dir . grad T),
+    //   Ja^dir . grad T = sum_m ((Ja^dir . Ja^m) / J) dT_m
+    R q[3][4], hT[3];
+    {
+      R jj[9];
 #pragma unroll
-  for (int dir = 0; dir < 3; ++dir)
+      for (int c = 0; c < 9; ++c) jj[c] = m.JaJ[(size_t)c * S + g];
 #pragma unroll
-    for (int v = 0; v < 4; ++v)
-      G[dir][v] = ja[dir * 3 + 0] * Fv[0][v] + ja[dir * 3 + 1] * Fv[1][v] + ja[dir * 3 + 2] * Fv[2][v];
+      for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int v = 0; v < 3; ++v) q[d][v] = jj[0 * 3 + d] * dW[0][v] + jj[1 * 3 + d] * dW[1][v] + jj[2 * 3 + d] * dW[2][v];
+      R mm[6];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) mm[c] = m.Mj[(size_t)c * S + g];
+      hT[0] = mm[0] * dW[0][3] + mm[3] * dW[1][3] + mm[4] * dW[2][3];
+      hT[1] = mm[3] * dW[0][3] + mm[1] * dW[1][3] + mm[5] * dW[2][3];
+      hT[2] = mm[4] * dW[0][3] + mm[5] * dW[1][3] + mm[2] * dW[2][3];
+    }
+    R tau[3][3];
+    stress(q, tau);
+    R ja[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) ja[c] = m.Ja[(size_t)c * S + g];
+#pragma unroll
+    for (int dir = 0; dir < 3; ++dir) {
+#pragma unroll
+      for (int v = 0; v < 3; ++v)
+        G[dir][v] = ja[dir * 3 + 0] * tau[v][0] + ja[dir * 3 + 1] * tau[v][1] + ja[dir * 3 + 2] * tau[v][2];
+      G[dir][3] = uu * G[dir][0] + vv * G[dir][1] + ww * G[dir][2] + kc * hT[dir];
+    }
+  } else {
+    // own metrics (loaded here, after the contractions, to keep them out of
+    // the registers live across those)
+    R ja[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) ja[c] = m.Ja[(size_t)c * S + g];
+    const R iJ = m.invJ[g];
+    // physical gradients q[d][v] = (1/J) sum_dir Ja^dir_d dW_dir
+    R q[3][4];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const R j0 = iJ * ja[0 * 3 + d], j1 = iJ * ja[1 * 3 + d], j2 = iJ * ja[2 * 3 + d];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) q[d][v] = j0 * dW[0][v] + j1 * dW[1][v] + j2 * dW[2][v];
+    }
+    R tau[3][3];
+    stress(q, tau);
+    R Fv[3][4];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      Fv[d][0] = tau[0][d]; Fv[d][1] = tau[1][d]; Fv[d][2] = tau[2][d];
+      Fv[d][3] = tau[0][d] * uu + tau[1][d] * vv + tau[2][d] * ww + kc * q[d][3];
+    }
+#pragma unroll
+    for (int dir = 0; dir < 3; ++dir)
+#pragma unroll
+      for (int v = 0; v < 4; ++v)
+        G[dir][v] = ja[dir * 3 + 0] * Fv[0][v] + ja[dir * 3 + 1] * Fv[1][v] + ja[dir * 3 + 2] * Fv[2][v];
+  }
   // own outward viscous flux at face nodes: Gf[e][l][v][ab] = +-G^{l/2}
   auto gface = [&](int l, int ab, R sgn) {
     R* dst = Gf + ((size_t)e * 6 + l) * 4 * n2 + ab;
@@ -1152,9 +1220,9 @@ k_face(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
     }
     riemann_d<float>(ph, unshift32(A, ph), unshift32(B, ph), dU, nx, ny, nz, F);
   } else {
-    // both sides' FP64 primitives: from the lifting kernel's array where it
-    // ran, else (and for a remote trace) by primitive_T, whose one compiled
-    // body also wrote that array
+    // both sides' FP64 primitives: from the stored array in the viscous form,
+    // else (and for a remote trace) by primitive_T, whose one compiled body
+    // also writes that array
     Prim<double> A, B;
     double dU[5] = {0.0, 0.0, 0.0, 0.0, 0.0}, T;
     const bool llf = ph.surf_flux == 1;

@@ -43,9 +43,15 @@ struct OpArgs {
   // (mode 1) leaves the primitives of Uout in W32.
   float* W32;
   int w32_valid;
-  // FP64 viscous form: [6][K n^3] primitives of Uin, written by the lifting
-  // kernel for the face and volume kernels (null: each kernel forms its own)
+  // FP64 viscous form: [7][K n^3] primitives of Uin (null: each kernel forms
+  // its own); w64_valid = 1 when they are already those of Uin (else k_prim64
+  // forms them before the lifting kernel)
   double* W64;
+  int w64_valid;
+  // FP64 viscous form: the lifting kernel's metric products, [9][K n^3] Ja / J
+  // and [6][K n^3] (Ja Ja^T) / J (order 00, 11, 22, 01, 02, 12)
+  const double* JaJ;
+  const double* Mj;
   double* wm_t;  // wall-law warm-start values per wall node (null: cold solves)
   // partitioned meshes: n_halo halo faces (the last faces), remote traces in
   // halo_U / halo_G, local traces packed into send_U / send_G.  phase selects

@@ -39,6 +39,8 @@ static int run_typed(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {
   m.W32 = std::is_same<R, float>::value ? a.W32 : nullptr;
   // written by the lifting kernel, so only when it runs
   m.W64 = std::is_same<R, double>::value && ph.viscous ? a.W64 : nullptr;
+  m.JaJ = a.JaJ; m.Mj = a.Mj;
+  if (std::is_same<R, double>::value && ph.viscous && (!a.JaJ || !a.Mj)) return (int)cudaErrorInvalidValue;
   m.wm_t = a.wm_t;
   m.n_halo = a.n_halo; m.halo_U = a.halo_U; m.halo_G = static_cast<const R*>(a.halo_G);
   const Tables<N> tab = make_tables<N>(a.D, a.w);
@@ -88,6 +90,12 @@ static int run_typed(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {
       cudaEventRecord(a.join, a.side);
     }
     if (a.ev) cudaEventRecord(a.ev[0], s);
+    // the FP64 primitives of the input (timed with the lifting kernel, their
+    // first reader; kept between evaluations of an unchanged state)
+    if (m.W64 && !a.w64_valid) {
+      const long long S = (long long)a.K * n3;
+      k_prim64<<<(unsigned)std::min<long long>((S + 255) / 256, 152 * 16), 256, 0, s>>>(S, a.Uin, ph, m.W64);
+    }
     if (ph.viscous) k_lift<N, R><<<a.K, n3, smem_lift, s>>>(a.Uin, m, ph, tab, Rv, Gf);
     if (a.ev) cudaEventRecord(a.ev[1], s);
     if (a.n_halo > 0 && a.send_G && ph.viscous)
