@@ -46,17 +46,22 @@ NCU_TRAFFIC_PER_DOF = {("k_volume", "fp64", 7): 592.0e6 / 2097152,
 MIXED_VOLUME_BYTES_PER_DOF = lambda N: 40 + 40 + 80 + 24 + 24 + 40 + 16 + 3.0 / (N + 1) * 5 * 4 * 2
 
 
-def algorithmic_flops_per_dof(N, kernel, viscous=True, surf="roe"):
+def algorithmic_flops_per_dof(N, kernel, viscous=True, surf="roe", stored_prims=None):
     """Algorithmic FP64 flops per DOF and operator evaluation (FMA = 2).
 
     Counted on the formulas of the operator, independent of how a kernel
     schedules them (each unordered two-point pair once, as the split form
-    with a symmetric flux allows)."""
+    with a symmetric flux allows).  The primitive recovery is counted where it
+    runs: in the FP64 viscous form (stored_prims, the default there) once per
+    node in the lifting window, which stores them for the face and volume
+    kernels."""
     n = N + 1
+    if stored_prims is None:
+        stored_prims = viscous
     if kernel == "volume":
         pairs = 3 * N / 2.0                     # unordered pairs per node, 3 directions
         pair = 6 + 3 + 5 + 1 + 9 + 1 + 20       # averages, metric sum, u.a, m, F_m, F_E, 2 x 5 FMA
-        prim = 13                               # 1/rho, u, |u|^2, p, h
+        prim = 1 if stored_prims else 13        # 4 p' (stored) | 1/rho, u, |u|^2, p, h
         surf_int = (6.0 / n) * 5 * 2            # face nodes per DOF x 5 FMA
         return pairs * pair + prim + (4 if viscous else 0) + surf_int + 5 + 20
     if kernel == "lift":
@@ -75,7 +80,8 @@ def algorithmic_flops_per_dof(N, kernel, viscous=True, surf="roe"):
         contr = 12 * (n + 2) if n % 2 == 0 else 24 * n
         return 13 + contr + (6.0 / n) * 24 + 45 + 15 + 17 + 45 + 21 + contr + (8 if n % 2 == 0 else 0)
     if kernel == "face":
-        per_node = 26 + 25 + (80 if surf == "roe" else 12) + 8 + 10
+        # (both sides' primitives 26 unless stored) + two-point flux 25 + dissipation + viscous average + scaling
+        per_node = (0 if stored_prims else 26) + 25 + (80 if surf == "roe" else 12) + 8 + 10
         return (3.0 / n) * per_node
     return 0.0
 
@@ -438,7 +444,8 @@ def run_ours(args):
     kernels = {}
     for k, (ms, cnt) in prof.items():
         if cnt:
-            flops = algorithmic_flops_per_dof(wl.spec.N, k, bool(wl.viscous), "roe" if wl.surf_flux == 2 else "llf")
+            flops = algorithmic_flops_per_dof(wl.spec.N, k, bool(wl.viscous), "roe" if wl.surf_flux == 2 else "llf",
+                                              stored_prims=bool(wl.viscous) and precision == dg.FP64)
             avg = ms / cnt
             kernels[k] = {"ms_per_launch": avg, "launches": cnt, "share": ms / max(ms_total, 1e-30),
                           "flops_per_dof": flops,

@@ -1761,7 +1761,10 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
     // of the warps, the zeta pairs of its own lines (lanes pos < n/2) and of
     // the lines of warp + WARPS_LINES/2 (lanes pos >= n/2, through shared
     // memory: the xi metrics, no longer read after the xi pass).  A lane
-    // carries the result for its next pass's node in `carry`.
+    // carries that pair's flux for its next pass's node in `carry`.
+    // A node's sum runs through the passes: the xi pass starts it with the
+    // weak viscous divergence R_v, the eta and zeta passes from the sum the
+    // previous pass stored (with the carried pair's term as its first FMA).
     constexpr bool HALF = std::is_same<R, double>::value && n == 8 && Sh::WARPS_LINES % 2 == 0;
     constexpr int DMAX = HALF ? n / 2 - 1 : n / 2;
     constexpr int HW = Sh::WARPS_LINES / 2, NX = HW * LPW * (n / 2);
@@ -1770,20 +1773,29 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
 #pragma unroll 1
     for (int dir = 0; dir < 3; ++dir) {
       const int me = node_at(dir, pos);
+      const int ms = vslot<N, R>(me);
       const VolNode<R> A = load_node(me, dir);
-      if constexpr (HALF) {
-        if (dir == 2 && warp >= HW) {
-          const int px = pos ^ (n / 2);
-          const R c8 = sC8[pos * n + px], c16 = sC16[pos * n + px];
-          const int x = ((warp - HW) * LPW + seg) * (n / 2) + (pos & (n / 2 - 1));
-          carry[0] = c8 * sX[x];
-#pragma unroll
-          for (int v = 1; v < 5; ++v) carry[v] = c16 * sX[v * NX + x];
-        }
-      }
       R acc[5];
+      if (dir == 0) {
+        acc[0] = R(0);
+        const R* rv = Rv + (size_t)e * n3 + me;
 #pragma unroll
-      for (int v = 0; v < 5; ++v) acc[v] = carry[v];
+        for (int v = 1; v < 5; ++v) acc[v] = ph.viscous ? rv[(size_t)(v - 1) * S] : R(0);
+      } else if constexpr (HALF) {
+        const int px = pos ^ (n / 2);
+        const R c8 = sC8[pos * n + px], c16 = sC16[pos * n + px];
+        if (dir == 2 && warp >= HW) {
+          const int x = ((warp - HW) * LPW + seg) * (n / 2) + (pos & (n / 2 - 1));
+#pragma unroll
+          for (int v = 0; v < 5; ++v) carry[v] = sX[v * NX + x];
+        }
+        acc[0] = fma(c8, carry[0], sR[ms]);
+#pragma unroll
+        for (int v = 1; v < 5; ++v) acc[v] = fma(c16, carry[v], sR[v * n3 + ms]);
+      } else {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) acc[v] = sR[v * n3 + ms];
+      }
 #pragma unroll
       for (int d = 1; d <= DMAX; ++d) {
         const int pm = pos + d < n ? pos + d : pos + d - n;
@@ -1842,9 +1854,8 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
 #pragma unroll
           for (int v = 0; v < 5; ++v) {
             const R Fx = __shfl_xor_sync(0xffffffffu, F[v], h);
-            const R cv = v == 0 ? c8 : c16;
-            acc[v] += cv * (lo ? F[v] : Fx);
-            carry[v] = cv * (lo ? Fx : F[v]);
+            acc[v] += (v == 0 ? c8 : c16) * (lo ? F[v] : Fx);
+            carry[v] = lo ? Fx : F[v];
           }
         } else if (dir == 1 && warp < HW) {
           const bool lo = pos < h;
@@ -1856,20 +1867,14 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
 #pragma unroll
           for (int v = 0; v < 5; ++v) {
             const R Fx = __shfl_xor_sync(0xffffffffu, F[v], h);
-            carry[v] = (v == 0 ? c8 : c16) * (lo ? F[v] : Fx);
+            carry[v] = lo ? F[v] : Fx;
             if (!lo) sX[v * NX + x] = F[v];
           }
         }
       }
       if (active) {
-        const int ms = vslot<N, R>(me);
-        if (dir == 0) {
 #pragma unroll
-          for (int v = 0; v < 5; ++v) sR[v * n3 + ms] = acc[v];
-        } else {
-#pragma unroll
-          for (int v = 0; v < 5; ++v) sR[v * n3 + ms] += acc[v];
-        }
+        for (int v = 0; v < 5; ++v) sR[v * n3 + ms] = acc[v];
       }
       __syncthreads();
     }
@@ -1893,13 +1898,9 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
   // than kept in registers through the passes)
 #pragma unroll
   for (int v = 0; v < 5; ++v) Uo[v] = Uin[v * S + g];
-  R acc[5];
+  R acc[5];  // the passes' sums (with R_v)
 #pragma unroll
   for (int v = 0; v < 5; ++v) acc[v] = sR[v * n3 + vslot<N, R>(nd)];
-  if (ph.viscous) {
-#pragma unroll
-    for (int v = 0; v < 4; ++v) acc[v + 1] += Rv[(size_t)v * S + g];
-  }
   // surface integral: + sgn * Fs / w_perp on the faces that touch the node
   auto surf = [&](int l, int ab, R iw) {
     const int code = m.elem_face[e * 6 + l];
