@@ -419,8 +419,10 @@ __device__ __forceinline__ void riemann_dissipation(const PhysDev& ph, const Pri
 #pragma unroll
     for (int v = 0; v < 5; ++v) F[v] -= lam * dU[v];
   } else if (ph.surf_flux == 2) {  // Roe with Harten's entropy fix on the acoustic waves
+    // (reciprocals by rcp_t: in FP64 a Newton-refined estimate, the FP64
+    // pipe being the bound; the correctly rounded reciprocal in FP32)
     const R sA = sqrt(A.rho), sB = sqrt(B.rho);
-    const R is = R(1) / (sA + sB);
+    const R is = rcp_t<R>(sA + sB);
     const R rt = sA * sB;
     const R u = (sA * A.u + sB * B.u) * is, v = (sA * A.v + sB * B.v) * is, w = (sA * A.w + sB * B.w) * is;
     const R H = (sA * A.h + sB * B.h) * is;
@@ -431,9 +433,9 @@ __device__ __forceinline__ void riemann_dissipation(const PhysDev& ph, const Pri
     const R dr = drho ? *drho : B.rho - A.rho, dp = B.p - A.p;
     const R du = B.u - A.u, dv = B.v - A.v, dw = B.w - A.w;
     const R dun = du * nx + dv * ny + dw * nz;
-    const R i2c2 = R(0.5) / c2;
+    const R i2c2 = R(0.5) * rcp_t<R>(c2);
     const R a1 = (dp - rt * c * dun) * i2c2;
-    const R a2 = dr - dp / c2;
+    const R a2 = dr - R(2) * dp * i2c2;
     const R a5 = (dp + rt * c * dun) * i2c2;
     R l1 = fabs(un - c), l2 = fabs(un), l5 = fabs(un + c);
     const R del = R(0.1) * c;
