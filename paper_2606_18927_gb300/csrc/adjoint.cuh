@@ -477,14 +477,14 @@ k_adj_element(const double* __restrict__ U, const double* __restrict__ lam, cons
   double* sGQ = sW + 4 * n3;                           // [6][n3]
   double* sC = sGQ + 6 * n3;                           // [6][4][n2]
   double* sD = sC + 24 * n2;                           // [n2]
-  double* sDVS = sD + n2;                              // [n2]
+  double* sDVS = sD + n2;                              // [n2] w_a DVS_ab
   double* sDv = sDVS + n2;                             // [n2]
   double* siw = sDv + n2;                              // [n]
   const int e = blockIdx.x, t = threadIdx.x;
   const size_t S = (size_t)m.K * n3;
   for (int x = t; x < n2; x += T) {
     sD[x] = tab.D[x];
-    sDVS[x] = 8.0 * tab.DVS8[x];
+    sDVS[x] = 8.0 * tab.DVS8[x] / tab.iw[x / n];
     sDv[x] = tab.Dvisc[x];
   }
   if (t < n) siw[t] = tab.iw[t];
@@ -514,6 +514,13 @@ k_adj_element(const double* __restrict__ U, const double* __restrict__ lam, cons
     const bool active = (seg < LPW) && (L0 < n2);
     const int L = active ? L0 : 0;
     const int base = seg * n;
+    // The pair terms are linear in the combined cotangent
+    //   mu = DVS_im lam~_i + DVS_mi lam~_m = w_i DVS_im (lam~_i / w_i - lam~_m / w_m)
+    // (w_i DVS_im = -w_m DVS_mi off the diagonal, the SBP property), so each
+    // pass first stores lam~ / w along its direction and a pair forms the
+    // difference; the factor w_i DVS_im (table sDVS) scales its terms as they
+    // are summed, for the partner lane's pair w_m DVS_mi.
+    double* sLt = sQ + 6 * n3;  // [5][n3] lam~ / w (the unused half of the Q slots)
 #pragma unroll 1
     for (int dir = 0; dir < 3; ++dir) {
       const int a = L % n, b = L / n;
@@ -521,6 +528,12 @@ k_adj_element(const double* __restrict__ U, const double* __restrict__ lam, cons
         return dir == 0 ? q + n * L : (dir == 1 ? a + n * q + n2 * b : L + n2 * q);
       };
       const int me = node(pos);
+      if (active) {
+        const double iwp = siw[pos];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) sLt[v * n3 + me] = sL[v * n3 + me] * iwp;
+      }
+      __syncthreads();
       // the pair terms below carry constant factors (1/8 for rho, u, v, w,
       // 1/4 for p, 1/16 for h) that are applied once per node after the sums
       double g0 = 0, g1 = 0, g2 = 0, g3 = 0, g4 = 0, g5 = 0;
@@ -536,10 +549,9 @@ k_adj_element(const double* __restrict__ U, const double* __restrict__ lam, cons
         const double Sa0 = sA[(dir * 3 + 0) * n3 + me] + sA[(dir * 3 + 0) * n3 + q];
         const double Sa1 = sA[(dir * 3 + 1) * n3 + me] + sA[(dir * 3 + 1) * n3 + q];
         const double Sa2 = sA[(dir * 3 + 2) * n3 + me] + sA[(dir * 3 + 2) * n3 + q];
-        const double cim = sDVS[pos * n + pm], cmi = sDVS[pm * n + pos];
-        double mu[5];
+        double mu[5];  // mu / (w_i DVS_im)
 #pragma unroll
-        for (int v = 0; v < 5; ++v) mu[v] = cim * sL[v * n3 + me] + cmi * sL[v * n3 + q];
+        for (int v = 0; v < 5; ++v) mu[v] = sLt[v * n3 + me] - sLt[v * n3 + q];
         // F0 = {rho} qa, Fk = {rho} qa {u_k} + {p} {a_k}, F4 = {rho} qa {h}, qa = {u}.{a} = Q / 4;
         // tt = mu . dF/d({rho} qa) = mu0 + (mu1 Su + mu2 Sv + mu3 Sw + mu4 Sh) / 2;
         // half of each average's cotangent goes to each node:
@@ -554,15 +566,18 @@ k_adj_element(const double* __restrict__ U, const double* __restrict__ lam, cons
         const double h3 = Sr * fma(tt, Sa2, hQ * mu[3]);
         const double h4 = mu[1] * Sa0 + mu[2] * Sa1 + mu[3] * Sa2;
         const double h5 = Sr * Q * mu[4];
-        g0 += h0; g1 += h1; g2 += h2; g3 += h3; g4 += h4; g5 += h5;
+        const double cw = sDVS[pos * n + pm];
+        g0 = fma(cw, h0, g0); g1 = fma(cw, h1, g1); g2 = fma(cw, h2, g2);
+        g3 = fma(cw, h3, g3); g4 = fma(cw, h4, g4); g5 = fma(cw, h5, g5);
         if (2 * d != n) {
           const int src = base + (pos - d >= 0 ? pos - d : pos - d + n);
-          g0 += __shfl_sync(0xffffffffu, h0, src);
-          g1 += __shfl_sync(0xffffffffu, h1, src);
-          g2 += __shfl_sync(0xffffffffu, h2, src);
-          g3 += __shfl_sync(0xffffffffu, h3, src);
-          g4 += __shfl_sync(0xffffffffu, h4, src);
-          g5 += __shfl_sync(0xffffffffu, h5, src);
+          const double cs = sDVS[(src - base) * n + pos];
+          g0 = fma(cs, __shfl_sync(0xffffffffu, h0, src), g0);
+          g1 = fma(cs, __shfl_sync(0xffffffffu, h1, src), g1);
+          g2 = fma(cs, __shfl_sync(0xffffffffu, h2, src), g2);
+          g3 = fma(cs, __shfl_sync(0xffffffffu, h3, src), g3);
+          g4 = fma(cs, __shfl_sync(0xffffffffu, h4, src), g4);
+          g5 = fma(cs, __shfl_sync(0xffffffffu, h5, src), g5);
         }
       }
       g0 *= 0.125; g1 *= 0.125; g2 *= 0.125; g3 *= 0.125; g4 *= 0.25; g5 *= 0.0625;
@@ -612,9 +627,9 @@ k_adj_element(const double* __restrict__ U, const double* __restrict__ lam, cons
       double ja[9];
 #pragma unroll
       for (int c = 0; c < 9; ++c) ja[c] = sA[c * n3 + t];
-      const double iJ = m.invJ[g];
       // forward gradients q[d][v]: reference-space derivatives, the BR1
-      // surface corrections on them, then the metric transform
+      // surface corrections on them, then the metric transform (with the
+      // stored Ja / J, which also maps gq back to the reference space below)
       double dW[3][4];
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
@@ -634,13 +649,15 @@ k_adj_element(const double* __restrict__ U, const double* __restrict__ lam, cons
       if (i == 0 || i == N) surf(0, i == 0 ? 0 : 1, j + n * k, i == 0 ? -siw[0] : siw[N]);
       if (j == 0 || j == N) surf(1, j == 0 ? 2 : 3, i + n * k, j == 0 ? -siw[0] : siw[N]);
       if (k == 0 || k == N) surf(2, k == 0 ? 4 : 5, i + n * j, k == 0 ? -siw[0] : siw[N]);
+      double jj[9];
+#pragma unroll
+      for (int c = 0; c < 9; ++c) jj[c] = m.JaJ[(size_t)c * S + g];
       double q[3][4];
 #pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        const double j0 = iJ * ja[0 * 3 + d], j1 = iJ * ja[1 * 3 + d], j2 = iJ * ja[2 * 3 + d];
+      for (int d = 0; d < 3; ++d)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) q[d][v] = j0 * dW[0][v] + j1 * dW[1][v] + j2 * dW[2][v];
-      }
+        for (int v = 0; v < 4; ++v)
+          q[d][v] = jj[0 * 3 + d] * dW[0][v] + jj[1 * 3 + d] * dW[1][v] + jj[2 * 3 + d] * dW[2][v];
       // cotangent of the contravariant viscous flux G^dir at this node:
       // from R_v = sum_i Dvisc_i,m G_m (transposed) and from the face fluxes
       double gG[3][4];
@@ -702,18 +719,14 @@ k_adj_element(const double* __restrict__ U, const double* __restrict__ lam, cons
         gdiv -= 2.0 / 3.0 * mu * gtau[aa][aa];
       }
       gq[0][0] += gdiv; gq[1][1] += gdiv; gq[2][2] += gdiv;
-      // lifting transposed: q = (1/J)(sum_dir Ja^dir dW_dir + surface)
-#pragma unroll
-      for (int d = 0; d < 3; ++d)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) gq[d][v] *= iJ;
-      // cotangent of the reference-space gradient: H^dir = Ja^dir . gq
+      // lifting transposed: q = (1/J)(sum_dir Ja^dir dW_dir + surface), so the
+      // cotangent of the reference-space gradient is H^dir = (Ja^dir / J) . gq
       double H[3][4];
 #pragma unroll
       for (int dir = 0; dir < 3; ++dir)
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-          H[dir][v] = ja[dir * 3 + 0] * gq[0][v] + ja[dir * 3 + 1] * gq[1][v] + ja[dir * 3 + 2] * gq[2][v];
+          H[dir][v] = jj[dir * 3 + 0] * gq[0][v] + jj[dir * 3 + 1] * gq[1][v] + jj[dir * 3 + 2] * gq[2][v];
           sH[(dir * 4 + v) * n3 + t] = H[dir][v];
         }
       // surface terms: dW_dir += (W* - W) (+-1 / w) at the line ends

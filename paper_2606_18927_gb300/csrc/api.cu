@@ -735,6 +735,7 @@ static dg::OpArgs adjoint_args(dg_ctx* c, const double* U, const double* lam, do
   a.D = c->geo.basis.D.data(); a.w = c->geo.basis.w.data();
   a.Uin = U; a.status = c->status;
   a.lam = lam; a.gU = gU; a.gUf = c->gUf; a.gGf = c->gGf; a.gWf = c->gWf; a.gUs = c->gUs; a.gtheta = gth;
+  a.JaJ = c->JaJ; a.Mj = c->Mj;
   return a;
 }
 

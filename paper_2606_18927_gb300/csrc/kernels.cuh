@@ -1081,7 +1081,8 @@ k_lift(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
 #pragma unroll
       for (int d = 0; d < 3; ++d)
 #pragma unroll
-        for (int v = 0; v < 3; ++v) q[d][v] = jj[0 * 3 + d] * dW[0][v] + jj[1 * 3 + d] * dW[1][v] + jj[2 * 3 + d] * dW[2][v];
+        for (int v = 0; v < 3; ++v)
+          q[d][v] = jj[0 * 3 + d] * dW[0][v] + jj[1 * 3 + d] * dW[1][v] + jj[2 * 3 + d] * dW[2][v];
       R mm[6];
 #pragma unroll
       for (int c = 0; c < 6; ++c) mm[c] = m.Mj[(size_t)c * S + g];

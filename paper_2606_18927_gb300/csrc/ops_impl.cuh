@@ -149,6 +149,8 @@ static int run_vjp_typed(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {
   m.Ja = static_cast<const double*>(a.Ja); m.invJ = static_cast<const double*>(a.invJ);
   m.fgeo = a.fgeo; m.nbr = a.nbr; m.elem_face = a.elem_face; m.faces = a.faces;
   m.ws_elem = a.ws_elem; m.ws_lag = a.ws_lag;
+  m.JaJ = a.JaJ; m.Mj = a.Mj;
+  if (ph.viscous && !a.JaJ) return (int)cudaErrorInvalidValue;
   const Tables<N> tab = make_tables<N>(a.D, a.w);
   const double iw = tab.iw[0];
   const size_t smem = (size_t)AdjShape<N>::SMEM_D * sizeof(double);
