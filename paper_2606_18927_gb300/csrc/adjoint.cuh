@@ -482,10 +482,21 @@ k_adj_element(const double* __restrict__ U, const double* __restrict__ lam, cons
   double* siw = sDv + n2;                              // [n]
   const int e = blockIdx.x, t = threadIdx.x;
   const size_t S = (size_t)m.K * n3;
+  // N = 7: the viscous part's line contractions in even/odd form (as in the
+  // lifting kernel): sD holds the tables of D and of D^T, sDv that of Dvisc^T
+  constexpr bool EO = (n == 8) && (T == n3);
   for (int x = t; x < n2; x += T) {
-    sD[x] = tab.D[x];
     sDVS[x] = 8.0 * tab.DVS8[x] / tab.iw[x / n];
-    sDv[x] = tab.Dvisc[x];
+    if constexpr (EO) {
+      if (x < n * (n / 2)) {
+        sD[x] = LineEO<N>::coef(tab.D, x);
+        sD[n * (n / 2) + x] = LineEO<N>::coef_t(tab.D, x);
+        sDv[x] = LineEO<N>::coef_t(tab.Dvisc, x);
+      }
+    } else {
+      sD[x] = tab.D[x];
+      sDv[x] = tab.Dvisc[x];
+    }
   }
   if (t < n) siw[t] = tab.iw[t];
   if (t < n3) {
@@ -594,6 +605,20 @@ k_adj_element(const double* __restrict__ U, const double* __restrict__ lam, cons
     }
   }
   // ---- viscous part: recompute the lifted gradients, then transpose
+  // this thread's node from here on (N = 7: warp a + 4 b holds the xi lines at
+  // eta in {a, N - a} and zeta in {b, N - b}, so that a node's mirror nodes
+  // along xi, eta, zeta are lanes ^ 7, ^ 8, ^ 16 of its own warp)
+  int i, j, k;
+  if constexpr (EO) {
+    const int lane = t & 31, w = t >> 5, a = w & 3, b = w >> 2;
+    i = lane & 7;
+    j = (lane & 8) ? N - a : a;
+    k = (lane & 16) ? N - b : b;
+  } else {
+    i = t % n; j = (t / n) % n; k = t / n2;
+  }
+  const int p = i + n * (j + n * k);
+  double* sX = sQ;  // [3][4][n3] even/odd half sums (the Q slots, free after the pair phase)
   double gWo[4] = {0, 0, 0, 0};
   if (ph.viscous) {
     // W* - W at the faces (as in the forward lifting)
@@ -621,26 +646,50 @@ k_adj_element(const double* __restrict__ U, const double* __restrict__ lam, cons
       for (int v = 0; v < 4; ++v) sC[(l * 4 + v) * n2 + ab] = d[v];
     }
     __syncthreads();
+    double H[3][4];
     if (t < n3) {
-      const int i = t % n, j = (t / n) % n, k = t / n2;
-      const size_t g = (size_t)e * n3 + t;
+      const size_t g = (size_t)e * n3 + p;
+      const int qd[3] = {i, j, k};
       double ja[9];
 #pragma unroll
-      for (int c = 0; c < 9; ++c) ja[c] = sA[c * n3 + t];
+      for (int c = 0; c < 9; ++c) ja[c] = sA[c * n3 + p];
       // forward gradients q[d][v]: reference-space derivatives, the BR1
       // surface corrections on them, then the metric transform (with the
       // stored Ja / J, which also maps gq back to the reference space below)
       double dW[3][4];
+      if constexpr (EO) {
 #pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        double s0 = 0, s1 = 0, s2 = 0;
+        for (int dir = 0; dir < 3; ++dir)
 #pragma unroll
-        for (int mm = 0; mm < n; ++mm) {
-          s0 += sD[i * n + mm] * sW[v * n3 + mm + n * (j + n * k)];
-          s1 += sD[j * n + mm] * sW[v * n3 + i + n * (mm + n * k)];
-          s2 += sD[k * n + mm] * sW[v * n3 + i + n * (j + n * mm)];
+          for (int v = 0; v < 4; ++v)
+            sX[(dir * 4 + v) * n3 + p] =
+                LineEO<N>::half(qd[dir], sW[v * n3 + p], sW[v * n3 + LineEO<N>::at(p, dir, qd[dir], N - qd[dir])]);
+        __syncthreads();
+#pragma unroll
+        for (int dir = 0; dir < 3; ++dir)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) dW[dir][v] = LineEO<N>::apply(sD, sX + (dir * 4 + v) * n3, p, dir, qd[dir]);
+        __syncthreads();
+        // the half sums of lam~ for the transposed weak divergence below
+#pragma unroll
+        for (int dir = 0; dir < 3; ++dir)
+#pragma unroll
+          for (int v = 0; v < 4; ++v)
+            sX[(dir * 4 + v) * n3 + p] = LineEO<N>::half(
+                qd[dir], sL[(v + 1) * n3 + p], sL[(v + 1) * n3 + LineEO<N>::at(p, dir, qd[dir], N - qd[dir])]);
+        __syncthreads();
+      } else {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          double s0 = 0, s1 = 0, s2 = 0;
+#pragma unroll
+          for (int mm = 0; mm < n; ++mm) {
+            s0 += sD[i * n + mm] * sW[v * n3 + mm + n * (j + n * k)];
+            s1 += sD[j * n + mm] * sW[v * n3 + i + n * (mm + n * k)];
+            s2 += sD[k * n + mm] * sW[v * n3 + i + n * (j + n * mm)];
+          }
+          dW[0][v] = s0; dW[1][v] = s1; dW[2][v] = s2;
         }
-        dW[0][v] = s0; dW[1][v] = s1; dW[2][v] = s2;
       }
       auto surf = [&](int dir, int l, int ab, double sgn_iw) {
 #pragma unroll
@@ -661,16 +710,23 @@ k_adj_element(const double* __restrict__ U, const double* __restrict__ lam, cons
       // cotangent of the contravariant viscous flux G^dir at this node:
       // from R_v = sum_i Dvisc_i,m G_m (transposed) and from the face fluxes
       double gG[3][4];
+      if constexpr (EO) {
 #pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        double s0 = 0, s1 = 0, s2 = 0;
+        for (int dir = 0; dir < 3; ++dir)
 #pragma unroll
-        for (int ii = 0; ii < n; ++ii) {
-          s0 += sDv[ii * n + i] * sL[(v + 1) * n3 + ii + n * (j + n * k)];
-          s1 += sDv[ii * n + j] * sL[(v + 1) * n3 + i + n * (ii + n * k)];
-          s2 += sDv[ii * n + k] * sL[(v + 1) * n3 + i + n * (j + n * ii)];
+          for (int v = 0; v < 4; ++v) gG[dir][v] = LineEO<N>::apply(sDv, sX + (dir * 4 + v) * n3, p, dir, qd[dir]);
+      } else {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          double s0 = 0, s1 = 0, s2 = 0;
+#pragma unroll
+          for (int ii = 0; ii < n; ++ii) {
+            s0 += sDv[ii * n + i] * sL[(v + 1) * n3 + ii + n * (j + n * k)];
+            s1 += sDv[ii * n + j] * sL[(v + 1) * n3 + i + n * (ii + n * k)];
+            s2 += sDv[ii * n + k] * sL[(v + 1) * n3 + i + n * (j + n * ii)];
+          }
+          gG[0][v] = s0; gG[1][v] = s1; gG[2][v] = s2;
         }
-        gG[0][v] = s0; gG[1][v] = s1; gG[2][v] = s2;
       }
       auto gface = [&](int l, int ab, double sgn) {
         const double* src = gGf + ((size_t)e * 6 + l) * 4 * n2 + ab;
@@ -697,7 +753,7 @@ k_adj_element(const double* __restrict__ U, const double* __restrict__ lam, cons
       for (int aa = 0; aa < 3; ++aa)
 #pragma unroll
         for (int bb = 0; bb < 3; ++bb) tau[aa][bb] = mu * (q[bb][aa] + q[aa][bb]) - (aa == bb ? 2.0 / 3.0 * mu * div : 0.0);
-      const double uvw[3] = {sW[t], sW[n3 + t], sW[2 * n3 + t]};
+      const double uvw[3] = {sW[p], sW[n3 + p], sW[2 * n3 + p]};
       double gq[3][4] = {{0}};
       double gtau[3][3];
 #pragma unroll
@@ -721,13 +777,12 @@ k_adj_element(const double* __restrict__ U, const double* __restrict__ lam, cons
       gq[0][0] += gdiv; gq[1][1] += gdiv; gq[2][2] += gdiv;
       // lifting transposed: q = (1/J)(sum_dir Ja^dir dW_dir + surface), so the
       // cotangent of the reference-space gradient is H^dir = (Ja^dir / J) . gq
-      double H[3][4];
 #pragma unroll
       for (int dir = 0; dir < 3; ++dir)
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
           H[dir][v] = jj[dir * 3 + 0] * gq[0][v] + jj[dir * 3 + 1] * gq[1][v] + jj[dir * 3 + 2] * gq[2][v];
-          sH[(dir * 4 + v) * n3 + t] = H[dir][v];
+          if constexpr (!EO) sH[(dir * 4 + v) * n3 + p] = H[dir][v];
         }
       // surface terms: dW_dir += (W* - W) (+-1 / w) at the line ends
       auto surf_t = [&](int l, int ab, double sgn_iw) {
@@ -757,9 +812,26 @@ k_adj_element(const double* __restrict__ U, const double* __restrict__ lam, cons
       if (k == 0 || k == N) surf_t(k == 0 ? 4 : 5, i + n * j, k == 0 ? -siw[0] : siw[N]);
     }
     __syncthreads();
-    if (t < n3) {
+    if constexpr (EO) {  // (every thread holds a node: T == n3)
+      // gW_m += sum_dir sum_i D_{i, m} H^dir_i along the lines through m (D^T
+      // in even/odd form; the half sums from this node's H and its mirror's)
+      const int qd[3] = {i, j, k};
+#pragma unroll
+      for (int dir = 0; dir < 3; ++dir)
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+          sX[(dir * 4 + v) * n3 + p] = LineEO<N>::half(qd[dir], H[dir][v], LineEO<N>::mirror(H[dir][v], dir));
+      __syncthreads();
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        double s = 0;
+#pragma unroll
+        for (int dir = 0; dir < 3; ++dir)
+          s += LineEO<N>::apply(sD + n * (n / 2), sX + (dir * 4 + v) * n3, p, dir, qd[dir]);
+        gWo[v] += s;
+      }
+    } else if (t < n3) {
       // gW_m += sum_dir sum_i D_{i, m} H^dir_i along the lines through m
-      const int i = t % n, j = (t / n) % n, k = t / n2;
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
         double s = 0;
@@ -775,13 +847,13 @@ k_adj_element(const double* __restrict__ U, const double* __restrict__ lam, cons
   }
   if (t >= n3) return;
   // ---- own part of gU: primitives, lifting variables and the source term
-  const size_t g = (size_t)e * n3 + t;
+  const size_t g = (size_t)e * n3 + p;
   double Uo[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) Uo[v] = U[v * S + g];
   double gQ[6];
 #pragma unroll
-  for (int v = 0; v < 6; ++v) gQ[v] = sGQ[v * n3 + t];
+  for (int v = 0; v < 6; ++v) gQ[v] = sGQ[v * n3 + p];
   double out[5] = {0, 0, 0, 0, 0};
   prim_vjp(Uo, ph, gQ, out);
   if (ph.viscous) vt_vjp(Uo, ph, gWo, out);

@@ -864,6 +864,13 @@ struct LineEO {
     const double a = M[r * n + mm], b = M[r * n + N - mm];
     return q < h ? 0.5 * (a + b) : 0.5 * (a - b);
   }
+  // the same table for the transpose of M
+  __device__ static double coef_t(const double* M, int t) {
+    const int q = t / h, mm = t % h;
+    const int r = q < h ? q : N - q;
+    const double a = M[mm * n + r], b = M[(N - mm) * n + r];
+    return q < h ? 0.5 * (a + b) : 0.5 * (a - b);
+  }
   // node at line position pos on the line along dir through node p (at q)
   __device__ static int at(int p, int dir, int q, int pos) {
     return p + (pos - q) * (dir == 0 ? 1 : (dir == 1 ? n : n * n));
