@@ -136,7 +136,8 @@ void free_all(dg_ctx* c) {
   void* ptrs[] = {c->U, c->dU, c->io, c->io2, c->Ja, c->invJ, c->fgeo, c->nbr, c->elem_face, c->faces,
                   c->ws_elem, c->ws_lag, c->Rv, c->Gf, c->Fs, c->tau, c->status,
                   c->gUf, c->gGf, c->gWf, c->gUs, c->gtheta, c->wq, c->ro_ckpt, c->ro_stage, c->ro_work,
-                  c->ro_scalar, c->wJ, c->W32, c->W64, c->JaJ, c->Mj, c->halo_U, c->send_U, c->halo_G, c->send_G, c->wm_t};
+                  c->ro_scalar, c->wJ, c->W32, c->W64, c->JaJ, c->Mj, c->halo_U, c->send_U, c->halo_G, c->send_G,
+                  c->wm_t};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -478,19 +479,22 @@ int dg_init_mesh(dg_ctx** out, const dg_mesh_desc* m, const dg_phys* p, const dg
       // physical gradient) and the symmetric (Ja^n . Ja^m) / J (the heat flux
       // projected on Ja^n straight from the reference-space gradient of T),
       // M in the order 00, 11, 22, 01, 02, 12
-      std::vector<double> jj(9 * S), mj(6 * S);
+      // (one component at a time: the host holds one extra array of S values)
+      std::vector<double> buf(S);
+      for (int cc = 0; cc < 9; ++cc) {
+        for (size_t x = 0; x < S; ++x) buf[x] = ja[cc * S + x] * ij[x];
+        chk(cudaMemcpy(c->JaJ + cc * S, buf.data(), S * sizeof(double), cudaMemcpyHostToDevice));
+      }
       static const int mn[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
-      for (size_t x = 0; x < S; ++x) {
-        for (int cc = 0; cc < 9; ++cc) jj[cc * S + x] = ja[cc * S + x] * ij[x];
-        for (int r = 0; r < 6; ++r) {
-          const int a = mn[r][0], b = mn[r][1];
+      for (int r = 0; r < 6; ++r) {
+        const int a = mn[r][0], b = mn[r][1];
+        for (size_t x = 0; x < S; ++x) {
           double dot = 0.0;
           for (int d = 0; d < 3; ++d) dot += ja[(a * 3 + d) * S + x] * ja[(b * 3 + d) * S + x];
-          mj[r * S + x] = dot * ij[x];
+          buf[x] = dot * ij[x];
         }
+        chk(cudaMemcpy(c->Mj + r * S, buf.data(), S * sizeof(double), cudaMemcpyHostToDevice));
       }
-      chk(cudaMemcpy(c->JaJ, jj.data(), jj.size() * sizeof(double), cudaMemcpyHostToDevice));
-      chk(cudaMemcpy(c->Mj, mj.data(), mj.size() * sizeof(double), cudaMemcpyHostToDevice));
     }
   }
   chk(cudaMemcpy(c->fgeo, c->geo.fgeo.data(), c->geo.fgeo.size() * sizeof(double), cudaMemcpyHostToDevice));

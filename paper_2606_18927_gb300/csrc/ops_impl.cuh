@@ -37,10 +37,12 @@ static int run_typed(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {
   m.fgeo = a.fgeo; m.nbr = a.nbr; m.elem_face = a.elem_face; m.faces = a.faces;
   m.ws_elem = a.ws_elem; m.ws_lag = a.ws_lag;
   m.W32 = std::is_same<R, float>::value ? a.W32 : nullptr;
-  // written by the lifting kernel, so only when it runs
+  // FP64 viscous form: the primitives stored by k_prim64 (before the lifting
+  // kernel) and the lifting kernel's metric products
   m.W64 = std::is_same<R, double>::value && ph.viscous ? a.W64 : nullptr;
   m.JaJ = a.JaJ; m.Mj = a.Mj;
-  if (std::is_same<R, double>::value && ph.viscous && (!a.JaJ || !a.Mj)) return (int)cudaErrorInvalidValue;
+  if (std::is_same<R, double>::value && ph.viscous && (!a.JaJ || !a.Mj))
+    return (int)cudaErrorInvalidValue;
   m.wm_t = a.wm_t;
   m.n_halo = a.n_halo; m.halo_U = a.halo_U; m.halo_G = static_cast<const R*>(a.halo_G);
   const Tables<N> tab = make_tables<N>(a.D, a.w);
