@@ -151,7 +151,10 @@ int dg_lgl_nodes(int N, double* xi, double* w);
 /* Builds the geometry (curl-form metrics, Jacobians, face normals, wall-model
  * sampling points) on the host, validates it, allocates the device storage
  * and uploads it.  stream: cudaStream_t (may be 0).  On success *out owns
- * everything; free it with dg_destroy.  Errors: DG_ERR_ARG, DG_ERR_MESH,
+ * everything; free it with dg_destroy.  Device storage at N = 7: about 500
+ * bytes per DOF in the FP64 viscous form (state, RK register, metrics and the
+ * stored products Ja / J and (Ja Ja^T) / J, the stored primitives, scratch),
+ * about 280 in the FP32-mixed form.  Errors: DG_ERR_ARG, DG_ERR_MESH,
  * DG_ERR_OOM, DG_ERR_CUDA (the message is then available through
  * dg_last_error(NULL)). */
 int dg_init_mesh(dg_ctx** out, const dg_mesh_desc* m, const dg_phys* p, const dg_options* o,
@@ -319,7 +322,9 @@ int dg_time_derivative_phase(dg_ctx* c, int phase, const double* U, double* Ut);
 
 /* Per-kernel timing with CUDA events on the context's stream (tracing).
  * dg_profile_enable(c, 1) records events around the lift, face, wall and
- * volume kernels of every subsequent operator evaluation; dg_profile_read
+ * volume kernels of every subsequent operator evaluation (in the FP64
+ * viscous form the lift window also holds the kernel that forms the input
+ * state's primitives, when they are not already stored); dg_profile_read
  * synchronises the stream, returns the summed milliseconds ms[4] and the
  * launch counts launches[4] (order: lift, face, wall, volume) since the last
  * read, and resets them. */
