@@ -170,7 +170,7 @@ int dg_set_stream(dg_ctx* c, void* stream);
  * wall-model kernel (which reads only the state and writes only the wall
  * faces' fluxes) on a side stream of the highest priority, beside the lifting
  * and the interior-face kernels, rejoining the caller's stream before the
- * volume kernel (the prioritised streams and events of the paper's Sec. 2.3).
+ * volume kernel (the prioritised streams and events of the paper's Sec. 2.1).
  * enable = 0 launches it in line on the caller's stream.  Results are bitwise
  * the same either way; a CUDA graph captured by dg_rk_steps_graph records the
  * fork and join of the setting in force when it is captured. */
@@ -209,9 +209,11 @@ int dg_rk_steps(dg_ctx* c, double t, double dt, int nsteps);
  * U: device array or NULL for the context's state; lam, gU: device arrays
  * double[5][K][n^3]; gtheta: device double[2] or NULL.  The transposed
  * split-form volume integral, viscous flux, BR1 lifting and primitive
- * recovery are written out by hand; the local Jacobians of the Riemann
- * solver and of the wall model (with the implicit function theorem for the
- * law of the wall, Sec. 3.2) come from forward-mode dual numbers.  FP64
+ * recovery are written out by hand, and so is the reverse mode of the
+ * Riemann flux (one forward sweep keeping the intermediates of the two-point
+ * flux and of its dissipation, one backward sweep); the local derivatives of
+ * the wall model come from forward-mode dual numbers, with the implicit
+ * function theorem for the law-of-the-wall solve (Sec. 3.2).  FP64
  * contexts with the Pirozzoli volume flux, a constant viscosity, adiabatic
  * walls and no inflow, outflow or halo faces (else DG_ERR_NOT_IMPLEMENTED).
  * The first call allocates the adjoint scratch of the context. */
@@ -219,6 +221,15 @@ int dg_vjp(dg_ctx* c, const double* U, const double* lam, double* gU, double* gt
 
 /* Sets the wall-law constants (kappa, B) used by later calls (Sec. 3.2). */
 int dg_set_params(dg_ctx* c, double kappa, double B);
+
+/* Iteration cap of the wall model's law-of-the-wall solve (SolveWallStress,
+ * Sec. 3.2 Algorithms 1-2): bracket growth and Newton steps together, at
+ * most max_iter evaluations of the law per wall node (default 200; the
+ * converged solve takes about eight).  A wall node whose solve reaches the
+ * cap keeps its last iterate and sets the status flag that dg_check_status
+ * reports as DG_ERR_WM_NOCONV; nothing waits or traps on the GPU.
+ * max_iter >= 1, else DG_ERR_ARG.  Used by later calls. */
+int dg_set_wall_solve_limit(dg_ctx* c, int max_iter);
 
 /* Explicit time step dt = cfl * 2/(2N+1) * min_nodes J / sum_dir(|u . Ja^dir|
  * + c |Ja^dir|) (CFL-based step of the explicit LSERK4, paper Sec. 4 uses
@@ -267,7 +278,7 @@ int dg_set_rk_register(dg_ctx* c, const double* dU, int on_device);
 int dg_check_status(dg_ctx* c);
 
 /* ---------------------------------------------------------------------------
- * Partitioned meshes (Sec. 2.3: non-overlapping subdomains along a
+ * Partitioned meshes (Sec. 2.1: non-overlapping subdomains along a
  * space-filling curve, one per rank and GPU).  Host functions need no GPU.
  *
  * dg_partition_sfc: part[K] (host) <- the rank of every element: elements
@@ -350,7 +361,10 @@ int dg_profile_read(dg_ctx* c, double* ms, int* launches);
  *   Errors DG_ERR_ARG if the mesh needs more scratch than the static array
  *   holds (the viscous FP64 operator needs about 84 bytes per DOF at N = 5
  *   and 72 at N = 7, so about 4e5 DOF fit, e.g. the 221,184-DOF channel;
- *   the message gives the bytes needed), DG_ERR_CUDA on a CUDA failure.
+ *   the message gives the bytes needed) or if the current device is not
+ *   the one the context was created on, DG_ERR_CUDA on a CUDA failure.
+ * In the FP32-mixed form the call also rewrites the context's own FP32
+ * primitive array (allocated by dg_init_mesh) with those of U.
  * The first call on a device looks up the array's device address (the host
  * symbol is only a stand-in) and caches it; make that first call before any
  * stream capture.  All calls share the array: calls whose kernels overlap on

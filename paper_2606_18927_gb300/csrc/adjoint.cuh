@@ -106,7 +106,7 @@ static __device__ void wall_stress_jvp(const PhysDev& ph, const DualD Us[5], dou
   const DualD a = sqrt(r / (2.0 * ph.cp * Tw));
   const DualD uvd = asin(a * um) / a;
   const DualD nuw = ph.mu / rhow;
-  const double ut = solve_utau(ph.law, uvd.v, ph.hwm, nuw.v, ph.kappa, ph.B, ok);
+  const double ut = solve_utau(ph.law, uvd.v, ph.hwm, nuw.v, ph.kappa, ph.B, ph.wm_maxit, ok);
   // explicit variable of the law at the solution
   const double wv = ph.law == 1 ? ut * ph.hwm / nuw.v : uvd.v / ut;
   double L, wdL, Lk, LB;

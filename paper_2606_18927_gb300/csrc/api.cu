@@ -16,6 +16,9 @@
 // Five-stage fourth-order 2N-storage Runge-Kutta scheme of Carpenter and
 // Kennedy (1994), the low-storage scheme of paper Sec. 4.  These are the
 // published rational coefficients.
+// Default iteration cap of the law-of-the-wall solve (bracket growth and
+// Newton steps together); dg_set_wall_solve_limit changes it.
+static const int kWallSolveMaxIter = 200;
 static const double kRkA[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
                                -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
 static const double kRkB[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
@@ -213,6 +216,13 @@ int refresh_w32(dg_ctx* c) {
   return DG_OK;
 }
 
+// A captured LSERK4 step holds the kernel arguments of its capture (the
+// physical constants among them): it is recaptured at its next use.
+void drop_step_graph(dg_ctx* c) {
+  if (c->step_graph) cudaGraphExecDestroy(c->step_graph);
+  c->step_graph = nullptr;
+}
+
 }  // namespace
 
 namespace dg {
@@ -302,7 +312,7 @@ namespace dg {
 // Operator arguments of a context for dg_time_derivative_noalloc (noalloc.cu):
 // everything except the scratch pointers, plus the scratch sizes in bytes.
 int noalloc_args(dg_ctx* c, const double* U, double* Ut, OpArgs* a, const PhysDev** ph, cudaStream_t* s,
-                 size_t* rv_bytes, size_t* gf_bytes, size_t* fs_bytes) {
+                 int* device, size_t* rv_bytes, size_t* gf_bytes, size_t* fs_bytes) {
   const size_t rs = c->opts.precision == DG_FP32_MIXED ? sizeof(float) : sizeof(double);
   *a = OpArgs{};
   a->N = c->N; a->K = c->K; a->F = c->F; a->n_interior = c->geo.n_interior; a->n_wall = c->geo.n_wall;
@@ -317,6 +327,7 @@ int noalloc_args(dg_ctx* c, const double* U, double* Ut, OpArgs* a, const PhysDe
   a->mode = 0; a->Out = Ut;
   *ph = &c->ph;
   *s = c->stream;
+  *device = c->device;
   *rv_bytes = (c->opts.viscous ? 4 * c->S : 1) * rs;
   *gf_bytes = (c->opts.viscous ? 24 * (size_t)c->K * c->n2 : 1) * rs;
   *fs_bytes = (c->ph.fs_diff ? 10 : 5) * (size_t)c->F * c->n2 * rs;
@@ -324,8 +335,13 @@ int noalloc_args(dg_ctx* c, const double* U, double* Ut, OpArgs* a, const PhysDe
   // (allocated with the context); they are formed afresh from U
   a->W32 = c->W32;
   a->w32_valid = 0;
-  if (a->fp32) c->w32_of_U = (U == c->U);
   return DG_OK;
+}
+// After the launches of dg_time_derivative_noalloc: in the FP32-mixed form the
+// context's W32 now holds the primitives of U (if the launches succeeded), so
+// they are those of the context's state only when U is the state.
+void noalloc_done(dg_ctx* c, const double* U, bool ok) {
+  if (c->opts.precision == DG_FP32_MIXED) c->w32_of_U = ok && (U == c->U);
 }
 int noalloc_fail(dg_ctx* c, int code, const std::string& msg) { return fail(c, code, msg); }
 }  // namespace dg
@@ -399,6 +415,7 @@ int dg_init_mesh(dg_ctx** out, const dg_mesh_desc* m, const dg_phys* p, const dg
   for (int v = 0; v < 5; ++v) ph.U_in[v] = p->U_in[v];
   ph.p_out = p->p_out;
   ph.T_wall = p->T_wall;
+  ph.wm_maxit = kWallSolveMaxIter;
   ph.sutherland = ph.suth_S > 0.0 ? 1 : 0;
   ph.fs_diff = (o->precision == DG_FP32_MIXED && o->vol_flux == DG_VOL_KEP_PIROZZOLI) ? 1 : 0;
   ph.has_force = (ph.f[0] != 0.0 || ph.f[1] != 0.0 || ph.f[2] != 0.0) ? 1 : 0;
@@ -703,6 +720,15 @@ int dg_set_params(dg_ctx* c, double kappa, double B) {
   if (!(kappa > 0.0)) return fail(c, DG_ERR_ARG, "dg_set_params: kappa must be positive");
   c->phys.kappa = kappa; c->phys.B = B;
   c->ph.kappa = kappa; c->ph.B = B;
+  drop_step_graph(c);  // a captured step holds the old constants
+  return DG_OK;
+}
+
+int dg_set_wall_solve_limit(dg_ctx* c, int max_iter) {
+  if (!c) return DG_ERR_ARG;
+  if (max_iter < 1) return fail(c, DG_ERR_ARG, "dg_set_wall_solve_limit: max_iter must be >= 1");
+  c->ph.wm_maxit = max_iter;
+  drop_step_graph(c);
   return DG_OK;
 }
 

@@ -54,6 +54,7 @@ struct PhysDev {
   int fs_diff;                // FP32 Pirozzoli form: surface fluxes stored per side as F* - F(U_side)
   double U_in[5], p_out;      // inflow state (conservative) and outflow pressure
   double T_wall;              // isothermal wall temperature (<= 0: adiabatic walls)
+  int wm_maxit;               // iteration cap of the law-of-the-wall solve (bracket growth + Newton)
   // FP32 copies of the constants the FP32 kernels use (a double-to-float
   // conversion is an FP64-pipe instruction)
   struct {
@@ -623,7 +624,8 @@ __device__ __forceinline__ void law_eval(int law, double w, double kap, double B
 // steps from the laminar estimate t = ln(Re_h)/2, then Newton with bisection
 // whenever a step would leave the bracket.  Returns u_tau (and *ok).  F is
 // increasing in t; its value at the starting point is evaluated once.
-static __device__ double solve_utau(int law, double u, double h, double nu, double kap, double B, bool* ok) {
+static __device__ double solve_utau(int law, double u, double h, double nu, double kap, double B, int maxit,
+                                    bool* ok) {
   *ok = true;
   if (!(u > 0.0)) return 0.0;
   const double lnRe = log(h * u / nu);
@@ -641,14 +643,14 @@ static __device__ double solve_utau(int law, double u, double h, double nu, doub
   double lo = t0, hi = t0, st = 1.0;
   int it = 0;
   double Flo = F0;
-  while (!(Flo < 0.0) && it < 200) { lo -= st; st *= 2.0; ++it; Flo = F(lo, &dF); }
+  while (!(Flo < 0.0) && it < maxit) { lo -= st; st *= 2.0; ++it; Flo = F(lo, &dF); }
   st = 1.0;
   double Fhi = F0;
-  while (!(Fhi > 0.0) && it < 200) { hi += st; st *= 2.0; ++it; Fhi = F(hi, &dF); }
+  while (!(Fhi > 0.0) && it < maxit) { hi += st; st *= 2.0; ++it; Fhi = F(hi, &dF); }
   double t = t0;
   if (!(t > lo && t < hi)) t = 0.5 * (lo + hi);
   bool done = false;
-  for (; it < 200; ++it) {
+  for (; it < maxit; ++it) {
     const double Ft = F(t, &dF);
     if (Ft == 0.0) { done = true; break; }
     if (Ft < 0.0) lo = t; else hi = t;
@@ -669,7 +671,7 @@ static __device__ double solve_utau(int law, double u, double h, double nu, doub
 // bracketed solve; if they do not converge, the bracketed solve from scratch.
 // *t_out receives the converged t.  The state changes little between stages, so
 // one or two evaluations of F usually suffice instead of about eight.
-static __device__ double solve_utau_warm(int law, double u, double h, double nu, double kap, double B,
+static __device__ double solve_utau_warm(int law, double u, double h, double nu, double kap, double B, int maxit,
                                          double t_prev, double* t_out, bool* ok) {
   *ok = true;
   if (!(u > 0.0)) { *t_out = t_prev; return 0.0; }
@@ -677,7 +679,7 @@ static __device__ double solve_utau_warm(int law, double u, double h, double nu,
     const double lnRe = log(h * u / nu);
     const double cst = law_const(law, kap, B);
     double t = t_prev;
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < 4 && k < maxit; ++k) {
       const double w = exp(t);
       double L, wdL;
       law_eval_c(law, w, kap, cst, &L, &wdL);
@@ -691,7 +693,7 @@ static __device__ double solve_utau_warm(int law, double u, double h, double nu,
       if (step <= 1e-12 * fmax(1.0, fabs(t))) { *t_out = t; return law == 1 ? exp(t) * nu / h : u / exp(t); }
     }
   }
-  const double ut = solve_utau(law, u, h, nu, kap, B, ok);
+  const double ut = solve_utau(law, u, h, nu, kap, B, maxit, ok);
   *t_out = law == 1 ? log(ut * h / nu) : log(u / ut);
   return ut;
 }
@@ -716,7 +718,7 @@ __device__ __forceinline__ void law_eval_cf(int law, float w, float kap, float c
   }
 }
 
-static __device__ float solve_utau_f(int law, float u, float h, float nu, float kap, float B, bool* ok) {
+static __device__ float solve_utau_f(int law, float u, float h, float nu, float kap, float B, int maxit, bool* ok) {
   *ok = true;
   if (!(u > 0.0f)) return 0.0f;
   const float lnRe = logf(h * u / nu);
@@ -734,14 +736,14 @@ static __device__ float solve_utau_f(int law, float u, float h, float nu, float 
   float lo = t0, hi = t0, st = 1.0f;
   int it = 0;
   float Flo = F0;
-  while (!(Flo < 0.0f) && it < 200) { lo -= st; st *= 2.0f; ++it; Flo = F(lo, &dF); }
+  while (!(Flo < 0.0f) && it < maxit) { lo -= st; st *= 2.0f; ++it; Flo = F(lo, &dF); }
   st = 1.0f;
   float Fhi = F0;
-  while (!(Fhi > 0.0f) && it < 200) { hi += st; st *= 2.0f; ++it; Fhi = F(hi, &dF); }
+  while (!(Fhi > 0.0f) && it < maxit) { hi += st; st *= 2.0f; ++it; Fhi = F(hi, &dF); }
   float t = t0;
   if (!(t > lo && t < hi)) t = 0.5f * (lo + hi);
   bool done = false;
-  for (; it < 200; ++it) {
+  for (; it < maxit; ++it) {
     const float Ft = F(t, &dF);
     if (Ft == 0.0f) { done = true; break; }
     if (Ft < 0.0f) lo = t; else hi = t;
@@ -786,7 +788,7 @@ static __device__ void wall_stress_f(const PhysDev& ph, float rho, float u, floa
   }
   const float rhow = rho * T / Tw;
   const float muw = ph.sutherland ? sutherland<float>(ph, Tw) : ph.f32c.mu;
-  const float ut = solve_utau_f(ph.law, uvd, (float)ph.hwm, muw / rhow, (float)ph.kappa, (float)ph.B, ok);
+  const float ut = solve_utau_f(ph.law, uvd, (float)ph.hwm, muw / rhow, (float)ph.kappa, (float)ph.B, ph.wm_maxit, ok);
   const float tw = rhow * ut * ut / um;
   tau[0] = tw * ux; tau[1] = tw * uy; tau[2] = tw * uz;
   if (ph.T_wall > 0.0) *qw = -(cp / Pr) * (rhow * ut * ut) * (Taw - Tw) / um;
@@ -833,8 +835,9 @@ static __device__ void wall_stress(const PhysDev& ph, const double Us[5], double
   }
   const double rhow = rho * T / Tw;
   const double muw = ph.sutherland ? sutherland<double>(ph, Tw) : ph.mu;
-  const double ut = t_warm ? solve_utau_warm(ph.law, uvd, ph.hwm, muw / rhow, ph.kappa, ph.B, *t_warm, t_warm, ok)
-                           : solve_utau(ph.law, uvd, ph.hwm, muw / rhow, ph.kappa, ph.B, ok);
+  const double ut = t_warm ? solve_utau_warm(ph.law, uvd, ph.hwm, muw / rhow, ph.kappa, ph.B, ph.wm_maxit, *t_warm,
+                                             t_warm, ok)
+                           : solve_utau(ph.law, uvd, ph.hwm, muw / rhow, ph.kappa, ph.B, ph.wm_maxit, ok);
   const double tw = rhow * ut * ut / um;
   tau[0] = tw * ux; tau[1] = tw * uy; tau[2] = tw * uz;
   if (ph.T_wall > 0.0) *qw = -(ph.cp / ph.Pr) * (rhow * ut * ut) * (Taw - Tw) / um;

@@ -47,7 +47,8 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 // implemented in api.cu: fills the operator arguments from a context
 namespace dg {
 int noalloc_args(dg_ctx* c, const double* U, double* Ut, OpArgs* a, const PhysDev** ph, cudaStream_t* s,
-                 size_t* rv_bytes, size_t* gf_bytes, size_t* fs_bytes);
+                 int* device, size_t* rv_bytes, size_t* gf_bytes, size_t* fs_bytes);
+void noalloc_done(dg_ctx* c, const double* U, bool ok);
 int noalloc_fail(dg_ctx* c, int code, const std::string& msg);
 }  // namespace dg
 
@@ -58,7 +59,8 @@ extern "C" int dg_time_derivative_noalloc(dg_ctx* c, const double* U, double* Ut
   const dg::PhysDev* ph = nullptr;
   cudaStream_t stream = nullptr;
   size_t rv = 0, gf = 0, fs = 0;
-  int rc = dg::noalloc_args(c, U, Ut, &a, &ph, &stream, &rv, &gf, &fs);
+  int ctx_device = 0;
+  int rc = dg::noalloc_args(c, U, Ut, &a, &ph, &stream, &ctx_device, &rv, &gf, &fs);
   if (rc != DG_OK) return rc;
   if (a.n_halo > 0)
     return dg::noalloc_fail(c, DG_ERR_ARG, "dg_time_derivative_noalloc: not for partitioned contexts");
@@ -68,10 +70,18 @@ extern "C" int dg_time_derivative_noalloc(dg_ctx* c, const double* U, double* Ut
                             "dg_time_derivative_noalloc: mesh needs " + std::to_string(need) +
                                 " scratch bytes, more than the static limit of " +
                                 std::to_string((size_t)DG_NOALLOC_SCRATCH_BYTES));
+  // The scratch array used must be the one on the context's device, and the
+  // kernels run on the current device: the two must agree.
   int device = 0;
   cudaError_t e = cudaGetDevice(&device);
+  if (e != cudaSuccess)
+    return dg::noalloc_fail(c, DG_ERR_CUDA, std::string("dg_time_derivative_noalloc: ") + cudaGetErrorString(e));
+  if (device != ctx_device)
+    return dg::noalloc_fail(c, DG_ERR_ARG,
+                            "dg_time_derivative_noalloc: the current device (" + std::to_string(device) +
+                                ") is not the context's device (" + std::to_string(ctx_device) + ")");
   void* base = nullptr;
-  if (e == cudaSuccess) e = scratch_address(device, &base);
+  e = scratch_address(ctx_device, &base);
   if (e != cudaSuccess)
     return dg::noalloc_fail(c, DG_ERR_CUDA, std::string("dg_time_derivative_noalloc: ") + cudaGetErrorString(e));
   // Every scratch word is written before it is read within one call (each
@@ -85,6 +95,7 @@ extern "C" int dg_time_derivative_noalloc(dg_ctx* c, const double* U, double* Ut
   a.tau = nullptr;
   a.ev = nullptr;
   rc = dg::run_operator(a, *ph, stream);
+  dg::noalloc_done(c, U, rc == 0);
   if (rc != 0)
     return dg::noalloc_fail(c, DG_ERR_CUDA,
                             std::string("dg_time_derivative_noalloc: ") + cudaGetErrorString((cudaError_t)rc));

@@ -35,7 +35,7 @@ struct OpArgs {
   cudaEvent_t* ev;          // null, or 7 events: lift [0,1], face [1,2], wall [3,4], volume [5,6]
   // optional side stream for the wall-model kernel: it forks from the main
   // stream before the lifting and joins it before the volume kernel (the
-  // paper's prioritised boundary work, Sec. 2.3); null side: one stream
+  // paper's prioritised boundary work, Sec. 2.1); null side: one stream
   cudaStream_t side;
   cudaEvent_t fork, join;
   // FP32-mixed form: [6][K n^3] FP32 primitives of Uin; w32_valid = 1 when they

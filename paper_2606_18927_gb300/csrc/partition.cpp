@@ -2,7 +2,7 @@
 // per-rank local meshes with their halo faces (host code, no GPU needed).
 //
 // The paper divides the domain into non-overlapping subdomains along a
-// space-filling curve, one per process and GPU (Sec. 2.3).  Here the curve is
+// space-filling curve, one per process and GPU (Sec. 2.1).  Here the curve is
 // the Morton (Z-order) curve of the element centroids.  A rank's local mesh
 // keeps its own elements; a face whose neighbour lives on another rank becomes
 // a halo face, whose remote trace arrives in the context's halo buffers.

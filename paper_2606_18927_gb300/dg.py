@@ -92,6 +92,7 @@ def lib():
         "dg_time_derivative_noalloc": (c_int, [vp, vp, vp]),
         "dg_vjp": (c_int, [vp, vp, vp, vp, vp]),
         "dg_set_params": (c_int, [vp, c_double, c_double]),
+        "dg_set_wall_solve_limit": (c_int, [vp, c_int]),
         "dg_wall_shear": (c_int, [vp, vp, dp]),
         "dg_kinetic_energy": (c_int, [vp, vp, dp]),
         "dg_time_step": (c_int, [vp, vp, c_double, dp]),
@@ -303,6 +304,10 @@ class Operator:
 
     def set_params(self, kappa, B):
         self._check(lib().dg_set_params(self.h, float(kappa), float(B)))
+
+    def set_wall_solve_limit(self, max_iter):
+        """Iteration cap of the wall model's law-of-the-wall solve (default 200)."""
+        self._check(lib().dg_set_wall_solve_limit(self.h, int(max_iter)))
 
     def time_step(self, cfl=0.9, U=None):
         out = ctypes.c_double(0.0)

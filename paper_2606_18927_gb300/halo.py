@@ -1,5 +1,5 @@
 """Partitioned meshes: halo bookkeeping and the exchanges between the phases
-of an evaluation (paper Sec. 2.3: space-filling-curve subdomains, one per
+of an evaluation (paper Sec. 2.1: space-filling-curve subdomains, one per
 rank and GPU, with the face data of the subdomain boundaries exchanged).
 
 The library evaluates a partitioned context in three phases (``dg.h``):

@@ -28,3 +28,49 @@ def rel_max_err(a, b):
     """max over variables of max|a_v - b_v| / max|b_v| (the parity norm)."""
     a = a.reshape(5, -1); b = b.reshape(5, -1)
     return float(max(np.abs(a[v] - b[v]).max() / max(np.abs(b[v]).max(), 1e-300) for v in range(5)))
+
+
+OUTFLOW = -3
+
+
+def submesh(nbr, sel, rings=2):
+    """Elements of sel and `rings` rings of face neighbours: (global ids,
+    local connectivity with the faces leaving the set marked as outflow
+    boundaries, local ids of sel in the order of sel)."""
+    keep = set(int(e) for e in sel)
+    front = set(keep)
+    for _ in range(rings):
+        nxt = set()
+        for e in front:
+            for q in nbr[e]:
+                if q >= 0 and int(q) not in keep:
+                    nxt.add(int(q))
+        keep |= nxt
+        front = nxt
+    ids = np.array(sorted(keep), dtype=np.int64)
+    g2l = {int(e): k for k, e in enumerate(ids)}
+    loc = np.array([[g2l.get(int(q), OUTFLOW) if q >= 0 else int(q) for q in nbr[e]] for e in ids],
+                   dtype=np.int32)
+    return ids, loc, np.array([g2l[int(e)] for e in sel], dtype=np.int32)
+
+
+class SampledOracle:
+    """The oracle's time derivative on sampled elements of a mesh too large to
+    evaluate whole.  The oracle runs on the sub-mesh of the samples and the two
+    rings of face neighbours their time derivative depends on (lifted
+    gradients of ring 1, primitives of ring 2), with its subset evaluation
+    restricted to the samples; faces leaving the sub-mesh become outflow
+    boundaries, which only ring 2 touches (its lifting and time derivative are
+    not evaluated).  Periodic meshes without walls only."""
+
+    def __init__(self, ora, N, X, nbr, phys, sel, extended=True, **opts):
+        self.n3 = (N + 1) ** 3
+        self.K = X.size // (3 * self.n3)
+        self.ids, loc, self.lsel = submesh(nbr, sel)
+        Xs = np.ascontiguousarray(X.reshape(3, self.K, -1)[:, self.ids])
+        self.o = ora.Oracle(N, Xs, loc, phys, extended=extended, subset=self.lsel, **opts)
+
+    def time_derivative_on_sample(self, U):
+        """Ut of the sampled elements, [5][len(sel)][n^3]."""
+        Us = np.ascontiguousarray(U.reshape(5, self.K, -1)[:, self.ids])
+        return self.o.time_derivative(Us)[:, self.lsel]

@@ -34,6 +34,12 @@ CASES = [
     ("sine_n5_central_euler", I.BoxSpec(5, 2, 2, 2, geometry="sine", amplitude=0.2), 0, 0, "tgv_shift"),
     ("sine_n4_roe_sonic", I.BoxSpec(4, 3, 2, 2, geometry="sine", amplitude=0.2), 2, 1, "tgv_sonic"),
     ("tgv_n3_llf_sonic", I.BoxSpec(3, 3, 2, 2), 1, 1, "tgv_sonic"),
+    # N = 7: the adjoint element kernel's even/odd contractions and its warp
+    # layout (the path of the benchmarked VJP), curved, viscous, Roe; the
+    # sonic state puts part of the xi faces inside Harten's entropy fix
+    ("sine_n7_roe", I.BoxSpec(7, 2, 2, 2, geometry="sine", amplitude=0.2), 2, 1, "tgv_shift"),
+    ("sine_n7_roe_sonic", I.BoxSpec(7, 2, 2, 2, geometry="sine", amplitude=0.2), 2, 1, "tgv_sonic"),
+    ("sine_n7_llf_ragged", I.BoxSpec(7, 3, 1, 2, geometry="sine", amplitude=0.1), 1, 1, "tgv_shift"),
 ]
 
 
@@ -52,17 +58,18 @@ def test_dot_product_against_oracle_jvp(ora, label, spec, surf, visc, ic):
         assert abs(a - b) <= 1e-11 * (np.abs(lam * Jd).sum())
 
 
-@pytest.mark.parametrize("law", [1, 0])
-def test_channel_state_and_parameters(ora, law):
+@pytest.mark.parametrize("N,law", [(3, 1), (3, 0), (5, 1), (5, 0)])
+def test_channel_state_and_parameters(ora, N, law):
+    # N = 5 is the degree of the wall-modelled channel workload
     torch = torch_cuda()
-    wl = I.workload("channel_n5", N=3, elems=(4, 4, 2))
+    wl = I.workload("channel_n5", N=N, elems=(4, 4, 2))
     o, g, X, U = case(ora, wl.spec, wl.phys, surf_flux=2, law=law, ic="channel")
     lam = I.random_direction(U.shape, seed=6)
     gU, gth = _vjp(torch, g, U, lam)
     d = I.random_direction(U.shape, seed=7) * np.abs(U)
     _, Jd = o.jvp(U, d)
     a = float((lam * Jd).sum()); b = float((gU * d).sum())
-    print("channel law", law, "dot", a, b)
+    print("channel N", N, "law", law, "dot", a, b)
     assert abs(a - b) <= 1e-11 * np.abs(lam * Jd).sum()
     for k, (dk, dB) in enumerate(((1.0, 0.0), (0.0, 1.0))):
         _, Jt = o.jvp(U, None, dk, dB)
@@ -96,9 +103,10 @@ def test_full_transpose_on_tiny_mesh(ora, label, spec, ic, law):
     assert err <= 1e-10
 
 
-def test_finite_differences_of_the_gpu_operator(ora):
+@pytest.mark.parametrize("N", [3, 5])
+def test_finite_differences_of_the_gpu_operator(ora, N):
     torch = torch_cuda()
-    wl = I.workload("channel_n5", N=3, elems=(4, 4, 2))
+    wl = I.workload("channel_n5", N=N, elems=(4, 4, 2))
     o, g, X, U = case(ora, wl.spec, wl.phys, surf_flux=2, law=1, ic="channel")
     lam = I.random_direction(U.shape, seed=10)
     gU, gth = _vjp(torch, g, U, lam)
@@ -125,3 +133,24 @@ def test_finite_differences_of_the_gpu_operator(ora):
         fdt = float((lam * (vals[0] - vals[1])).sum()) / (2 * eps)
         print("FD", key, fdt, gth[k])
         assert abs(fdt - gth[k]) <= 1e-6 * abs(gth[k])
+
+
+def test_full_transpose_at_n7_one_element(ora):
+    """N = 7 on one periodic curved element (each face its own neighbour):
+    J^T lam against J assembled from the oracle's 2560 JVP columns, so that
+    every entry of the even/odd adjoint element kernel is checked, not only
+    its action on random directions."""
+    torch = torch_cuda()
+    phys = I.phys_params(Ma=0.3, Re=200.0)
+    spec = I.BoxSpec(7, 1, 1, 1, geometry="sine", amplitude=0.2)
+    o, g, X, U = case(ora, spec, phys, surf_flux=2, ic="tgv_shift", rel=1e-2, extended=False)
+    lam = I.random_direction(U.shape, seed=12)
+    gU, _ = _vjp(torch, g, U, lam)
+    ref = np.zeros(U.size)
+    for k in range(U.size):
+        e = np.zeros(U.size); e[k] = 1.0
+        _, col = o.jvp(U, e.reshape(U.shape))
+        ref[k] = float((lam.reshape(-1) * col.reshape(-1)).sum())
+    err = np.abs(gU.reshape(-1) - ref).max() / np.abs(ref).max()
+    print("n7 one element J^T lam max rel", err)
+    assert err <= 1e-10

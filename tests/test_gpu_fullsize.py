@@ -1,17 +1,20 @@
-"""Parity at the full benchmark size, in the bench's launch configuration.
+"""Parity at the full benchmark sizes, in the bench's launch configuration.
 
-Taylor-Green, N = 7, 32^3 elements (16.8M DOF, Roe, BR1): the GPU operator
-and one fused LSERK4 stage are compared with the extended-precision oracle
-on a seeded sample of elements (the oracle evaluates those elements and the
-two neighbour rings they depend on).  The 48^3 sine-mapped case (56.6M DOF)
-runs when DG_FULLSIZE_LARGE=1 (it needs ~40 GB of host memory)."""
-import os
-
+Taylor-Green, N = 7, 32^3 elements (16.8M DOF, Roe, BR1) and the 48^3
+sine-mapped box at Ma 0.3 (56.6M DOF): the GPU operator on the whole mesh and
+one fused LSERK4 stage are compared with the extended-precision oracle on a
+seeded sample of elements.  The oracle runs on the sub-mesh of the sampled
+elements and the two rings of face neighbours their time derivative depends
+on (primitives of ring 2, lifted gradients of ring 1); faces leaving that
+sub-mesh become outflow boundaries, which touch only ring 2, whose lifting
+and time derivative the oracle's subset evaluation skips.  The FP32-mixed
+form is held to the 1e-5 relative L2 goal on the 32^3 case."""
 import numpy as np
 import pytest
 
 from paper_2606_18927_gb300 import dg, inputs as I
 from gpu_helpers import parity_per_var, torch_cuda
+from helpers import SampledOracle
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-12
@@ -30,8 +33,8 @@ def _full_case(ora, name, count=12):
     nbr = I.connectivity(wl.spec)
     U = I.initial_state(wl, X)
     sel = _sample(wl.spec.K, count, seed=99)
-    o = ora.Oracle(wl.spec.N, X, nbr, wl.phys, vol_flux=wl.vol_flux, surf_flux=wl.surf_flux, extended=True,
-                   subset=sel)
+    o = SampledOracle(ora, wl.spec.N, X, nbr, wl.phys, sel, vol_flux=wl.vol_flux,
+                       surf_flux=wl.surf_flux)
     return torch, wl, X, nbr, U, sel, o
 
 
@@ -41,9 +44,9 @@ def _check(torch, wl, X, nbr, U, sel, o, precision, tol):
     Ud = torch.from_numpy(U).cuda()
     Ut = torch.empty_like(Ud)
     g.time_derivative(Ut, Ud)
-    ref = o.time_derivative(U)
+    ref = o.time_derivative_on_sample(U)
     got = Ut.cpu().numpy()[:, sel]
-    e = parity_per_var(got, ref[:, sel])
+    e = parity_per_var(got, ref)
     print(wl.name, "precision", precision, "sampled Ut parity", ["%.1e" % v for v in e])
     if precision == dg.FP64:
         assert max(e) <= tol
@@ -54,11 +57,11 @@ def _check(torch, wl, X, nbr, U, sel, o, precision, tol):
         dUg = torch.empty_like(Ud)
         g.get_rk_register(dUg)
         g.check_status()
-        e2 = parity_per_var(dUg.cpu().numpy()[:, sel], dt * ref[:, sel])
+        e2 = parity_per_var(dUg.cpu().numpy()[:, sel], dt * ref)
         print(wl.name, "sampled stage register parity", ["%.1e" % v for v in e2])
         assert max(e2) <= tol
     else:
-        a = got.reshape(5, -1); b = ref[:, sel].reshape(5, -1)
+        a = got.reshape(5, -1); b = ref.reshape(5, -1)
         l2 = [float(np.linalg.norm(a[v] - b[v]) / np.linalg.norm(b[v])) for v in range(5)]
         print(wl.name, "mixed sampled rel L2", ["%.1e" % v for v in l2])
         assert max(l2) <= tol
@@ -68,10 +71,9 @@ def _check(torch, wl, X, nbr, U, sel, o, precision, tol):
 def test_tgv_n7_32_full_size(ora):
     torch, wl, X, nbr, U, sel, o = _full_case(ora, "tgv_n7_32")
     _check(torch, wl, X, nbr, U, sel, o, dg.FP64, TOL)
-    _check(torch, wl, X, nbr, U, sel, o, dg.FP32_MIXED, 1e-3)
+    _check(torch, wl, X, nbr, U, sel, o, dg.FP32_MIXED, 1e-5)
 
 
-@pytest.mark.skipif(os.environ.get("DG_FULLSIZE_LARGE") != "1", reason="set DG_FULLSIZE_LARGE=1 (56.6M DOF)")
 def test_tgv_sine_n7_48_full_size(ora):
     torch, wl, X, nbr, U, sel, o = _full_case(ora, "tgv_sine_n7_48", count=8)
     _check(torch, wl, X, nbr, U, sel, o, dg.FP64, TOL)

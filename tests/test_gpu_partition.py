@@ -1,12 +1,35 @@
 """Partitioned meshes on one GPU: the ranks of a space-filling-curve
-partition (paper Sec. 2.3) as contexts in one process, their halo exchanges
+partition (paper Sec. 2.1) as contexts in one process, their halo exchanges
 done by device copies between the phases.  Every stage must reproduce the
-unpartitioned context bitwise; the time derivative likewise."""
+unpartitioned context bitwise; the time derivative likewise.  The assembled
+partitioned results are also compared with the extended-precision oracle
+directly (relative max norm 1e-12 in FP64, relative L2 1e-5 in the
+FP32-mixed form)."""
 import numpy as np
 import pytest
 
 from paper_2606_18927_gb300 import dg, halo, inputs as I
-from gpu_helpers import tgv_with_offset, torch_cuda
+from gpu_helpers import parity, tgv_with_offset, torch_cuda
+
+TOL = 1e-12
+
+
+def _oracle_check(ora, spec, X, nbr, phys, U, ut, state, dt, nsteps, opts, law=1):
+    """Partitioned Ut and state increment over nsteps against the oracle."""
+    o = ora.Oracle(spec.N, X, nbr, phys, vol_flux=opts.get("vol_flux", 0), surf_flux=opts.get("surf_flux", 1),
+                   viscous=opts.get("viscous", 1), law=law, extended=True)
+    ref_ut = o.time_derivative(U)
+    ref_inc = o.rk_steps(U, dt, nsteps) - U
+    got_ut = ut.cpu().numpy(); got_inc = state.cpu().numpy() - U
+    if opts.get("precision", dg.FP64) == dg.FP64:
+        e1 = parity(got_ut, ref_ut); e2 = parity(got_inc, ref_inc)
+        print("  vs oracle: Ut", e1, "state increment", e2)
+        assert e1 <= TOL and e2 <= TOL
+    else:
+        a = got_ut.reshape(5, -1); b = ref_ut.reshape(5, -1)
+        l2 = max(float(np.linalg.norm(a[v] - b[v]) / np.linalg.norm(b[v])) for v in range(5))
+        print("  vs oracle (mixed): Ut rel L2", l2)
+        assert l2 <= 1e-5
 
 pytestmark = pytest.mark.gpu
 
@@ -19,7 +42,7 @@ def _setup(spec, phys, **opts):
     return X, nbr, U
 
 
-def _compare(torch, spec, phys, P, nsteps=2, **opts):
+def _compare(torch, spec, phys, P, nsteps=2, ora=None, **opts):
     X, nbr, U = _setup(spec, phys)
     Ud = torch.from_numpy(U).cuda()
     g = dg.Operator(spec.N, X, nbr, phys, **opts)
@@ -43,36 +66,38 @@ def _compare(torch, spec, phys, P, nsteps=2, **opts):
     torch.cuda.synchronize()
     nh = [len(h) for h in ranks.halo]
     ranks.close(); g.close()
+    if ora is not None:
+        _oracle_check(ora, spec, X, nbr, phys, U, ut, out, dt, nsteps, opts)
     return ref, out, ut_ref, ut, nh
 
 
 @pytest.mark.parametrize("P", [2, 3, 5])
-def test_partitioned_tgv_bitwise(P):
+def test_partitioned_tgv_bitwise(ora, P):
     torch = torch_cuda()
     phys = I.phys_params(Ma=0.1, Re=1600.0)
     spec = I.BoxSpec(3, 4, 4, 3, geometry="sine", amplitude=0.2)
-    ref, out, ut_ref, ut, nh = _compare(torch, spec, phys, P, surf_flux=2)
+    ref, out, ut_ref, ut, nh = _compare(torch, spec, phys, P, ora=ora, surf_flux=2)
     print("TGV P", P, "halo faces", nh)
     assert min(nh) > 0
     assert torch.equal(out, ref)
     assert torch.equal(ut, ut_ref)
 
 
-def test_partitioned_tgv_n7_bitwise():
+def test_partitioned_tgv_n7_bitwise(ora):
     # N = 7 runs the even/odd lifting contractions, the once-formed
     # half-distance pairs and the swizzled shared-memory layout of the volume
     # kernel; the halo faces take the FP64 primitives the lifting kernel keeps
     torch = torch_cuda()
     phys = I.phys_params(Ma=0.1, Re=1600.0)
     spec = I.BoxSpec(7, 4, 2, 2, geometry="sine", amplitude=0.1)
-    ref, out, ut_ref, ut, nh = _compare(torch, spec, phys, 3, surf_flux=2)
+    ref, out, ut_ref, ut, nh = _compare(torch, spec, phys, 3, ora=ora, surf_flux=2)
     assert min(nh) > 0
     assert torch.equal(out, ref)
     assert torch.equal(ut, ut_ref)
 
 
 @pytest.mark.parametrize("P", [2, 5])
-def test_partitioned_tgv_mixed(P):
+def test_partitioned_tgv_mixed(ora, P):
     # the FP32 flux arithmetic of a halo face runs in another kernel than that
     # of an interior face, where the compiler may contract it differently:
     # agreement to FP32 rounding of the fluxes, not bitwise
@@ -81,26 +106,26 @@ def test_partitioned_tgv_mixed(P):
     spec = I.BoxSpec(3, 4, 4, 3, geometry="sine", amplitude=0.2)
     X, nbr, U = _setup(spec, phys)
     U0 = torch.from_numpy(U).cuda()
-    ref, out, ut_ref, ut, nh = _compare(torch, spec, phys, P, precision=dg.FP32_MIXED, surf_flux=2)
+    ref, out, ut_ref, ut, nh = _compare(torch, spec, phys, P, ora=ora, precision=dg.FP32_MIXED, surf_flux=2)
     e_state = float((out - ref).abs().max() / (ref - U0).abs().max())
     e_ut = max(float((ut[v] - ut_ref[v]).abs().max() / ut_ref[v].abs().max()) for v in range(5))
     print("mixed P", P, "state increment diff", e_state, "Ut diff", e_ut, "bitwise", torch.equal(out, ref))
     assert e_state <= 1e-5 and e_ut <= 1e-5
 
 
-def test_partitioned_production_scheme_with_inflow_outflow_bitwise():
+def test_partitioned_production_scheme_with_inflow_outflow_bitwise(ora):
     torch = torch_cuda()
     phys = I.phys_params(Ma=0.3, Re=400.0, sutherland=True)
     g0, p0 = phys["gamma"], phys["p0"]
     phys.update(U_in=np.array([1.0, 0.5, 0.0, 0.0, p0 / (g0 - 1) + 0.125]), p_out=0.99 * p0)
     spec = I.BoxSpec(4, 5, 2, 3, geometry="sine", amplitude=0.1, periodic=(False, True, True),
                      boundary=((I.INFLOW, I.OUTFLOW), (I.WALL, I.WALL), (I.WALL, I.WALL)))
-    ref, out, ut_ref, ut, nh = _compare(torch, spec, phys, 3, vol_flux=dg.VOL_EC_CHANDRASHEKAR, surf_flux=2)
+    ref, out, ut_ref, ut, nh = _compare(torch, spec, phys, 3, ora=ora, vol_flux=dg.VOL_EC_CHANDRASHEKAR, surf_flux=2)
     assert torch.equal(out, ref) and torch.equal(ut, ut_ref)
 
 
 @pytest.mark.parametrize("P", [2, 4])
-def test_partitioned_wall_modelled_channel_bitwise(P):
+def test_partitioned_wall_modelled_channel_bitwise(ora, P):
     torch = torch_cuda()
     wl = I.workload("channel_n5", N=3, elems=(8, 4, 4))
     X, nbr, U = _setup(wl.spec, wl.phys)
@@ -119,6 +144,11 @@ def test_partitioned_wall_modelled_channel_bitwise(P):
     ranks.get_state(out)
     ranks.check_status()
     assert torch.equal(out, ref)
+    ut = torch.empty_like(Ud)
+    ranks.time_derivative(ut, Ud)
+    torch.cuda.synchronize()
+    ranks.close(); g.close()
+    _oracle_check(ora, wl.spec, X, nbr, wl.phys, U, ut, out, dt, 2, dict(surf_flux=2), law=1)
 
 
 def test_fused_calls_refuse_partitioned_contexts():

@@ -15,8 +15,8 @@ pytestmark = pytest.mark.gpu
 NSTEPS = 20
 
 
-def _setup(ora, law=1, extended=False):
-    wl = I.workload("channel_n5", N=3, elems=(4, 4, 2))
+def _setup(ora, law=1, extended=False, N=3, elems=(4, 4, 2)):
+    wl = I.workload("channel_n5", N=N, elems=elems)
     o, g, X, U = case(ora, wl.spec, wl.phys, surf_flux=2, law=law, ic="channel", extended=extended)
     dt = 0.5 * o.dt(U, 0.9)
     return wl, o, g, X, U, dt
@@ -31,10 +31,12 @@ def test_wall_shear_loss_matches_oracle(ora):
     assert abs(L - ref) <= 1e-12 * abs(ref)
 
 
-@pytest.mark.parametrize("law", [1, 0])
-def test_rollout_gradient_matches_oracle_derivative(ora, law):
+# (16, 8, 8) at N = 5 is the full wall-modelled channel workload (221,184 DOF)
+@pytest.mark.parametrize("N,elems,law", [(3, (4, 4, 2), 1), (3, (4, 4, 2), 0), (5, (4, 4, 2), 0),
+                                         (5, (16, 8, 8), 1)])
+def test_rollout_gradient_matches_oracle_derivative(ora, N, elems, law):
     torch = torch_cuda()
-    wl, o, g, X, U, dt = _setup(ora, law)
+    wl, o, g, X, U, dt = _setup(ora, law, N=N, elems=elems)
     Ud = torch.from_numpy(U).cuda()
     gU0 = torch.empty_like(Ud)
     gth = torch.zeros(2, dtype=torch.float64, device="cuda")
@@ -46,16 +48,17 @@ def test_rollout_gradient_matches_oracle_derivative(ora, law):
     _, dLB = o.rollout_jvp(U, None, 0.0, 1.0, NSTEPS, dt)
     ad = float((gU0.cpu().numpy() * d).sum())
     th = gth.cpu().numpy()
-    print("law", law, "loss", L, L_ref, "dU0", ad, dL, "dkappa", th[0], dLk, "dB", th[1], dLB)
+    print("N", N, elems, "law", law, "loss", L, L_ref, "dU0", ad, dL, "dkappa", th[0], dLk, "dB", th[1], dLB)
     assert abs(L - L_ref) <= 1e-11 * abs(L_ref)
     assert abs(ad - dL) <= 1e-9 * abs(dL)
     assert abs(th[0] - dLk) <= 1e-9 * abs(dLk)
     assert abs(th[1] - dLB) <= 1e-9 * abs(dLB)
 
 
-def test_rollout_gradient_finite_differences(ora):
+@pytest.mark.parametrize("N", [3, 5])
+def test_rollout_gradient_finite_differences(ora, N):
     torch = torch_cuda()
-    wl, o, g, X, U, dt = _setup(ora)
+    wl, o, g, X, U, dt = _setup(ora, N=N)
     Ud = torch.from_numpy(U).cuda()
     gU0 = torch.empty_like(Ud)
     gth = torch.zeros(2, dtype=torch.float64, device="cuda")

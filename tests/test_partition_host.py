@@ -1,4 +1,4 @@
-"""Host logic of the partitioned meshes (paper Sec. 2.3: space-filling-curve
+"""Host logic of the partitioned meshes (paper Sec. 2.1: space-filling-curve
 subdomains): the partition, the local meshes and the pairing of their halo
 faces.  The library's host functions run without a GPU."""
 import numpy as np
