@@ -43,6 +43,7 @@ def lib(extended=False):
         L.ora_get_metrics.argtypes = [vp, dp, dp]
         L.ora_num_wall.argtypes = [vp]
         L.ora_get_wall_samples.argtypes = [vp, ip, dp]
+        L.ora_get_wall_weights.argtypes = [vp, dp]
         L.ora_time_derivative.argtypes = [vp, dp, ctypes.c_double, dp]
         L.ora_wall_heat.argtypes = [vp, dp, dp]
         L.ora_jvp.argtypes = [vp, dp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp]
@@ -155,6 +156,13 @@ class Oracle:
         el = np.zeros(nw, dtype=np.int32); ref = np.zeros((nw, 3))
         self.L.ora_get_wall_samples(self.h, _ip(el), _p(ref))
         return el, ref
+
+    def wall_weights(self):
+        """Lagrange weights of the wall samples, [n_wall][3][n]."""
+        nw = self.L.ora_num_wall(self.h)
+        out = np.zeros((nw, 3, self.n))
+        self.L.ora_get_wall_weights(self.h, _p(out))
+        return out
 
     def time_derivative(self, U, t=0.0):
         U = _f64(U); Ut = np.zeros_like(U)

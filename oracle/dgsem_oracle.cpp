@@ -353,10 +353,12 @@ static bool check_connectivity(const Mesh& M, std::string& err) {
 // Wall-model sampling points (reading of Sec. 3.1: the wall model samples
 // the LES solution at distance h_wm from the wall): for every wall face node
 // the point x_w - h_wm * n_out is located by Newton on each candidate
-// element's polynomial mapping.  The lowest-index element that contains it
-// (max |xi| <= 1 + 1e-8) is used: points on a face shared by two elements
-// (e.g. above an edge node of the wall face) then get one well-defined
-// element although the DG solution is discontinuous there.
+// element's polynomial mapping.  The first element that contains it
+// (max |xi| <= 1 + 1e-8) is used, searching the wall element's column first
+// (the wall element, then its neighbours across the faces opposite the wall,
+// up to 3 layers) and then all elements by ascending index: points on a face
+// shared by two elements (e.g. above an edge node of the wall face) then get
+// one well-defined element although the DG solution is discontinuous there.
 static bool locate_point(const Mesh& M, int e, const real xs[3], real ref[3]) {
   const int n = M.n, n3 = M.n3, K = M.K;
   real r[3] = {0.0, 0.0, 0.0};
@@ -1312,6 +1314,15 @@ int ora_get_wall_samples(void* h, int* elem, double* ref) {
     elem[s] = c->M.ws_elem[s];
     for (int d = 0; d < 3; ++d) ref[s * 3 + d] = (double)c->M.ws_ref[s * 3 + d];
   }
+  return 0;
+}
+
+// Lagrange weights of the wall-model samples: l[slot][3][n] (per reference
+// direction, the weights of the n nodes at the sample's coordinate).
+int ora_get_wall_weights(void* h, double* l) {
+  Ctx* c = (Ctx*)h;
+  const size_t cnt = (size_t)c->M.nwall * 3 * c->M.n;
+  for (size_t x = 0; x < cnt; ++x) l[x] = (double)c->M.ws_l[x];
   return 0;
 }
 

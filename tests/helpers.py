@@ -74,3 +74,18 @@ class SampledOracle:
         """Ut of the sampled elements, [5][len(sel)][n^3]."""
         Us = np.ascontiguousarray(U.reshape(5, self.K, -1)[:, self.ids])
         return self.o.time_derivative(Us)[:, self.lsel]
+
+
+def bump_wall(X, A=0.15):
+    """Bottom wall y = A s(x) s(z), s(t) = sin^2(t - pi/2) on pi/2 < t < 3 pi/2
+    and 0 elsewhere (continuous with its slope; the mesh lines x, z = pi/2,
+    3 pi/2 bound the curved part), blended linearly to the flat top wall
+    y = 2.  A sample point is located in the mesh as it is, without periodic
+    images, so the elements at the periodic boundaries are kept affine (their
+    discrete normals are exactly +-y and no sample leaves through them)."""
+    x, y, z = X
+
+    def s(t):
+        return np.where((t > np.pi / 2) & (t < 1.5 * np.pi), np.sin(t - np.pi / 2) ** 2, 0.0)
+
+    return np.ascontiguousarray(np.stack([x, y + A * s(x) * s(z) * (1 - y / 2), z]))

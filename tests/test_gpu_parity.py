@@ -254,3 +254,25 @@ def test_wall_side_stream_and_graph_on_channel(ora):
     prof = g.profile_read()
     g.profile_enable(False)
     assert prof["wall"][1] == 1 and prof["wall"][0] > 0.0
+
+
+@pytest.mark.parametrize("N", [3, 5])
+def test_curved_wall_model_matches_oracle(ora, N):
+    """Wall model on a curved wall (a bump of the lower wall): the sample
+    points leave their wall elements at some nodes, so the CUDA path's host
+    geometry must locate them in the same elements and at the same reference
+    coordinates as the oracle (Sec. 3.2; reading R10)."""
+    from helpers import bump_wall
+    torch = torch_cuda()
+    phys = I.phys_params(Ma=0.2, Re=2000.0, force=(0.01, 0.0, 0.0), hwm=0.3)
+    spec = I.BoxSpec(N, 4, 3, 4, lengths=(2 * math.pi, 2.0, 2 * math.pi), periodic=(True, False, True))
+    x, w, D = ora.lgl(N)
+    X = bump_wall(I.node_coordinates(spec, x))
+    nbr = I.connectivity(spec)
+    from paper_2606_18927_gb300 import dg
+    o = ora.Oracle(N, X, nbr, phys, surf_flux=2, law=1, extended=True)
+    g = dg.Operator(N, X, nbr, phys, surf_flux=2, law=1)
+    U = I.channel_profile(X, phys)
+    e = parity(gpu_ut(torch, g, U), o.time_derivative(U))
+    print("curved wall N", N, "parity", e)
+    assert e <= TOL, e
