@@ -85,20 +85,41 @@ enum dg_wall_law { DG_LAW_SPALDING = 0, DG_LAW_REICHARDT = 1 };
 
 typedef struct dg_ctx dg_ctx;
 
-/* Mesh of K hexahedra of degree N (paper Sec. 2.2: tensor-product LGL nodes).
- *   X   host, double[3][K][n^3]: node coordinates at the LGL nodes returned by
- *       dg_lgl_nodes (degree-N geometry).  Copied during dg_init_mesh.
- *   nbr host, int[K][6]: neighbour across local face l (0 -xi, 1 +xi, 2 -eta,
- *       3 +eta, 4 -zeta, 5 +zeta).  A neighbour e' must list e across face
- *       l^1 and share its face nodes in the same order (faces may differ by
- *       one translation: periodic images).  Negative entries are boundary
- *       codes (DG_BC_WALL, DG_BC_INFLOW, DG_BC_OUTFLOW).  Copied during
- *       dg_init_mesh. */
+/* Mesh of K conforming hexahedra of degree N (paper Sec. 2.2: tensor-product
+ * LGL nodes; the unstructured meshes of Sec. 4 and the space-filling-curve
+ * subdomains of Sec. 2.1).
+ *   X        host, double[3][K][n^3]: node coordinates at the LGL nodes
+ *            returned by dg_lgl_nodes (degree-N geometry).
+ *   nbr      host, int[K][6]: neighbour across local face l (0 -xi, 1 +xi,
+ *            2 -eta, 3 +eta, 4 -zeta, 5 +zeta), or a negative boundary code
+ *            (DG_BC_WALL, DG_BC_INFLOW, DG_BC_OUTFLOW, halo codes).
+ *   nbr_face host, int[K][6] or NULL: the neighbour's local face that face l
+ *            is joined to (NULL: l ^ 1 everywhere, the structured case).
+ *   orient   host, int[K][6] or NULL (all 0): orientation code o in 0..7 of
+ *            the joined faces.  Face-local node coordinates (a, b) in 0..N
+ *            are (j, k) on the xi faces, (i, k) on the eta faces and (i, j) on
+ *            the zeta faces; node (a, b) of face l of e coincides with node
+ *            (a', b') of face nbr_face[e][l] of nbr[e][l], where
+ *              (s, t) = (o & 1) ? (b, a) : (a, b),
+ *              a' = (o & 2) ? N - s : s,   b' = (o & 4) ? N - t : t.
+ *            The neighbour must list e back with the inverse code (o with
+ *            the bits 2 and 4 exchanged when bit 1 is set, else o itself).
+ *            On the local mesh of a partition (dg_partition_local) a halo
+ *            face's code carries 8 when the local element is the face's
+ *            master.
+ * The joined faces must coincide node by node up to one translation
+ * (periodic images), else DG_ERR_MESH.  Each interior face is evaluated once,
+ * from its master side (the side with the odd local face when the two local
+ * faces differ in parity, else the side with the smaller (element, face)
+ * pair), whose metrics give the face normal.  All arrays are copied during
+ * dg_init_mesh. */
 typedef struct {
   int N;
   int K;
   const double* X;
   const int* nbr;
+  const int* nbr_face;
+  const int* orient;
 } dg_mesh_desc;
 
 /* Ideal gas and wall-model constants (paper Sec. 4: ideal gas with
@@ -289,17 +310,22 @@ int dg_check_status(dg_ctx* c);
  * dg_partition_local: the local mesh of `rank`: K_local elements (its own,
  *   in ascending global order; l2g[K_local] their global ids), nbr_local
  *   [K_local][6] with local neighbours, the global boundary codes, and
- *   DG_BC_HALO_BASE - h for the h-th face shared with another rank.
+ *   DG_BC_HALO_BASE - h for the h-th face shared with another rank;
+ *   nbr_face_local and orient_local [K_local][6] (may be NULL) the neighbour
+ *   faces and orientation codes of the local elements (from nbr_face and
+ *   orient, which may be NULL for the structured case), with 8 added to the
+ *   code of a halo face whose master is the local element.
  *   halo[n_halo][4] (peer rank, local element, local face, 1 if the local
- *   element is the face's master, i.e. it is its +xi/+eta/+zeta face).  The
- *   halo faces are ordered by peer, then by (global master element, master
- *   face), so two ranks list the faces they share in the same order and their
- *   halo buffers line up.  Call once with NULL arrays to get K_local and
- *   n_halo, then with arrays of those sizes.
+ *   element is the face's master by the rule of dg_mesh_desc).  The halo
+ *   faces are ordered by peer, then by (global master element, master face),
+ *   so two ranks list the faces they share in the same order and their halo
+ *   buffers line up.  Call once with NULL arrays to get K_local and n_halo,
+ *   then with arrays of those sizes.
  *
- * A context built from a local mesh (dg_init_mesh with nbr_local) owns halo
- * buffers: recv_U/send_U double[n_halo][5][n^2] (state traces at the halo
- * faces' nodes, in the local face's node order, which the neighbour shares)
+ * A context built from a local mesh (dg_init_mesh with nbr_local,
+ * nbr_face_local and orient_local) owns halo buffers: recv_U/send_U
+ * double[n_halo][5][n^2] (state traces at the halo faces' nodes, in the
+ * face-node order of the face's master, which both ranks know)
  * and recv_G/send_G [n_halo][4][n^2] in the flux type (float in the
  * FP32-mixed form): each side's outward viscous flux there.  The caller moves
  * send_* of one rank into recv_* of the peer (the rows of the faces they
@@ -319,8 +345,9 @@ int dg_check_status(dg_ctx* c);
  * Results equal those of the unpartitioned mesh bitwise.
  * ------------------------------------------------------------------------- */
 int dg_partition_sfc(int N, int K, const double* X, int nranks, int* part);
-int dg_partition_local(int K, const int* nbr, const int* part, int rank, int* K_local, int* l2g, int* nbr_local,
-                       int* n_halo, int* halo);
+int dg_partition_local(int K, const int* nbr, const int* nbr_face, const int* orient, const int* part, int rank,
+                       int* K_local, int* l2g, int* nbr_local, int* nbr_face_local, int* orient_local, int* n_halo,
+                       int* halo);
 int dg_halo_buffers(dg_ctx* c, int* n_halo, void** send_U, void** recv_U, void** send_G, void** recv_G);
 int dg_halo_geometry(dg_ctx* c, double* fgeo);
 int dg_halo_set_geometry(dg_ctx* c, const double* fgeo);

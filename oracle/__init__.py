@@ -34,9 +34,9 @@ def lib(extended=False):
         L.ora_lserk4.argtypes = [dp, dp, dp]
         L.ora_set_threads.argtypes = [ctypes.c_int]
         L.ora_max_threads.restype = ctypes.c_int
-        L.ora_create.argtypes = [ctypes.c_int, ctypes.c_int, dp, ip, dp, ip, ctypes.c_char_p, ctypes.c_int]
+        L.ora_create.argtypes = [ctypes.c_int, ctypes.c_int, dp, ip, ip, ip, dp, ip, ctypes.c_char_p, ctypes.c_int]
         L.ora_create.restype = vp
-        L.ora_create_subset.argtypes = [ctypes.c_int, ctypes.c_int, dp, ip, dp, ip, ctypes.c_int, ip,
+        L.ora_create_subset.argtypes = [ctypes.c_int, ctypes.c_int, dp, ip, ip, ip, dp, ip, ctypes.c_int, ip,
                                         ctypes.c_char_p, ctypes.c_int]
         L.ora_create_subset.restype = vp
         L.ora_destroy.argtypes = [vp]
@@ -116,9 +116,11 @@ class Oracle:
     rounds the results to double: the parity reference.  subset: element
     indices; Ut is then evaluated on those elements only (the rest of the
     output is 0), which lets the oracle sample meshes too large to evaluate
-    whole."""
+    whole.  nbr_face, orient: [K, 6] neighbour faces and orientation codes of
+    a general conforming mesh (None: the structured default)."""
 
-    def __init__(self, N, X, nbr, phys, vol_flux=0, surf_flux=1, viscous=1, law=1, extended=False, subset=None):
+    def __init__(self, N, X, nbr, phys, vol_flux=0, surf_flux=1, viscous=1, law=1, extended=False, subset=None,
+                 nbr_face=None, orient=None):
         self.L = lib(extended)
         self.extended = extended
         self.N = int(N)
@@ -127,15 +129,20 @@ class Oracle:
         X = _f64(X)
         self.K = X.size // (3 * self.n3)
         nbr = np.ascontiguousarray(nbr, dtype=np.int32)
+        nf = None if nbr_face is None else np.ascontiguousarray(nbr_face, dtype=np.int32)
+        ori = None if orient is None else np.ascontiguousarray(orient, dtype=np.int32)
+        pnf = None if nf is None else _ip(nf)
+        por = None if ori is None else _ip(ori)
         self._phys = phys_array(phys)
         opts = np.array([vol_flux, surf_flux, viscous, law], dtype=np.int32)
         err = ctypes.create_string_buffer(512)
         if subset is None:
-            self.h = self.L.ora_create(self.N, self.K, _p(X), _ip(nbr), _p(self._phys), _ip(opts), err, 512)
+            self.h = self.L.ora_create(self.N, self.K, _p(X), _ip(nbr), pnf, por, _p(self._phys), _ip(opts), err,
+                                       512)
         else:
             sel = np.ascontiguousarray(subset, dtype=np.int32)
-            self.h = self.L.ora_create_subset(self.N, self.K, _p(X), _ip(nbr), _p(self._phys), _ip(opts),
-                                              int(sel.size), _ip(sel), err, 512)
+            self.h = self.L.ora_create_subset(self.N, self.K, _p(X), _ip(nbr), pnf, por, _p(self._phys),
+                                              _ip(opts), int(sel.size), _ip(sel), err, 512)
         if not self.h:
             raise ValueError("oracle mesh rejected: " + err.value.decode())
         self.shape = (5, self.K, self.n3)

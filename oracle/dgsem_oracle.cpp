@@ -210,14 +210,22 @@ struct Opts {
 // ---------------------------------------------------------------------------
 // Mesh: nodes X[c][e][p] (p = i + n (j + n k)), neighbours nbr[e][l]
 // (l = 0:-xi 1:+xi 2:-eta 3:+eta 4:-zeta 5:+zeta; value >= 0 is the
-// neighbour element whose face l^1 is shared with orientation identity;
-// -1 is a wall-modelled slip wall).
+// neighbour element, negative values are boundary codes, -1 a wall-modelled
+// slip wall).  A conforming hexahedral mesh joins face l of e to face
+// nface[e][l] of the neighbour, whose face-local node (a', b') coincides with
+// node (a, b) of face l by the orientation code o = orient[e][l]:
+//   (s, t) = (o & 1) ? (b, a) : (a, b);  a' = (o & 2) ? N - s : s;
+//   b' = (o & 4) ? N - t : t
+// (face-local coordinates as in face_node below).  A structured mesh has
+// nface = l ^ 1 and o = 0 everywhere.
 // ---------------------------------------------------------------------------
 struct Mesh {
   int N = 0, n = 0, n2 = 0, n3 = 0, K = 0;
   std::vector<real> xi, w, D;
   std::vector<real> X;    // [3][K*n3]
   std::vector<int> nbr;     // [K*6]
+  std::vector<int> nface;   // [K*6] neighbour's local face
+  std::vector<int> orient;  // [K*6] orientation code (see above)
   std::vector<real> Ja;   // [(e*n3+p)*9 + dir*3 + comp]
   std::vector<real> J;    // [e*n3+p]
   // wall model: one slot per wall face node, ordered by (e, l, b, a)
@@ -252,6 +260,32 @@ inline int face_node(const Mesh& M, int l, int a, int b) {
   }
 }
 inline real face_sign(int l) { return (l & 1) ? 1.0 : -1.0; }
+
+// the node of the neighbour's face that coincides with node (a, b) of face
+// l of e (interior faces only)
+inline void neighbour_node(const Mesh& M, int e, int l, int a, int b, int* nb, int* q) {
+  const int o = M.orient[e * 6 + l];
+  const int s = (o & 1) ? b : a, t = (o & 1) ? a : b;
+  const int a2 = (o & 2) ? M.N - s : s, b2 = (o & 4) ? M.N - t : t;
+  *nb = M.nbr[e * 6 + l];
+  *q = face_node(M, M.nface[e * 6 + l], a2, b2);
+}
+
+// inverse of an orientation code
+inline int orient_inverse(int o) {
+  return (o & 1) ? (1 | (((o >> 2) & 1) << 1) | (((o >> 1) & 1) << 2)) : o;
+}
+
+// The side of an interior face whose metrics give the face normal and whose
+// node order indexes the face (reading R21, generalised to any pair of local
+// faces): the side with the odd local face (+xi, +eta, +zeta) when the two
+// local faces differ in parity, else the side with the smaller (element,
+// face) pair.
+inline bool is_master(const Mesh& M, int e, int l) {
+  const int nb = M.nbr[e * 6 + l], l2 = M.nface[e * 6 + l];
+  if ((l & 1) != (l2 & 1)) return (l & 1) != 0;
+  return e * 6 + l < nb * 6 + l2;
+}
 
 static bool build_metrics(Mesh& M, std::string& err) {
   const int n = M.n, n3 = M.n3, K = M.K;
@@ -330,12 +364,19 @@ static bool check_connectivity(const Mesh& M, std::string& err) {
       int nb = M.nbr[e * 6 + l];
       if (nb < BC_OUTFLOW || nb >= K) { err = "bad neighbour id"; return false; }
       if (nb < 0) continue;
-      if (M.nbr[nb * 6 + (l ^ 1)] != e) { err = "non-reciprocal connectivity"; return false; }
+      const int l2 = M.nface[e * 6 + l], o = M.orient[e * 6 + l];
+      if (l2 < 0 || l2 > 5 || o < 0 || o > 7) { err = "bad neighbour face or orientation"; return false; }
+      if (nb == e && l2 == l) { err = "a face cannot be its own neighbour"; return false; }
+      if (M.nbr[nb * 6 + l2] != e || M.nface[nb * 6 + l2] != l || M.orient[nb * 6 + l2] != orient_inverse(o)) {
+        err = "non-reciprocal connectivity";
+        return false;
+      }
       // faces must coincide up to one translation (periodic image)
       real shift[3];
       for (int b = 0; b < M.n; ++b)
         for (int a = 0; a < M.n; ++a) {
-          int p = face_node(M, l, a, b), q = face_node(M, l ^ 1, a, b);
+          int p = face_node(M, l, a, b), q, nbq;
+          neighbour_node(M, e, l, a, b, &nbq, &q);
           for (int c = 0; c < 3; ++c) {
             real dx = M.X[(size_t)c * K * n3 + (size_t)nb * n3 + q] -
                         M.X[(size_t)c * K * n3 + (size_t)e * n3 + p];
@@ -445,8 +486,9 @@ static bool build_wall_samples(Mesh& M, real hwm, std::string& err) {
           }
           int best = -1; real bref[3] = {0, 0, 0};
           // first the wall element's column: the wall element, then its
-          // neighbours across the faces opposite the wall (up to 3 layers)
-          for (int c2 = e, layer = 0; c2 >= 0 && layer < 4 && best < 0; ++layer) {
+          // neighbours across the faces opposite the wall (up to 3 layers;
+          // in each element the face opposite the one it was entered by)
+          for (int c2 = e, layer = 0, lin = l; c2 >= 0 && layer < 4 && best < 0; ++layer) {
             real ref[3];
             if (locate_point(M, c2, xs, ref)) {
               real rm = std::max(std::fabs(ref[0]), std::max(std::fabs(ref[1]), std::fabs(ref[2])));
@@ -455,7 +497,9 @@ static bool build_wall_samples(Mesh& M, real hwm, std::string& err) {
                 for (int c = 0; c < 3; ++c) bref[c] = ref[c];
               }
             }
-            c2 = M.nbr[c2 * 6 + (l ^ 1)];
+            const int lout = lin ^ 1, nxt = M.nbr[c2 * 6 + lout];
+            if (nxt >= 0) lin = M.nface[c2 * 6 + lout];
+            c2 = nxt;
           }
           // else the lowest-index element containing the point
           for (int c2 = 0; c2 < K && best < 0; ++c2) {
@@ -850,8 +894,12 @@ static void face_geometry(const Mesh& M, int e, int l, int a, int b, real nh[3],
   int nb = M.nbr[e * 6 + l];
   int me = e, ml = l;
   bool master = true;
-  if (nb >= 0 && (l & 1) == 0) { me = nb; ml = l ^ 1; master = false; }
-  int p = face_node(M, ml, a, b);
+  int p = face_node(M, l, a, b);
+  if (nb >= 0 && !is_master(M, e, l)) {
+    neighbour_node(M, e, l, a, b, &me, &p);
+    ml = M.nface[e * 6 + l];
+    master = false;
+  }
   const real* ja = &M.Ja[((size_t)me * M.n3 + p) * 9 + (ml / 2) * 3];
   real ss = std::sqrt(ja[0] * ja[0] + ja[1] * ja[1] + ja[2] * ja[2]);
   for (int c = 0; c < 3; ++c) nh[c] = face_sign(ml) * ja[c] / ss;
@@ -919,7 +967,8 @@ int time_derivative(const Mesh& M, const Phys<T>& P, const Opts& O, const T* U, 
           for (int w = 0; w < 4; ++w) Wo[w] = Wv(e, p, w);
           int nb = M.nbr[e * 6 + l];
           if (nb >= 0) {
-            int q = face_node(M, l ^ 1, a, b);
+            int q;
+            neighbour_node(M, e, l, a, b, &nb, &q);
             for (int w = 0; w < 4; ++w) Wn[w] = Wv(nb, q, w);
           } else if (nb == BC_WALL) {
             // slip wall: mirror state (normal velocity reversed, same T)
@@ -1046,7 +1095,8 @@ int time_derivative(const Mesh& M, const Phys<T>& P, const Opts& O, const T* U, 
         Prim<T> qm, qs;
         T gm[3][4], gs[3][4];
         if (nb >= 0) {
-          int q = face_node(M, l ^ 1, a, b);
+          int q;
+          neighbour_node(M, e, l, a, b, &nb, &q);
           T Un[5]; load_U(M, U, nb, q, Un);
           const Prim<T>& qn = W.q[(size_t)nb * n3 + q];
           if (own_master) {
@@ -1243,14 +1293,21 @@ int ora_max_threads(void) {
 #endif
 }
 
-static void* create_impl(int N, int K, const double* X, const int* nbr, const double* phys, const int* opts,
-                         int n_sel, const int* sel, char* err, int errlen) {
+static void* create_impl(int N, int K, const double* X, const int* nbr, const int* nface, const int* orient,
+                         const double* phys, const int* opts, int n_sel, const int* sel, char* err, int errlen) {
   Ctx* c = new Ctx();
   Mesh& M = c->M;
   M.N = N; M.n = N + 1; M.n2 = M.n * M.n; M.n3 = M.n2 * M.n; M.K = K;
   lgl(N, M.xi, M.w, M.D);
   M.X = to_real(X, (size_t)3 * K * M.n3);
   M.nbr.assign(nbr, nbr + (size_t)6 * K);
+  // neighbour faces and orientations (null: the structured default l ^ 1, 0)
+  M.nface.assign((size_t)6 * K, 0);
+  M.orient.assign((size_t)6 * K, 0);
+  for (size_t x = 0; x < (size_t)6 * K; ++x) {
+    M.nface[x] = nface ? nface[x] : (int)(x % 6) ^ 1;
+    M.orient[x] = orient ? orient[x] : 0;
+  }
   if (n_sel > 0) {
     // the selected elements, their neighbours, and one more ring
     M.mask_out.assign(K, 0); M.mask_grad.assign(K, 0); M.mask_q.assign(K, 0);
@@ -1285,16 +1342,18 @@ static void* create_impl(int N, int K, const double* X, const int* nbr, const do
   return c;
 }
 
-void* ora_create(int N, int K, const double* X, const int* nbr, const double* phys, const int* opts,
-                 char* err, int errlen) {
-  return create_impl(N, K, X, nbr, phys, opts, 0, nullptr, err, errlen);
+// nface, orient: neighbour faces and orientation codes [K][6] (see Mesh), or
+// null for the structured default (face l ^ 1, orientation 0).
+void* ora_create(int N, int K, const double* X, const int* nbr, const int* nface, const int* orient,
+                 const double* phys, const int* opts, char* err, int errlen) {
+  return create_impl(N, K, X, nbr, nface, orient, phys, opts, 0, nullptr, err, errlen);
 }
 
 // As ora_create, but Ut is evaluated only on the n_sel selected elements
 // (other entries of the output stay 0).
-void* ora_create_subset(int N, int K, const double* X, const int* nbr, const double* phys, const int* opts,
-                        int n_sel, const int* sel, char* err, int errlen) {
-  return create_impl(N, K, X, nbr, phys, opts, n_sel, sel, err, errlen);
+void* ora_create_subset(int N, int K, const double* X, const int* nbr, const int* nface, const int* orient,
+                        const double* phys, const int* opts, int n_sel, const int* sel, char* err, int errlen) {
+  return create_impl(N, K, X, nbr, nface, orient, phys, opts, n_sel, sel, err, errlen);
 }
 
 void ora_destroy(void* h) { delete (Ctx*)h; }

@@ -313,7 +313,9 @@ k_adj_face(const double* __restrict__ U, const double* __restrict__ lam, const M
   const int4 fc = m.faces[f];
   const size_t S = (size_t)m.K * n3;
   const size_t gM = (size_t)fc.x * n3 + fnode<N>(fc.y, ab % n, ab / n);
-  const size_t gS = (size_t)fc.z * n3 + fnode<N>(fc.w, ab % n, ab / n);
+  // ab indexes the master's face nodes; abS the slave's (orientation fc.w >> 3)
+  const int abS = omap_ab<N>(fc.w >> 3, ab), lS = fc.w & 7;
+  const size_t gS = (size_t)fc.z * n3 + fnode<N>(lS, abS % n, abS / n);
   const double jM = m.invJ[gM], jS = m.invJ[gS];
   double gFs[5], UA[5], UB[5];
 #pragma unroll
@@ -329,7 +331,7 @@ k_adj_face(const double* __restrict__ U, const double* __restrict__ lam, const M
   if (ph.viscous) {
     // Fs = F* s - (Gf_M - Gf_S) / 2
     double* dM = gGf + ((size_t)fc.x * 6 + fc.y) * 4 * n2 + ab;
-    double* dS = gGf + ((size_t)fc.z * 6 + fc.w) * 4 * n2 + ab;
+    double* dS = gGf + ((size_t)fc.z * 6 + lS) * 4 * n2 + abS;
 #pragma unroll
     for (int v = 0; v < 4; ++v) { dM[v * n2] = -0.5 * gFs[v + 1]; dS[v * n2] = 0.5 * gFs[v + 1]; }
   }
@@ -338,7 +340,7 @@ k_adj_face(const double* __restrict__ U, const double* __restrict__ lam, const M
   for (int v = 0; v < 5; ++v) gF[v] = gFs[v] * s;
   face_flux_vjp(ph, UA, UB, nx, ny, nz, gF, gA, gB);
   double* oM = gUf + ((size_t)fc.x * 6 + fc.y) * 5 * n2 + ab;
-  double* oS = gUf + ((size_t)fc.z * 6 + fc.w) * 5 * n2 + ab;
+  double* oS = gUf + ((size_t)fc.z * 6 + lS) * 5 * n2 + abS;
 #pragma unroll
   for (int v = 0; v < 5; ++v) { oM[v * n2] = gA[v]; oS[v * n2] = gB[v]; }
 }
@@ -628,7 +630,8 @@ k_adj_element(const double* __restrict__ U, const double* __restrict__ lam, cons
       const int nb = m.nbr[e * 6 + l];
       double d[4];
       if (nb >= 0) {
-        const size_t gn = (size_t)nb * n3 + fnode<N>(l ^ 1, a, b);
+        const NbrNode<N> nn = neighbour_node<N>(m.elem_face, m.faces, e, l, ab);
+        const size_t gn = (size_t)nn.e * n3 + fnode<N>(nn.l, nn.ab % n, nn.ab / n);
         double un, vn, wn, Tn;
         velocity_temperature<double>(U[gn], U[S + gn], U[2 * S + gn], U[3 * S + gn], U[4 * S + gn], ph, un, vn,
                                      wn, Tn);
@@ -889,7 +892,8 @@ k_adj_gather(const double* __restrict__ U, const MeshDev<double> m, const PhysDe
     for (int v = 0; v < 5; ++v) add[v] += src[v * n2];
     const int nb = m.nbr[e * 6 + l];
     if (ph.viscous && nb >= 0) {
-      const double* w = gWf + ((size_t)nb * 6 + (l ^ 1)) * 4 * n2 + ab;
+      const NbrNode<N> nn = neighbour_node<N>(m.elem_face, m.faces, e, l, ab);
+      const double* w = gWf + ((size_t)nn.e * 6 + nn.l) * 4 * n2 + nn.ab;
 #pragma unroll
       for (int v = 0; v < 4; ++v) gW[v] += w[v * n2];
       any_w = true;

@@ -378,7 +378,7 @@ int dg_init_mesh(dg_ctx** out, const dg_mesh_desc* m, const dg_phys* p, const dg
   c->S = (size_t)c->K * c->n3;
   c->phys = *p; c->opts = *o;
   c->stream = static_cast<cudaStream_t>(stream);
-  std::string gerr = dg::build_geometry(c->geo, c->N, c->K, m->X, m->nbr, p->hwm);
+  std::string gerr = dg::build_geometry(c->geo, c->N, c->K, m->X, m->nbr, m->nbr_face, m->orient, p->hwm);
   if (!gerr.empty()) { delete c; return fail(nullptr, DG_ERR_MESH, "dg_init_mesh: " + gerr); }
   if (c->geo.n_wall > 0 && o->viscous && !(p->hwm > 0.0)) {
     delete c;
@@ -457,7 +457,7 @@ int dg_init_mesh(dg_ctx** out, const dg_mesh_desc* m, const dg_phys* p, const dg
   chk(cudaMalloc(&c->Rv, (o->viscous ? 4 * S : 1) * rs));
   chk(cudaMalloc(&c->Gf, (o->viscous ? 24 * (size_t)c->K * n2 : 1) * rs));
   chk(cudaMalloc(&c->Fs, (ph.fs_diff ? 10 : 5) * (size_t)c->F * n2 * rs));
-  if (f32) chk(alloc(&c->W32, 6 * S));
+  if (f32) chk(alloc(&c->W32, 9 * S));  // primitives and the velocity's low parts
   if (!f32 && o->viscous) {
     chk(alloc(&c->W64, 7 * S));
     chk(alloc(&c->JaJ, 9 * S));
@@ -522,7 +522,9 @@ int dg_init_mesh(dg_ctx** out, const dg_mesh_desc* m, const dg_phys* p, const dg
     std::vector<int4> fc(c->F);
     for (int f = 0; f < c->F; ++f) {
       const dg::Face& x = c->geo.faces[f];
-      fc[f] = make_int4(x.eM, x.lM, x.eS, x.lS);
+      // interior faces: slave face | 8 orientation; halo faces: master flag | 8 o_own
+      const bool packed = (int)f < c->geo.n_interior || (int)f >= c->F - c->geo.n_halo;
+      fc[f] = make_int4(x.eM, x.lM, x.eS, packed ? (x.lS | (x.o << 3)) : x.lS);
     }
     if (c->F) chk(cudaMemcpy(c->faces, fc.data(), fc.size() * sizeof(int4), cudaMemcpyHostToDevice));
   }

@@ -228,11 +228,19 @@ static bool faces(Geometry& g, std::string& err) {
       const int nb = g.nbr[e * 6 + l];
       if ((nb < BC_CODE_MIN && nb > HALO_BASE) || nb >= K) { err = "neighbour index out of range"; return false; }
       if (nb < 0) continue;
-      if (g.nbr[nb * 6 + (l ^ 1)] != e) { err = "connectivity is not reciprocal"; return false; }
+      const int l2 = g.nface[e * 6 + l], o = g.orient[e * 6 + l];
+      if (l2 < 0 || l2 > 5 || o < 0 || o > 7) { err = "bad neighbour face or orientation code"; return false; }
+      if (nb == e && l2 == l) { err = "a face cannot be its own neighbour"; return false; }
+      if (g.nbr[nb * 6 + l2] != e || g.nface[nb * 6 + l2] != l || g.orient[nb * 6 + l2] != orient_inverse(o)) {
+        err = "connectivity is not reciprocal";
+        return false;
+      }
       // the two sides must coincide up to a single translation
       double sh[3] = {0, 0, 0};
       for (int ab = 0; ab < n2; ++ab) {
-        const int p = face_node(n, l, ab % n, ab / n), q = face_node(n, l ^ 1, ab % n, ab / n);
+        int a2, b2;
+        orient_map(o, n - 1, ab % n, ab / n, &a2, &b2);
+        const int p = face_node(n, l, ab % n, ab / n), q = face_node(n, l2, a2, b2);
         for (int c = 0; c < 3; ++c) {
           const double d = g.X[(size_t)c * K * n3 + (size_t)nb * n3 + q] - g.X[(size_t)c * K * n3 + (size_t)e * n3 + p];
           if (ab == 0) sh[c] = d;
@@ -245,14 +253,17 @@ static bool faces(Geometry& g, std::string& err) {
     }
   g.faces.clear();
   g.elem_face.assign((size_t)K * 6, -1);
+  // interior faces, listed from their masters in (element, face) order
   for (int e = 0; e < K; ++e)
-    for (int l = 1; l < 6; l += 2) {
+    for (int l = 0; l < 6; ++l) {
       const int nb = g.nbr[e * 6 + l];
       if (nb < 0) continue;
+      const int l2 = g.nface[e * 6 + l], o = g.orient[e * 6 + l];
+      if (!face_is_master(e, l, nb, l2)) continue;
       const int id = (int)g.faces.size();
-      g.faces.push_back({e, l, nb, l ^ 1});
-      g.elem_face[e * 6 + l] = 2 * id;
-      g.elem_face[nb * 6 + (l ^ 1)] = 2 * id + 1;
+      g.faces.push_back({e, l, nb, l2, o});
+      g.elem_face[e * 6 + l] = 16 * id;
+      g.elem_face[nb * 6 + l2] = 16 * id + 2 * orient_inverse(o) + 1;
     }
   g.n_interior = (int)g.faces.size();
   // boundary faces: walls first, then inflow / outflow faces (eS = the code)
@@ -260,8 +271,8 @@ static bool faces(Geometry& g, std::string& err) {
     for (int l = 0; l < 6; ++l)
       if (g.nbr[e * 6 + l] == BC_CODE_WALL) {
         const int id = (int)g.faces.size();
-        g.faces.push_back({e, l, BC_CODE_WALL, -1});
-        g.elem_face[e * 6 + l] = 2 * id;
+        g.faces.push_back({e, l, BC_CODE_WALL, -1, 0});
+        g.elem_face[e * 6 + l] = 16 * id;
       }
   g.n_wall = (int)g.faces.size() - g.n_interior;
   for (int e = 0; e < K; ++e)
@@ -269,13 +280,16 @@ static bool faces(Geometry& g, std::string& err) {
       const int nb = g.nbr[e * 6 + l];
       if (nb < 0 && nb != BC_CODE_WALL && nb > HALO_BASE) {
         const int id = (int)g.faces.size();
-        g.faces.push_back({e, l, nb, -1});
-        g.elem_face[e * 6 + l] = 2 * id;
+        g.faces.push_back({e, l, nb, -1, 0});
+        g.elem_face[e * 6 + l] = 16 * id;
       }
     }
   g.n_bc = (int)g.faces.size() - g.n_interior - g.n_wall;
-  // halo faces, in halo-index order; the local element is the face's master
-  // when the face is its +xi / +eta / +zeta face, as for interior faces
+  // halo faces, in halo-index order.  The local element is the face's master
+  // by the rule of face_is_master: when its local face and the remote one
+  // (nface) differ in parity, the odd one; else the partitioner decides from
+  // the global element ids and marks the master side with bit 3 (value 8)
+  // of the orientation code.  Traces cross in the master's face-node order.
   {
     std::vector<int> hid;
     for (int e = 0; e < K; ++e)
@@ -286,9 +300,12 @@ static bool faces(Geometry& g, std::string& err) {
       const int e = hid[i] / 6, l = hid[i] % 6, h = HALO_BASE - g.nbr[hid[i]];
       if (h != (int)i) { err = "halo face indices must be 0 .. n_halo-1, each once"; return false; }
       const int id = (int)g.faces.size();
-      const int master = (l & 1) ? 1 : 0;
-      g.faces.push_back({e, l, h, master});
-      g.elem_face[e * 6 + l] = 2 * id + (master ? 0 : 1);
+      const int l2 = g.nface[e * 6 + l], oc = g.orient[e * 6 + l];
+      if (l2 < 0 || l2 > 5 || oc < 0 || oc > 15) { err = "bad halo face or orientation code"; return false; }
+      const int master = ((l & 1) != (l2 & 1)) ? (l & 1) : ((oc >> 3) & 1);
+      const int o_own = master ? 0 : (oc & 7);  // own face nodes -> the master's
+      g.faces.push_back({e, l, h, master, o_own});
+      g.elem_face[e * 6 + l] = 16 * id + 2 * o_own + (master ? 0 : 1);
     }
     g.n_halo = (int)hid.size();
   }
@@ -300,9 +317,13 @@ static bool faces(Geometry& g, std::string& err) {
     // the master's outward normal; a halo face whose local element is the
     // slave takes the negated own normal until the master's is installed
     double sgn = (fc.lM & 1) ? 1.0 : -1.0;
-    if (f >= F_halo0 && fc.lS == 0) sgn = -sgn;
+    const bool halo_slave = f >= F_halo0 && fc.lS == 0;
+    if (halo_slave) sgn = -sgn;
     for (int ab = 0; ab < n2; ++ab) {
-      const int p = face_node(n, fc.lM, ab % n, ab / n);
+      // (a halo face's slave side: its own node at the master's index ab)
+      int a = ab % n, b = ab / n;
+      if (halo_slave) orient_map(orient_inverse(fc.o), n - 1, ab % n, ab / n, &a, &b);
+      const int p = face_node(n, fc.lM, a, b);
       const double* ja = &g.Ja[((size_t)fc.eM * n3 + p) * 9 + (fc.lM / 2) * 3];
       const dd s = dd_sqrt(dd(ja[0]) * dd(ja[0]) + dd(ja[1]) * dd(ja[1]) + dd(ja[2]) * dd(ja[2]));
       for (int c = 0; c < 3; ++c) g.fgeo[(size_t)c * F * n2 + f * n2 + ab] = sgn * (dd(ja[c]) / s).hi;
@@ -401,9 +422,12 @@ static bool wall_samples(Geometry& g, double hwm, std::string& err) {
     // choice that does not depend on element numbering or partitioning), then
     // the remaining candidates by ascending index
     std::vector<int> order;
-    for (int c = fc.eM, layer = 0; c >= 0 && layer < 4; ++layer) {
+    for (int c = fc.eM, layer = 0, lin = fc.lM; c >= 0 && layer < 4; ++layer) {
       order.push_back(c);
-      c = g.nbr[c * 6 + (fc.lM ^ 1)];
+      // the face opposite the one the column entered this element by
+      const int lout = lin ^ 1, nxt = g.nbr[c * 6 + lout];
+      if (nxt >= 0) lin = g.nface[c * 6 + lout];
+      c = nxt;
     }
     for (int c : cand)
       if (std::find(order.begin(), order.end(), c) == order.end()) order.push_back(c);
@@ -449,11 +473,18 @@ static bool wall_samples(Geometry& g, double hwm, std::string& err) {
   return true;
 }
 
-std::string build_geometry(Geometry& g, int N, int K, const double* X, const int* nbr, double hwm) {
+std::string build_geometry(Geometry& g, int N, int K, const double* X, const int* nbr, const int* nface,
+                           const int* orient, double hwm) {
   g.N = N; g.n = N + 1; g.n2 = g.n * g.n; g.n3 = g.n2 * g.n; g.K = K;
   g.basis = make_basis(N);
   g.X.assign(X, X + (size_t)3 * K * g.n3);
   g.nbr.assign(nbr, nbr + (size_t)6 * K);
+  g.nface.resize((size_t)6 * K);
+  g.orient.resize((size_t)6 * K);
+  for (size_t x = 0; x < (size_t)6 * K; ++x) {
+    g.nface[x] = nface ? nface[x] : (int)(x % 6) ^ 1;
+    g.orient[x] = orient ? orient[x] : 0;
+  }
   std::string err;
   if (!metrics(g, err)) return err;
   if (!faces(g, err)) return err;

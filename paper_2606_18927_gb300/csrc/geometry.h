@@ -32,22 +32,39 @@ constexpr int BC_CODE_WALL = -1, BC_CODE_INFLOW = -2, BC_CODE_OUTFLOW = -3, BC_C
 // halo face h of a partitioned mesh: neighbour code HALO_BASE - h (dg.h: DG_BC_HALO_BASE)
 constexpr int HALO_BASE = -16;
 
+// Orientation codes of conforming faces (dg.h): node (a, b) of one side's
+// face coincides with node (a', b') of the other side's face, where
+//   (s, t) = (o & 1) ? (b, a) : (a, b);  a' = (o & 2) ? N - s : s;  b' = (o & 4) ? N - t : t.
+inline void orient_map(int o, int N, int a, int b, int* a2, int* b2) {
+  const int s = (o & 1) ? b : a, t = (o & 1) ? a : b;
+  *a2 = (o & 2) ? N - s : s;
+  *b2 = (o & 4) ? N - t : t;
+}
+inline int orient_inverse(int o) {
+  return (o & 1) ? (1 | (((o >> 2) & 1) << 1) | (((o >> 1) & 1) << 2)) : o;
+}
+
 struct Face {
   int eM, lM;  // master element and its local face
   int eS, lS;  // slave element and local face; boundary faces: eS = the code, lS = -1;
                // halo faces: eS = the halo index, lS = 1 if the local element is the master
+  int o;       // interior faces: orientation from the master's face nodes to the slave's;
+               // halo faces: from the local element's face nodes to the master's
 };
 
 struct Geometry {
   int N = 0, n = 0, n2 = 0, n3 = 0, K = 0;
   Basis basis;
   std::vector<int> nbr;          // [K*6]
+  std::vector<int> nface;        // [K*6] the neighbour's local face (interior faces)
+  std::vector<int> orient;       // [K*6] orientation code towards the neighbour's face nodes
   std::vector<double> X;         // [3][K*n3]
   std::vector<double> Ja;        // [K*n3][3 dir][3 comp]
   std::vector<double> J;         // [K*n3]
   std::vector<Face> faces;       // interior, wall, inflow / outflow, then halo faces
   int n_interior = 0, n_wall = 0, n_bc = 0, n_halo = 0;
-  std::vector<int> elem_face;    // [K*6] = 2 * face id + side (0 master, 1 slave)
+  std::vector<int> elem_face;    // [K*6] = 16 * face id + 2 * o + side (0 master, 1 slave), o the
+                                 // orientation from this element's face nodes to the master's
   std::vector<double> fgeo;      // [4][F*n2]: unit normal (master outward) and s
   std::vector<int> ws_elem;      // [n_wall*n2] element containing the sample point
   std::vector<double> ws_ref;    // [n_wall*n2][3] its reference coordinates
@@ -55,7 +72,20 @@ struct Geometry {
 };
 
 // Returns an empty string on success, else the reason for rejecting the mesh.
-std::string build_geometry(Geometry& g, int N, int K, const double* X, const int* nbr, double hwm);
+// nface, orient: [K*6] neighbour faces and orientation codes, or null for the
+// structured default (face l ^ 1, code 0).
+std::string build_geometry(Geometry& g, int N, int K, const double* X, const int* nbr, const int* nface,
+                           const int* orient, double hwm);
+
+// The side of an interior face that is its master (whose node order indexes
+// the face and whose metrics give its normal): the side with the odd local
+// face (+xi, +eta, +zeta) when the two local faces differ in parity, else the
+// side with the smaller (element, face) pair.  Element ids are global ones
+// on partitioned meshes.
+inline bool face_is_master(long long e, int l, long long nb, int l2) {
+  if ((l & 1) != (l2 & 1)) return (l & 1) != 0;
+  return e * 6 + l < nb * 6 + l2;
+}
 
 inline int face_node(int n, int l, int a, int b) {
   const int N = n - 1;

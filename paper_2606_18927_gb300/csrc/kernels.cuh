@@ -121,6 +121,47 @@ __device__ __forceinline__ int fnode(int l, int a, int b) {
   }
 }
 
+// Face-local index a' + n b' of the node of the other side's face that
+// coincides with node ab = a + n b of this side's face, for the orientation
+// code o (dg.h): (s, t) = (o & 1) ? (b, a) : (a, b), a' = (o & 2) ? N - s : s,
+// b' = (o & 4) ? N - t : t.
+template <int N>
+__device__ __forceinline__ int omap_ab(int o, int ab) {
+  constexpr int n = N + 1;
+  const int a = ab % n, b = ab / n;
+  const int s = (o & 1) ? b : a, t = (o & 1) ? a : b;
+  return ((o & 2) ? N - s : s) + n * ((o & 4) ? N - t : t);
+}
+
+__device__ __forceinline__ int orient_inv(int o) {
+  return (o & 1) ? (1 | (((o >> 2) & 1) << 1) | (((o >> 1) & 1) << 2)) : o;
+}
+
+// Encodings of the face tables (built by the host geometry):
+//   faces[f] = (master element, master face, slave element, slave face
+//     | 8 o) for interior faces, o the orientation from the master's face
+//     nodes to the slave's; halo faces: (local element, local face, halo
+//     index, master | 8 o_own), o_own from the local face's nodes to the
+//     master's (0 when the local element is the master);
+//   elem_face[e * 6 + l] = 16 f + 2 o_own + side (side 1: the slave).
+// The face arrays (surface fluxes, normals, halo traces) are indexed in the
+// master's face-node order.
+template <int N>
+struct NbrNode {
+  int e;     // neighbour element
+  int l;     // its local face
+  int ab;    // face-local index of the coinciding node on that face
+};
+
+template <int N>
+__device__ __forceinline__ NbrNode<N> neighbour_node(const int* __restrict__ elem_face, const int4* __restrict__ faces,
+                                                     int e, int l, int ab) {
+  const int code = elem_face[e * 6 + l];
+  const int4 fc = faces[code >> 4];
+  if (code & 1) return NbrNode<N>{fc.x, fc.y, omap_ab<N>((code >> 1) & 7, ab)};
+  return NbrNode<N>{fc.z, fc.w & 7, omap_ab<N>(fc.w >> 3, ab)};
+}
+
 // 1/x for x > 0 in double: an FP32 estimate refined by two Newton steps
 // (relative error ~1e-7 -> 1e-14 -> below 1 ulp), 4 FP64 FMAs instead of
 // the IEEE division sequence (GB300 issues 2 FP64 operations per clock per SM).
@@ -257,10 +298,28 @@ __device__ __forceinline__ Prim<float> primitive<float>(const double U0, const d
 // FP32 (ideal gas, E = p / (gamma - 1) + rho |u|^2 / 2):
 //   h - h_ref = (gamma / (gamma - 1) (p' - (p_ref / rho_ref) rho') + rho |u|^2 / 2) / rho
 // (rho_ref = 0: h = (gamma / (gamma - 1) (p' + p_ref) + rho |u|^2 / 2) / rho)
+//
+// With lo given, the velocity is also returned as an unevaluated sum of two
+// floats, u = q.u + lo->u to about 1e-12 relative (q.u itself carries a few
+// FP32 roundings: of m, of 1 / rho and of the product).  The flux-difference
+// form takes the velocity differences of two nodes from these pairs: rounded
+// to FP32, the velocity (O(1) at any Mach number) put an error of eps32 |u|
+// into every difference, the largest input error of the form (about 1.6e-5
+// of the Ut of the 48^3 curved box at Mach 0.3).  The low parts come from
+// the exact FP32 residual m - u rho, formed with FMAs:
+//   r = (m_hi - u rho_ref) - u rho_hi' - u rho_lo' + m_lo,  lo = r / rho,
+// where m_lo = m - m_hi and rho_lo' = (rho - rho_ref) - rho_hi' are the
+// roundings of the conversions to FP32 (three FP64 operations each).
+struct Lo3 {
+  float u, v, w;
+};
+
 __device__ __forceinline__ Prim<float> prim32_shifted(const double U0, const double U1, const double U2,
-                                                      const double U3, const double U4, const PhysDev& ph) {
+                                                      const double U3, const double U4, const PhysDev& ph,
+                                                      Lo3* lo = nullptr) {
   Prim<float> q;
-  q.rho = (float)(U0 - ph.rho_ref);
+  const double rd = U0 - ph.rho_ref;
+  q.rho = (float)rd;
   const float ir = 1.0f / (ph.f32c.rho_ref + q.rho);
   const float m1 = (float)U1, m2 = (float)U2, m3 = (float)U3;
   q.u = m1 * ir; q.v = m2 * ir; q.w = m3 * ir;
@@ -268,6 +327,19 @@ __device__ __forceinline__ Prim<float> prim32_shifted(const double U0, const dou
   const double pr = fma(ph.gm1, U4 - (double)ke, -ph.p_ref);  // p - p_ref
   q.p = (float)pr;
   q.h = fmaf(ph.f32c.g_gm1, q.p + ph.f32c.h_p - ph.f32c.h_r * q.rho, ke) * ir;
+  if (lo) {
+    const float rl = (float)(rd - (double)q.rho);
+    auto low = [&](double mf, float mh, float uh) {
+      const float ml = (float)(mf - (double)mh);
+      float r = fmaf(-uh, ph.f32c.rho_ref, mh);
+      r = fmaf(-uh, q.rho, r);
+      r = fmaf(-uh, rl, r);
+      return (r + ml) * ir;
+    };
+    lo->u = low(U1, m1, q.u);
+    lo->v = low(U2, m2, q.v);
+    lo->w = low(U3, m3, q.w);
+  }
   return q;
 }
 
@@ -467,15 +539,30 @@ __device__ __forceinline__ void riemann_d(const PhysDev& ph, const Prim<R>& A, c
 // formed from the differences of the two nodes' primitives (x_m = x_i + dx,
 // {x} = x_i + dx / 2), so that their FP32 rounding error scales with the
 // difference, not with the flux itself:
-//   {u}.{a} - u_i.a_i = du/2 . {a} + u_i . da/2 =: dua
-//   G_rho = rho_i dua + drho/2 ({u}.{a})
+//   {u}.{a} - u_i.a_i = du/2 . {a} + u_i . da/2
+//   G_rho = rho_i ({u}.{a} - u_i.a_i) + drho/2 ({u}.{a})
 //   G_m   = G_rho {u} + rho_i (u_i.a_i) du/2 + dp/2 {a} + p_i da/2   (p = p - p_ref)
 //   G_E   = G_rho {h} + rho_i (u_i.a_i) dh/2
 // The split-form volume term is sum_m DVS_im G(i -> m) (the F(U_i) part sums to
 // the boundary rows' -B/w F(U_i), which the surface term carries in the same
 // difference form, F* - F(U_i)).
+//
+// G holds the part F(U_i) . da / 2, whose sum over a node's pairs is
+// F(U_i) . sum_dir sum_m DVS_im (a_m - a_i) / 2 = F(U_i) . sum_dir sum_m D_im a_m:
+// zero by the discrete metric identities of the curl-form metrics.  With the
+// metrics rounded to FP32 the identities hold only to eps32 |a|, and that part
+// then leaves an error eps32 |F(U_i)| N^2 / h in Ut, which the flux
+// differences do not remove (the free-stream error of the rounded metrics;
+// the largest error of the form on curved meshes, in the mass and energy rows
+// where no p_ref shift makes F(U_i) small).  So G' = G - F(U_i) . da / 2 is
+// summed instead, i.e. the identity is applied exactly:
+//   G'_rho = rho_i du/2 . {a} + drho/2 ({u}.{a})
+//   G'_m   = G'_rho {u} + rho_i (u_i . da/2) du/2 + rho_i (u_i.a_i) du/2 + dp/2 {a}
+//   G'_E   = G'_rho {h} + rho_i (u_i . da/2) dh/2 + rho_i (u_i.a_i) dh/2
+// (at faces da = 0 and G' = G).
 struct NodeF {
   float rho, u, v, w, p, h;
+  float ul, vl, wl;  // low parts of the velocity (u = u + ul, see prim32_shifted)
 };
 
 // i, m in the storage form of the FP32 primitives (rho, h shifted by
@@ -483,35 +570,38 @@ struct NodeF {
 // density and enthalpy of node i are rebuilt where they multiply
 __device__ __forceinline__ void flux_delta(const NodeF& i, const NodeF& m, float ai0, float ai1, float ai2, float da0,
                                            float da1, float da2, float rho_ref, float h_ref, float G[5]) {
-  const float du = m.u - i.u, dv = m.v - i.v, dw = m.w - i.w;
+  const float du = (m.u - i.u) + (m.ul - i.ul), dv = (m.v - i.v) + (m.vl - i.vl), dw = (m.w - i.w) + (m.wl - i.wl);
   const float dr = m.rho - i.rho, dp = m.p - i.p, dh = m.h - i.h;
   const float ri = rho_ref + i.rho;
   const float ab0 = fmaf(0.5f, da0, ai0), ab1 = fmaf(0.5f, da1, ai1), ab2 = fmaf(0.5f, da2, ai2);
-  const float uia = i.u * ai0 + i.v * ai1 + i.w * ai2;
-  const float dua = 0.5f * (du * ab0 + dv * ab1 + dw * ab2 + i.u * da0 + i.v * da1 + i.w * da2);
-  const float g0 = ri * dua + 0.5f * dr * (uia + dua);
-  const float ruia = ri * uia;
+  const float uia = i.u * ai0 + i.v * ai1 + i.w * ai2;          // u_i . a_i
+  const float uida = 0.5f * (i.u * da0 + i.v * da1 + i.w * da2);  // u_i . da / 2
+  const float dua = 0.5f * (du * ab0 + dv * ab1 + dw * ab2);      // du/2 . {a}
+  const float g0 = ri * dua + 0.5f * dr * (uia + uida + dua);
+  const float ruia = ri * (uia + uida);  // rho_i (u_i.a_i + u_i . da/2)
   G[0] = g0;
-  G[1] = g0 * fmaf(0.5f, du, i.u) + 0.5f * (ruia * du + dp * ab0 + i.p * da0);
-  G[2] = g0 * fmaf(0.5f, dv, i.v) + 0.5f * (ruia * dv + dp * ab1 + i.p * da1);
-  G[3] = g0 * fmaf(0.5f, dw, i.w) + 0.5f * (ruia * dw + dp * ab2 + i.p * da2);
+  G[1] = g0 * fmaf(0.5f, du, i.u) + 0.5f * (ruia * du + dp * ab0);
+  G[2] = g0 * fmaf(0.5f, dv, i.v) + 0.5f * (ruia * dv + dp * ab1);
+  G[3] = g0 * fmaf(0.5f, dw, i.w) + 0.5f * (ruia * dw + dp * ab2);
   G[4] = g0 * (h_ref + fmaf(0.5f, dh, i.h)) + 0.5f * ruia * dh;
 }
 
-__device__ __forceinline__ NodeF nodef(const Prim<float>& q) { return NodeF{q.rho, q.u, q.v, q.w, q.p, q.h}; }
+__device__ __forceinline__ NodeF nodef(const Prim<float>& q, const Lo3& l) {
+  return NodeF{q.rho, q.u, q.v, q.w, q.p, q.h, l.u, l.v, l.w};
+}
 
 // face flux differences for both sides: D_A = F* - F(U_A).n, D_B = F* - F(U_B).n;
 // A, B in the storage form (the dissipation takes the full values and the
 // density jump of the shifted ones)
 __device__ __forceinline__ void face_flux_delta(const PhysDev& ph, const Prim<float>& A, const Prim<float>& B,
-                                                const float dU[5], float nx, float ny, float nz, float DA[5],
-                                                float DB[5]) {
+                                                const Lo3& la, const Lo3& lb, const float dU[5], float nx, float ny,
+                                                float nz, float DA[5], float DB[5]) {
   float Z[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
   const float drho = B.rho - A.rho;
   riemann_dissipation<float>(ph, unshift32(A, ph), unshift32(B, ph), dU, nx, ny, nz, Z, &drho);
   const float rr = ph.f32c.rho_ref, hr = ph.f32c.h_ref;
-  flux_delta(nodef(A), nodef(B), nx, ny, nz, 0.f, 0.f, 0.f, rr, hr, DA);
-  flux_delta(nodef(B), nodef(A), nx, ny, nz, 0.f, 0.f, 0.f, rr, hr, DB);
+  flux_delta(nodef(A, la), nodef(B, lb), nx, ny, nz, 0.f, 0.f, 0.f, rr, hr, DA);
+  flux_delta(nodef(B, lb), nodef(A, la), nx, ny, nz, 0.f, 0.f, 0.f, rr, hr, DB);
 #pragma unroll
   for (int v = 0; v < 5; ++v) { DA[v] += Z[v]; DB[v] += Z[v]; }
 }
@@ -520,11 +610,11 @@ __device__ __forceinline__ void face_flux_delta(const PhysDev& ph, const Prim<fl
 // F* s - F(U_side).(n s) minus the viscous flux vis_w (gA - gB) (gB null: gA)
 // into out (master) and out + 5 n2 (slave)
 __device__ __forceinline__ void store_face_delta(const PhysDev& ph, const Prim<float>& A, const Prim<float>& B,
-                                                 const float dU[5], float nx, float ny, float nz, float s,
-                                                 const float* gA, const float* gB, float vis_w, float* out, int n2,
-                                                 bool both) {
+                                                 const Lo3& la, const Lo3& lb, const float dU[5], float nx, float ny,
+                                                 float nz, float s, const float* gA, const float* gB, float vis_w,
+                                                 float* out, int n2, bool both) {
   float DA[5], DB[5];
-  face_flux_delta(ph, A, B, dU, nx, ny, nz, DA, DB);
+  face_flux_delta(ph, A, B, la, lb, dU, nx, ny, nz, DA, DB);
   out[0] = DA[0] * s;
   if (both) out[5 * n2] = DB[0] * s;
 #pragma unroll
@@ -546,14 +636,21 @@ __device__ __forceinline__ void riemann(const PhysDev& ph, const Prim<R>& A, con
 
 // ---------------------------------------------------------------------------
 // FP32-mixed form: the FP32 primitives (rho, u, v, w, p - p_ref, h) of every
-// node, W[6][K n^3], formed once per stage from the FP64 state (by k_prim32,
+// node and the low parts of its velocity, W[9][K n^3] (rows 6-8: see
+// prim32_shifted), formed once per stage from the FP64 state (by k_prim32,
 // or by the previous stage's volume epilogue from the updated state) and read
 // by the lifting, face and volume kernels.  The FP64 work of the primitive
 // recovery (and of the double-to-float conversions) is then done once per node
 // and stage instead of once per use.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void store_prim32(float* __restrict__ W, size_t S, size_t g, const Prim<float>& q) {
+__device__ __forceinline__ void store_prim32(float* __restrict__ W, size_t S, size_t g, const Prim<float>& q,
+                                             const Lo3& l) {
   W[g] = q.rho; W[S + g] = q.u; W[2 * S + g] = q.v; W[3 * S + g] = q.w; W[4 * S + g] = q.p; W[5 * S + g] = q.h;
+  W[6 * S + g] = l.u; W[7 * S + g] = l.v; W[8 * S + g] = l.w;
+}
+
+__device__ __forceinline__ Lo3 load_lo32(const float* __restrict__ W, size_t S, size_t g) {
+  return Lo3{W[6 * S + g], W[7 * S + g], W[8 * S + g]};
 }
 
 // storage form (rho - rho_ref, u, v, w, p - p_ref, h - h_ref)
@@ -573,9 +670,10 @@ __device__ __forceinline__ Prim<float> load_prim32_full(const float* __restrict_
 // trace: FP64 directly; FP32 in the storage form (*st, for the flux-difference
 // form) with the full values rebuilt from it
 template <typename R>
-__device__ __forceinline__ Prim<R> trace_prims(const double Ut[5], const PhysDev& ph, Prim<R>* st) {
+__device__ __forceinline__ Prim<R> trace_prims(const double Ut[5], const PhysDev& ph, Prim<R>* st, Lo3* lo) {
   if constexpr (std::is_same<R, float>::value) {
-    *st = prim32_shifted(Ut[0], Ut[1], Ut[2], Ut[3], Ut[4], ph);
+    *st = prim32_shifted(Ut[0], Ut[1], Ut[2], Ut[3], Ut[4], ph, ph.fs_diff ? lo : nullptr);
+    if (!ph.fs_diff) *lo = Lo3{0.f, 0.f, 0.f};
     return unshift32(*st, ph);
   } else {
     return primitive<R>(Ut[0], Ut[1], Ut[2], Ut[3], Ut[4], ph);
@@ -584,8 +682,9 @@ __device__ __forceinline__ Prim<R> trace_prims(const double Ut[5], const PhysDev
 
 static __global__ void k_prim32(long long S, const double* __restrict__ U, const PhysDev ph, float* __restrict__ W) {
   for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < S; x += (long long)gridDim.x * blockDim.x) {
-    const Prim<float> q = prim32_shifted(U[x], U[S + x], U[2 * S + x], U[3 * S + x], U[4 * S + x], ph);
-    store_prim32(W, (size_t)S, (size_t)x, q);
+    Lo3 l;
+    const Prim<float> q = prim32_shifted(U[x], U[S + x], U[2 * S + x], U[3 * S + x], U[4 * S + x], ph, &l);
+    store_prim32(W, (size_t)S, (size_t)x, q, l);
   }
 }
 
@@ -963,7 +1062,8 @@ k_lift(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
     const R Wo0 = sW[q], Wo1 = sW[n3 + q], Wo2 = sW[2 * n3 + q], Wo3 = sW[3 * n3 + q];
     R d0, d1, d2, d3;
     if (nb >= 0) {
-      const size_t gn = (size_t)nb * n3 + fnode<N>(l ^ 1, a, b);
+      const NbrNode<N> nn = neighbour_node<N>(m.elem_face, m.faces, e, l, ab);
+      const size_t gn = (size_t)nn.e * n3 + fnode<N>(nn.l, nn.ab % n, nn.ab / n);
       R u, v, w, T;
       if constexpr (std::is_same<R, float>::value) {
         velocity_temperature32(load_prim32_full(m.W32, S, gn, ph), ph, u, v, w, T);
@@ -974,8 +1074,10 @@ k_lift(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
       }
       d0 = u - Wo0; d1 = v - Wo1; d2 = w - Wo2; d3 = T - Wo3;
     } else if (nb <= -16) {
-      // halo face: the remote element's trace from the halo buffer
-      const double* src = m.halo_U + (size_t)(-16 - nb) * 5 * n2 + ab;
+      // halo face: the remote element's trace from the halo buffer (in the
+      // master's face-node order)
+      const int abm = omap_ab<N>((m.elem_face[e * 6 + l] >> 1) & 7, ab);
+      const double* src = m.halo_U + (size_t)(-16 - nb) * 5 * n2 + abm;
       R u, v, w, T;
       if constexpr (std::is_same<R, double>::value) {
         if (m.W64) {
@@ -1215,11 +1317,13 @@ k_face(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
   const R* gA;
   const R* gB;
   if constexpr (!D) {
+    const int abS = omap_ab<N>(fc.w >> 3, ab), lS = fc.w & 7;
     const size_t gM = (size_t)fc.x * n3 + fnode<N>(fc.y, ab % n, ab / n);
-    const size_t gS = (size_t)fc.z * n3 + fnode<N>(fc.w, ab % n, ab / n);
+    const size_t gS = (size_t)fc.z * n3 + fnode<N>(lS, abS % n, abS / n);
     gA = Gf + ((size_t)fc.x * 6 + fc.y) * 4 * n2 + ab;
-    gB = Gf + ((size_t)fc.z * 6 + fc.w) * 4 * n2 + ab;
+    gB = Gf + ((size_t)fc.z * 6 + lS) * 4 * n2 + abS;
     const Prim<float> A = load_prim32(m.W32, S, gM), B = load_prim32(m.W32, S, gS);
+    const Lo3 la = load_lo32(m.W32, S, gM), lb = load_lo32(m.W32, S, gS);
     // U_B - U_A for the Lax-Friedrichs dissipation, differenced in FP64 (from
     // rounded FP32 states the difference would carry an error of eps |U|)
     float dU[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
@@ -1228,7 +1332,7 @@ k_face(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
       for (int v = 0; v < 5; ++v) dU[v] = (float)(U[v * S + gS] - U[v * S + gM]);
     }
     if (ph.fs_diff) {
-      store_face_delta(ph, A, B, dU, nx, ny, nz, s, gA, gB, R(0.5), Fs + (size_t)f * 10 * n2 + ab, n2, true);
+      store_face_delta(ph, A, B, la, lb, dU, nx, ny, nz, s, gA, gB, R(0.5), Fs + (size_t)f * 10 * n2 + ab, n2, true);
       return;
     }
     riemann_d<float>(ph, unshift32(A, ph), unshift32(B, ph), dU, nx, ny, nz, F);
@@ -1240,10 +1344,11 @@ k_face(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
     double dU[5] = {0.0, 0.0, 0.0, 0.0, 0.0}, T;
     const bool llf = ph.surf_flux == 1;
     if (!is_halo) {
+      const int abS = omap_ab<N>(fc.w >> 3, ab), lS = fc.w & 7;
       const size_t gM = (size_t)fc.x * n3 + fnode<N>(fc.y, ab % n, ab / n);
-      const size_t gS = (size_t)fc.z * n3 + fnode<N>(fc.w, ab % n, ab / n);
+      const size_t gS = (size_t)fc.z * n3 + fnode<N>(lS, abS % n, abS / n);
       gA = Gf + ((size_t)fc.x * 6 + fc.y) * 4 * n2 + ab;
-      gB = Gf + ((size_t)fc.z * 6 + fc.w) * 4 * n2 + ab;
+      gB = Gf + ((size_t)fc.z * 6 + lS) * 4 * n2 + abS;
       if (m.W64) {
         A = load_prim64(m.W64, S, gM);
         B = load_prim64(m.W64, S, gS);
@@ -1256,18 +1361,20 @@ k_face(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
         for (int v = 0; v < 5; ++v) dU[v] = U[v * S + gS] - U[v * S + gM];
       }
     } else {
-      // fc = (local element, local face, halo index, local side is master)
+      // fc = (local element, local face, halo index, local side is master
+      // | 8 o_own); ab is the master's face-node index, abl the local one
       const int h = f0 - m.n_interior;
-      const size_t gL = (size_t)fc.x * n3 + fnode<N>(fc.y, ab % n, ab / n);
+      const int abl = omap_ab<N>(orient_inv(fc.w >> 3), ab);
+      const size_t gL = (size_t)fc.x * n3 + fnode<N>(fc.y, abl % n, abl / n);
       const double* rU = m.halo_U + (size_t)h * 5 * n2 + ab;
-      const bool master = fc.w != 0;
+      const bool master = (fc.w & 1) != 0;
       const Prim<double> loc =
           m.W64 ? load_prim64(m.W64, S, gL)
                 : primitive_T(U[gL], U[S + gL], U[2 * S + gL], U[3 * S + gL], U[4 * S + gL], ph, T);
       const Prim<double> rem = primitive_T(rU[0], rU[n2], rU[2 * n2], rU[3 * n2], rU[4 * n2], ph, T);
       A = master ? loc : rem;
       B = master ? rem : loc;
-      const R* gl = Gf + ((size_t)fc.x * 6 + fc.y) * 4 * n2 + ab;
+      const R* gl = Gf + ((size_t)fc.x * 6 + fc.y) * 4 * n2 + abl;
       const R* gr = m.halo_G + (size_t)h * 4 * n2 + ab;
       gA = master ? gl : gr;
       gB = master ? gr : gl;
@@ -1306,11 +1413,14 @@ k_halo_face(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, 
   const int h = tid / n2, ab = tid - h * n2;
   if (h >= m.n_halo) return;
   const int f = m.F - m.n_halo + h;
-  const int4 fc = m.faces[f];  // (local element, local face, halo index, local is master)
+  // (local element, local face, halo index, local is master | 8 o_own); ab
+  // is the master's face-node index, abl the local one
+  const int4 fc = m.faces[f];
   const size_t S = (size_t)m.K * n3;
-  const size_t gL = (size_t)fc.x * n3 + fnode<N>(fc.y, ab % n, ab / n);
+  const int abl = omap_ab<N>(orient_inv(fc.w >> 3), ab);
+  const size_t gL = (size_t)fc.x * n3 + fnode<N>(fc.y, abl % n, abl / n);
   const double* rU = m.halo_U + (size_t)h * 5 * n2 + ab;
-  const bool master = fc.w != 0;
+  const bool master = (fc.w & 1) != 0;
   double UA[5], UB[5];
 #pragma unroll
   for (int v = 0; v < 5; ++v) {
@@ -1321,15 +1431,16 @@ k_halo_face(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, 
   const size_t FN = (size_t)m.F * n2, fg = (size_t)f * n2 + ab;
   const R nx = (R)m.fgeo[fg], ny = (R)m.fgeo[FN + fg], nz = (R)m.fgeo[2 * FN + fg], s = (R)m.fgeo[3 * FN + fg];
   Prim<R> As, Bs;
-  const Prim<R> A = trace_prims<R>(UA, ph, &As), B = trace_prims<R>(UB, ph, &Bs);
+  Lo3 la, lb;
+  const Prim<R> A = trace_prims<R>(UA, ph, &As, &la), B = trace_prims<R>(UB, ph, &Bs, &lb);
   if constexpr (std::is_same<R, float>::value) {
     if (ph.fs_diff) {
       float dU[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) dU[v] = (float)(UB[v] - UA[v]);
-      const R* gl = Gf + ((size_t)fc.x * 6 + fc.y) * 4 * n2 + ab;
+      const R* gl = Gf + ((size_t)fc.x * 6 + fc.y) * 4 * n2 + abl;
       const R* gr = m.halo_G + (size_t)h * 4 * n2 + ab;
-      store_face_delta(ph, As, Bs, dU, nx, ny, nz, s, master ? gl : gr, master ? gr : gl, 0.5f,
+      store_face_delta(ph, As, Bs, la, lb, dU, nx, ny, nz, s, master ? gl : gr, master ? gr : gl, 0.5f,
                        Fs + (size_t)f * 10 * n2 + ab, n2, true);
       return;
     }
@@ -1339,7 +1450,7 @@ k_halo_face(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, 
   R* out = Fs + (size_t)f * 5 * n2 + ab;
   out[0] = F[0] * s;
   if (ph.viscous) {
-    const R* gl = Gf + ((size_t)fc.x * 6 + fc.y) * 4 * n2 + ab;
+    const R* gl = Gf + ((size_t)fc.x * 6 + fc.y) * 4 * n2 + abl;
     const R* gr = m.halo_G + (size_t)h * 4 * n2 + ab;
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
@@ -1353,7 +1464,8 @@ k_halo_face(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, 
 }
 
 // the local traces of the halo faces: state (before the lifting) and own
-// outward viscous flux (after it), in the halo-buffer layout
+// outward viscous flux (after it), in the halo-buffer layout (the master's
+// face-node order)
 template <int N, typename R>
 __global__ void __launch_bounds__(256)
 k_halo_pack(const double* __restrict__ U, const MeshDev<R> m, const R* __restrict__ Gf, double* __restrict__ sendU,
@@ -1363,14 +1475,16 @@ k_halo_pack(const double* __restrict__ U, const MeshDev<R> m, const R* __restric
   const int h = tid / n2, ab = tid - h * n2;
   if (h >= m.n_halo) return;
   const int4 fc = m.faces[m.F - m.n_halo + h];
+  // ab is the index in the master's face-node order; abl the local one
+  const int abl = omap_ab<N>(orient_inv(fc.w >> 3), ab);
   if (sendU) {
     const size_t S = (size_t)m.K * n3;
-    const size_t gL = (size_t)fc.x * n3 + fnode<N>(fc.y, ab % n, ab / n);
+    const size_t gL = (size_t)fc.x * n3 + fnode<N>(fc.y, abl % n, abl / n);
 #pragma unroll
     for (int v = 0; v < 5; ++v) sendU[((size_t)h * 5 + v) * n2 + ab] = U[v * S + gL];
   }
   if (sendG) {
-    const R* gl = Gf + ((size_t)fc.x * 6 + fc.y) * 4 * n2 + ab;
+    const R* gl = Gf + ((size_t)fc.x * 6 + fc.y) * 4 * n2 + abl;
 #pragma unroll
     for (int v = 0; v < 4; ++v) sendG[((size_t)h * 4 + v) * n2 + ab] = gl[v * n2];
   }
@@ -1398,7 +1512,8 @@ k_bc(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const R
   for (int v = 0; v < 5; ++v) UA[v] = U[v * S + gM];
   ghost_state(ph, fc.z, UA, UB);
   Prim<R> As, Bs;  // FP32: the storage form, for the flux-difference form
-  const Prim<R> A = trace_prims<R>(UA, ph, &As), B = trace_prims<R>(UB, ph, &Bs);
+  Lo3 la, lb;
+  const Prim<R> A = trace_prims<R>(UA, ph, &As, &la), B = trace_prims<R>(UB, ph, &Bs, &lb);
   const size_t FN = (size_t)m.F * n2, fg = (size_t)f * n2 + ab;
   const R nx = (R)m.fgeo[fg], ny = (R)m.fgeo[FN + fg], nz = (R)m.fgeo[2 * FN + fg], s = (R)m.fgeo[3 * FN + fg];
   if constexpr (std::is_same<R, float>::value) {
@@ -1406,7 +1521,8 @@ k_bc(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const R
       float dU[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) dU[v] = (float)(UB[v] - UA[v]);
-      store_face_delta(ph, As, Bs, dU, nx, ny, nz, s, Gf + ((size_t)fc.x * 6 + fc.y) * 4 * n2 + ab, nullptr, 1.f,
+      store_face_delta(ph, As, Bs, la, lb, dU, nx, ny, nz, s, Gf + ((size_t)fc.x * 6 + fc.y) * 4 * n2 + ab, nullptr,
+                       1.f,
                        Fs + (size_t)f * 10 * n2 + ab, n2, false);
       return;
     }
@@ -1454,7 +1570,8 @@ k_wall(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, R* __
   UB[0] = UA[0]; UB[1] = UA[1] - 2.0 * mn * nxd; UB[2] = UA[2] - 2.0 * mn * nyd;
   UB[3] = UA[3] - 2.0 * mn * nzd; UB[4] = UA[4];
   Prim<R> As, Bs;  // FP32: the storage form, for the flux-difference form
-  const Prim<R> A = trace_prims<R>(UA, ph, &As), B = trace_prims<R>(UB, ph, &Bs);
+  Lo3 la, lb;
+  const Prim<R> A = trace_prims<R>(UA, ph, &As, &la), B = trace_prims<R>(UB, ph, &Bs, &lb);
   R F[5];
   int fss = 5;  // surface-flux values per face node (10: FP32 difference form)
   if constexpr (std::is_same<R, float>::value) {
@@ -1462,7 +1579,7 @@ k_wall(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, R* __
       float dU[5], DB[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) dU[v] = (float)(UB[v] - UA[v]);
-      face_flux_delta(ph, As, Bs, dU, (R)nxd, (R)nyd, (R)nzd, F, DB);
+      face_flux_delta(ph, As, Bs, la, lb, dU, (R)nxd, (R)nyd, (R)nzd, F, DB);
       fss = 10;
     }
   }
@@ -1615,9 +1732,11 @@ struct VolShape {
   static constexpr int WARPS_NODES = (n3 + 31) / 32;
   static constexpr int THREADS = 32 * (WARPS_LINES > WARPS_NODES ? WARPS_LINES : WARPS_NODES);
   // shared memory (in units of R): 7 prim slots (9 with the entropy-
-  // conserving flux), 9 metric, 5 residual per node, three coefficient tables, 1/w
+  // conserving flux, 10 in the FP32 form of the KEP fluxes: the low parts of
+  // the velocity), 9 metric, 5 residual per node, three coefficient tables, 1/w
   static constexpr int SMEM_R = 21 * n3 + 3 * n2 + n;
   static constexpr int SMEM_R_EC = 23 * n3 + 3 * n2 + n;
+  static constexpr int SMEM_R_F32 = 24 * n3 + 3 * n2 + n;
 };
 
 // Resident CTAs per SM asked of the register allocator: two for CTAs of up to
@@ -1638,8 +1757,9 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
   using Sh = VolShape<N>;
   constexpr int n = Sh::n, n2 = Sh::n2, n3 = Sh::n3, T = Sh::THREADS, LPW = Sh::LPW;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int QS = EC ? 9 : 7;
-  R* sQ = reinterpret_cast<R*>(smem_raw);  // [QS][n3]: rho u v w 4p' h|e 2p (KG); EC see above
+  constexpr bool F32 = std::is_same<R, float>::value;
+  constexpr int QS = EC ? 9 : (F32 ? 10 : 7);
+  R* sQ = reinterpret_cast<R*>(smem_raw);  // [QS][n3]: rho u v w 4p' h|e 2p (KG) (+ FP32: ul vl wl); EC see above
   R* sA = sQ + QS * n3;                     // [9][n3]: Ja (dir*3+comp)
   R* sR = sA + 9 * n3;                      // [5][n3]: residual
   R* sC8 = sR + 5 * n3;                     // [n2]: DVS / 8
@@ -1660,14 +1780,21 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
   if (t < n) siw[t] = (R)tab.iw[t];
   // prologue: node t (the FP32-mixed form reads the stage's FP32 primitives
   // and loads the FP64 state only in the epilogue)
-  constexpr bool F32 = std::is_same<R, float>::value;
   double Uo[5];
   if (t < n3) {
     const size_t g = (size_t)e * n3 + t;
     Prim<R> q;
     if constexpr (F32) {
-      // the difference form works on the storage form (shifted rho, h)
+      // the difference form works on the storage form (shifted rho, h) and
+      // the velocity's low parts
       q = dif ? load_prim32(m.W32, S, g) : load_prim32_full(m.W32, S, g, ph);
+      if constexpr (!EC) {
+        if (dif) {
+          const int ts = vslot<N, R>(t);
+          const Lo3 l = load_lo32(m.W32, S, g);
+          sQ[7 * n3 + ts] = l.u; sQ[8 * n3 + ts] = l.v; sQ[9 * n3 + ts] = l.w;
+        }
+      }
     } else if (m.W64) {
       q = load_prim64(m.W64, S, g);
     } else {
@@ -1788,6 +1915,11 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
       const int me = node_at(dir, pos);
       const int ms = vslot<N, R>(me);
       const VolNode<R> A = load_node(me, dir);
+      // FP32 difference form: the low parts of this lane's node velocity
+      float Aul = 0.f, Avl = 0.f, Awl = 0.f;
+      if constexpr (F32 && !EC) {
+        if (dif) { Aul = sQ[7 * n3 + ms]; Avl = sQ[8 * n3 + ms]; Awl = sQ[9 * n3 + ms]; }
+      }
       R acc[5];
       if (dir == 0) {
         acc[0] = R(0);
@@ -1815,9 +1947,10 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
         const int q = node_at(dir, pm);
         if constexpr (std::is_same<R, float>::value && !EC) {
           if (dif) {
-            const NodeF mi{A.rho, A.u, A.v, A.w, A.p4, A.hh};
+            const NodeF mi{A.rho, A.u, A.v, A.w, A.p4, A.hh, Aul, Avl, Awl};
             const int qs = vslot<N, R>(q);
-            const NodeF mq{sQ[qs], sQ[n3 + qs], sQ[2 * n3 + qs], sQ[3 * n3 + qs], sQ[4 * n3 + qs], sQ[5 * n3 + qs]};
+            const NodeF mq{sQ[qs],          sQ[n3 + qs],     sQ[2 * n3 + qs], sQ[3 * n3 + qs], sQ[4 * n3 + qs],
+                           sQ[5 * n3 + qs], sQ[7 * n3 + qs], sQ[8 * n3 + qs], sQ[9 * n3 + qs]};
             const float aq0 = sA[(dir * 3 + 0) * n3 + qs], aq1 = sA[(dir * 3 + 1) * n3 + qs],
                         aq2 = sA[(dir * 3 + 2) * n3 + qs];
             float G[5];
@@ -1917,8 +2050,9 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
   // surface integral: + sgn * Fs / w_perp on the faces that touch the node
   auto surf = [&](int l, int ab, R iw) {
     const int code = m.elem_face[e * 6 + l];
-    const int f = code >> 1;
+    const int f = code >> 4;
     const R sg = (code & 1) ? -iw : iw;
+    ab = omap_ab<N>((code >> 1) & 7, ab);  // the node's index in the master's face order
     // difference form: the face's own side, F* - F(U_side), in rows 5 n2 apart
     const R* src = dif ? Fs + (size_t)f * 10 * n2 + ((code & 1) ? 5 * n2 : 0) + ab : Fs + (size_t)f * 5 * n2 + ab;
 #pragma unroll
@@ -1961,7 +2095,11 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
     if (bad) atomicOr(status, ST_NONFINITE);
     // the next stage's FP32 primitives, from the updated FP64 state
     if constexpr (F32) {
-      if (st.write_w32) store_prim32(m.W32, S, g, prim32_shifted(Uo[0], Uo[1], Uo[2], Uo[3], Uo[4], ph));
+      if (st.write_w32) {
+        Lo3 l;
+        const Prim<float> q = prim32_shifted(Uo[0], Uo[1], Uo[2], Uo[3], Uo[4], ph, &l);
+        store_prim32(m.W32, S, g, q, l);
+      }
     }
   }
 }

@@ -50,7 +50,9 @@ static int run_typed(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {
   R* Gf = static_cast<R*>(a.Gf);
   R* Fs = static_cast<R*>(a.Fs);
   const size_t smem_lift = (size_t)(16 * n3 + 26 * n2 + n) * sizeof(R);
-  const size_t smem_vol = (size_t)(ph.vol_flux == 2 ? VolShape<N>::SMEM_R_EC : VolShape<N>::SMEM_R) * sizeof(R);
+  const size_t smem_vol = (size_t)(ph.vol_flux == 2 ? VolShape<N>::SMEM_R_EC
+                                   : (std::is_same<R, float>::value ? VolShape<N>::SMEM_R_F32 : VolShape<N>::SMEM_R)) *
+                          sizeof(R);
   constexpr int vol_threads = VolShape<N>::THREADS;
   // per device and cheap: set on every call
   cudaFuncSetAttribute(k_lift<N, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_lift);

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "../../include/dg.h"
+#include "geometry.h"
 
 namespace {
 
@@ -66,9 +67,12 @@ extern "C" int dg_partition_sfc(int N, int K, const double* X, int nranks, int* 
   return DG_OK;
 }
 
-extern "C" int dg_partition_local(int K, const int* nbr, const int* part, int rank, int* K_local, int* l2g,
-                                  int* nbr_local, int* n_halo, int* halo) {
+extern "C" int dg_partition_local(int K, const int* nbr, const int* nbr_face, const int* orient, const int* part,
+                                  int rank, int* K_local, int* l2g, int* nbr_local, int* nbr_face_local,
+                                  int* orient_local, int* n_halo, int* halo) {
   if (K < 1 || !nbr || !part || !K_local || !n_halo) return DG_ERR_ARG;
+  auto nface_of = [&](int e, int l) { return nbr_face ? nbr_face[e * 6 + l] : (l ^ 1); };
+  auto orient_of = [&](int e, int l) { return orient ? orient[e * 6 + l] : 0; };
   std::vector<int> g2l(K, -1);
   int Kr = 0;
   for (int e = 0; e < K; ++e)
@@ -81,9 +85,11 @@ extern "C" int dg_partition_local(int K, const int* nbr, const int* part, int ra
       const int nb = nbr[e * 6 + l];
       if (nb < 0 || part[nb] == rank) continue;
       if (nb >= K) return DG_ERR_ARG;
-      // the master of a face is the element whose +xi/+eta/+zeta face it is
-      const bool master = (l & 1) != 0;
-      const int me = master ? e : nb, ml = master ? l : (l ^ 1);
+      // the face's master by the rule of the host geometry (global ids)
+      const int l2 = nface_of(e, l);
+      if (l2 < 0 || l2 > 5) return DG_ERR_ARG;
+      const bool master = dg::face_is_master(e, l, nb, l2);
+      const int me = master ? e : nb, ml = master ? l : l2;
       recs.push_back({part[nb], (long long)me * 6 + ml, e, l, master ? 1 : 0});
     }
   }
@@ -106,6 +112,20 @@ extern "C" int dg_partition_local(int K, const int* nbr, const int* part, int ra
     }
     for (size_t h = 0; h < recs.size(); ++h)
       nbr_local[g2l[recs[h].elem] * 6 + recs[h].face] = DG_BC_HALO_BASE - (int)h;
+  }
+  // neighbour faces and orientations of the local elements; a halo face's
+  // code carries 8 when the local element is the face's master
+  if (nbr_face_local || orient_local) {
+    for (int e = 0; e < K; ++e) {
+      if (g2l[e] < 0) continue;
+      for (int l = 0; l < 6; ++l) {
+        if (nbr_face_local) nbr_face_local[g2l[e] * 6 + l] = nface_of(e, l);
+        if (orient_local) orient_local[g2l[e] * 6 + l] = orient_of(e, l);
+      }
+    }
+    if (orient_local)
+      for (size_t h = 0; h < recs.size(); ++h)
+        if (recs[h].master) orient_local[g2l[recs[h].elem] * 6 + recs[h].face] |= 8;
   }
   if (halo) {
     for (size_t h = 0; h < recs.size(); ++h) {

@@ -38,7 +38,8 @@ class DGError(RuntimeError):
 
 class _MeshDesc(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int), ("K", ctypes.c_int),
-                ("X", ctypes.POINTER(ctypes.c_double)), ("nbr", ctypes.POINTER(ctypes.c_int))]
+                ("X", ctypes.POINTER(ctypes.c_double)), ("nbr", ctypes.POINTER(ctypes.c_int)),
+                ("nbr_face", ctypes.POINTER(ctypes.c_int)), ("orient", ctypes.POINTER(ctypes.c_int))]
 
 
 class _Phys(ctypes.Structure):
@@ -101,7 +102,7 @@ def lib():
         "dg_set_overlap": (c_int, [vp, c_int]),
         "dg_profile_read": (c_int, [vp, dp, ip]),
         "dg_partition_sfc": (c_int, [c_int, c_int, dp, c_int, ip]),
-        "dg_partition_local": (c_int, [c_int, ip, ip, c_int, ip, ip, ip, ip, ip]),
+        "dg_partition_local": (c_int, [c_int, ip, ip, ip, ip, c_int, ip, ip, ip, ip, ip, ip, ip]),
         "dg_halo_buffers": (c_int, [vp, ip, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                     ctypes.POINTER(vp)]),
         "dg_halo_geometry": (c_int, [vp, dp]),
@@ -164,27 +165,35 @@ def partition_sfc(N, X, nranks):
     return part
 
 
-def partition_local(nbr, part, rank):
-    """(l2g, nbr_local, halo[n_halo, 4]) of one rank (dg_partition_local)."""
+def partition_local(nbr, part, rank, nbr_face=None, orient=None):
+    """(l2g, nbr_local, nbr_face_local, orient_local, halo[n_halo, 4]) of one
+    rank (dg_partition_local)."""
     nbr = np.ascontiguousarray(nbr, dtype=np.int32)
     part = np.ascontiguousarray(part, dtype=np.int32)
     K = part.size
     ip = ctypes.POINTER(ctypes.c_int)
+    nf = None if nbr_face is None else np.ascontiguousarray(nbr_face, dtype=np.int32)
+    ori = None if orient is None else np.ascontiguousarray(orient, dtype=np.int32)
+    pnf = None if nf is None else nf.ctypes.data_as(ip)
+    por = None if ori is None else ori.ctypes.data_as(ip)
     Kl, nh = ctypes.c_int(), ctypes.c_int()
     L = lib()
-    rc = L.dg_partition_local(K, nbr.ctypes.data_as(ip), part.ctypes.data_as(ip), int(rank), ctypes.byref(Kl),
-                              None, None, ctypes.byref(nh), None)
+    rc = L.dg_partition_local(K, nbr.ctypes.data_as(ip), pnf, por, part.ctypes.data_as(ip), int(rank),
+                              ctypes.byref(Kl), None, None, None, None, ctypes.byref(nh), None)
     if rc != 0:
         raise DGError(rc, "dg_partition_local failed")
     l2g = np.zeros(Kl.value, dtype=np.int32)
     nbl = np.zeros((Kl.value, 6), dtype=np.int32)
+    nfl = np.zeros((Kl.value, 6), dtype=np.int32)
+    orl = np.zeros((Kl.value, 6), dtype=np.int32)
     halo = np.zeros((max(nh.value, 1), 4), dtype=np.int32)
-    rc = L.dg_partition_local(K, nbr.ctypes.data_as(ip), part.ctypes.data_as(ip), int(rank), ctypes.byref(Kl),
-                              l2g.ctypes.data_as(ip), nbl.ctypes.data_as(ip), ctypes.byref(nh),
+    rc = L.dg_partition_local(K, nbr.ctypes.data_as(ip), pnf, por, part.ctypes.data_as(ip), int(rank),
+                              ctypes.byref(Kl), l2g.ctypes.data_as(ip), nbl.ctypes.data_as(ip),
+                              nfl.ctypes.data_as(ip), orl.ctypes.data_as(ip), ctypes.byref(nh),
                               halo.ctypes.data_as(ip))
     if rc != 0:
         raise DGError(rc, "dg_partition_local failed")
-    return l2g, nbl, halo[: nh.value]
+    return l2g, nbl, nfl, orl, halo[: nh.value]
 
 
 def _stream_handle(stream):
@@ -201,15 +210,20 @@ class Operator:
     """Ut = DG_Operator(U) and LSERK4 stages on one mesh (one GPU)."""
 
     def __init__(self, N, X, nbr, phys, precision=FP64, vol_flux=VOL_KEP_PIROZZOLI, surf_flux=SURF_LLF,
-                 viscous=1, law=LAW_REICHARDT, stream=None):
+                 viscous=1, law=LAW_REICHARDT, stream=None, nbr_face=None, orient=None):
+        """nbr_face, orient: [K, 6] neighbour faces and orientation codes of a
+        general conforming mesh (None: the structured default)."""
         L = lib()
         self.N = int(N)
         self.n3 = (self.N + 1) ** 3
         X = np.ascontiguousarray(X, dtype=np.float64)
         nbr = np.ascontiguousarray(nbr, dtype=np.int32)
         self.K = X.size // (3 * self.n3)
-        md = _MeshDesc(self.N, self.K, X.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                       nbr.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+        ip = ctypes.POINTER(ctypes.c_int)
+        nf = None if nbr_face is None else np.ascontiguousarray(nbr_face, dtype=np.int32)
+        ori = None if orient is None else np.ascontiguousarray(orient, dtype=np.int32)
+        md = _MeshDesc(self.N, self.K, X.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), nbr.ctypes.data_as(ip),
+                       None if nf is None else nf.ctypes.data_as(ip), None if ori is None else ori.ctypes.data_as(ip))
         ph = _Phys(phys["gamma"], phys["R"], phys["mu"], phys["Pr"],
                    (ctypes.c_double * 3)(phys.get("fx", 0.0), phys.get("fy", 0.0), phys.get("fz", 0.0)),
                    phys.get("kappa", 0.41), phys.get("B", 5.2), phys.get("hwm", 0.1), int(law),

@@ -57,16 +57,16 @@ class LocalRanks:
     time_derivative() run the three phases on every rank with the halo
     exchanges between them as device copies."""
 
-    def __init__(self, N, X, nbr, phys, nranks, part=None, **opts):
+    def __init__(self, N, X, nbr, phys, nranks, part=None, nbr_face=None, orient=None, **opts):
         self.N = N
         self.part = dg.partition_sfc(N, X, nranks) if part is None else np.asarray(part, dtype=np.int32)
         self.nranks = nranks
         self.l2g, self.halo, self.ops = [], [], []
         for r in range(nranks):
-            l2g, nbl, halo = dg.partition_local(nbr, self.part, r)
+            l2g, nbl, nfl, orl, halo = dg.partition_local(nbr, self.part, r, nbr_face, orient)
             self.l2g.append(l2g)
             self.halo.append(halo)
-            self.ops.append(dg.Operator(N, local_coordinates(X, l2g), nbl, phys, **opts))
+            self.ops.append(dg.Operator(N, local_coordinates(X, l2g), nbl, phys, nbr_face=nfl, orient=orl, **opts))
         self.buf = [op.halo_buffers() for op in self.ops]
         # the slave side of each halo face takes the master's normals
         geo = [op.halo_geometry() for op in self.ops]

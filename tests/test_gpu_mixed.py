@@ -29,8 +29,9 @@ def rel_l2(a, ref):
 @pytest.mark.parametrize("label,spec,surf,ma,bound", [
     ("tgv_n3_4^3_llf", I.BoxSpec(3, 4, 4, 4), 1, 0.1, 1e-5),
     ("tgv_n7_4^3_roe", I.BoxSpec(7, 4, 4, 4), 2, 0.1, 1e-5),
-    ("sine_n7_roe_ma03", I.BoxSpec(7, 3, 2, 2, geometry="sine", amplitude=0.1), 2, 0.3, 5e-5),
-    ("n5_central", I.BoxSpec(5, 2, 3, 2, geometry="sine", amplitude=0.2), 0, 0.1, 5e-5),
+    ("sine_n7_roe_ma03", I.BoxSpec(7, 3, 2, 2, geometry="sine", amplitude=0.1), 2, 0.3, 1e-5),
+    ("n5_central", I.BoxSpec(5, 2, 3, 2, geometry="sine", amplitude=0.2), 0, 0.1, 1e-5),
+    ("sine_n7_central_ma03", I.BoxSpec(7, 2, 2, 2, geometry="sine", amplitude=0.1), 0, 0.3, 1e-5),
 ])
 def test_mixed_time_derivative_error(ora, label, spec, surf, ma, bound):
     torch = torch_cuda()

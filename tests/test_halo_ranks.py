@@ -53,7 +53,7 @@ def _rank(rank, world, port, q):
         X = I.node_coordinates(spec, x)
         nbr = I.connectivity(spec)
         part = dg.partition_sfc(N, X, world)
-        l2g, nbl, hl = dg.partition_local(nbr, part, rank)
+        l2g, nbl, _, _, hl = dg.partition_local(nbr, part, rank)
         nh = len(hl)
         sendU = torch.zeros((nh, 5, n * n), dtype=torch.float64)
         sendG = torch.zeros((nh, 4, n * n), dtype=torch.float64)

@@ -85,7 +85,7 @@ def test_inflow_and_outflow_states_must_be_physical():
 def test_halo_codes_must_be_dense():
     spec, X, nbr = _mesh(e=(4, 2, 2))
     part = dg.partition_sfc(spec.N, X, 2)
-    l2g, nbl, hl = dg.partition_local(nbr, part, 0)
+    l2g, nbl, _, _, hl = dg.partition_local(nbr, part, 0)
     Xl = X[:, l2g, :]
     bad = nbl.copy()
     bad[bad == dg.DG_BC_HALO_BASE] = dg.DG_BC_HALO_BASE - 1000   # halo index beyond n_halo

@@ -54,9 +54,9 @@ def test_local_meshes_and_halo_pairing(P, periodic):
     part = dg.partition_sfc(spec.N, X, P)
     locs = [dg.partition_local(nbr, part, r) for r in range(P)]
     # every element on exactly one rank, in ascending global order
-    allg = np.concatenate([l2g for l2g, _, _ in locs])
+    allg = np.concatenate([loc[0] for loc in locs])
     assert np.array_equal(np.sort(allg), np.arange(spec.K))
-    for r, (l2g, nbl, hl) in enumerate(locs):
+    for r, (l2g, nbl, _, _, hl) in enumerate(locs):
         assert np.all(np.diff(l2g) > 0) and np.all(part[l2g] == r)
         g2l = {g: i for i, g in enumerate(l2g)}
         for i, g in enumerate(l2g):
@@ -71,7 +71,7 @@ def test_local_meshes_and_halo_pairing(P, periodic):
                     assert tuple(hl[h]) == (part[gn], i, l, l % 2)
         # the blocks shared with a peer line up face by face
         for q, (a, b) in halo.peer_blocks(hl).items():
-            l2q, _, hq = locs[q]
+            l2q, _, _, _, hq = locs[q]
             qa, qb = halo.peer_blocks(hq)[r]
             assert b - a == qb - qa
             for k in range(b - a):
@@ -84,6 +84,6 @@ def test_local_meshes_and_halo_pairing(P, periodic):
 def test_halo_codes_are_negative_and_distinct():
     spec, X, nbr = _mesh()
     part = dg.partition_sfc(spec.N, X, 4)
-    l2g, nbl, hl = dg.partition_local(nbr, part, 1)
+    l2g, nbl, _, _, hl = dg.partition_local(nbr, part, 1)
     codes = nbl[nbl <= dg.DG_BC_HALO_BASE]
     assert len(codes) == len(hl) and len(set(codes.tolist())) == len(codes)
