@@ -295,7 +295,14 @@ int dg_get_rk_register(dg_ctx* c, double* dU, int on_device);
 int dg_set_rk_register(dg_ctx* c, const double* dU, int on_device);
 
 /* Reads and clears the device status flags.  Returns DG_OK,
- * DG_ERR_NONFINITE or DG_ERR_WM_NOCONV (synchronises the stream). */
+ * DG_ERR_DEVICE_BOUNDS, DG_ERR_NONFINITE or DG_ERR_WM_NOCONV (in that order
+ * of precedence; synchronises the stream).  DG_ERR_DEVICE_BOUNDS comes only
+ * from the bounds-checking build of the library (libdg_gb300_debug.so,
+ * compiled with DG_DEBUG_BOUNDS): there every index that a kernel gathers
+ * through the mesh tables (neighbour and face elements, face ids, halo
+ * indices, wall-model sample elements) is checked against its range, and an
+ * out-of-range one sets the flag and is replaced by 0 instead of being used,
+ * so the GPU never reads outside an array. */
 int dg_check_status(dg_ctx* c);
 
 /* ---------------------------------------------------------------------------

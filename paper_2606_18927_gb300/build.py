@@ -3,6 +3,13 @@
 Each polynomial degree lives in its own translation unit (csrc/op_n<N>.cu)
 so the units compile in parallel; the host geometry and the C ABI are two
 more units.  The result is ``paper_2606_18927_gb300/_build/libdg_gb300.so``.
+
+The bounds-checking variant (``variant="debug"``) compiles the same sources
+with DG_DEBUG_BOUNDS: every index the kernels gather through the mesh tables
+is checked against its range, and one that is out of range sets a device flag
+(reported as DG_ERR_DEVICE_BOUNDS by dg_check_status) and is replaced by 0
+instead of being used.  It is ``_build/debug/libdg_gb300_debug.so``, loaded
+by the binding when DG_LIBRARY_VARIANT=debug.
 """
 import concurrent.futures as cf
 import glob
@@ -15,6 +22,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libdg_gb300.so")
+VARIANTS = {"release": (OUT, LIB, []),
+            "debug": (os.path.join(OUT, "debug"), os.path.join(OUT, "debug", "libdg_gb300_debug.so"),
+                      ["-DDG_DEBUG_BOUNDS"])}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 
@@ -35,15 +45,15 @@ def _headers():
                   glob.glob(os.path.join(HERE, "..", "include", "*.h")))
 
 
-def _stale():
-    if not os.path.exists(LIB):
+def _stale(lib):
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(f) > t for f in _sources() + _headers())
 
 
-def _compile(src, extra):
-    obj = os.path.join(OUT, os.path.basename(src) + ".o")
+def _compile(src, extra, out):
+    obj = os.path.join(out, os.path.basename(src) + ".o")
     cmd = [nvcc()] + ARCH + FLAGS + extra + ["-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
@@ -51,23 +61,33 @@ def _compile(src, extra):
     return obj
 
 
-def build(force=False, jobs=None, extra=()):
-    """Compile the library if it is missing or older than its sources."""
-    os.makedirs(OUT, exist_ok=True)
-    if not force and not _stale():
-        return LIB
+def build(force=False, jobs=None, extra=(), variant="release"):
+    """Compile the library (or its bounds-checking variant) if it is missing
+    or older than its sources."""
+    out, lib, flags = VARIANTS[variant]
+    os.makedirs(out, exist_ok=True)
+    if not force and not _stale(lib):
+        return lib
     srcs = _sources()
     jobs = jobs or min(len(srcs), max(1, os.cpu_count() or 1))
     with cf.ThreadPoolExecutor(jobs) as ex:
-        objs = list(ex.map(lambda s: _compile(s, list(extra)), srcs))
-    tmp = LIB + ".tmp%d" % os.getpid()
+        objs = list(ex.map(lambda s: _compile(s, flags + list(extra), out), srcs))
+    tmp = lib + ".tmp%d" % os.getpid()
     cmd = [nvcc()] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + r.stdout + r.stderr)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
+
+
+def build_all(force=False):
+    """Both variants, compiled side by side."""
+    with cf.ThreadPoolExecutor(2) as ex:
+        libs = list(ex.map(lambda v: build(force=force, jobs=max(1, (os.cpu_count() or 2) // 2), variant=v),
+                           ("release", "debug")))
+    return libs
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv))
+    print(build_all(force="--force" in sys.argv))

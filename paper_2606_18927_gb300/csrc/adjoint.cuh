@@ -310,7 +310,9 @@ k_adj_face(const double* __restrict__ U, const double* __restrict__ lam, const M
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int f = tid / n2, ab = tid - f * n2;
   if (f >= m.n_interior) return;
-  const int4 fc = m.faces[f];
+  int4 fc = m.faces[f];
+  fc.x = chk_idx(fc.x, m.K, m.status);
+  fc.z = chk_idx(fc.z, m.K, m.status);
   const size_t S = (size_t)m.K * n3;
   const size_t gM = (size_t)fc.x * n3 + fnode<N>(fc.y, ab % n, ab / n);
   // ab indexes the master's face nodes; abS the slave's (orientation fc.w >> 3)
@@ -360,7 +362,8 @@ k_adj_wall(const double* __restrict__ U, const double* __restrict__ lam, const M
   double gk = 0.0, gb = 0.0;
   if (wf < m.n_wall) {
     const int f = m.n_interior + wf;
-    const int4 fc = m.faces[f];
+    int4 fc = m.faces[f];
+    fc.x = chk_idx(fc.x, m.K, m.status);
     const size_t S = (size_t)m.K * n3;
     const size_t gM = (size_t)fc.x * n3 + fnode<N>(fc.y, ab % n, ab / n);
     const double jM = m.invJ[gM];
@@ -397,7 +400,7 @@ k_adj_wall(const double* __restrict__ U, const double* __restrict__ lam, const M
     // wall model: Fs_mom += tau s
     const size_t slot = (size_t)wf * n2 + ab;
     if (ph.viscous) {
-      const int es = m.ws_elem[slot];
+      const int es = chk_idx(m.ws_elem[slot], m.K, m.status);
       const double* L = m.ws_lag + slot * 3 * n;
       double Us[5] = {0, 0, 0, 0, 0};
       for (int kk = 0; kk < n; ++kk)
@@ -630,7 +633,7 @@ k_adj_element(const double* __restrict__ U, const double* __restrict__ lam, cons
       const int nb = m.nbr[e * 6 + l];
       double d[4];
       if (nb >= 0) {
-        const NbrNode<N> nn = neighbour_node<N>(m.elem_face, m.faces, e, l, ab);
+        const NbrNode<N> nn = neighbour_node<N>(m, e, l, ab);
         const size_t gn = (size_t)nn.e * n3 + fnode<N>(nn.l, nn.ab % n, nn.ab / n);
         double un, vn, wn, Tn;
         velocity_temperature<double>(U[gn], U[S + gn], U[2 * S + gn], U[3 * S + gn], U[4 * S + gn], ph, un, vn,
@@ -892,7 +895,7 @@ k_adj_gather(const double* __restrict__ U, const MeshDev<double> m, const PhysDe
     for (int v = 0; v < 5; ++v) add[v] += src[v * n2];
     const int nb = m.nbr[e * 6 + l];
     if (ph.viscous && nb >= 0) {
-      const NbrNode<N> nn = neighbour_node<N>(m.elem_face, m.faces, e, l, ab);
+      const NbrNode<N> nn = neighbour_node<N>(m, e, l, ab);
       const double* w = gWf + ((size_t)nn.e * 6 + nn.l) * 4 * n2 + nn.ab;
 #pragma unroll
       for (int v = 0; v < 4; ++v) gW[v] += w[v * n2];
@@ -925,7 +928,7 @@ k_adj_scatter(const MeshDev<double> m, const double* __restrict__ gUs, double* _
   const int slot = blockIdx.x * blockDim.x + threadIdx.x;
   if (slot >= m.n_wall * n2) return;
   const size_t S = (size_t)m.K * n3;
-  const int es = m.ws_elem[slot];
+  const int es = chk_idx(m.ws_elem[slot], m.K, m.status);
   const double* L = m.ws_lag + (size_t)slot * 3 * n;
   double gs[5];
 #pragma unroll
@@ -961,7 +964,7 @@ k_wall_loss(const double* __restrict__ U, const MeshDev<double> m, const PhysDev
     const size_t S = (size_t)m.K * n3;
     const size_t FN = (size_t)m.F * n2, fg = (size_t)f * n2 + ab;
     const double nx = m.fgeo[fg], ny = m.fgeo[FN + fg], nz = m.fgeo[2 * FN + fg];
-    const int es = m.ws_elem[slot];
+    const int es = chk_idx(m.ws_elem[slot], m.K, m.status);
     const double* L = m.ws_lag + (size_t)slot * 3 * n;
     double Us[5] = {0, 0, 0, 0, 0};
     for (int kk = 0; kk < n; ++kk)

@@ -434,6 +434,7 @@ int dg_init_mesh(dg_ctx** out, const dg_mesh_desc* m, const dg_phys* p, const dg
   ph.f32c.g_gm1 = (float)(p->gamma / (p->gamma - 1.0));
   ph.f32c.h_p = p->rho_ref > 0.0 ? 0.0f : (float)p->p_ref;
   ph.f32c.h_r = p->rho_ref > 0.0 ? (float)(p->p_ref / p->rho_ref) : 0.0f;
+  ph.f32c.T_lift = p->rho_ref > 0.0 ? (float)(p->p_ref / (p->rho_ref * p->R)) : 0.0f;
   cudaGetDevice(&c->device);
   // device storage
   const size_t S = c->S, n2 = c->n2;
@@ -1025,6 +1026,8 @@ int dg_check_status(dg_ctx* c) {
   if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, sizeof(int), c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "dg_check_status");
+  if (h & dg::ST_BOUNDS)
+    return fail(c, DG_ERR_DEVICE_BOUNDS, "a kernel gathered an index outside its array (bounds-checking build)");
   if (h & dg::ST_NONFINITE) return fail(c, DG_ERR_NONFINITE, "non-finite value in the state");
   if (h & dg::ST_WM_NOCONV) return fail(c, DG_ERR_WM_NOCONV, "wall-model Newton iteration did not converge");
   return DG_OK;

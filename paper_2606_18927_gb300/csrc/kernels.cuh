@@ -36,7 +36,24 @@
 
 namespace dg {
 
-enum { ST_NONFINITE = 1, ST_WM_NOCONV = 2 };
+enum { ST_NONFINITE = 1, ST_WM_NOCONV = 2, ST_BOUNDS = 4 };
+
+// Index checks of the bounds-checking build (DG_DEBUG_BOUNDS): an index
+// gathered through the mesh tables that lies outside [0, n) sets the status
+// flag that dg_check_status reports as DG_ERR_DEVICE_BOUNDS and is replaced by
+// 0, so that the access stays inside the array; nothing traps.  The ordinary
+// build compiles the checks away.
+__device__ __forceinline__ int chk_idx(int i, int n, int* status) {
+#ifdef DG_DEBUG_BOUNDS
+  if (i < 0 || i >= n) {
+    if (status) atomicOr(status, ST_BOUNDS);
+    return 0;
+  }
+#else
+  (void)n; (void)status;
+#endif
+  return i;
+}
 
 struct PhysDev {
   double gamma, gm1, R, mu, Pr, cp, kcond, rcp_R;
@@ -60,6 +77,7 @@ struct PhysDev {
   struct {
     float p_ref, rcp_R, rgm1, gamma, mu, kcond, cp_Pr, suth_C, suth_S, rho_ref, h_ref;
     float g_gm1, h_p, h_r;  // gamma / (gamma - 1); p_ref (rho_ref = 0) or 0; p_ref / rho_ref or 0
+    float T_lift;           // rho_ref > 0: p_ref / (rho_ref R), else 0
     float ec_q[5];
   } f32c;
 };
@@ -98,6 +116,7 @@ struct MeshDev {
   const double* JaJ;     // FP64 viscous form: [9][K*n3] Ja / J (dir*3+comp)
   const double* Mj;      // FP64 viscous form: [6][K*n3] (Ja Ja^T) / J (00, 11, 22, 01, 02, 12)
   double* wm_t;          // [n_wall*n2] last wall-law solution per wall node (warm start; may be null)
+  int* status;           // device status flags (index checks of the bounds-checking build)
 };
 
 template <int N>
@@ -153,13 +172,12 @@ struct NbrNode {
   int ab;    // face-local index of the coinciding node on that face
 };
 
-template <int N>
-__device__ __forceinline__ NbrNode<N> neighbour_node(const int* __restrict__ elem_face, const int4* __restrict__ faces,
-                                                     int e, int l, int ab) {
-  const int code = elem_face[e * 6 + l];
-  const int4 fc = faces[code >> 4];
-  if (code & 1) return NbrNode<N>{fc.x, fc.y, omap_ab<N>((code >> 1) & 7, ab)};
-  return NbrNode<N>{fc.z, fc.w & 7, omap_ab<N>(fc.w >> 3, ab)};
+template <int N, typename M>
+__device__ __forceinline__ NbrNode<N> neighbour_node(const M& m, int e, int l, int ab) {
+  const int code = m.elem_face[e * 6 + l];
+  const int4 fc = m.faces[chk_idx(code >> 4, m.F, m.status)];
+  if (code & 1) return NbrNode<N>{chk_idx(fc.x, m.K, m.status), fc.y, omap_ab<N>((code >> 1) & 7, ab)};
+  return NbrNode<N>{chk_idx(fc.z, m.K, m.status), fc.w & 7, omap_ab<N>(fc.w >> 3, ab)};
 }
 
 // 1/x for x > 0 in double: an FP32 estimate refined by two Newton steps
@@ -407,6 +425,36 @@ __device__ __forceinline__ void velocity_temperature<float>(const double U0, con
   T = (q.p + ph.f32c.p_ref) * ph.f32c.rcp_R / q.rho;
 }
 
+// FP32 lifting: the velocity and the temperature relative to T_lift =
+// p_ref / (rho_ref R), the temperature of the storage form's reference state:
+//   T - T_lift = (p' rho_ref - p_ref rho') / (rho rho_ref R)
+// from the shifted density and pressure of the storage form.  Rounded to FP32
+// the temperature itself (O(p_ref / rho_ref): 7.9 at Mach 0.3, 71 at Mach 0.1)
+// would put an error eps32 T into every node's value, which the heat flux,
+// the derivative of the lifted gradient, amplifies by (N^2 / h)^2; the
+// deviation carries the rounding of the deviation only.  (rho_ref = 0: T.)
+__device__ __forceinline__ void velocity_temperature32s(const Prim<float>& q, const PhysDev& ph, float& u, float& v,
+                                                        float& w, float& Tp) {
+  u = q.u; v = q.v; w = q.w;
+  if (ph.f32c.rho_ref > 0.0f) {
+    const float rho = ph.f32c.rho_ref + q.rho;
+    Tp = fmaf(-ph.f32c.h_r, q.rho, q.p) * ph.f32c.rcp_R / rho;  // h_r = p_ref / rho_ref
+  } else {
+    Tp = (q.p + ph.f32c.p_ref) * ph.f32c.rcp_R / q.rho;
+  }
+}
+
+// the same from an FP64 state (traces of halo and boundary faces)
+__device__ __forceinline__ void velocity_temperature32s_of(const double U0, const double U1, const double U2,
+                                                           const double U3, const double U4, const PhysDev& ph,
+                                                           float& u, float& v, float& w, float& Tp) {
+  const double ir = 1.0 / U0;
+  const double ud = U1 * ir, vd = U2 * ir, wd = U3 * ir;
+  const double pr = ph.gm1 * (U4 - 0.5 * U0 * (ud * ud + vd * vd + wd * wd));
+  u = (float)ud; v = (float)vd; w = (float)wd;
+  Tp = (float)(pr * ph.rcp_R * ir - (double)ph.f32c.T_lift);
+}
+
 // Entropy-conserving two-point flux of Chandrashekar (the paper's Sec. 4
 // volume flux) along a (a need not be unit), with beta = rho / (2 p):
 //   F_rho = ln-mean(rho) {u}.a,  F_m = p~ a + {u} F_rho,
@@ -481,7 +529,7 @@ __device__ __forceinline__ void twopoint(int kind, const Prim<R>& A, const Prim<
 template <typename R>
 __device__ __forceinline__ void riemann_dissipation(const PhysDev& ph, const Prim<R>& A, const Prim<R>& B,
                                                     const R dU[5], R nx, R ny, R nz, R F[5],
-                                                    const R* drho = nullptr) {
+                                                    const R* drho = nullptr, const R* dvel = nullptr) {
   const R pref = cR<R>(ph.p_ref, ph.f32c.p_ref);
   const R g = cR<R>(ph.gamma, ph.f32c.gamma);
   if (ph.surf_flux == 1) {  // local Lax-Friedrichs (sound speed from the full pressure)
@@ -504,7 +552,10 @@ __device__ __forceinline__ void riemann_dissipation(const PhysDev& ph, const Pri
     const R c = sqrt(c2);
     const R un = u * nx + v * ny + w * nz;
     const R dr = drho ? *drho : B.rho - A.rho, dp = B.p - A.p;
-    const R du = B.u - A.u, dv = B.v - A.v, dw = B.w - A.w;
+    // (the FP32 difference form passes the velocity jump from the velocities'
+    // high and low parts: from the rounded velocities it would carry an error
+    // eps32 |u| that the acoustic waves multiply by rho c)
+    const R du = dvel ? dvel[0] : B.u - A.u, dv = dvel ? dvel[1] : B.v - A.v, dw = dvel ? dvel[2] : B.w - A.w;
     const R dun = du * nx + dv * ny + dw * nz;
     const R i2c2 = R(0.5) * rcp_t<R>(c2);
     const R a1 = (dp - rt * c * dun) * i2c2;
@@ -598,7 +649,8 @@ __device__ __forceinline__ void face_flux_delta(const PhysDev& ph, const Prim<fl
                                                 float nz, float DA[5], float DB[5]) {
   float Z[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
   const float drho = B.rho - A.rho;
-  riemann_dissipation<float>(ph, unshift32(A, ph), unshift32(B, ph), dU, nx, ny, nz, Z, &drho);
+  const float dvel[3] = {(B.u - A.u) + (lb.u - la.u), (B.v - A.v) + (lb.v - la.v), (B.w - A.w) + (lb.w - la.w)};
+  riemann_dissipation<float>(ph, unshift32(A, ph), unshift32(B, ph), dU, nx, ny, nz, Z, &drho, dvel);
   const float rr = ph.f32c.rho_ref, hr = ph.f32c.h_ref;
   flux_delta(nodef(A, la), nodef(B, lb), nx, ny, nz, 0.f, 0.f, 0.f, rr, hr, DA);
   flux_delta(nodef(B, lb), nodef(A, la), nx, ny, nz, 0.f, 0.f, 0.f, rr, hr, DB);
@@ -1042,7 +1094,7 @@ k_lift(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
   {
     R u, v, w, T;
     if constexpr (std::is_same<R, float>::value) {
-      velocity_temperature32(load_prim32_full(m.W32, S, g, ph), ph, u, v, w, T);
+      velocity_temperature32s(load_prim32(m.W32, S, g), ph, u, v, w, T);  // T: T - T_lift
     } else if (m.W64) {
       // the FP64 primitives k_prim64 stored for this evaluation
       u = m.W64[S + g]; v = m.W64[2 * S + g]; w = m.W64[3 * S + g]; T = m.W64[6 * S + g];
@@ -1062,11 +1114,11 @@ k_lift(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
     const R Wo0 = sW[q], Wo1 = sW[n3 + q], Wo2 = sW[2 * n3 + q], Wo3 = sW[3 * n3 + q];
     R d0, d1, d2, d3;
     if (nb >= 0) {
-      const NbrNode<N> nn = neighbour_node<N>(m.elem_face, m.faces, e, l, ab);
+      const NbrNode<N> nn = neighbour_node<N>(m, e, l, ab);
       const size_t gn = (size_t)nn.e * n3 + fnode<N>(nn.l, nn.ab % n, nn.ab / n);
       R u, v, w, T;
       if constexpr (std::is_same<R, float>::value) {
-        velocity_temperature32(load_prim32_full(m.W32, S, gn, ph), ph, u, v, w, T);
+        velocity_temperature32s(load_prim32(m.W32, S, gn), ph, u, v, w, T);
       } else if (m.W64) {
         u = m.W64[S + gn]; v = m.W64[2 * S + gn]; w = m.W64[3 * S + gn]; T = m.W64[6 * S + gn];
       } else {
@@ -1077,7 +1129,7 @@ k_lift(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
       // halo face: the remote element's trace from the halo buffer (in the
       // master's face-node order)
       const int abm = omap_ab<N>((m.elem_face[e * 6 + l] >> 1) & 7, ab);
-      const double* src = m.halo_U + (size_t)(-16 - nb) * 5 * n2 + abm;
+      const double* src = m.halo_U + (size_t)chk_idx(-16 - nb, m.n_halo, m.status) * 5 * n2 + abm;
       R u, v, w, T;
       if constexpr (std::is_same<R, double>::value) {
         if (m.W64) {
@@ -1088,7 +1140,7 @@ k_lift(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
           velocity_temperature<R>(src[0], src[n2], src[2 * n2], src[3 * n2], src[4 * n2], ph, u, v, w, T);
         }
       } else {
-        velocity_temperature<R>(src[0], src[n2], src[2 * n2], src[3 * n2], src[4 * n2], ph, u, v, w, T);
+        velocity_temperature32s_of(src[0], src[n2], src[2 * n2], src[3 * n2], src[4 * n2], ph, u, v, w, T);
       }
       d0 = u - Wo0; d1 = v - Wo1; d2 = w - Wo2; d3 = T - Wo3;
     } else if (nb != -1) {
@@ -1099,7 +1151,10 @@ k_lift(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
       for (int v = 0; v < 5; ++v) Ui[v] = U[v * S + gq];
       ghost_state(ph, nb, Ui, Ub);
       R u, v, w, T;
-      velocity_temperature<R>(Ub[0], Ub[1], Ub[2], Ub[3], Ub[4], ph, u, v, w, T);
+      if constexpr (std::is_same<R, float>::value)
+        velocity_temperature32s_of(Ub[0], Ub[1], Ub[2], Ub[3], Ub[4], ph, u, v, w, T);
+      else
+        velocity_temperature<R>(Ub[0], Ub[1], Ub[2], Ub[3], Ub[4], ph, u, v, w, T);
       d0 = u - Wo0; d1 = v - Wo1; d2 = w - Wo2; d3 = T - Wo3;
     } else {
       // mirror: 2 (W* - W) = -2 (u . n) n, T unchanged (n: own outward unit normal)
@@ -1162,7 +1217,8 @@ k_lift(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
   // viscous flux Fv_d = (0, tau_1d, tau_2d, tau_3d, tau_jd u_j + k dT/dx_d)
   R mu = cR<R>(ph.mu, ph.f32c.mu), kc = cR<R>(ph.kcond, ph.f32c.kcond);
   if (ph.sutherland) {
-    mu = sutherland<R>(ph, sW[3 * n3 + p]);
+    // (FP32: the lifted temperature is T - T_lift)
+    mu = sutherland<R>(ph, sW[3 * n3 + p] + cR<R>(0.0, ph.f32c.T_lift));
     kc = mu * cR<R>(ph.cp_Pr, ph.f32c.cp_Pr);
   }
   const R uu = sW[p], vv = sW[n3 + p], ww = sW[2 * n3 + p];
@@ -1318,10 +1374,11 @@ k_face(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
   const R* gB;
   if constexpr (!D) {
     const int abS = omap_ab<N>(fc.w >> 3, ab), lS = fc.w & 7;
-    const size_t gM = (size_t)fc.x * n3 + fnode<N>(fc.y, ab % n, ab / n);
-    const size_t gS = (size_t)fc.z * n3 + fnode<N>(lS, abS % n, abS / n);
-    gA = Gf + ((size_t)fc.x * 6 + fc.y) * 4 * n2 + ab;
-    gB = Gf + ((size_t)fc.z * 6 + lS) * 4 * n2 + abS;
+    const int eM = chk_idx(fc.x, m.K, m.status), eS = chk_idx(fc.z, m.K, m.status);
+    const size_t gM = (size_t)eM * n3 + fnode<N>(fc.y, ab % n, ab / n);
+    const size_t gS = (size_t)eS * n3 + fnode<N>(lS, abS % n, abS / n);
+    gA = Gf + ((size_t)eM * 6 + fc.y) * 4 * n2 + ab;
+    gB = Gf + ((size_t)eS * 6 + lS) * 4 * n2 + abS;
     const Prim<float> A = load_prim32(m.W32, S, gM), B = load_prim32(m.W32, S, gS);
     const Lo3 la = load_lo32(m.W32, S, gM), lb = load_lo32(m.W32, S, gS);
     // U_B - U_A for the Lax-Friedrichs dissipation, differenced in FP64 (from
@@ -1345,10 +1402,11 @@ k_face(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
     const bool llf = ph.surf_flux == 1;
     if (!is_halo) {
       const int abS = omap_ab<N>(fc.w >> 3, ab), lS = fc.w & 7;
-      const size_t gM = (size_t)fc.x * n3 + fnode<N>(fc.y, ab % n, ab / n);
-      const size_t gS = (size_t)fc.z * n3 + fnode<N>(lS, abS % n, abS / n);
-      gA = Gf + ((size_t)fc.x * 6 + fc.y) * 4 * n2 + ab;
-      gB = Gf + ((size_t)fc.z * 6 + lS) * 4 * n2 + abS;
+      const int eM = chk_idx(fc.x, m.K, m.status), eS = chk_idx(fc.z, m.K, m.status);
+      const size_t gM = (size_t)eM * n3 + fnode<N>(fc.y, ab % n, ab / n);
+      const size_t gS = (size_t)eS * n3 + fnode<N>(lS, abS % n, abS / n);
+      gA = Gf + ((size_t)eM * 6 + fc.y) * 4 * n2 + ab;
+      gB = Gf + ((size_t)eS * 6 + lS) * 4 * n2 + abS;
       if (m.W64) {
         A = load_prim64(m.W64, S, gM);
         B = load_prim64(m.W64, S, gS);
@@ -1365,7 +1423,8 @@ k_face(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
       // | 8 o_own); ab is the master's face-node index, abl the local one
       const int h = f0 - m.n_interior;
       const int abl = omap_ab<N>(orient_inv(fc.w >> 3), ab);
-      const size_t gL = (size_t)fc.x * n3 + fnode<N>(fc.y, abl % n, abl / n);
+      const int eL = chk_idx(fc.x, m.K, m.status);
+      const size_t gL = (size_t)eL * n3 + fnode<N>(fc.y, abl % n, abl / n);
       const double* rU = m.halo_U + (size_t)h * 5 * n2 + ab;
       const bool master = (fc.w & 1) != 0;
       const Prim<double> loc =
@@ -1374,7 +1433,7 @@ k_face(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
       const Prim<double> rem = primitive_T(rU[0], rU[n2], rU[2 * n2], rU[3 * n2], rU[4 * n2], ph, T);
       A = master ? loc : rem;
       B = master ? rem : loc;
-      const R* gl = Gf + ((size_t)fc.x * 6 + fc.y) * 4 * n2 + abl;
+      const R* gl = Gf + ((size_t)eL * 6 + fc.y) * 4 * n2 + abl;
       const R* gr = m.halo_G + (size_t)h * 4 * n2 + ab;
       gA = master ? gl : gr;
       gB = master ? gr : gl;
@@ -1418,7 +1477,8 @@ k_halo_face(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, 
   const int4 fc = m.faces[f];
   const size_t S = (size_t)m.K * n3;
   const int abl = omap_ab<N>(orient_inv(fc.w >> 3), ab);
-  const size_t gL = (size_t)fc.x * n3 + fnode<N>(fc.y, abl % n, abl / n);
+  const int eL = chk_idx(fc.x, m.K, m.status);
+  const size_t gL = (size_t)eL * n3 + fnode<N>(fc.y, abl % n, abl / n);
   const double* rU = m.halo_U + (size_t)h * 5 * n2 + ab;
   const bool master = (fc.w & 1) != 0;
   double UA[5], UB[5];
@@ -1438,7 +1498,7 @@ k_halo_face(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, 
       float dU[5];
 #pragma unroll
       for (int v = 0; v < 5; ++v) dU[v] = (float)(UB[v] - UA[v]);
-      const R* gl = Gf + ((size_t)fc.x * 6 + fc.y) * 4 * n2 + abl;
+      const R* gl = Gf + ((size_t)eL * 6 + fc.y) * 4 * n2 + abl;
       const R* gr = m.halo_G + (size_t)h * 4 * n2 + ab;
       store_face_delta(ph, As, Bs, la, lb, dU, nx, ny, nz, s, master ? gl : gr, master ? gr : gl, 0.5f,
                        Fs + (size_t)f * 10 * n2 + ab, n2, true);
@@ -1450,7 +1510,7 @@ k_halo_face(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, 
   R* out = Fs + (size_t)f * 5 * n2 + ab;
   out[0] = F[0] * s;
   if (ph.viscous) {
-    const R* gl = Gf + ((size_t)fc.x * 6 + fc.y) * 4 * n2 + abl;
+    const R* gl = Gf + ((size_t)eL * 6 + fc.y) * 4 * n2 + abl;
     const R* gr = m.halo_G + (size_t)h * 4 * n2 + ab;
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
@@ -1477,14 +1537,15 @@ k_halo_pack(const double* __restrict__ U, const MeshDev<R> m, const R* __restric
   const int4 fc = m.faces[m.F - m.n_halo + h];
   // ab is the index in the master's face-node order; abl the local one
   const int abl = omap_ab<N>(orient_inv(fc.w >> 3), ab);
+  const int eL = chk_idx(fc.x, m.K, m.status);
   if (sendU) {
     const size_t S = (size_t)m.K * n3;
-    const size_t gL = (size_t)fc.x * n3 + fnode<N>(fc.y, abl % n, abl / n);
+    const size_t gL = (size_t)eL * n3 + fnode<N>(fc.y, abl % n, abl / n);
 #pragma unroll
     for (int v = 0; v < 5; ++v) sendU[((size_t)h * 5 + v) * n2 + ab] = U[v * S + gL];
   }
   if (sendG) {
-    const R* gl = Gf + ((size_t)fc.x * 6 + fc.y) * 4 * n2 + abl;
+    const R* gl = Gf + ((size_t)eL * 6 + fc.y) * 4 * n2 + abl;
 #pragma unroll
     for (int v = 0; v < 4; ++v) sendG[((size_t)h * 4 + v) * n2 + ab] = gl[v * n2];
   }
@@ -1504,7 +1565,8 @@ k_bc(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const R
   const int bf = tid / n2, ab = tid - bf * n2;
   if (bf >= m.n_bc) return;
   const int f = m.n_interior + m.n_wall + bf;
-  const int4 fc = m.faces[f];
+  int4 fc = m.faces[f];
+  fc.x = chk_idx(fc.x, m.K, m.status);
   const size_t S = (size_t)m.K * n3;
   const size_t gM = (size_t)fc.x * n3 + fnode<N>(fc.y, ab % n, ab / n);
   double UA[5], UB[5];
@@ -1558,7 +1620,8 @@ k_wall(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, R* __
   const int wf = tid / n2, ab = tid - wf * n2;
   if (wf >= m.n_wall) return;
   const int f = m.n_interior + wf;
-  const int4 fc = m.faces[f];
+  int4 fc = m.faces[f];
+  fc.x = chk_idx(fc.x, m.K, m.status);
   const size_t S = (size_t)m.K * n3;
   const size_t gM = (size_t)fc.x * n3 + fnode<N>(fc.y, ab % n, ab / n);
   const size_t FN = (size_t)m.F * n2, fg = (size_t)f * n2 + ab;
@@ -1592,7 +1655,7 @@ k_wall(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, R* __
       // p_ref / (gamma - 1) (the interpolation weights sum to one), then the
       // FP32 wall model
       const size_t slot = (size_t)wf * n2 + ab;
-      const int es = m.ws_elem[slot];
+      const int es = chk_idx(m.ws_elem[slot], m.K, m.status);
       const double* Ld = m.ws_lag + slot * 3 * n;
       float L[3 * n];
 #pragma unroll
@@ -1631,7 +1694,7 @@ k_wall(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, R* __
   } else if (ph.viscous) {
     // sample state at h_wm: tensor-product Lagrange interpolation of U
     const size_t slot = (size_t)wf * n2 + ab;
-    const int es = m.ws_elem[slot];
+    const int es = chk_idx(m.ws_elem[slot], m.K, m.status);
     const double* L = m.ws_lag + slot * 3 * n;
     double Us[5] = {0, 0, 0, 0, 0};
     for (int kk = 0; kk < n; ++kk)
@@ -2050,7 +2113,7 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
   // surface integral: + sgn * Fs / w_perp on the faces that touch the node
   auto surf = [&](int l, int ab, R iw) {
     const int code = m.elem_face[e * 6 + l];
-    const int f = code >> 4;
+    const int f = chk_idx(code >> 4, m.F, m.status);
     const R sg = (code & 1) ? -iw : iw;
     ab = omap_ab<N>((code >> 1) & 7, ab);  // the node's index in the master's face order
     // difference form: the face's own side, F* - F(U_side), in rows 5 n2 apart

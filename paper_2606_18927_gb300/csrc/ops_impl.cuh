@@ -36,6 +36,7 @@ static int run_typed(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {
   m.Ja = static_cast<const R*>(a.Ja); m.invJ = static_cast<const R*>(a.invJ);
   m.fgeo = a.fgeo; m.nbr = a.nbr; m.elem_face = a.elem_face; m.faces = a.faces;
   m.ws_elem = a.ws_elem; m.ws_lag = a.ws_lag;
+  m.status = a.status;
   m.W32 = std::is_same<R, float>::value ? a.W32 : nullptr;
   // FP64 viscous form: the primitives stored by k_prim64 (before the lifting
   // kernel) and the lifting kernel's metric products
@@ -153,6 +154,7 @@ static int run_vjp_typed(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {
   m.Ja = static_cast<const double*>(a.Ja); m.invJ = static_cast<const double*>(a.invJ);
   m.fgeo = a.fgeo; m.nbr = a.nbr; m.elem_face = a.elem_face; m.faces = a.faces;
   m.ws_elem = a.ws_elem; m.ws_lag = a.ws_lag;
+  m.status = a.status;
   m.JaJ = a.JaJ; m.Mj = a.Mj;
   if (ph.viscous && !a.JaJ) return (int)cudaErrorInvalidValue;
   const Tables<N> tab = make_tables<N>(a.D, a.w);
@@ -187,6 +189,7 @@ static int run_wall_loss_typed(const OpArgs& a, const PhysDev& ph, const double*
   m.Ja = static_cast<const double*>(a.Ja); m.invJ = static_cast<const double*>(a.invJ);
   m.fgeo = a.fgeo; m.nbr = a.nbr; m.elem_face = a.elem_face; m.faces = a.faces;
   m.ws_elem = a.ws_elem; m.ws_lag = a.ws_lag;
+  m.status = a.status;
   if (a.n_wall == 0) return 0;
   const long long work = (long long)a.n_wall * n2;
   k_wall_loss<N><<<(unsigned)((work + WALL_THREADS - 1) / WALL_THREADS), WALL_THREADS, 0, s>>>(a.Uin, m, ph, wq, inv_total, grad, loss, a.gUs,

@@ -68,7 +68,8 @@ def lib():
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.build()
+    # DG_LIBRARY_VARIANT=debug: the bounds-checking build (index checks in the kernels)
+    path = _build.build(variant=os.environ.get("DG_LIBRARY_VARIANT", "release"))
     L = ctypes.CDLL(path)
     vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
     c_int, c_double = ctypes.c_int, ctypes.c_double

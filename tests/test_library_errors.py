@@ -90,3 +90,19 @@ def test_halo_codes_must_be_dense():
     bad = nbl.copy()
     bad[bad == dg.DG_BC_HALO_BASE] = dg.DG_BC_HALO_BASE - 1000   # halo index beyond n_halo
     assert _init(spec.N, Xl, bad)[0] == MESH
+
+
+def test_face_orientation_must_be_consistent():
+    """A neighbour face or orientation code that the neighbour does not list
+    back, or under which the face nodes do not coincide, is rejected."""
+    spec, X, nbr = _mesh()
+    nf = np.tile(np.arange(6, dtype=np.int32) ^ 1, (spec.K, 1))
+    ori = np.zeros((spec.K, 6), dtype=np.int32)
+    bad = ori.copy(); bad[0, 1] = 9                   # not a code
+    assert _init(spec.N, X, nbr, nbr_face=nf, orient=bad)[0] == MESH
+    bad = ori.copy(); bad[0, 1] = 2                   # the neighbour lists 0
+    assert _init(spec.N, X, nbr, nbr_face=nf, orient=bad)[0] == MESH
+    bad = ori.copy(); bad[0, 1] = 2; bad[nbr[0, 1], 0] = 2   # reciprocal, nodes do not meet
+    assert _init(spec.N, X, nbr, nbr_face=nf, orient=bad)[0] == MESH
+    badf = nf.copy(); badf[0, 1] = 3                  # wrong neighbour face
+    assert _init(spec.N, X, nbr, nbr_face=badf, orient=ori)[0] == MESH

@@ -31,3 +31,13 @@ def test_host_lgl_rejects_bad_degree():
     with pytest.raises(dg.DGError) as e:
         dg.lgl_nodes(0)
     assert e.value.code == -1
+
+
+def test_bounds_checking_build_exports_every_header_symbol():
+    """The bounds-checking variant (DG_DEBUG_BOUNDS) builds and exports the
+    same C ABI."""
+    import ctypes
+    from paper_2606_18927_gb300 import build
+    L = ctypes.CDLL(build.build(variant="debug"))
+    missing = [n for n in dg.header_functions() if not hasattr(L, n)]
+    assert not missing, missing
