@@ -324,10 +324,10 @@ __device__ __forceinline__ Prim<float> primitive<float>(const double U0, const d
 // to FP32, the velocity (O(1) at any Mach number) put an error of eps32 |u|
 // into every difference, the largest input error of the form (about 1.6e-5
 // of the Ut of the 48^3 curved box at Mach 0.3).  The low parts come from
-// the exact FP32 residual m - u rho, formed with FMAs:
-//   r = (m_hi - u rho_ref) - u rho_hi' - u rho_lo' + m_lo,  lo = r / rho,
-// where m_lo = m - m_hi and rho_lo' = (rho - rho_ref) - rho_hi' are the
-// roundings of the conversions to FP32 (three FP64 operations each).
+// the FP32 residual m - u rho, formed with FMAs:
+//   r = (m_hi - u rho_ref) - u rho' + m_lo,  lo = r / rho,
+// where m_lo = m - m_hi is the rounding of the conversion to FP32 (three FP64
+// operations per component).
 struct Lo3 {
   float u, v, w;
 };
@@ -346,12 +346,12 @@ __device__ __forceinline__ Prim<float> prim32_shifted(const double U0, const dou
   q.p = (float)pr;
   q.h = fmaf(ph.f32c.g_gm1, q.p + ph.f32c.h_p - ph.f32c.h_r * q.rho, ke) * ir;
   if (lo) {
-    const float rl = (float)(rd - (double)q.rho);
+    // (the rounding of rho - rho_ref, relative eps32 of a small deviation,
+    // changes u by a relative 1e-10 or so: left out)
     auto low = [&](double mf, float mh, float uh) {
       const float ml = (float)(mf - (double)mh);
       float r = fmaf(-uh, ph.f32c.rho_ref, mh);
       r = fmaf(-uh, q.rho, r);
-      r = fmaf(-uh, rl, r);
       return (r + ml) * ir;
     };
     lo->u = low(U1, m1, q.u);
