@@ -235,8 +235,10 @@ int dg_rk_steps(dg_ctx* c, double t, double dt, int nsteps);
  * flux and of its dissipation, one backward sweep); the local derivatives of
  * the wall model come from forward-mode dual numbers, with the implicit
  * function theorem for the law-of-the-wall solve (Sec. 3.2).  FP64
- * contexts with the Pirozzoli volume flux, a constant viscosity, adiabatic
- * walls and no inflow, outflow or halo faces (else DG_ERR_NOT_IMPLEMENTED).
+ * contexts with the Pirozzoli or the entropy-conserving volume flux (the
+ * paper's Sec. 4 scheme, with Roe + Harten faces), constant viscosity or
+ * Sutherland's law, adiabatic walls and no inflow, outflow or halo faces
+ * (else DG_ERR_NOT_IMPLEMENTED).
  * The first call allocates the adjoint scratch of the context. */
 int dg_vjp(dg_ctx* c, const double* U, const double* lam, double* gU, double* gtheta);
 
@@ -277,7 +279,7 @@ int dg_wall_shear(dg_ctx* c, const double* U, double* loss);
  * the transposed 2N-storage recurrence with dg_vjp per stage.  Returns L
  * (host double), gU0 = dL/dU0 (device array) and gtheta = dL/d(kappa, B)
  * (device double[2] or NULL).  The context's state is not touched.
- * FP64 contexts with the Pirozzoli flux and wall-modelled walls. */
+ * FP64 contexts with wall-modelled walls and the options dg_vjp accepts. */
 int dg_rollout_vjp(dg_ctx* c, const double* U0, int nsteps, double dt, double* loss, double* gU0,
                    double* gtheta);
 

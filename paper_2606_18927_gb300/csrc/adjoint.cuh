@@ -105,7 +105,9 @@ static __device__ void wall_stress_jvp(const PhysDev& ph, const DualD Us[5], dou
   const DualD rhow = rho * T / Tw;
   const DualD a = sqrt(r / (2.0 * ph.cp * Tw));
   const DualD uvd = asin(a * um) / a;
-  const DualD nuw = ph.mu / rhow;
+  // wall viscosity: constant, or Sutherland's law at the wall temperature
+  const DualD muw = ph.sutherland ? ph.suth_C * Tw * sqrt(Tw) / (Tw + ph.suth_S) : DualD(ph.mu);
+  const DualD nuw = muw / rhow;
   const double ut = solve_utau(ph.law, uvd.v, ph.hwm, nuw.v, ph.kappa, ph.B, ph.wm_maxit, ok);
   // explicit variable of the law at the solution
   const double wv = ph.law == 1 ? ut * ph.hwm / nuw.v : uvd.v / ut;
@@ -157,7 +159,8 @@ __device__ __forceinline__ void vt_vjp(const double U[5], const PhysDev& ph, con
 
 // ---------------------------------------------------------------------------
 // Reverse mode of the inviscid interface flux F*(U_A, U_B; n) (two-point
-// Pirozzoli flux plus the central / Lax-Friedrichs / Roe-Harten dissipation,
+// Pirozzoli or entropy-conserving two-point flux plus the central / Lax-Friedrichs /
+// Roe-Harten dissipation,
 // as riemann<double> forms it): gUA += (dF*/dU_A)^T gF, gUB += (dF*/dU_B)^T gF.
 // One forward sweep keeps the intermediates, one backward sweep applies the
 // chain rule to them in reverse order (about three flux evaluations, against
@@ -166,13 +169,85 @@ __device__ __forceinline__ void vt_vjp(const double U[5], const PhysDev& ph, con
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double sgn1(double x) { return x < 0.0 ? -1.0 : 1.0; }
 
+// Logarithmic mean L(a, b) = (a - b) / ln(a / b) and its partial derivatives:
+// dL/da = (1 - L / a) / ln(a / b), dL/db = (L / b - 1) / ln(a / b); for nearby
+// values (u = ((a - b) / (a + b))^2 below the forward kernels' cut) from the
+// series L = (s / 2) g(u) with g' = -1/3 - 8u/45 - 132u^2/945 and
+// du/da = 4 (a - b) b / s^3, du/db = -4 (a - b) a / s^3.
+__device__ __forceinline__ void logmean_d(double a, double b, double* L, double* La, double* Lb) {
+  const double s = a + b, d = a - b, f = d / s, u = f * f;
+  if (u < LogMeanCut<double>::v) {
+    const double g = logmean_g<double>(u);
+    const double gp = -(1.0 / 3.0 + u * (8.0 / 45.0 + u * (132.0 / 945.0)));
+    const double c = 2.0 * d * gp / (s * s);
+    *L = 0.5 * s * g;
+    *La = 0.5 * g + c * b;
+    *Lb = 0.5 * g - c * a;
+  } else {
+    const double l = log1p(d / b);
+    *L = d / l;
+    *La = (1.0 - *L / a) / l;
+    *Lb = (*L / b - 1.0) / l;
+  }
+}
+
+// Reverse mode of Chandrashekar's entropy-conserving two-point flux along a
+// (twopoint_ec): gA, gB += (dF/dq_A)^T mu, (dF/dq_B)^T mu for the primitives
+// q = (rho, u, v, w, p - p_ref) of the two nodes.  With beta = rho / (2 p),
+//   f0 = L(rho) ua, ua = {u}.a, p~' = (bA p'A + bB p'B) / (bA + bB),
+//   F = (f0, f0 {u} + p~' a, f0 X + (p~' + p_ref) ua),
+//   X = 1 / (2 (gamma - 1) L(beta)) + |{u}|^2 - ({|u|^2}) / 2.
+__device__ __forceinline__ void ec_flux_vjp(const PhysDev& ph, const Prim<double>& A, const Prim<double>& B,
+                                            double a0, double a1, double a2, const double mu[5], double gA[5],
+                                            double gB[5]) {
+  const double pref = ph.p_ref;
+  const double PA = A.p + pref, PB = B.p + pref;
+  const double bA = 0.5 * A.rho / PA, bB = 0.5 * B.rho / PB;
+  double Lr, Lra, Lrb, Lb, Lba, Lbb;
+  logmean_d(A.rho, B.rho, &Lr, &Lra, &Lrb);
+  logmean_d(bA, bB, &Lb, &Lba, &Lbb);
+  const double Mb = 1.0 / Lb, rb = 1.0 / (bA + bB);
+  const double u = 0.5 * (A.u + B.u), v = 0.5 * (A.v + B.v), w = 0.5 * (A.w + B.w);
+  const double ua = u * a0 + v * a1 + w * a2;
+  const double pt = (bA * A.p + bB * B.p) * rb;
+  const double f0 = Lr * ua;
+  const double k2 = 0.25 * (A.u * A.u + A.v * A.v + A.w * A.w + B.u * B.u + B.v * B.v + B.w * B.w);
+  const double X = 0.5 * Mb * ph.rgm1 + (u * u + v * v + w * w) - k2;
+  // backward sweep
+  const double gf0 = mu[0] + mu[1] * u + mu[2] * v + mu[3] * w + mu[4] * X;
+  const double gpt = mu[1] * a0 + mu[2] * a1 + mu[3] * a2 + mu[4] * ua;
+  const double gua = gf0 * Lr + mu[4] * (pt + pref);
+  const double gLr = gf0 * ua;
+  const double gX = mu[4] * f0;
+  const double gu = mu[1] * f0 + 2.0 * u * gX + a0 * gua;
+  const double gv = mu[2] * f0 + 2.0 * v * gX + a1 * gua;
+  const double gw = mu[3] * f0 + 2.0 * w * gX + a2 * gua;
+  const double gLb = -Mb * Mb * (0.5 * ph.rgm1 * gX);
+  double gbA = gpt * rb * (A.p - pt) + gLb * Lba;
+  double gbB = gpt * rb * (B.p - pt) + gLb * Lbb;
+  double gpA = gpt * rb * bA, gpB = gpt * rb * bB;
+  // beta = rho / (2 P): d/drho = 1 / (2 P), d/dP = -beta / P
+  gA[0] += gLr * Lra + gbA * 0.5 / PA;
+  gB[0] += gLr * Lrb + gbB * 0.5 / PB;
+  gpA -= gbA * bA / PA;
+  gpB -= gbB * bB / PB;
+  // velocities: {u} and the kinetic-energy term k2
+  gA[1] += 0.5 * gu - 0.5 * gX * A.u; gB[1] += 0.5 * gu - 0.5 * gX * B.u;
+  gA[2] += 0.5 * gv - 0.5 * gX * A.v; gB[2] += 0.5 * gv - 0.5 * gX * B.v;
+  gA[3] += 0.5 * gw - 0.5 * gX * A.w; gB[3] += 0.5 * gw - 0.5 * gX * B.w;
+  gA[4] += gpA; gB[4] += gpB;
+}
+
 static __device__ void face_flux_vjp(const PhysDev& ph, const double UA[5], const double UB[5], double nx,
                                      double ny, double nz, const double gF[5], double gUA[5], double gUB[5]) {
   const Prim<double> A = primitive<double>(UA[0], UA[1], UA[2], UA[3], UA[4], ph);
   const Prim<double> B = primitive<double>(UB[0], UB[1], UB[2], UB[3], UB[4], ph);
   // cotangents of the primitives (rho, u, v, w, p - p_ref, h) of each side
   double qA[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, qB[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-  {
+  if (ph.vol_flux == 2) {
+    // the entropy-conserving flux as the central part (Sec. 4's scheme)
+    ec_flux_vjp(ph, A, B, nx, ny, nz, gF, qA, qB);
+  } else {
     // two-point flux: m = {rho} ({u}.n); F = (m, m {u} + {p} n, m {h})
     const double rho = 0.5 * (A.rho + B.rho), u = 0.5 * (A.u + B.u), v = 0.5 * (A.v + B.v), w = 0.5 * (A.w + B.w);
     const double hb = 0.5 * (A.h + B.h);
@@ -466,7 +541,11 @@ struct AdjShape {
   static constexpr int SMEM_D = 36 * n3 + 24 * n2 + 3 * n2 + n;
 };
 
-template <int N>
+// EC: the entropy-conserving volume flux; SUTH: Sutherland's law (own
+// instantiations: the reverse mode of the entropy-conserving pair flux and
+// the temperature-dependent viscosity need registers that the Pirozzoli,
+// constant-viscosity kernel would otherwise spill)
+template <int N, bool EC, bool SUTH>
 __global__ void __launch_bounds__(AdjShape<N>::THREADS)
 k_adj_element(const double* __restrict__ U, const double* __restrict__ lam, const MeshDev<double> m,
               const PhysDev ph, const Tables<N> tab, const double* __restrict__ gGf, double* __restrict__ gU,
@@ -553,6 +632,39 @@ k_adj_element(const double* __restrict__ U, const double* __restrict__ lam, cons
       // the pair terms below carry constant factors (1/8 for rho, u, v, w,
       // 1/4 for p, 1/16 for h) that are applied once per node after the sums
       double g0 = 0, g1 = 0, g2 = 0, g3 = 0, g4 = 0, g5 = 0;
+      if constexpr (EC) {
+        // entropy-conserving flux: the two nodes of a pair get different
+        // cotangents (the logarithmic means are symmetric, their partial
+        // derivatives are not); the lane keeps its node's share and hands the
+        // partner's share (pos + d) over by a shuffle
+#pragma unroll 1
+        for (int d = 1; d <= n / 2; ++d) {
+          const int pm = pos + d < n ? pos + d : pos + d - n;
+          const int q = node(pm);
+          const Prim<double> Pa{sQ[me], sQ[n3 + me], sQ[2 * n3 + me], sQ[3 * n3 + me], sQ[4 * n3 + me], 0.0};
+          const Prim<double> Pb{sQ[q], sQ[n3 + q], sQ[2 * n3 + q], sQ[3 * n3 + q], sQ[4 * n3 + q], 0.0};
+          const double a0 = 0.5 * (sA[(dir * 3 + 0) * n3 + me] + sA[(dir * 3 + 0) * n3 + q]);
+          const double a1 = 0.5 * (sA[(dir * 3 + 1) * n3 + me] + sA[(dir * 3 + 1) * n3 + q]);
+          const double a2 = 0.5 * (sA[(dir * 3 + 2) * n3 + me] + sA[(dir * 3 + 2) * n3 + q]);
+          double mu[5];
+#pragma unroll
+          for (int v = 0; v < 5; ++v) mu[v] = sLt[v * n3 + me] - sLt[v * n3 + q];
+          double gA[5] = {0, 0, 0, 0, 0}, gB[5] = {0, 0, 0, 0, 0};
+          ec_flux_vjp(ph, Pa, Pb, a0, a1, a2, mu, gA, gB);
+          const double cw = sDVS[pos * n + pm];
+          g0 = fma(cw, gA[0], g0); g1 = fma(cw, gA[1], g1); g2 = fma(cw, gA[2], g2);
+          g3 = fma(cw, gA[3], g3); g4 = fma(cw, gA[4], g4);
+          if (2 * d != n) {
+            const int src = base + (pos - d >= 0 ? pos - d : pos - d + n);
+            const double cs = sDVS[(src - base) * n + pos];
+            g0 = fma(cs, __shfl_sync(0xffffffffu, gB[0], src), g0);
+            g1 = fma(cs, __shfl_sync(0xffffffffu, gB[1], src), g1);
+            g2 = fma(cs, __shfl_sync(0xffffffffu, gB[2], src), g2);
+            g3 = fma(cs, __shfl_sync(0xffffffffu, gB[3], src), g3);
+            g4 = fma(cs, __shfl_sync(0xffffffffu, gB[4], src), g4);
+          }
+        }
+      } else {
 #pragma unroll
       for (int d = 1; d <= n / 2; ++d) {
         const int pm = pos + d < n ? pos + d : pos + d - n;
@@ -597,6 +709,7 @@ k_adj_element(const double* __restrict__ U, const double* __restrict__ lam, cons
         }
       }
       g0 *= 0.125; g1 *= 0.125; g2 *= 0.125; g3 *= 0.125; g4 *= 0.25; g5 *= 0.0625;
+      }  // Pirozzoli
       if (active) {
         if (dir == 0) {
           sGQ[me] = g0; sGQ[n3 + me] = g1; sGQ[2 * n3 + me] = g2; sGQ[3 * n3 + me] = g3;
@@ -751,8 +864,16 @@ k_adj_element(const double* __restrict__ U, const double* __restrict__ lam, cons
       for (int d = 0; d < 3; ++d)
 #pragma unroll
         for (int v = 0; v < 4; ++v) gF[d][v] = ja[0 * 3 + d] * gG[0][v] + ja[1 * 3 + d] * gG[1][v] + ja[2 * 3 + d] * gG[2][v];
-      // viscous flux Fv_d = (tau_0d, tau_1d, tau_2d, tau_jd u_j + k q[d][T])
-      const double mu = ph.mu, kc = ph.kcond;
+      // viscous flux Fv_d = (tau_0d, tau_1d, tau_2d, tau_jd u_j + k q[d][T]);
+      // with Sutherland's law mu(T) and k = mu(T) cp / Pr (Sec. 4), whose
+      // derivatives dmu/dT = mu (3 / (2T) - 1 / (T + S)) give T a cotangent too
+      double mu = ph.mu, kc = ph.kcond, dmu = 0.0;
+      if constexpr (SUTH) {
+        const double Tn = sW[3 * n3 + p];
+        mu = sutherland<double>(ph, Tn);
+        dmu = mu * (1.5 / Tn - 1.0 / (Tn + ph.suth_S));
+        kc = mu * ph.cp_Pr;
+      }
       const double div = q[0][0] + q[1][1] + q[2][2];
       double tau[3][3];
 #pragma unroll
@@ -781,6 +902,18 @@ k_adj_element(const double* __restrict__ U, const double* __restrict__ lam, cons
         gdiv -= 2.0 / 3.0 * mu * gtau[aa][aa];
       }
       gq[0][0] += gdiv; gq[1][1] += gdiv; gq[2][2] += gdiv;
+      if constexpr (SUTH) {
+        // tau = mu(T) S(q), heat flux k(T) q_T: T's cotangent
+        double gT = 0.0;
+#pragma unroll
+        for (int aa = 0; aa < 3; ++aa)
+#pragma unroll
+          for (int bb = 0; bb < 3; ++bb) gT += gtau[aa][bb] * tau[aa][bb];
+        gT *= dmu / mu;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) gT += dmu * ph.cp_Pr * gF[d][3] * q[d][3];
+        gWo[3] += gT;
+      }
       // lifting transposed: q = (1/J)(sum_dir Ja^dir dW_dir + surface), so the
       // cotangent of the reference-space gradient is H^dir = (Ja^dir / J) . gq
 #pragma unroll

@@ -775,10 +775,9 @@ static dg::OpArgs adjoint_args(dg_ctx* c, const double* U, const double* lam, do
 static int check_adjoint_options(dg_ctx* c, const char* who) {
   if (c->opts.precision != DG_FP64)
     return fail(c, DG_ERR_NOT_IMPLEMENTED, std::string(who) + ": the adjoint is available for FP64 contexts");
-  if (c->opts.vol_flux != DG_VOL_KEP_PIROZZOLI)
-    return fail(c, DG_ERR_NOT_IMPLEMENTED, std::string(who) + ": the adjoint needs the Pirozzoli volume flux");
-  if (c->phys.suth_S > 0.0)
-    return fail(c, DG_ERR_NOT_IMPLEMENTED, std::string(who) + ": the adjoint needs a constant viscosity");
+  if (c->opts.vol_flux == DG_VOL_KEP_KENNEDY_GRUBER)
+    return fail(c, DG_ERR_NOT_IMPLEMENTED,
+                std::string(who) + ": the adjoint covers the Pirozzoli and entropy-conserving volume fluxes");
   if (c->geo.n_bc > 0 || c->geo.n_halo > 0)
     return fail(c, DG_ERR_NOT_IMPLEMENTED, std::string(who) + ": the adjoint covers periodic and wall faces only");
   if (c->phys.T_wall > 0.0)

@@ -160,7 +160,15 @@ static int run_vjp_typed(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {
   const Tables<N> tab = make_tables<N>(a.D, a.w);
   const double iw = tab.iw[0];
   const size_t smem = (size_t)AdjShape<N>::SMEM_D * sizeof(double);
-  cudaFuncSetAttribute(k_adj_element<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // the adjoint element kernel's instantiation: entropy-conserving flux,
+  // Sutherland's law
+  auto element = [&](auto kern) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return kern;
+  };
+  const bool ec = ph.vol_flux == 2, su = ph.sutherland != 0;
+  auto kel = ec ? (su ? element(k_adj_element<N, true, true>) : element(k_adj_element<N, true, false>))
+                : (su ? element(k_adj_element<N, false, true>) : element(k_adj_element<N, false, false>));
   if (a.n_interior > 0) {
     const long long work = (long long)a.n_interior * n2;
     k_adj_face<N><<<(unsigned)((work + 127) / 128), 128, 0, s>>>(a.Uin, a.lam, m, ph, iw, a.gUf, a.gGf);
@@ -170,7 +178,7 @@ static int run_vjp_typed(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {
     k_adj_wall<N><<<(unsigned)((work + WALL_THREADS - 1) / WALL_THREADS), WALL_THREADS, 0, s>>>(a.Uin, a.lam, m, ph, iw, a.gUf, a.gGf, a.gUs,
                                                                  a.gtheta, a.status);
   }
-  k_adj_element<N><<<a.K, AdjShape<N>::THREADS, smem, s>>>(a.Uin, a.lam, m, ph, tab, a.gGf, a.gU, a.gWf);
+  kel<<<a.K, AdjShape<N>::THREADS, smem, s>>>(a.Uin, a.lam, m, ph, tab, a.gGf, a.gU, a.gWf);
   const long long S = (long long)a.K * n3;
   k_adj_gather<N><<<(unsigned)((S + 255) / 256), 256, 0, s>>>(a.Uin, m, ph, a.gUf, a.gWf, a.gU);
   if (a.n_wall > 0 && ph.viscous) {

@@ -107,13 +107,80 @@ def test_ec_mixed_error(ora, label, spec, surf):
     assert max(e) <= 1e-4, e
 
 
-def test_adjoint_refuses_ec_and_sutherland(ora):
+def _vjp(torch, g, U, lam):
+    Ud = torch.from_numpy(U).cuda()
+    gU = torch.empty_like(Ud)
+    gth = torch.zeros(2, dtype=torch.float64, device="cuda")
+    g.vjp(torch.from_numpy(np.ascontiguousarray(lam)).cuda(), gU, Ud, gth)
+    torch.cuda.synchronize()
+    g.check_status()
+    return gU.cpu().numpy(), gth.cpu().numpy()
+
+
+@pytest.mark.parametrize("label,spec,surf,suth,ic", [
+    ("n3_sine_roe_suth", I.BoxSpec(3, 3, 2, 2, geometry="sine", amplitude=0.2), 2, True, "tgv_shift"),
+    ("n3_llf_const", I.BoxSpec(3, 2, 3, 2), 1, False, "tgv_shift"),
+    ("n7_sine_roe_suth", I.BoxSpec(7, 2, 2, 2, geometry="sine", amplitude=0.2), 2, True, "tgv_shift"),
+    ("n7_sine_roe_suth_sonic", I.BoxSpec(7, 2, 2, 2, geometry="sine", amplitude=0.2), 2, True, "tgv_sonic"),
+    ("n4_central_euler", I.BoxSpec(4, 2, 2, 3, geometry="sine", amplitude=0.2), 0, False, "tgv_shift"),
+])
+def test_production_scheme_adjoint_against_oracle_jvp(ora, label, spec, surf, suth, ic):
+    """The adjoint of the paper's Sec. 4 scheme (entropy-conserving volume
+    flux, Roe + Harten faces, Sutherland's law): dot-product test
+    <lam, J d> = <J^T lam, d> with J d the extended oracle's forward-mode
+    derivative (the reverse mode of the logarithmic means and of mu(T), k(T))."""
+    torch = torch_cuda()
+    phys = I.phys_params(Ma=0.3, Re=200.0, sutherland=suth)
+    visc = 0 if "euler" in label else 1
+    o, g, X, U = case(ora, spec, phys, surf_flux=surf, vol_flux=EC, viscous=visc, rel=1e-2, ic=ic)
+    lam = I.random_direction(U.shape, seed=3)
+    gU, _ = _vjp(torch, g, U, lam)
+    for seed in (4, 5):
+        d = I.random_direction(U.shape, seed=seed) * np.abs(U)
+        _, Jd = o.jvp(U, d)
+        a = float((lam * Jd).sum()); b = float((gU * d).sum())
+        print(label, "dot", a, b, abs(a - b) / abs(a))
+        assert abs(a - b) <= 1e-11 * np.abs(lam * Jd).sum()
+
+
+@pytest.mark.parametrize("law", [1, 0])
+def test_production_scheme_channel_adjoint(ora, law):
+    """Wall-modelled channel with the production scheme: state and (kappa, B)
+    cotangents against the oracle (the wall viscosity mu(T_w) by Sutherland's
+    law in the wall model's derivative), and central finite differences of the
+    GPU operator."""
+    torch = torch_cuda()
+    wl = I.workload("channel_n5", N=3, elems=(4, 4, 2))
+    phys = dict(wl.phys)
+    phys.update(T_ref=phys["p0"], suth_S=phys["p0"] * 110.4 / 288.15)
+    o, g, X, U = case(ora, wl.spec, phys, surf_flux=2, vol_flux=EC, law=law, ic="channel")
+    lam = I.random_direction(U.shape, seed=6)
+    gU, gth = _vjp(torch, g, U, lam)
+    d = I.random_direction(U.shape, seed=7) * np.abs(U)
+    _, Jd = o.jvp(U, d)
+    a = float((lam * Jd).sum()); b = float((gU * d).sum())
+    print("EC channel law", law, "dot", a, b)
+    assert abs(a - b) <= 1e-11 * np.abs(lam * Jd).sum()
+    for k, (dk, dB) in enumerate(((1.0, 0.0), (0.0, 1.0))):
+        _, Jt = o.jvp(U, None, dk, dB)
+        ref = float((lam * Jt).sum())
+        print("  dtheta", k, ref, gth[k])
+        assert abs(ref - gth[k]) <= 1e-10 * np.abs(lam * Jt).sum()
+    # central finite differences of the GPU operator along d
+    eps = 1e-6
+    Up = torch.from_numpy(U + eps * d).cuda(); Um = torch.from_numpy(U - eps * d).cuda()
+    fa = torch.empty_like(Up); fb = torch.empty_like(Up)
+    g.time_derivative(fa, Up); g.time_derivative(fb, Um)
+    fd = float((lam * (fa - fb).cpu().numpy()).sum()) / (2 * eps)
+    print("  FD", fd, "adjoint", b)
+    assert abs(fd - b) <= 1e-6 * abs(b)
+
+
+def test_adjoint_refuses_kennedy_gruber(ora):
     torch = torch_cuda()
     spec = I.BoxSpec(2, 2, 2, 2)
-    for vol, suth in ((EC, False), (0, True)):
-        phys = I.phys_params(sutherland=suth)
-        o, g, X, U = case(ora, spec, phys, surf_flux=2, vol_flux=vol)
-        Ud = torch.from_numpy(U).cuda()
-        with pytest.raises(dg.DGError) as ei:
-            g.vjp(torch.ones_like(Ud), torch.empty_like(Ud), U=Ud)
-        assert ei.value.code == -8
+    o, g, X, U = case(ora, spec, I.phys_params(), surf_flux=2, vol_flux=1)
+    Ud = torch.from_numpy(U).cuda()
+    with pytest.raises(dg.DGError) as ei:
+        g.vjp(torch.ones_like(Ud), torch.empty_like(Ud), U=Ud)
+    assert ei.value.code == -8
