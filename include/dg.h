@@ -237,8 +237,10 @@ int dg_rk_steps(dg_ctx* c, double t, double dt, int nsteps);
  * function theorem for the law-of-the-wall solve (Sec. 3.2).  FP64
  * contexts with the Pirozzoli or the entropy-conserving volume flux (the
  * paper's Sec. 4 scheme, with Roe + Harten faces), constant viscosity or
- * Sutherland's law, adiabatic walls and no inflow, outflow or halo faces
- * (else DG_ERR_NOT_IMPLEMENTED).
+ * Sutherland's law, adiabatic or isothermal walls (the wall heat flux's
+ * derivative with the stress's), inflow and outflow faces (through the
+ * exterior state's dependence on the interior one) and no halo faces (else
+ * DG_ERR_NOT_IMPLEMENTED).
  * The first call allocates the adjoint scratch of the context. */
 int dg_vjp(dg_ctx* c, const double* U, const double* lam, double* gU, double* gtheta);
 

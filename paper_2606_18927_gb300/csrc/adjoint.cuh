@@ -87,8 +87,9 @@ __device__ __forceinline__ void law_param_derivs(int law, double w, double kap, 
   }
 }
 
+// qw (may be null): the wall heat flux of isothermal walls (0 for adiabatic ones)
 static __device__ void wall_stress_jvp(const PhysDev& ph, const DualD Us[5], double dk, double dB, double nx,
-                                double ny, double nz, DualD tau[3], bool* ok) {
+                                double ny, double nz, DualD tau[3], bool* ok, DualD* qw = nullptr) {
   const DualD rho = Us[0], ir = 1.0 / rho;
   const DualD u = Us[1] * ir, v = Us[2] * ir, w = Us[3] * ir;
   const DualD p = ph.gm1 * (Us[4] - 0.5 * rho * (u * u + v * v + w * w));
@@ -97,14 +98,28 @@ static __device__ void wall_stress_jvp(const PhysDev& ph, const DualD Us[5], dou
   const DualD ux = u - un * nx, uy = v - un * ny, uz = w - un * nz;
   const DualD u2 = ux * ux + uy * uy + uz * uz;
   tau[0] = tau[1] = tau[2] = DualD(0.0);
+  if (qw) *qw = DualD(0.0);
   *ok = true;
   if (!(u2.v > 0.0)) return;
   const DualD um = sqrt(u2);
   const double r = cbrt(ph.Pr);
-  const DualD Tw = T + r * u2 / (2.0 * ph.cp);
+  const DualD Taw = T + r * u2 / (2.0 * ph.cp);
+  // the Van Driest transform: adiabatic (T_w = T_aw) or, at an isothermal
+  // wall, the closed form of the Crocco-Busemann integral (as wall_stress)
+  DualD Tw, uvd;
+  if (ph.T_wall > 0.0) {
+    Tw = DualD(ph.T_wall);
+    const DualD b = (Taw - Tw) / (Tw * um);
+    const DualD a2 = r / (2.0 * ph.cp * Tw);
+    const DualD aa = sqrt(a2);
+    const DualD q = sqrt(b * b + 4.0 * a2);
+    uvd = (asin((2.0 * a2 * um - b) / q) + asin(b / q)) / aa;
+  } else {
+    Tw = Taw;
+    const DualD a = sqrt(r / (2.0 * ph.cp * Tw));
+    uvd = asin(a * um) / a;
+  }
   const DualD rhow = rho * T / Tw;
-  const DualD a = sqrt(r / (2.0 * ph.cp * Tw));
-  const DualD uvd = asin(a * um) / a;
   // wall viscosity: constant, or Sutherland's law at the wall temperature
   const DualD muw = ph.sutherland ? ph.suth_C * Tw * sqrt(Tw) / (Tw + ph.suth_S) : DualD(ph.mu);
   const DualD nuw = muw / rhow;
@@ -121,6 +136,7 @@ static __device__ void wall_stress_jvp(const PhysDev& ph, const DualD Us[5], dou
   const DualD utD(ut, dut);
   const DualD tw = rhow * utD * utD / um;
   tau[0] = tw * ux; tau[1] = tw * uy; tau[2] = tw * uz;
+  if (qw && ph.T_wall > 0.0) *qw = -(ph.cp / ph.Pr) * (rhow * utD * utD) * (Taw - Tw) / um;
 }
 
 // ---------------------------------------------------------------------------
@@ -490,18 +506,19 @@ k_adj_wall(const double* __restrict__ U, const double* __restrict__ lam, const M
 #pragma unroll
           for (int v = 0; v < 5; ++v) Us[v] += ljk * row[v];
         }
-      const double gt0 = gFs[1] * s, gt1 = gFs[2] * s, gt2 = gFs[3] * s;
+      const double gt0 = gFs[1] * s, gt1 = gFs[2] * s, gt2 = gFs[3] * s, gt4 = -gFs[4] * s;
       bool ok = true;
 #pragma unroll 1
       for (int k = 0; k < 7; ++k) {
         DualD Ud[5];
 #pragma unroll
         for (int v = 0; v < 5; ++v) Ud[v] = DualD(Us[v], k == v ? 1.0 : 0.0);
-        DualD tau[3];
+        DualD tau[3], qwd;
         bool okk;
-        wall_stress_jvp(ph, Ud, k == 5 ? 1.0 : 0.0, k == 6 ? 1.0 : 0.0, nx, ny, nz, tau, &okk);
+        wall_stress_jvp(ph, Ud, k == 5 ? 1.0 : 0.0, k == 6 ? 1.0 : 0.0, nx, ny, nz, tau, &okk, &qwd);
         ok = ok && okk;
-        const double gdot = tau[0].d * gt0 + tau[1].d * gt1 + tau[2].d * gt2;
+        // (the wall flux: Fs_mom += tau s, Fs_E -= q_w s)
+        const double gdot = tau[0].d * gt0 + tau[1].d * gt1 + tau[2].d * gt2 + qwd.d * gt4;
         if (k < 5) gUs[slot * 5 + k] = gdot;
         else if (k == 5) gk = gdot;
         else gb = gdot;
@@ -524,6 +541,58 @@ k_adj_wall(const double* __restrict__ U, const double* __restrict__ lam, const M
       atomicAdd(&gtheta[1], gb);
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// k_adj_bc: one thread per node of an inflow or outflow face.  The forward
+// flux Fs = F*(U, U_B(U)) s - (0, Gf) with the exterior state U_B: the
+// prescribed inflow state (a constant), or at an outflow the interior
+// density and momentum with the energy of the prescribed pressure,
+// E_B = p_out / (gamma - 1) + |m|^2 / (2 rho).
+// ---------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(128)
+k_adj_bc(const double* __restrict__ U, const double* __restrict__ lam, const MeshDev<double> m, const PhysDev ph,
+         double iw, double* __restrict__ gUf, double* __restrict__ gGf) {
+  constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int bf = tid / n2, ab = tid - bf * n2;
+  if (bf >= m.n_bc) return;
+  const int f = m.n_interior + m.n_wall + bf;
+  int4 fc = m.faces[f];
+  fc.x = chk_idx(fc.x, m.K, m.status);
+  const size_t S = (size_t)m.K * n3;
+  const size_t gM = (size_t)fc.x * n3 + fnode<N>(fc.y, ab % n, ab / n);
+  const double jM = m.invJ[gM];
+  double gFs[5], UA[5], UB[5];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) {
+    gFs[v] = -lam[v * S + gM] * jM * iw;
+    UA[v] = U[v * S + gM];
+  }
+  ghost_state(ph, fc.z, UA, UB);
+  const size_t FN = (size_t)m.F * n2, fg = (size_t)f * n2 + ab;
+  const double nx = m.fgeo[fg], ny = m.fgeo[FN + fg], nz = m.fgeo[2 * FN + fg], s = m.fgeo[3 * FN + fg];
+  if (ph.viscous) {
+    double* dM = gGf + ((size_t)fc.x * 6 + fc.y) * 4 * n2 + ab;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) dM[v * n2] = -gFs[v + 1];
+  }
+  double gF[5], g[5] = {0.0, 0.0, 0.0, 0.0, 0.0}, gB[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+  for (int v = 0; v < 5; ++v) gF[v] = gFs[v] * s;
+  face_flux_vjp(ph, UA, UB, nx, ny, nz, gF, g, gB);
+  if (fc.z == -3) {
+    // dE_B/drho = -|m|^2 / (2 rho^2), dE_B/dm = m / rho
+    const double ir = 1.0 / UA[0];
+    const double m2 = UA[1] * UA[1] + UA[2] * UA[2] + UA[3] * UA[3];
+    g[0] += gB[0] - 0.5 * m2 * ir * ir * gB[4];
+#pragma unroll
+    for (int v = 1; v < 4; ++v) g[v] += gB[v] + UA[v] * ir * gB[4];
+  }
+  double* oM = gUf + ((size_t)fc.x * 6 + fc.y) * 5 * n2 + ab;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) oM[v * n2] = g[v];
 }
 
 // ---------------------------------------------------------------------------
@@ -738,6 +807,7 @@ k_adj_element(const double* __restrict__ U, const double* __restrict__ lam, cons
   const int p = i + n * (j + n * k);
   double* sX = sQ;  // [3][4][n3] even/odd half sums (the Q slots, free after the pair phase)
   double gWo[4] = {0, 0, 0, 0};
+  double gText = 0.0;  // cotangent of the outflow exterior temperature p_out / (rho R)
   if (ph.viscous) {
     // W* - W at the faces (as in the forward lifting)
     for (int x = t; x < 6 * n2; x += T) {
@@ -753,6 +823,17 @@ k_adj_element(const double* __restrict__ U, const double* __restrict__ lam, cons
                                      wn, Tn);
         d[0] = 0.5 * (un - sW[q]); d[1] = 0.5 * (vn - sW[n3 + q]); d[2] = 0.5 * (wn - sW[2 * n3 + q]);
         d[3] = 0.5 * (Tn - sW[3 * n3 + q]);
+      } else if (nb == -2 || nb == -3) {
+        // inflow / outflow: W* - W = (W(exterior) - W) / 2
+        const size_t gq = (size_t)e * n3 + q;
+        double Ui[5], Ub[5];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) Ui[v] = U[v * S + gq];
+        ghost_state(ph, nb, Ui, Ub);
+        double ub, vb, wb, Tb;
+        velocity_temperature<double>(Ub[0], Ub[1], Ub[2], Ub[3], Ub[4], ph, ub, vb, wb, Tb);
+        d[0] = 0.5 * (ub - sW[q]); d[1] = 0.5 * (vb - sW[n3 + q]); d[2] = 0.5 * (wb - sW[2 * n3 + q]);
+        d[3] = 0.5 * (Tb - sW[3 * n3 + q]);
       } else {
         const int dir = l >> 1;
         const double a0 = sA[(dir * 3 + 0) * n3 + q], a1 = sA[(dir * 3 + 1) * n3 + q], a2 = sA[(dir * 3 + 2) * n3 + q];
@@ -937,6 +1018,15 @@ k_adj_element(const double* __restrict__ U, const double* __restrict__ lam, cons
           double* dst = gWf + ((size_t)e * 6 + l) * 4 * n2 + ab;
 #pragma unroll
           for (int v = 0; v < 4; ++v) dst[v * n2] = 0.5 * tv[v];
+        } else if (nb == -2) {
+          // inflow: the exterior state is the prescribed one
+#pragma unroll
+          for (int v = 0; v < 4; ++v) gWo[v] -= 0.5 * tv[v];
+        } else if (nb == -3) {
+          // outflow: the exterior velocity is the interior one (W* - W = 0),
+          // the exterior temperature p_out / (rho R)
+          gWo[3] -= 0.5 * tv[3];
+          gText += 0.5 * tv[3];
         } else {
           // W* - W = -(u . n) n (mirror), T unchanged
           const double a0 = ja[dir * 3 + 0], a1 = ja[dir * 3 + 1], a2 = ja[dir * 3 + 2];
@@ -996,6 +1086,7 @@ k_adj_element(const double* __restrict__ U, const double* __restrict__ lam, cons
   double out[5] = {0, 0, 0, 0, 0};
   prim_vjp(Uo, ph, gQ, out);
   if (ph.viscous) vt_vjp(Uo, ph, gWo, out);
+  if (gText != 0.0) out[0] -= gText * ph.p_out * ph.rcp_R / (Uo[0] * Uo[0]);
   if (ph.f[0] != 0.0 || ph.f[1] != 0.0 || ph.f[2] != 0.0) {
     // S_E = f . m / rho
     const double l4 = lam[4 * S + g], ir = 1.0 / Uo[0];

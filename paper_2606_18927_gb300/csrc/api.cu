@@ -778,10 +778,8 @@ static int check_adjoint_options(dg_ctx* c, const char* who) {
   if (c->opts.vol_flux == DG_VOL_KEP_KENNEDY_GRUBER)
     return fail(c, DG_ERR_NOT_IMPLEMENTED,
                 std::string(who) + ": the adjoint covers the Pirozzoli and entropy-conserving volume fluxes");
-  if (c->geo.n_bc > 0 || c->geo.n_halo > 0)
-    return fail(c, DG_ERR_NOT_IMPLEMENTED, std::string(who) + ": the adjoint covers periodic and wall faces only");
-  if (c->phys.T_wall > 0.0)
-    return fail(c, DG_ERR_NOT_IMPLEMENTED, std::string(who) + ": the adjoint covers adiabatic walls only");
+  if (c->geo.n_halo > 0)
+    return fail(c, DG_ERR_NOT_IMPLEMENTED, std::string(who) + ": the adjoint covers single-partition meshes");
   return DG_OK;
 }
 
@@ -843,7 +841,6 @@ int dg_kinetic_energy(dg_ctx* c, const double* U, double* ke) {
 int dg_wall_shear(dg_ctx* c, const double* U, double* loss) {
   if (!c || !loss) return c ? fail(c, DG_ERR_ARG, "dg_wall_shear: null loss") : DG_ERR_ARG;
   if (c->geo.n_wall == 0 || !c->opts.viscous) return fail(c, DG_ERR_ARG, "dg_wall_shear: no wall-modelled walls");
-  if (c->phys.T_wall > 0.0) return fail(c, DG_ERR_NOT_IMPLEMENTED, "dg_wall_shear: adiabatic walls only");
   const double* Uin = U ? U : c->U;
   if (!U && !c->state_set) return fail(c, DG_ERR_NOT_INIT, "dg_wall_shear: state not set");
   int rc = ensure_scalar(c);

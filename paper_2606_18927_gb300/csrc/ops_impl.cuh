@@ -178,6 +178,10 @@ static int run_vjp_typed(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {
     k_adj_wall<N><<<(unsigned)((work + WALL_THREADS - 1) / WALL_THREADS), WALL_THREADS, 0, s>>>(a.Uin, a.lam, m, ph, iw, a.gUf, a.gGf, a.gUs,
                                                                  a.gtheta, a.status);
   }
+  if (a.n_bc > 0) {
+    const long long work = (long long)a.n_bc * n2;
+    k_adj_bc<N><<<(unsigned)((work + 127) / 128), 128, 0, s>>>(a.Uin, a.lam, m, ph, iw, a.gUf, a.gGf);
+  }
   kel<<<a.K, AdjShape<N>::THREADS, smem, s>>>(a.Uin, a.lam, m, ph, tab, a.gGf, a.gU, a.gWf);
   const long long S = (long long)a.K * n3;
   k_adj_gather<N><<<(unsigned)((S + 255) / 256), 256, 0, s>>>(a.Uin, m, ph, a.gUf, a.gWf, a.gU);

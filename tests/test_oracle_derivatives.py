@@ -89,3 +89,37 @@ def test_lserk4_temporal_order(ora):
     e = [np.abs(sols[i] - sols[i + 1]).max() for i in range(3)]
     rates = [math.log2(e[i] / e[i + 1]) for i in range(2)]
     assert rates[-1] > 3.7, (e, rates)
+
+
+def test_jvp_inflow_outflow_and_isothermal(ora):
+    """The forward-mode derivative through the inflow and outflow exterior
+    states and through an isothermal wall's heat flux (the GPU adjoint's
+    source at those faces) against central differences."""
+    phys = I.phys_params(Ma=0.3, Re=400.0)
+    g, p0 = phys["gamma"], phys["p0"]
+    rho, u, v = 1.02, 0.75, 0.05
+    phys.update(U_in=np.array([rho, rho * u, rho * v, 0.0, 1.03 * p0 / (g - 1) + 0.5 * rho * (u * u + v * v)]),
+                p_out=0.98 * p0)
+    spec = I.BoxSpec(3, 3, 2, 2, geometry="sine", amplitude=0.2, periodic=(False, True, True),
+                     boundary=((I.INFLOW, I.OUTFLOW), (I.WALL, I.WALL), (I.WALL, I.WALL)))
+    o, X, nbr = oracle_case(ora, spec, phys, vol_flux=2, surf_flux=2)
+    U = I.perturb(I.taylor_green(X, phys), rel=1e-2)
+    U[1] += 0.6 * U[0]
+    d = I.random_direction(U.shape, seed=11) * np.abs(U)
+    Ut, Jd = o.jvp(U, d)
+    h = 1e-6
+    fd = (o.time_derivative(U + h * d) - o.time_derivative(U - h * d)) / (2 * h)
+    assert np.abs(fd - Jd).max() <= 1e-6 * np.abs(Jd).max()
+    wl = I.workload("channel_n5", N=3, elems=(4, 4, 2))
+    phys = dict(wl.phys, T_wall=1.15 * wl.phys["p0"] / wl.phys["R"])
+    o, X, nbr = oracle_case(ora, wl.spec, phys, surf_flux=2)
+    U = I.initial_state(wl, X)
+    d = I.random_direction(U.shape, seed=12) * np.abs(U)
+    Ut, Jd = o.jvp(U, d)
+    fd = (o.time_derivative(U + h * d) - o.time_derivative(U - h * d)) / (2 * h)
+    assert np.abs(fd - Jd).max() <= 1e-6 * np.abs(Jd).max()
+    _, Jk = o.jvp(U, None, 1.0, 0.0)
+    op, _, _ = oracle_case(ora, wl.spec, dict(phys, kappa=phys["kappa"] + h), surf_flux=2)
+    om, _, _ = oracle_case(ora, wl.spec, dict(phys, kappa=phys["kappa"] - h), surf_flux=2)
+    fd = (op.time_derivative(U) - om.time_derivative(U)) / (2 * h)
+    assert np.abs(fd - Jk).max() <= 1e-6 * np.abs(Jk).max()
