@@ -256,6 +256,23 @@ int dg_set_params(dg_ctx* c, double kappa, double B);
  * max_iter >= 1, else DG_ERR_ARG.  Used by later calls. */
 int dg_set_wall_solve_limit(dg_ctx* c, int max_iter);
 
+/* Independent states from host memory through the LSERK4 stages, with the
+ * host transfers overlapped with the computation (a serving-style batch):
+ * for every item i < nitems, U_in[i] (host double[5][K][n^3]) is copied to
+ * the device, stages 0 .. nstages-1 of one step of size dt run on it with
+ * the item's own register dU (zero at the start, as at a step's start), and
+ * the result is copied to U_out[i] (host).  Two device slots: the copy of
+ * item i+1 in and of item i-1 out run on their own streams while item i
+ * computes on the context's stream (2 x 2 x 5 K n^3 doubles, allocated at the
+ * first call).  Results equal those of dg_set_state, the stages and
+ * dg_get_state bitwise.  The context's own state and register are not
+ * touched; wall-law solves start afresh for every item.  Host buffers should
+ * be page-locked for the copies to overlap; U_out[i] must not alias a later
+ * item's input.  Synchronises the stream.  1 <= nstages <= 5; unpartitioned
+ * contexts only (else DG_ERR_ARG). */
+int dg_rk_stage_batch(dg_ctx* c, int nitems, const double* const* U_in, double* const* U_out, int nstages,
+                      double t, double dt);
+
 /* Explicit time step dt = cfl * 2/(2N+1) * min_nodes J / sum_dir(|u . Ja^dir|
  * + c |Ja^dir|) (CFL-based step of the explicit LSERK4, paper Sec. 4 uses
  * CFL 0.9).  U: device array or NULL for the state; dt: host double.
@@ -272,6 +289,18 @@ int dg_kinetic_energy(dg_ctx* c, const double* U, double* ke);
  * array or NULL for the state; loss: host double.  Synchronises the stream.
  * DG_ERR_ARG without wall-modelled walls. */
 int dg_wall_shear(dg_ctx* c, const double* U, double* loss);
+
+/* The FP64 <-> FP32 conversions of the FP32-mixed kernels, built from the
+ * bit patterns with integer operations (the conversion instructions issue to
+ * GB300's FP64 pipe), for testing them: for i < n (device arrays)
+ *   f[i]   = d[i] rounded to the nearest float, ties to even (signed zero
+ *            below the FP32 normal range, infinity above it, NaN kept),
+ *   rem[i] = d[i] - f[i] as a float, to 2^-46 |d[i]| (zero where that
+ *            scale is below the FP32 normal range, and for non-finite d[i]),
+ *   gd[i]  = g[i] widened exactly (FP32 subnormals give signed zero).
+ * Runs on the current device and synchronises it.  DG_ERR_ARG for n < 0 or
+ * null arrays, DG_ERR_CUDA on a launch failure. */
+int dg_convert_fp32(long long n, const double* d, float* f, float* rem, const float* g, double* gd);
 
 /* Rollout adjoint: runs nsteps LSERK4 steps of size dt from U0 (device),
  * keeping one checkpoint of U per step (A_0 = 0, so U alone restarts a

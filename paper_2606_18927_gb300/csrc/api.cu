@@ -98,6 +98,12 @@ struct dg_ctx {
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t step_graph = nullptr;
   double step_graph_dt = 0.0;
+  // host batches (dg_rk_stage_batch): two device slots (state, register),
+  // copy-in and copy-out streams and their events
+  double* bU[2] = {nullptr, nullptr};
+  double* bdU[2] = {nullptr, nullptr};
+  cudaStream_t cp_in = nullptr, cp_out = nullptr;
+  cudaEvent_t ev_loaded[2] = {nullptr, nullptr}, ev_done[2] = {nullptr, nullptr}, ev_freed[2] = {nullptr, nullptr};
   // optional per-kernel timing: 5 events per operator evaluation
   bool profiling = false;
   std::vector<cudaEvent_t> events;
@@ -136,6 +142,18 @@ void free_all(dg_ctx* c) {
   if (c->side) cudaStreamDestroy(c->side);
   c->fork_ev = c->join_ev = nullptr;
   c->side = nullptr;
+  for (int k = 0; k < 2; ++k) {
+    for (cudaEvent_t* ev : {&c->ev_loaded[k], &c->ev_done[k], &c->ev_freed[k]}) {
+      if (*ev) cudaEventDestroy(*ev);
+      *ev = nullptr;
+    }
+    if (c->bU[k]) cudaFree(c->bU[k]);
+    if (c->bdU[k]) cudaFree(c->bdU[k]);
+    c->bU[k] = c->bdU[k] = nullptr;
+  }
+  if (c->cp_in) cudaStreamDestroy(c->cp_in);
+  if (c->cp_out) cudaStreamDestroy(c->cp_out);
+  c->cp_in = c->cp_out = nullptr;
   void* ptrs[] = {c->U, c->dU, c->io, c->io2, c->Ja, c->invJ, c->fgeo, c->nbr, c->elem_face, c->faces,
                   c->ws_elem, c->ws_lag, c->Rv, c->Gf, c->Fs, c->tau, c->status,
                   c->gUf, c->gGf, c->gWf, c->gUs, c->gtheta, c->wq, c->ro_ckpt, c->ro_stage, c->ro_work,
@@ -270,6 +288,16 @@ __global__ void k_wave_speed(long long S, const double* __restrict__ U, const R*
   }
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
   if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(mx));
+}
+// the FP64 <-> FP32 conversions of the FP32-mixed kernels, for their tests
+__global__ void k_convert_fp32(long long n, const double* __restrict__ d, float* __restrict__ f,
+                               float* __restrict__ rem, const float* __restrict__ g, double* __restrict__ gd) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float r;
+  f[i] = d2f_bits(d[i], &r);
+  rem[i] = r;
+  gd[i] = f2d_bits(g[i]);
 }
 __global__ void k_axpby_api(long long n, double a, const double* __restrict__ x, double b, double* __restrict__ y) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -654,6 +682,66 @@ int dg_rk_stage(dg_ctx* c, int s, double t, double dt) {
   return launch(c, c->U, 1, nullptr, kRkA[s], kRkB[s], dt, s > 0 ? 1 : 0, c->U);
 }
 
+// Independent host states through the stages, two device slots deep: the
+// copy of item i + 1 in and of item i - 1 out run on their own streams (the
+// two copy engines) while item i computes on the context's stream.
+int dg_rk_stage_batch(dg_ctx* c, int nitems, const double* const* U_in, double* const* U_out, int nstages,
+                      double t, double dt) {
+  (void)t;  // the operator is autonomous (constant body force)
+  if (!c) return DG_ERR_ARG;
+  if (nitems < 0 || nstages < 1 || nstages > 5 || (nitems > 0 && (!U_in || !U_out)))
+    return fail(c, DG_ERR_ARG, "dg_rk_stage_batch: bad item count, stage count or arrays");
+  for (int i = 0; i < nitems; ++i)
+    if (!U_in[i] || !U_out[i]) return fail(c, DG_ERR_ARG, "dg_rk_stage_batch: null item buffer");
+  if (c->geo.n_halo > 0)
+    return fail(c, DG_ERR_ARG, "dg_rk_stage_batch: a partitioned context evaluates in phases");
+  if (nitems == 0) return DG_OK;
+  const size_t n5 = 5 * c->S, bytes = n5 * sizeof(double);
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+  if (!c->cp_in) {
+    for (int k = 0; k < 2; ++k) {
+      chk(alloc(&c->bU[k], n5));
+      chk(alloc(&c->bdU[k], n5));
+      chk(cudaEventCreateWithFlags(&c->ev_loaded[k], cudaEventDisableTiming));
+      chk(cudaEventCreateWithFlags(&c->ev_done[k], cudaEventDisableTiming));
+      chk(cudaEventCreateWithFlags(&c->ev_freed[k], cudaEventDisableTiming));
+    }
+    chk(cudaStreamCreateWithFlags(&c->cp_in, cudaStreamNonBlocking));
+    chk(cudaStreamCreateWithFlags(&c->cp_out, cudaStreamNonBlocking));
+    if (e != cudaSuccess) return cuda_fail(c, e, "dg_rk_stage_batch: slots");
+  }
+  // the slots start after the work already queued on the context's stream
+  chk(cudaEventRecord(c->ev_done[0], c->stream));
+  chk(cudaStreamWaitEvent(c->cp_in, c->ev_done[0], 0));
+  int rc = DG_OK;
+  for (int i = 0; i < nitems && e == cudaSuccess && rc == DG_OK; ++i) {
+    const int k = i & 1;
+    // slot k is free once the result of item i - 2 has left it
+    if (i >= 2) chk(cudaStreamWaitEvent(c->cp_in, c->ev_freed[k], 0));
+    chk(cudaMemcpyAsync(c->bU[k], U_in[i], bytes, cudaMemcpyHostToDevice, c->cp_in));
+    chk(cudaEventRecord(c->ev_loaded[k], c->cp_in));
+    chk(cudaStreamWaitEvent(c->stream, c->ev_loaded[k], 0));
+    // each item starts the wall-law solves afresh, as after dg_set_state
+    if (c->wm_t) chk(cudaMemsetAsync(c->wm_t, 0xff, (size_t)c->geo.n_wall * c->n2 * sizeof(double), c->stream));
+    for (int st = 0; st < nstages && e == cudaSuccess && rc == DG_OK; ++st)
+      rc = launch(c, c->bU[k], 1, nullptr, kRkA[st], kRkB[st], dt, st > 0 ? 1 : 0, c->bU[k], c->bdU[k]);
+    chk(cudaEventRecord(c->ev_done[k], c->stream));
+    chk(cudaStreamWaitEvent(c->cp_out, c->ev_done[k], 0));
+    chk(cudaMemcpyAsync(U_out[i], c->bU[k], bytes, cudaMemcpyDeviceToHost, c->cp_out));
+    chk(cudaEventRecord(c->ev_freed[k], c->cp_out));
+  }
+  // the context's own stream continues after the last result is out
+  chk(cudaEventRecord(c->ev_freed[0], c->cp_out));
+  chk(cudaStreamWaitEvent(c->stream, c->ev_freed[0], 0));
+  const cudaError_t es = cudaStreamSynchronize(c->cp_out);
+  const cudaError_t ec = cudaStreamSynchronize(c->stream);
+  if (rc != DG_OK) return rc;
+  if (e == cudaSuccess) e = es != cudaSuccess ? es : ec;
+  if (e != cudaSuccess) return cuda_fail(c, e, "dg_rk_stage_batch");
+  return DG_OK;
+}
+
 int dg_rk_steps(dg_ctx* c, double t, double dt, int nsteps) {
   if (!c || nsteps < 0) return c ? fail(c, DG_ERR_ARG, "dg_rk_steps: nsteps < 0") : DG_ERR_ARG;
   for (int it = 0; it < nsteps; ++it)
@@ -836,6 +924,15 @@ int dg_kinetic_energy(dg_ctx* c, const double* U, double* ke) {
   if (e != cudaSuccess) return cuda_fail(c, e, "dg_kinetic_energy");
   *ke = sum / c->vol;
   return DG_OK;
+}
+
+int dg_convert_fp32(long long n, const double* d, float* f, float* rem, const float* g, double* gd) {
+  if (n < 0 || (n > 0 && (!d || !f || !rem || !g || !gd))) return DG_ERR_ARG;
+  if (n == 0) return DG_OK;
+  dg::k_convert_fp32<<<(unsigned)((n + 255) / 256), 256>>>(n, d, f, rem, g, gd);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  return e == cudaSuccess ? DG_OK : DG_ERR_CUDA;
 }
 
 int dg_wall_shear(dg_ctx* c, const double* U, double* loss) {

@@ -268,6 +268,52 @@ __device__ __forceinline__ bool finite_bits(double x) {
   return (hi & 0x7ff00000u) != 0x7ff00000u;
 }
 
+// Conversions between FP64 and FP32 built from the bit patterns with integer
+// operations.  On GB300 the conversion instructions issue to the FP64 pipe
+// (2 lanes per clock and SM, a 64th of the FP32 rate); the FP32-mixed
+// kernels convert some twenty values per node and stage.
+//
+// f2d_bits: the exact widening of a float (FP32 subnormals give signed zero;
+// infinities and NaN stay so).
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned x = __float_as_uint(f);
+  const unsigned e = (x >> 23) & 0xffu;
+  const unsigned s = x & 0x80000000u;
+  const unsigned ed = e == 0xffu ? 0x7ffu : e + 896u;  // 1023 - 127
+  const unsigned hi = e == 0u ? s : (s | (ed << 20) | ((x >> 3) & 0xfffffu));
+  const unsigned lo = e == 0u ? 0u : (x << 29);
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+// d2f_bits: rounding to the nearest float, ties to even, for results in the
+// FP32 normal range (smaller magnitudes give signed zero, larger ones
+// infinity; NaN stays NaN).  With rem, also the rounding remainder d - f as
+// a float, to 2^-46 |d| (the remainder's 29 bits are kept to 23; zero where
+// 2^-46 |d| falls below the FP32 normal range).
+__device__ __forceinline__ float d2f_bits(double d, float* rem = nullptr) {
+  const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+  const unsigned s = hi & 0x80000000u;
+  const int ed = (int)((hi >> 20) & 0x7ffu);
+  const int e = ed - 896;
+  const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);  // the 23 bits kept
+  const unsigned r = lo & 0x1fffffffu;                        // the 29 bits dropped
+  const unsigned up = (r > 0x10000000u || (r == 0x10000000u && (m & 1u))) ? 1u : 0u;
+  unsigned bits = ((unsigned)e << 23 | m) + up;  // a carry moves into the exponent
+  bits = e <= 0 ? 0u : bits;
+  bits = e >= 255 ? 0x7f800000u : bits;
+  bits = (ed == 0x7ff && ((hi & 0xfffffu) | lo)) ? 0x7fc00000u : bits;
+  if (rem) {
+    // d - f = (r - up 2^29) 2^(E - 52), E = ed - 1023; |r - up 2^29| <= 2^28,
+    // taken to 23 bits (>> 6) and converted exactly by the 1.5 2^23 shift
+    const int q = ((int)r - (int)(up << 29)) >> 6;
+    const float qf = __int_as_float(0x4B400000 + q) - 12582912.0f;
+    const int pe = ed - 1023 - 46 + 127;  // biased exponent of 2^(E - 46)
+    const float rm = (pe >= 1 && ed != 0x7ff) ? qf * __int_as_float(pe << 23) : 0.0f;
+    *rem = __uint_as_float(__float_as_uint(rm) ^ s);  // the sign of d
+  }
+  return __uint_as_float(s | bits);
+}
+
 // Primitive state in the flux type.  p is recovered in double from the
 // double state (p = (gamma-1)(E - rho |u|^2 / 2) cancels at low Mach number)
 // and stored as p - p_ref (the momentum fluxes see only the deviation from
@@ -326,8 +372,8 @@ __device__ __forceinline__ Prim<float> primitive<float>(const double U0, const d
 // of the Ut of the 48^3 curved box at Mach 0.3).  The low parts come from
 // the FP32 residual m - u rho, formed with FMAs:
 //   r = (m_hi - u rho_ref) - u rho' + m_lo,  lo = r / rho,
-// where m_lo = m - m_hi is the rounding of the conversion to FP32 (three FP64
-// operations per component).
+// where m_lo = m - m_hi is the rounding of the conversion to FP32 (the
+// remainder that d2f_bits returns from the dropped bits).
 struct Lo3 {
   float u, v, w;
 };
@@ -337,26 +383,26 @@ __device__ __forceinline__ Prim<float> prim32_shifted(const double U0, const dou
                                                       Lo3* lo = nullptr) {
   Prim<float> q;
   const double rd = U0 - ph.rho_ref;
-  q.rho = (float)rd;
+  q.rho = d2f_bits(rd);
   const float ir = 1.0f / (ph.f32c.rho_ref + q.rho);
-  const float m1 = (float)U1, m2 = (float)U2, m3 = (float)U3;
+  float ml1, ml2, ml3;  // the roundings m - (float)m
+  const float m1 = d2f_bits(U1, &ml1), m2 = d2f_bits(U2, &ml2), m3 = d2f_bits(U3, &ml3);
   q.u = m1 * ir; q.v = m2 * ir; q.w = m3 * ir;
   const float ke = 0.5f * (m1 * q.u + m2 * q.v + m3 * q.w);
-  const double pr = fma(ph.gm1, U4 - (double)ke, -ph.p_ref);  // p - p_ref
-  q.p = (float)pr;
+  const double pr = fma(ph.gm1, U4 - f2d_bits(ke), -ph.p_ref);  // p - p_ref
+  q.p = d2f_bits(pr);
   q.h = fmaf(ph.f32c.g_gm1, q.p + ph.f32c.h_p - ph.f32c.h_r * q.rho, ke) * ir;
   if (lo) {
     // (the rounding of rho - rho_ref, relative eps32 of a small deviation,
     // changes u by a relative 1e-10 or so: left out)
-    auto low = [&](double mf, float mh, float uh) {
-      const float ml = (float)(mf - (double)mh);
+    auto low = [&](float ml, float mh, float uh) {
       float r = fmaf(-uh, ph.f32c.rho_ref, mh);
       r = fmaf(-uh, q.rho, r);
       return (r + ml) * ir;
     };
-    lo->u = low(U1, m1, q.u);
-    lo->v = low(U2, m2, q.v);
-    lo->w = low(U3, m3, q.w);
+    lo->u = low(ml1, m1, q.u);
+    lo->v = low(ml2, m2, q.v);
+    lo->w = low(ml3, m3, q.w);
   }
   return q;
 }
@@ -1386,7 +1432,7 @@ k_face(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
     float dU[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     if (ph.surf_flux == 1) {
 #pragma unroll
-      for (int v = 0; v < 5; ++v) dU[v] = (float)(U[v * S + gS] - U[v * S + gM]);
+      for (int v = 0; v < 5; ++v) dU[v] = d2f_bits(U[v * S + gS] - U[v * S + gM]);
     }
     if (ph.fs_diff) {
       store_face_delta(ph, A, B, la, lb, dU, nx, ny, nz, s, gA, gB, R(0.5), Fs + (size_t)f * 10 * n2 + ab, n2, true);
@@ -1497,7 +1543,7 @@ k_halo_face(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, 
     if (ph.fs_diff) {
       float dU[5];
 #pragma unroll
-      for (int v = 0; v < 5; ++v) dU[v] = (float)(UB[v] - UA[v]);
+      for (int v = 0; v < 5; ++v) dU[v] = d2f_bits(UB[v] - UA[v]);
       const R* gl = Gf + ((size_t)eL * 6 + fc.y) * 4 * n2 + abl;
       const R* gr = m.halo_G + (size_t)h * 4 * n2 + ab;
       store_face_delta(ph, As, Bs, la, lb, dU, nx, ny, nz, s, master ? gl : gr, master ? gr : gl, 0.5f,
@@ -1582,7 +1628,7 @@ k_bc(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const R
     if (ph.fs_diff) {
       float dU[5];
 #pragma unroll
-      for (int v = 0; v < 5; ++v) dU[v] = (float)(UB[v] - UA[v]);
+      for (int v = 0; v < 5; ++v) dU[v] = d2f_bits(UB[v] - UA[v]);
       store_face_delta(ph, As, Bs, la, lb, dU, nx, ny, nz, s, Gf + ((size_t)fc.x * 6 + fc.y) * 4 * n2 + ab, nullptr,
                        1.f,
                        Fs + (size_t)f * 10 * n2 + ab, n2, false);
@@ -1641,7 +1687,7 @@ k_wall(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, R* __
     if (ph.fs_diff) {
       float dU[5], DB[5];
 #pragma unroll
-      for (int v = 0; v < 5; ++v) dU[v] = (float)(UB[v] - UA[v]);
+      for (int v = 0; v < 5; ++v) dU[v] = d2f_bits(UB[v] - UA[v]);
       face_flux_delta(ph, As, Bs, la, lb, dU, (R)nxd, (R)nyd, (R)nzd, F, DB);
       fss = 10;
     }
@@ -2146,7 +2192,9 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
     bool bad = false;
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
-      double d = F32 ? (double)(cf * acc[v]) : c * (double)acc[v];
+      double d;
+      if constexpr (F32) d = f2d_bits(cf * acc[v]);
+      else d = c * (double)acc[v];
       if (force) d = fma(st.dt, src[v], d);
       if (st.read_dU) d = fma(st.A, dU[v * S + g], d);
       const double un = fma(st.B, d, Uo[v]);

@@ -87,6 +87,8 @@ def lib():
         "dg_rk_stage": (c_int, [vp, c_int, c_double, c_double]),
         "dg_rk_steps": (c_int, [vp, c_double, c_double, c_int]),
         "dg_rk_steps_graph": (c_int, [vp, c_double, c_double, c_int]),
+        "dg_rk_stage_batch": (c_int, [vp, c_int, ctypes.POINTER(vp), ctypes.POINTER(vp), c_int, c_double,
+                                      c_double]),
         "dg_check_status": (c_int, [vp]),
         "dg_get_rk_register": (c_int, [vp, vp, c_int]),
         "dg_set_rk_register": (c_int, [vp, vp, c_int]),
@@ -98,6 +100,7 @@ def lib():
         "dg_wall_shear": (c_int, [vp, vp, dp]),
         "dg_kinetic_energy": (c_int, [vp, vp, dp]),
         "dg_time_step": (c_int, [vp, vp, c_double, dp]),
+        "dg_convert_fp32": (c_int, [ctypes.c_longlong, vp, vp, vp, vp, vp]),
         "dg_rollout_vjp": (c_int, [vp, vp, c_int, c_double, dp, vp, vp]),
         "dg_profile_enable": (c_int, [vp, c_int]),
         "dg_set_overlap": (c_int, [vp, c_int]),
@@ -133,6 +136,23 @@ def lgl_nodes(N):
     if rc != 0:
         raise DGError(rc, lib().dg_last_error(None).decode())
     return x, w
+
+
+def convert_fp32(d, g):
+    """The FP32-mixed kernels' conversions (dg_convert_fp32) on CUDA tensors:
+    d (float64) -> (f, rem) float32, g (float32) -> float64."""
+    assert d.is_cuda and d.dtype.is_floating_point and d.element_size() == 8 and d.is_contiguous()
+    assert g.is_cuda and g.element_size() == 4 and g.is_contiguous() and g.numel() == d.numel()
+    import torch
+    f = torch.empty(d.shape, dtype=torch.float32, device=d.device)
+    rem = torch.empty_like(f)
+    gd = torch.empty(d.shape, dtype=torch.float64, device=d.device)
+    rc = lib().dg_convert_fp32(d.numel(), ctypes.c_void_p(d.data_ptr()), ctypes.c_void_p(f.data_ptr()),
+                               ctypes.c_void_p(rem.data_ptr()), ctypes.c_void_p(g.data_ptr()),
+                               ctypes.c_void_p(gd.data_ptr()))
+    if rc != 0:
+        raise DGError(rc, "dg_convert_fp32 failed")
+    return f, rem, gd
 
 
 def _ptr(t):
@@ -359,6 +379,22 @@ class Operator:
     def rk_steps_graph(self, t, dt, nsteps):
         """LSERK4 steps replayed from a CUDA graph of one step."""
         self._check(lib().dg_rk_steps_graph(self.h, float(t), float(dt), int(nsteps)))
+
+    def rk_stage_batch(self, U_in, U_out, nstages, t, dt):
+        """Independent host states through stages 0 .. nstages-1 of a step,
+        host copies overlapped with the computation (dg_rk_stage_batch).
+        U_in, U_out: sequences of C-contiguous float64 host arrays (or CPU
+        tensors) of the state's shape, page-locked for the overlap."""
+        if len(U_in) != len(U_out):
+            raise ValueError("rk_stage_batch: as many outputs as inputs")
+        n5 = 5 * self.K * self.n3
+        for a in list(U_in) + list(U_out):
+            p, dev = _ptr(a)
+            if dev or (a.size if isinstance(a, np.ndarray) else a.numel()) != n5:
+                raise ValueError("rk_stage_batch: host arrays of the state's size")
+        ins = (ctypes.c_void_p * max(1, len(U_in)))(*[_ptr(a)[0].value for a in U_in])
+        outs = (ctypes.c_void_p * max(1, len(U_out)))(*[_ptr(a)[0].value for a in U_out])
+        self._check(lib().dg_rk_stage_batch(self.h, len(U_in), ins, outs, int(nstages), float(t), float(dt)))
 
     def check_status(self):
         self._check(lib().dg_check_status(self.h))

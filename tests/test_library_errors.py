@@ -106,3 +106,10 @@ def test_face_orientation_must_be_consistent():
     assert _init(spec.N, X, nbr, nbr_face=nf, orient=bad)[0] == MESH
     badf = nf.copy(); badf[0, 1] = 3                  # wrong neighbour face
     assert _init(spec.N, X, nbr, nbr_face=badf, orient=ori)[0] == MESH
+
+
+def test_batch_call_refuses_a_null_context():
+    import ctypes
+    from paper_2606_18927_gb300 import dg
+    L = dg.lib()
+    assert L.dg_rk_stage_batch(None, 1, None, None, 1, 0.0, 1e-3) == -1
