@@ -683,6 +683,44 @@ __device__ __forceinline__ void flux_delta(const NodeF& i, const NodeF& m, float
   G[4] = g0 * (h_ref + fmaf(0.5f, dh, i.h)) + 0.5f * ruia * dh;
 }
 
+// both orientations of a pair, G(i -> m) into Gi and G(m -> i) into Gm: the
+// differences change sign between them and {a} does not, so they are formed
+// once
+__device__ __forceinline__ void flux_delta_pair(const NodeF& i, const NodeF& m, float ai0, float ai1, float ai2,
+                                                float am0, float am1, float am2, float rho_ref, float h_ref,
+                                                float Gi[5], float Gm[5]) {
+  const float du = (m.u - i.u) + (m.ul - i.ul), dv = (m.v - i.v) + (m.vl - i.vl), dw = (m.w - i.w) + (m.wl - i.wl);
+  const float dr = m.rho - i.rho, dp = m.p - i.p, dh = m.h - i.h;
+  const float da0 = am0 - ai0, da1 = am1 - ai1, da2 = am2 - ai2;
+  const float ab0 = fmaf(0.5f, da0, ai0), ab1 = fmaf(0.5f, da1, ai1), ab2 = fmaf(0.5f, da2, ai2);
+  const float dua = 0.5f * (du * ab0 + dv * ab1 + dw * ab2);  // du/2 . {a}
+  {
+    const float ri = rho_ref + i.rho;
+    const float uia = i.u * ai0 + i.v * ai1 + i.w * ai2;
+    const float uida = 0.5f * (i.u * da0 + i.v * da1 + i.w * da2);
+    const float g0 = ri * dua + 0.5f * dr * (uia + uida + dua);
+    const float ruia = ri * (uia + uida);
+    Gi[0] = g0;
+    Gi[1] = g0 * fmaf(0.5f, du, i.u) + 0.5f * (ruia * du + dp * ab0);
+    Gi[2] = g0 * fmaf(0.5f, dv, i.v) + 0.5f * (ruia * dv + dp * ab1);
+    Gi[3] = g0 * fmaf(0.5f, dw, i.w) + 0.5f * (ruia * dw + dp * ab2);
+    Gi[4] = g0 * (h_ref + fmaf(0.5f, dh, i.h)) + 0.5f * ruia * dh;
+  }
+  {
+    // (with du -> -du, drho -> -drho, ..., da -> -da)
+    const float rm = rho_ref + m.rho;
+    const float uma = m.u * am0 + m.v * am1 + m.w * am2;
+    const float umda = -0.5f * (m.u * da0 + m.v * da1 + m.w * da2);
+    const float g0 = -(rm * dua + 0.5f * dr * (uma + umda - dua));
+    const float ruma = rm * (uma + umda);
+    Gm[0] = g0;
+    Gm[1] = g0 * fmaf(-0.5f, du, m.u) - 0.5f * (ruma * du + dp * ab0);
+    Gm[2] = g0 * fmaf(-0.5f, dv, m.v) - 0.5f * (ruma * dv + dp * ab1);
+    Gm[3] = g0 * fmaf(-0.5f, dw, m.w) - 0.5f * (ruma * dw + dp * ab2);
+    Gm[4] = g0 * (h_ref + fmaf(-0.5f, dh, m.h)) - 0.5f * ruma * dh;
+  }
+}
+
 __device__ __forceinline__ NodeF nodef(const Prim<float>& q, const Lo3& l) {
   return NodeF{q.rho, q.u, q.v, q.w, q.p, q.h, l.u, l.v, l.w};
 }
@@ -698,8 +736,7 @@ __device__ __forceinline__ void face_flux_delta(const PhysDev& ph, const Prim<fl
   const float dvel[3] = {(B.u - A.u) + (lb.u - la.u), (B.v - A.v) + (lb.v - la.v), (B.w - A.w) + (lb.w - la.w)};
   riemann_dissipation<float>(ph, unshift32(A, ph), unshift32(B, ph), dU, nx, ny, nz, Z, &drho, dvel);
   const float rr = ph.f32c.rho_ref, hr = ph.f32c.h_ref;
-  flux_delta(nodef(A, la), nodef(B, lb), nx, ny, nz, 0.f, 0.f, 0.f, rr, hr, DA);
-  flux_delta(nodef(B, lb), nodef(A, la), nx, ny, nz, 0.f, 0.f, 0.f, rr, hr, DB);
+  flux_delta_pair(nodef(A, la), nodef(B, lb), nx, ny, nz, nx, ny, nz, rr, hr, DA, DB);
 #pragma unroll
   for (int v = 0; v < 5; ++v) { DA[v] += Z[v]; DB[v] += Z[v]; }
 }
@@ -2062,20 +2099,22 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
                            sQ[5 * n3 + qs], sQ[7 * n3 + qs], sQ[8 * n3 + qs], sQ[9 * n3 + qs]};
             const float aq0 = sA[(dir * 3 + 0) * n3 + qs], aq1 = sA[(dir * 3 + 1) * n3 + qs],
                         aq2 = sA[(dir * 3 + 2) * n3 + qs];
-            float G[5];
-            flux_delta(mi, mq, A.a0, A.a1, A.a2, aq0 - A.a0, aq1 - A.a1, aq2 - A.a2, ph.f32c.rho_ref, ph.f32c.h_ref,
-                       G);
+            float G[5], Gq[5];
             const float c1 = sC1[pos * n + pm];
-#pragma unroll
-            for (int v = 0; v < 5; ++v) acc[v] += c1 * G[v];
             if (2 * d != n) {
-              // G(q -> i) for the partner lane (pos + d); receive G(i -> pos - d)
-              flux_delta(mq, mi, aq0, aq1, aq2, A.a0 - aq0, A.a1 - aq1, A.a2 - aq2, ph.f32c.rho_ref, ph.f32c.h_ref,
-                         G);
+              // and G(q -> i) for the partner lane (pos + d); receive G(i -> pos - d)
+              flux_delta_pair(mi, mq, A.a0, A.a1, A.a2, aq0, aq1, aq2, ph.f32c.rho_ref, ph.f32c.h_ref, G, Gq);
+#pragma unroll
+              for (int v = 0; v < 5; ++v) acc[v] += c1 * G[v];
               const int src = base + (pos - d >= 0 ? pos - d : pos - d + n);
               const float r1 = sC1[pos * n + (src - base)];
 #pragma unroll
-              for (int v = 0; v < 5; ++v) acc[v] += r1 * __shfl_sync(0xffffffffu, G[v], src);
+              for (int v = 0; v < 5; ++v) acc[v] += r1 * __shfl_sync(0xffffffffu, Gq[v], src);
+            } else {
+              flux_delta(mi, mq, A.a0, A.a1, A.a2, aq0 - A.a0, aq1 - A.a1, aq2 - A.a2, ph.f32c.rho_ref,
+                         ph.f32c.h_ref, G);
+#pragma unroll
+              for (int v = 0; v < 5; ++v) acc[v] += c1 * G[v];
             }
             continue;
           }
