@@ -125,7 +125,21 @@ struct Tables {
   double DVS8[(N + 1) * (N + 1)];   // (2D - B/w) / 8
   double Dvisc[(N + 1) * (N + 1)];  // (w_m / w_i) D_mi
   double iw[N + 1];                 // 1 / w
+  float D32[(N + 1) * (N + 1)];     // D and Dvisc rounded to FP32 (kernel-parameter
+  float Dvisc32[(N + 1) * (N + 1)]; // operands of the FP32 line contractions)
 };
+
+// Node slot in shared memory of the FP32 lifting kernel at N = 7 (node index
+// i + 8 j + 64 k): bank bits (i0^j0^k0, i1^j1^k1, i2^j2^k2, i1^j0, i0^i1^j1),
+// row (j2, k).  A bijection of the 512 nodes under which the 32 lanes of a
+// warp hit 32 distinct banks when they hold one node each (consecutive
+// nodes) and when each holds a line along xi, eta or zeta (consecutive line
+// indices, the same position on the line): checked on the host.
+__device__ __forceinline__ int lift_slot8(int node) {
+  const int i = node & 7, j = (node >> 3) & 7, k = node >> 6;
+  const int bank = ((i ^ j ^ k) & 7) | ((((i >> 1) ^ j) & 1) << 3) | (((i ^ (i >> 1) ^ (j >> 1)) & 1) << 4);
+  return bank | (((j >> 2) | (k << 1)) << 5);
+}
 
 template <int N>
 __device__ __forceinline__ int fnode(int l, int a, int b) {
@@ -1142,6 +1156,16 @@ k_lift(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
   // of each node sharing a warp with its three mirror nodes (the FP32 kernel is
   // not bound by its multiply-adds: the extra barriers and shuffles cost more)
   constexpr bool EO = (n == 8) && std::is_same<R, double>::value;
+  // FP32, N = 7: the line contractions by one thread per line (n outputs from
+  // the line's n values held in registers, the coefficients as operands from
+  // the kernel parameters) instead of one thread per node (n shared-memory
+  // loads per output, the kernel's bound), the node slots swizzled
+  // (lift_slot8)
+  constexpr bool LT = (n == 8) && std::is_same<R, float>::value;
+  auto ws = [](int node) {
+    if constexpr (LT) return lift_slot8(node);
+    else return node;
+  };
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* sW = reinterpret_cast<R*>(smem_raw);      // [4][n3]
   R* sC = sW + 4 * n3;                          // [6][4][n2]
@@ -1184,7 +1208,8 @@ k_lift(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
     } else {
       velocity_temperature<R>(U[g], U[S + g], U[2 * S + g], U[3 * S + g], U[4 * S + g], ph, u, v, w, T);
     }
-    sW[p] = u; sW[n3 + p] = v; sW[2 * n3 + p] = w; sW[3 * n3 + p] = T;
+    const int sp = ws(p);
+    sW[sp] = u; sW[n3 + sp] = v; sW[2 * n3 + sp] = w; sW[3 * n3 + sp] = T;
   }
   __syncthreads();
   // 2 (W* - W) at the six faces (BR1 average with the neighbour, or the
@@ -1194,7 +1219,8 @@ k_lift(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
     const int l = t / n2, ab = t - l * n2, a = ab % n, b = ab / n;
     const int q = fnode<N>(l, a, b);
     const int nb = m.nbr[e * 6 + l];
-    const R Wo0 = sW[q], Wo1 = sW[n3 + q], Wo2 = sW[2 * n3 + q], Wo3 = sW[3 * n3 + q];
+    const int sq = ws(q);
+    const R Wo0 = sW[sq], Wo1 = sW[n3 + sq], Wo2 = sW[2 * n3 + sq], Wo3 = sW[3 * n3 + sq];
     R d0, d1, d2, d3;
     if (nb >= 0) {
       const NbrNode<N> nn = neighbour_node<N>(m, e, l, ab);
@@ -1270,6 +1296,40 @@ k_lift(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
 #pragma unroll
       for (int dir = 0; dir < 3; ++dir)
         dW[dir][v] = LineEO<N>::apply(sD, sG + (dir * 4 + v) * n3, p, dir, qd[dir]);
+  } else if constexpr (LT) {
+    // thread tid < 3 n2 takes line L of direction dir and writes the
+    // reference-space derivatives of its n nodes into sG
+    if (tid < 3 * n2) {
+      const int dir = tid / n2, L = tid - dir * n2;
+      const int n0 = dir == 0 ? n * L : (dir == 1 ? (L % n) + n2 * (L / n) : L);
+      // node n0 + q stride has slot slot(n0) ^ slot(q stride) (the slot map
+      // is linear in the index bits, and n0 has no bits of the line's axis)
+      const int s0 = lift_slot8(n0);
+      int sl[n];
+#pragma unroll
+      for (int q = 0; q < n; ++q)
+        sl[q] = s0 ^ (dir == 0 ? lift_slot8(q) : (dir == 1 ? lift_slot8(q * n) : lift_slot8(q * n2)));
+      R x[4][n];
+#pragma unroll
+      for (int q = 0; q < n; ++q)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) x[v][q] = sW[v * n3 + sl[q]];
+#pragma unroll
+      for (int q = 0; q < n; ++q)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          R y = R(0);
+#pragma unroll
+          for (int mm = 0; mm < n; ++mm) y = fmaf(tab.D32[q * n + mm], x[v][mm], y);
+          sG[(dir * 4 + v) * n3 + sl[q]] = y;
+        }
+    }
+    __syncthreads();
+    const int sp = lift_slot8(p);
+#pragma unroll
+    for (int dir = 0; dir < 3; ++dir)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) dW[dir][v] = sG[(dir * 4 + v) * n3 + sp];
   } else {
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
@@ -1301,10 +1361,10 @@ k_lift(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
   R mu = cR<R>(ph.mu, ph.f32c.mu), kc = cR<R>(ph.kcond, ph.f32c.kcond);
   if (ph.sutherland) {
     // (FP32: the lifted temperature is T - T_lift)
-    mu = sutherland<R>(ph, sW[3 * n3 + p] + cR<R>(0.0, ph.f32c.T_lift));
+    mu = sutherland<R>(ph, sW[3 * n3 + ws(p)] + cR<R>(0.0, ph.f32c.T_lift));
     kc = mu * cR<R>(ph.cp_Pr, ph.f32c.cp_Pr);
   }
-  const R uu = sW[p], vv = sW[n3 + p], ww = sW[2 * n3 + p];
+  const R uu = sW[ws(p)], vv = sW[n3 + ws(p)], ww = sW[2 * n3 + ws(p)];
   // contravariant G^dir = sum_d Ja^dir_d Fv_d
   R G[3][4];
   // symmetric stress: tau_ab = mu (q_ba + q_ab) - (2/3) mu div delta_ab
@@ -1411,6 +1471,43 @@ k_lift(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
       for (int dir = 0; dir < 3; ++dir) s += LineEO<N>::apply(sDv, sG + (dir * 4 + v) * n3, p, dir, qd[dir]);
       Rv[(size_t)v * S + g] = s;
     }
+  } else if constexpr (LT) {
+    __syncthreads();  // the nodes have read their derivatives from sG
+    const int sp = lift_slot8(p);
+#pragma unroll
+    for (int dir = 0; dir < 3; ++dir)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) sG[(dir * 4 + v) * n3 + sp] = G[dir][v];
+    __syncthreads();
+    // one thread per line: its direction's part of R_v at its n nodes, in
+    // place (a line's slots of its direction belong to its thread alone)
+    if (tid < 3 * n2) {
+      const int dir = tid / n2, L = tid - dir * n2;
+      const int n0 = dir == 0 ? n * L : (dir == 1 ? (L % n) + n2 * (L / n) : L);
+      const int s0 = lift_slot8(n0);
+      int sl[n];
+#pragma unroll
+      for (int q = 0; q < n; ++q)
+        sl[q] = s0 ^ (dir == 0 ? lift_slot8(q) : (dir == 1 ? lift_slot8(q * n) : lift_slot8(q * n2)));
+      R x[4][n];
+#pragma unroll
+      for (int q = 0; q < n; ++q)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) x[v][q] = sG[(dir * 4 + v) * n3 + sl[q]];
+#pragma unroll
+      for (int q = 0; q < n; ++q)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          R y = R(0);
+#pragma unroll
+          for (int mm = 0; mm < n; ++mm) y = fmaf(tab.Dvisc32[q * n + mm], x[v][mm], y);
+          sG[(dir * 4 + v) * n3 + sl[q]] = y;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+      Rv[(size_t)v * S + g] = sG[(0 * 4 + v) * n3 + sp] + sG[(1 * 4 + v) * n3 + sp] + sG[(2 * 4 + v) * n3 + sp];
   } else {
 #pragma unroll
     for (int dir = 0; dir < 3; ++dir)

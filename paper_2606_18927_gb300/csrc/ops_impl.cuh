@@ -23,6 +23,8 @@ static Tables<N> make_tables(const double* D, const double* w) {
       t.D[i * n + m] = D[i * n + m];
       t.DVS8[i * n + m] = dvs / 8.0;
       t.Dvisc[i * n + m] = w[m] / w[i] * D[m * n + i];
+      t.D32[i * n + m] = (float)t.D[i * n + m];
+      t.Dvisc32[i * n + m] = (float)t.Dvisc[i * n + m];
     }
   }
   return t;
