@@ -1147,8 +1147,17 @@ struct LineEO {
 // ---------------------------------------------------------------------------
 // k_lift: one CTA of n^3 threads per element.
 // ---------------------------------------------------------------------------
+// Resident CTAs per SM asked of the register allocator for the lifting
+// kernel: two for CTAs of up to 512 threads, three for the FP32 kernel at
+// N = 7 (42 registers; its line phases leave the other threads waiting at a
+// barrier, which a third CTA per SM covers)
 template <int N, typename R>
-__global__ void __launch_bounds__((N + 1) * (N + 1) * (N + 1), ((N + 1) * (N + 1) * (N + 1) <= 512 ? 2 : 1))
+constexpr int lift_min_blocks() {
+  return ((N + 1) * (N + 1) * (N + 1) > 512) ? 1 : ((N == 7 && std::is_same<R, float>::value) ? 3 : 2);
+}
+
+template <int N, typename R>
+__global__ void __launch_bounds__((N + 1) * (N + 1) * (N + 1), (lift_min_blocks<N, R>()))
 k_lift(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const Tables<N> tab,
        R* __restrict__ Rv, R* __restrict__ Gf) {
   constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
@@ -1156,11 +1165,11 @@ k_lift(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
   // of each node sharing a warp with its three mirror nodes (the FP32 kernel is
   // not bound by its multiply-adds: the extra barriers and shuffles cost more)
   constexpr bool EO = (n == 8) && std::is_same<R, double>::value;
-  // FP32, N = 7: the line contractions by one thread per line (n outputs from
-  // the line's n values held in registers, the coefficients as operands from
-  // the kernel parameters) instead of one thread per node (n shared-memory
-  // loads per output, the kernel's bound), the node slots swizzled
-  // (lift_slot8)
+  // FP32, N = 7: the line contractions by two threads per line, two
+  // variables each (n outputs from the line's n values held in registers, the
+  // coefficients as operands from the kernel parameters) instead of one thread
+  // per node (n shared-memory loads per output, the kernel's bound), the node
+  // slots swizzled (lift_slot8)
   constexpr bool LT = (n == 8) && std::is_same<R, float>::value;
   auto ws = [](int node) {
     if constexpr (LT) return lift_slot8(node);
@@ -1297,10 +1306,11 @@ k_lift(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
       for (int dir = 0; dir < 3; ++dir)
         dW[dir][v] = LineEO<N>::apply(sD, sG + (dir * 4 + v) * n3, p, dir, qd[dir]);
   } else if constexpr (LT) {
-    // thread tid < 3 n2 takes line L of direction dir and writes the
-    // reference-space derivatives of its n nodes into sG
-    if (tid < 3 * n2) {
-      const int dir = tid / n2, L = tid - dir * n2;
+    // thread tid < 6 n2 takes two of the four variables (v0, v0 + 1) on line
+    // L of direction dir and writes the reference-space derivatives of its n
+    // nodes into sG
+    if (tid < 6 * n2) {
+      const int dir = tid / (2 * n2), r = tid - dir * 2 * n2, v0 = 2 * (r / n2), L = r % n2;
       const int n0 = dir == 0 ? n * L : (dir == 1 ? (L % n) + n2 * (L / n) : L);
       // node n0 + q stride has slot slot(n0) ^ slot(q stride) (the slot map
       // is linear in the index bits, and n0 has no bits of the line's axis)
@@ -1309,19 +1319,19 @@ k_lift(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
 #pragma unroll
       for (int q = 0; q < n; ++q)
         sl[q] = s0 ^ (dir == 0 ? lift_slot8(q) : (dir == 1 ? lift_slot8(q * n) : lift_slot8(q * n2)));
-      R x[4][n];
+      R x[2][n];
 #pragma unroll
       for (int q = 0; q < n; ++q)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) x[v][q] = sW[v * n3 + sl[q]];
+        for (int v = 0; v < 2; ++v) x[v][q] = sW[(v0 + v) * n3 + sl[q]];
 #pragma unroll
       for (int q = 0; q < n; ++q)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) {
+        for (int v = 0; v < 2; ++v) {
           R y = R(0);
 #pragma unroll
           for (int mm = 0; mm < n; ++mm) y = fmaf(tab.D32[q * n + mm], x[v][mm], y);
-          sG[(dir * 4 + v) * n3 + sl[q]] = y;
+          sG[(dir * 4 + v0 + v) * n3 + sl[q]] = y;
         }
     }
     __syncthreads();
@@ -1479,29 +1489,30 @@ k_lift(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
 #pragma unroll
       for (int v = 0; v < 4; ++v) sG[(dir * 4 + v) * n3 + sp] = G[dir][v];
     __syncthreads();
-    // one thread per line: its direction's part of R_v at its n nodes, in
-    // place (a line's slots of its direction belong to its thread alone)
-    if (tid < 3 * n2) {
-      const int dir = tid / n2, L = tid - dir * n2;
+    // two threads per line: its direction's part of R_v at its n nodes, in
+    // place (a line's slots of its direction and variables belong to its
+    // thread alone)
+    if (tid < 6 * n2) {
+      const int dir = tid / (2 * n2), r = tid - dir * 2 * n2, v0 = 2 * (r / n2), L = r % n2;
       const int n0 = dir == 0 ? n * L : (dir == 1 ? (L % n) + n2 * (L / n) : L);
       const int s0 = lift_slot8(n0);
       int sl[n];
 #pragma unroll
       for (int q = 0; q < n; ++q)
         sl[q] = s0 ^ (dir == 0 ? lift_slot8(q) : (dir == 1 ? lift_slot8(q * n) : lift_slot8(q * n2)));
-      R x[4][n];
+      R x[2][n];
 #pragma unroll
       for (int q = 0; q < n; ++q)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) x[v][q] = sG[(dir * 4 + v) * n3 + sl[q]];
+        for (int v = 0; v < 2; ++v) x[v][q] = sG[(dir * 4 + v0 + v) * n3 + sl[q]];
 #pragma unroll
       for (int q = 0; q < n; ++q)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) {
+        for (int v = 0; v < 2; ++v) {
           R y = R(0);
 #pragma unroll
           for (int mm = 0; mm < n; ++mm) y = fmaf(tab.Dvisc32[q * n + mm], x[v][mm], y);
-          sG[(dir * 4 + v) * n3 + sl[q]] = y;
+          sG[(dir * 4 + v0 + v) * n3 + sl[q]] = y;
         }
     }
     __syncthreads();
@@ -1989,7 +2000,7 @@ struct VolShape {
 // CTA at 126 registers, in spite of its spills).
 template <int N, typename R, bool EC>
 constexpr int vol_min_blocks() {
-  return (VolShape<N>::THREADS * 64 * 2 <= 65536) ? 2 : 1;
+  return (N == 7 && !EC && std::is_same<R, float>::value) ? 3 : ((VolShape<N>::THREADS * 64 * 2 <= 65536) ? 2 : 1);
 }
 
 template <int N, typename R, int MODE, bool EC>
