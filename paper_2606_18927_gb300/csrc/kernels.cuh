@@ -2202,11 +2202,12 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
         if constexpr (std::is_same<R, float>::value && !EC) {
           if (dif) {
             const NodeF mi{A.rho, A.u, A.v, A.w, A.p4, A.hh, Aul, Avl, Awl};
-            const int qs = vslot<N, R>(q);
-            const NodeF mq{sQ[qs],          sQ[n3 + qs],     sQ[2 * n3 + qs], sQ[3 * n3 + qs], sQ[4 * n3 + qs],
-                           sQ[5 * n3 + qs], sQ[7 * n3 + qs], sQ[8 * n3 + qs], sQ[9 * n3 + qs]};
-            const float aq0 = sA[(dir * 3 + 0) * n3 + qs], aq1 = sA[(dir * 3 + 1) * n3 + qs],
-                        aq2 = sA[(dir * 3 + 2) * n3 + qs];
+            // the partner node's values from the lane that holds it (lane
+            // base + pm of this line's segment)
+            const int lq = base + pm;
+            auto sh = [&](float x) { return __shfl_sync(0xffffffffu, x, lq); };
+            const NodeF mq{sh(A.rho), sh(A.u), sh(A.v), sh(A.w), sh(A.p4), sh(A.hh), sh(Aul), sh(Avl), sh(Awl)};
+            const float aq0 = sh(A.a0), aq1 = sh(A.a1), aq2 = sh(A.a2);
             float G[5], Gq[5];
             const float c1 = sC1[pos * n + pm];
             if (2 * d != n) {
