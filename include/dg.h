@@ -239,10 +239,31 @@ int dg_rk_steps(dg_ctx* c, double t, double dt, int nsteps);
  * paper's Sec. 4 scheme, with Roe + Harten faces), constant viscosity or
  * Sutherland's law, adiabatic or isothermal walls (the wall heat flux's
  * derivative with the stress's), inflow and outflow faces (through the
- * exterior state's dependence on the interior one) and no halo faces (else
- * DG_ERR_NOT_IMPLEMENTED).
+ * exterior state's dependence on the interior one) (else
+ * DG_ERR_NOT_IMPLEMENTED); partitioned contexts run it in phases
+ * (dg_vjp_phase; dg_vjp answers DG_ERR_ARG there).
  * The first call allocates the adjoint scratch of the context. */
 int dg_vjp(dg_ctx* c, const double* U, const double* lam, double* gU, double* gtheta);
+
+/* The adjoint of a partitioned context (see the partitioned-mesh section
+ * below), in four phases with an exchange of the halo buffers after each of
+ * the first three (send_U -> recv_U, send_G -> recv_G, send_U -> recv_U), the
+ * reverse of an evaluation's:
+ *   phase 1  packs the state traces of the halo faces (send_U);
+ *   phase 2  the face, wall-model and boundary kernels: the cotangents of
+ *            the peers' viscous-flux traces into send_G and of their state
+ *            traces into send_U (needs the peers' state traces in recv_U);
+ *            zeroes gtheta first;
+ *   phase 3  adds the peers' viscous-flux cotangents (recv_G) and runs the
+ *            element kernel, which adds its lifting's share to send_U;
+ *   phase 4  gU from the local cotangents and the peers' state cotangents
+ *            (recv_U).
+ * Arguments as dg_vjp (the same U, lam, gU and gtheta in every phase);
+ * gtheta holds this rank's share of (dUt/d(kappa, B))^T lam, to be summed
+ * over the ranks.  The sum over ranks of the gU rows equals dg_vjp on the
+ * unpartitioned mesh to rounding.  DG_ERR_ARG on an unpartitioned context or
+ * a phase outside 1..4; option checks as dg_vjp. */
+int dg_vjp_phase(dg_ctx* c, int phase, const double* U, const double* lam, double* gU, double* gtheta);
 
 /* Sets the wall-law constants (kappa, B) used by later calls (Sec. 3.2). */
 int dg_set_params(dg_ctx* c, double kappa, double B);
@@ -380,7 +401,8 @@ int dg_check_status(dg_ctx* c);
  * host array; send it to the peer, whose dg_halo_set_geometry installs the
  * rows of the faces where its element is the slave.  The fused calls
  * (dg_time_derivative, dg_rk_stage, ...) refuse partitioned contexts with
- * DG_ERR_ARG, and the adjoint with DG_ERR_NOT_IMPLEMENTED.  Wall-model sample
+ * DG_ERR_ARG (the adjoint: dg_vjp_phase; the rollout adjoint answers
+ * DG_ERR_NOT_IMPLEMENTED).  Wall-model sample
  * points must lie in local elements (else dg_init_mesh fails, DG_ERR_MESH).
  * Results equal those of the unpartitioned mesh bitwise.
  * ------------------------------------------------------------------------- */

@@ -391,16 +391,62 @@ static __device__ void face_flux_vjp(const PhysDev& ph, const double UA[5], cons
 }
 
 // ---------------------------------------------------------------------------
-// k_adj_face: one thread per node of an interior face.
+// k_adj_face: one thread per node of an interior face, then (partitioned
+// meshes) of a halo face.  A halo face's flux enters this rank's bracket on
+// its own side only; the cotangents of the remote side's state and outward
+// viscous flux go to sendU / sendG [n_halo][5 or 4][n2] (master's face-node
+// order) for the peer.
 // ---------------------------------------------------------------------------
 template <int N>
 __global__ void __launch_bounds__(128)
 k_adj_face(const double* __restrict__ U, const double* __restrict__ lam, const MeshDev<double> m,
-           const PhysDev ph, double iw, double* __restrict__ gUf, double* __restrict__ gGf) {
+           const PhysDev ph, double iw, double* __restrict__ gUf, double* __restrict__ gGf,
+           double* __restrict__ sendU, double* __restrict__ sendG) {
   constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int f = tid / n2, ab = tid - f * n2;
-  if (f >= m.n_interior) return;
+  if (f >= m.n_interior + (sendU ? m.n_halo : 0)) return;
+  if (f >= m.n_interior) {
+    // fc = (local element, local face, halo index, local side is master | 8 o_own)
+    const int h = f - m.n_interior, fh = m.F - m.n_halo + h;
+    const int4 fc = m.faces[fh];
+    const int abl = omap_ab<N>(orient_inv(fc.w >> 3), ab);
+    const int eL = chk_idx(fc.x, m.K, m.status);
+    const bool master = (fc.w & 1) != 0;
+    const size_t S = (size_t)m.K * n3;
+    const size_t gL = (size_t)eL * n3 + fnode<N>(fc.y, abl % n, abl / n);
+    const double jL = m.invJ[gL];
+    const double* rU = m.halo_U + (size_t)h * 5 * n2 + ab;
+    double gFs[5], UL[5], UR[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      gFs[v] = (master ? -lam[v * S + gL] : lam[v * S + gL]) * jL * iw;
+      UL[v] = U[v * S + gL];
+      UR[v] = rU[v * n2];
+    }
+    const size_t FN = (size_t)m.F * n2, fg = (size_t)fh * n2 + ab;
+    const double nx = m.fgeo[fg], ny = m.fgeo[FN + fg], nz = m.fgeo[2 * FN + fg], s = m.fgeo[3 * FN + fg];
+    if (ph.viscous) {
+      // Fs = F* s - (Gf_M - Gf_S) / 2
+      double* dL = gGf + ((size_t)eL * 6 + fc.y) * 4 * n2 + abl;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        dL[v * n2] = (master ? -0.5 : 0.5) * gFs[v + 1];
+        sendG[((size_t)h * 4 + v) * n2 + ab] = (master ? 0.5 : -0.5) * gFs[v + 1];
+      }
+    }
+    double gF[5], gA[5] = {0.0, 0.0, 0.0, 0.0, 0.0}, gB[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int v = 0; v < 5; ++v) gF[v] = gFs[v] * s;
+    face_flux_vjp(ph, master ? UL : UR, master ? UR : UL, nx, ny, nz, gF, gA, gB);
+    double* oL = gUf + ((size_t)eL * 6 + fc.y) * 5 * n2 + abl;
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      oL[v * n2] = master ? gA[v] : gB[v];
+      sendU[((size_t)h * 5 + v) * n2 + ab] = master ? gB[v] : gA[v];
+    }
+    return;
+  }
   int4 fc = m.faces[f];
   fc.x = chk_idx(fc.x, m.K, m.status);
   fc.z = chk_idx(fc.z, m.K, m.status);
@@ -596,6 +642,25 @@ k_adj_bc(const double* __restrict__ U, const double* __restrict__ lam, const Mes
 }
 
 // ---------------------------------------------------------------------------
+// k_adj_halo_in: the peers' cotangents of this rank's outward viscous fluxes
+// at the halo faces (recvG, master's face-node order) into gGf.
+// ---------------------------------------------------------------------------
+template <int N>
+__global__ void __launch_bounds__(128)
+k_adj_halo_in(const MeshDev<double> m, const double* __restrict__ recvG, double* __restrict__ gGf) {
+  constexpr int n = N + 1, n2 = n * n;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int h = tid / n2, ab = tid - h * n2;
+  if (h >= m.n_halo) return;
+  const int4 fc = m.faces[m.F - m.n_halo + h];
+  const int abl = omap_ab<N>(orient_inv(fc.w >> 3), ab);
+  const int eL = chk_idx(fc.x, m.K, m.status);
+  double* dL = gGf + ((size_t)eL * 6 + fc.y) * 4 * n2 + abl;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) dL[v * n2] += recvG[((size_t)h * 4 + v) * n2 + ab];
+}
+
+// ---------------------------------------------------------------------------
 // k_adj_element: one CTA per element.  Writes the element's own part of gU
 // and, for every interior face, the lifting cotangent of the neighbour's
 // face nodes (gWf[e][l]: for the node across face l).
@@ -618,7 +683,7 @@ template <int N, bool EC, bool SUTH>
 __global__ void __launch_bounds__(AdjShape<N>::THREADS)
 k_adj_element(const double* __restrict__ U, const double* __restrict__ lam, const MeshDev<double> m,
               const PhysDev ph, const Tables<N> tab, const double* __restrict__ gGf, double* __restrict__ gU,
-              double* __restrict__ gWf) {
+              double* __restrict__ gWf, double* __restrict__ gHaloU) {
   using Sh = AdjShape<N>;
   constexpr int n = Sh::n, n2 = Sh::n2, n3 = Sh::n3, T = Sh::THREADS, LPW = VolShape<N>::LPW;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -823,6 +888,14 @@ k_adj_element(const double* __restrict__ U, const double* __restrict__ lam, cons
                                      wn, Tn);
         d[0] = 0.5 * (un - sW[q]); d[1] = 0.5 * (vn - sW[n3 + q]); d[2] = 0.5 * (wn - sW[2 * n3 + q]);
         d[3] = 0.5 * (Tn - sW[3 * n3 + q]);
+      } else if (nb <= -16) {
+        // halo face: the remote element's trace (master's face-node order)
+        const int abm = omap_ab<N>((m.elem_face[e * 6 + l] >> 1) & 7, ab);
+        const double* src = m.halo_U + (size_t)chk_idx(-16 - nb, m.n_halo, m.status) * 5 * n2 + abm;
+        double un, vn, wn, Tn;
+        velocity_temperature<double>(src[0], src[n2], src[2 * n2], src[3 * n2], src[4 * n2], ph, un, vn, wn, Tn);
+        d[0] = 0.5 * (un - sW[q]); d[1] = 0.5 * (vn - sW[n3 + q]); d[2] = 0.5 * (wn - sW[2 * n3 + q]);
+        d[3] = 0.5 * (Tn - sW[3 * n3 + q]);
       } else if (nb == -2 || nb == -3) {
         // inflow / outflow: W* - W = (W(exterior) - W) / 2
         const size_t gq = (size_t)e * n3 + q;
@@ -1018,6 +1091,20 @@ k_adj_element(const double* __restrict__ U, const double* __restrict__ lam, cons
           double* dst = gWf + ((size_t)e * 6 + l) * 4 * n2 + ab;
 #pragma unroll
           for (int v = 0; v < 4; ++v) dst[v * n2] = 0.5 * tv[v];
+        } else if (nb <= -16) {
+          // halo face: the remote node's share, through its W(U), to the peer
+          // (gHaloU holds the face kernel's share already)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) gWo[v] -= 0.5 * tv[v];
+          const int abm = omap_ab<N>((m.elem_face[e * 6 + l] >> 1) & 7, ab);
+          const size_t hb = (size_t)chk_idx(-16 - nb, m.n_halo, m.status) * 5 * n2 + abm;
+          double Ur[5], gr[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+          const double gWr[4] = {0.5 * tv[0], 0.5 * tv[1], 0.5 * tv[2], 0.5 * tv[3]};
+#pragma unroll
+          for (int v = 0; v < 5; ++v) Ur[v] = m.halo_U[hb + v * n2];
+          vt_vjp(Ur, ph, gWr, gr);
+#pragma unroll
+          for (int v = 0; v < 5; ++v) gHaloU[hb + v * n2] += gr[v];
         } else if (nb == -2) {
           // inflow: the exterior state is the prescribed one
 #pragma unroll
@@ -1104,7 +1191,8 @@ k_adj_element(const double* __restrict__ U, const double* __restrict__ lam, cons
 template <int N>
 __global__ void __launch_bounds__(256)
 k_adj_gather(const double* __restrict__ U, const MeshDev<double> m, const PhysDev ph,
-             const double* __restrict__ gUf, const double* __restrict__ gWf, double* __restrict__ gU) {
+             const double* __restrict__ gUf, const double* __restrict__ gWf, const double* __restrict__ recvGU,
+             double* __restrict__ gU) {
   constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
   const size_t S = (size_t)m.K * n3;
   const size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1124,6 +1212,13 @@ k_adj_gather(const double* __restrict__ U, const MeshDev<double> m, const PhysDe
 #pragma unroll
       for (int v = 0; v < 4; ++v) gW[v] += w[v * n2];
       any_w = true;
+    } else if (recvGU && nb <= -16) {
+      // a halo face: the peer's cotangent of this node's state (its face
+      // flux and its lifting, master's face-node order)
+      const int abm = omap_ab<N>((m.elem_face[e * 6 + l] >> 1) & 7, ab);
+      const double* r = recvGU + (size_t)chk_idx(-16 - nb, m.n_halo, m.status) * 5 * n2 + abm;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) add[v] += r[v * n2];
     }
   };
   if (i == 0) face(0, j + n * k);

@@ -857,6 +857,8 @@ static dg::OpArgs adjoint_args(dg_ctx* c, const double* U, const double* lam, do
   a.Uin = U; a.status = c->status;
   a.lam = lam; a.gU = gU; a.gUf = c->gUf; a.gGf = c->gGf; a.gWf = c->gWf; a.gUs = c->gUs; a.gtheta = gth;
   a.JaJ = c->JaJ; a.Mj = c->Mj;
+  a.n_halo = c->geo.n_halo;
+  a.halo_U = c->halo_U; a.halo_G = c->halo_G; a.send_U = c->send_U; a.send_G = c->send_G;
   return a;
 }
 
@@ -866,8 +868,6 @@ static int check_adjoint_options(dg_ctx* c, const char* who) {
   if (c->opts.vol_flux == DG_VOL_KEP_KENNEDY_GRUBER)
     return fail(c, DG_ERR_NOT_IMPLEMENTED,
                 std::string(who) + ": the adjoint covers the Pirozzoli and entropy-conserving volume fluxes");
-  if (c->geo.n_halo > 0)
-    return fail(c, DG_ERR_NOT_IMPLEMENTED, std::string(who) + ": the adjoint covers single-partition meshes");
   return DG_OK;
 }
 
@@ -958,6 +958,9 @@ int dg_rollout_vjp(dg_ctx* c, const double* U0, int nsteps, double dt, double* l
   if (!U0 || !loss || !gU0 || nsteps < 0) return fail(c, DG_ERR_ARG, "dg_rollout_vjp: bad argument");
   int rc = check_adjoint_options(c, "dg_rollout_vjp");
   if (rc != DG_OK) return rc;
+  if (c->geo.n_halo > 0)
+    return fail(c, DG_ERR_NOT_IMPLEMENTED, "dg_rollout_vjp: unpartitioned contexts only (a partitioned context "
+                                           "steps and differentiates in phases)");
   if (c->geo.n_wall == 0 || !c->opts.viscous)
     return fail(c, DG_ERR_ARG, "dg_rollout_vjp: the loss needs wall-modelled walls");
   rc = ensure_adjoint_scratch(c);
@@ -1029,6 +1032,8 @@ int dg_vjp(dg_ctx* c, const double* U, const double* lam, double* gU, double* gt
   if (!lam || !gU) return fail(c, DG_ERR_ARG, "dg_vjp: null lam or gU");
   int rc = check_adjoint_options(c, "dg_vjp");
   if (rc != DG_OK) return rc;
+  if (c->geo.n_halo > 0)
+    return fail(c, DG_ERR_ARG, "dg_vjp: a partitioned context runs the adjoint in phases (dg_vjp_phase)");
   const double* Uin = U;
   if (!Uin) {
     if (!c->state_set) return fail(c, DG_ERR_NOT_INIT, "dg_vjp: state not set");
@@ -1042,6 +1047,32 @@ int dg_vjp(dg_ctx* c, const double* U, const double* lam, double* gU, double* gt
   dg::OpArgs a = adjoint_args(c, Uin, lam, gU, gth);
   rc = dg::run_vjp(a, c->ph, c->stream);
   if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "dg_vjp launch");
+  return DG_OK;
+}
+
+int dg_vjp_phase(dg_ctx* c, int phase, const double* U, const double* lam, double* gU, double* gtheta) {
+  if (!c) return DG_ERR_ARG;
+  if (phase < 1 || phase > 4) return fail(c, DG_ERR_ARG, "dg_vjp_phase: phase must be 1, 2, 3 or 4");
+  if (c->geo.n_halo == 0) return fail(c, DG_ERR_ARG, "dg_vjp_phase: for partitioned contexts (else dg_vjp)");
+  if (!lam || !gU) return fail(c, DG_ERR_ARG, "dg_vjp_phase: null lam or gU");
+  int rc = check_adjoint_options(c, "dg_vjp_phase");
+  if (rc != DG_OK) return rc;
+  const double* Uin = U;
+  if (!Uin) {
+    if (!c->state_set) return fail(c, DG_ERR_NOT_INIT, "dg_vjp_phase: state not set");
+    Uin = c->U;
+  }
+  rc = ensure_adjoint_scratch(c);
+  if (rc != DG_OK) return rc;
+  double* gth = gtheta ? gtheta : c->gtheta;
+  if (phase == 2) {
+    cudaError_t e = cudaMemsetAsync(gth, 0, 2 * sizeof(double), c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "dg_vjp_phase");
+  }
+  dg::OpArgs a = adjoint_args(c, Uin, lam, gU, gth);
+  a.phase = phase;
+  rc = dg::run_vjp(a, c->ph, c->stream);
+  if (rc != 0) return cuda_fail(c, (cudaError_t)rc, "dg_vjp_phase launch");
   return DG_OK;
 }
 

@@ -158,6 +158,7 @@ static int run_vjp_typed(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {
   m.ws_elem = a.ws_elem; m.ws_lag = a.ws_lag;
   m.status = a.status;
   m.JaJ = a.JaJ; m.Mj = a.Mj;
+  m.n_halo = a.n_halo; m.halo_U = a.halo_U; m.halo_G = static_cast<const double*>(a.halo_G);
   if (ph.viscous && !a.JaJ) return (int)cudaErrorInvalidValue;
   const Tables<N> tab = make_tables<N>(a.D, a.w);
   const double iw = tab.iw[0];
@@ -171,25 +172,50 @@ static int run_vjp_typed(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {
   const bool ec = ph.vol_flux == 2, su = ph.sutherland != 0;
   auto kel = ec ? (su ? element(k_adj_element<N, true, true>) : element(k_adj_element<N, true, false>))
                 : (su ? element(k_adj_element<N, false, true>) : element(k_adj_element<N, false, false>));
-  if (a.n_interior > 0) {
-    const long long work = (long long)a.n_interior * n2;
-    k_adj_face<N><<<(unsigned)((work + 127) / 128), 128, 0, s>>>(a.Uin, a.lam, m, ph, iw, a.gUf, a.gGf);
+  // Partitioned meshes run in four phases around three exchanges (the
+  // reverse of the evaluation's): 1 packs the state traces of the halo
+  // faces (send_U); 2 the face, wall and boundary kernels, which leave the
+  // cotangents of the peers' viscous-flux traces in send_G and of their
+  // state traces in send_U; 3 adds the peers' viscous-flux cotangents
+  // (halo_G) and runs the element kernel, which adds its lifting's share to
+  // send_U; 4 gathers, with the peers' state cotangents (halo_U).
+  const bool part = a.n_halo > 0;
+  const int phase = part ? a.phase : 14;
+  double* sendU = part ? a.send_U : nullptr;
+  double* sendG = part ? static_cast<double*>(a.send_G) : nullptr;
+  const unsigned halo_blocks = (unsigned)(((long long)a.n_halo * n2 + 127) / 128);
+  if (phase == 1) {
+    k_halo_pack<N, double><<<(unsigned)(((long long)a.n_halo * n2 + 255) / 256), 256, 0, s>>>(
+        a.Uin, m, static_cast<const double*>(nullptr), a.send_U, static_cast<double*>(nullptr));
+    return (int)cudaGetLastError();
   }
-  if (a.n_wall > 0) {
-    const long long work = (long long)a.n_wall * n2;
-    k_adj_wall<N><<<(unsigned)((work + WALL_THREADS - 1) / WALL_THREADS), WALL_THREADS, 0, s>>>(a.Uin, a.lam, m, ph, iw, a.gUf, a.gGf, a.gUs,
-                                                                 a.gtheta, a.status);
+  if (phase == 2 || phase == 14) {
+    const long long work = (long long)(a.n_interior + (part ? a.n_halo : 0)) * n2;
+    if (work > 0)
+      k_adj_face<N><<<(unsigned)((work + 127) / 128), 128, 0, s>>>(a.Uin, a.lam, m, ph, iw, a.gUf, a.gGf, sendU,
+                                                                   sendG);
+    if (a.n_wall > 0) {
+      const long long ww = (long long)a.n_wall * n2;
+      k_adj_wall<N><<<(unsigned)((ww + WALL_THREADS - 1) / WALL_THREADS), WALL_THREADS, 0, s>>>(
+          a.Uin, a.lam, m, ph, iw, a.gUf, a.gGf, a.gUs, a.gtheta, a.status);
+    }
+    if (a.n_bc > 0) {
+      const long long wb = (long long)a.n_bc * n2;
+      k_adj_bc<N><<<(unsigned)((wb + 127) / 128), 128, 0, s>>>(a.Uin, a.lam, m, ph, iw, a.gUf, a.gGf);
+    }
   }
-  if (a.n_bc > 0) {
-    const long long work = (long long)a.n_bc * n2;
-    k_adj_bc<N><<<(unsigned)((work + 127) / 128), 128, 0, s>>>(a.Uin, a.lam, m, ph, iw, a.gUf, a.gGf);
+  if (phase == 3 || phase == 14) {
+    if (part && ph.viscous) k_adj_halo_in<N><<<halo_blocks, 128, 0, s>>>(m, m.halo_G, a.gGf);
+    kel<<<a.K, AdjShape<N>::THREADS, smem, s>>>(a.Uin, a.lam, m, ph, tab, a.gGf, a.gU, a.gWf, sendU);
   }
-  kel<<<a.K, AdjShape<N>::THREADS, smem, s>>>(a.Uin, a.lam, m, ph, tab, a.gGf, a.gU, a.gWf);
-  const long long S = (long long)a.K * n3;
-  k_adj_gather<N><<<(unsigned)((S + 255) / 256), 256, 0, s>>>(a.Uin, m, ph, a.gUf, a.gWf, a.gU);
-  if (a.n_wall > 0 && ph.viscous) {
-    const long long work = (long long)a.n_wall * n2;
-    k_adj_scatter<N><<<(unsigned)((work + 127) / 128), 128, 0, s>>>(m, a.gUs, a.gU);
+  if (phase == 4 || phase == 14) {
+    const long long S = (long long)a.K * n3;
+    k_adj_gather<N><<<(unsigned)((S + 255) / 256), 256, 0, s>>>(a.Uin, m, ph, a.gUf, a.gWf,
+                                                                 part ? a.halo_U : nullptr, a.gU);
+    if (a.n_wall > 0 && ph.viscous) {
+      const long long work = (long long)a.n_wall * n2;
+      k_adj_scatter<N><<<(unsigned)((work + 127) / 128), 128, 0, s>>>(m, a.gUs, a.gU);
+    }
   }
   return (int)cudaGetLastError();
 }

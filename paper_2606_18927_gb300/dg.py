@@ -95,6 +95,7 @@ def lib():
         "dg_get_metrics": (c_int, [vp, dp, dp]),
         "dg_time_derivative_noalloc": (c_int, [vp, vp, vp]),
         "dg_vjp": (c_int, [vp, vp, vp, vp, vp]),
+        "dg_vjp_phase": (c_int, [vp, c_int, vp, vp, vp, vp]),
         "dg_set_params": (c_int, [vp, c_double, c_double]),
         "dg_set_wall_solve_limit": (c_int, [vp, c_int]),
         "dg_wall_shear": (c_int, [vp, vp, dp]),
@@ -335,6 +336,16 @@ class Operator:
         pu = _ptr(U)[0] if U is not None else None
         pt = _ptr(gtheta)[0] if gtheta is not None else None
         self._check(lib().dg_vjp(self.h, pu, pl, pg, pt))
+        return gU
+
+    def vjp_phase(self, phase, lam, gU, U=None, gtheta=None):
+        """One phase (1-4) of the adjoint of a partitioned context (dg_vjp_phase)."""
+        for a in (lam, gU, U):
+            if a is not None and a.numel() != self.numel:
+                raise ValueError("array has the wrong size for this mesh")
+        pu = _ptr(U)[0] if U is not None else None
+        pt = _ptr(gtheta)[0] if gtheta is not None else None
+        self._check(lib().dg_vjp_phase(self.h, int(phase), pu, _ptr(lam)[0], _ptr(gU)[0], pt))
         return gU
 
     def set_params(self, kappa, B):

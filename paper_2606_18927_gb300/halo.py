@@ -5,7 +5,9 @@ rank and GPU, with the face data of the subdomain boundaries exchanged).
 The library evaluates a partitioned context in three phases (``dg.h``):
 phase 1 packs the state traces of the halo faces, phase 2 runs the lifting
 and packs the viscous-flux traces, phase 4 evaluates the face fluxes and the
-volume kernel.  Between them every rank sends each peer the rows of the
+volume kernel.  Its adjoint runs in four phases around three exchanges
+(state traces; the cotangents of the viscous-flux traces; the cotangents of
+the state traces).  Between them every rank sends each peer the rows of the
 faces they share; both ranks list those faces in the same order, so the
 exchange is a block copy per peer.
 
@@ -128,6 +130,31 @@ class LocalRanks:
                 self._move(*move)
         for idx, Ul, Utl in loc:
             Ut[:, idx, :] = Utl
+
+    def vjp(self, lam, gU, U, gtheta=None):
+        """gU <- (dUt/dU)^T lam over the whole mesh (device tensors [5][K][n^3]),
+        gtheta (device tensor of 2) <- (dUt/d(kappa, B))^T lam summed over the
+        ranks: the four adjoint phases with the three exchanges between them
+        (state traces; cotangents of the viscous-flux traces; cotangents of the
+        state traces)."""
+        import torch
+        loc = []
+        for r, op in enumerate(self.ops):
+            idx = torch.as_tensor(self.l2g[r], device=U.device, dtype=torch.long)
+            loc.append((idx, U[:, idx, :].contiguous(), lam[:, idx, :].contiguous(),
+                        torch.empty((5, len(idx), U.shape[2]), dtype=U.dtype, device=U.device),
+                        torch.zeros(2, dtype=U.dtype, device=U.device)))
+        for phase, move in ((1, ("send_U", "recv_U")), (2, ("send_G", "recv_G")), (3, ("send_U", "recv_U")),
+                            (4, None)):
+            for (idx, Ul, laml, gl, th), op in zip(loc, self.ops):
+                op.vjp_phase(phase, laml, gl, Ul, th)
+            if move:
+                self._move(*move)
+        for idx, Ul, laml, gl, th in loc:
+            gU[:, idx, :] = gl
+        if gtheta is not None:
+            gtheta.copy_(sum(th for *_, th in loc))
+        return gU
 
     def check_status(self):
         for op in self.ops:

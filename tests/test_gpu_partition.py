@@ -166,3 +166,100 @@ def test_fused_calls_refuse_partitioned_contexts():
     with pytest.raises(dg.DGError) as ei:
         op.vjp(torch.ones_like(Ul), torch.empty_like(Ul), U=Ul)
     assert ei.value.code in (-1, -8)
+
+
+def _vjp_compare(torch, ora, spec, phys, P, X=None, nbr=None, U=None, nbr_face=None, orient=None, law=1, **opts):
+    """The partitioned adjoint (four phases, three exchanges) against dg_vjp
+    on the unpartitioned mesh, and a dot product against the extended
+    oracle's forward-mode derivative."""
+    if X is None:
+        X, nbr, U = _setup(spec, phys)
+    Ud = torch.from_numpy(U).cuda()
+    lam = torch.from_numpy(I.random_direction(U.shape, seed=51)).cuda()
+    g = dg.Operator(spec.N, X, nbr, phys, nbr_face=nbr_face, orient=orient, law=law, **opts)
+    ref = torch.empty_like(Ud)
+    th_ref = torch.zeros(2, dtype=torch.float64, device="cuda")
+    g.vjp(lam, ref, Ud, th_ref)
+    g.check_status()
+    ranks = halo.LocalRanks(spec.N, X, nbr, phys, P, nbr_face=nbr_face, orient=orient, law=law, **opts)
+    assert sum(len(h) for h in ranks.halo) > 0
+    out = torch.empty_like(Ud)
+    th = torch.zeros(2, dtype=torch.float64, device="cuda")
+    ranks.vjp(lam, out, Ud, th)
+    ranks.check_status()
+    torch.cuda.synchronize()
+    a = out.cpu().numpy(); b = ref.cpu().numpy()
+    e = parity(a, b)
+    print("  partitioned VJP vs unpartitioned", e, "gtheta", th.cpu().numpy(), th_ref.cpu().numpy())
+    assert e <= 1e-13
+    thr = th_ref.cpu().numpy()
+    assert np.all(np.abs(th.cpu().numpy() - thr) <= 1e-12 * np.abs(thr).max() + 1e-300)
+    o = ora.Oracle(spec.N, X, nbr, phys, vol_flux=opts.get("vol_flux", 0), surf_flux=opts.get("surf_flux", 1),
+                   viscous=opts.get("viscous", 1), law=law, extended=True, nbr_face=nbr_face, orient=orient)
+    d = I.random_direction(U.shape, seed=52) * np.abs(U)
+    _, Jd = o.jvp(U, d)
+    lm = lam.cpu().numpy()
+    x = float((lm * Jd).sum()); y = float((a * d).sum())
+    print("  dot", x, y)
+    assert abs(x - y) <= 1e-11 * np.abs(lm * Jd).sum()
+    ranks.close(); g.close()
+
+
+@pytest.mark.parametrize("P", [2, 3])
+def test_partitioned_adjoint_taylor_green(ora, P):
+    torch = torch_cuda()
+    phys = I.phys_params(Ma=0.3, Re=200.0)
+    _vjp_compare(torch, ora, I.BoxSpec(3, 4, 3, 2, geometry="sine", amplitude=0.2), phys, P, surf_flux=2)
+
+
+def test_partitioned_adjoint_production_scheme_with_boundaries(ora):
+    torch = torch_cuda()
+    phys = I.phys_params(Ma=0.3, Re=400.0, sutherland=True)
+    g0, p0 = phys["gamma"], phys["p0"]
+    phys.update(U_in=np.array([1.0, 0.5, 0.0, 0.0, p0 / (g0 - 1) + 0.125]), p_out=0.99 * p0)
+    spec = I.BoxSpec(4, 5, 2, 3, geometry="sine", amplitude=0.1, periodic=(False, True, True),
+                     boundary=((I.INFLOW, I.OUTFLOW), (I.WALL, I.WALL), (I.WALL, I.WALL)))
+    _vjp_compare(torch, ora, spec, phys, 3, vol_flux=dg.VOL_EC_CHANDRASHEKAR, surf_flux=2)
+
+
+@pytest.mark.parametrize("P", [2, 4])
+def test_partitioned_adjoint_wall_modelled_channel(ora, P):
+    torch = torch_cuda()
+    wl = I.workload("channel_n5", N=3, elems=(8, 4, 4))
+    X, nbr, _ = _setup(wl.spec, wl.phys)
+    U = I.channel_profile(X, wl.phys)
+    _vjp_compare(torch, ora, wl.spec, wl.phys, P, X=X, nbr=nbr, U=U, surf_flux=2)
+
+
+def test_partitioned_adjoint_refusals():
+    torch = torch_cuda()
+    phys = I.phys_params()
+    spec = I.BoxSpec(2, 4, 2, 2)
+    X, nbr, U = _setup(spec, phys)
+    ranks = halo.LocalRanks(spec.N, X, nbr, phys, 2)
+    op = ranks.ops[0]
+    Ul = torch.from_numpy(halo.local_state(U, ranks.l2g[0])).cuda()
+    for bad in (0, 5):
+        with pytest.raises(dg.DGError) as ei:
+            op.vjp_phase(bad, torch.ones_like(Ul), torch.empty_like(Ul), Ul)
+        assert ei.value.code == -1
+    g = dg.Operator(spec.N, X, nbr, phys)
+    Ud = torch.from_numpy(U).cuda()
+    with pytest.raises(dg.DGError) as ei:
+        g.vjp_phase(2, torch.ones_like(Ud), torch.empty_like(Ud), Ud)
+    assert ei.value.code == -1
+    ranks.close(); g.close()
+
+
+@pytest.mark.parametrize("P", [2, 3])
+def test_partitioned_adjoint_rotated_mesh(ora, P):
+    """General conforming connectivity: the cotangent traces cross in the
+    master's face-node order like the state traces."""
+    from helpers import rotated_mesh
+    torch = torch_cuda()
+    phys = I.phys_params(Ma=0.1, Re=1600.0)
+    spec = I.BoxSpec(3, 4, 3, 3, geometry="sine", amplitude=0.15)
+    x, w, D = ora.lgl(3)
+    X, nbr, nf, ori, rots = rotated_mesh(spec, x, seed=11)
+    U = I.perturb(tgv_with_offset(X, phys, offset=(0.3, 0.1, 0.05)), rel=1e-3)
+    _vjp_compare(torch, ora, spec, phys, P, X=X, nbr=nbr, U=U, nbr_face=nf, orient=ori, surf_flux=2)
