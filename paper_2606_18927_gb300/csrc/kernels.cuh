@@ -194,22 +194,9 @@ __device__ __forceinline__ NbrNode<N> neighbour_node(const M& m, int e, int l, i
   return NbrNode<N>{chk_idx(fc.z, m.K, m.status), fc.w & 7, omap_ab<N>(fc.w >> 3, ab)};
 }
 
-// 1/x for x > 0 in double: an FP32 estimate refined by two Newton steps
-// (relative error ~1e-7 -> 1e-14 -> below 1 ulp), 4 FP64 FMAs instead of
-// the IEEE division sequence (GB300 issues 2 FP64 operations per clock per SM).
-__device__ __forceinline__ double rcp_pos(double x) {
-  double r = (double)__frcp_rn((float)x);
-  r = fma(r, fma(-x, r, 1.0), r);
-  r = fma(r, fma(-x, r, 1.0), r);
-  return r;
-}
-
+// (1/x for x > 0: rcp_t, defined after the FP64 <-> FP32 conversions below)
 template <typename R>
 __device__ __forceinline__ R rcp_t(R x);
-template <>
-__device__ __forceinline__ double rcp_t<double>(double x) { return rcp_pos(x); }
-template <>
-__device__ __forceinline__ float rcp_t<float>(float x) { return __frcp_rn(x); }
 
 // Dynamic viscosity at temperature T: constant mu, or Sutherland's law
 // mu_ref (T / T_ref)^(3/2) (T_ref + S) / (T + S) (the paper's Sec. 4 gas model).
@@ -327,6 +314,45 @@ __device__ __forceinline__ float d2f_bits(double d, float* rem = nullptr) {
   }
   return __uint_as_float(s | bits);
 }
+
+// 1/x for x > 0 in double (in the FP32 normal range): the FP32 reciprocal of
+// x rounded to FP32, refined by two Newton steps (relative error ~1e-7 ->
+// 1e-14 -> below 1 ulp), 4 FP64 FMAs instead of the IEEE division sequence
+// (GB300 issues 2 FP64 operations per clock per SM); the conversions are
+// built from the bit patterns (the same values as the conversion
+// instructions, without their FP64-pipe slots).
+__device__ __forceinline__ double rcp_pos(double x) {
+  double r = f2d_bits(__frcp_rn(d2f_bits(x)));
+  r = fma(r, fma(-x, r, 1.0), r);
+  r = fma(r, fma(-x, r, 1.0), r);
+  return r;
+}
+
+template <>
+__device__ __forceinline__ double rcp_t<double>(double x) { return rcp_pos(x); }
+template <>
+__device__ __forceinline__ float rcp_t<float>(float x) { return __frcp_rn(x); }
+
+// sqrt(x) for x > 0 in the FP32 normal range: s = x r with r the FP32
+// reciprocal square root of x rounded to FP32 (relative error d ~ 2^-22),
+// then two Newton steps s <- s + (x - s^2) r / 2, each taking the relative
+// error e to about -d e - e^2 / 2 (d -> 1.5 d^2 ~ 1e-13 -> ~1e-20, below
+// the final rounding): 5 FP64 operations
+__device__ __forceinline__ double sqrt_pos(double x) {
+  const float rf = rsqrtf(d2f_bits(x));
+  const double r = f2d_bits(rf), hr = f2d_bits(0.5f * rf);
+  double s = x * r;
+  s = fma(fma(-s, s, x), hr, s);
+  s = fma(fma(-s, s, x), hr, s);
+  return s;
+}
+
+template <typename R>
+__device__ __forceinline__ R sqrt_t(R x);
+template <>
+__device__ __forceinline__ double sqrt_t<double>(double x) { return sqrt_pos(x); }
+template <>
+__device__ __forceinline__ float sqrt_t<float>(float x) { return sqrtf(x); }
 
 // Primitive state in the flux type.  p is recovered in double from the
 // double state (p = (gamma-1)(E - rho |u|^2 / 2) cancels at low Mach number)
@@ -593,7 +619,7 @@ __device__ __forceinline__ void riemann_dissipation(const PhysDev& ph, const Pri
   const R pref = cR<R>(ph.p_ref, ph.f32c.p_ref);
   const R g = cR<R>(ph.gamma, ph.f32c.gamma);
   if (ph.surf_flux == 1) {  // local Lax-Friedrichs (sound speed from the full pressure)
-    const R cA = sqrt(g * (A.p + pref) / A.rho), cB = sqrt(g * (B.p + pref) / B.rho);
+    const R cA = sqrt_t<R>(g * (A.p + pref) * rcp_t<R>(A.rho)), cB = sqrt_t<R>(g * (B.p + pref) * rcp_t<R>(B.rho));
     const R lA = fabs(A.u * nx + A.v * ny + A.w * nz) + cA;
     const R lB = fabs(B.u * nx + B.v * ny + B.w * nz) + cB;
     const R lam = R(0.5) * (lA >= lB ? lA : lB);
@@ -602,14 +628,14 @@ __device__ __forceinline__ void riemann_dissipation(const PhysDev& ph, const Pri
   } else if (ph.surf_flux == 2) {  // Roe with Harten's entropy fix on the acoustic waves
     // (reciprocals by rcp_t: in FP64 a Newton-refined estimate, the FP64
     // pipe being the bound; the correctly rounded reciprocal in FP32)
-    const R sA = sqrt(A.rho), sB = sqrt(B.rho);
+    const R sA = sqrt_t<R>(A.rho), sB = sqrt_t<R>(B.rho);
     const R is = rcp_t<R>(sA + sB);
     const R rt = sA * sB;
     const R u = (sA * A.u + sB * B.u) * is, v = (sA * A.v + sB * B.v) * is, w = (sA * A.w + sB * B.w) * is;
     const R H = (sA * A.h + sB * B.h) * is;
     const R q2 = u * u + v * v + w * w;
     const R c2 = (g - R(1)) * (H - R(0.5) * q2);
-    const R c = sqrt(c2);
+    const R c = sqrt_t<R>(c2);
     const R un = u * nx + v * ny + w * nz;
     const R dr = drho ? *drho : B.rho - A.rho, dp = B.p - A.p;
     // (the FP32 difference form passes the velocity jump from the velocities'
