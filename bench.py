@@ -379,6 +379,8 @@ def run_ours(args):
     free0 = torch.cuda.mem_get_info()[0]
     op = dg.Operator(wl.spec.N, X, nbr, wl.phys, precision=precision, vol_flux=wl.vol_flux,
                      surf_flux=wl.surf_flux, viscous=wl.viscous, law=wl.law, stream=stream)
+    if args.lifting == "df":
+        op.set_lifting_arithmetic(1)
     op.set_state(Ud)
     footprint = free0 - torch.cuda.mem_get_info()[0]
     dofs = wl.spec.dofs
@@ -518,6 +520,8 @@ def main():
                     help="element counts of a smaller case of the same workload (profiling)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--lifting", choices=["fp64", "df"], default="fp64",
+                    help="arithmetic of the FP64 form's lifting kernel at N = 7 (df: double-float)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the FP32-mixed and VJP measurements appended to the line")
     args = ap.parse_args()

@@ -268,6 +268,16 @@ int dg_vjp_phase(dg_ctx* c, int phase, const double* U, const double* lam, doubl
 /* Sets the wall-law constants (kappa, B) used by later calls (Sec. 3.2). */
 int dg_set_params(dg_ctx* c, double kappa, double B);
 
+/* Arithmetic of the FP64 viscous form's lifting kernel at N = 7 (BR1
+ * lifting, viscous flux, weak viscous divergence): mode 0 FP64 (the
+ * default), 1 double-float (each value an unevaluated sum of two floats, the
+ * operations built from error-free transformations on the FP32 pipe, about
+ * 2^-47 relative rounding per operation; the state, the primitives, the
+ * metric products and the kernel's outputs stay FP64, the temperature is
+ * lifted relative to p_ref / (rho_ref R)).  Other degrees and forms ignore
+ * it.  DG_ERR_ARG for another mode.  Used by later calls. */
+int dg_set_lifting_arithmetic(dg_ctx* c, int mode);
+
 /* Iteration cap of the wall model's law-of-the-wall solve (SolveWallStress,
  * Sec. 3.2 Algorithms 1-2): bracket growth and Newton steps together, at
  * most max_iter evaluations of the law per wall node (default 200; the

@@ -444,6 +444,7 @@ int dg_init_mesh(dg_ctx** out, const dg_mesh_desc* m, const dg_phys* p, const dg
   ph.p_out = p->p_out;
   ph.T_wall = p->T_wall;
   ph.wm_maxit = kWallSolveMaxIter;
+  ph.lift_df = 0;
   ph.sutherland = ph.suth_S > 0.0 ? 1 : 0;
   ph.fs_diff = (o->precision == DG_FP32_MIXED && o->vol_flux == DG_VOL_KEP_PIROZZOLI) ? 1 : 0;
   ph.has_force = (ph.f[0] != 0.0 || ph.f[1] != 0.0 || ph.f[2] != 0.0) ? 1 : 0;
@@ -812,6 +813,14 @@ int dg_set_params(dg_ctx* c, double kappa, double B) {
   c->phys.kappa = kappa; c->phys.B = B;
   c->ph.kappa = kappa; c->ph.B = B;
   drop_step_graph(c);  // a captured step holds the old constants
+  return DG_OK;
+}
+
+int dg_set_lifting_arithmetic(dg_ctx* c, int mode) {
+  if (!c) return DG_ERR_ARG;
+  if (mode != 0 && mode != 1) return fail(c, DG_ERR_ARG, "dg_set_lifting_arithmetic: mode must be 0 or 1");
+  c->ph.lift_df = mode;
+  drop_step_graph(c);
   return DG_OK;
 }
 

@@ -72,6 +72,7 @@ struct PhysDev {
   double U_in[5], p_out;      // inflow state (conservative) and outflow pressure
   double T_wall;              // isothermal wall temperature (<= 0: adiabatic walls)
   int wm_maxit;               // iteration cap of the law-of-the-wall solve (bracket growth + Newton)
+  int lift_df;                // FP64 viscous form at N = 7: lifting in double-float arithmetic (k_lift_df)
   // FP32 copies of the constants the FP32 kernels use (a double-to-float
   // conversion is an FP64-pipe instruction)
   struct {
@@ -126,7 +127,9 @@ struct Tables {
   double Dvisc[(N + 1) * (N + 1)];  // (w_m / w_i) D_mi
   double iw[N + 1];                 // 1 / w
   float D32[(N + 1) * (N + 1)];     // D and Dvisc rounded to FP32 (kernel-parameter
-  float Dvisc32[(N + 1) * (N + 1)]; // operands of the FP32 line contractions)
+  float Dvisc32[(N + 1) * (N + 1)]; // operands of the FP32 line contractions) and
+  float D32lo[(N + 1) * (N + 1)];   // their rounding remainders (the double-float
+  float Dvisc32lo[(N + 1) * (N + 1)];  // lifting's coefficients hi + lo)
 };
 
 // Node slot in shared memory of the FP32 lifting kernel at N = 7 (node index
@@ -1173,6 +1176,73 @@ struct LineEO {
 // ---------------------------------------------------------------------------
 // k_lift: one CTA of n^3 threads per element.
 // ---------------------------------------------------------------------------
+// 2 (W* - W) of the BR1 lifting at node ab of face l of element e (own
+// node q, own values Wo in the lifted form): the neighbour's trace (interior
+// and halo faces), the exterior state (inflow / outflow) or the mirror state
+// (slip wall)
+template <int N, typename R>
+__device__ __forceinline__ void lift_face_jump(const double* __restrict__ U, const MeshDev<R>& m, const PhysDev& ph,
+                                               size_t S, int e, int l, int ab, int q, int nb, R Wo0, R Wo1, R Wo2,
+                                               R Wo3, R dd[4]) {
+  constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
+  R d0, d1, d2, d3;
+  if (nb >= 0) {
+    const NbrNode<N> nn = neighbour_node<N>(m, e, l, ab);
+    const size_t gn = (size_t)nn.e * n3 + fnode<N>(nn.l, nn.ab % n, nn.ab / n);
+    R u, v, w, T;
+    if constexpr (std::is_same<R, float>::value) {
+      velocity_temperature32s(load_prim32(m.W32, S, gn), ph, u, v, w, T);
+    } else if (m.W64) {
+      u = m.W64[S + gn]; v = m.W64[2 * S + gn]; w = m.W64[3 * S + gn]; T = m.W64[6 * S + gn];
+    } else {
+      velocity_temperature<R>(U[gn], U[S + gn], U[2 * S + gn], U[3 * S + gn], U[4 * S + gn], ph, u, v, w, T);
+    }
+    d0 = u - Wo0; d1 = v - Wo1; d2 = w - Wo2; d3 = T - Wo3;
+  } else if (nb <= -16) {
+    // halo face: the remote element's trace from the halo buffer (in the
+    // master's face-node order)
+    const int abm = omap_ab<N>((m.elem_face[e * 6 + l] >> 1) & 7, ab);
+    const double* src = m.halo_U + (size_t)chk_idx(-16 - nb, m.n_halo, m.status) * 5 * n2 + abm;
+    R u, v, w, T;
+    if constexpr (std::is_same<R, double>::value) {
+      if (m.W64) {
+        // as the remote element's stored primitives (same function)
+        const Prim<double> q = primitive_T(src[0], src[n2], src[2 * n2], src[3 * n2], src[4 * n2], ph, T);
+        u = q.u; v = q.v; w = q.w;
+      } else {
+        velocity_temperature<R>(src[0], src[n2], src[2 * n2], src[3 * n2], src[4 * n2], ph, u, v, w, T);
+      }
+    } else {
+      velocity_temperature32s_of(src[0], src[n2], src[2 * n2], src[3 * n2], src[4 * n2], ph, u, v, w, T);
+    }
+    d0 = u - Wo0; d1 = v - Wo1; d2 = w - Wo2; d3 = T - Wo3;
+  } else if (nb != -1) {
+    // inflow / outflow: 2 (W* - W) = W(exterior) - W
+    const size_t gq = (size_t)e * n3 + q;
+    double Ui[5], Ub[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) Ui[v] = U[v * S + gq];
+    ghost_state(ph, nb, Ui, Ub);
+    R u, v, w, T;
+    if constexpr (std::is_same<R, float>::value)
+      velocity_temperature32s_of(Ub[0], Ub[1], Ub[2], Ub[3], Ub[4], ph, u, v, w, T);
+    else
+      velocity_temperature<R>(Ub[0], Ub[1], Ub[2], Ub[3], Ub[4], ph, u, v, w, T);
+    d0 = u - Wo0; d1 = v - Wo1; d2 = w - Wo2; d3 = T - Wo3;
+  } else {
+    // mirror: 2 (W* - W) = -2 (u . n) n, T unchanged (n: own outward unit normal)
+    const size_t gq = (size_t)e * n3 + q;
+    const int dir = l >> 1;
+    const R a0 = m.Ja[(size_t)(dir * 3 + 0) * S + gq], a1 = m.Ja[(size_t)(dir * 3 + 1) * S + gq],
+            a2 = m.Ja[(size_t)(dir * 3 + 2) * S + gq];
+    const R is = R(1) / sqrt(a0 * a0 + a1 * a1 + a2 * a2);
+    const R nx = a0 * is, ny = a1 * is, nz = a2 * is;  // sign irrelevant: (u.n) n
+    const R un2 = R(-2) * (Wo0 * nx + Wo1 * ny + Wo2 * nz);
+    d0 = un2 * nx; d1 = un2 * ny; d2 = un2 * nz; d3 = R(0);
+  }
+  dd[0] = d0; dd[1] = d1; dd[2] = d2; dd[3] = d3;
+}
+
 // Resident CTAs per SM asked of the register allocator for the lifting
 // kernel: two for CTAs of up to 512 threads, three for the FP32 kernel at
 // N = 7 (42 registers; its line phases leave the other threads waiting at a
@@ -1256,61 +1326,9 @@ k_lift(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
     const int nb = m.nbr[e * 6 + l];
     const int sq = ws(q);
     const R Wo0 = sW[sq], Wo1 = sW[n3 + sq], Wo2 = sW[2 * n3 + sq], Wo3 = sW[3 * n3 + sq];
-    R d0, d1, d2, d3;
-    if (nb >= 0) {
-      const NbrNode<N> nn = neighbour_node<N>(m, e, l, ab);
-      const size_t gn = (size_t)nn.e * n3 + fnode<N>(nn.l, nn.ab % n, nn.ab / n);
-      R u, v, w, T;
-      if constexpr (std::is_same<R, float>::value) {
-        velocity_temperature32s(load_prim32(m.W32, S, gn), ph, u, v, w, T);
-      } else if (m.W64) {
-        u = m.W64[S + gn]; v = m.W64[2 * S + gn]; w = m.W64[3 * S + gn]; T = m.W64[6 * S + gn];
-      } else {
-        velocity_temperature<R>(U[gn], U[S + gn], U[2 * S + gn], U[3 * S + gn], U[4 * S + gn], ph, u, v, w, T);
-      }
-      d0 = u - Wo0; d1 = v - Wo1; d2 = w - Wo2; d3 = T - Wo3;
-    } else if (nb <= -16) {
-      // halo face: the remote element's trace from the halo buffer (in the
-      // master's face-node order)
-      const int abm = omap_ab<N>((m.elem_face[e * 6 + l] >> 1) & 7, ab);
-      const double* src = m.halo_U + (size_t)chk_idx(-16 - nb, m.n_halo, m.status) * 5 * n2 + abm;
-      R u, v, w, T;
-      if constexpr (std::is_same<R, double>::value) {
-        if (m.W64) {
-          // as the remote element's stored primitives (same function)
-          const Prim<double> q = primitive_T(src[0], src[n2], src[2 * n2], src[3 * n2], src[4 * n2], ph, T);
-          u = q.u; v = q.v; w = q.w;
-        } else {
-          velocity_temperature<R>(src[0], src[n2], src[2 * n2], src[3 * n2], src[4 * n2], ph, u, v, w, T);
-        }
-      } else {
-        velocity_temperature32s_of(src[0], src[n2], src[2 * n2], src[3 * n2], src[4 * n2], ph, u, v, w, T);
-      }
-      d0 = u - Wo0; d1 = v - Wo1; d2 = w - Wo2; d3 = T - Wo3;
-    } else if (nb != -1) {
-      // inflow / outflow: 2 (W* - W) = W(exterior) - W
-      const size_t gq = (size_t)e * n3 + q;
-      double Ui[5], Ub[5];
-#pragma unroll
-      for (int v = 0; v < 5; ++v) Ui[v] = U[v * S + gq];
-      ghost_state(ph, nb, Ui, Ub);
-      R u, v, w, T;
-      if constexpr (std::is_same<R, float>::value)
-        velocity_temperature32s_of(Ub[0], Ub[1], Ub[2], Ub[3], Ub[4], ph, u, v, w, T);
-      else
-        velocity_temperature<R>(Ub[0], Ub[1], Ub[2], Ub[3], Ub[4], ph, u, v, w, T);
-      d0 = u - Wo0; d1 = v - Wo1; d2 = w - Wo2; d3 = T - Wo3;
-    } else {
-      // mirror: 2 (W* - W) = -2 (u . n) n, T unchanged (n: own outward unit normal)
-      const size_t gq = (size_t)e * n3 + q;
-      const int dir = l >> 1;
-      const R a0 = m.Ja[(size_t)(dir * 3 + 0) * S + gq], a1 = m.Ja[(size_t)(dir * 3 + 1) * S + gq],
-              a2 = m.Ja[(size_t)(dir * 3 + 2) * S + gq];
-      const R is = R(1) / sqrt(a0 * a0 + a1 * a1 + a2 * a2);
-      const R nx = a0 * is, ny = a1 * is, nz = a2 * is;  // sign irrelevant: (u.n) n
-      const R un2 = R(-2) * (Wo0 * nx + Wo1 * ny + Wo2 * nz);
-      d0 = un2 * nx; d1 = un2 * ny; d2 = un2 * nz; d3 = R(0);
-    }
+    R dd[4];
+    lift_face_jump<N, R>(U, m, ph, S, e, l, ab, q, nb, Wo0, Wo1, Wo2, Wo3, dd);
+    const R d0 = dd[0], d1 = dd[1], d2 = dd[2], d3 = dd[3];
     sC[(l * 4 + 0) * n2 + ab] = d0; sC[(l * 4 + 1) * n2 + ab] = d1;
     sC[(l * 4 + 2) * n2 + ab] = d2; sC[(l * 4 + 3) * n2 + ab] = d3;
   }

@@ -1,0 +1,291 @@
+// BR1 lifting, viscous flux and weak viscous divergence of the FP64 operator
+// at N = 7 in double-float arithmetic: every FP64 value of the kernel is an
+// unevaluated sum hi + lo of two floats, and the arithmetic is built from
+// error-free transformations on the FP32 pipe (which on GB300 issues 64 times
+// as many lanes per clock as the FP64 pipe):
+//   TwoSum (Knuth): s = a + b, e = (a - (s - b')) + (b - b'), b' = s - a;
+//   TwoProd by FMA: p = a b, e = fma(a, b, -p);
+//   products of two double-floats (Dekker's product with the cross terms
+//   a_hi b_lo + a_lo b_hi folded into the FMA), and sums of products
+//   accumulated as in Ogita, Rump and Oishi's Dot2 (the high parts by
+//   TwoSum, every rounding error and low part into a second float).
+// The relative rounding of a double-float operation is about 2^-47 against
+// FP64's 2^-53.  The viscous terms are a small part of Ut (1/Re), so their
+// rounding at that level stays far below the operator's FP64 parity bound;
+// the temperature is lifted relative to T_ref = p_ref / (rho_ref R) (its
+// gradient is the same) so that no O(T) value is rounded.  The inviscid
+// volume term, whose rounding the derivative amplifies against Ut, stays in
+// FP64.
+#pragma once
+
+#include "kernels.cuh"
+
+namespace dg {
+
+struct DFl {
+  float hi, lo;
+};
+
+__device__ __forceinline__ DFl df_of(double x) {
+  float lo;
+  const float hi = d2f_bits(x, &lo);
+  return DFl{hi, lo};
+}
+
+__device__ __forceinline__ double df_to(DFl a) { return f2d_bits(a.hi) + f2d_bits(a.lo); }
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// (s, t) with |t| small against |s|: the nearest float and the remainder
+__device__ __forceinline__ DFl df_norm(float s, float t) {
+  const float h = __fadd_rn(s, t);
+  return DFl{h, __fsub_rn(t, __fsub_rn(h, s))};
+}
+
+__device__ __forceinline__ DFl df_add(DFl a, DFl b) {
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  return df_norm(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+}
+
+__device__ __forceinline__ DFl df_neg(DFl a) { return DFl{-a.hi, -a.lo}; }
+__device__ __forceinline__ DFl df_sub(DFl a, DFl b) { return df_add(a, df_neg(b)); }
+
+__device__ __forceinline__ DFl df_mul(DFl a, DFl b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return df_norm(p, e);
+}
+
+// sum of products: s the TwoSum-exact sum of the products' high parts, t the
+// rest (product errors, cross terms, the sums' errors)
+struct DFAcc {
+  float s, t;
+};
+
+__device__ __forceinline__ void acc_fma(DFAcc& A, DFl c, DFl x) {
+  const float p = __fmul_rn(c.hi, x.hi);
+  float e = __fmaf_rn(c.hi, x.hi, -p);
+  e = __fmaf_rn(c.hi, x.lo, e);
+  e = __fmaf_rn(c.lo, x.hi, e);
+  float s, r;
+  two_sum(A.s, p, s, r);
+  A.s = s;
+  A.t = __fadd_rn(A.t, __fadd_rn(e, r));
+}
+
+__device__ __forceinline__ void acc_add(DFAcc& A, DFl x) {
+  float s, r;
+  two_sum(A.s, x.hi, s, r);
+  A.s = s;
+  A.t = __fadd_rn(A.t, __fadd_rn(x.lo, r));
+}
+
+__device__ __forceinline__ DFl acc_val(const DFAcc& A) { return df_norm(A.s, A.t); }
+
+__device__ __forceinline__ DFl dot3(DFl a0, DFl b0, DFl a1, DFl b1, DFl a2, DFl b2) {
+  DFAcc A{0.f, 0.f};
+  acc_fma(A, a0, b0);
+  acc_fma(A, a1, b1);
+  acc_fma(A, a2, b2);
+  return acc_val(A);
+}
+
+__device__ __forceinline__ DFl df_ld(const float2* p) {
+  const float2 v = *p;
+  return DFl{v.x, v.y};
+}
+__device__ __forceinline__ void df_st(float2* p, DFl a) { *p = make_float2(a.hi, a.lo); }
+
+// shared memory of k_lift_df (in float2): W 4 n3, face jumps 24 n2, G 12 n3
+template <int N>
+struct LiftDfShape {
+  static constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
+  static constexpr int SMEM_F2 = 16 * n3 + 24 * n2;
+};
+
+// One CTA of n^3 threads per element (N = 7): the roles of k_lift (own face
+// fluxes Gf and the weak divergence R_v, both FP64 in memory) with the line
+// contractions on two threads per line, two variables each, over the node
+// slots of lift_slot8.
+template <int N>
+__global__ void __launch_bounds__((N + 1) * (N + 1) * (N + 1), 1)
+k_lift_df(const double* __restrict__ U, const MeshDev<double> m, const PhysDev ph, const Tables<N> tab,
+          double* __restrict__ Rv, double* __restrict__ Gf) {
+  static_assert(N == 7, "the double-float lifting kernel is written for N = 7");
+  constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* sW = reinterpret_cast<float2*>(smem_raw);  // [4][n3] u, v, w, T - T_ref
+  float2* sC = sW + 4 * n3;                          // [6][4][n2] 2 (W* - W)
+  float2* sG = sC + 24 * n2;                         // [3][4][n3]
+  const int e = blockIdx.x, tid = threadIdx.x;
+  const int i = tid % n, j = (tid / n) % n, k = tid / n2;
+  const int p = tid;
+  const size_t S = (size_t)m.K * n3;
+  const size_t g = (size_t)e * n3 + p;
+  const double Tref = ph.rho_ref > 0.0 ? ph.p_ref * ph.rcp_R / ph.rho_ref : 0.0;
+  const int sp = lift_slot8(p);
+  // own primitives (stored by k_prim64)
+  {
+    df_st(&sW[sp], df_of(m.W64[S + g]));
+    df_st(&sW[n3 + sp], df_of(m.W64[2 * S + g]));
+    df_st(&sW[2 * n3 + sp], df_of(m.W64[3 * S + g]));
+    df_st(&sW[3 * n3 + sp], df_of(m.W64[6 * S + g] - Tref));
+  }
+  // 2 (W* - W) at the six faces, in FP64 from the stored primitives (the
+  // jumps are differences of nearby values: exact or nearly so), then split
+  for (int t = tid; t < 6 * n2; t += n3) {
+    const int l = t / n2, ab = t - l * n2, a = ab % n, b = ab / n;
+    const int q = fnode<N>(l, a, b);
+    const int nb = m.nbr[e * 6 + l];
+    const size_t gq = (size_t)e * n3 + q;
+    double dd[4];
+    lift_face_jump<N, double>(U, m, ph, S, e, l, ab, q, nb, m.W64[S + gq], m.W64[2 * S + gq], m.W64[3 * S + gq],
+                              m.W64[6 * S + gq], dd);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) df_st(&sC[(l * 4 + v) * n2 + ab], df_of(dd[v]));
+  }
+  __syncthreads();
+  // line contraction by thread tid < 6 n2: two variables (v0, v0 + 1) on line L of
+  // direction dir, y_q = sum_m C_qm x_m for the n nodes, in place or into dst
+  auto line_pass = [&](const float2* src, float2* dst, bool divergence) {
+    if (tid < 6 * n2) {
+      const int dir = tid / (2 * n2), r = tid - dir * 2 * n2, v0 = 2 * (r / n2), L = r % n2;
+      const int n0 = dir == 0 ? n * L : (dir == 1 ? (L % n) + n2 * (L / n) : L);
+      const int s0 = lift_slot8(n0);
+      int sl[n];
+#pragma unroll
+      for (int q = 0; q < n; ++q)
+        sl[q] = s0 ^ (dir == 0 ? lift_slot8(q) : (dir == 1 ? lift_slot8(q * n) : lift_slot8(q * n2)));
+      DFl x[2][n];
+#pragma unroll
+      for (int q = 0; q < n; ++q)
+#pragma unroll
+        for (int v = 0; v < 2; ++v)
+          x[v][q] = df_ld(&src[(divergence ? (dir * 4 + v0 + v) : (v0 + v)) * n3 + sl[q]]);
+#pragma unroll
+      for (int q = 0; q < n; ++q)
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+          DFAcc A{0.f, 0.f};
+#pragma unroll
+          for (int mm = 0; mm < n; ++mm) {
+            const DFl c = divergence ? DFl{tab.Dvisc32[q * n + mm], tab.Dvisc32lo[q * n + mm]}
+                                     : DFl{tab.D32[q * n + mm], tab.D32lo[q * n + mm]};
+            acc_fma(A, c, x[v][mm]);
+          }
+          df_st(&dst[(dir * 4 + v0 + v) * n3 + sl[q]], acc_val(A));
+        }
+    }
+  };
+  // reference-space gradients
+  line_pass(sW, sG, false);
+  __syncthreads();
+  DFl dW[3][4];
+#pragma unroll
+  for (int dir = 0; dir < 3; ++dir)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) dW[dir][v] = df_ld(&sG[(dir * 4 + v) * n3 + sp]);
+  // surface corrections: sC holds 2 (W* - W), the weights are 1 / (2 w)
+  const DFl shw0 = df_of(0.5 * tab.iw[0]), shwN = df_of(0.5 * tab.iw[N]);
+  auto surf = [&](int dir, int l, int ab, DFl sw) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) dW[dir][v] = df_add(dW[dir][v], df_mul(sw, df_ld(&sC[(l * 4 + v) * n2 + ab])));
+  };
+  if (i == 0 || i == N) surf(0, i == 0 ? 0 : 1, j + n * k, i == 0 ? df_neg(shw0) : shwN);
+  if (j == 0 || j == N) surf(1, j == 0 ? 2 : 3, i + n * k, j == 0 ? df_neg(shw0) : shwN);
+  if (k == 0 || k == N) surf(2, k == 0 ? 4 : 5, i + n * j, k == 0 ? df_neg(shw0) : shwN);
+  // viscosity and conductivity (FP64, then split)
+  double mu_d = ph.mu, kc_d = ph.kcond;
+  if (ph.sutherland) {
+    mu_d = sutherland<double>(ph, m.W64[6 * S + g]);
+    kc_d = mu_d * ph.cp_Pr;
+  }
+  const DFl mu = df_of(mu_d), kc = df_of(kc_d), mu2 = df_of(2.0 * mu_d), mu23 = df_of(2.0 / 3.0 * mu_d);
+  // velocity gradients q[d][c] = sum_dir (Ja^dir_d / J) dW_dir and the
+  // contravariant temperature gradients hT[dir] = sum_m ((Ja^dir . Ja^m) / J) dT_m
+  DFl q[3][3], hT[3];
+  {
+    DFl jj[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) jj[c] = df_of(m.JaJ[(size_t)c * S + g]);
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) q[d][c] = dot3(jj[d], dW[0][c], jj[3 + d], dW[1][c], jj[6 + d], dW[2][c]);
+  }
+  {
+    DFl mm[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) mm[c] = df_of(m.Mj[(size_t)c * S + g]);
+    hT[0] = dot3(mm[0], dW[0][3], mm[3], dW[1][3], mm[4], dW[2][3]);
+    hT[1] = dot3(mm[3], dW[0][3], mm[1], dW[1][3], mm[5], dW[2][3]);
+    hT[2] = dot3(mm[4], dW[0][3], mm[5], dW[1][3], mm[2], dW[2][3]);
+  }
+  // stress tau_ab = mu (q_ba + q_ab) - (2/3) mu div delta_ab
+  DFl tau[3][3];
+  {
+    const DFl div = df_add(df_add(q[0][0], q[1][1]), q[2][2]);
+    const DFl mdiv = df_mul(mu23, div);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) tau[a][a] = df_sub(df_mul(mu2, q[a][a]), mdiv);
+    tau[0][1] = tau[1][0] = df_mul(mu, df_add(q[0][1], q[1][0]));
+    tau[0][2] = tau[2][0] = df_mul(mu, df_add(q[0][2], q[2][0]));
+    tau[1][2] = tau[2][1] = df_mul(mu, df_add(q[1][2], q[2][1]));
+  }
+  // contravariant viscous fluxes G^dir = sum_d Ja^dir_d Fv_d; energy row
+  // G^dir_E = sum_c u_c G^dir_c + k (Ja^dir . grad T)
+  DFl G[3][4];
+  {
+    const DFl uu = df_ld(&sW[sp]), vv = df_ld(&sW[n3 + sp]), ww = df_ld(&sW[2 * n3 + sp]);
+#pragma unroll
+    for (int dir = 0; dir < 3; ++dir) {
+      const DFl a0 = df_of(m.Ja[(size_t)(dir * 3 + 0) * S + g]), a1 = df_of(m.Ja[(size_t)(dir * 3 + 1) * S + g]),
+                a2 = df_of(m.Ja[(size_t)(dir * 3 + 2) * S + g]);
+#pragma unroll
+      for (int v = 0; v < 3; ++v) G[dir][v] = dot3(a0, tau[v][0], a1, tau[v][1], a2, tau[v][2]);
+      DFAcc A{0.f, 0.f};
+      acc_fma(A, uu, G[dir][0]);
+      acc_fma(A, vv, G[dir][1]);
+      acc_fma(A, ww, G[dir][2]);
+      acc_fma(A, kc, hT[dir]);
+      G[dir][3] = acc_val(A);
+    }
+  }
+  // own outward viscous flux at face nodes: Gf[e][l][v][ab] = +-G^{l/2}
+  auto gface = [&](int l, int ab, double sgn) {
+    double* dst = Gf + ((size_t)e * 6 + l) * 4 * n2 + ab;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) dst[v * n2] = sgn * df_to(G[l >> 1][v]);
+  };
+  if (i == 0) gface(0, j + n * k, -1.0);
+  if (i == N) gface(1, j + n * k, 1.0);
+  if (j == 0) gface(2, i + n * k, -1.0);
+  if (j == N) gface(3, i + n * k, 1.0);
+  if (k == 0) gface(4, i + n * j, -1.0);
+  if (k == N) gface(5, i + n * j, 1.0);
+  // weak-form viscous volume term R_v = sum_dir sum_m (w_m / w_i) D_mi G^dir_m
+  __syncthreads();  // the nodes have read their derivatives from sG
+#pragma unroll
+  for (int dir = 0; dir < 3; ++dir)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) df_st(&sG[(dir * 4 + v) * n3 + sp], G[dir][v]);
+  __syncthreads();
+  line_pass(sG, sG, true);  // in place: a line's slots belong to its thread
+  __syncthreads();
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    DFAcc A{0.f, 0.f};
+#pragma unroll
+    for (int dir = 0; dir < 3; ++dir) acc_add(A, df_ld(&sG[(dir * 4 + v) * n3 + sp]));
+    Rv[(size_t)v * S + g] = df_to(acc_val(A));
+  }
+}
+
+}  // namespace dg

@@ -6,6 +6,7 @@
 
 #include "adjoint.cuh"
 #include "kernels.cuh"
+#include "lift_df.cuh"
 #include "ops.h"
 
 namespace dg {
@@ -25,6 +26,8 @@ static Tables<N> make_tables(const double* D, const double* w) {
       t.Dvisc[i * n + m] = w[m] / w[i] * D[m * n + i];
       t.D32[i * n + m] = (float)t.D[i * n + m];
       t.Dvisc32[i * n + m] = (float)t.Dvisc[i * n + m];
+      t.D32lo[i * n + m] = (float)(t.D[i * n + m] - (double)t.D32[i * n + m]);
+      t.Dvisc32lo[i * n + m] = (float)(t.Dvisc[i * n + m] - (double)t.Dvisc32[i * n + m]);
     }
   }
   return t;
@@ -103,7 +106,19 @@ static int run_typed(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {
       const long long S = (long long)a.K * n3;
       k_prim64<<<(unsigned)std::min<long long>((S + 255) / 256, 152 * 16), 256, 0, s>>>(S, a.Uin, ph, m.W64);
     }
-    if (ph.viscous) k_lift<N, R><<<a.K, n3, smem_lift, s>>>(a.Uin, m, ph, tab, Rv, Gf);
+    if (ph.viscous) {
+      bool done = false;
+      if constexpr (N == 7 && std::is_same<R, double>::value) {
+        // the double-float lifting (it reads the stored primitives and metric products)
+        if (ph.lift_df && m.W64 && m.JaJ && m.Mj) {
+          const size_t smem_df = (size_t)LiftDfShape<N>::SMEM_F2 * sizeof(float2);
+          cudaFuncSetAttribute(k_lift_df<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_df);
+          k_lift_df<N><<<a.K, n3, smem_df, s>>>(a.Uin, m, ph, tab, Rv, Gf);
+          done = true;
+        }
+      }
+      if (!done) k_lift<N, R><<<a.K, n3, smem_lift, s>>>(a.Uin, m, ph, tab, Rv, Gf);
+    }
     if (a.ev) cudaEventRecord(a.ev[1], s);
     if (a.n_halo > 0 && a.send_G && ph.viscous)
       k_halo_pack<N, R><<<halo_blocks, 256, 0, s>>>(a.Uin, m, Gf, nullptr, static_cast<R*>(a.send_G));

@@ -98,6 +98,7 @@ def lib():
         "dg_vjp_phase": (c_int, [vp, c_int, vp, vp, vp, vp]),
         "dg_set_params": (c_int, [vp, c_double, c_double]),
         "dg_set_wall_solve_limit": (c_int, [vp, c_int]),
+        "dg_set_lifting_arithmetic": (c_int, [vp, c_int]),
         "dg_wall_shear": (c_int, [vp, vp, dp]),
         "dg_kinetic_energy": (c_int, [vp, vp, dp]),
         "dg_time_step": (c_int, [vp, vp, c_double, dp]),
@@ -350,6 +351,10 @@ class Operator:
 
     def set_params(self, kappa, B):
         self._check(lib().dg_set_params(self.h, float(kappa), float(B)))
+
+    def set_lifting_arithmetic(self, mode):
+        """0: FP64 lifting kernel; 1: double-float lifting (FP64 viscous form, N = 7)."""
+        self._check(lib().dg_set_lifting_arithmetic(self.h, int(mode)))
 
     def set_wall_solve_limit(self, max_iter):
         """Iteration cap of the wall model's law-of-the-wall solve (default 200)."""
