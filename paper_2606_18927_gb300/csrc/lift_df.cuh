@@ -115,7 +115,7 @@ struct LiftDfShape {
 // contractions on two threads per line, two variables each, over the node
 // slots of lift_slot8.
 template <int N>
-__global__ void __launch_bounds__((N + 1) * (N + 1) * (N + 1), 1)
+__global__ void __launch_bounds__((N + 1) * (N + 1) * (N + 1), 2)
 k_lift_df(const double* __restrict__ U, const MeshDev<double> m, const PhysDev ph, const Tables<N> tab,
           double* __restrict__ Rv, double* __restrict__ Gf) {
   static_assert(N == 7, "the double-float lifting kernel is written for N = 7");
