@@ -49,6 +49,10 @@ struct dg_ctx {
   bool w64_of_U = false;
   double* JaJ = nullptr;  // FP64 viscous: [9][S] Ja / J
   double* Mj = nullptr;   // FP64 viscous: [6][S] (Ja Ja^T) / J
+  // double-float lifting (N = 7, FP64 viscous): (hi, lo) pairs of Ja, Ja / J,
+  // (Ja Ja^T) / J [24][S] and of the lifted primitives [4][S]
+  float2* lift_M2 = nullptr;
+  float2* lift_W2 = nullptr;
   double* wm_t = nullptr;  // wall-law warm start per wall node (NaN: none yet)
   // partitioned meshes: halo buffers [n_halo][5][n2] (state traces, FP64) and
   // [n_halo][4][n2] (viscous-flux traces, flux type), received and sent
@@ -157,7 +161,8 @@ void free_all(dg_ctx* c) {
   void* ptrs[] = {c->U, c->dU, c->io, c->io2, c->Ja, c->invJ, c->fgeo, c->nbr, c->elem_face, c->faces,
                   c->ws_elem, c->ws_lag, c->Rv, c->Gf, c->Fs, c->tau, c->status,
                   c->gUf, c->gGf, c->gWf, c->gUs, c->gtheta, c->wq, c->ro_ckpt, c->ro_stage, c->ro_work,
-                  c->ro_scalar, c->wJ, c->W32, c->W64, c->JaJ, c->Mj, c->halo_U, c->send_U, c->halo_G, c->send_G,
+                  c->ro_scalar, c->wJ, c->W32, c->W64, c->JaJ, c->Mj, c->lift_M2, c->lift_W2, c->halo_U, c->send_U,
+                  c->halo_G, c->send_G,
                   c->wm_t};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -203,6 +208,7 @@ int launch(dg_ctx* c, const double* Uin, int mode, double* Out, double A, double
   a.W64 = c->W64;
   a.w64_valid = (c->W64 && !a.fp32 && Uin == c->U && c->w64_of_U) ? 1 : 0;
   a.JaJ = c->JaJ; a.Mj = c->Mj;
+  a.lift_M2 = c->lift_M2; a.lift_W2 = c->lift_W2;
   a.wm_t = c->wm_t;
   int rc = dg::run_operator(a, c->ph, c->stream);
   if (rc != 0) {
@@ -349,6 +355,7 @@ int noalloc_args(dg_ctx* c, const double* U, double* Ut, OpArgs* a, const PhysDe
   a->fp32 = c->opts.precision == DG_FP32_MIXED;
   a->Ja = c->Ja; a->invJ = c->invJ; a->fgeo = c->fgeo; a->nbr = c->nbr; a->elem_face = c->elem_face;
   a->JaJ = c->JaJ; a->Mj = c->Mj;  // geometry, owned by the context
+  a->lift_M2 = nullptr; a->lift_W2 = nullptr;  // (the FP64 lifting: no stored primitives here)
   a->faces = c->faces; a->ws_elem = c->ws_elem; a->ws_lag = c->ws_lag;
   a->D = c->geo.basis.D.data(); a->w = c->geo.basis.w.data();
   a->Uin = U; a->status = c->status;
@@ -819,7 +826,23 @@ int dg_set_params(dg_ctx* c, double kappa, double B) {
 int dg_set_lifting_arithmetic(dg_ctx* c, int mode) {
   if (!c) return DG_ERR_ARG;
   if (mode != 0 && mode != 1) return fail(c, DG_ERR_ARG, "dg_set_lifting_arithmetic: mode must be 0 or 1");
+  const bool applies = c->N == 7 && c->opts.precision == DG_FP64 && c->opts.viscous && c->JaJ && c->W64;
+  if (mode == 1 && applies && !c->lift_M2) {
+    // the metric arrays as (hi, lo) pairs, split once on the device
+    cudaError_t e = alloc(&c->lift_M2, 24 * c->S);
+    if (e == cudaSuccess) e = alloc(&c->lift_W2, 4 * c->S);
+    const long long S = (long long)c->S;
+    const unsigned blocks = (unsigned)std::min<long long>((9 * S + 255) / 256, 152 * 16);
+    if (e == cudaSuccess) {
+      dg::k_split_pairs<<<blocks, 256, 0, c->stream>>>(9 * S, static_cast<const double*>(c->Ja), c->lift_M2);
+      dg::k_split_pairs<<<blocks, 256, 0, c->stream>>>(9 * S, c->JaJ, c->lift_M2 + 9 * c->S);
+      dg::k_split_pairs<<<blocks, 256, 0, c->stream>>>(6 * S, c->Mj, c->lift_M2 + 18 * c->S);
+      e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "dg_set_lifting_arithmetic");
+  }
   c->ph.lift_df = mode;
+  c->w64_of_U = false;  // the next evaluation forms the stored primitives (and their pairs) again
   drop_step_graph(c);
   return DG_OK;
 }

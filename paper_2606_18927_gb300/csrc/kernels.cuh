@@ -116,6 +116,11 @@ struct MeshDev {
                          // per use)
   const double* JaJ;     // FP64 viscous form: [9][K*n3] Ja / J (dir*3+comp)
   const double* Mj;      // FP64 viscous form: [6][K*n3] (Ja Ja^T) / J (00, 11, 22, 01, 02, 12)
+  // double-float lifting: Ja, Ja / J and (Ja Ja^T) / J as (hi, lo) float pairs
+  // [24][K*n3], and the lifted primitives (u, v, w, T - T_ref) [4][K*n3]
+  // written by k_prim64 (null unless that lifting is selected)
+  const float2* lift_M2;
+  float2* lift_W2;
   double* wm_t;          // [n_wall*n2] last wall-law solution per wall node (warm start; may be null)
   int* status;           // device status flags (index checks of the bounds-checking build)
 };
@@ -129,7 +134,10 @@ struct Tables {
   float D32[(N + 1) * (N + 1)];     // D and Dvisc rounded to FP32 (kernel-parameter
   float Dvisc32[(N + 1) * (N + 1)]; // operands of the FP32 line contractions) and
   float D32lo[(N + 1) * (N + 1)];   // their rounding remainders (the double-float
-  float Dvisc32lo[(N + 1) * (N + 1)];  // lifting's coefficients hi + lo)
+  float Dvisc32lo[(N + 1) * (N + 1)];  // lifting's coefficients hi + lo), and the
+  // even/odd tables of D and Dvisc (LineEO::coef) as hi + lo
+  float Deo32[(N + 1) * ((N + 1) / 2)], Deo32lo[(N + 1) * ((N + 1) / 2)];
+  float Dveo32[(N + 1) * ((N + 1) / 2)], Dveo32lo[(N + 1) * ((N + 1) / 2)];
 };
 
 // Node slot in shared memory of the FP32 lifting kernel at N = 7 (node index
@@ -486,11 +494,33 @@ __device__ __forceinline__ void store_prim64(double* __restrict__ W, size_t S, s
 
 // the primitives of the input state, stored for the operator's kernels (FP64
 // viscous form); run before the lifting kernel whenever they are stale
-static __global__ void k_prim64(long long S, const double* __restrict__ U, const PhysDev ph, double* __restrict__ W) {
+// (W2: the double-float lifting's (u, v, w, T - T_ref) as (hi, lo) float
+// pairs, or null)
+static __global__ void k_prim64(long long S, const double* __restrict__ U, const PhysDev ph, double* __restrict__ W,
+                                float2* __restrict__ W2) {
+  const double Tref = ph.rho_ref > 0.0 ? ph.p_ref * ph.rcp_R / ph.rho_ref : 0.0;
   for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < S; g += (long long)gridDim.x * blockDim.x) {
     double T;
     const Prim<double> q = primitive_T(U[g], U[S + g], U[2 * S + g], U[3 * S + g], U[4 * S + g], ph, T);
     store_prim64(W, (size_t)S, (size_t)g, q, T);
+    if (W2) {
+      const double x[4] = {q.u, q.v, q.w, T - Tref};
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        float lo;
+        const float hi = d2f_bits(x[v], &lo);
+        W2[v * S + g] = make_float2(hi, lo);
+      }
+    }
+  }
+}
+
+// x -> (hi, lo) float pairs (the double-float lifting's metric arrays)
+static __global__ void k_split_pairs(long long n, const double* __restrict__ x, float2* __restrict__ y) {
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < n; g += (long long)gridDim.x * blockDim.x) {
+    float lo;
+    const float hi = d2f_bits(x[g], &lo);
+    y[g] = make_float2(hi, lo);
   }
 }
 

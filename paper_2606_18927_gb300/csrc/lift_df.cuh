@@ -129,15 +129,10 @@ k_lift_df(const double* __restrict__ U, const MeshDev<double> m, const PhysDev p
   const int p = tid;
   const size_t S = (size_t)m.K * n3;
   const size_t g = (size_t)e * n3 + p;
-  const double Tref = ph.rho_ref > 0.0 ? ph.p_ref * ph.rcp_R / ph.rho_ref : 0.0;
   const int sp = lift_slot8(p);
-  // own primitives (stored by k_prim64)
-  {
-    df_st(&sW[sp], df_of(m.W64[S + g]));
-    df_st(&sW[n3 + sp], df_of(m.W64[2 * S + g]));
-    df_st(&sW[2 * n3 + sp], df_of(m.W64[3 * S + g]));
-    df_st(&sW[3 * n3 + sp], df_of(m.W64[6 * S + g] - Tref));
-  }
+  // own primitives (stored as (hi, lo) pairs by k_prim64)
+#pragma unroll
+  for (int v = 0; v < 4; ++v) sW[v * n3 + sp] = m.lift_W2[v * S + g];
   // 2 (W* - W) at the six faces, in FP64 from the stored primitives (the
   // jumps are differences of nearby values: exact or nearly so), then split
   for (int t = tid; t < 6 * n2; t += n3) {
@@ -153,8 +148,12 @@ k_lift_df(const double* __restrict__ U, const MeshDev<double> m, const PhysDev p
   }
   __syncthreads();
   // line contraction by thread tid < 6 n2: two variables (v0, v0 + 1) on line L of
-  // direction dir, y_q = sum_m C_qm x_m for the n nodes, in place or into dst
+  // direction dir, y_q = sum_m C_qm x_m for the n nodes, in place or into dst;
+  // in even/odd form (C centro-antisymmetric: with xe_m = x_m + x_{N-m},
+  // xo_m = x_m - x_{N-m}, E_q = sum_{m<n/2} Ce_qm xe_m, O_q = sum Co_qm xo_m:
+  // y_q = E_q + O_q, y_{N-q} = O_q - E_q; tables as LineEO::coef)
   auto line_pass = [&](const float2* src, float2* dst, bool divergence) {
+    constexpr int h = n / 2;
     if (tid < 6 * n2) {
       const int dir = tid / (2 * n2), r = tid - dir * 2 * n2, v0 = 2 * (r / n2), L = r % n2;
       const int n0 = dir == 0 ? n * L : (dir == 1 ? (L % n) + n2 * (L / n) : L);
@@ -163,25 +162,35 @@ k_lift_df(const double* __restrict__ U, const MeshDev<double> m, const PhysDev p
 #pragma unroll
       for (int q = 0; q < n; ++q)
         sl[q] = s0 ^ (dir == 0 ? lift_slot8(q) : (dir == 1 ? lift_slot8(q * n) : lift_slot8(q * n2)));
-      DFl x[2][n];
+      const float* ch = divergence ? tab.Dveo32 : tab.Deo32;
+      const float* cl = divergence ? tab.Dveo32lo : tab.Deo32lo;
 #pragma unroll
-      for (int q = 0; q < n; ++q)
+      for (int v = 0; v < 2; ++v) {
+        const int row = divergence ? (dir * 4 + v0 + v) : (v0 + v);
+        DFl xe[h], xo[h];
 #pragma unroll
-        for (int v = 0; v < 2; ++v)
-          x[v][q] = df_ld(&src[(divergence ? (dir * 4 + v0 + v) : (v0 + v)) * n3 + sl[q]]);
-#pragma unroll
-      for (int q = 0; q < n; ++q)
-#pragma unroll
-        for (int v = 0; v < 2; ++v) {
-          DFAcc A{0.f, 0.f};
-#pragma unroll
-          for (int mm = 0; mm < n; ++mm) {
-            const DFl c = divergence ? DFl{tab.Dvisc32[q * n + mm], tab.Dvisc32lo[q * n + mm]}
-                                     : DFl{tab.D32[q * n + mm], tab.D32lo[q * n + mm]};
-            acc_fma(A, c, x[v][mm]);
-          }
-          df_st(&dst[(dir * 4 + v0 + v) * n3 + sl[q]], acc_val(A));
+        for (int mm = 0; mm < h; ++mm) {
+          const DFl a = df_ld(&src[row * n3 + sl[mm]]), b = df_ld(&src[row * n3 + sl[N - mm]]);
+          xe[mm] = df_add(a, b);
+          xo[mm] = df_sub(a, b);
         }
+#pragma unroll
+        for (int q = 0; q < h; ++q) {
+          DFAcc E{0.f, 0.f}, O{0.f, 0.f};
+#pragma unroll
+          for (int mm = 0; mm < h; ++mm) {
+            acc_fma(E, DFl{ch[q * h + mm], cl[q * h + mm]}, xe[mm]);
+            acc_fma(O, DFl{ch[(N - q) * h + mm], cl[(N - q) * h + mm]}, xo[mm]);
+          }
+          float s, e;
+          two_sum(O.s, E.s, s, e);
+          const DFl yq = df_norm(s, __fadd_rn(__fadd_rn(O.t, E.t), e));
+          two_sum(O.s, -E.s, s, e);
+          const DFl ym = df_norm(s, __fadd_rn(__fsub_rn(O.t, E.t), e));
+          df_st(&dst[(dir * 4 + v0 + v) * n3 + sl[q]], yq);
+          df_st(&dst[(dir * 4 + v0 + v) * n3 + sl[N - q]], ym);
+        }
+      }
     }
   };
   // reference-space gradients
@@ -214,7 +223,7 @@ k_lift_df(const double* __restrict__ U, const MeshDev<double> m, const PhysDev p
   {
     DFl jj[9];
 #pragma unroll
-    for (int c = 0; c < 9; ++c) jj[c] = df_of(m.JaJ[(size_t)c * S + g]);
+    for (int c = 0; c < 9; ++c) jj[c] = df_ld(&m.lift_M2[(size_t)(9 + c) * S + g]);
 #pragma unroll
     for (int d = 0; d < 3; ++d)
 #pragma unroll
@@ -223,7 +232,7 @@ k_lift_df(const double* __restrict__ U, const MeshDev<double> m, const PhysDev p
   {
     DFl mm[6];
 #pragma unroll
-    for (int c = 0; c < 6; ++c) mm[c] = df_of(m.Mj[(size_t)c * S + g]);
+    for (int c = 0; c < 6; ++c) mm[c] = df_ld(&m.lift_M2[(size_t)(18 + c) * S + g]);
     hT[0] = dot3(mm[0], dW[0][3], mm[3], dW[1][3], mm[4], dW[2][3]);
     hT[1] = dot3(mm[3], dW[0][3], mm[1], dW[1][3], mm[5], dW[2][3]);
     hT[2] = dot3(mm[4], dW[0][3], mm[5], dW[1][3], mm[2], dW[2][3]);
@@ -246,8 +255,9 @@ k_lift_df(const double* __restrict__ U, const MeshDev<double> m, const PhysDev p
     const DFl uu = df_ld(&sW[sp]), vv = df_ld(&sW[n3 + sp]), ww = df_ld(&sW[2 * n3 + sp]);
 #pragma unroll
     for (int dir = 0; dir < 3; ++dir) {
-      const DFl a0 = df_of(m.Ja[(size_t)(dir * 3 + 0) * S + g]), a1 = df_of(m.Ja[(size_t)(dir * 3 + 1) * S + g]),
-                a2 = df_of(m.Ja[(size_t)(dir * 3 + 2) * S + g]);
+      const DFl a0 = df_ld(&m.lift_M2[(size_t)(dir * 3 + 0) * S + g]),
+                a1 = df_ld(&m.lift_M2[(size_t)(dir * 3 + 1) * S + g]),
+                a2 = df_ld(&m.lift_M2[(size_t)(dir * 3 + 2) * S + g]);
 #pragma unroll
       for (int v = 0; v < 3; ++v) G[dir][v] = dot3(a0, tau[v][0], a1, tau[v][1], a2, tau[v][2]);
       DFAcc A{0.f, 0.f};

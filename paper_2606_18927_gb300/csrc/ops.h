@@ -52,6 +52,10 @@ struct OpArgs {
   // and [6][K n^3] (Ja Ja^T) / J (order 00, 11, 22, 01, 02, 12)
   const double* JaJ;
   const double* Mj;
+  // the double-float lifting's (hi, lo) pairs of Ja, Ja / J, (Ja Ja^T) / J
+  // [24][K n^3] and of the lifted primitives [4][K n^3] (null: not selected)
+  const float2* lift_M2;
+  float2* lift_W2;
   double* wm_t;  // wall-law warm-start values per wall node (null: cold solves)
   // partitioned meshes: n_halo halo faces (the last faces), remote traces in
   // halo_U / halo_G, local traces packed into send_U / send_G.  phase selects

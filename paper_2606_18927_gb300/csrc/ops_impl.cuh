@@ -30,6 +30,19 @@ static Tables<N> make_tables(const double* D, const double* w) {
       t.Dvisc32lo[i * n + m] = (float)(t.Dvisc[i * n + m] - (double)t.Dvisc32[i * n + m]);
     }
   }
+  // even/odd tables [n][n/2] (as LineEO::coef): rows q < n/2 hold
+  // (M_qm + M_q,N-m) / 2, rows q >= n/2 (M_q'm - M_q',N-m) / 2 with q' = N - q
+  constexpr int h = n / 2;
+  for (int t2 = 0; t2 < n * h; ++t2) {
+    const int q = t2 / h, mm = t2 % h, r = q < h ? q : N - q;
+    auto co = [&](const double* M) {
+      const double a = M[r * n + mm], b = M[r * n + N - mm];
+      return q < h ? 0.5 * (a + b) : 0.5 * (a - b);
+    };
+    const double cd = co(t.D), cv = co(t.Dvisc);
+    t.Deo32[t2] = (float)cd; t.Deo32lo[t2] = (float)(cd - (double)t.Deo32[t2]);
+    t.Dveo32[t2] = (float)cv; t.Dveo32lo[t2] = (float)(cv - (double)t.Dveo32[t2]);
+  }
   return t;
 }
 
@@ -49,6 +62,7 @@ static int run_typed(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {
   m.JaJ = a.JaJ; m.Mj = a.Mj;
   if (std::is_same<R, double>::value && ph.viscous && (!a.JaJ || !a.Mj))
     return (int)cudaErrorInvalidValue;
+  m.lift_M2 = a.lift_M2; m.lift_W2 = a.lift_W2;
   m.wm_t = a.wm_t;
   m.n_halo = a.n_halo; m.halo_U = a.halo_U; m.halo_G = static_cast<const R*>(a.halo_G);
   const Tables<N> tab = make_tables<N>(a.D, a.w);
@@ -104,13 +118,14 @@ static int run_typed(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {
     // first reader; kept between evaluations of an unchanged state)
     if (m.W64 && !a.w64_valid) {
       const long long S = (long long)a.K * n3;
-      k_prim64<<<(unsigned)std::min<long long>((S + 255) / 256, 152 * 16), 256, 0, s>>>(S, a.Uin, ph, m.W64);
+      k_prim64<<<(unsigned)std::min<long long>((S + 255) / 256, 152 * 16), 256, 0, s>>>(
+          S, a.Uin, ph, m.W64, (ph.lift_df && N == 7) ? a.lift_W2 : nullptr);
     }
     if (ph.viscous) {
       bool done = false;
       if constexpr (N == 7 && std::is_same<R, double>::value) {
         // the double-float lifting (it reads the stored primitives and metric products)
-        if (ph.lift_df && m.W64 && m.JaJ && m.Mj) {
+        if (ph.lift_df && m.W64 && m.lift_M2 && m.lift_W2) {
           const size_t smem_df = (size_t)LiftDfShape<N>::SMEM_F2 * sizeof(float2);
           cudaFuncSetAttribute(k_lift_df<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_df);
           k_lift_df<N><<<a.K, n3, smem_df, s>>>(a.Uin, m, ph, tab, Rv, Gf);
