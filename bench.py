@@ -292,6 +292,27 @@ def measure_variants(args, wl, X, nbr, U, op64, stream, dt):
     e1.record(stream)
     torch.cuda.synchronize()
     out["fp64_graph_replay"] = {"ms_per_stage": e0.elapsed_time(e1) / (5 * nst), "steps": nst}
+    if wl.spec.N == 7 and wl.viscous:
+        # the same stages with the FP64 lifting kernel instead of the
+        # double-float one (the other lifting arithmetic of the FP64 form)
+        other = 0 if args.lifting == "df" else 1
+        op64.set_lifting_arithmetic(other)
+        op64.set_state(Ud)
+        for s in range(3):
+            op64.rk_stage(s, 0.0, dt)
+        op64.profile_enable(True)
+        e0.record(stream)
+        for s in range(args.steps):
+            op64.rk_stage(s % 5, 0.0, dt)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        prof = op64.profile_read()
+        op64.profile_enable(False)
+        op64.set_lifting_arithmetic(1 - other)
+        ms = e0.elapsed_time(e1) / args.steps
+        out["fp64_lifting_" + ("fp64" if other == 0 else "df")] = {
+            "ms_per_step": ms, "value": wl.spec.dofs / (ms * 1e-3), "unit": UNIT,
+            "kernels_ms_per_launch": {k: (v[0] / v[1] if v[1] else None) for k, v in prof.items()}}
     # FP32-mixed form
     free2 = torch.cuda.mem_get_info()[0]
     opm = dg.Operator(wl.spec.N, X, nbr, wl.phys, precision=dg.FP32_MIXED, vol_flux=wl.vol_flux,
@@ -379,8 +400,8 @@ def run_ours(args):
     free0 = torch.cuda.mem_get_info()[0]
     op = dg.Operator(wl.spec.N, X, nbr, wl.phys, precision=precision, vol_flux=wl.vol_flux,
                      surf_flux=wl.surf_flux, viscous=wl.viscous, law=wl.law, stream=stream)
-    if args.lifting == "df":
-        op.set_lifting_arithmetic(1)
+    if wl.spec.N == 7 and wl.viscous and precision == dg.FP64:
+        op.set_lifting_arithmetic(1 if args.lifting == "df" else 0)
     op.set_state(Ud)
     footprint = free0 - torch.cuda.mem_get_info()[0]
     dofs = wl.spec.dofs
@@ -491,6 +512,9 @@ def run_ours(args):
         "config": {"workload": wl.name, "N": wl.spec.N, "elements": [wl.spec.nx, wl.spec.ny, wl.spec.nz],
                    "dofs": dofs, "precision": args.precision, "vol_flux": "kep_pirozzoli",
                    "surf_flux": {0: "central", 1: "llf", 2: "roe"}[wl.surf_flux], "lifting": "br1",
+                   "lifting_arithmetic": ("double-float (FP32 pipe, error-free transformations)"
+                                          if wl.spec.N == 7 and wl.viscous and precision == dg.FP64
+                                          and args.lifting == "df" else "fp64"),
                    "pid_ns": 1e9 / (value / world), "l2": "inputs larger than L2 (U alone %.0f MB)" % (nbytes / 1e6),
                    "footprint_gb": footprint / 1e9, "parallelism": "replicas" if world > 1 else "single"},
         "roofline": roof,
@@ -520,8 +544,9 @@ def main():
                     help="element counts of a smaller case of the same workload (profiling)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--lifting", choices=["fp64", "df"], default="fp64",
-                    help="arithmetic of the FP64 form's lifting kernel at N = 7 (df: double-float)")
+    ap.add_argument("--lifting", choices=["fp64", "df"], default="df",
+                    help="arithmetic of the FP64 form's lifting kernel at N = 7 (df: double-float, the "
+                         "library's default there; fp64: the FP64 kernel)")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the FP32-mixed and VJP measurements appended to the line")
     args = ap.parse_args()

@@ -594,6 +594,15 @@ int dg_init_mesh(dg_ctx** out, const dg_mesh_desc* m, const dg_phys* p, const dg
   chk(cudaMemset(c->status, 0, sizeof(int)));
   chk(cudaMemset(c->dU, 0, 5 * S * sizeof(double)));
   if (e != cudaSuccess) { free_all(c); delete c; return cuda_fail(nullptr, e, "dg_init_mesh: upload"); }
+  // N = 7, FP64 viscous form: the double-float lifting by default
+  if (c->N == 7 && o->precision == DG_FP64 && o->viscous) {
+    const int rc = dg_set_lifting_arithmetic(c, 1);
+    if (rc != DG_OK) {
+      const std::string msg = c->err;
+      free_all(c); delete c;
+      return fail(nullptr, rc, "dg_init_mesh: " + msg);
+    }
+  }
   *out = c;
   return DG_OK;
 }

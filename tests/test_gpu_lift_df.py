@@ -1,5 +1,6 @@
-"""The double-float lifting kernel (FP64 viscous form at N = 7,
-dg_set_lifting_arithmetic(1)) against the extended-precision oracle: FP64
+"""The double-float lifting kernel (FP64 viscous form at N = 7, the
+library's default there, dg_set_lifting_arithmetic(1)) against the
+extended-precision oracle and against the FP64 lifting kernel (mode 0): FP64
 parity bound 1e-12 in the relative max norm per variable, on the cases of the
 FP64 parity suite at N = 7 (curved meshes, Roe with sonic states, walls with
 the wall model, inflow / outflow, the entropy-conserving flux with
@@ -26,6 +27,7 @@ def test_double_float_lifting_matches_oracle(ora, label, spec, surf, vol, ic, ma
     phys = I.phys_params(Ma=ma, Re=1600.0 if not suth else 200.0, sutherland=suth)
     o, g, X, U = case(ora, spec, phys, surf_flux=surf, vol_flux=vol, ic=ic)
     ref = o.time_derivative(U)
+    g.set_lifting_arithmetic(0)
     f64 = gpu_ut(torch, g, U)
     g.set_lifting_arithmetic(1)
     out = gpu_ut(torch, g, U)
