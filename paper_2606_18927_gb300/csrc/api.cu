@@ -53,6 +53,7 @@ struct dg_ctx {
   // (Ja Ja^T) / J [24][S] and of the lifted primitives [4][S]
   float2* lift_M2 = nullptr;
   float2* lift_W2 = nullptr;
+  double* pairA = nullptr;  // FP64, N = 7: the volume kernel's pair metric sums [16128 K]
   double* wm_t = nullptr;  // wall-law warm start per wall node (NaN: none yet)
   // partitioned meshes: halo buffers [n_halo][5][n2] (state traces, FP64) and
   // [n_halo][4][n2] (viscous-flux traces, flux type), received and sent
@@ -161,7 +162,7 @@ void free_all(dg_ctx* c) {
   void* ptrs[] = {c->U, c->dU, c->io, c->io2, c->Ja, c->invJ, c->fgeo, c->nbr, c->elem_face, c->faces,
                   c->ws_elem, c->ws_lag, c->Rv, c->Gf, c->Fs, c->tau, c->status,
                   c->gUf, c->gGf, c->gWf, c->gUs, c->gtheta, c->wq, c->ro_ckpt, c->ro_stage, c->ro_work,
-                  c->ro_scalar, c->wJ, c->W32, c->W64, c->JaJ, c->Mj, c->lift_M2, c->lift_W2, c->halo_U, c->send_U,
+                  c->ro_scalar, c->wJ, c->W32, c->W64, c->JaJ, c->Mj, c->lift_M2, c->lift_W2, c->pairA, c->halo_U, c->send_U,
                   c->halo_G, c->send_G,
                   c->wm_t};
   for (void* p : ptrs)
@@ -209,6 +210,7 @@ int launch(dg_ctx* c, const double* Uin, int mode, double* Out, double A, double
   a.w64_valid = (c->W64 && !a.fp32 && Uin == c->U && c->w64_of_U) ? 1 : 0;
   a.JaJ = c->JaJ; a.Mj = c->Mj;
   a.lift_M2 = c->lift_M2; a.lift_W2 = c->lift_W2;
+  a.pairA = c->pairA;
   a.wm_t = c->wm_t;
   int rc = dg::run_operator(a, c->ph, c->stream);
   if (rc != 0) {
@@ -356,6 +358,7 @@ int noalloc_args(dg_ctx* c, const double* U, double* Ut, OpArgs* a, const PhysDe
   a->Ja = c->Ja; a->invJ = c->invJ; a->fgeo = c->fgeo; a->nbr = c->nbr; a->elem_face = c->elem_face;
   a->JaJ = c->JaJ; a->Mj = c->Mj;  // geometry, owned by the context
   a->lift_M2 = nullptr; a->lift_W2 = nullptr;  // (the FP64 lifting: no stored primitives here)
+  a->pairA = c->pairA;
   a->faces = c->faces; a->ws_elem = c->ws_elem; a->ws_lag = c->ws_lag;
   a->D = c->geo.basis.D.data(); a->w = c->geo.basis.w.data();
   a->Uin = U; a->status = c->status;
@@ -594,6 +597,17 @@ int dg_init_mesh(dg_ctx** out, const dg_mesh_desc* m, const dg_phys* p, const dg
   chk(cudaMemset(c->status, 0, sizeof(int)));
   chk(cudaMemset(c->dU, 0, 5 * S * sizeof(double)));
   if (e != cudaSuccess) { free_all(c); delete c; return cuda_fail(nullptr, e, "dg_init_mesh: upload"); }
+  // FP64 at N = 7: the volume kernel's pair metric sums
+  if (c->N == 7 && o->precision == DG_FP64) {
+    e = alloc(&c->pairA, (size_t)16128 * c->K);
+    if (e == cudaSuccess) {
+      const long long work = (long long)c->K * 576;
+      dg::k_pair_metric_sums<<<(unsigned)((work + 255) / 256), 256, 0, c->stream>>>(
+          c->K, static_cast<const double*>(c->Ja), c->pairA);
+      e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) { free_all(c); delete c; return cuda_fail(nullptr, e, "dg_init_mesh: pair sums"); }
+  }
   // N = 7, FP64 viscous form: the double-float lifting by default
   if (c->N == 7 && o->precision == DG_FP64 && o->viscous) {
     const int rc = dg_set_lifting_arithmetic(c, 1);

@@ -121,6 +121,9 @@ struct MeshDev {
   // written by k_prim64 (null unless that lifting is selected)
   const float2* lift_M2;
   float2* lift_W2;
+  // FP64 volume kernel at N = 7: the metric sums a_i + a_m of every pair it
+  // evaluates (pair_main / pair_half below), fixed with the mesh
+  const double* pairA;
   double* wm_t;          // [n_wall*n2] last wall-law solution per wall node (warm start; may be null)
   int* status;           // device status flags (index checks of the bounds-checking build)
 };
@@ -2046,6 +2049,41 @@ __device__ __forceinline__ int vslot(int node) {
   }
 }
 
+// Metric sums a_i + a_m (a = Ja^dir) of the pairs that the FP64 volume kernel
+// evaluates at N = 7, per element 16128 doubles: the pairs (pos, pos + d mod 8)
+// at cyclic distance d = 1..3 of line L (0..63) along dir at
+// pair_main(e, dir, c, d, L, pos), and the pairs (pa, pa + 4) at
+// pair_half(K, e, dir, c, L, pa) after all of those.  The volume kernel reads
+// them instead of summing the two nodes' metrics (3 FP64 additions of a pair's
+// 30), the FP64 pipe being its bound.
+__host__ __device__ __forceinline__ size_t pair_main(int e, int dir, int c, int d, int L, int pos) {
+  return ((((size_t)e * 3 + dir) * 3 + c) * 3 + (d - 1)) * 512 + (size_t)L * 8 + pos;
+}
+__host__ __device__ __forceinline__ size_t pair_half(int K, int e, int dir, int c, int L, int pa) {
+  return (size_t)K * 13824 + (((size_t)e * 3 + dir) * 3 + c) * 256 + (size_t)L * 4 + pa;
+}
+__host__ __device__ __forceinline__ int line_node8(int dir, int L, int q) {
+  return dir == 0 ? q + 8 * L : (dir == 1 ? (L % 8) + 8 * q + 64 * (L / 8) : L + 64 * q);
+}
+
+// one thread per (element, direction, component, line)
+static __global__ void k_pair_metric_sums(int K, const double* __restrict__ Ja, double* __restrict__ out) {
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (tid >= (long long)K * 3 * 3 * 64) return;
+  const int L = (int)(tid % 64), c = (int)((tid / 64) % 3), dir = (int)((tid / 192) % 3), e = (int)(tid / 576);
+  const size_t S = (size_t)K * 512;
+  const double* a = Ja + (size_t)(dir * 3 + c) * S + (size_t)e * 512;
+  double x[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) x[q] = a[line_node8(dir, L, q)];
+#pragma unroll
+  for (int d = 1; d <= 3; ++d)
+#pragma unroll
+    for (int pos = 0; pos < 8; ++pos) out[pair_main(e, dir, c, d, L, pos)] = x[pos] + x[(pos + d) & 7];
+#pragma unroll
+  for (int pa = 0; pa < 4; ++pa) out[pair_half(K, e, dir, c, L, pa)] = x[pa] + x[pa + 4];
+}
+
 // the values of one node that the two-point flux of a direction reads
 template <class R>
 struct VolNode {
@@ -2086,6 +2124,8 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
   constexpr int n = Sh::n, n2 = Sh::n2, n3 = Sh::n3, T = Sh::THREADS, LPW = Sh::LPW;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr bool F32 = std::is_same<R, float>::value;
+  // FP64 at N = 7: the pairs' metric sums read from m.pairA
+  constexpr bool PSUM = std::is_same<R, double>::value && n == 8;
   constexpr int QS = EC ? 9 : (F32 ? 10 : 7);
   R* sQ = reinterpret_cast<R*>(smem_raw);  // [QS][n3]: rho u v w 4p' h|e 2p (KG) (+ FP32: ul vl wl); EC see above
   R* sA = sQ + QS * n3;                     // [9][n3]: Ja (dir*3+comp)
@@ -2147,8 +2187,11 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
       sQ[5 * n3 + ts] = q.h - pf / q.rho;  // e = E / rho
       sQ[6 * n3 + ts] = R(2) * pf;
     }
+    // (FP64 at N = 7: the pairs' metric sums come from m.pairA instead)
+    if constexpr (!PSUM) {
 #pragma unroll
-    for (int c = 0; c < 9; ++c) sA[c * n3 + ts] = m.Ja[(size_t)c * S + g];
+      for (int c = 0; c < 9; ++c) sA[c * n3 + ts] = m.Ja[(size_t)c * S + g];
+    }
   }
   __syncthreads();
   // three direction passes over the lines
@@ -2173,16 +2216,20 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
       X.p2 = (kg || EC) ? sQ[6 * n3 + node] : R(0);
       X.ib = EC ? sQ[7 * n3 + node] : R(0);
       X.irh = EC ? sQ[8 * n3 + node] : R(0);
-      X.a0 = sA[(dir * 3 + 0) * n3 + node]; X.a1 = sA[(dir * 3 + 1) * n3 + node];
-      X.a2 = sA[(dir * 3 + 2) * n3 + node];
+      if constexpr (!PSUM) {
+        X.a0 = sA[(dir * 3 + 0) * n3 + node]; X.a1 = sA[(dir * 3 + 1) * n3 + node];
+        X.a2 = sA[(dir * 3 + 2) * n3 + node];
+      } else {
+        X.a0 = X.a1 = X.a2 = R(0);
+      }
       return X;
     };
     // symmetric two-point flux F#(A, B) . 4 {Ja} in the scaled form of the
     // coefficient tables (mass row against DVS / 8, the others against DVS / 16)
-    auto sym_flux = [&](const VolNode<R>& A, const VolNode<R>& B, R F[5]) {
+    // (Sa: the sum of the two nodes' metrics, given or formed here)
+    auto sym_flux_s = [&](const VolNode<R>& A, const VolNode<R>& B, R Sa0, R Sa1, R Sa2, R F[5]) {
       const R Sr = A.rho + B.rho, Su = A.u + B.u, Sv = A.v + B.v, Sw = A.w + B.w;
       const R Sp = A.p4 + B.p4;
-      const R Sa0 = A.a0 + B.a0, Sa1 = A.a1 + B.a1, Sa2 = A.a2 + B.a2;
       const R ua = Su * Sa0 + Sv * Sa1 + Sw * Sa2;  // 4 {u}.{a}
       if constexpr (EC) {
         // nodes hold ib = 1 / (2 beta) and irh = 1 / (2 rho), so that with
@@ -2221,6 +2268,17 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
         F[4] = mf * (A.hh + B.hh);                // 16 F4
         if (kg) F[4] += (A.p2 + B.p2) * ua;
       }
+    };
+    auto sym_flux = [&](const VolNode<R>& A, const VolNode<R>& B, R F[5]) {
+      sym_flux_s(A, B, A.a0 + B.a0, A.a1 + B.a1, A.a2 + B.a2, F);
+    };
+    auto sums_main = [&](int dir, int d, R Sa[3]) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) Sa[c] = m.pairA[pair_main(e, dir, c, d, L, pos)];
+    };
+    auto sums_half = [&](int dir, int Lx, int pa, R Sa[3]) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) Sa[c] = m.pairA[pair_half(m.K, e, dir, c, Lx, pa)];
     };
     // FP64, N = 7: the n/2 pairs at distance n/2 of a line would be formed twice
     // (once in each lane); instead the distance-n/2 step of the xi pass forms
@@ -2303,7 +2361,13 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
           }
         }
         R F[5];
-        sym_flux(A, load_node(q, dir), F);
+        if constexpr (PSUM) {
+          R Sa[3];
+          sums_main(dir, d, Sa);
+          sym_flux_s(A, load_node(q, dir), Sa[0], Sa[1], Sa[2], F);
+        } else {
+          sym_flux(A, load_node(q, dir), F);
+        }
         const R c8 = sC8[pos * n + pm], c16 = sC16[pos * n + pm];
         acc[0] += c8 * F[0];
 #pragma unroll
@@ -2327,7 +2391,13 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
           const bool lo = pos < h;
           const int dd = lo ? 0 : 1, pa = pos & (h - 1);
           R F[5];
-          sym_flux(load_node(node_at(dd, pa), dd), load_node(node_at(dd, pa + h), dd), F);
+          if constexpr (PSUM) {
+            R Sa[3];
+            sums_half(dd, L, pa, Sa);
+            sym_flux_s(load_node(node_at(dd, pa), dd), load_node(node_at(dd, pa + h), dd), Sa[0], Sa[1], Sa[2], F);
+          } else {
+            sym_flux(load_node(node_at(dd, pa), dd), load_node(node_at(dd, pa + h), dd), F);
+          }
 #pragma unroll
           for (int v = 0; v < 5; ++v) {
             const R Fx = __shfl_xor_sync(0xffffffffu, F[v], h);
@@ -2339,7 +2409,13 @@ k_volume(const double* __restrict__ Uin, const MeshDev<R> m, const PhysDev ph, c
           const int pa = pos & (h - 1);
           const int Lz = lo ? L : L + HW * LPW;  // zeta line of this warp or of warp + HW
           R F[5];
-          sym_flux(load_node(Lz + n2 * pa, 2), load_node(Lz + n2 * (pa + h), 2), F);
+          if constexpr (PSUM) {
+            R Sa[3];
+            sums_half(2, Lz, pa, Sa);
+            sym_flux_s(load_node(Lz + n2 * pa, 2), load_node(Lz + n2 * (pa + h), 2), Sa[0], Sa[1], Sa[2], F);
+          } else {
+            sym_flux(load_node(Lz + n2 * pa, 2), load_node(Lz + n2 * (pa + h), 2), F);
+          }
           const int x = (warp * LPW + seg) * h + pa;
 #pragma unroll
           for (int v = 0; v < 5; ++v) {

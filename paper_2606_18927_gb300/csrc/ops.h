@@ -56,6 +56,7 @@ struct OpArgs {
   // [24][K n^3] and of the lifted primitives [4][K n^3] (null: not selected)
   const float2* lift_M2;
   float2* lift_W2;
+  const double* pairA;  // FP64 at N = 7: the volume kernel's pair metric sums (required there)
   double* wm_t;  // wall-law warm-start values per wall node (null: cold solves)
   // partitioned meshes: n_halo halo faces (the last faces), remote traces in
   // halo_U / halo_G, local traces packed into send_U / send_G.  phase selects

@@ -63,6 +63,8 @@ static int run_typed(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {
   if (std::is_same<R, double>::value && ph.viscous && (!a.JaJ || !a.Mj))
     return (int)cudaErrorInvalidValue;
   m.lift_M2 = a.lift_M2; m.lift_W2 = a.lift_W2;
+  m.pairA = a.pairA;
+  if (N == 7 && std::is_same<R, double>::value && !a.pairA) return (int)cudaErrorInvalidValue;
   m.wm_t = a.wm_t;
   m.n_halo = a.n_halo; m.halo_U = a.halo_U; m.halo_G = static_cast<const R*>(a.halo_G);
   const Tables<N> tab = make_tables<N>(a.D, a.w);
