@@ -38,7 +38,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) of one launch of the dominant kernel, from an ncu
 # capture of the same kernel build on a 16^3-element case, scaled to the
 # launch size by the DOF count (traffic is proportional to the DOF count).
-NCU_TRAFFIC_PER_DOF = {("k_volume", "fp64", 7): (451.83e6 + 139.14e6) / 2097152,
+NCU_TRAFFIC_PER_DOF = {("k_volume", "fp64", 7): (830.92e6 + 157.87e6) / 2097152,
                        ("k_volume", "fp32", 7): (308.57e6 + 192.35e6) / 2097152}
 # algorithmic HBM bytes per DOF of the FP32-mixed volume kernel (stage form):
 # U read 40 and written 40, dU read and written 80, FP32 primitives and the
@@ -47,7 +47,7 @@ NCU_TRAFFIC_PER_DOF = {("k_volume", "fp64", 7): (451.83e6 + 139.14e6) / 2097152,
 MIXED_VOLUME_BYTES_PER_DOF = lambda N: 40 + 40 + 80 + 36 + 36 + 40 + 16 + 3.0 / (N + 1) * 5 * 4 * 2
 
 
-def algorithmic_flops_per_dof(N, kernel, viscous=True, surf="roe", stored_prims=None):
+def algorithmic_flops_per_dof(N, kernel, viscous=True, surf="roe", stored_prims=None, pair_sums=None):
     """Algorithmic FP64 flops per DOF and operator evaluation (FMA = 2).
 
     Counted on the formulas of the operator, independent of how a kernel
@@ -55,13 +55,17 @@ def algorithmic_flops_per_dof(N, kernel, viscous=True, surf="roe", stored_prims=
     with a symmetric flux allows).  The primitive recovery is counted where it
     runs: in the FP64 viscous form (stored_prims, the default there) once per
     node in the lifting window, which stores them for the face and volume
-    kernels."""
+    kernels.  The FP64 volume kernel at N = 7 reads each pair's metric sum,
+    stored with the mesh (pair_sums, the default there): those 3 additions
+    are not counted."""
     n = N + 1
     if stored_prims is None:
         stored_prims = viscous
+    if pair_sums is None:
+        pair_sums = N == 7
     if kernel == "volume":
         pairs = 3 * N / 2.0                     # unordered pairs per node, 3 directions
-        pair = 6 + 3 + 5 + 1 + 9 + 1 + 20       # averages, metric sum, u.a, m, F_m, F_E, 2 x 5 FMA
+        pair = 6 + (0 if pair_sums else 3) + 5 + 1 + 9 + 1 + 20  # averages, metric sum, u.a, m, F_m, F_E, 2 x 5 FMA
         prim = 1 if stored_prims else 13        # 4 p' (stored) | 1/rho, u, |u|^2, p, h
         surf_int = (6.0 / n) * 5 * 2            # face nodes per DOF x 5 FMA
         return pairs * pair + prim + (4 if viscous else 0) + surf_int + 5 + 20
