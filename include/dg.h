@@ -268,16 +268,16 @@ int dg_vjp_phase(dg_ctx* c, int phase, const double* U, const double* lam, doubl
 /* Sets the wall-law constants (kappa, B) used by later calls (Sec. 3.2). */
 int dg_set_params(dg_ctx* c, double kappa, double B);
 
-/* Arithmetic of the FP64 viscous form's lifting kernel at N = 7 (BR1
+/* Arithmetic of the FP64 viscous form's lifting kernel at odd N (BR1
  * lifting, viscous flux, weak viscous divergence): mode 1 double-float (the
- * default at N = 7: each value an unevaluated sum of two floats, the
+ * default at odd N: each value an unevaluated sum of two floats, the
  * operations built from error-free transformations on the FP32 pipe, about
  * 2^-47 relative rounding per operation; the state, the primitives, the
  * metric data and the kernel's outputs stay FP64, the temperature is lifted
  * relative to p_ref / (rho_ref R); the viscous terms are a small part of Ut,
  * and the operator's parity with the oracle is unchanged), 0 FP64.  Mode 1
  * keeps (hi, lo) float pairs of the metric data and of the lifted
- * primitives: 224 more bytes per DOF.  Other degrees and forms ignore it.
+ * primitives: 224 more bytes per DOF.  Even degrees and other forms ignore it.
  * DG_ERR_ARG for another mode.  Used by later calls. */
 int dg_set_lifting_arithmetic(dg_ctx* c, int mode);
 

@@ -608,8 +608,8 @@ int dg_init_mesh(dg_ctx** out, const dg_mesh_desc* m, const dg_phys* p, const dg
     }
     if (e != cudaSuccess) { free_all(c); delete c; return cuda_fail(nullptr, e, "dg_init_mesh: pair sums"); }
   }
-  // N = 7, FP64 viscous form: the double-float lifting by default
-  if (c->N == 7 && o->precision == DG_FP64 && o->viscous) {
+  // odd N, FP64 viscous form: the double-float lifting by default
+  if (c->N % 2 == 1 && o->precision == DG_FP64 && o->viscous) {
     const int rc = dg_set_lifting_arithmetic(c, 1);
     if (rc != DG_OK) {
       const std::string msg = c->err;
@@ -849,7 +849,7 @@ int dg_set_params(dg_ctx* c, double kappa, double B) {
 int dg_set_lifting_arithmetic(dg_ctx* c, int mode) {
   if (!c) return DG_ERR_ARG;
   if (mode != 0 && mode != 1) return fail(c, DG_ERR_ARG, "dg_set_lifting_arithmetic: mode must be 0 or 1");
-  const bool applies = c->N == 7 && c->opts.precision == DG_FP64 && c->opts.viscous && c->JaJ && c->W64;
+  const bool applies = c->N % 2 == 1 && c->opts.precision == DG_FP64 && c->opts.viscous && c->JaJ && c->W64;
   if (mode == 1 && applies && !c->lift_M2) {
     // the metric arrays as (hi, lo) pairs, split once on the device
     cudaError_t e = alloc(&c->lift_M2, 24 * c->S);

@@ -72,7 +72,7 @@ struct PhysDev {
   double U_in[5], p_out;      // inflow state (conservative) and outflow pressure
   double T_wall;              // isothermal wall temperature (<= 0: adiabatic walls)
   int wm_maxit;               // iteration cap of the law-of-the-wall solve (bracket growth + Newton)
-  int lift_df;                // FP64 viscous form at N = 7: lifting in double-float arithmetic (k_lift_df)
+  int lift_df;                // FP64 viscous form at odd N: lifting in double-float arithmetic (k_lift_df)
   // FP32 copies of the constants the FP32 kernels use (a double-to-float
   // conversion is an FP64-pipe instruction)
   struct {

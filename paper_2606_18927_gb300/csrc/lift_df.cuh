@@ -110,15 +110,23 @@ struct LiftDfShape {
   static constexpr int SMEM_F2 = 16 * n3 + 24 * n2;
 };
 
-// One CTA of n^3 threads per element (N = 7): the roles of k_lift (own face
-// fluxes Gf and the weak divergence R_v, both FP64 in memory) with the line
-// contractions on two threads per line, two variables each, over the node
-// slots of lift_slot8.
+// node slot: lift_slot8 at N = 7 (bank-conflict free for the node- and
+// line-ordered warps), the natural order otherwise
 template <int N>
-__global__ void __launch_bounds__((N + 1) * (N + 1) * (N + 1), 2)
+__device__ __forceinline__ int df_slot(int node) {
+  if constexpr (N == 7) return lift_slot8(node);
+  else return node;
+}
+
+// One CTA of n^3 threads per element (odd N: the even/odd contractions need
+// an even node count): the roles of k_lift (own face fluxes Gf and the weak
+// divergence R_v, both FP64 in memory) with the line contractions on two
+// threads per line, two variables each.
+template <int N>
+__global__ void __launch_bounds__((N + 1) * (N + 1) * (N + 1), ((N + 1) * (N + 1) * (N + 1) <= 512 ? 2 : 1))
 k_lift_df(const double* __restrict__ U, const MeshDev<double> m, const PhysDev ph, const Tables<N> tab,
           double* __restrict__ Rv, double* __restrict__ Gf) {
-  static_assert(N == 7, "the double-float lifting kernel is written for N = 7");
+  static_assert(N % 2 == 1, "the double-float lifting kernel needs an even node count");
   constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* sW = reinterpret_cast<float2*>(smem_raw);  // [4][n3] u, v, w, T - T_ref
@@ -129,7 +137,7 @@ k_lift_df(const double* __restrict__ U, const MeshDev<double> m, const PhysDev p
   const int p = tid;
   const size_t S = (size_t)m.K * n3;
   const size_t g = (size_t)e * n3 + p;
-  const int sp = lift_slot8(p);
+  const int sp = df_slot<N>(p);
   // own primitives (stored as (hi, lo) pairs by k_prim64)
 #pragma unroll
   for (int v = 0; v < 4; ++v) sW[v * n3 + sp] = m.lift_W2[v * S + g];
@@ -154,14 +162,20 @@ k_lift_df(const double* __restrict__ U, const MeshDev<double> m, const PhysDev p
   // y_q = E_q + O_q, y_{N-q} = O_q - E_q; tables as LineEO::coef)
   auto line_pass = [&](const float2* src, float2* dst, bool divergence) {
     constexpr int h = n / 2;
-    if (tid < 6 * n2) {
-      const int dir = tid / (2 * n2), r = tid - dir * 2 * n2, v0 = 2 * (r / n2), L = r % n2;
+    for (int task = tid; task < 6 * n2; task += n3) {
+      const int dir = task / (2 * n2), r = task - dir * 2 * n2, v0 = 2 * (r / n2), L = r % n2;
       const int n0 = dir == 0 ? n * L : (dir == 1 ? (L % n) + n2 * (L / n) : L);
-      const int s0 = lift_slot8(n0);
+      const int stride = dir == 0 ? 1 : (dir == 1 ? n : n2);
       int sl[n];
+      if constexpr (N == 7) {
+        const int s0 = lift_slot8(n0);
 #pragma unroll
-      for (int q = 0; q < n; ++q)
-        sl[q] = s0 ^ (dir == 0 ? lift_slot8(q) : (dir == 1 ? lift_slot8(q * n) : lift_slot8(q * n2)));
+        for (int q = 0; q < n; ++q)
+          sl[q] = s0 ^ (dir == 0 ? lift_slot8(q) : (dir == 1 ? lift_slot8(q * n) : lift_slot8(q * n2)));
+      } else {
+#pragma unroll
+        for (int q = 0; q < n; ++q) sl[q] = n0 + q * stride;
+      }
       const float* ch = divergence ? tab.Dveo32 : tab.Deo32;
       const float* cl = divergence ? tab.Dveo32lo : tab.Deo32lo;
 #pragma unroll

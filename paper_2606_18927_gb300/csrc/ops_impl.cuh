@@ -121,11 +121,11 @@ static int run_typed(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {
     if (m.W64 && !a.w64_valid) {
       const long long S = (long long)a.K * n3;
       k_prim64<<<(unsigned)std::min<long long>((S + 255) / 256, 152 * 16), 256, 0, s>>>(
-          S, a.Uin, ph, m.W64, (ph.lift_df && N == 7) ? a.lift_W2 : nullptr);
+          S, a.Uin, ph, m.W64, (ph.lift_df && N % 2 == 1) ? a.lift_W2 : nullptr);
     }
     if (ph.viscous) {
       bool done = false;
-      if constexpr (N == 7 && std::is_same<R, double>::value) {
+      if constexpr (N % 2 == 1 && std::is_same<R, double>::value) {
         // the double-float lifting (it reads the stored primitives and metric products)
         if (ph.lift_df && m.W64 && m.lift_M2 && m.lift_W2) {
           const size_t smem_df = (size_t)LiftDfShape<N>::SMEM_F2 * sizeof(float2);

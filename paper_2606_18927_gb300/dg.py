@@ -353,7 +353,7 @@ class Operator:
         self._check(lib().dg_set_params(self.h, float(kappa), float(B)))
 
     def set_lifting_arithmetic(self, mode):
-        """0: FP64 lifting kernel; 1: double-float lifting (FP64 viscous form, N = 7)."""
+        """0: FP64 lifting kernel; 1: double-float lifting (FP64 viscous form, odd N; the default)."""
         self._check(lib().dg_set_lifting_arithmetic(self.h, int(mode)))
 
     def set_wall_solve_limit(self, max_iter):
