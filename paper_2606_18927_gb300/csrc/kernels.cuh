@@ -689,12 +689,14 @@ __device__ __forceinline__ void riemann_dissipation(const PhysDev& ph, const Pri
     if (l5 < del) l5 = (l5 * l5 + del * del) / (R(2) * del);
     const R w1 = l1 * a1, w2 = l2 * a2, w5 = l5 * a5, ws = l2 * rt;
     const R dut = du - dun * nx, dvt = dv - dun * ny, dwt = dw - dun * nz;
-    const R D0 = w1 + w2 + w5;
-    const R D1 = w1 * (u - c * nx) + w2 * u + w5 * (u + c * nx) + ws * dut;
-    const R D2 = w1 * (v - c * ny) + w2 * v + w5 * (v + c * ny) + ws * dvt;
-    const R D3 = w1 * (w - c * nz) + w2 * w + w5 * (w + c * nz) + ws * dwt;
-    const R D4 = w1 * (H - c * un) + w2 * (R(0.5) * q2) + w5 * (H + c * un) +
-                 ws * (u * du + v * dv + w * dw - un * dun);
+    // sum of the waves' |lambda| alpha r: with the acoustic pair's sum and
+    // difference, w1 (u - c n) + w2 u + w5 (u + c n) = u D0 + n c (w5 - w1)
+    const R sw = w1 + w5, cdw = c * (w5 - w1);
+    const R D0 = sw + w2;
+    const R D1 = u * D0 + nx * cdw + ws * dut;
+    const R D2 = v * D0 + ny * cdw + ws * dvt;
+    const R D3 = w * D0 + nz * cdw + ws * dwt;
+    const R D4 = H * sw + un * cdw + w2 * (R(0.5) * q2) + ws * (u * du + v * dv + w * dw - un * dun);
     F[0] -= R(0.5) * D0; F[1] -= R(0.5) * D1; F[2] -= R(0.5) * D2;
     F[3] -= R(0.5) * D3; F[4] -= R(0.5) * D4;
   }
