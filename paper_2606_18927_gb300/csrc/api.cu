@@ -862,7 +862,14 @@ int dg_set_lifting_arithmetic(dg_ctx* c, int mode) {
       dg::k_split_pairs<<<blocks, 256, 0, c->stream>>>(6 * S, c->Mj, c->lift_M2 + 18 * c->S);
       e = cudaGetLastError();
     }
-    if (e != cudaSuccess) return cuda_fail(c, e, "dg_set_lifting_arithmetic");
+    if (e != cudaSuccess) {
+      // leave no half-built pair arrays behind: the FP64 lifting stays in use
+      if (c->lift_M2) cudaFree(c->lift_M2);
+      if (c->lift_W2) cudaFree(c->lift_W2);
+      c->lift_M2 = nullptr;
+      c->lift_W2 = nullptr;
+      return cuda_fail(c, e, "dg_set_lifting_arithmetic");
+    }
   }
   c->ph.lift_df = mode;
   c->w64_of_U = false;  // the next evaluation forms the stored primitives (and their pairs) again
