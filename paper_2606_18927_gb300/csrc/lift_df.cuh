@@ -103,6 +103,114 @@ __device__ __forceinline__ DFl df_ld(const float2* p) {
 }
 __device__ __forceinline__ void df_st(float2* p, DFl a) { *p = make_float2(a.hi, a.lo); }
 
+// Two floats in one 64-bit register pair, operands of the packed FP32
+// instructions of sm_100 and later (add/sub/mul/fma.rn.f32x2: one instruction
+// for two lanes, each rounded to nearest as its scalar form, so that the
+// error-free transformations stay exact lane by lane).
+typedef unsigned long long f32x2;
+
+__device__ __forceinline__ f32x2 pk2(float a, float b) {
+  f32x2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void upk2(f32x2 r, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
+  f32x2 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
+  f32x2 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
+  f32x2 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+  f32x2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
+// two double-floats side by side: (hi0, hi1) and (lo0, lo1)
+struct DF2 {
+  f32x2 hi, lo;
+};
+
+// TwoSum and its mirror TwoDiff (a - b, the TwoSum of a and -b), lane by lane
+__device__ __forceinline__ void two_sum2(f32x2 a, f32x2 b, f32x2& s, f32x2& e) {
+  s = add2(a, b);
+  const f32x2 bb = sub2(s, a);
+  e = add2(sub2(a, sub2(s, bb)), sub2(b, bb));
+}
+__device__ __forceinline__ void two_diff2(f32x2 a, f32x2 b, f32x2& s, f32x2& e) {
+  s = sub2(a, b);
+  const f32x2 bb = sub2(s, a);
+  e = sub2(sub2(a, sub2(s, bb)), add2(b, bb));
+}
+__device__ __forceinline__ DF2 df_norm2(f32x2 s, f32x2 t) {
+  const f32x2 h = add2(s, t);
+  return DF2{h, sub2(t, sub2(h, s))};
+}
+__device__ __forceinline__ DF2 df_add2(DF2 a, DF2 b) {
+  f32x2 s, e;
+  two_sum2(a.hi, b.hi, s, e);
+  return df_norm2(s, add2(e, add2(a.lo, b.lo)));
+}
+__device__ __forceinline__ DF2 df_sub2(DF2 a, DF2 b) {
+  f32x2 s, e;
+  two_diff2(a.hi, b.hi, s, e);
+  return df_norm2(s, add2(e, sub2(a.lo, b.lo)));
+}
+
+// Dot2 step A += c x with the coefficient given as (c_hi, -c_hi, -c_lo), both
+// lanes alike: the product's error is formed negated, -(c x - p) =
+// fma(-c_hi, x_hi, p) - c_hi x_lo - c_lo x_hi, which rounds exactly as the
+// scalar acc_fma's positive form (rounding to nearest is symmetric)
+struct DFAcc2 {
+  f32x2 s, t;
+};
+__device__ __forceinline__ void acc_fma2(DFAcc2& A, f32x2 ch, f32x2 chn, f32x2 cln, DF2 x) {
+  const f32x2 p = mul2(ch, x.hi);
+  f32x2 en = fma2(chn, x.hi, p);
+  en = fma2(chn, x.lo, en);
+  en = fma2(cln, x.hi, en);
+  f32x2 s, r;
+  two_sum2(A.s, p, s, r);
+  A.s = s;
+  A.t = add2(A.t, sub2(r, en));
+}
+
+__device__ __forceinline__ DF2 df2_ld(const float4* p) {
+  const float4 v = *p;
+  return DF2{pk2(v.x, v.y), pk2(v.z, v.w)};
+}
+__device__ __forceinline__ void df2_st(float4* p, DF2 a) {
+  float h0, h1, l0, l1;
+  upk2(a.hi, h0, h1);
+  upk2(a.lo, l0, l1);
+  *p = make_float4(h0, h1, l0, l1);
+}
+// variable 0 or 1 of a stored pair (hi0, hi1, lo0, lo1)
+__device__ __forceinline__ DFl df_ld4(const float4* p, int which) {
+  const float4 v = *p;
+  return which ? DFl{v.y, v.w} : DFl{v.x, v.z};
+}
+
+// even/odd line coefficients of the lifting (D) and of the weak divergence
+// (w_m / w_i D_mi) as packed broadcasts (c_hi, -c_hi, -c_lo), LineEO::coef order
+template <int N>
+struct LiftDfCoef {
+  static constexpr int NE = (N + 1) * ((N + 1) / 2);
+  f32x2 g[3][NE], v[3][NE];
+};
+
 // shared memory of k_lift_df (in float2): W 4 n3, face jumps 24 n2, G 12 n3
 template <int N>
 struct LiftDfShape {
@@ -125,13 +233,16 @@ __device__ __forceinline__ int df_slot(int node) {
 template <int N>
 __global__ void __launch_bounds__((N + 1) * (N + 1) * (N + 1), ((N + 1) * (N + 1) * (N + 1) <= 512 ? 2 : 1))
 k_lift_df(const double* __restrict__ U, const MeshDev<double> m, const PhysDev ph, const Tables<N> tab,
-          double* __restrict__ Rv, double* __restrict__ Gf) {
+          const LiftDfCoef<N> cf, double* __restrict__ Rv, double* __restrict__ Gf) {
   static_assert(N % 2 == 1, "the double-float lifting kernel needs an even node count");
   constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* sW = reinterpret_cast<float2*>(smem_raw);  // [4][n3] u, v, w, T - T_ref
-  float2* sC = sW + 4 * n3;                          // [6][4][n2] 2 (W* - W)
-  float2* sG = sC + 24 * n2;                         // [3][4][n3]
+  // the four lifted variables in two pairs (u, v), (w, T - T_ref), each slot
+  // one float4 (hi0, hi1, lo0, lo1): a line thread contracts both variables
+  // of a pair with packed instructions
+  float4* sW = reinterpret_cast<float4*>(smem_raw);          // [2][n3]
+  float2* sC = reinterpret_cast<float2*>(sW + 2 * n3);       // [6][4][n2] 2 (W* - W)
+  float4* sG = reinterpret_cast<float4*>(sC + 24 * n2);      // [3][2][n3]
   const int e = blockIdx.x, tid = threadIdx.x;
   const int i = tid % n, j = (tid / n) % n, k = tid / n2;
   const int p = tid;
@@ -140,7 +251,10 @@ k_lift_df(const double* __restrict__ U, const MeshDev<double> m, const PhysDev p
   const int sp = df_slot<N>(p);
   // own primitives (stored as (hi, lo) pairs by k_prim64)
 #pragma unroll
-  for (int v = 0; v < 4; ++v) sW[v * n3 + sp] = m.lift_W2[v * S + g];
+  for (int pr = 0; pr < 2; ++pr) {
+    const float2 a = m.lift_W2[2 * pr * S + g], b = m.lift_W2[(2 * pr + 1) * S + g];
+    sW[pr * n3 + sp] = make_float4(a.x, b.x, a.y, b.y);
+  }
   // 2 (W* - W) at the six faces, in FP64 from the stored primitives (the
   // jumps are differences of nearby values: exact or nearly so), then split
   for (int t = tid; t < 6 * n2; t += n3) {
@@ -155,15 +269,16 @@ k_lift_df(const double* __restrict__ U, const MeshDev<double> m, const PhysDev p
     for (int v = 0; v < 4; ++v) df_st(&sC[(l * 4 + v) * n2 + ab], df_of(dd[v]));
   }
   __syncthreads();
-  // line contraction by thread tid < 6 n2: two variables (v0, v0 + 1) on line L of
-  // direction dir, y_q = sum_m C_qm x_m for the n nodes, in place or into dst;
-  // in even/odd form (C centro-antisymmetric: with xe_m = x_m + x_{N-m},
+  // line contraction by thread tid < 6 n2: the variable pair pr (both
+  // variables in the lanes of the packed instructions) on line L of direction
+  // dir, y_q = sum_m C_qm x_m for the n nodes, in place or into dst; in
+  // even/odd form (C centro-antisymmetric: with xe_m = x_m + x_{N-m},
   // xo_m = x_m - x_{N-m}, E_q = sum_{m<n/2} Ce_qm xe_m, O_q = sum Co_qm xo_m:
   // y_q = E_q + O_q, y_{N-q} = O_q - E_q; tables as LineEO::coef)
-  auto line_pass = [&](const float2* src, float2* dst, bool divergence) {
+  auto line_pass = [&](const float4* src, float4* dst, bool divergence) {
     constexpr int h = n / 2;
     for (int task = tid; task < 6 * n2; task += n3) {
-      const int dir = task / (2 * n2), r = task - dir * 2 * n2, v0 = 2 * (r / n2), L = r % n2;
+      const int dir = task / (2 * n2), r = task - dir * 2 * n2, pr = r / n2, L = r % n2;
       const int n0 = dir == 0 ? n * L : (dir == 1 ? (L % n) + n2 * (L / n) : L);
       const int stride = dir == 0 ? 1 : (dir == 1 ? n : n2);
       int sl[n];
@@ -176,34 +291,32 @@ k_lift_df(const double* __restrict__ U, const MeshDev<double> m, const PhysDev p
 #pragma unroll
         for (int q = 0; q < n; ++q) sl[q] = n0 + q * stride;
       }
-      const float* ch = divergence ? tab.Dveo32 : tab.Deo32;
-      const float* cl = divergence ? tab.Dveo32lo : tab.Deo32lo;
+      const f32x2(*c)[LiftDfCoef<N>::NE] = divergence ? cf.v : cf.g;
+      const float4* xs = src + (divergence ? (dir * 2 + pr) : pr) * n3;
+      float4* ys = dst + (dir * 2 + pr) * n3;
+      DF2 xe[h], xo[h];
 #pragma unroll
-      for (int v = 0; v < 2; ++v) {
-        const int row = divergence ? (dir * 4 + v0 + v) : (v0 + v);
-        DFl xe[h], xo[h];
+      for (int mm = 0; mm < h; ++mm) {
+        const DF2 a = df2_ld(&xs[sl[mm]]), b = df2_ld(&xs[sl[N - mm]]);
+        xe[mm] = df_add2(a, b);
+        xo[mm] = df_sub2(a, b);
+      }
+#pragma unroll
+      for (int q = 0; q < h; ++q) {
+        DFAcc2 E{0ull, 0ull}, O{0ull, 0ull};
 #pragma unroll
         for (int mm = 0; mm < h; ++mm) {
-          const DFl a = df_ld(&src[row * n3 + sl[mm]]), b = df_ld(&src[row * n3 + sl[N - mm]]);
-          xe[mm] = df_add(a, b);
-          xo[mm] = df_sub(a, b);
+          const int te = q * h + mm, to = (N - q) * h + mm;
+          acc_fma2(E, c[0][te], c[1][te], c[2][te], xe[mm]);
+          acc_fma2(O, c[0][to], c[1][to], c[2][to], xo[mm]);
         }
-#pragma unroll
-        for (int q = 0; q < h; ++q) {
-          DFAcc E{0.f, 0.f}, O{0.f, 0.f};
-#pragma unroll
-          for (int mm = 0; mm < h; ++mm) {
-            acc_fma(E, DFl{ch[q * h + mm], cl[q * h + mm]}, xe[mm]);
-            acc_fma(O, DFl{ch[(N - q) * h + mm], cl[(N - q) * h + mm]}, xo[mm]);
-          }
-          float s, e;
-          two_sum(O.s, E.s, s, e);
-          const DFl yq = df_norm(s, __fadd_rn(__fadd_rn(O.t, E.t), e));
-          two_sum(O.s, -E.s, s, e);
-          const DFl ym = df_norm(s, __fadd_rn(__fsub_rn(O.t, E.t), e));
-          df_st(&dst[(dir * 4 + v0 + v) * n3 + sl[q]], yq);
-          df_st(&dst[(dir * 4 + v0 + v) * n3 + sl[N - q]], ym);
-        }
+        f32x2 s, e;
+        two_sum2(O.s, E.s, s, e);
+        const DF2 yq = df_norm2(s, add2(add2(O.t, E.t), e));
+        two_diff2(O.s, E.s, s, e);
+        const DF2 ym = df_norm2(s, add2(sub2(O.t, E.t), e));
+        df2_st(&ys[sl[q]], yq);
+        df2_st(&ys[sl[N - q]], ym);
       }
     }
   };
@@ -214,7 +327,7 @@ k_lift_df(const double* __restrict__ U, const MeshDev<double> m, const PhysDev p
 #pragma unroll
   for (int dir = 0; dir < 3; ++dir)
 #pragma unroll
-    for (int v = 0; v < 4; ++v) dW[dir][v] = df_ld(&sG[(dir * 4 + v) * n3 + sp]);
+    for (int v = 0; v < 4; ++v) dW[dir][v] = df_ld4(&sG[(dir * 2 + (v >> 1)) * n3 + sp], v & 1);
   // surface corrections: sC holds 2 (W* - W), the weights are 1 / (2 w)
   const DFl shw0 = df_of(0.5 * tab.iw[0]), shwN = df_of(0.5 * tab.iw[N]);
   auto surf = [&](int dir, int l, int ab, DFl sw) {
@@ -266,7 +379,7 @@ k_lift_df(const double* __restrict__ U, const MeshDev<double> m, const PhysDev p
   // G^dir_E = sum_c u_c G^dir_c + k (Ja^dir . grad T)
   DFl G[3][4];
   {
-    const DFl uu = df_ld(&sW[sp]), vv = df_ld(&sW[n3 + sp]), ww = df_ld(&sW[2 * n3 + sp]);
+    const DFl uu = df_ld4(&sW[sp], 0), vv = df_ld4(&sW[sp], 1), ww = df_ld4(&sW[n3 + sp], 0);
 #pragma unroll
     for (int dir = 0; dir < 3; ++dir) {
       const DFl a0 = df_ld(&m.lift_M2[(size_t)(dir * 3 + 0) * S + g]),
@@ -299,7 +412,10 @@ k_lift_df(const double* __restrict__ U, const MeshDev<double> m, const PhysDev p
 #pragma unroll
   for (int dir = 0; dir < 3; ++dir)
 #pragma unroll
-    for (int v = 0; v < 4; ++v) df_st(&sG[(dir * 4 + v) * n3 + sp], G[dir][v]);
+    for (int pr = 0; pr < 2; ++pr) {
+      const DFl a = G[dir][2 * pr], b = G[dir][2 * pr + 1];
+      sG[(dir * 2 + pr) * n3 + sp] = make_float4(a.hi, b.hi, a.lo, b.lo);
+    }
   __syncthreads();
   line_pass(sG, sG, true);  // in place: a line's slots belong to its thread
   __syncthreads();
@@ -307,7 +423,7 @@ k_lift_df(const double* __restrict__ U, const MeshDev<double> m, const PhysDev p
   for (int v = 0; v < 4; ++v) {
     DFAcc A{0.f, 0.f};
 #pragma unroll
-    for (int dir = 0; dir < 3; ++dir) acc_add(A, df_ld(&sG[(dir * 4 + v) * n3 + sp]));
+    for (int dir = 0; dir < 3; ++dir) acc_add(A, df_ld4(&sG[(dir * 2 + (v >> 1)) * n3 + sp], v & 1));
     Rv[(size_t)v * S + g] = df_to(acc_val(A));
   }
 }

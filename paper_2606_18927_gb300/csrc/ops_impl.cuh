@@ -1,6 +1,8 @@
 // ops_impl.cuh -- host launch code for one polynomial degree (included by
 // op_n<N>.cu with DG_N defined).
 #pragma once
+
+#include <cstring>
 #include <algorithm>
 #include <type_traits>
 
@@ -44,6 +46,27 @@ static Tables<N> make_tables(const double* D, const double* w) {
     t.Dveo32[t2] = (float)cv; t.Dveo32lo[t2] = (float)(cv - (double)t.Dveo32[t2]);
   }
   return t;
+}
+
+// the double-float lifting's line coefficients as packed broadcasts
+// (c_hi, -c_hi, -c_lo) of the even/odd tables
+static inline unsigned long long bcast2(float x) {
+  unsigned int b;
+  std::memcpy(&b, &x, 4);
+  return (unsigned long long)b | ((unsigned long long)b << 32);
+}
+template <int N>
+static LiftDfCoef<N> make_lift_df_coef(const Tables<N>& t) {
+  LiftDfCoef<N> c;
+  for (int i = 0; i < LiftDfCoef<N>::NE; ++i) {
+    c.g[0][i] = bcast2(t.Deo32[i]);
+    c.g[1][i] = bcast2(-t.Deo32[i]);
+    c.g[2][i] = bcast2(-t.Deo32lo[i]);
+    c.v[0][i] = bcast2(t.Dveo32[i]);
+    c.v[1][i] = bcast2(-t.Dveo32[i]);
+    c.v[2][i] = bcast2(-t.Dveo32lo[i]);
+  }
+  return c;
 }
 
 template <int N, typename R>
@@ -130,7 +153,7 @@ static int run_typed(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {
         if (ph.lift_df && m.W64 && m.lift_M2 && m.lift_W2) {
           const size_t smem_df = (size_t)LiftDfShape<N>::SMEM_F2 * sizeof(float2);
           cudaFuncSetAttribute(k_lift_df<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_df);
-          k_lift_df<N><<<a.K, n3, smem_df, s>>>(a.Uin, m, ph, tab, Rv, Gf);
+          k_lift_df<N><<<a.K, n3, smem_df, s>>>(a.Uin, m, ph, tab, make_lift_df_coef<N>(tab), Rv, Gf);
           done = true;
         }
       }
