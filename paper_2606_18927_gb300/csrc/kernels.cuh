@@ -518,12 +518,12 @@ static __global__ void k_prim64(long long S, const double* __restrict__ U, const
   }
 }
 
-// x -> (hi, lo) float pairs (the double-float lifting's metric arrays)
+// x -> (hi, lo) float pairs, both rounded to nearest (hi + lo = x to 2^-48;
+// the double-float kernels' metric arrays, split once)
 static __global__ void k_split_pairs(long long n, const double* __restrict__ x, float2* __restrict__ y) {
   for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < n; g += (long long)gridDim.x * blockDim.x) {
-    float lo;
-    const float hi = d2f_bits(x[g], &lo);
-    y[g] = make_float2(hi, lo);
+    const float hi = __double2float_rn(x[g]);
+    y[g] = make_float2(hi, __double2float_rn(x[g] - (double)hi));
   }
 }
 
