@@ -40,7 +40,7 @@ L2_BYTES = 129e6  # GB300 L2 (nominal)
 # capture of the same kernel build on a 16^3-element case, scaled to the
 # launch size by the DOF count (traffic is proportional to the DOF count).
 NCU_TRAFFIC_PER_DOF = {("k_volume", "fp64", 7): (830.92e6 + 157.87e6) / 2097152,
-                       ("k_volume", "fp32", 7): (308.57e6 + 192.35e6) / 2097152}
+                       ("k_volume", "fp32", 7): (308.59e6 + 204.15e6) / 2097152}
 # algorithmic HBM bytes per DOF of the FP32-mixed volume kernel (stage form):
 # U read 40 and written 40, dU read and written 80, FP32 primitives and the
 # velocity's low parts read 36 and written 36, Ja + 1/J 40, R_v 16, surface
