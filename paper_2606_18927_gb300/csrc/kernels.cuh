@@ -667,17 +667,20 @@ __device__ __forceinline__ void riemann_dissipation(const PhysDev& ph, const Pri
     const R sA = sqrt_t<R>(A.rho), sB = sqrt_t<R>(B.rho);
     const R is = rcp_t<R>(sA + sB);
     const R rt = sA * sB;
-    const R u = (sA * A.u + sB * B.u) * is, v = (sA * A.v + sB * B.v) * is, w = (sA * A.w + sB * B.w) * is;
-    const R H = (sA * A.h + sB * B.h) * is;
+    // (the FP32 difference form passes the velocity jump from the velocities'
+    // high and low parts: from the rounded velocities it would carry an error
+    // eps32 |u| that the acoustic waves multiply by rho c)
+    const R du = dvel ? dvel[0] : B.u - A.u, dv = dvel ? dvel[1] : B.v - A.v, dw = dvel ? dvel[2] : B.w - A.w;
+    // Roe averages (sqrt(rho_A) x_A + sqrt(rho_B) x_B) / (sqrt(rho_A) + sqrt(rho_B))
+    // as x_A + f (x_B - x_A), f = sqrt(rho_B) / (sqrt(rho_A) + sqrt(rho_B))
+    const R f = sB * is;
+    const R u = fma(f, du, A.u), v = fma(f, dv, A.v), w = fma(f, dw, A.w);
+    const R H = fma(f, B.h - A.h, A.h);
     const R q2 = u * u + v * v + w * w;
     const R c2 = (g - R(1)) * (H - R(0.5) * q2);
     const R c = sqrt_t<R>(c2);
     const R un = u * nx + v * ny + w * nz;
     const R dr = drho ? *drho : B.rho - A.rho, dp = B.p - A.p;
-    // (the FP32 difference form passes the velocity jump from the velocities'
-    // high and low parts: from the rounded velocities it would carry an error
-    // eps32 |u| that the acoustic waves multiply by rho c)
-    const R du = dvel ? dvel[0] : B.u - A.u, dv = dvel ? dvel[1] : B.v - A.v, dw = dvel ? dvel[2] : B.w - A.w;
     const R dun = du * nx + dv * ny + dw * nz;
     const R i2c2 = R(0.5) * rcp_t<R>(c2);
     const R a1 = (dp - rt * c * dun) * i2c2;
@@ -696,7 +699,8 @@ __device__ __forceinline__ void riemann_dissipation(const PhysDev& ph, const Pri
     const R D1 = u * D0 + nx * cdw + ws * dut;
     const R D2 = v * D0 + ny * cdw + ws * dvt;
     const R D3 = w * D0 + nz * cdw + ws * dwt;
-    const R D4 = H * sw + un * cdw + w2 * (R(0.5) * q2) + ws * (u * du + v * dv + w * dw - un * dun);
+    // (u . du - un dun = u . (du - dun n))
+    const R D4 = H * sw + un * cdw + w2 * (R(0.5) * q2) + ws * (u * dut + v * dvt + w * dwt);
     F[0] -= R(0.5) * D0; F[1] -= R(0.5) * D1; F[2] -= R(0.5) * D2;
     F[3] -= R(0.5) * D3; F[4] -= R(0.5) * D4;
   }
