@@ -1282,6 +1282,48 @@ __device__ __forceinline__ void lift_face_jump(const double* __restrict__ U, con
   dd[0] = d0; dd[1] = d1; dd[2] = d2; dd[3] = d3;
 }
 
+// Two floats in one 64-bit register pair, operands of the packed FP32
+// instructions of sm_100 and later (add/sub/mul/fma.rn.f32x2: one instruction
+// for two lanes, each rounded to nearest as its scalar form, so that the
+// error-free transformations stay exact lane by lane).
+typedef unsigned long long f32x2;
+
+__device__ __forceinline__ f32x2 pk2(float a, float b) {
+  f32x2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void upk2(f32x2 r, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
+  f32x2 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
+  f32x2 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
+  f32x2 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+  f32x2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
+// the FP32 lifting kernel's line coefficients (D and Dvisc, rounded to FP32)
+// as packed broadcasts (c, c): a line thread contracts two variables at once
+template <int N>
+struct LiftPk {
+  f32x2 d[(N + 1) * (N + 1)], dv[(N + 1) * (N + 1)];
+};
+
 // Resident CTAs per SM asked of the register allocator for the lifting
 // kernel: two for CTAs of up to 512 threads, three for the FP32 kernel at
 // N = 7 (42 registers; its line phases leave the other threads waiting at a
@@ -1294,7 +1336,7 @@ constexpr int lift_min_blocks() {
 template <int N, typename R>
 __global__ void __launch_bounds__((N + 1) * (N + 1) * (N + 1), (lift_min_blocks<N, R>()))
 k_lift(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const Tables<N> tab,
-       R* __restrict__ Rv, R* __restrict__ Gf) {
+       const LiftPk<N> pk, R* __restrict__ Rv, R* __restrict__ Gf) {
   constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
   // FP64, N = 7: line contractions in even/odd form (LineEO), with the thread
   // of each node sharing a warp with its three mirror nodes (the FP32 kernel is
@@ -1402,20 +1444,21 @@ k_lift(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
 #pragma unroll
       for (int q = 0; q < n; ++q)
         sl[q] = s0 ^ (dir == 0 ? lift_slot8(q) : (dir == 1 ? lift_slot8(q * n) : lift_slot8(q * n2)));
-      R x[2][n];
+      // the two variables in the lanes of packed FMAs (each lane the scalar
+      // FMA chain's roundings)
+      f32x2 x[n];
 #pragma unroll
-      for (int q = 0; q < n; ++q)
+      for (int q = 0; q < n; ++q) x[q] = pk2(sW[v0 * n3 + sl[q]], sW[(v0 + 1) * n3 + sl[q]]);
 #pragma unroll
-        for (int v = 0; v < 2; ++v) x[v][q] = sW[(v0 + v) * n3 + sl[q]];
+      for (int q = 0; q < n; ++q) {
+        f32x2 y = pk2(0.f, 0.f);
 #pragma unroll
-      for (int q = 0; q < n; ++q)
-#pragma unroll
-        for (int v = 0; v < 2; ++v) {
-          R y = R(0);
-#pragma unroll
-          for (int mm = 0; mm < n; ++mm) y = fmaf(tab.D32[q * n + mm], x[v][mm], y);
-          sG[(dir * 4 + v0 + v) * n3 + sl[q]] = y;
-        }
+        for (int mm = 0; mm < n; ++mm) y = fma2(pk.d[q * n + mm], x[mm], y);
+        float y0, y1;
+        upk2(y, y0, y1);
+        sG[(dir * 4 + v0) * n3 + sl[q]] = y0;
+        sG[(dir * 4 + v0 + 1) * n3 + sl[q]] = y1;
+      }
     }
     __syncthreads();
     const int sp = lift_slot8(p);
@@ -1583,20 +1626,20 @@ k_lift(const double* __restrict__ U, const MeshDev<R> m, const PhysDev ph, const
 #pragma unroll
       for (int q = 0; q < n; ++q)
         sl[q] = s0 ^ (dir == 0 ? lift_slot8(q) : (dir == 1 ? lift_slot8(q * n) : lift_slot8(q * n2)));
-      R x[2][n];
+      f32x2 x[n];
 #pragma unroll
       for (int q = 0; q < n; ++q)
+        x[q] = pk2(sG[(dir * 4 + v0) * n3 + sl[q]], sG[(dir * 4 + v0 + 1) * n3 + sl[q]]);
 #pragma unroll
-        for (int v = 0; v < 2; ++v) x[v][q] = sG[(dir * 4 + v0 + v) * n3 + sl[q]];
+      for (int q = 0; q < n; ++q) {
+        f32x2 y = pk2(0.f, 0.f);
 #pragma unroll
-      for (int q = 0; q < n; ++q)
-#pragma unroll
-        for (int v = 0; v < 2; ++v) {
-          R y = R(0);
-#pragma unroll
-          for (int mm = 0; mm < n; ++mm) y = fmaf(tab.Dvisc32[q * n + mm], x[v][mm], y);
-          sG[(dir * 4 + v0 + v) * n3 + sl[q]] = y;
-        }
+        for (int mm = 0; mm < n; ++mm) y = fma2(pk.dv[q * n + mm], x[mm], y);
+        float y0, y1;
+        upk2(y, y0, y1);
+        sG[(dir * 4 + v0) * n3 + sl[q]] = y0;
+        sG[(dir * 4 + v0 + 1) * n3 + sl[q]] = y1;
+      }
     }
     __syncthreads();
 #pragma unroll

@@ -69,6 +69,16 @@ static LiftDfCoef<N> make_lift_df_coef(const Tables<N>& t) {
   return c;
 }
 
+template <int N>
+static LiftPk<N> make_lift_pk(const Tables<N>& t) {
+  LiftPk<N> c;
+  for (int i = 0; i < (N + 1) * (N + 1); ++i) {
+    c.d[i] = bcast2(t.D32[i]);
+    c.dv[i] = bcast2(t.Dvisc32[i]);
+  }
+  return c;
+}
+
 template <int N, typename R>
 static int run_typed(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {
   constexpr int n = N + 1, n2 = n * n, n3 = n2 * n;
@@ -157,7 +167,7 @@ static int run_typed(const OpArgs& a, const PhysDev& ph, cudaStream_t s) {
           done = true;
         }
       }
-      if (!done) k_lift<N, R><<<a.K, n3, smem_lift, s>>>(a.Uin, m, ph, tab, Rv, Gf);
+      if (!done) k_lift<N, R><<<a.K, n3, smem_lift, s>>>(a.Uin, m, ph, tab, make_lift_pk<N>(tab), Rv, Gf);
     }
     if (a.ev) cudaEventRecord(a.ev[1], s);
     if (a.n_halo > 0 && a.send_G && ph.viscous)
