@@ -480,8 +480,9 @@ static __device__ __noinline__ Prim<double> primitive_T(const double U0, const d
   const double u = U1 * ir, v = U2 * ir, w = U3 * ir;
   const double p = ph.gm1 * (U4 - 0.5 * (U1 * u + U2 * v + U3 * w));
   q.rho = U0; q.u = u; q.v = v; q.w = w; q.p = p - ph.p_ref;
-  q.h = (U4 + p) * ir;
-  T = p * ph.rcp_R * ir;
+  const double pir = p * ir;  // p / rho: h = E / rho + p / rho, T = (p / rho) / R
+  q.h = fma(U4, ir, pir);
+  T = pir * ph.rcp_R;
   return q;
 }
 
@@ -626,6 +627,20 @@ __device__ __forceinline__ void twopoint(int kind, const Prim<R>& A, const Prim<
     }
   }
   const R pref = cR<R>(ph.p_ref, ph.f32c.p_ref);
+  if (kind == 0) {
+    // Pirozzoli from the sums S = x_A + x_B ({x} = S / 2), the powers of two
+    // applied once: m = {rho}{u}.a = Sr (Su.a) / 4, F_k = m {u_k} + {p} a_k =
+    // (m / 2) Su_k + (Sp / 2) a_k, F_4 = m {h} = (m / 2) Sh
+    const R Sr = A.rho + B.rho, Su = A.u + B.u, Sv = A.v + B.v, Sw = A.w + B.w, Sp = A.p + B.p;
+    const R m4 = Sr * (Su * a0 + Sv * a1 + Sw * a2);
+    const R m8 = R(0.125) * m4, hp = R(0.5) * Sp;
+    F[0] = R(0.25) * m4;
+    F[1] = m8 * Su + hp * a0;
+    F[2] = m8 * Sv + hp * a1;
+    F[3] = m8 * Sw + hp * a2;
+    F[4] = m8 * (A.h + B.h);
+    return;
+  }
   const R rho = R(0.5) * (A.rho + B.rho);
   const R u = R(0.5) * (A.u + B.u), v = R(0.5) * (A.v + B.v), w = R(0.5) * (A.w + B.w);
   const R p = R(0.5) * (A.p + B.p);
@@ -635,9 +650,7 @@ __device__ __forceinline__ void twopoint(int kind, const Prim<R>& A, const Prim<
   F[1] = m * u + p * a0;
   F[2] = m * v + p * a1;
   F[3] = m * w + p * a2;
-  if (kind == 0) {
-    F[4] = m * (R(0.5) * (A.h + B.h));
-  } else {  // Kennedy-Gruber: {rho}{u.a}{e} + {p}{u.a}, e = E / rho = h - p / rho (full p)
+  {  // Kennedy-Gruber: {rho}{u.a}{e} + {p}{u.a}, e = E / rho = h - p / rho (full p)
     const R pA = A.p + pref, pB = B.p + pref;
     const R eA = A.h - pA / A.rho, eB = B.h - pB / B.rho;
     F[4] = m * (R(0.5) * (eA + eB)) + (p + pref) * ua;
