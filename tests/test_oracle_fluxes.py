@@ -2,7 +2,9 @@
 
 Numerical fluxes: consistency, symmetry of the two-point flux and Roe's
 property A~ (UR - UL) = F(UR) - F(UL) (paper Sec. 4: Roe solver with
-Harten's entropy fix).  Wall model (paper Sec. 3.2 and Algorithms 1-2):
+Harten's entropy fix), and for subsonic states the dissipation of single
+waves (contact, shear: exactly |u_n| dU / 2; acoustic: |u_n +- c| dU / 2 to
+first order), which fixes each wave's |lambda| and eigenvector.  Wall model (paper Sec. 3.2 and Algorithms 1-2):
 Spalding's law as printed, the Reichardt law's limits, the Newton solve of
 SolveWallStress, and the Van Driest transform against its defining
 integral."""
@@ -83,6 +85,57 @@ def test_roe_entropy_fix_continuous(ora):
         V = _state(1.0, [un, 0.1, 0.0], 1.0 + 1e-3)
         out.append(ora.riemann(phys, 0, 2, U, V, n))
     assert np.abs(out[0] - out[1]).max() < 1e-7
+
+
+@pytest.mark.parametrize("wave", ["contact", "shear"])
+def test_roe_linear_waves_subsonic(ora, wave):
+    # a jump in density alone (contact) or in the tangential velocity alone
+    # (shear), at equal pressure and normal velocity, is an eigenvector of
+    # Roe's matrix with eigenvalue u_n: the dissipation is |u_n| (UR - UL) / 2
+    # exactly, whatever the sign of u_n (subsonic: the acoustic waves, absent
+    # here, would have eigenvalues of both signs)
+    phys = I.phys_params()
+    rng = np.random.default_rng(7)
+    for it in range(20):
+        n = _rand_unit(rng)
+        t = np.cross(n, _rand_unit(rng))
+        t /= np.linalg.norm(t)
+        un = (0.6 if it % 2 else -0.6) * rng.uniform(0.2, 1.0)
+        rho, p = rng.uniform(0.8, 1.2), rng.uniform(0.8, 1.2)
+        uL = un * n + rng.normal() * t
+        if wave == "contact":
+            UL, UR = _state(rho, uL, p), _state(rho * rng.uniform(1.1, 1.5), uL, p)
+        else:
+            UL, UR = _state(rho, uL, p), _state(rho, uL + rng.uniform(0.2, 0.5) * t, p)
+        Froe = ora.riemann(phys, 0, 2, UL, UR, n)
+        Fc = ora.riemann(phys, 0, 0, UL, UR, n)
+        assert np.allclose(Froe - Fc, -0.5 * abs(un) * (UR - UL), rtol=1e-12, atol=1e-13)
+
+
+@pytest.mark.parametrize("family", [-1.0, 1.0])
+def test_roe_acoustic_waves_subsonic(ora, family):
+    # UR = UL + eps r with r = (1, u +- c n, H +- c u_n), the acoustic
+    # eigenvector of the Euler Jacobian at UL: the Roe dissipation is
+    # |u_n +- c| (UR - UL) / 2 to first order in eps (the Roe average differs
+    # from UL by O(eps)); u_n +- c stays outside Harten's band
+    phys = I.phys_params()
+    g = 1.4
+    rng = np.random.default_rng(8)
+    eps = 1e-6
+    for _ in range(20):
+        n = _rand_unit(rng)
+        rho, p = rng.uniform(0.8, 1.2), rng.uniform(0.8, 1.2)
+        c = math.sqrt(g * p / rho)
+        u = rng.uniform(-0.5, 0.5) * c * n + 0.3 * c * np.cross(n, _rand_unit(rng))
+        UL = _state(rho, u, p)
+        un = u @ n
+        H = (UL[4] + p) / rho
+        r = np.array([1.0, *(u + family * c * n), H + family * c * un])
+        UR = UL + eps * r
+        Froe = ora.riemann(phys, 0, 2, UL, UR, n)
+        Fc = ora.riemann(phys, 0, 0, UL, UR, n)
+        expect = -0.5 * abs(un + family * c) * (UR - UL)
+        assert np.allclose(Froe - Fc, expect, rtol=1e-5, atol=1e-5 * np.abs(expect).max())
 
 
 def test_llf_dissipation_bounds(ora):
