@@ -23,46 +23,52 @@ PHYS_DEFAULTS = {"suth_S": 0.0, "T_ref": 1.0, "U_in0": 1.0, "U_in4": 1.0, "p_out
 def lib(extended=False):
     """The FP64 oracle library, or its extended-precision build."""
     if extended not in _libs:
-        path = _build.build(extended=extended)
-        L = ctypes.CDLL(path)
-        dp = ctypes.POINTER(ctypes.c_double)
-        ip = ctypes.POINTER(ctypes.c_int)
-        vp = ctypes.c_void_p
-        L.ora_viscosity.argtypes = [dp, ctypes.c_double]
-        L.ora_viscosity.restype = ctypes.c_double
-        L.ora_lgl.argtypes = [ctypes.c_int, dp, dp, dp]
-        L.ora_lserk4.argtypes = [dp, dp, dp]
-        L.ora_set_threads.argtypes = [ctypes.c_int]
-        L.ora_max_threads.restype = ctypes.c_int
-        L.ora_create.argtypes = [ctypes.c_int, ctypes.c_int, dp, ip, ip, ip, dp, ip, ctypes.c_char_p, ctypes.c_int]
-        L.ora_create.restype = vp
-        L.ora_create_subset.argtypes = [ctypes.c_int, ctypes.c_int, dp, ip, ip, ip, dp, ip, ctypes.c_int, ip,
-                                        ctypes.c_char_p, ctypes.c_int]
-        L.ora_create_subset.restype = vp
-        L.ora_destroy.argtypes = [vp]
-        L.ora_get_metrics.argtypes = [vp, dp, dp]
-        L.ora_num_wall.argtypes = [vp]
-        L.ora_get_wall_samples.argtypes = [vp, ip, dp]
-        L.ora_get_wall_weights.argtypes = [vp, dp]
-        L.ora_time_derivative.argtypes = [vp, dp, ctypes.c_double, dp]
-        L.ora_wall_heat.argtypes = [vp, dp, dp]
-        L.ora_jvp.argtypes = [vp, dp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp]
-        L.ora_rk_stage.argtypes = [vp, dp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double]
-        L.ora_rk_steps.argtypes = [vp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_int]
-        L.ora_dt.argtypes = [vp, dp, ctypes.c_double, dp]
-        L.ora_wall_shear.argtypes = [vp, dp, dp]
-        L.ora_rollout_jvp.argtypes = [vp, dp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_int,
-                                      ctypes.c_double, dp, dp]
-        L.ora_kinetic_energy.argtypes = [vp, dp, dp]
-        L.ora_solve_utau.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                     ctypes.c_double, ctypes.c_double, dp]
-        L.ora_law_value.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double]
-        L.ora_law_value.restype = ctypes.c_double
-        L.ora_wall_flux.argtypes = [dp, ctypes.c_int, dp, dp, dp, dp, dp]
-        L.ora_riemann.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp]
-        L.ora_real_digits.restype = ctypes.c_int
-        _libs[extended] = L
+        _libs[extended] = bind(_build.build(extended=extended))
     return _libs[extended]
+
+
+def bind(path):
+    """The oracle's C interface from the shared library at path (its own
+    builds; the pin-strength tests also load copies built with a planted
+    mistake)."""
+    L = ctypes.CDLL(path)
+    dp = ctypes.POINTER(ctypes.c_double)
+    ip = ctypes.POINTER(ctypes.c_int)
+    vp = ctypes.c_void_p
+    L.ora_viscosity.argtypes = [dp, ctypes.c_double]
+    L.ora_viscosity.restype = ctypes.c_double
+    L.ora_lgl.argtypes = [ctypes.c_int, dp, dp, dp]
+    L.ora_lserk4.argtypes = [dp, dp, dp]
+    L.ora_set_threads.argtypes = [ctypes.c_int]
+    L.ora_max_threads.restype = ctypes.c_int
+    L.ora_create.argtypes = [ctypes.c_int, ctypes.c_int, dp, ip, ip, ip, dp, ip, ctypes.c_char_p, ctypes.c_int]
+    L.ora_create.restype = vp
+    L.ora_create_subset.argtypes = [ctypes.c_int, ctypes.c_int, dp, ip, ip, ip, dp, ip, ctypes.c_int, ip,
+                                    ctypes.c_char_p, ctypes.c_int]
+    L.ora_create_subset.restype = vp
+    L.ora_destroy.argtypes = [vp]
+    L.ora_get_metrics.argtypes = [vp, dp, dp]
+    L.ora_num_wall.argtypes = [vp]
+    L.ora_get_wall_samples.argtypes = [vp, ip, dp]
+    L.ora_get_wall_weights.argtypes = [vp, dp]
+    L.ora_time_derivative.argtypes = [vp, dp, ctypes.c_double, dp]
+    L.ora_wall_heat.argtypes = [vp, dp, dp]
+    L.ora_jvp.argtypes = [vp, dp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp]
+    L.ora_rk_stage.argtypes = [vp, dp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double]
+    L.ora_rk_steps.argtypes = [vp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_int]
+    L.ora_dt.argtypes = [vp, dp, ctypes.c_double, dp]
+    L.ora_wall_shear.argtypes = [vp, dp, dp]
+    L.ora_rollout_jvp.argtypes = [vp, dp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                  ctypes.c_double, dp, dp]
+    L.ora_kinetic_energy.argtypes = [vp, dp, dp]
+    L.ora_solve_utau.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                 ctypes.c_double, ctypes.c_double, dp]
+    L.ora_law_value.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+    L.ora_law_value.restype = ctypes.c_double
+    L.ora_wall_flux.argtypes = [dp, ctypes.c_int, dp, dp, dp, dp, dp]
+    L.ora_riemann.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp]
+    L.ora_real_digits.restype = ctypes.c_int
+    return L
 
 
 def _p(a):

@@ -1,12 +1,21 @@
-"""Strength of the Roe-flux pins: each test here plants one plausible
-mistake in a copy of the oracle's Roe solver (a sign, a factor, a missing
-absolute value, swapped Roe-average weights; paper Sec. 4: Roe solver with
-Harten's entropy fix), builds that copy with the oracle's own compiler
-flags, and requires that at least one of the pins of `test_oracle_fluxes`
-(Roe's property on supersonic states, the single-wave dissipations on
-subsonic states) rejects it.  The unchanged source built the same way must
-pass all of them (the control)."""
+"""Strength of the oracle's pins: each test here plants one plausible
+mistake in a copy of the oracle's source (a sign, a factor, a missing
+absolute value or average, a transposed index), builds that copy with the
+oracle's own compiler flags, and requires that at least one pin rejects it.
+
+* Roe solver (paper Sec. 4: Roe with Harten's entropy fix): the pins of
+  `test_oracle_fluxes` (Roe's property on supersonic states, the single-wave
+  dissipations on subsonic states).
+* The operator (Sec. 2.2: split-form DGSEM, BR1 lifting, viscous fluxes):
+  the invariants (metric identities, free stream, conservation, kinetic
+  energy), the point-flux symmetry, the manufactured-solution convergence
+  and the BR1 closed form, run on the planted copy in place of the oracle's
+  library.
+
+The unchanged source built the same way must pass all of them (the
+controls)."""
 import concurrent.futures as cf
+import contextlib
 import ctypes
 import hashlib
 import os
@@ -16,7 +25,11 @@ import numpy as np
 import pytest
 
 import oracle
-from test_oracle_fluxes import check_roe_acoustic_wave, check_roe_linear_wave, check_roe_supersonic
+import test_oracle_invariants as inv
+import test_oracle_lifting as lifting
+import test_oracle_mms as mms_tests
+from test_oracle_fluxes import (check_roe_acoustic_wave, check_roe_linear_wave, check_roe_supersonic,
+                                test_consistency_and_symmetry)
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "dgsem_oracle.cpp")
@@ -123,5 +136,113 @@ def test_control_passes_every_pin(libs):
 @pytest.mark.parametrize("mutant", [m[0] for m in MUTANTS])
 def test_planted_mistake_is_caught(libs, mutant):
     failed = _failing(_riemann_of(libs[mutant]))
+    print(mutant, "rejected by", failed)
+    assert failed, mutant
+
+
+# ---------------------------------------------------------------------------
+# the operator
+# ---------------------------------------------------------------------------
+OPERATOR_MUTANTS = [
+    ("pirozzoli_enthalpy_one_sided",
+     "T h = 0.5 * (L.h + R.h);",
+     "T h = L.h;"),
+    ("pirozzoli_pressure_sign",
+     "for (int c = 0; c < 3; ++c) F[1 + c] = rho * ua * u[c] + p * a[c];",
+     "for (int c = 0; c < 3; ++c) F[1 + c] = rho * ua * u[c] - p * a[c];"),
+    ("volume_metric_not_averaged",
+     "for (int c = 0; c < 3; ++c) abar[c] = 0.5 * (jao[dir * 3 + c] + jam[dir * 3 + c]);",
+     "for (int c = 0; c < 3; ++c) abar[c] = jao[dir * 3 + c];"),
+    ("volume_factor_two_dropped",
+     "for (int v = 0; v < 5; ++v) V[v] += 2.0 * Dim * F[v];",
+     "for (int v = 0; v < 5; ++v) V[v] += Dim * F[v];"),
+    ("viscous_volume_term_sign",
+     "V[v] -= Dim * W.G[",
+     "V[v] += Dim * W.G["),
+    ("br1_average_one_sided",
+     "T Ws = 0.5 * (Wo[w] + Wn[w]);",
+     "T Ws = Wn[w];"),
+    ("lifting_surface_weight_inverted",
+     "(Ws - Wo[w]) * ns[d] * invJ / wperp;",
+     "(Ws - Wo[w]) * ns[d] * invJ * wperp;"),
+    ("stress_transposed_index",
+     "tau[i][j] = mu * (g[j][i] + g[i][j]);",
+     "tau[i][j] = mu * (g[j][i] + g[j][i]);"),
+    ("stress_bulk_factor",
+     "if (i == j) tau[i][j] -= (2.0 / 3.0) * mu * div;",
+     "if (i == j) tau[i][j] -= (1.0 / 3.0) * mu * div;"),
+    ("heat_flux_sign",
+     "+ kcond * g[d][3];",
+     "- kcond * g[d][3];"),
+    ("face_viscous_flux_one_sided",
+     "for (int v = 0; v < 5; ++v) Fv[v] = 0.5 * (Fa[v] + Fb[v]);",
+     "for (int v = 0; v < 5; ++v) Fv[v] = Fa[v];"),
+]
+
+
+@pytest.fixture(scope="module")
+def operator_libs():
+    with open(SRC) as f:
+        base = f.read()
+    texts = {"control": base}
+    for name, old, new in OPERATOR_MUTANTS:
+        assert base.count(old) == 1, name
+        texts[name] = base.replace(old, new)
+    with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
+        paths = dict(zip(texts, ex.map(_build, texts.values())))
+    return paths
+
+
+@pytest.fixture(scope="module")
+def mms_sources():
+    return mms_tests._mms_source(), mms_tests._mms_source(mu=0.0)
+
+
+@contextlib.contextmanager
+def _oracle_with(path):
+    """The oracle module with its FP64 library replaced by the build at path."""
+    saved = oracle._libs.get(False)
+    oracle._libs[False] = oracle.bind(path)
+    try:
+        yield oracle
+    finally:
+        if saved is None:
+            oracle._libs.pop(False, None)
+        else:
+            oracle._libs[False] = saved
+
+
+def _operator_checks(sources):
+    ns, euler = sources
+    return [
+        ("point-flux symmetry", lambda o: [test_consistency_and_symmetry(o, v, k) for v in (0, 1) for k in (0, 2)]),
+        ("metric identities", lambda o: inv.test_metric_identities(o, "sine", 3)),
+        ("free stream", lambda o: inv.test_free_stream_sine_mesh(o, 3, 2, 0.8)),
+        ("conservation", lambda o: [inv.test_discrete_conservation(o, vs, sf) for vs, sf in ((0, 1), (1, 2))]),
+        ("kinetic energy", lambda o: inv.test_kinetic_energy_preservation(o, 0)),
+        ("MMS Euler N=3", lambda o: mms_tests.test_manufactured_solution_convergence_euler(o, euler, 3)),
+        ("MMS Navier-Stokes N=3", lambda o: mms_tests.test_manufactured_solution_convergence(o, ns, 3)),
+        ("BR1 closed form N=3", lambda o: lifting.test_br1_piecewise_constant_temperature(o, 3)),
+    ]
+
+
+def _operator_failing(path, sources):
+    failed = []
+    with _oracle_with(path) as o:
+        for name, chk in _operator_checks(sources):
+            try:
+                chk(o)
+            except AssertionError:
+                failed.append(name)
+    return failed
+
+
+def test_operator_control_passes_every_pin(operator_libs, mms_sources):
+    assert _operator_failing(operator_libs["control"], mms_sources) == []
+
+
+@pytest.mark.parametrize("mutant", [m[0] for m in OPERATOR_MUTANTS])
+def test_planted_operator_mistake_is_caught(operator_libs, mms_sources, mutant):
+    failed = _operator_failing(operator_libs[mutant], mms_sources)
     print(mutant, "rejected by", failed)
     assert failed, mutant
