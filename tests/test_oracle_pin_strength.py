@@ -11,6 +11,11 @@ oracle's own compiler flags, and requires that at least one pin rejects it.
   energy), the point-flux symmetry, the manufactured-solution convergence
   and the BR1 closed form, run on the planted copy in place of the oracle's
   library.
+* The models (Sec. 3 wall model, Sec. 4 entropy-conserving flux, Sutherland's
+  law, LSERK4, the inflow / outflow and isothermal-wall boundaries): their
+  pins (Tadmor's condition, the air table, the LSERK4 order conditions, the
+  Van Driest chain and the isothermal wall's limits, free stream through the
+  boundaries and the energy balance).
 
 The unchanged source built the same way must pass all of them (the
 controls)."""
@@ -25,6 +30,9 @@ import numpy as np
 import pytest
 
 import oracle
+import test_oracle_basis as basis
+import test_oracle_boundaries as bnd
+import test_oracle_fluxes as fluxes
 import test_oracle_invariants as inv
 import test_oracle_lifting as lifting
 import test_oracle_mms as mms_tests
@@ -244,5 +252,100 @@ def test_operator_control_passes_every_pin(operator_libs, mms_sources):
 @pytest.mark.parametrize("mutant", [m[0] for m in OPERATOR_MUTANTS])
 def test_planted_operator_mistake_is_caught(operator_libs, mms_sources, mutant):
     failed = _operator_failing(operator_libs[mutant], mms_sources)
+    print(mutant, "rejected by", failed)
+    assert failed, mutant
+
+
+# ---------------------------------------------------------------------------
+# the models: entropy-conserving flux, Sutherland, LSERK4, wall model, boundaries
+# ---------------------------------------------------------------------------
+MODEL_MUTANTS = [
+    ("sutherland_ratio_inverted",
+     "return P.mu * x * sqrt(x) * (P.T_ref + P.suth_S) / (Tt + P.suth_S);",
+     "return P.mu * x * sqrt(x) * (Tt + P.suth_S) / (P.T_ref + P.suth_S);"),
+    ("logmean_wrong_denominator",
+     "return d / log1p(d / b);",
+     "return d / log1p(d / (a + b));"),
+    ("ec_energy_factor_two_dropped",
+     "F[4] = F[0] * (1.0 / (2.0 * (gamma - 1.0) * b_ln) - 0.5 * u2) + u[0] * F[1] + u[1] * F[2] + u[2] * F[3];",
+     "F[4] = F[0] * (1.0 / ((gamma - 1.0) * b_ln) - 0.5 * u2) + u[0] * F[1] + u[1] * F[2] + u[2] * F[3];"),
+    ("ec_pressure_arithmetic_mean",
+     "T pt = 0.5 * (L.rho + R.rho) / (bL + bR);",
+     "T pt = 0.5 * (L.p + R.p);"),
+    ("lserk4_coefficient_digit",
+     "5161836677717.0 / 13612068292357.0,",
+     "5161836677717.0 / 13612068292367.0,"),
+    ("wall_heat_flux_sign",
+     "if (P.T_wall > 0.0) *qw = -(cp / P.Pr) * tw * (Taw - Tw) / umag;",
+     "if (P.T_wall > 0.0) *qw = (cp / P.Pr) * tw * (Taw - Tw) / umag;"),
+    ("van_driest_transform_dropped",
+     "uvd = asin(a * umag) / a;",
+     "uvd = umag;"),
+    ("recovery_temperature_factor",
+     "T Taw = s.T_ + r * u2 / (2.0 * cp);",
+     "T Taw = s.T_ + r * u2 / cp;"),
+    ("wall_density_temperature_ratio_inverted",
+     "T rhow = s.rho * s.T_ / Tw;",
+     "T rhow = s.rho * Tw / s.T_;"),
+    ("reichardt_friction_velocity",
+     "if (law == LAW_REICHARDT) ut = exp(tT) * nu / h;",
+     "if (law == LAW_REICHARDT) ut = exp(tT) * h / nu;"),
+    ("outflow_energy_factor",
+     "Ub[4] = P.p_out / (P.gamma - 1.0) + 0.5 * (U[1] * U[1] + U[2] * U[2] + U[3] * U[3]) / U[0];",
+     "Ub[4] = P.p_out / P.gamma + 0.5 * (U[1] * U[1] + U[2] * U[2] + U[3] * U[3]) / U[0];"),
+]
+
+
+@pytest.fixture(scope="module")
+def model_libs():
+    with open(SRC) as f:
+        base = f.read()
+    texts = {"control": base}
+    for name, old, new in MODEL_MUTANTS:
+        assert base.count(old) == 1, name
+        texts[name] = base.replace(old, new)
+    with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
+        paths = dict(zip(texts, ex.map(_build, texts.values())))
+    return paths
+
+
+MODEL_CHECKS = [
+    ("Tadmor condition", lambda o: [fluxes.test_chandrashekar_entropy_conservation(o, c) for c in (False, True)]),
+    ("EC kinetic-energy form", lambda o: fluxes.test_chandrashekar_kinetic_energy_form(o)),
+    ("entropy conservation", lambda o: inv.test_entropy_conservation(o, 3)),
+    ("Sutherland air table", lambda o: fluxes.test_sutherland_air_table(o)),
+    ("LSERK4 order conditions", lambda o: basis.test_lserk4_order_conditions(o)),
+    ("Spalding as printed", lambda o: fluxes.test_spalding_as_printed(o)),
+    ("Reichardt limits", lambda o: fluxes.test_reichardt_limits(o)),
+    ("wall law solve", lambda o: [fluxes.test_wall_law_solve(o, law) for law in (0, 1)]),
+    ("Van Driest chain", lambda o: [fluxes.test_wall_flux_van_driest_chain(o, law, Ma)
+                                    for law in (0, 1) for Ma in (0.1, 0.8)]),
+    ("isothermal wall model", lambda o: [fluxes.test_isothermal_wall_model(o, law, 0.8) for law in (0, 1)]),
+    ("isothermal at recovery temperature", lambda o: fluxes.test_isothermal_wall_at_recovery_temperature_is_adiabatic(o)),
+    ("isothermal conduction limit", lambda o: fluxes.test_isothermal_wall_laminar_conduction_limit(o)),
+    ("free stream through inflow / outflow", lambda o: bnd.test_free_stream_with_inflow_outflow(o, 2, 3)),
+    ("boundary flux balance", lambda o: bnd.test_boundary_flux_balance(o, 2)),
+    ("energy balance, isothermal walls", lambda o: inv.test_energy_balance_with_isothermal_walls(o)),
+]
+
+
+def _model_failing(path):
+    failed = []
+    with _oracle_with(path) as o:
+        for name, chk in MODEL_CHECKS:
+            try:
+                chk(o)
+            except (AssertionError, RuntimeError):
+                failed.append(name)
+    return failed
+
+
+def test_model_control_passes_every_pin(model_libs):
+    assert _model_failing(model_libs["control"]) == []
+
+
+@pytest.mark.parametrize("mutant", [m[0] for m in MODEL_MUTANTS])
+def test_planted_model_mistake_is_caught(model_libs, mutant):
+    failed = _model_failing(model_libs[mutant])
     print(mutant, "rejected by", failed)
     assert failed, mutant
