@@ -16,6 +16,13 @@ oracle's own compiler flags, and requires that at least one pin rejects it.
   pins (Tadmor's condition, the air table, the LSERK4 order conditions, the
   Van Driest chain and the isothermal wall's limits, free stream through the
   boundaries and the energy balance).
+* The geometry, the basis and the derivatives (LGL weights and derivative
+  matrix, the curl-form metrics, the face normals, the Lagrange basis of the
+  wall samples, the dual numbers of the forward-mode derivative): the basis
+  closed forms and exactness, the metric identities and affine metrics, free
+  stream and conservation (also through inflow / outflow faces), the rotated
+  element frames, the wall-sample geometry and the JVP against central
+  differences.
 
 The unchanged source built the same way must pass all of them (the
 controls)."""
@@ -32,10 +39,13 @@ import pytest
 import oracle
 import test_oracle_basis as basis
 import test_oracle_boundaries as bnd
+import test_oracle_derivatives as deriv
 import test_oracle_fluxes as fluxes
 import test_oracle_invariants as inv
 import test_oracle_lifting as lifting
 import test_oracle_mms as mms_tests
+import test_oracle_orientation as orient
+import test_oracle_wall_samples as wsamp
 from test_oracle_fluxes import (check_roe_acoustic_wave, check_roe_linear_wave, check_roe_supersonic,
                                 test_consistency_and_symmetry)
 
@@ -347,5 +357,83 @@ def test_model_control_passes_every_pin(model_libs):
 @pytest.mark.parametrize("mutant", [m[0] for m in MODEL_MUTANTS])
 def test_planted_model_mistake_is_caught(model_libs, mutant):
     failed = _model_failing(model_libs[mutant])
+    print(mutant, "rejected by", failed)
+    assert failed, mutant
+
+
+# ---------------------------------------------------------------------------
+# geometry, basis, derivatives
+# ---------------------------------------------------------------------------
+GEOMETRY_MUTANTS = [
+    ("lgl_weight_power",
+     "w[i] = 2.0 / (N * (N + 1.0) * P * P);",
+     "w[i] = 2.0 / (N * (N + 1.0) * P);"),
+    ("derivative_matrix_barycentric_ratio",
+     "D[i * n + j] = (lam[j] / lam[i]) / (x[i] - x[j]);",
+     "D[i * n + j] = (lam[i] / lam[j]) / (x[i] - x[j]);"),
+    ("curl_metric_component_sign",
+     "ja[1 * 3 + nn] = -(dv[0][2] - dv[2][0]);",
+     "ja[1 * 3 + nn] = (dv[0][2] - dv[2][0]);"),
+    ("face_normal_orientation_dropped",
+     "for (int c = 0; c < 3; ++c) nh[c] = face_sign(ml) * ja[c] / ss;",
+     "for (int c = 0; c < 3; ++c) nh[c] = ja[c] / ss;"),
+    ("lagrange_basis_denominator",
+     "real f = (s - x[k]) / (x[j] - x[k]);",
+     "real f = (s - x[k]) / (x[j] + x[k]);"),
+    ("dual_sqrt_derivative",
+     "inline Dual sqrt(Dual a) { real s = std::sqrt(a.v); return Dual(s, a.d / (2.0 * s)); }",
+     "inline Dual sqrt(Dual a) { real s = std::sqrt(a.v); return Dual(s, a.d / s); }"),
+    ("dual_quotient_rule_sign",
+     "return Dual(r, (a.d - r * b.d) / b.v);",
+     "return Dual(r, (a.d + r * b.d) / b.v);"),
+]
+
+
+@pytest.fixture(scope="module")
+def geometry_libs():
+    with open(SRC) as f:
+        base = f.read()
+    texts = {"control": base}
+    for name, old, new in GEOMETRY_MUTANTS:
+        assert base.count(old) == 1, name
+        texts[name] = base.replace(old, new)
+    with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
+        paths = dict(zip(texts, ex.map(_build, texts.values())))
+    return paths
+
+
+GEOMETRY_CHECKS = [
+    ("LGL closed forms", lambda o: basis.test_lgl_closed_forms(o, 3)),
+    ("quadrature and derivative exactness", lambda o: basis.test_lgl_quadrature_and_derivative_exactness(o, 5)),
+    ("summation by parts", lambda o: basis.test_summation_by_parts(o, 3)),
+    ("metric identities", lambda o: inv.test_metric_identities(o, "sine", 3)),
+    ("affine metrics", lambda o: inv.test_affine_metrics_closed_form(o)),
+    ("free stream", lambda o: inv.test_free_stream_sine_mesh(o, 3, 2, 0.8)),
+    ("conservation", lambda o: inv.test_discrete_conservation(o, 1, 2)),
+    ("wall samples", lambda o: wsamp.test_channel_wall_samples(o, 3)),
+    ("JVP vs central differences", lambda o: deriv.test_jvp_matches_central_differences_tgv(o, 2)),
+    ("free stream through inflow / outflow", lambda o: bnd.test_free_stream_with_inflow_outflow(o, 2, 3)),
+    ("rotated element frames", lambda o: orient.test_free_stream_and_conservation_on_rotated_mesh(o)),
+]
+
+
+def _geometry_failing(path):
+    failed = []
+    with _oracle_with(path) as o:
+        for name, chk in GEOMETRY_CHECKS:
+            try:
+                chk(o)
+            except (AssertionError, ValueError, RuntimeError):
+                failed.append(name)
+    return failed
+
+
+def test_geometry_control_passes_every_pin(geometry_libs):
+    assert _geometry_failing(geometry_libs["control"]) == []
+
+
+@pytest.mark.parametrize("mutant", [m[0] for m in GEOMETRY_MUTANTS])
+def test_planted_geometry_mistake_is_caught(geometry_libs, mutant):
+    failed = _geometry_failing(geometry_libs[mutant])
     print(mutant, "rejected by", failed)
     assert failed, mutant
