@@ -151,6 +151,41 @@ def test_roe_acoustic_waves_subsonic(ora, family):
     check_roe_acoustic_wave(ora.riemann, family)
 
 
+def check_roe_entropy_fix(riemann, family):
+    # an acoustic jump UR = UL + eps r (as above) whose wave speed
+    # lambda = u_n +- c lies inside Harten's band |lambda| < delta = c / 10:
+    # the dissipation is |lambda|_fixed (UR - UL) / 2 to first order with
+    # |lambda|_fixed = (lambda^2 + delta^2) / (2 delta)  (paper Sec. 4: Roe
+    # with Harten's entropy fix; the band width is the reading stated in the
+    # oracle's Roe solver)
+    phys = I.phys_params()
+    g = 1.4
+    rng = np.random.default_rng(9)
+    eps = 1e-7
+    for _ in range(20):
+        n = _rand_unit(rng)
+        rho, p = rng.uniform(0.8, 1.2), rng.uniform(0.8, 1.2)
+        c = math.sqrt(g * p / rho)
+        lam = rng.uniform(-0.09, 0.09) * c
+        un = lam - family * c
+        u = un * n + 0.2 * c * np.cross(n, _rand_unit(rng))
+        UL = _state(rho, u, p)
+        H = (UL[4] + p) / rho
+        r = np.array([1.0, *(u + family * c * n), H + family * c * un])
+        UR = UL + eps * r
+        Froe = riemann(phys, 0, 2, UL, UR, n)
+        Fc = riemann(phys, 0, 0, UL, UR, n)
+        delta = 0.1 * c
+        fixed = (lam * lam + delta * delta) / (2 * delta)
+        expect = -0.5 * fixed * (UR - UL)
+        assert np.allclose(Froe - Fc, expect, rtol=1e-4, atol=1e-4 * np.abs(expect).max())
+
+
+@pytest.mark.parametrize("family", [-1.0, 1.0])
+def test_roe_entropy_fix_inside_the_band(ora, family):
+    check_roe_entropy_fix(ora.riemann, family)
+
+
 def test_llf_dissipation_bounds(ora):
     # LLF dissipation: the upwind flux of a supersonic pair is bracketed
     phys = I.phys_params()

@@ -5,7 +5,7 @@ oracle's own compiler flags, and requires that at least one pin rejects it.
 
 * Roe solver (paper Sec. 4: Roe with Harten's entropy fix): the pins of
   `test_oracle_fluxes` (Roe's property on supersonic states, the single-wave
-  dissipations on subsonic states).
+  dissipations on subsonic states, the fixed wave speed inside Harten's band).
 * The operator (Sec. 2.2: split-form DGSEM, BR1 lifting, viscous fluxes):
   the invariants (metric identities, free stream, conservation, kinetic
   energy), the point-flux symmetry, the manufactured-solution convergence
@@ -46,8 +46,8 @@ import test_oracle_lifting as lifting
 import test_oracle_mms as mms_tests
 import test_oracle_orientation as orient
 import test_oracle_wall_samples as wsamp
-from test_oracle_fluxes import (check_roe_acoustic_wave, check_roe_linear_wave, check_roe_supersonic,
-                                test_consistency_and_symmetry)
+from test_oracle_fluxes import (check_roe_acoustic_wave, check_roe_entropy_fix, check_roe_linear_wave,
+                                check_roe_supersonic, test_consistency_and_symmetry)
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "dgsem_oracle.cpp")
@@ -79,6 +79,12 @@ MUTANTS = [
     ("roe_average_weights_swapped",
      "T Ht = (sL * L.h + sR * R.h) / (sL + sR);",
      "T Ht = (sR * L.h + sL * R.h) / (sL + sR);"),
+    ("harten_band_width",
+     "T delta = 0.1 * ct;",
+     "T delta = 0.2 * ct;"),
+    ("harten_fixed_speed_factor",
+     "if (val(l5) < val(delta)) l5 = (l5 * l5 + delta * delta) / (2.0 * delta);",
+     "if (val(l5) < val(delta)) l5 = (l5 * l5 + delta * delta) / delta;"),
 ]
 
 
@@ -134,6 +140,8 @@ CHECKS = [
     ("shear", lambda r: check_roe_linear_wave(r, "shear")),
     ("acoustic -", lambda r: check_roe_acoustic_wave(r, -1.0)),
     ("acoustic +", lambda r: check_roe_acoustic_wave(r, 1.0)),
+    ("entropy fix -", lambda r: check_roe_entropy_fix(r, -1.0)),
+    ("entropy fix +", lambda r: check_roe_entropy_fix(r, 1.0)),
 ]
 
 
