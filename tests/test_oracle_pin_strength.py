@@ -311,6 +311,18 @@ MODEL_MUTANTS = [
     ("outflow_energy_factor",
      "Ub[4] = P.p_out / (P.gamma - 1.0) + 0.5 * (U[1] * U[1] + U[2] * U[2] + U[3] * U[3]) / U[0];",
      "Ub[4] = P.p_out / P.gamma + 0.5 * (U[1] * U[1] + U[2] * U[2] + U[3] * U[3]) / U[0];"),
+    ("llf_minimum_speed",
+     "T lam = val(lamL) >= val(lamR) ? lamL : lamR;",
+     "T lam = val(lamL) >= val(lamR) ? lamR : lamL;"),
+    ("kennedy_gruber_pressure_work_dropped",
+     "F[4] = rho * ua * e + p * ua;",
+     "F[4] = rho * ua * e;"),
+    ("slip_wall_mirror_factor",
+     "for (int c = 0; c < 3; ++c) Ub[1 + c] = U[1 + c] - 2.0 * mn * nh[c];",
+     "for (int c = 0; c < 3; ++c) Ub[1 + c] = U[1 + c] - mn * nh[c];"),
+    ("wall_sample_outward",
+     "xs[c] = M.X[(size_t)c * K * n3 + (size_t)e * n3 + p] - hwm * nout;",
+     "xs[c] = M.X[(size_t)c * K * n3 + (size_t)e * n3 + p] + hwm * nout;"),
 ]
 
 
@@ -344,6 +356,10 @@ MODEL_CHECKS = [
     ("free stream through inflow / outflow", lambda o: bnd.test_free_stream_with_inflow_outflow(o, 2, 3)),
     ("boundary flux balance", lambda o: bnd.test_boundary_flux_balance(o, 2)),
     ("energy balance, isothermal walls", lambda o: inv.test_energy_balance_with_isothermal_walls(o)),
+    ("LLF dissipation bounds", lambda o: fluxes.test_llf_dissipation_bounds(o)),
+    ("point-flux consistency", lambda o: [test_consistency_and_symmetry(o, v, k) for v in (0, 1, 2) for k in (0, 1, 2)]),
+    ("free stream, walled channel", lambda o: inv.test_free_stream_channel_mesh(o, 3)),
+    ("wall samples", lambda o: wsamp.test_channel_wall_samples(o, 3)),
 ]
 
 
@@ -353,7 +369,7 @@ def _model_failing(path):
         for name, chk in MODEL_CHECKS:
             try:
                 chk(o)
-            except (AssertionError, RuntimeError):
+            except (AssertionError, RuntimeError, ValueError):
                 failed.append(name)
     return failed
 
