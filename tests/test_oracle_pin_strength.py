@@ -18,11 +18,13 @@ oracle's own compiler flags, and requires that at least one pin rejects it.
   boundaries and the energy balance).
 * The geometry, the basis and the derivatives (LGL weights and derivative
   matrix, the curl-form metrics, the face normals, the Lagrange basis of the
-  wall samples, the dual numbers of the forward-mode derivative): the basis
-  closed forms and exactness, the metric identities and affine metrics, free
-  stream and conservation (also through inflow / outflow faces), the rotated
-  element frames, the wall-sample geometry and the JVP against central
-  differences.
+  wall samples, the dual numbers of the forward-mode derivative, the
+  implicit-function-theorem derivative of the wall-law solve, the LSERK4
+  register update): the basis closed forms and exactness, the metric
+  identities and affine metrics, free stream and conservation (also through
+  inflow / outflow faces), the rotated element frames, the wall-sample
+  geometry, the JVPs against central differences (state, wall-law
+  constants, a rollout's loss) and the temporal order of LSERK4.
 
 The unchanged source built the same way must pass all of them (the
 controls)."""
@@ -410,6 +412,12 @@ GEOMETRY_MUTANTS = [
     ("dual_quotient_rule_sign",
      "return Dual(r, (a.d - r * b.d) / b.v);",
      "return Dual(r, (a.d + r * b.d) / b.v);"),
+    ("implicit_function_theorem_sign",
+     "tT = T(t) - (FT - T(val(FT))) / Ft_t;",
+     "tT = T(t) + (FT - T(val(FT))) / Ft_t;"),
+    ("lserk4_register_update_order",
+     "dU[x] = RK_A[s] * dU[x] + dt * Ut[x];",
+     "dU[x] = RK_B[s] * dU[x] + dt * Ut[x];"),
 ]
 
 
@@ -438,6 +446,9 @@ GEOMETRY_CHECKS = [
     ("JVP vs central differences", lambda o: deriv.test_jvp_matches_central_differences_tgv(o, 2)),
     ("free stream through inflow / outflow", lambda o: bnd.test_free_stream_with_inflow_outflow(o, 2, 3)),
     ("rotated element frames", lambda o: orient.test_free_stream_and_conservation_on_rotated_mesh(o)),
+    ("JVP of the wall-law constants", lambda o: deriv.test_jvp_wall_model_parameters(o, 1)),
+    ("rollout loss derivative", lambda o: deriv.test_rollout_loss_derivative(o)),
+    ("LSERK4 temporal order", lambda o: deriv.test_lserk4_temporal_order(o)),
 ]
 
 
