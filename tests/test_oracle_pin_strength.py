@@ -25,6 +25,11 @@ oracle's own compiler flags, and requires that at least one pin rejects it.
   inflow / outflow faces), the rotated element frames, the wall-sample
   geometry, the JVPs against central differences (state, wall-law
   constants, a rollout's loss) and the temporal order of LSERK4.
+* General conforming meshes (the face node maps of the orientation codes):
+  rotated element frames against the structured mesh, free stream,
+  conservation and the wall model across rotated elements, and the
+  rejection of inconsistent connectivity (built in both arithmetics, since
+  those pins run the extended build).
 
 The unchanged source built the same way must pass all of them (the
 controls)."""
@@ -90,17 +95,18 @@ MUTANTS = [
 ]
 
 
-def _build(text):
+def _build(text, extended=False):
     os.makedirs(OUT, exist_ok=True)
-    tag = hashlib.sha1(text.encode()).hexdigest()[:16]
+    tag = hashlib.sha1(text.encode()).hexdigest()[:16] + ("_ext" if extended else "")
     lib = os.path.join(OUT, "libora_%s.so" % tag)
     if not os.path.exists(lib):
         src = os.path.join(OUT, "ora_%s.cpp" % tag)
         with open(src, "w") as f:
             f.write(text)
         tmp = lib + ".tmp%d" % os.getpid()
-        subprocess.check_call(["g++", "-std=c++17", "-O2", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
-                               src, "-o", tmp])
+        defines = ["-DORA_REAL=long double"] if extended else []
+        subprocess.check_call(["g++", "-std=c++17", "-O2", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared"] +
+                              defines + [src, "-o", tmp])
         os.replace(tmp, lib)
     return lib
 
@@ -470,5 +476,84 @@ def test_geometry_control_passes_every_pin(geometry_libs):
 @pytest.mark.parametrize("mutant", [m[0] for m in GEOMETRY_MUTANTS])
 def test_planted_geometry_mistake_is_caught(geometry_libs, mutant):
     failed = _geometry_failing(geometry_libs[mutant])
+    print(mutant, "rejected by", failed)
+    assert failed, mutant
+
+
+# ---------------------------------------------------------------------------
+# general conforming meshes: face maps and orientations (their pins compare
+# rotated meshes with the structured one in the extended build, so the
+# planted copies are built in both arithmetics)
+# ---------------------------------------------------------------------------
+ORIENTATION_MUTANTS = [
+    ("orientation_flip_bits_swapped",
+     "const int a2 = (o & 2) ? M.N - s : s, b2 = (o & 4) ? M.N - t : t;",
+     "const int a2 = (o & 4) ? M.N - s : s, b2 = (o & 2) ? M.N - t : t;"),
+    ("orientation_transpose_inverted",
+     "const int s = (o & 1) ? b : a, t = (o & 1) ? a : b;",
+     "const int s = (o & 1) ? a : b, t = (o & 1) ? b : a;"),
+    ("orientation_inverse_identity",
+     "return (o & 1) ? (1 | (((o >> 2) & 1) << 1) | (((o >> 1) & 1) << 2)) : o;",
+     "return o;"),
+]
+
+
+@pytest.fixture(scope="module")
+def orientation_libs():
+    with open(SRC) as f:
+        base = f.read()
+    texts = {"control": base}
+    for name, old, new in ORIENTATION_MUTANTS:
+        assert base.count(old) == 1, name
+        texts[name] = base.replace(old, new)
+    jobs = [(name, text, ext) for name, text in texts.items() for ext in (False, True)]
+    with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
+        built = list(ex.map(lambda j: _build(j[1], j[2]), jobs))
+    paths = {}
+    for (name, _, ext), path in zip(jobs, built):
+        paths.setdefault(name, {})[ext] = path
+    return paths
+
+
+@contextlib.contextmanager
+def _oracle_with_both(paths):
+    """The oracle module with both of its libraries replaced."""
+    saved = dict(oracle._libs)
+    oracle._libs[False] = oracle.bind(paths[False])
+    oracle._libs[True] = oracle.bind(paths[True])
+    try:
+        yield oracle
+    finally:
+        oracle._libs.clear()
+        oracle._libs.update(saved)
+
+
+ORIENTATION_CHECKS = [
+    ("rotated frames give the structured operator",
+     lambda o: orient.test_rotated_frames_give_the_structured_operator(o, 3, 2, 1)),
+    ("free stream and conservation, rotated mesh", lambda o: orient.test_free_stream_and_conservation_on_rotated_mesh(o)),
+    ("wall model across rotated elements", lambda o: orient.test_wall_model_across_rotated_elements(o, 1)),
+    ("inconsistent connectivity rejected", lambda o: orient.test_inconsistent_connectivity_is_rejected(o)),
+]
+
+
+def _orientation_failing(paths):
+    failed = []
+    with _oracle_with_both(paths) as o:
+        for name, chk in ORIENTATION_CHECKS:
+            try:
+                chk(o)
+            except (AssertionError, ValueError, RuntimeError):
+                failed.append(name)
+    return failed
+
+
+def test_orientation_control_passes_every_pin(orientation_libs):
+    assert _orientation_failing(orientation_libs["control"]) == []
+
+
+@pytest.mark.parametrize("mutant", [m[0] for m in ORIENTATION_MUTANTS])
+def test_planted_orientation_mistake_is_caught(orientation_libs, mutant):
+    failed = _orientation_failing(orientation_libs[mutant])
     print(mutant, "rejected by", failed)
     assert failed, mutant
