@@ -9,8 +9,8 @@ oracle's own compiler flags, and requires that at least one pin rejects it.
 * The operator (Sec. 2.2: split-form DGSEM, BR1 lifting, viscous fluxes):
   the invariants (metric identities, free stream, conservation, kinetic
   energy), the point-flux symmetry, the manufactured-solution convergence
-  and the BR1 closed form, run on the planted copy in place of the oracle's
-  library.
+  and the BR1 closed forms (temperature and shear), run on the planted copy
+  in place of the oracle's library.
 * The models (Sec. 3 wall model, Sec. 4 entropy-conserving flux, Sutherland's
   law, LSERK4, the inflow / outflow and isothermal-wall boundaries): their
   pins (Tadmor's condition, the air table, the LSERK4 order conditions, the
@@ -257,6 +257,7 @@ def _operator_checks(sources):
         ("MMS Euler N=3", lambda o: mms_tests.test_manufactured_solution_convergence_euler(o, euler, 3)),
         ("MMS Navier-Stokes N=3", lambda o: mms_tests.test_manufactured_solution_convergence(o, ns, 3)),
         ("BR1 closed form N=3", lambda o: lifting.test_br1_piecewise_constant_temperature(o, 3)),
+        ("BR1 shear closed form N=3", lambda o: lifting.test_br1_piecewise_constant_shear(o, 3)),
     ]
 
 
